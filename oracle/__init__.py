@@ -1,0 +1,289 @@
+"""FP64 CPU oracle for QV-Tree Search -- test infrastructure only.
+
+Only the test suite, the package smoke check and the benchmark's CPU-baseline
+leg may import this package.  It wraps `qv_oracle.c` (plain C, FP64) through
+ctypes and shares nothing with the CUDA library: its own build, its own
+loader, its own unpadded [H][W] layout.  Inputs come from
+`paper_1810_00204_gb300.workloads` (seeded generators, no method arithmetic).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qv_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+FREQ, MARGINAL = 0, 1
+A = 5
+
+
+def build(force: bool = False) -> str:
+    """Compile qv_oracle.c into liboracle.so (gcc, OpenMP over tree nodes)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "qv_oracle.h"))):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Problem(C.Structure):
+    _fields_ = [("H", C.c_int), ("W", C.c_int), ("occ", C.c_void_p), ("B", C.c_int),
+                ("beacon", C.c_void_p), ("range", C.c_int), ("goal", C.c_int),
+                ("slip", C.c_double), ("acc", C.c_double), ("gamma", C.c_double),
+                ("cost", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB_PATH)
+        P = C.POINTER(_Problem)
+        vp = C.c_void_p
+        L.or_labels.argtypes = [P, vp]
+        L.or_transition_row.argtypes = [P, C.c_int, C.c_int, vp, vp]
+        L.or_transition_row.restype = C.c_int
+        L.or_reward_table.argtypes = [P, vp]
+        L.or_value_iteration.argtypes = [P, C.c_double, C.c_int, C.c_int, vp, vp, vp, vp, vp]
+        L.or_value_iteration.restype = C.c_int
+        L.or_predict.argtypes = [P, vp, C.c_int, vp]
+        L.or_obs_marginal.argtypes = [P, vp, vp, vp]
+        L.or_correct.argtypes = [P, vp, vp, C.c_int, vp]
+        L.or_correct.restype = C.c_double
+        L.or_belief_reward.argtypes = [P, vp, vp, C.c_int]
+        L.or_belief_reward.restype = C.c_double
+        L.or_leaf_value.argtypes = [P, vp, vp, vp]
+        L.or_leaf_value.restype = C.c_double
+        L.or_philox4x32_10.argtypes = [vp, vp, vp]
+        L.or_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_uint64, C.c_int]
+        L.or_uniform.restype = C.c_float
+        L.or_sample_obs.argtypes = [vp, C.c_int, C.c_float]
+        L.or_sample_obs.restype = C.c_int
+        L.or_is_boundary.argtypes = [vp, C.c_int, C.c_float]
+        L.or_is_boundary.restype = C.c_int
+        L.or_tree_plan.argtypes = [P, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int,
+                                   vp, vp, C.c_int] + [vp] * 16
+        L.or_tree_plan.restype = C.c_int
+        L.or_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Problem:
+    """The model tuple of Sec. II built from a Workload (arrays kept alive)."""
+
+    def __init__(self, w, slip=None, accuracy=None, cost="workload"):
+        self.w = w
+        self.H, self.W = w.H, w.W
+        self.n = w.H * w.W
+        self.B = w.B
+        self.occ = np.ascontiguousarray(w.occ.reshape(-1), np.uint8)
+        self.beacons = np.ascontiguousarray(w.beacons, np.int32)
+        c = w.cost if isinstance(cost, str) else cost
+        self.cost = None if c is None else np.ascontiguousarray(np.asarray(c, np.float64).reshape(-1))
+        self.slip = w.slip if slip is None else slip
+        self.acc = w.accuracy if accuracy is None else accuracy
+        self.s = _Problem(self.H, self.W, self.occ.ctypes.data, self.B, self.beacons.ctypes.data,
+                          w.sense_range, w.goal, self.slip, self.acc, w.discount,
+                          None if self.cost is None else self.cost.ctypes.data)
+        self.ref = C.byref(self.s)
+
+
+def _prob(w, **kw):
+    return w if isinstance(w, Problem) else Problem(w, **kw)
+
+
+def labels(w):
+    p = _prob(w)
+    out = np.zeros(p.n, np.int32)
+    lib().or_labels(p.ref, _p(out))
+    return out
+
+
+def transition_row(w, x, a):
+    p = _prob(w)
+    y = np.zeros(4, np.int32)
+    pr = np.zeros(4, np.float64)
+    m = lib().or_transition_row(p.ref, int(x), int(a), _p(y), _p(pr))
+    return {int(y[i]): float(pr[i]) for i in range(m)}
+
+
+def reward_table(w):
+    p = _prob(w)
+    R = np.zeros(A * p.n, np.float64)
+    lib().or_reward_table(p.ref, _p(R))
+    return R.reshape(A, p.n)
+
+
+def value_iteration(w, tol=None, max_sweeps=100000, truncated=None, **kw):
+    """Returns dict(V [n], Q [5][n], sweeps, residual, hist, converged)."""
+    p = _prob(w, **kw)
+    ww = p.w
+    tol = ww.vi_tol if tol is None else tol
+    truncated = ww.vi_truncated if truncated is None else truncated
+    V = np.zeros(p.n, np.float64)
+    Q = np.zeros(A * p.n, np.float64)
+    sw = C.c_int(0)
+    res = C.c_double(0)
+    hist = np.zeros(max(truncated, max_sweeps) + 1, np.float64)
+    st = lib().or_value_iteration(p.ref, tol, max_sweeps, truncated, _p(V), _p(Q),
+                                  C.byref(sw), C.byref(res), _p(hist))
+    return dict(V=V, Q=Q.reshape(A, p.n), sweeps=sw.value, residual=res.value,
+                hist=hist[:sw.value].copy(), converged=(st == 0))
+
+
+def predict(w, b, a):
+    p = _prob(w)
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    out = np.zeros(p.n, np.float64)
+    lib().or_predict(p.ref, _p(b), int(a), _p(out))
+    return out
+
+
+def obs_marginal(w, bbar, label=None):
+    p = _prob(w)
+    label = labels(p) if label is None else label
+    bbar = np.ascontiguousarray(np.asarray(bbar, np.float64).reshape(-1))
+    P = np.zeros(p.B + 1, np.float64)
+    lib().or_obs_marginal(p.ref, _p(label), _p(bbar), _p(P))
+    return P
+
+
+def correct(w, bbar, z, label=None):
+    """Returns (b', P(z))."""
+    p = _prob(w)
+    label = labels(p) if label is None else label
+    bbar = np.ascontiguousarray(np.asarray(bbar, np.float64).reshape(-1))
+    out = np.zeros(p.n, np.float64)
+    pz = lib().or_correct(p.ref, _p(label), _p(bbar), int(z), _p(out))
+    return out, pz
+
+
+def belief_reward(w, b, a, R=None):
+    p = _prob(w)
+    R = reward_table(p) if R is None else R
+    R = np.ascontiguousarray(R, np.float64)
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    return lib().or_belief_reward(p.ref, _p(R), _p(b), int(a))
+
+
+def leaf_value(w, Q, b):
+    p = _prob(w)
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(A, p.n))
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    qa = np.zeros(A, np.float64)
+    v = lib().or_leaf_value(p.ref, _p(Q), _p(b), _p(qa))
+    return v, qa
+
+
+def philox(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def uniform(seed, episode, level, path, k):
+    return lib().or_uniform(seed, episode, level, path, k)
+
+
+def sample_obs(P, u):
+    P = np.ascontiguousarray(P, np.float64)
+    return lib().or_sample_obs(_p(P), len(P), float(u))
+
+
+def is_boundary(P, u):
+    P = np.ascontiguousarray(P, np.float64)
+    return bool(lib().or_is_boundary(_p(P), len(P), float(u)))
+
+
+def level_capacity(B, K, depth):
+    """Worst-case V-nodes per level: (5 * min(K, B+1))^l."""
+    m = A * min(K, B + 1)
+    return [m ** l for l in range(depth + 1)]
+
+
+def tree_plan(w, Q, depth=None, K=None, seed=None, episode=None, weight_mode=FREQ,
+              replay=None, store_levels=-1, b0=None, caps=None, **kw):
+    """Level-synchronous QV-tree (Alg. 2-7).  Returns a dict with per-level
+    arrays (lists indexed by level) and the root action / value / Q."""
+    p = _prob(w, **kw)
+    ww = p.w
+    depth = ww.depth if depth is None else depth
+    K = ww.K if K is None else K
+    seed = ww.seed if seed is None else seed
+    episode = ww.episode if episode is None else episode
+    caps = level_capacity(p.B, K, depth) if caps is None else caps
+    off = np.zeros(depth + 2, np.int64)
+    off[1:] = np.cumsum(caps)
+    tot = int(off[-1])
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(A, p.n))
+    b0 = ww.b0 if b0 is None else b0
+    b0 = np.ascontiguousarray(np.asarray(b0, np.float64).reshape(-1))
+    n_level = np.zeros(depth + 1, np.int32)
+    parent = np.full(tot, -1, np.int32)
+    action = np.full(tot, -1, np.int32)
+    obs = np.full(tot, -1, np.int32)
+    weight = np.zeros(tot, np.float64)
+    pz = np.zeros(tot, np.float64)
+    value = np.zeros(tot, np.float64)
+    R = np.zeros(tot * A, np.float64)
+    UQ = np.zeros(tot * A, np.float64)
+    samples = np.full(tot * A * K, -1, np.int32)
+    boundary = np.zeros(tot * A * K, np.uint8)
+    belief = None
+    if store_levels >= 0:
+        nst = int(off[min(store_levels, depth) + 1])
+        belief = np.zeros(nst * p.n, np.float64)
+    if replay is not None:
+        replay = np.ascontiguousarray(replay, np.int32)
+    ra = C.c_int(0)
+    rv = C.c_double(0)
+    rq = np.zeros(A, np.float64)
+    bc = C.c_long(0)
+    st = lib().or_tree_plan(
+        p.ref, _p(Q), _p(b0), depth, K, seed, episode, weight_mode,
+        None if replay is None else _p(replay), _p(off), store_levels,
+        _p(n_level), _p(parent), _p(action), _p(obs), _p(weight), _p(pz), _p(value),
+        _p(R), _p(UQ), _p(samples), _p(boundary),
+        None if belief is None else _p(belief), C.byref(ra), C.byref(rv), _p(rq), C.byref(bc))
+    if st != 0:
+        raise RuntimeError("oracle tree exceeded its level capacity")
+    out = dict(root_action=ra.value, root_value=rv.value, root_q=rq, boundary_count=bc.value,
+               n_level=n_level.copy(), off=off, depth=depth, K=K,
+               samples_flat=samples, boundary_flat=boundary)
+    lv = {k: [] for k in ("parent", "action", "obs", "weight", "pz", "value", "R", "UQ",
+                          "samples", "boundary", "belief")}
+    for l in range(depth + 1):
+        s, n = int(off[l]), int(n_level[l])
+        lv["parent"].append(parent[s:s + n])
+        lv["action"].append(action[s:s + n])
+        lv["obs"].append(obs[s:s + n])
+        lv["weight"].append(weight[s:s + n])
+        lv["pz"].append(pz[s:s + n])
+        lv["value"].append(value[s:s + n])
+        lv["R"].append(R[s * A:(s + n) * A].reshape(n, A))
+        lv["UQ"].append(UQ[s * A:(s + n) * A].reshape(n, A))
+        lv["samples"].append(samples[s * A * K:(s + n) * A * K].reshape(n, A, K))
+        lv["boundary"].append(boundary[s * A * K:(s + n) * A * K].reshape(n, A, K))
+        if belief is not None and l <= store_levels:
+            lv["belief"].append(belief[s * p.n:(s + n) * p.n].reshape(n, p.n))
+    out.update(lv)
+    return out
+
+
+def num_threads():
+    return lib().or_num_threads()

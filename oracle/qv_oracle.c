@@ -1,0 +1,441 @@
+/*
+ * qv_oracle.c -- plain, slow FP64 CPU reference for QV-Tree Search.
+ *
+ * Test infrastructure: only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg use this file.  Every function follows one
+ * passage of the paper (cited beside it) without blocking, fusion or
+ * reordering beyond what that passage states.  Where the paper is silent the
+ * reading taken is stated in the comment.
+ */
+#include "qv_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static const int DR[4] = {-1, 0, 1, 0};  /* N E S W: row step */
+static const int DC[4] = {0, 1, 0, -1};  /*          col step */
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static int is_free(const or_problem *p, int r, int c) {
+    if (r < 0 || r >= p->H || c < 0 || c >= p->W) return 0;  /* outside = occupied */
+    return p->occ[r * p->W + c] == 0;
+}
+
+/* Stage reward r(y) of arriving in y.  Reading of the paper's r(x) (Sec. V)
+ * with this workload's values: +100 at the goal, -1 - c(y) elsewhere.      */
+static double stage_reward(const or_problem *p, int y) {
+    if (y == p->goal) return 100.0;
+    return -1.0 - (p->cost ? p->cost[y] : 0.0);
+}
+
+/* Observation label: nearest beacon by Manhattan distance within range,
+ * ties to the lower id; none in range -> the null observation B.          */
+void or_labels(const or_problem *p, int *label) {
+    for (int r = 0; r < p->H; ++r)
+        for (int c = 0; c < p->W; ++c) {
+            int best = p->B, bestd = 1 << 30;
+            for (int k = 0; k < p->B; ++k) {
+                int br = p->beacon[k] / p->W, bc = p->beacon[k] % p->W;
+                int d = abs(br - r) + abs(bc - c);
+                if (d <= p->range && d < bestd) { best = k; bestd = d; }
+            }
+            label[r * p->W + c] = best;
+        }
+}
+
+/* T(x, a, .) -- Sec. II dynamics with Eq. 10: the mass aimed at an occupied
+ * (or outside) cell y is added to T(x, a, x).  Free-space kernel T': the
+ * intended move w.p. 1 - 2 eps, each perpendicular move w.p. eps; stay is
+ * deterministic.  Occupied cells and the goal are absorbing.              */
+int or_transition_row(const or_problem *p, int x, int a, int *y, double *pr) {
+    int n = 0;
+    if (p->occ[x] || x == p->goal || a == 4) {
+        y[0] = x; pr[0] = 1.0;
+        return 1;
+    }
+    int r = x / p->W, c = x % p->W;
+    int dirs[3] = {a, (a + 1) % 4, (a + 3) % 4};
+    double w[3] = {1.0 - 2.0 * p->slip, p->slip, p->slip};
+    for (int i = 0; i < 3; ++i) {
+        int rr = r + DR[dirs[i]], cc = c + DC[dirs[i]];
+        int t = is_free(p, rr, cc) ? rr * p->W + cc : x;   /* Eq. 10 */
+        int j;
+        for (j = 0; j < n; ++j)
+            if (y[j] == t) { pr[j] += w[i]; break; }
+        if (j == n) { y[n] = t; pr[n] = w[i]; ++n; }
+    }
+    return n;
+}
+
+/* R(x, a) = sum_y T(x, a, y) r(y) (Sec. V, the reward through the transition
+ * model); the goal and occupied cells earn nothing.                       */
+void or_reward_table(const or_problem *p, double *R) {
+    int n = p->H * p->W;
+    for (int a = 0; a < OR_NUM_ACTIONS; ++a)
+        for (int x = 0; x < n; ++x) {
+            double s = 0.0;
+            if (!p->occ[x] && x != p->goal) {
+                int y[3]; double pr[3];
+                int m = or_transition_row(p, x, a, y, pr);
+                for (int j = 0; j < m; ++j) s += pr[j] * stage_reward(p, y[j]);
+            }
+            R[a * n + x] = s;
+        }
+}
+
+/* O(x', z): alpha for the cell's own label, eta = (1 - alpha)/B otherwise. */
+double or_obs_lik(const or_problem *p, const int *label, int x, int z) {
+    double eta = (1.0 - p->acc) / (double)p->B;
+    return label[x] == z ? p->acc : eta;
+}
+
+/* MDP value iteration (Sec. V-B baseline; Bellman operator of Eq. 2 with a
+ * known state): V_{k+1}(x) = max_a [R(x,a) + gamma sum_y T(x,a,y) V_k(y)],
+ * Jacobi sweeps from V_0 = 0, V(goal) = 0, occupied cells 0.  The result Q is
+ * R + gamma T V_final, the QMDP alpha-vectors used at the leaves (Eq. 4). */
+int or_value_iteration(const or_problem *p, double tol, int max_sweeps, int truncated,
+                       double *V, double *Q, int *sweeps, double *residual,
+                       double *residual_hist) {
+    int n = p->H * p->W;
+    double *R = (double *)malloc(sizeof(double) * 5 * n);
+    double *Vn = (double *)malloc(sizeof(double) * n);
+    or_reward_table(p, R);
+    for (int x = 0; x < n; ++x) V[x] = 0.0;
+    int k = 0, status = 1;
+    double res = 0.0;
+    int limit = truncated > 0 ? truncated : max_sweeps;
+    while (k < limit) {
+        res = 0.0;
+        for (int x = 0; x < n; ++x) {
+            if (p->occ[x] || x == p->goal) { Vn[x] = 0.0; continue; }
+            double best = -HUGE_VAL;
+            for (int a = 0; a < OR_NUM_ACTIONS; ++a) {
+                int y[3]; double pr[3];
+                int m = or_transition_row(p, x, a, y, pr);
+                double s = 0.0;
+                for (int j = 0; j < m; ++j) s += pr[j] * V[y[j]];
+                double q = R[a * n + x] + p->gamma * s;
+                if (q > best) best = q;
+            }
+            Vn[x] = best;
+            double d = fabs(best - V[x]);
+            if (d > res) res = d;
+        }
+        memcpy(V, Vn, sizeof(double) * n);
+        if (residual_hist) residual_hist[k] = res;
+        ++k;
+        if (truncated <= 0 && res < tol) { status = 0; break; }
+    }
+    if (truncated > 0) status = 0;
+    for (int a = 0; a < OR_NUM_ACTIONS; ++a)
+        for (int x = 0; x < n; ++x) {
+            if (p->occ[x] || x == p->goal) { Q[a * n + x] = 0.0; continue; }
+            int y[3]; double pr[3];
+            int m = or_transition_row(p, x, a, y, pr);
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s += pr[j] * V[y[j]];
+            Q[a * n + x] = R[a * n + x] + p->gamma * s;
+        }
+    *sweeps = k;
+    *residual = res;
+    free(R); free(Vn);
+    return status;
+}
+
+/* Numerator of Eq. 3: bbar(x') = sum_x T(x, a, x') b(x).  A belief carries
+ * no mass on occupied cells (Sec. II); values stored there are read as 0. */
+void or_predict(const or_problem *p, const double *b, int a, double *bbar) {
+    int n = p->H * p->W;
+    for (int x = 0; x < n; ++x) bbar[x] = 0.0;
+    for (int x = 0; x < n; ++x) {
+        if (p->occ[x]) continue;
+        int y[3]; double pr[3];
+        int m = or_transition_row(p, x, a, y, pr);
+        for (int j = 0; j < m; ++j) bbar[y[j]] += pr[j] * b[x];
+    }
+}
+
+/* Denominator of Eq. 3: P(z | b, a) = sum_x' O(x', z) bbar(x'), z = 0..B. */
+void or_obs_marginal(const or_problem *p, const int *label, const double *bbar, double *P) {
+    int n = p->H * p->W;
+    for (int z = 0; z <= p->B; ++z) {
+        double s = 0.0;
+        for (int x = 0; x < n; ++x) s += or_obs_lik(p, label, x, z) * bbar[x];
+        P[z] = s;
+    }
+}
+
+/* Eq. 3: Phi(b, a, z)(x') = O(x', z) bbar(x') / P(z | b, a).              */
+double or_correct(const or_problem *p, const int *label, const double *bbar, int z, double *bout) {
+    int n = p->H * p->W;
+    double pz = 0.0;
+    for (int x = 0; x < n; ++x) pz += or_obs_lik(p, label, x, z) * bbar[x];
+    for (int x = 0; x < n; ++x) bout[x] = or_obs_lik(p, label, x, z) * bbar[x] / pz;
+    return pz;
+}
+
+/* R(b, a) = sum_x R(x, a) b(x)  (Sec. III, after Eq. 2).                   */
+double or_belief_reward(const or_problem *p, const double *R, const double *b, int a) {
+    int n = p->H * p->W;
+    double s = 0.0;
+    for (int x = 0; x < n; ++x)
+        if (!p->occ[x]) s += R[a * n + x] * b[x];
+    return s;
+}
+
+/* Leaf value, Eq. 4 with Gamma = {Q(., a)}: max_a sum_x b(x) Q(a, x).
+ * Ties keep the lowest action index.                                      */
+double or_leaf_value(const or_problem *p, const double *Q, const double *b, double *qa) {
+    int n = p->H * p->W;
+    double best = -HUGE_VAL;
+    for (int a = 0; a < OR_NUM_ACTIONS; ++a) {
+        double s = 0.0;
+        for (int x = 0; x < n; ++x)
+            if (!p->occ[x]) s += b[x] * Q[a * n + x];
+        if (qa) qa[a] = s;
+        if (s > best) best = s;
+    }
+    return best;
+}
+
+/* Philox4x32-10, from Salmon, Moraes, Dror and Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64-bit
+ * multiplies with a Weyl-sequence key schedule.                          */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Sample stream of one (V-node, action): counter {k/4, episode, path_lo,
+ * (level << 24) | path_hi}, key = seed; word k%4 -> u = (2 (r >> 9) + 1) 2^-24,
+ * which is exact in FP32 and lies in (0, 1).                              */
+float or_uniform(uint64_t seed, uint32_t episode, int level, uint64_t path, int k) {
+    uint32_t ctr[4] = {(uint32_t)(k / 4), episode, (uint32_t)(path & 0xFFFFFFFFu),
+                       ((uint32_t)level << 24) | (uint32_t)(path >> 32)};
+    uint32_t key[2] = {(uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    uint32_t r = out[k % 4];
+    return (float)(2u * (r >> 9) + 1u) * (1.0f / 16777216.0f);
+}
+
+/* Forward sampling (Alg. 4) draws z from P(z | b, a); here by inverting the
+ * cumulative sum of the exact marginal, in FP32.                          */
+int or_sample_obs(const double *P, int nz, float u) {
+    float *C = (float *)malloc(sizeof(float) * nz);
+    float s = 0.0f;
+    for (int z = 0; z < nz; ++z) { s = s + (float)P[z]; C[z] = s; }
+    float t = u * C[nz - 1];
+    int pick = nz - 1;
+    for (int z = 0; z < nz; ++z)
+        if (t < C[z]) { pick = z; break; }
+    free(C);
+    return pick;
+}
+
+int or_is_boundary(const double *P, int nz, float u) {
+    double tot = 0.0;
+    for (int z = 0; z < nz; ++z) tot += P[z];
+    double s = 0.0;
+    for (int z = 0; z + 1 < nz; ++z) {
+        s += P[z];
+        if (fabs((double)u - s / tot) < 1e-6) return 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree search: Alg. 2 (V-node expansion over every action), Alg. 3 (Q-node:
+ * n forward samples, the unique measurements with their frequencies, one
+ * belief update and one V-node per unique measurement), Alg. 5 (a leaf's
+ * value from the offline bound), Alg. 6 and 7 (Q- and V-node updates).
+ * Readings: every V-node above depth d is expanded (full width, level by
+ * level); the Q update discounts the children by gamma as Eq. 2 does; the
+ * weight of a child is its sample frequency f/K (FREQ) or its marginal
+ * P(z)/sum over the sampled z (MARGINAL).                                   */
+int or_tree_plan(const or_problem *p, const double *Q, const double *b0,
+                 int depth, int K, uint64_t seed, uint32_t episode, int weight_mode,
+                 const int *replay, const long *off, int store_levels,
+                 int *n_level, int *parent, int *action, int *obs,
+                 double *weight, double *pz, double *value,
+                 double *R, double *UQ, int *samples, unsigned char *boundary,
+                 double *belief, int *root_action, double *root_value,
+                 double *root_q, long *boundary_count) {
+    const int n = p->H * p->W, nz = p->B + 1, A = OR_NUM_ACTIONS;
+    int *label = (int *)malloc(sizeof(int) * n);
+    double *Rt = (double *)malloc(sizeof(double) * A * n);
+    or_labels(p, label);
+    or_reward_table(p, Rt);
+
+    /* beliefs of the current and next level; path codes for the sampler */
+    double **lev_b = (double **)calloc(depth + 1, sizeof(double *));
+    uint64_t **code = (uint64_t **)calloc(depth + 1, sizeof(uint64_t *));
+    long bcount = 0;
+    int status = 0;
+
+    /* root V-node */
+    n_level[0] = 1;
+    lev_b[0] = (double *)malloc(sizeof(double) * n);
+    for (int x = 0; x < n; ++x) lev_b[0][x] = p->occ[x] ? 0.0 : b0[x];
+    code[0] = (uint64_t *)malloc(sizeof(uint64_t));
+    code[0][0] = 0;
+    parent[off[0]] = -1; action[off[0]] = -1; obs[off[0]] = -1;
+    weight[off[0]] = 1.0; pz[off[0]] = 1.0;
+
+    for (int l = 0; l < depth && status == 0; ++l) {
+        const int nl = n_level[l];
+        const long base = off[l];
+        /* per (node, action): unique sampled measurements and frequencies */
+        int *uz = (int *)malloc(sizeof(int) * (size_t)nl * A * K);
+        int *uf = (int *)malloc(sizeof(int) * (size_t)nl * A * K);
+        double *up = (double *)malloc(sizeof(double) * (size_t)nl * A * K);
+        int *un = (int *)calloc((size_t)nl * A, sizeof(int));
+        long lb = 0;
+#pragma omp parallel for schedule(dynamic) reduction(+ : lb)
+        for (int i = 0; i < nl; ++i) {
+            const double *b = lev_b[l] + (size_t)i * n;
+            double *bbar = (double *)malloc(sizeof(double) * n);
+            double *P = (double *)malloc(sizeof(double) * nz);
+            int *cnt = (int *)malloc(sizeof(int) * nz);
+            for (int a = 0; a < A; ++a) {
+                const long s = (base + i) * A + a;
+                R[s] = or_belief_reward(p, Rt, b, a);
+                or_predict(p, b, a, bbar);
+                or_obs_marginal(p, label, bbar, P);
+                const uint64_t path = code[l][i] * A + (uint64_t)a;
+                for (int z = 0; z < nz; ++z) cnt[z] = 0;
+                for (int k = 0; k < K; ++k) {
+                    float u = or_uniform(seed, episode, l, path, k);
+                    int z = replay ? replay[s * K + k] : or_sample_obs(P, nz, u);
+                    unsigned char bd = (unsigned char)or_is_boundary(P, nz, u);
+                    samples[s * K + k] = z;
+                    boundary[s * K + k] = bd;
+                    lb += bd;
+                    cnt[z] += 1;
+                }
+                int m = 0;
+                for (int z = 0; z < nz; ++z)
+                    if (cnt[z]) {
+                        uz[((size_t)i * A + a) * K + m] = z;
+                        uf[((size_t)i * A + a) * K + m] = cnt[z];
+                        up[((size_t)i * A + a) * K + m] = P[z];
+                        ++m;
+                    }
+                un[(size_t)i * A + a] = m;
+            }
+            free(bbar); free(P); free(cnt);
+        }
+        bcount += lb;
+        /* children of level l+1 in (parent, action, z) order */
+        long nn = 0;
+        for (long s = 0; s < (long)nl * A; ++s) nn += un[s];
+        if (off[l] + nl > off[l + 1] || off[l + 1] + nn > off[l + 2]) status = -1;
+        if (status == 0) {
+            n_level[l + 1] = (int)nn;
+            long c = 0;
+            for (int i = 0; i < nl; ++i)
+                for (int a = 0; a < A; ++a) {
+                    const int m = un[(size_t)i * A + a];
+                    double psum = 0.0;
+                    for (int j = 0; j < m; ++j) psum += up[((size_t)i * A + a) * K + j];
+                    for (int j = 0; j < m; ++j) {
+                        const long t = off[l + 1] + c + j;
+                        parent[t] = i;
+                        action[t] = a;
+                        obs[t] = uz[((size_t)i * A + a) * K + j];
+                        pz[t] = up[((size_t)i * A + a) * K + j];
+                        weight[t] = weight_mode == OR_WEIGHT_MARGINAL
+                                        ? pz[t] / psum
+                                        : (double)uf[((size_t)i * A + a) * K + j] / (double)K;
+                    }
+                    c += m;
+                }
+            code[l + 1] = (uint64_t *)malloc(sizeof(uint64_t) * (nn > 0 ? nn : 1));
+            const int leaf = (l + 1 == depth);
+            if (!leaf || store_levels >= l + 1)
+                lev_b[l + 1] = (double *)malloc(sizeof(double) * (size_t)(nn > 0 ? nn : 1) * n);
+#pragma omp parallel for schedule(dynamic)
+            for (long j = 0; j < nn; ++j) {
+                const long t = off[l + 1] + j;
+                const double *b = lev_b[l] + (size_t)parent[t] * n;
+                code[l + 1][j] = (code[l][parent[t]] * A + (uint64_t)action[t]) * (uint64_t)nz
+                                 + (uint64_t)obs[t];
+                double *bbar = (double *)malloc(sizeof(double) * n);
+                double *bn = lev_b[l + 1] ? lev_b[l + 1] + (size_t)j * n
+                                          : (double *)malloc(sizeof(double) * n);
+                or_predict(p, b, action[t], bbar);
+                or_correct(p, label, bbar, obs[t], bn);           /* Eq. 3 */
+                if (leaf) value[t] = or_leaf_value(p, Q, bn, NULL); /* Alg. 5 */
+                if (!lev_b[l + 1]) free(bn);
+                free(bbar);
+            }
+        }
+        free(uz); free(uf); free(up); free(un);
+    }
+    if (depth == 0) value[off[0]] = or_leaf_value(p, Q, lev_b[0], NULL);
+
+    /* Alg. 6 / 7 from the deepest internal level up to the root */
+    for (int l = depth - 1; l >= 0 && status == 0; --l) {
+        const long cb = off[l + 1];
+        long c = 0;
+        for (int i = 0; i < n_level[l]; ++i) {
+            double best = -HUGE_VAL;
+            for (int a = 0; a < A; ++a) {
+                double s = 0.0;
+                while (c < n_level[l + 1] && parent[cb + c] == i && action[cb + c] == a) {
+                    s += weight[cb + c] * value[cb + c];
+                    ++c;
+                }
+                double uq = R[(off[l] + i) * A + a] + p->gamma * s;
+                UQ[(off[l] + i) * A + a] = uq;
+                if (uq > best) best = uq;
+            }
+            value[off[l] + i] = best;
+        }
+    }
+    if (status == 0) {
+        int best = 0;
+        if (depth == 0) {
+            double qa[5];
+            *root_value = or_leaf_value(p, Q, lev_b[0], qa);
+            for (int a = 0; a < A; ++a) root_q[a] = qa[a];
+            for (int a = 1; a < A; ++a) if (qa[a] > qa[best]) best = a;
+        } else {
+            for (int a = 0; a < A; ++a) root_q[a] = UQ[off[0] * A + a];
+            for (int a = 1; a < A; ++a) if (root_q[a] > root_q[best]) best = a;
+            *root_value = value[off[0]];
+        }
+        *root_action = best;
+        *boundary_count = bcount;
+    }
+    if (belief && status == 0)
+        for (int l = 0; l <= depth && l <= store_levels; ++l)
+            if (lev_b[l])
+                memcpy(belief + (size_t)off[l] * n, lev_b[l], sizeof(double) * (size_t)n_level[l] * n);
+    for (int l = 0; l <= depth; ++l) { free(lev_b[l]); free(code[l]); }
+    free(lev_b); free(code); free(label); free(Rt);
+    return status;
+}

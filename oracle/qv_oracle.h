@@ -1,0 +1,85 @@
+/*
+ * qv_oracle.h -- plain FP64 CPU reference for QV-Tree Search (test infrastructure).
+ *
+ * This is the oracle that the CUDA library is checked against.  Only the test
+ * suite, the package smoke check and the benchmark's CPU-baseline leg may use
+ * it; the product path never links, loads or calls it.  It shares no code, no
+ * header and no table with the CUDA library.
+ *
+ * Layout: unpadded row-major grids, cell x = r*W + c.  Actions 0=N (row-1),
+ * 1=E (col+1), 2=S (row+1), 3=W (col-1), 4=stay.
+ */
+#ifndef QV_ORACLE_H
+#define QV_ORACLE_H
+#include <stdint.h>
+
+#define OR_NUM_ACTIONS 5
+#define OR_MAX_DEPTH 6
+#define OR_WEIGHT_FREQ 0
+#define OR_WEIGHT_MARGINAL 1
+
+typedef struct {
+    int H, W;
+    const unsigned char *occ;  /* [H*W] m(x): 1 occupied, 0 free            */
+    int B;                     /* number of beacons; |Z| = B + 1            */
+    const int *beacon;         /* [B] flat cell of each beacon              */
+    int range;                 /* Manhattan sensing range                   */
+    int goal;                  /* flat goal cell                            */
+    double slip;               /* epsilon, per perpendicular side           */
+    double acc;                /* alpha                                     */
+    double gamma;              /* discount                                  */
+    const double *cost;        /* [H*W] per-cell cost c(y), or NULL (c = 0) */
+} or_problem;
+
+/* Observation label of every cell: nearest beacon id within range, else B. */
+void or_labels(const or_problem *p, int *label);
+/* Row x of T(x, a, .): returns the number of distinct targets (<= 3).      */
+int or_transition_row(const or_problem *p, int x, int a, int *y, double *pr);
+/* R(x, a) for every x, a: R[a*n + x].                                      */
+void or_reward_table(const or_problem *p, double *R);
+/* O(x', z).                                                                */
+double or_obs_lik(const or_problem *p, const int *label, int x, int z);
+
+/* MDP value iteration (Jacobi).  truncated > 0: run exactly that many
+ * sweeps; else stop at the first sweep whose max-abs change < tol (or after
+ * max_sweeps).  V[n], Q[5*n]; residual_hist[k] = |V_{k+1} - V_k|_inf.
+ * Returns 0 when converged (or truncated), 1 when max_sweeps was reached.  */
+int or_value_iteration(const or_problem *p, double tol, int max_sweeps, int truncated,
+                       double *V, double *Q, int *sweeps, double *residual,
+                       double *residual_hist);
+
+void or_predict(const or_problem *p, const double *b, int a, double *bbar);
+void or_obs_marginal(const or_problem *p, const int *label, const double *bbar, double *P);
+double or_correct(const or_problem *p, const int *label, const double *bbar, int z, double *bout);
+double or_belief_reward(const or_problem *p, const double *R, const double *b, int a);
+double or_leaf_value(const or_problem *p, const double *Q, const double *b, double *qa);
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+/* The k-th uniform of the (level, path) sample stream.                     */
+float or_uniform(uint64_t seed, uint32_t episode, int level, uint64_t path, int k);
+/* Inverse-CDF decision, taken in FP32 like the CUDA path: first z with
+ * u * C(B) < C(z), C the FP32 running sum of (float)P in ascending z.      */
+int or_sample_obs(const double *P, int nz, float u);
+/* 1 when u lies within 1e-6 of an FP64 CDF boundary C(z)/C(B), z < B.      */
+int or_is_boundary(const double *P, int nz, float u);
+
+/* Level-synchronous tree of depth d.  Level l nodes occupy the flat slots
+ * [off[l], off[l] + n_level[l]) of every per-node array; capacity
+ * off[l+1]-off[l]; off has depth+2 entries.
+ * Per-(node, action) arrays use index (slot*5 + a), per-sample ones
+ * ((slot*5 + a)*K + k).  belief (nullable) holds levels 0..store_levels in
+ * slots [off[l]..] of n cells each.  replay (nullable) replaces the Philox
+ * draws with given observation samples, same indexing as samples.
+ * Returns 0, or -1 when a level exceeds its capacity.                      */
+int or_tree_plan(const or_problem *p, const double *Q, const double *b0,
+                 int depth, int K, uint64_t seed, uint32_t episode, int weight_mode,
+                 const int *replay, const long *off, int store_levels,
+                 int *n_level, int *parent, int *action, int *obs,
+                 double *weight, double *pz, double *value,
+                 double *R, double *UQ, int *samples, unsigned char *boundary,
+                 double *belief, int *root_action, double *root_value,
+                 double *root_q, long *boundary_count);
+
+int or_num_threads(void);
+
+#endif
