@@ -1,0 +1,211 @@
+/*
+ * qvts.h -- C ABI of the GB300 (sm_103a) QV-Tree Search library.
+ *
+ * The operations follow "Stochastic 2-D Motion Planning with a POMDP
+ * Framework" (Sun and Kumar): the model tuple (X, A, Z, T, O, R, b0, gamma) of
+ * Sec. II, the Bayes update Phi of Eq. 3, the QMDP leaf bound of Eq. 4, MDP
+ * value iteration for the offline Q (Sec. V-B), and the QV-tree expansion and
+ * backup of Alg. 2-7.
+ *
+ * Conventions shared by every call:
+ *   - Grids are row-major [H][pitch] with pitch = round_up(W, 4); cell
+ *     y = row * pitch + col.  Columns W..pitch-1 are padding (occupied).
+ *   - Actions: 0 = N (row - 1), 1 = E (col + 1), 2 = S (row + 1), 3 = W
+ *     (col - 1), 4 = stay.  The intended move succeeds w.p. 1 - 2*slip, each
+ *     perpendicular move happens w.p. slip; a move into an occupied or outside
+ *     cell leaves the mass in place (Eq. 10).  The goal is absorbing.
+ *   - Observations z = 0..B: the id of the nearest beacon within the sensing
+ *     range (Manhattan distance, ties to the lower id) or B (null); observed
+ *     w.p. accuracy, every other value w.p. (1 - accuracy)/B.
+ *   - Rewards: arriving in the goal pays +100, any other arrival -1 - c(y)
+ *     with c the optional cost map; the goal and occupied cells earn 0.
+ *   - Pointers named d_* are device pointers owned by the caller and must stay
+ *     valid until the stream work that uses them completes.  h_* / plain
+ *     pointers are host memory.  Beliefs and Q are FP32, 16-byte aligned.
+ *   - Every call is asynchronous on `stream` unless its comment says it
+ *     synchronises.  Calls return a status and never abort; the message of the
+ *     last failure on the calling thread is returned by qv_last_error().
+ *   - Device scratch comes from a caller-provided workspace (d_ws, ws_bytes);
+ *     the matching *_workspace_bytes call gives its size.  The library itself
+ *     allocates no device memory in any call declared here.
+ */
+#ifndef QVTS_H
+#define QVTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *qv_stream_t; /* a cudaStream_t; NULL = the legacy default stream */
+
+typedef enum {
+    QV_OK = 0,
+    QV_ERR_INVALID = 1,        /* bad argument (size, range, null pointer, alignment) */
+    QV_ERR_CUDA = 2,           /* a CUDA runtime call failed                          */
+    QV_ERR_WORKSPACE = 3,      /* ws_bytes smaller than the *_workspace_bytes figure  */
+    QV_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up                  */
+    QV_ERR_NOT_CONVERGED = 5,  /* value iteration hit max_sweeps before tol           */
+    QV_ERR_CAPACITY = 6        /* a tree level outgrew its preallocated capacity      */
+} qv_status;
+
+#define QV_NUM_ACTIONS 5
+#define QV_MAX_DEPTH 6
+#define QV_MAX_BEACONS 126
+#define QV_MAX_K 64
+#define QV_MAX_WIDTH 4096
+
+#define QV_F32 0
+#define QV_F64 1
+#define QV_WEIGHT_FREQ 0       /* child weight = sample frequency f/K (Alg. 3, Alg. 6)  */
+#define QV_WEIGHT_MARGINAL 1   /* child weight = P(z|b,a) / sum over sampled z          */
+#define QV_LEAF_FUSED 0        /* leaf values from the parent pass, no leaf beliefs     */
+#define QV_LEAF_MATERIALISE 1  /* leaf beliefs written, then streamed against Q         */
+
+/* A built model (Sec. II tuple on one grid).  d_cell comes from
+ * qv_model_build; the struct itself is plain host memory. */
+typedef struct {
+    int32_t H, W, pitch;       /* grid size; pitch = round_up(W, 4)                     */
+    const uint16_t *d_cell;    /* [H][pitch] cell words written by qv_model_build       */
+    int32_t num_beacons;       /* B in 1..QV_MAX_BEACONS; |Z| = B + 1                   */
+    int32_t goal;              /* goal cell, row * pitch + col, must be free            */
+    float slip;                /* epsilon in [0, 0.5]                                   */
+    float accuracy;            /* alpha in (0, 1]                                       */
+    float discount;            /* gamma in (0, 1)                                       */
+    const float *d_cost;       /* nullable [H][pitch] per-cell cost c(y)                */
+} qv_model_t;
+
+/* Tree-search parameters (Alg. 1-3 with the level-synchronous reading). */
+typedef struct {
+    int32_t depth;             /* d in 0..QV_MAX_DEPTH                                  */
+    int32_t K;                 /* forward samples per (V-node, action), 1..QV_MAX_K     */
+    uint64_t seed;             /* Philox4x32-10 key                                     */
+    uint32_t episode;          /* Philox counter word 1                                 */
+    int32_t weight_mode;       /* QV_WEIGHT_FREQ or QV_WEIGHT_MARGINAL                  */
+    int32_t leaf_mode;         /* QV_LEAF_FUSED or QV_LEAF_MATERIALISE                  */
+    const int32_t *d_replay;   /* nullable: observation samples to use instead of
+                                  Philox draws, laid out like the samples array of
+                                  qv_plan_level (per level, [node][action][K])         */
+} qv_plan_params_t;
+
+typedef struct {
+    int32_t action;            /* argmax_a U_Q(b0, a); ties to the lower index          */
+    float value;               /* U_V(b0)                                               */
+    float q[QV_NUM_ACTIONS];   /* U_Q(b0, a)                                            */
+    int32_t nodes_per_level[QV_MAX_DEPTH + 1];
+    int64_t boundary_samples;  /* draws whose uniform fell within 1e-6 of a CDF step    */
+} qv_plan_result_t;
+
+const char *qv_last_error(void);
+const char *qv_version(void);
+
+/* ---------------------------------------------------------------- model (Sec. II)
+ * Builds the cell words of one grid: for every cell, which of its four
+ * neighbours are blocked (occupied or outside; Eq. 10), which neighbours may
+ * move mass into it, its observation label, and whether it is free.
+ *   d_occ     [H][pitch] uint8, 1 = occupied (padding columns are ignored)
+ *   d_beacons [B] int32 beacon cells (row * pitch + col), free and distinct
+ *   d_cell    [H][pitch] uint16 output
+ * Errors: QV_ERR_INVALID for sizes outside the QV_MAX_* limits. */
+qv_status qv_model_build(int32_t H, int32_t W, int32_t pitch, const uint8_t *d_occ,
+                         const int32_t *d_beacons, int32_t B, int32_t sense_range,
+                         int32_t goal, uint16_t *d_cell, qv_stream_t stream);
+
+/* ---------------------------------------------------------------- value iteration
+ * MDP value iteration for the offline alpha-vectors Q (Sec. V-B baseline;
+ * Bellman operator of Eq. 2 on a known state; contraction as in Sec. IV-A):
+ *   V_{k+1}(x) = max_a [R(x, a) + gamma sum_y T(x, a, y) V_k(y)], V_0 = 0,
+ * Jacobi sweeps, V(goal) = 0.  Stops at the first sweep with
+ * max_x |V_{k+1} - V_k| < tol, or after exactly `truncated` sweeps when
+ * truncated > 0.  Writes V (dtype QV_F32 or QV_F64, [H][pitch]) and
+ * Q[a][y] = R(y, a) + gamma sum T V_final as FP32 [5][H][pitch].
+ * Synchronises the stream (sweeps and residual are returned to the host).
+ * Returns QV_ERR_NOT_CONVERGED when max_sweeps ran out first. */
+size_t mdp_value_iterate_workspace_bytes(const qv_model_t *model, int32_t dtype);
+qv_status mdp_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
+                            int32_t max_sweeps, int32_t truncated, void *d_V, float *d_Q,
+                            void *d_ws, size_t ws_bytes, int32_t *sweeps_out,
+                            double *residual_out, qv_stream_t stream);
+
+/* ---------------------------------------------------------------- belief update (Eq. 3)
+ * belief_predict: bbar(y) = sum_x T(x, action, y) b(x), the numerator of
+ * Eq. 3.  Values stored on occupied cells of b are read as 0. */
+qv_status belief_predict(const qv_model_t *model, const float *d_b, int32_t action,
+                         float *d_bbar, qv_stream_t stream);
+
+/* belief_correct: b'(y) = O(y, z) bbar(y) / P(z), P(z) = sum_y O(y, z) bbar(y)
+ * (Eq. 3); writes P(z) to the device scalar d_pz. */
+size_t belief_correct_workspace_bytes(const qv_model_t *model);
+qv_status belief_correct(const qv_model_t *model, const float *d_bbar, int32_t z,
+                         float *d_bout, float *d_pz, void *d_ws, size_t ws_bytes,
+                         qv_stream_t stream);
+
+/* leaf_value: v[i] = max_a sum_y b_i(y) Q[a][y] for n beliefs stored at
+ * d_b + i * H * pitch (Eq. 4 with the QMDP alpha-vectors; Alg. 5). */
+qv_status leaf_value(const qv_model_t *model, const float *d_Q, const float *d_b,
+                     int32_t n, float *d_value, qv_stream_t stream);
+
+/* ---------------------------------------------------------------- tree search (Alg. 1-7)
+ * A plan holds the layout of one batch of E episodes (E = 1 for a single
+ * tree) inside a caller workspace.  Every episode shares `params` except the
+ * Philox episode word, which is params->episode + e.  qv_plan_create uploads
+ * the episode descriptors (a synchronous host-to-device copy); qv_plan_run
+ * launches the whole search (no host synchronisation, no allocation; it may be
+ * captured in a CUDA graph); qv_plan_read copies the E results to the host and
+ * synchronises.  The workspace stays the plan's until qv_plan_destroy.  */
+typedef struct qv_plan qv_plan_t;
+
+size_t qv_plan_workspace_bytes(int32_t E, const qv_model_t *models,
+                               const qv_plan_params_t *params);
+qv_status qv_plan_create(int32_t E, const qv_model_t *models, const float *const *d_Q,
+                         const float *const *d_b0, const qv_plan_params_t *params,
+                         void *d_ws, size_t ws_bytes, qv_plan_t **plan_out,
+                         qv_stream_t stream);
+qv_status qv_plan_run(qv_plan_t *plan, qv_stream_t stream);
+/* Capture the launches of qv_plan_run in a CUDA graph owned by the plan;
+ * later qv_plan_run calls launch the graph. */
+qv_status qv_plan_capture_graph(qv_plan_t *plan, qv_stream_t stream);
+qv_status qv_plan_read(qv_plan_t *plan, qv_plan_result_t *h_results, qv_stream_t stream);
+void qv_plan_destroy(qv_plan_t *plan);
+
+/* Device views of one level of episode e after a run (for inspection and
+ * tests).  Level l nodes are ordered by (parent, action, z ascending).
+ * Arrays with a NULL out-pointer are skipped.  Per-node arrays have
+ * capacity cap; per-(node, action) arrays are [cap][5]; samples [cap][5][K].
+ * belief is NULL for levels that hold no beliefs (fused leaves). */
+typedef struct {
+    int32_t cap;               /* capacity of the level (worst case)                   */
+    const int32_t *d_count;    /* device scalar: nodes in the level                    */
+    const int32_t *d_parent;   /* parent index in level l-1                            */
+    const int32_t *d_action;   /* action from the parent                               */
+    const int32_t *d_obs;      /* observation z from the parent                        */
+    const float *d_weight;     /* child weight (FREQ or MARGINAL)                      */
+    const float *d_pz;         /* P(z | parent belief, action)                         */
+    const float *d_value;      /* U_V                                                  */
+    const float *d_R;          /* [cap][5] R(b, a)                                     */
+    const float *d_UQ;         /* [cap][5] U_Q(b, a)                                   */
+    const int32_t *d_nchild;   /* [cap][5] unique children per action                  */
+    const int32_t *d_samples;  /* [cap][5][K] raw sampled z                            */
+    const float *d_belief;     /* [cap][H][pitch] or NULL                              */
+} qv_level_view_t;
+qv_status qv_plan_level(const qv_plan_t *plan, int32_t e, int32_t level, qv_level_view_t *view);
+
+/* One plan from b0 to the chosen action: create + run + read + destroy.
+ * Synchronises the stream. */
+qv_status qv_tree_plan(const qv_model_t *model, const float *d_Q, const float *d_b0,
+                       const qv_plan_params_t *params, void *d_ws, size_t ws_bytes,
+                       qv_plan_result_t *h_result, qv_stream_t stream);
+
+/* E independent episodes on grids of uneven size, every level of every
+ * episode in one launch per kernel.  Synchronises the stream. */
+qv_status qv_tree_plan_batched(int32_t E, const qv_model_t *models, const float *const *d_Q,
+                               const float *const *d_b0, const qv_plan_params_t *params,
+                               void *d_ws, size_t ws_bytes, qv_plan_result_t *h_results,
+                               qv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QVTS_H */

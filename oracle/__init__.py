@@ -84,7 +84,7 @@ def _p(a):
 class Problem:
     """The model tuple of Sec. II built from a Workload (arrays kept alive)."""
 
-    def __init__(self, w, slip=None, accuracy=None, cost="workload"):
+    def __init__(self, w, slip=None, accuracy=None, cost="workload", discount=None):
         self.w = w
         self.H, self.W = w.H, w.W
         self.n = w.H * w.W
@@ -95,8 +95,9 @@ class Problem:
         self.cost = None if c is None else np.ascontiguousarray(np.asarray(c, np.float64).reshape(-1))
         self.slip = w.slip if slip is None else slip
         self.acc = w.accuracy if accuracy is None else accuracy
+        self.discount = w.discount if discount is None else discount
         self.s = _Problem(self.H, self.W, self.occ.ctypes.data, self.B, self.beacons.ctypes.data,
-                          w.sense_range, w.goal, self.slip, self.acc, w.discount,
+                          w.sense_range, w.goal, self.slip, self.acc, self.discount,
                           None if self.cost is None else self.cost.ctypes.data)
         self.ref = C.byref(self.s)
 

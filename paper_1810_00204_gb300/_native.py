@@ -1,0 +1,105 @@
+"""ctypes declarations of include/qvts.h.
+
+Loads the in-tree `libqvts.so`; there is no fallback: when the library is
+missing or fails to load the import raises, so nothing can silently run on
+another path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libqvts.so")
+
+QV_OK, QV_ERR_INVALID, QV_ERR_CUDA, QV_ERR_WORKSPACE, QV_ERR_TIMEOUT, QV_ERR_NOT_CONVERGED, QV_ERR_CAPACITY = range(7)
+STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_INVALID", 2: "QV_ERR_CUDA", 3: "QV_ERR_WORKSPACE",
+                4: "QV_ERR_TIMEOUT", 5: "QV_ERR_NOT_CONVERGED", 6: "QV_ERR_CAPACITY"}
+QV_NUM_ACTIONS = 5
+QV_MAX_DEPTH = 6
+QV_MAX_BEACONS = 126
+QV_MAX_K = 64
+QV_MAX_WIDTH = 4096
+QV_F32, QV_F64 = 0, 1
+QV_WEIGHT_FREQ, QV_WEIGHT_MARGINAL = 0, 1
+QV_LEAF_FUSED, QV_LEAF_MATERIALISE = 0, 1
+
+
+class qv_model_t(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("pitch", C.c_int32), ("d_cell", C.c_void_p),
+                ("num_beacons", C.c_int32), ("goal", C.c_int32), ("slip", C.c_float),
+                ("accuracy", C.c_float), ("discount", C.c_float), ("d_cost", C.c_void_p)]
+
+
+class qv_plan_params_t(C.Structure):
+    _fields_ = [("depth", C.c_int32), ("K", C.c_int32), ("seed", C.c_uint64), ("episode", C.c_uint32),
+                ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p)]
+
+
+class qv_plan_result_t(C.Structure):
+    _fields_ = [("action", C.c_int32), ("value", C.c_float), ("q", C.c_float * QV_NUM_ACTIONS),
+                ("nodes_per_level", C.c_int32 * (QV_MAX_DEPTH + 1)), ("boundary_samples", C.c_int64)]
+
+
+class qv_level_view_t(C.Structure):
+    _fields_ = [("cap", C.c_int32), ("d_count", C.c_void_p), ("d_parent", C.c_void_p),
+                ("d_action", C.c_void_p), ("d_obs", C.c_void_p), ("d_weight", C.c_void_p),
+                ("d_pz", C.c_void_p), ("d_value", C.c_void_p), ("d_R", C.c_void_p), ("d_UQ", C.c_void_p),
+                ("d_nchild", C.c_void_p), ("d_samples", C.c_void_p), ("d_belief", C.c_void_p)]
+
+
+# every symbol include/qvts.h declares, with (restype, argtypes)
+_vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
+_M = C.POINTER(qv_model_t)
+_PP = C.POINTER(qv_plan_params_t)
+SIGNATURES = {
+    "qv_last_error": (C.c_char_p, []),
+    "qv_version": (C.c_char_p, []),
+    "qv_model_build": (C.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "mdp_value_iterate_workspace_bytes": (_sz, [_M, _i32]),
+    "mdp_value_iterate": (C.c_int, [_M, _i32, C.c_double, _i32, _i32, _vp, _vp, _vp, _sz,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_double), _vp]),
+    "belief_predict": (C.c_int, [_M, _vp, _i32, _vp, _vp]),
+    "belief_correct_workspace_bytes": (_sz, [_M]),
+    "belief_correct": (C.c_int, [_M, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "leaf_value": (C.c_int, [_M, _vp, _vp, _i32, _vp, _vp]),
+    "qv_plan_workspace_bytes": (_sz, [_i32, _M, _PP]),
+    "qv_plan_create": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(_vp), _vp]),
+    "qv_plan_run": (C.c_int, [_vp, _vp]),
+    "qv_plan_capture_graph": (C.c_int, [_vp, _vp]),
+    "qv_plan_read": (C.c_int, [_vp, C.POINTER(qv_plan_result_t), _vp]),
+    "qv_plan_destroy": (None, [_vp]),
+    "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
+    "qv_tree_plan": (C.c_int, [_M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
+    "qv_tree_plan_batched": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises when libqvts.so is absent: no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class QVError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().qv_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, where):
+    if status != QV_OK:
+        raise QVError(status, where)

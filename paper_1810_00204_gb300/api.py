@@ -1,0 +1,251 @@
+"""Thin Python binding over the C ABI of include/qvts.h.
+
+Argument marshalling only: tensors in, device pointers and the current CUDA
+stream out to libqvts.so.  Every step of the computation runs in the CUDA
+library; nothing here computes any part of the method.  PyTorch provides the
+device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import check, lib
+
+__all__ = ["Model", "Plan", "qv_model_build", "mdp_value_iterate", "belief_predict", "belief_correct",
+           "leaf_value", "qv_tree_plan", "qv_tree_plan_batched", "pitch_of"]
+
+
+def pitch_of(W: int) -> int:
+    return (W + 3) // 4 * 4
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def qv_model_build(H, W, pitch, occ, beacons, B, sense_range, goal, cell, stream=None):
+    """Cell words of one grid (occ uint8 [H][pitch], beacons int32 [B], cell int16 [H][pitch])."""
+    check(lib().qv_model_build(H, W, pitch, _ptr(occ), _ptr(beacons), B, sense_range, goal, _ptr(cell),
+                               _stream(stream)), "qv_model_build")
+    return cell
+
+
+class Model:
+    """Device form of one generated problem: the padded grids, the cell words
+    written by qv_model_build, and the qv_model_t that points at them."""
+
+    def __init__(self, w, device="cuda", slip=None, accuracy=None, cost="workload", stream=None):
+        self.w = w
+        self.H, self.W = w.H, w.W
+        self.P = pitch_of(w.W)
+        self.B = w.B
+        self.device = torch.device(device)
+        occ = np.ones((self.H, self.P), np.uint8)
+        occ[:, :self.W] = w.occ
+        self.occ = torch.from_numpy(occ).to(self.device)
+        self.beacons = torch.from_numpy(np.asarray([self.pcell(b) for b in w.beacons], np.int32)).to(self.device)
+        self.goal = self.pcell(w.goal)
+        self.cell = torch.empty((self.H, self.P), dtype=torch.int16, device=self.device)
+        qv_model_build(self.H, self.W, self.P, self.occ, self.beacons, self.B, w.sense_range, self.goal,
+                       self.cell, stream)
+        c = w.cost if isinstance(cost, str) else cost
+        self.cost = None if c is None else self.to_grid(np.asarray(c, np.float32))
+        self.slip = float(w.slip if slip is None else slip)
+        self.accuracy = float(w.accuracy if accuracy is None else accuracy)
+        self.discount = float(w.discount)
+        self.struct = N.qv_model_t(self.H, self.W, self.P, self.cell.data_ptr(), self.B, self.goal,
+                                   self.slip, self.accuracy, self.discount,
+                                   None if self.cost is None else self.cost.data_ptr())
+
+    def pcell(self, x: int) -> int:
+        """Unpadded cell index r*W + c -> pitched index r*pitch + c."""
+        r, c = divmod(int(x), self.W)
+        return r * self.P + c
+
+    def to_grid(self, a) -> torch.Tensor:
+        """[..., H, W] array -> float32 [..., H, pitch] device tensor (padding 0)."""
+        a = torch.as_tensor(np.asarray(a, np.float32) if not torch.is_tensor(a) else a)
+        a = a.reshape(*a.shape[:-1], self.H, self.W) if a.shape[-1] == self.H * self.W else a
+        out = torch.zeros(*a.shape[:-2], self.H, self.P, dtype=torch.float32, device=self.device)
+        out[..., :self.W] = a.to(self.device, torch.float32)
+        return out
+
+    def from_grid(self, t: torch.Tensor) -> np.ndarray:
+        """[..., H, pitch] -> numpy [..., H*W] (unpadded, row-major)."""
+        t = t.reshape(*t.shape[:-1], self.H, self.P) if t.shape[-1] == self.H * self.P else t
+        a = t[..., :self.W].detach().cpu().numpy()
+        return a.reshape(*a.shape[:-2], self.H * self.W)
+
+    def b0(self) -> torch.Tensor:
+        return self.to_grid(self.w.b0)
+
+
+def mdp_value_iterate(model: Model, dtype="f32", tol=None, max_sweeps=100000, truncated=None, stream=None):
+    """Returns dict(V [H][pitch], Q [5][H][pitch] float32, sweeps, residual, status)."""
+    w = model.w
+    tol = w.vi_tol if tol is None else tol
+    truncated = w.vi_truncated if truncated is None else truncated
+    dt = N.QV_F64 if dtype in ("f64", torch.float64) else N.QV_F32
+    V = torch.zeros((model.H, model.P), dtype=torch.float64 if dt == N.QV_F64 else torch.float32,
+                    device=model.device)
+    Q = torch.empty((5, model.H, model.P), dtype=torch.float32, device=model.device)
+    nbytes = lib().mdp_value_iterate_workspace_bytes(C.byref(model.struct), dt)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.device)
+    sweeps = C.c_int32(0)
+    res = C.c_double(0)
+    st = lib().mdp_value_iterate(C.byref(model.struct), dt, float(tol), int(max_sweeps), int(truncated), _ptr(V),
+                                 _ptr(Q), _ptr(ws), nbytes, C.byref(sweeps), C.byref(res), _stream(stream))
+    if st not in (N.QV_OK, N.QV_ERR_NOT_CONVERGED):
+        check(st, "mdp_value_iterate")
+    return dict(V=V, Q=Q, sweeps=sweeps.value, residual=res.value, status=st)
+
+
+def belief_predict(model: Model, b: torch.Tensor, action: int, out=None, stream=None):
+    out = torch.empty_like(b) if out is None else out
+    check(lib().belief_predict(C.byref(model.struct), _ptr(b), int(action), _ptr(out), _stream(stream)),
+          "belief_predict")
+    return out
+
+
+def belief_correct(model: Model, bbar: torch.Tensor, z: int, out=None, stream=None):
+    out = torch.empty_like(bbar) if out is None else out
+    pz = torch.empty(1, dtype=torch.float32, device=bbar.device)
+    nbytes = lib().belief_correct_workspace_bytes(C.byref(model.struct))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=bbar.device)
+    check(lib().belief_correct(C.byref(model.struct), _ptr(bbar), int(z), _ptr(out), _ptr(pz), _ptr(ws), nbytes,
+                               _stream(stream)), "belief_correct")
+    return out, pz
+
+
+def leaf_value(model: Model, Q: torch.Tensor, b: torch.Tensor, stream=None):
+    n = b.shape[0] if b.dim() == 3 else 1
+    out = torch.empty(n, dtype=torch.float32, device=b.device)
+    check(lib().leaf_value(C.byref(model.struct), _ptr(Q), _ptr(b.contiguous()), n, _ptr(out), _stream(stream)),
+          "leaf_value")
+    return out
+
+
+def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay):
+    return N.qv_plan_params_t(int(depth), int(K), int(seed), int(episode), int(weight_mode), int(leaf_mode),
+                              None if replay is None else replay.data_ptr())
+
+
+def _result_dict(r: N.qv_plan_result_t, depth: int):
+    return dict(action=int(r.action), value=float(r.value), q=np.array(list(r.q), np.float32),
+                nodes_per_level=[int(r.nodes_per_level[l]) for l in range(depth + 1)],
+                boundary_samples=int(r.boundary_samples))
+
+
+class Plan:
+    """One batch of E episodes laid out in a caller workspace (a torch tensor).
+
+    run() launches the search (asynchronous, no host synchronisation);
+    read() synchronises and returns the root results; capture_graph() turns
+    later run() calls into one CUDA-graph launch; level() exposes the device
+    arrays of one tree level as tensors viewing the workspace."""
+
+    def __init__(self, models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor],
+                 depth=2, K=4, seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED,
+                 replay: Optional[torch.Tensor] = None, stream=None):
+        self.models = list(models)
+        self.E = len(self.models)
+        self.depth, self.K = int(depth), int(K)
+        self.Qs = [q.contiguous() for q in Qs]
+        self.b0s = [b.contiguous() for b in b0s]
+        self.replay = replay
+        self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay)
+        self.mstructs = (N.qv_model_t * self.E)(*[m.struct for m in self.models])
+        self.qptrs = (C.c_void_p * self.E)(*[q.data_ptr() for q in self.Qs])
+        self.bptrs = (C.c_void_p * self.E)(*[b.data_ptr() for b in self.b0s])
+        nbytes = lib().qv_plan_workspace_bytes(self.E, self.mstructs, C.byref(self.params))
+        if nbytes == 0:
+            raise N.QVError(N.QV_ERR_INVALID, "qv_plan_workspace_bytes")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.models[0].device)
+        self.handle = C.c_void_p()
+        check(lib().qv_plan_create(self.E, self.mstructs, self.qptrs, self.bptrs, C.byref(self.params),
+                                   _ptr(self.ws), nbytes, C.byref(self.handle), _stream(stream)), "qv_plan_create")
+
+    @property
+    def workspace_bytes(self):
+        return self.ws.numel()
+
+    def run(self, stream=None):
+        check(lib().qv_plan_run(self.handle, _stream(stream)), "qv_plan_run")
+
+    def capture_graph(self, stream=None):
+        s = torch.cuda.Stream() if stream is None else stream
+        s.wait_stream(torch.cuda.current_stream())
+        check(lib().qv_plan_capture_graph(self.handle, C.c_void_p(s.cuda_stream)), "qv_plan_capture_graph")
+        torch.cuda.current_stream().wait_stream(s)
+
+    def read(self, stream=None) -> List[dict]:
+        res = (N.qv_plan_result_t * self.E)()
+        check(lib().qv_plan_read(self.handle, res, _stream(stream)), "qv_plan_read")
+        return [_result_dict(res[e], self.depth) for e in range(self.E)]
+
+    def _view(self, ptr, count, dtype, shape=None):
+        if not ptr:
+            return None
+        esz = torch.tensor([], dtype=dtype).element_size()
+        off = ptr - self.ws.data_ptr()
+        if 0 <= off < self.ws.numel():
+            t = self.ws[off:off + count * esz].view(dtype)
+        else:  # level 0 belief is the caller's b0
+            return None
+        return t if shape is None else t.view(*shape)
+
+    def level(self, e: int, l: int) -> dict:
+        v = N.qv_level_view_t()
+        check(lib().qv_plan_level(self.handle, e, l, C.byref(v)), "qv_plan_level")
+        cap = v.cap
+        n = int(self._view(v.d_count, 1, torch.int32).item())
+        m = self.models[e]
+        out = dict(count=n, cap=cap)
+        for key, ptr, dt in (("parent", v.d_parent, torch.int32), ("action", v.d_action, torch.int32),
+                             ("obs", v.d_obs, torch.int32), ("weight", v.d_weight, torch.float32),
+                             ("pz", v.d_pz, torch.float32), ("value", v.d_value, torch.float32)):
+            out[key] = self._view(ptr, cap, dt)[:n]
+        for key, ptr, dt in (("R", v.d_R, torch.float32), ("UQ", v.d_UQ, torch.float32),
+                             ("nchild", v.d_nchild, torch.int32)):
+            t = self._view(ptr, cap * 5, dt, (cap, 5)) if ptr else None
+            out[key] = None if t is None else t[:n]
+        t = self._view(v.d_samples, cap * 5 * self.K, torch.int32, (cap, 5, self.K)) if v.d_samples else None
+        out["samples"] = None if t is None else t[:n]
+        if l == 0:
+            out["belief"] = self.b0s[e].view(1, m.H, m.P)
+        else:
+            t = self._view(v.d_belief, cap * m.H * m.P, torch.float32, (cap, m.H, m.P)) if v.d_belief else None
+            out["belief"] = None if t is None else t[:n]
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            lib().qv_plan_destroy(h)
+            self.handle = C.c_void_p()
+
+
+def qv_tree_plan(model: Model, Q: torch.Tensor, b0: torch.Tensor, depth=2, K=4, seed=0, episode=0,
+                 weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED, replay=None, keep=False, stream=None):
+    """One plan from b0 to the chosen action (Alg. 1 inner loop, one step)."""
+    p = Plan([model], [Q], [b0], depth, K, seed, episode, weight_mode, leaf_mode, replay, stream)
+    p.run(stream)
+    r = p.read(stream)[0]
+    return (r, p) if keep else r
+
+
+def qv_tree_plan_batched(models, Qs, b0s, depth=3, K=8, seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ,
+                         leaf_mode=N.QV_LEAF_FUSED, stream=None):
+    p = Plan(models, Qs, b0s, depth, K, seed, episode, weight_mode, leaf_mode, None, stream)
+    p.run(stream)
+    return p.read(stream)

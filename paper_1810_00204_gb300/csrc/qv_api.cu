@@ -1,0 +1,33 @@
+// qv_api.cu -- error reporting and device queries shared by the entry points.
+#include <cstdarg>
+#include <cstdio>
+
+#include "qv_common.cuh"
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+qv_status qv_set_error(qv_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+qv_status qv_check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return QV_OK;
+    return qv_set_error(QV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int qv_num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+extern "C" const char *qv_last_error(void) { return g_last_error; }
+
+extern "C" const char *qv_version(void) { return "qvts-gb300 0.1 (sm_103a)"; }

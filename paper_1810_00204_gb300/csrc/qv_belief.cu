@@ -1,0 +1,205 @@
+// qv_belief.cu -- single-belief primitives: the predict step (numerator of
+// Eq. 3 with the blocked-move rule of Eq. 10), the Bayes correction with its
+// normaliser P(z | b, a) (Eq. 3), and QMDP leaf values (Eq. 4).
+#include "qv_common.cuh"
+
+namespace qv {
+
+struct ModelArgs {
+    int H, W, P, N, B, goal;
+    float slip, acc, eta;
+    const uint16_t *cell;
+};
+
+__host__ ModelArgs model_args(const qv_model_t *m) {
+    ModelArgs a;
+    a.H = m->H;
+    a.W = m->W;
+    a.P = m->pitch;
+    a.N = m->H * m->pitch;
+    a.B = m->num_beacons;
+    a.goal = m->goal;
+    a.slip = m->slip;
+    a.acc = m->accuracy;
+    a.eta = (1.0f - m->accuracy) / static_cast<float>(m->num_beacons);
+    a.cell = m->d_cell;
+    return a;
+}
+
+// One thread per group of 4 cells of a row; neighbours read through L1.
+__global__ void __launch_bounds__(256) k_predict(ModelArgs m, const float *__restrict__ b, int action,
+                                                 float *__restrict__ out) {
+    __shared__ float lut[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, m.slip);
+    __syncthreads();
+    const int P4 = m.P >> 2, ng = m.H * P4;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const int r = g / P4, col = (g - r * P4) << 2, y = r * m.P + col;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 up = r > 0 ? __ldg(reinterpret_cast<const float4 *>(b + y - m.P)) : z4;
+        const float4 mid = __ldg(reinterpret_cast<const float4 *>(b + y));
+        const float4 dn = r + 1 < m.H ? __ldg(reinterpret_cast<const float4 *>(b + y + m.P)) : z4;
+        const float left = col > 0 ? __ldg(b + y - 1) : 0.0f;
+        const float right = col + 4 < m.P ? __ldg(b + y + 4) : 0.0f;
+        const ushort4 cw4 = __ldg(reinterpret_cast<const ushort4 *>(m.cell + y));
+        const float u[4] = {up.x, up.y, up.z, up.w};
+        const float mm[6] = {left, mid.x, mid.y, mid.z, mid.w, right};
+        const float d[4] = {dn.x, dn.y, dn.z, dn.w};
+        const unsigned cws[4] = {cw4.x, cw4.y, cw4.z, cw4.w};
+        float res[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const unsigned in = QV_CELL_INFLOW(cws[j]);
+            float nb[4], o[5];
+            nb[kDirN] = (in & 1u) ? u[j] : 0.0f;
+            nb[kDirE] = (in & 2u) ? mm[j + 2] : 0.0f;
+            nb[kDirS] = (in & 4u) ? d[j] : 0.0f;
+            nb[kDirW] = (in & 8u) ? mm[j] : 0.0f;
+            predict_cell(nb, mm[j + 1], cws[j], (y + j) == m.goal, m.slip, lut, o);
+            res[j] = o[action];
+        }
+        *reinterpret_cast<float4 *>(out + y) = make_float4(res[0], res[1], res[2], res[3]);
+    }
+}
+
+// P(z) = sum_y O(y, z) bbar(y): per-CTA partial sums, the last CTA adds them
+// in CTA order and writes the scalar.
+__global__ void __launch_bounds__(256) k_obs_partial(ModelArgs m, const float *__restrict__ bbar, int z,
+                                                     float *__restrict__ partials, unsigned *__restrict__ counter,
+                                                     float *__restrict__ pz) {
+    __shared__ float s_red[8];
+    __shared__ int s_last;
+    float acc = 0.0f;
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < m.N; y += gridDim.x * blockDim.x) {
+        const unsigned cw = __ldg(m.cell + y);
+        const float v = QV_CELL_FREE(cw) ? __ldg(bbar + y) : 0.0f;
+        acc = fmaf(static_cast<int>(QV_CELL_LABEL(cw)) == z ? m.acc : m.eta, v, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w];
+        partials[blockIdx.x] = t;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        float t = 0.0f;
+        for (unsigned i = 0; i < gridDim.x; ++i) t += __ldcg(partials + i);
+        *pz = t;
+        *counter = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_correct_scale(ModelArgs m, const float *__restrict__ bbar, int z,
+                                                       const float *__restrict__ pz, float *__restrict__ out) {
+    const float inv = 1.0f / __ldcg(pz);
+    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < m.N; y += gridDim.x * blockDim.x) {
+        const unsigned cw = __ldg(m.cell + y);
+        const float v = QV_CELL_FREE(cw) ? __ldg(bbar + y) : 0.0f;
+        out[y] = v * (static_cast<int>(QV_CELL_LABEL(cw)) == z ? m.acc : m.eta) * inv;
+    }
+}
+
+// One CTA per belief: max_a sum_y b(y) Q[a][y].
+__global__ void __launch_bounds__(256) k_leaf_prim(ModelArgs m, const float *__restrict__ Q,
+                                                   const float *__restrict__ b, float *__restrict__ value) {
+    __shared__ float s_red[8][5];
+    const float *bi = b + static_cast<long long>(blockIdx.x) * m.N;
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n4 = m.N >> 2;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(bi) + i);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(Q + static_cast<long long>(a) * m.N) + i);
+            acc[a] = fmaf(v.x, q.x, fmaf(v.y, q.y, fmaf(v.z, q.z, fmaf(v.w, q.w, acc[a]))));
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        const float t = warp_sum(acc[a]);
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5][a] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float best = -3.402823466e38f;
+        for (int a = 0; a < 5; ++a) {
+            float t = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_red[w][a];
+            best = t > best ? t : best;
+        }
+        value[blockIdx.x] = best;
+    }
+}
+
+constexpr int kCorrectBlocks = 512;
+
+qv_status check_model(const qv_model_t *m, const char *who) {
+    if (!m || !m->d_cell) return qv_set_error(QV_ERR_INVALID, "%s: null model", who);
+    if (m->H < 1 || m->W < 1 || m->W > QV_MAX_WIDTH || m->pitch != ((m->W + 3) / 4) * 4)
+        return qv_set_error(QV_ERR_INVALID, "%s: bad grid %dx%d pitch %d", who, m->H, m->W, m->pitch);
+    if (m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
+        return qv_set_error(QV_ERR_INVALID, "%s: B=%d", who, m->num_beacons);
+    if (!(m->slip >= 0.f && m->slip <= 0.5f) || !(m->accuracy > 0.f && m->accuracy <= 1.f))
+        return qv_set_error(QV_ERR_INVALID, "%s: slip/accuracy out of range", who);
+    return QV_OK;
+}
+
+}  // namespace qv
+
+extern "C" qv_status belief_predict(const qv_model_t *m, const float *d_b, int32_t action, float *d_bbar,
+                                    qv_stream_t stream) {
+    qv_status st = qv::check_model(m, "belief_predict");
+    if (st != QV_OK) return st;
+    if (!d_b || !d_bbar) return qv_set_error(QV_ERR_INVALID, "belief_predict: null pointer");
+    if (action < 0 || action >= QV_NUM_ACTIONS) return qv_set_error(QV_ERR_INVALID, "belief_predict: action %d", action);
+    if ((reinterpret_cast<uintptr_t>(d_b) | reinterpret_cast<uintptr_t>(d_bbar)) & 15)
+        return qv_set_error(QV_ERR_INVALID, "belief_predict: buffers must be 16-byte aligned");
+    const qv::ModelArgs a = qv::model_args(m);
+    const int ng = a.H * (a.P / 4);
+    const int grid = std::max(1, std::min((ng + 255) / 256, 8 * qv_num_sms()));
+    qv::k_predict<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(a, d_b, action, d_bbar);
+    return qv_check_cuda(cudaGetLastError(), "belief_predict launch");
+}
+
+extern "C" size_t belief_correct_workspace_bytes(const qv_model_t *) {
+    return sizeof(float) * qv::kCorrectBlocks + 256;
+}
+
+extern "C" qv_status belief_correct(const qv_model_t *m, const float *d_bbar, int32_t z, float *d_bout, float *d_pz,
+                                    void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    qv_status st = qv::check_model(m, "belief_correct");
+    if (st != QV_OK) return st;
+    if (!d_bbar || !d_bout || !d_pz || !d_ws) return qv_set_error(QV_ERR_INVALID, "belief_correct: null pointer");
+    if (z < 0 || z > m->num_beacons) return qv_set_error(QV_ERR_INVALID, "belief_correct: z %d", z);
+    if (ws_bytes < belief_correct_workspace_bytes(m))
+        return qv_set_error(QV_ERR_WORKSPACE, "belief_correct: workspace %zu bytes too small", ws_bytes);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const qv::ModelArgs a = qv::model_args(m);
+    float *partials = static_cast<float *>(d_ws);
+    unsigned *counter = reinterpret_cast<unsigned *>(static_cast<char *>(d_ws) + sizeof(float) * qv::kCorrectBlocks);
+    const int grid = std::max(1, std::min((a.N + 255) / 256, qv::kCorrectBlocks));
+    if (qv_check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), cs), "belief_correct memset") != QV_OK)
+        return QV_ERR_CUDA;
+    qv::k_obs_partial<<<grid, 256, 0, cs>>>(a, d_bbar, z, partials, counter, d_pz);
+    qv::k_correct_scale<<<grid, 256, 0, cs>>>(a, d_bbar, z, d_pz, d_bout);
+    return qv_check_cuda(cudaGetLastError(), "belief_correct launch");
+}
+
+extern "C" qv_status leaf_value(const qv_model_t *m, const float *d_Q, const float *d_b, int32_t n, float *d_value,
+                                qv_stream_t stream) {
+    qv_status st = qv::check_model(m, "leaf_value");
+    if (st != QV_OK) return st;
+    if (!d_Q || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "leaf_value: null pointer");
+    if (n < 0) return qv_set_error(QV_ERR_INVALID, "leaf_value: n %d", n);
+    if (n == 0) return QV_OK;
+    if ((reinterpret_cast<uintptr_t>(d_Q) | reinterpret_cast<uintptr_t>(d_b)) & 15)
+        return qv_set_error(QV_ERR_INVALID, "leaf_value: buffers must be 16-byte aligned");
+    qv::k_leaf_prim<<<n, 256, 0, static_cast<cudaStream_t>(stream)>>>(qv::model_args(m), d_Q, d_b, d_value);
+    return qv_check_cuda(cudaGetLastError(), "leaf_value launch");
+}

@@ -46,6 +46,13 @@ class Workload:
     vi_truncated: int = 0      # >0: run exactly this many sweeps
     cost: Optional[np.ndarray] = None  # float32 [H][W] per-cell cost, or None
 
+    def __setattr__(self, name, value):
+        # The model parameters are float32 numbers (the C ABI carries them as
+        # float); storing them rounded lets every consumer see the same value.
+        if name in ("slip", "accuracy", "discount"):
+            value = float(np.float32(value))
+        object.__setattr__(self, name, value)
+
     @property
     def B(self) -> int:
         return int(len(self.beacons))

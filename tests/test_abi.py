@@ -1,0 +1,71 @@
+"""The C ABI library builds, loads without a GPU, and exports every symbol
+include/qvts.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qvts.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w \*]*?\b([a-z][a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith(("sizeof",))))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1810_00204_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_paper_calls():
+    names = _declared()
+    for n in ("qv_model_build", "mdp_value_iterate", "belief_predict", "belief_correct", "leaf_value",
+              "qv_tree_plan", "qv_tree_plan_batched", "qv_plan_create", "qv_plan_run", "qv_plan_read"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(libpath):
+    from paper_1810_00204_gb300 import _native
+    assert sorted(_native.SIGNATURES) == _declared()
+    L = _native.lib()
+    assert L.qv_version().decode().startswith("qvts-gb300")
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path, monkeypatch):
+    from paper_1810_00204_gb300 import _native
+    monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libqvts.so"))
+    monkeypatch.setattr(_native, "_lib", None)
+    with pytest.raises(ImportError):
+        _native.lib()
+
+
+def test_invalid_arguments_are_rejected_without_gpu(libpath):
+    """Host-side validation runs before any CUDA call."""
+    from paper_1810_00204_gb300 import _native as N
+    L = N.lib()
+    assert L.qv_model_build(0, 5, 8, None, None, 1, 1, 0, None, None) == N.QV_ERR_INVALID
+    m = N.qv_model_t(4, 5, 7, 16, 1, 0, 0.1, 0.9, 0.95, None)    # bad pitch
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    assert b"pitch" in L.qv_last_error()
+    m = N.qv_model_t(4, 5, 8, 16, 1, 0, 0.1, 0.9, 0.95, None)
+    p = N.qv_plan_params_t(2, 0, 0, 0, 0, 0, None)                # K = 0
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    p = N.qv_plan_params_t(N.QV_MAX_DEPTH + 1, 4, 0, 0, 0, 0, None)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
+    m.num_beacons = N.QV_MAX_BEACONS + 1
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0

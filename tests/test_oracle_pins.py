@@ -17,13 +17,16 @@ GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
 def _grid(H, W, occ_cells=(), goal=0, slip=0.1, beacons=(0,), rng=3, acc=0.9, cost=None,
           b0=None, depth=1, K=4, discount=0.95):
+    """A hand-made problem with exact (FP64) model parameters."""
     occ = np.zeros(H * W, np.uint8)
     for c in occ_cells:
         occ[c] = 1
     if b0 is None:
         b0 = (1 - occ) / (1 - occ).sum()
-    return WL.custom(H, W, occ, list(beacons), rng, goal, goal, slip, acc, discount, b0,
-                     depth=depth, K=K, cost=cost)
+    w = WL.custom(H, W, occ, list(beacons), rng, goal, goal, slip, acc, discount, b0,
+                  depth=depth, K=K, cost=cost)
+    return O.Problem(w, slip=slip, accuracy=acc, discount=discount,
+                     cost=None if cost is None else np.asarray(cost, np.float64))
 
 
 def _lines(name):
@@ -88,8 +91,7 @@ def test_reward_golden():
         cost = [float(v) for v in f[:3]]
         x, a = int(f[3]), int(f[4])
         w = _grid(1, 3, goal=0, cost=None if not any(cost) else cost)
-        # cost inputs are float32, so 0.2 and 0.4 carry ~1e-8 representation error
-        assert O.reward_table(w)[a, x] == pytest.approx(float(rhs), abs=1e-6)
+        assert O.reward_table(w)[a, x] == pytest.approx(float(rhs), abs=1e-12)
 
 
 def test_correct_golden():
@@ -174,9 +176,10 @@ def test_obs_marginal_sums_to_one_and_floor(tinyw):
 
 
 def test_correct_uniform_sensor_is_renormalisation():
-    w = WL.tiny(2)
-    w.accuracy = 1.0 / (w.B + 1)         # O(x, z) = 1/(B+1) for every x, z
-    bb = O.predict(w, _rand_belief(w, 1), 2) * 0.7
+    w0 = WL.tiny(2)
+    # O(x, z) = 1/(B+1) for every x, z (exact FP64 parameter)
+    w = O.Problem(w0, accuracy=1.0 / (w0.B + 1))
+    bb = O.predict(w, _rand_belief(w0, 1), 2) * 0.7
     for z in range(w.B + 1):
         b, pz = O.correct(w, bb, z)
         assert np.allclose(b, bb / bb.sum(), atol=1e-15)
