@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""QV-Tree Search benchmark: plans/s and belief-state updates/s on GB300.
+
+Default workload: the 128x128 plain configuration (20 % rectangle obstacles,
+16 beacons with range 5 and accuracy 0.85, slip 0.1, discount 0.97, Gaussian
+b0 with sigma 4, depth 3, K = 8, FP32 beliefs and Q), one plan per launch
+sequence.  A step is R planning requests (different start cells on the same
+map), each a complete plan from b0 to the chosen action.  The offline value
+iteration is run once per map and reported separately.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) give every rank
+its own disjoint episodes (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QV-Tree plans/sec and belief-state updates/sec (1 GB300) and % HBM peak"
+L2_FLUSH_BYTES = 256 << 20
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mid", "large", "tiny"], default="mid")
+    ap.add_argument("--plans-per-step", type=int, default=32)
+    ap.add_argument("--leaf-mode", choices=["fused", "materialise"], default="fused")
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_workload(name, seed):
+    from paper_1810_00204_gb300 import workloads as WL
+    if name == "mid":
+        w = WL.mid(seed)
+        desc = ("mid 128x128, 20% rect obstacles, B=16 range 5 acc 0.85, slip 0.1, gamma 0.97, "
+                "gaussian b0 sigma 4, depth 3, K=8, one plan per launch")
+    elif name == "large":
+        w = WL.large(seed)
+        desc = ("large 512x512 rooms+walls 25%, B=64 range 8 acc 0.8, slip 0.1, gamma 0.97, "
+                "gaussian b0 sigma 4, depth 3, K=4, one plan per launch")
+    else:
+        w = WL.tiny(seed)
+        desc = "tiny 20x20, 15% iid obstacles, B=4 range 3 acc 0.9, depth 2, K=4"
+    return w, desc
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="qv_clocks_", suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------- roofline helpers
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def tree_sources_sha():
+    h = hashlib.sha256()
+    for p in ("paper_1810_00204_gb300/csrc/qv_tree.cu", "paper_1810_00204_gb300/csrc/qv_tree_device.cuh",
+              "paper_1810_00204_gb300/csrc/qv_common.cuh"):
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, level, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    sha = tree_sources_sha()
+    pat = re.compile(r"^traffic\s+kernel=(\S+)\s+level=(\d+)\s+workload=(\S+)\s+bytes_per_launch=(\d+)"
+                     r"\s+source_sha=(\S+)")
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith((".txt", ".md")):
+            continue
+        with open(os.path.join(d, fn)) as f:
+            for ln in f:
+                m = pat.match(ln.strip())
+                if m and m.group(1) == kernel and int(m.group(2)) == level and m.group(3) == workload \
+                        and m.group(5) == sha:
+                    return int(m.group(4))
+    return None
+
+
+def phase_bytes(name, level, nodes, N, depth, leaf_mode):
+    """Bytes a phase must move at minimum: every belief it reads or writes
+    once (4 B per cell), the cell words (2 B) once, Q (20 B) once when read.
+    expand(l) reads the level l-1 beliefs (b0 at the root) and writes level l
+    when a later phase reads it back."""
+    b = 4 * N
+    if name in ("expand", "expand_fused"):
+        rd = b if level == 0 else nodes[level - 1] * b
+        stored = level > 0 and (level < depth - 1 or leaf_mode == "materialise")
+        wr = nodes[level] * b if stored else 0
+        return rd + wr + 2 * N + (20 * N if name == "expand_fused" else 0)
+    if name == "update":
+        return nodes[level] * b + nodes[level + 1] * b + 2 * N
+    if name == "leaf":
+        return nodes[level] * b + 20 * N
+    return 0
+
+
+def plan_phases(depth, leaf_mode):
+    ph = [("expand_fused" if (l == depth - 1 and leaf_mode == "fused") else "expand", l) for l in range(depth)]
+    if depth > 0 and leaf_mode == "materialise":
+        ph.append(("update", depth - 1))
+    if depth == 0 or leaf_mode == "materialise":
+        ph.append(("leaf", depth))
+    return ph
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_plans(episodes, Q64, seconds, max_plans=None):
+    import oracle as O
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        w = episodes[n % len(episodes)]
+        O.tree_plan(w, Q64)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_plans and n >= max_plans):
+            return n, el
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_1810_00204_gb300 import workloads as WL
+    O.build()
+    w, desc = make_workload(args.workload, args.seed)
+    eps = WL.episodes(w, max(args.steps + args.warmup, 1), seed=args.seed)
+    Q64 = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)
+    for i in range(args.warmup):
+        O.tree_plan(eps[i % len(eps)], Q64)
+    t = 0.0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        O.tree_plan(eps[(args.warmup + k) % len(eps)], Q64)
+        t += time.perf_counter() - t0
+    value = args.steps / t
+    cores = O.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "plans_per_step": 1, "depth": w.depth, "K": w.K,
+                   "parallelism": "oracle on host cores"},
+        "cpu_baseline": {"value": value, "unit": "plans/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} plans of the workload, one per step, FP64 C oracle "
+                                   f"(OpenMP over tree nodes, {cores} threads)"},
+        "e2e": {"value": value, "unit": "plans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    from paper_1810_00204_gb300 import replicas
+    rank, local_rank, world_size = replicas.world()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    from paper_1810_00204_gb300 import _native as N
+    from paper_1810_00204_gb300 import api, workloads as WL
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world_size > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        G.build()
+    replicas.barrier(dev)
+    N.lib()
+    stream = torch.cuda.current_stream()
+
+    w, desc = make_workload(args.workload, args.seed)
+    R = args.plans_per_step
+    ep_ids = replicas.episode_range(rank, world_size, R)
+    eps = WL.episodes(w, R, seed=args.seed, first_episode=ep_ids.start)
+    model = api.Model(w, device=dev)
+    # offline value iteration (once per map), timed on its own
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vi = api.mdp_value_iterate(model, dtype="f32")
+    torch.cuda.synchronize()
+    vi_ms = 1e3 * (time.perf_counter() - t0)
+    Qd = vi["Q"]
+    leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
+    b0s = [model.to_grid(e.b0) for e in eps]
+    plans = [api.Plan([model], [Qd], [b0s[i]], depth=w.depth, K=w.K, seed=w.seed, episode=e.episode,
+                      leaf_mode=leaf_mode) for i, e in enumerate(eps)]
+    use_graph = not args.no_graph
+    if use_graph:
+        for p in plans:
+            p.capture_graph()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        for p in plans:
+            p.run()
+
+    # warm-up
+    for k in range(max(args.warmup, 0)):
+        flush.fill_(k & 255)
+        step()
+    torch.cuda.synchronize()
+    results = [p.read()[0] for p in plans]
+    nodes_per_plan = [r["nodes_per_level"] for r in results]
+    updates_per_step = sum(sum(n[1:]) for n in nodes_per_plan)
+
+    # timed region: K steps, each bracketed by events on the launching stream;
+    # L2 flushed (256 MiB write) before every step, outside the events
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(gpu_index(local_rank))
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    replicas.barrier(dev)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_((k + 7) & 255)
+        ev0[k].record(stream)
+        step()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    replicas.barrier(dev)
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    dev_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
+    dev_ms_max = replicas.reduce_max(dev_ms, dev)
+    total_plans = R * K * world_size
+    plans_per_s = total_plans / (dev_ms_max / 1e3)
+    updates_per_s = replicas.reduce_sum(updates_per_step * K, dev) / (dev_ms_max / 1e3)
+
+    # kernel profile: k_plan timed by CUDA events on the launching stream
+    # (L2 flushed before each plan), its phases by the device clock
+    Ncell = model.H * model.P
+    phases = plan_phases(w.depth, args.leaf_mode)
+    kplan_ms, ph_ms = [], {}
+    launches_per_plan = 1
+    for k in range(max(1, args.profile_steps)):
+        for p in plans:
+            flush.fill_(k & 255)
+            lst = p.profile()
+            kplan_ms.append(lst[0]["ms"])
+            for it in lst[1:]:
+                ph_ms.setdefault((it["name"].split(":", 1)[1], it["level"]), []).append(it["ms"])
+    abytes = sum(sum(phase_bytes(nm, lv, n, Ncell, w.depth, args.leaf_mode) for nm, lv in phases)
+                 for n in nodes_per_plan) \
+        / len(nodes_per_plan)
+    avg_ms = statistics.mean(kplan_ms)
+    peak, peak_kind = measured_peak()
+    achieved = abytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    traffic = recorded_traffic("k_plan", 0, args.workload)
+    per_phase = {}
+    for (nm, lv), v in ph_ms.items():
+        pb = sum(phase_bytes(nm, lv, n, Ncell, w.depth, args.leaf_mode) for n in nodes_per_plan) / len(nodes_per_plan)
+        ms = statistics.mean(v)
+        per_phase[f"{nm}[{lv}]"] = {"ms": ms, "bytes": pb, "GBps": pb / (ms * 1e-3) / 1e9 if ms > 0 else None}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_plan (whole plan, one launch)",
+                "kernel_share": 1.0, "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": avg_ms,
+                "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
+                else "fallback 6800 GB/s",
+                "phases": per_phase}
+
+    # end to end through the public API with host buffers: pinned b0 -> device,
+    # run, results -> host, every step
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(np.ascontiguousarray(
+            np.pad(e.b0.astype(np.float32), ((0, 0), (0, model.P - model.W))))).pin_memory() for e in eps]
+        h2d = sum(p.numel() * 4 for p in pinned)
+        res_bytes = 4 * 7 + 4 * (w.depth + 1) + 4 + 8
+        t_e2e = 0.0
+        for k in range(max(3, min(K, 200))):
+            flush.fill_(k & 255)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for i, p in enumerate(plans):
+                b0s[i].copy_(pinned[i], non_blocking=True)
+                p.run()
+            for p in plans:
+                p.read()
+            t_e2e += time.perf_counter() - t0
+        n_e2e = max(3, min(K, 200))
+        e2e_val = R * n_e2e / t_e2e
+        e2e_val = replicas.reduce_sum(e2e_val, dev) if world_size > 1 else e2e_val
+        e2e = {"value": e2e_val, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": R * res_bytes,
+               "steps": n_e2e}
+
+    # oracle CPU baseline (rank 0, N = 1 only), bounded sample
+    cpu = None
+    if rank == 0 and world_size == 1 and not args.no_cpu:
+        import oracle as O
+        O.build()
+        oq = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)
+        n, el = oracle_plans(eps, oq, args.cpu_seconds)
+        cpu = {"value": n / el, "unit": "plans/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{n} plans of this workload (same map, {len(eps)} start cells cycled), "
+                         f"{el:.1f} s, FP64 C oracle with OpenMP over tree nodes"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": plans_per_s, "unit": "plans/s", "n_gpus": world_size,
+            "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "plans_per_step": R, "depth": w.depth, "K": w.K,
+                       "leaf_mode": args.leaf_mode, "cuda_graph": use_graph,
+                       "l2": "flushed before every step (256 MiB device write outside the timed events)",
+                       "parallelism": "replicas" if world_size > 1 else "single GPU",
+                       "nodes_per_level": nodes_per_plan[0]},
+            "updates_per_s": updates_per_s,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_plan * R * K,
+            "clocks": clocks,
+            "vi": {"sweeps": vi["sweeps"], "ms": vi_ms, "cells": model.H * model.W,
+                   "cell_sweeps_per_s": model.H * model.W * vi["sweeps"] / (vi_ms / 1e3),
+                   "note": "offline, once per map; not part of plans/s"},
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world_size > 1:
+        replicas.barrier(dev)
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -8,8 +8,10 @@
  * backup of Alg. 2-7.
  *
  * Conventions shared by every call:
- *   - Grids are row-major [H][pitch] with pitch = round_up(W, 4); cell
- *     y = row * pitch + col.  Columns W..pitch-1 are padding (occupied).
+ *   - Grids are row-major [H][pitch] with pitch = QV_PITCH(W) = round_up(W, 8)
+ *     (rows of FP32 beliefs and of uint16 cell words are then whole 16-byte
+ *     units, as the bulk copies need); cell y = row * pitch + col.  Columns
+ *     W..pitch-1 are padding (occupied).
  *   - Actions: 0 = N (row - 1), 1 = E (col + 1), 2 = S (row + 1), 3 = W
  *     (col - 1), 4 = stay.  The intended move succeeds w.p. 1 - 2*slip, each
  *     perpendicular move happens w.p. slip; a move into an occupied or outside
@@ -55,7 +57,8 @@ typedef enum {
 #define QV_MAX_DEPTH 6
 #define QV_MAX_BEACONS 126
 #define QV_MAX_K 64
-#define QV_MAX_WIDTH 4096
+#define QV_MAX_WIDTH 2048
+#define QV_PITCH(W) ((((W) + 7) / 8) * 8)
 
 #define QV_F32 0
 #define QV_F64 1
@@ -67,7 +70,7 @@ typedef enum {
 /* A built model (Sec. II tuple on one grid).  d_cell comes from
  * qv_model_build; the struct itself is plain host memory. */
 typedef struct {
-    int32_t H, W, pitch;       /* grid size; pitch = round_up(W, 4)                     */
+    int32_t H, W, pitch;       /* grid size; pitch = QV_PITCH(W)                        */
     const uint16_t *d_cell;    /* [H][pitch] cell words written by qv_model_build       */
     int32_t num_beacons;       /* B in 1..QV_MAX_BEACONS; |Z| = B + 1                   */
     int32_t goal;              /* goal cell, row * pitch + col, must be free            */
@@ -75,6 +78,9 @@ typedef struct {
     float accuracy;            /* alpha in (0, 1]                                       */
     float discount;            /* gamma in (0, 1)                                       */
     const float *d_cost;       /* nullable [H][pitch] per-cell cost c(y)                */
+    const int32_t *d_beacons;  /* [B] beacon cells as given to qv_model_build; the tree
+                                  search walks each beacon's sensing diamond           */
+    int32_t sense_range;       /* Manhattan sensing range given to qv_model_build       */
 } qv_model_t;
 
 /* Tree-search parameters (Alg. 1-3 with the level-synchronous reading). */
@@ -168,6 +174,17 @@ qv_status qv_plan_run(qv_plan_t *plan, qv_stream_t stream);
  * later qv_plan_run calls launch the graph. */
 qv_status qv_plan_capture_graph(qv_plan_t *plan, qv_stream_t stream);
 qv_status qv_plan_read(qv_plan_t *plan, qv_plan_result_t *h_results, qv_stream_t stream);
+
+/* Run the plan once without the graph, with a CUDA event recorded on
+ * `stream` before the first launch and after every launch; returns for each
+ * launch its kernel name, tree level and duration (ms).  Synchronises. */
+typedef struct {
+    char name[32];
+    int32_t level;
+    float ms;
+} qv_launch_time_t;
+qv_status qv_plan_profile(qv_plan_t *plan, qv_launch_time_t *h_out, int32_t max_launches,
+                          int32_t *n_out, qv_stream_t stream);
 void qv_plan_destroy(qv_plan_t *plan);
 
 /* Device views of one level of episode e after a run (for inspection and

@@ -19,7 +19,7 @@ QV_NUM_ACTIONS = 5
 QV_MAX_DEPTH = 6
 QV_MAX_BEACONS = 126
 QV_MAX_K = 64
-QV_MAX_WIDTH = 4096
+QV_MAX_WIDTH = 2048
 QV_F32, QV_F64 = 0, 1
 QV_WEIGHT_FREQ, QV_WEIGHT_MARGINAL = 0, 1
 QV_LEAF_FUSED, QV_LEAF_MATERIALISE = 0, 1
@@ -28,7 +28,8 @@ QV_LEAF_FUSED, QV_LEAF_MATERIALISE = 0, 1
 class qv_model_t(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("pitch", C.c_int32), ("d_cell", C.c_void_p),
                 ("num_beacons", C.c_int32), ("goal", C.c_int32), ("slip", C.c_float),
-                ("accuracy", C.c_float), ("discount", C.c_float), ("d_cost", C.c_void_p)]
+                ("accuracy", C.c_float), ("discount", C.c_float), ("d_cost", C.c_void_p),
+                ("d_beacons", C.c_void_p), ("sense_range", C.c_int32)]
 
 
 class qv_plan_params_t(C.Structure):
@@ -46,6 +47,10 @@ class qv_level_view_t(C.Structure):
                 ("d_action", C.c_void_p), ("d_obs", C.c_void_p), ("d_weight", C.c_void_p),
                 ("d_pz", C.c_void_p), ("d_value", C.c_void_p), ("d_R", C.c_void_p), ("d_UQ", C.c_void_p),
                 ("d_nchild", C.c_void_p), ("d_samples", C.c_void_p), ("d_belief", C.c_void_p)]
+
+
+class qv_launch_time_t(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("level", C.c_int32), ("ms", C.c_float)]
 
 
 # every symbol include/qvts.h declares, with (restype, argtypes)
@@ -69,6 +74,7 @@ SIGNATURES = {
     "qv_plan_capture_graph": (C.c_int, [_vp, _vp]),
     "qv_plan_read": (C.c_int, [_vp, C.POINTER(qv_plan_result_t), _vp]),
     "qv_plan_destroy": (None, [_vp]),
+    "qv_plan_profile": (C.c_int, [_vp, C.POINTER(qv_launch_time_t), _i32, C.POINTER(C.c_int32), _vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
     "qv_tree_plan": (C.c_int, [_M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
     "qv_tree_plan_batched": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),

@@ -21,7 +21,8 @@ __all__ = ["Model", "Plan", "qv_model_build", "mdp_value_iterate", "belief_predi
 
 
 def pitch_of(W: int) -> int:
-    return (W + 3) // 4 * 4
+    """QV_PITCH(W): row pitch in cells, a multiple of 8."""
+    return (W + 7) // 8 * 8
 
 
 def _stream(stream=None):
@@ -63,9 +64,11 @@ class Model:
         self.slip = float(w.slip if slip is None else slip)
         self.accuracy = float(w.accuracy if accuracy is None else accuracy)
         self.discount = float(w.discount)
+        self.sense_range = int(w.sense_range)
         self.struct = N.qv_model_t(self.H, self.W, self.P, self.cell.data_ptr(), self.B, self.goal,
                                    self.slip, self.accuracy, self.discount,
-                                   None if self.cost is None else self.cost.data_ptr())
+                                   None if self.cost is None else self.cost.data_ptr(),
+                                   self.beacons.data_ptr(), self.sense_range)
 
     def pcell(self, x: int) -> int:
         """Unpadded cell index r*W + c -> pitched index r*pitch + c."""
@@ -192,6 +195,14 @@ class Plan:
         res = (N.qv_plan_result_t * self.E)()
         check(lib().qv_plan_read(self.handle, res, _stream(stream)), "qv_plan_read")
         return [_result_dict(res[e], self.depth) for e in range(self.E)]
+
+    def profile(self, stream=None) -> List[dict]:
+        """One eager run with a CUDA event after every launch (synchronises)."""
+        out = (N.qv_launch_time_t * 64)()
+        n = C.c_int32(0)
+        check(lib().qv_plan_profile(self.handle, out, 64, C.byref(n), _stream(stream)), "qv_plan_profile")
+        return [dict(name=out[i].name.decode(), level=int(out[i].level), ms=float(out[i].ms))
+                for i in range(n.value)]
 
     def _view(self, ptr, count, dtype, shape=None):
         if not ptr:

@@ -141,7 +141,7 @@ constexpr int kCorrectBlocks = 512;
 
 qv_status check_model(const qv_model_t *m, const char *who) {
     if (!m || !m->d_cell) return qv_set_error(QV_ERR_INVALID, "%s: null model", who);
-    if (m->H < 1 || m->W < 1 || m->W > QV_MAX_WIDTH || m->pitch != ((m->W + 3) / 4) * 4)
+    if (m->H < 1 || m->W < 1 || m->W > QV_MAX_WIDTH || m->pitch != QV_PITCH(m->W))
         return qv_set_error(QV_ERR_INVALID, "%s: bad grid %dx%d pitch %d", who, m->H, m->W, m->pitch);
     if (m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
         return qv_set_error(QV_ERR_INVALID, "%s: B=%d", who, m->num_beacons);

@@ -1,0 +1,1298 @@
+// qv_tree_device.cuh -- device side of the QV-tree search: one persistent
+// cooperative kernel (k_plan) per plan or per batch of episodes.
+//
+// Phases of k_plan, separated by a bounded grid barrier:
+//   expand(l)  for every V-node of level l (Alg. 2: every action) and a range
+//              of row bands: the node's belief band.  At the root that is b0;
+//              below it the band is recomputed from the parent's band (staged
+//              with a two-row halo) as Phi(parent, a, z) of Eq. 3, and
+//              written out when a later phase needs it.  On that band: the
+//              motion stencil for all five actions (Eq. 3 numerator, Eq. 10),
+//              the label histograms that give P(z | b, a) (Eq. 3
+//              denominator) and R(b, a) (Sec. III).  Cells of the null label
+//              are summed in registers; each beacon's sensing diamond is
+//              summed by one warp, so no histogram needs atomics.  The last
+//              work item of a node finalises it: K Philox draws per action
+//              inverted through the CDF (Alg. 3-4), the unique draws with
+//              their frequencies.  The last node of an episode numbers its
+//              children (prefix sum in (parent, action, z) order); the last
+//              episode publishes the next level's work list.  At the deepest
+//              internal level of the fused leaf mode the pass also sums
+//              Q-weighted histograms, so every leaf value
+//              max_a' sum_y b'(y) Q(a', y) (Eq. 4, Alg. 5) and the node's own
+//              Q-node values (Alg. 6) follow without forming the leaves.
+//   update     (materialised leaves) Phi(b, a, z) for every leaf: one read of
+//              the parent band, one coalesced write per leaf.
+//   leaf       (materialised leaves) streams leaf beliefs against Q.
+//   backup     Alg. 6 / 7 bottom-up and the root argmax.
+//
+// Every band a work item touches arrives in shared memory by bulk (TMA)
+// copies completing on one mbarrier: the belief rows with their halo, the
+// cell words and, at the fused level, the band's rows of Q.
+//
+// Work items are (episode, node, band range) entries of per-level lists whose
+// prefix sums and band splits are written on the device from the actual level
+// sizes, so one launch covers episodes of uneven size and the host never
+// waits for a level.
+#pragma once
+
+#include "qv_common.cuh"
+
+namespace qv {
+
+constexpr int kMaxD = QV_MAX_DEPTH;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kLeafGroup = 4;
+constexpr int kBandCells = 2048;
+constexpr float kBoundaryEps = 1e-6f;
+constexpr int kStamps = 4 * kMaxD + 8;
+
+struct __align__(16) EpDev {
+    int H, W, P, N;          // N = H * P
+    int B, goal;
+    float slip, acc, eta, gamma;
+    const uint16_t *cell;
+    const float *cost;
+    const float *Q;          // [5][N]
+    const float *b0;         // [N]
+    const int *beacons;      // [B] beacon cells (row * P + col)
+    int range;               // Manhattan sensing range
+    int band_rows, bands;
+    uint32_t episode;
+    int cap[kMaxD + 1];         // node capacity of each level
+    int node_base[kMaxD + 1];   // gid of local node 0 of level l
+    int inode_base[kMaxD + 1];  // iid of local node 0 of internal level l < d
+    int pad2;
+    long long belief_off[kMaxD + 1];  // float offset of stored level-l beliefs, -1 when not stored
+};
+static_assert(sizeof(EpDev) % 16 == 0, "EpDev is copied to smem in 16-byte words");
+
+// The scalars the band loops read, held in registers for the duration of a
+// work item (reading them from the shared-memory descriptor inside the loops
+// would reload them after every shared-memory store).
+struct EpReg {
+    int H, W, P, N, B, goal, range;
+    float slip;
+    const uint16_t *cell;
+    const float *cost, *Q;
+};
+__device__ __forceinline__ EpReg ep_reg(const EpDev &e) {
+    EpReg r;
+    r.H = e.H;
+    r.W = e.W;
+    r.P = e.P;
+    r.N = e.N;
+    r.B = e.B;
+    r.goal = e.goal;
+    r.range = e.range;
+    r.slip = e.slip;
+    r.cell = e.cell;
+    r.cost = e.cost;
+    r.Q = e.Q;
+    return r;
+}
+
+struct ResultDev {
+    int action;
+    float value;
+    float q[5];
+    int pad;
+};
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+struct PlanDev {
+    int E, depth, K, weight_mode, leaf_mode, Bmax, rec_len, target, n_part;
+    int sb_floats, sp_floats, q_floats;  // shared-memory band buffers
+    uint64_t seed;
+    const EpDev *eps;
+    float *beliefs;
+    int *count;        // [(d+1)][E] nodes per level
+    int *items;        // [(d+1)][E] expand work items per node
+    int *uitems;       // [(d+1)][E] update work items per node
+    int *wb_stats;     // [(d+1)][E+1] work-list prefixes
+    int *wb_upd;       // [(d+1)][E+1]
+    int *wb_leaf;      // [E+1]
+    // per node (gid over every level)
+    int *parent, *action, *obs;
+    float *weight, *pz, *value;
+    unsigned long long *code;
+    long long *src_slot;  // slot of the node in its parent's sample arrays
+    // per internal node (iid over levels < d)
+    unsigned *node_cnt;
+    float *R, *UQ;     // [iid][5]
+    int *nchild, *choff;
+    int *samples;      // [iid][5][K]
+    int *slot_z, *slot_cnt;
+    float *slot_P, *slot_w, *slot_val;
+    // arrival counters and scratch
+    unsigned *ep_cnt;  // [(d+1)][E]
+    unsigned *lvl_cnt; // [d+1]
+    float *partials;   // [n_part][rec_len]
+    unsigned *status;
+    unsigned long long *boundary;
+    GridBar *bar;
+    unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
+    ResultDev *result; // [E]
+    const int *replay;
+};
+
+// Shared-memory carve-up of k_plan (same arithmetic on host and device).
+struct SmemLayout {
+    size_t sb, sp, cw, q, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, u_n, u_off, u_z, u_sa, u_se, scan,
+        flags, total;
+    __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K) {
+        SmemLayout s;
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            o = (o + 15) & ~size_t(15);
+            const size_t r = o;
+            o += bytes;
+            return r;
+        };
+        s.sb = take(sizeof(float) * sb_floats);      // node band, one halo row
+        s.sp = take(sizeof(float) * sp_floats);      // parent band, two halo rows
+        s.cw = take(sizeof(uint16_t) * sb_floats);   // cell words, one halo row
+        s.q = take(sizeof(float) * q_floats);        // the band's rows of Q
+        s.ep = take(sizeof(EpDev));
+        s.bco = take(sizeof(int) * 2 * Bm);          // beacon (row, col)
+        s.hist = take(sizeof(float) * 5 * Bm);
+        s.histq = take(sizeof(float) * 25 * Bm);
+        s.tot = take(sizeof(float) * 36);
+        s.red = take(sizeof(float) * kWarps * 36);
+        s.P = take(sizeof(float) * 5 * (Bm + 1));
+        s.C = take(sizeof(float) * 5 * (Bm + 1));
+        s.cnt = take(sizeof(int) * 5 * (Bm + 1));
+        s.T = take(sizeof(float) * 28);
+        s.uq = take(sizeof(float) * 8);
+        s.lut = take(sizeof(float) * 64);
+        s.u_n = take(sizeof(int) * 8);
+        s.u_off = take(sizeof(int) * 8);
+        s.u_z = take(sizeof(int) * 5 * K);
+        s.u_sa = take(sizeof(float) * 5 * K);
+        s.u_se = take(sizeof(float) * 5 * K);
+        s.scan = take(sizeof(int) * (kWarps + 4));
+        s.flags = take(sizeof(int) * 8);
+        s.total = (o + 127) & ~size_t(127);
+        return s;
+    }
+};
+
+struct Smem {
+    float *sb, *sp, *q;
+    uint16_t *cw;
+    EpDev *ep;
+    int *bco;
+    float *hist, *histq, *tot, *red, *P, *C, *T, *uq, *lut;
+    int *cnt;
+    int *u_n, *u_off, *u_z;
+    float *u_sa, *u_se;
+    int *scan, *flags;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ int find_episode(const int *wb, int E, int w) {
+    int lo = 0, hi = E - 1;  // last e with wb[e] <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldcg(wb + mid) <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpDev &ep, int l, int local) {
+    if (l == 0) return ep.b0;
+    return pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N;
+}
+
+__device__ __forceinline__ void fill_self_lut(float *lut, float slip) {
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, slip);
+}
+
+// Copy the descriptor of episode e (and its beacon coordinates) into shared
+// memory, once per change of episode.
+__device__ __forceinline__ void load_ep(const PlanDev &pl, int e, Smem &S, int &cur_e) {
+    if (e == cur_e) return;
+    __syncthreads();
+    const int4 *src = reinterpret_cast<const int4 *>(pl.eps + e);
+    int4 *dst = reinterpret_cast<int4 *>(S.ep);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(EpDev) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const EpDev &ep = *S.ep;
+    for (int k = threadIdx.x; k < ep.B; k += blockDim.x) {
+        const int b = __ldg(ep.beacons + k);
+        S.bco[2 * k] = b / ep.P;
+        S.bco[2 * k + 1] = b - (b / ep.P) * ep.P;
+    }
+    fill_self_lut(S.lut, ep.slip);
+    __syncthreads();
+    cur_e = e;
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded grid barrier; every CTA of the cooperative launch calls it the
+// same number of times.  False (for every CTA) once any wait gave up.
+__device__ bool grid_sync(const PlanDev &pl) {
+    __shared__ int s_ok;
+    fence_proxy_async_global();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = &pl.bar->gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&pl.bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&pl.bar->count, 0u);
+            __threadfence();
+            atomicAdd(&pl.bar->gen, 1u);
+        } else {
+            unsigned i = 0;
+            while (*gen == g) {
+                if (++i > kSpinLimit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+                    atomicOr(pl.status, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*((volatile unsigned *)pl.status) & kErrTimeout) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void stamp(const PlanDev &pl, int slot) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && slot < kStamps) pl.stamps[slot] = globaltimer();
+}
+
+// Optional tracing (compiled in with -DQV_TRACE): device-clock timestamps of
+// the steps of every expand work item, for latency analysis.
+constexpr int kTraceWords = 16;
+constexpr int kTraceRecords = 1 << 16;
+#ifdef QV_TRACE
+__device__ unsigned long long g_trace[kTraceRecords][kTraceWords];
+__device__ unsigned g_trace_n;
+#define QV_TRACE_MARK(arr, k) \
+    do {                      \
+        if (threadIdx.x == 0) arr[k] = globaltimer(); \
+    } while (0)
+__device__ __forceinline__ void trace_commit(const unsigned long long *t, int n) {
+    if (threadIdx.x != 0) return;
+    const unsigned i = atomicAdd(&g_trace_n, 1u);
+    if (i < kTraceRecords)
+        for (int k = 0; k < n && k < kTraceWords; ++k) g_trace[i][k] = t[k];
+}
+#else
+#define QV_TRACE_MARK(arr, k) \
+    do {                      \
+    } while (0)
+#endif
+
+// Stage one band on one mbarrier: belief rows [r0-h, r1+h) of `b` (zero
+// outside the grid) into bbuf; the cell words of rows [r0-1, r1+1) into cw
+// (cw row i = grid row r0-1+i); and, when q is given, rows [r0, r1) of the
+// five Q planes into q (plane stride (r1-r0)*P).  Bounded wait, one decision
+// for the whole CTA.
+__device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int h, float *bbuf, uint16_t *cw,
+                           float *q, uint64_t *bar, unsigned &phase, unsigned *status) {
+    const int P = ep.P;
+    __syncthreads();  // previous readers of the buffers are done
+    for (int r = r0 - h; r < r0; ++r)
+        if (r < 0)
+            for (int i = threadIdx.x; i < P; i += blockDim.x) bbuf[(r - (r0 - h)) * P + i] = 0.0f;
+    for (int r = r1; r < r1 + h; ++r)
+        if (r >= ep.H)
+            for (int i = threadIdx.x; i < P; i += blockDim.x) bbuf[(r - (r0 - h)) * P + i] = 0.0f;
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fence_proxy_async_global();
+        const int lo = max(0, r0 - h), hi = min(ep.H, r1 + h);
+        const int clo = max(0, r0 - 1), chi = min(ep.H, r1 + 1);
+        const unsigned bb = static_cast<unsigned>((hi - lo) * P * sizeof(float));
+        const unsigned cb = static_cast<unsigned>((chi - clo) * P * sizeof(uint16_t));
+        const unsigned qb = static_cast<unsigned>((r1 - r0) * P * sizeof(float));
+        mbar_arrive_expect_tx(bar, bb + cb + (q ? 5u * qb : 0u));
+        bulk_copy_g2s(bbuf + (lo - (r0 - h)) * P, b + static_cast<size_t>(lo) * P, bb, bar);
+        bulk_copy_g2s(cw + (clo - (r0 - 1)) * P, ep.cell + static_cast<size_t>(clo) * P, cb, bar);
+        if (q)
+            for (int a = 0; a < 5; ++a)
+                bulk_copy_g2s(q + a * (r1 - r0) * P, ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0) * P,
+                              qb, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase);
+    const int failed = __syncthreads_or(ok ? 0 : 1);
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(status, kErrTimeout);
+        if (!ok) mbar_wait_bounded(bar, phase);  // let the copies in flight land before leaving
+    }
+    phase ^= 1u;
+    return failed == 0;
+}
+
+// Neighbourhood of the 4 cells (row, col..col+3): `mid` points at the
+// cell's row inside a staged belief buffer (rows P floats apart), `cwr` at
+// the same row of the staged cell words.
+struct Nbr4 {
+    float u[4], m[6], d[4];
+    unsigned cw[4];
+};
+__device__ __forceinline__ void load_nbr(const EpReg &ep, const float *mid, const uint16_t *cwr, int col, Nbr4 &n) {
+    const int P = ep.P;
+    const float4 up = *reinterpret_cast<const float4 *>(mid - P + col);
+    const float4 md = *reinterpret_cast<const float4 *>(mid + col);
+    const float4 dn = *reinterpret_cast<const float4 *>(mid + P + col);
+    n.u[0] = up.x; n.u[1] = up.y; n.u[2] = up.z; n.u[3] = up.w;
+    n.m[0] = col > 0 ? mid[col - 1] : 0.0f;
+    n.m[1] = md.x; n.m[2] = md.y; n.m[3] = md.z; n.m[4] = md.w;
+    n.m[5] = col + 4 < P ? mid[col + 4] : 0.0f;
+    n.d[0] = dn.x; n.d[1] = dn.y; n.d[2] = dn.z; n.d[3] = dn.w;
+    const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(cwr + col);
+    n.cw[0] = cw4.x; n.cw[1] = cw4.y; n.cw[2] = cw4.z; n.cw[3] = cw4.w;
+}
+
+__device__ __forceinline__ void inflow_nb(const Nbr4 &n, int j, float nb[4]) {
+    const unsigned in = QV_CELL_INFLOW(n.cw[j]);
+    nb[kDirN] = (in & 1u) ? n.u[j] : 0.0f;
+    nb[kDirE] = (in & 2u) ? n.m[j + 2] : 0.0f;
+    nb[kDirS] = (in & 4u) ? n.d[j] : 0.0f;
+    nb[kDirW] = (in & 8u) ? n.m[j] : 0.0f;
+}
+
+// Predicted mass of one cell (column c of the staged row `mid`) for all
+// five actions.
+__device__ __forceinline__ void predict_at(const EpReg &ep, const float *mid, int c, unsigned cw, bool is_goal,
+                                           const float *lut, float out[5]) {
+    const unsigned in = QV_CELL_INFLOW(cw);
+    float nb[4];
+    nb[kDirN] = (in & 1u) ? mid[c - ep.P] : 0.0f;
+    nb[kDirE] = (in & 2u) ? mid[c + 1] : 0.0f;
+    nb[kDirS] = (in & 4u) ? mid[c + ep.P] : 0.0f;
+    nb[kDirW] = (in & 8u) ? mid[c - 1] : 0.0f;
+    predict_cell(nb, mid[c], cw, is_goal, ep.slip, lut, out);
+}
+
+__device__ int block_exclusive_scan(int v, int *s_warp, int &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < kWarps; ++k) {
+            const int t = s_warp[k];
+            s_warp[k] = run;
+            run += t;
+        }
+        s_warp[kWarps] = run;
+    }
+    __syncthreads();
+    const int ex = x - v + s_warp[wid];
+    total = s_warp[kWarps];
+    __syncthreads();
+    return ex;
+}
+
+// ---------------------------------------------------------------- node finalisation
+// P(z | b, a) from the label histograms, R(b, a), K Philox draws per action
+// inverted through the FP32 CDF, the unique draws with their frequencies.
+// At the fused leaf level also each child's leaf value and then the node's
+// U_Q (Alg. 6, discounted as in Eq. 2) and U_V (Alg. 7).  One warp per action.
+__device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int local, bool fused, float bgoal,
+                              unsigned long long code, Smem &S) {
+    const int B = ep.B, nz = B + 1, K = pl.K, Bm = pl.Bmax;
+    const int iid = ep.inode_base[l] + local;
+    const float eta = ep.eta, acc = ep.acc;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 5 * nz; i += blockDim.x) S.cnt[i] = 0;
+    if (fused && threadIdx.x >= 160 && threadIdx.x < 185) {
+        const int t = threadIdx.x - 160, a = t / 5, ap = t % 5;
+        float s = S.tot[10 + t];
+        for (int z = 0; z < B; ++z) s += S.histq[(a * Bm + z) * 5 + ap];
+        S.T[t] = s;
+    }
+    if (wid < 5 && lane == 0) {
+        // the cumulative sum runs in ascending z, in FP32, as the sampler's
+        // inverse CDF is defined
+        const int a = wid;
+        float Ssum = S.tot[a];
+        for (int z = 0; z < B; ++z) Ssum += S.hist[a * Bm + z];
+        float run = 0.0f;
+        for (int z = 0; z < nz; ++z) {
+            const float M = z < B ? S.hist[a * Bm + z] : S.tot[a];
+            const float p = fmaf(acc - eta, M, eta * Ssum);
+            S.P[a * nz + z] = p;
+            run = run + p;
+            S.C[a * nz + z] = run;
+        }
+        pl.R[iid * 5 + a] = S.tot[5 + a] - 100.0f * bgoal;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 5 * K; t += blockDim.x) {
+        const int a = t / K, k = t - a * K;
+        const float *C = S.C + a * nz;
+        const float u = sample_uniform(pl.seed, ep.episode, l, code * 5ull + a, k);
+        int z;
+        if (pl.replay) {
+            z = __ldg(pl.replay + (static_cast<long long>(iid) * 5 + a) * K + k);
+            z = min(max(z, 0), B);
+        } else {
+            const float t_u = u * C[B];
+            int lo = 0, hi = B;  // first z with t_u < C[z]
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (t_u < C[mid]) hi = mid;
+                else lo = mid + 1;
+            }
+            z = lo;
+        }
+        const float inv = 1.0f / C[B];
+        const bool near = (z < B && fabsf(u - C[z] * inv) < kBoundaryEps) ||
+                          (z > 0 && fabsf(u - C[z - 1] * inv) < kBoundaryEps);
+        if (near) atomicAdd(pl.boundary, 1ull);
+        pl.samples[(static_cast<long long>(iid) * 5 + a) * K + k] = z;
+        atomicAdd(&S.cnt[a * nz + z], 1);
+    }
+    __syncthreads();
+    if (wid < 5) {
+        const int a = wid;
+        const long long sb = (static_cast<long long>(iid) * 5 + a) * K;
+        int base = 0;
+        float psum = 0.0f;
+        for (int zc = 0; zc < nz; zc += 32) {
+            const int z = zc + lane;
+            const int c = z < nz ? S.cnt[a * nz + z] : 0;
+            const float p = z < nz ? S.P[a * nz + z] : 0.0f;
+            const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (c > 0) {
+                pl.slot_z[sb + pos] = z;
+                pl.slot_cnt[sb + pos] = c;
+                pl.slot_P[sb + pos] = p;
+                if (fused) {
+                    float best = -3.402823466e38f;
+                    for (int ap = 0; ap < 5; ++ap) {
+                        const float mq = z < B ? S.histq[(a * Bm + z) * 5 + ap] : S.tot[10 + a * 5 + ap];
+                        const float v = fmaf(acc - eta, mq, eta * S.T[a * 5 + ap]) / p;
+                        best = v > best ? v : best;
+                    }
+                    pl.slot_val[sb + pos] = best;
+                }
+            }
+            psum += warp_sum(c > 0 ? p : 0.0f);
+            base += __popc(bal);
+        }
+        base = 0;
+        float sv = 0.0f;  // sum of weight * leaf value over this action's children
+        for (int zc = 0; zc < nz; zc += 32) {
+            const int z = zc + lane;
+            const int c = z < nz ? S.cnt[a * nz + z] : 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
+            const int pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (c > 0) {
+                const float wgt = pl.weight_mode == QV_WEIGHT_MARGINAL ? S.P[a * nz + z] / psum
+                                                                        : static_cast<float>(c) / K;
+                pl.slot_w[sb + pos] = wgt;
+                if (fused) sv += wgt * pl.slot_val[sb + pos];
+            }
+            base += __popc(bal);
+        }
+        if (lane == 0) pl.nchild[iid * 5 + a] = base;
+        if (fused) {
+            // children in ascending z, as the backup sums them
+            const float total = warp_sum(sv);
+            if (lane == 0) {
+                const float uq = fmaf(ep.gamma, total, S.tot[5 + a] - 100.0f * bgoal);
+                pl.UQ[iid * 5 + a] = uq;
+                S.uq[a] = uq;
+            }
+        }
+    }
+    __syncthreads();
+    if (fused && threadIdx.x == 0) {
+        float best = S.uq[0];
+        for (int a = 1; a < 5; ++a) best = fmaxf(best, S.uq[a]);
+        pl.value[ep.node_base[l] + local] = best;
+    }
+    __threadfence();
+    __syncthreads();
+}
+
+// Number the children of every node of episode e at level l in (parent,
+// action, z) order: prefix sum of the unique-sample counts, and for every
+// child the slot of its sample record.  The child's own records are written
+// by whoever first reads the child (the next expand phase, or the backup).
+__device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e, Smem &S) {
+    const int n = __ldcg(pl.count + l * pl.E + e);
+    const int M = n * 5;
+    const long long ia = static_cast<long long>(ep.inode_base[l]) * 5;
+    const int K = pl.K;
+    const int cap = ep.cap[l + 1];
+    int running = 0;
+    for (int base = 0; base < M; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const int v = i < M ? __ldcg(pl.nchild + ia + i) : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, S.scan, total);
+        if (i < M) {
+            const int off = running + ex;
+            pl.choff[ia + i] = off;
+            for (int j = 0; j < v; ++j)
+                if (off + j < cap) pl.src_slot[ep.node_base[l + 1] + off + j] = (ia + i) * K + j;
+        }
+        running += total;
+    }
+    int nn = running;
+    if (nn > cap) {
+        if (threadIdx.x == 0) atomicOr(pl.status, kErrCapacity);
+        nn = cap;
+    }
+    if (threadIdx.x == 0) pl.count[(l + 1) * pl.E + e] = nn;
+    __threadfence();
+    __syncthreads();
+}
+
+// The next level's work lists: band split per node from the actual level
+// size (about `target` items in all), then the per-episode prefix sums.
+__device__ void level_prefix(const PlanDev &pl, int l1) {
+    if (threadIdx.x != 0) return;
+    const int E = pl.E;
+    long long T = 0;
+    for (int e = 0; e < E; ++e) T += __ldcg(pl.count + l1 * E + e);
+    const long long want = T > 0 ? (pl.target + T - 1) / T : 1;
+    int ws = 0, wu = 0, wl = 0;
+    for (int e = 0; e < E; ++e) {
+        const int c = __ldcg(pl.count + l1 * E + e);
+        const int bands = __ldg(&pl.eps[e].bands);
+        const int it = static_cast<int>(min(max(want, 1LL), static_cast<long long>(bands)));
+        pl.items[l1 * E + e] = it;
+        pl.uitems[l1 * E + e] = it;
+        pl.wb_stats[l1 * (E + 1) + e] = ws;
+        pl.wb_upd[l1 * (E + 1) + e] = wu;
+        if (l1 == pl.depth) pl.wb_leaf[e] = wl;
+        if (l1 < pl.depth) ws += c * it;
+        wu += c * it;
+        wl += (c + kLeafGroup - 1) / kLeafGroup;
+    }
+    pl.wb_stats[l1 * (E + 1) + E] = ws;
+    pl.wb_upd[l1 * (E + 1) + E] = wu;
+    if (l1 == pl.depth) pl.wb_leaf[E] = wl;
+    __threadfence();
+}
+
+// A node of episode e at level l is final: the last one numbers the
+// episode's children, the last episode publishes the next level.
+__device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem &S) {
+    if (threadIdx.x == 0) {
+        const int n = __ldcg(pl.count + l * pl.E + e);
+        const unsigned prev = atomicAdd(pl.ep_cnt + l * pl.E + e, 1u);
+        const int last = prev == static_cast<unsigned>(n - 1);
+        if (last) pl.ep_cnt[l * pl.E + e] = 0u;
+        S.flags[1] = last;
+    }
+    __syncthreads();
+    if (!S.flags[1]) return;
+    __threadfence();
+    compact_episode(pl, l, ep, e, S);
+    if (threadIdx.x == 0) {
+        const unsigned prev = atomicAdd(pl.lvl_cnt + l, 1u);
+        const int last = prev == static_cast<unsigned>(pl.E - 1);
+        if (last) pl.lvl_cnt[l] = 0u;
+        S.flags[2] = last;
+    }
+    __syncthreads();
+    if (!S.flags[2]) return;
+    __threadfence();
+    level_prefix(pl, l + 1);
+    __syncthreads();
+}
+
+// Node band from the parent band: rows [r0-1, r1+1) of Phi(parent, a, z)
+// into `sb` (zero outside the grid), rows [r0, r1) also to `dst` if given.
+// `sp` holds parent rows [r0-2, r1+2), `cw` the cell words of [r0-1, r1+1).
+__device__ __forceinline__ void build_band(const EpReg &ep, const float *sp, const uint16_t *cw, float *sb, int r0,
+                                           int r1, int a, int z, float sa, float se, const float *lut, float *dst) {
+    const int P = ep.P, P4 = P >> 2;
+    const int rows = r1 - r0 + 2;
+    for (int gi = threadIdx.x; gi < rows * P4; gi += blockDim.x) {
+        const int ri = gi / P4, col = (gi - ri * P4) << 2;
+        const int r = r0 - 1 + ri;
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r >= 0 && r < ep.H) {
+            const int y = r * P + col;
+            Nbr4 n;
+            load_nbr(ep, sp + (ri + 1) * P, cw + ri * P, col, n);
+            float v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float nb[4], out[5];
+                inflow_nb(n, j, nb);
+                predict_cell(nb, n.m[j + 1], n.cw[j], (y + j) == ep.goal, ep.slip, lut, out);
+                float pa = out[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) pa = (a == q) ? out[q] : pa;
+                v[j] = pa * (static_cast<int>(QV_CELL_LABEL(n.cw[j])) == z ? sa : se);
+            }
+            o = make_float4(v[0], v[1], v[2], v[3]);
+            if (dst && ri >= 1 && ri <= r1 - r0) *reinterpret_cast<float4 *>(dst + y) = o;
+        }
+        *reinterpret_cast<float4 *>(sb + ri * P + col) = o;
+    }
+    __syncthreads();
+}
+
+// Integer floor(sqrt(t)) for 0 <= t < 2^24.
+__device__ __forceinline__ int isqrt_floor(int t) {
+    int i = static_cast<int>(sqrtf(static_cast<float>(t)));
+    while (i * i > t) --i;
+    while ((i + 1) * (i + 1) <= t) ++i;
+    return i;
+}
+
+// Cell t of the Manhattan diamond of radius R around (br, bc), counted row
+// by row from the top: rows i = 0..R hold 2i+1 cells (i^2 before row i), the
+// rows below mirror them.
+__device__ __forceinline__ void diamond_cell(int t, int R, int br, int bc, int &r, int &c) {
+    const int top = (R + 1) * (R + 1);
+    if (t < top) {
+        const int i = isqrt_floor(t);
+        r = br - R + i;
+        c = bc - i + (t - i * i);
+    } else {
+        const int t2 = (2 * R * R + 2 * R) - t;  // index counted from the last cell
+        const int i = isqrt_floor(t2);
+        r = br + R - i;
+        c = bc + i - (t2 - i * i);
+    }
+}
+
+// Label histograms of one staged band: every beacon's sensing diamond is
+// walked by one warp (lanes over the diamond's cells), cells whose label is
+// that beacon are summed in registers, then one warp reduction adds the
+// totals to the CTA's histograms.  Each beacon belongs to one warp, so no
+// two writers meet.
+template <bool FUSED>
+__device__ __forceinline__ void label_pass(const EpReg &ep, const float *sb, const uint16_t *cw, const float *q,
+                                           int r0, int r1, Smem &S, int Bm) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int R = ep.range;
+    const int ncell = 2 * R * R + 2 * R + 1;
+    const int qstride = (r1 - r0) * ep.P;
+    for (int k = wid; k < ep.B; k += kWarps) {
+        const int br = S.bco[2 * k], bc = S.bco[2 * k + 1];
+        if (br + R < r0 || br - R >= r1) continue;
+        float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float lq[FUSED ? 25 : 1];
+#pragma unroll
+        for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
+        for (int t = lane; t < ncell; t += 32) {
+            int r, c;
+            diamond_cell(t, R, br, bc, r, c);
+            if (r < r0 || r >= r1 || c < 0 || c >= ep.W) continue;
+            const int row = r - r0 + 1;
+            const unsigned cwv = cw[row * ep.P + c];
+            if (static_cast<int>(QV_CELL_LABEL(cwv)) != k) continue;
+            float out[5];
+            predict_at(ep, sb + row * ep.P, c, cwv, (r * ep.P + c) == ep.goal, S.lut, out);
+#pragma unroll
+            for (int a = 0; a < 5; ++a) la[a] += out[a];
+            if constexpr (FUSED) {
+                float qv[5];
+#pragma unroll
+                for (int ap = 0; ap < 5; ++ap) qv[ap] = q[ap * qstride + (r - r0) * ep.P + c];
+#pragma unroll
+                for (int a = 0; a < 5; ++a)
+#pragma unroll
+                    for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            const float t = warp_sum(la[a]);
+            if (lane == 0) S.hist[a * Bm + k] += t;
+        }
+        if constexpr (FUSED) {
+#pragma unroll
+            for (int i = 0; i < 25; ++i) {
+                const float t = warp_sum(lq[i]);
+                if (lane == 0) S.histq[((i / 5) * Bm + k) * 5 + i % 5] += t;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- expand phase
+template <bool FUSED>
+__device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S, uint64_t *mbar, unsigned &mphase,
+                             int &cur_e) {
+    const int E = pl.E, Bm = pl.Bmax, K = pl.K;
+    const int *wb = pl.wb_stats + l * (E + 1);
+    const int total = __ldcg(wb + E);
+    constexpr int NV = FUSED ? 35 : 10;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+#ifdef QV_TRACE
+        unsigned long long tr[kTraceWords] = {};
+#endif
+        QV_TRACE_MARK(tr, 2);
+        const int e = find_episode(wb, E, w);
+        load_ep(pl, e, S, cur_e);
+        const EpDev &ep = *S.ep;
+        const int items = __ldcg(pl.items + l * E + e);
+        const int w0e = __ldcg(wb + e);
+        const int rel = w - w0e;
+        const int local = rel / items, item = rel - local * items;
+#ifdef QV_TRACE
+        tr[0] = static_cast<unsigned long long>(l) | (static_cast<unsigned long long>(items) << 8) |
+                (static_cast<unsigned long long>(blockIdx.x) << 24);
+        tr[1] = static_cast<unsigned long long>(w);
+#endif
+        const int B = ep.B;
+        const int gid = ep.node_base[l] + local;
+        unsigned long long code = 0ull;
+        int pa = 0, pzv = 0;
+        float sa = 0.f, se = 0.f;
+        const float *src = ep.b0;
+        if (l > 0) {
+            // the node's sample record in its parent's arrays: (iid_p * 5 + a) * K + j
+            const long long s = __ldcg(pl.src_slot + gid);
+            const int iid_p = static_cast<int>(s / (5LL * K));
+            pa = static_cast<int>((s / K) % 5);
+            const int par = iid_p - ep.inode_base[l - 1];
+            pzv = __ldcg(pl.slot_z + s);
+            const float p = __ldcg(pl.slot_P + s);
+            const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l - 1] + par);
+            code = (pcode * 5ull + pa) * static_cast<unsigned long long>(B + 1) + pzv;
+            sa = ep.acc / p;
+            se = ep.eta / p;
+            src = node_belief(pl, ep, l - 1, par);
+            if (item == 0 && threadIdx.x == 0) {
+                pl.parent[gid] = par;
+                pl.action[gid] = pa;
+                pl.obs[gid] = pzv;
+                pl.weight[gid] = __ldcg(pl.slot_w + s);
+                pl.pz[gid] = p;
+                pl.code[gid] = code;
+            }
+        }
+        float *dst = (l > 0 && write_node) ? pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N
+                                           : nullptr;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 5 * Bm; i += blockDim.x) S.hist[i] = 0.0f;
+        if (FUSED)
+            for (int i = threadIdx.x; i < 25 * Bm; i += blockDim.x) S.histq[i] = 0.0f;
+        for (int i = threadIdx.x; i < kWarps * 36; i += blockDim.x) S.red[i] = 0.0f;
+        float bgoal = 0.0f;
+        const int band0 = static_cast<int>((static_cast<long long>(item) * ep.bands) / items);
+        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * ep.bands) / items);
+        const int band_rows = ep.band_rows;
+        const EpReg er = ep_reg(ep);
+        const int P = er.P, P4 = P >> 2, goal = er.goal;
+        const float slip = er.slip;
+        const float *cost = er.cost;
+        const int grow = goal / P;
+        QV_TRACE_MARK(tr, 3);
+        for (int band = band0; band < band1; ++band) {
+            const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows);
+            const int qstride = (r1 - r0) * P;
+            if (l == 0) {
+                if (!stage_band(er, src, r0, r1, 1, S.sb, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
+                    return false;
+            } else {
+                if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
+                    return false;
+                if (band == band0) QV_TRACE_MARK(tr, 10);
+                build_band(er, S.sp, S.cw, S.sb, r0, r1, pa, pzv, sa, se, S.lut, dst);
+            }
+            if (band == band0) QV_TRACE_MARK(tr, 11);
+            if (grow >= r0 && grow < r1) bgoal = S.sb[(grow - r0 + 1) * P + goal % P];
+            // null-label mass, rewards and (fused) Q-weighted null mass in
+            // registers; labelled cells only add their reward here
+            float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
+            const int ng = (r1 - r0) * P4;
+            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+                const int rr = gi / P4, col = (gi - rr * P4) << 2;
+                const int y = (r0 + rr) * P + col;
+                Nbr4 n;
+                load_nbr(er, S.sb + (rr + 1) * P, S.cw + (rr + 1) * P, col, n);
+                float4 q4[5];
+                if constexpr (FUSED) {
+#pragma unroll
+                    for (int ap = 0; ap < 5; ++ap)
+                        q4[ap] = *reinterpret_cast<const float4 *>(S.q + ap * qstride + rr * P + col);
+                }
+                float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (cost) c4 = __ldg(reinterpret_cast<const float4 *>(cost + y));
+                const float cst[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned cw = n.cw[j];
+                    float nb[4], out[5];
+                    inflow_nb(n, j, nb);
+                    predict_cell(nb, n.m[j + 1], cw, (y + j) == goal, slip, S.lut, out);
+                    const float r = stage_reward(QV_CELL_FREE(cw), (y + j) == goal, cst[j]);
+                    const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        const float v = out[a];
+                        acc_r[a] = fmaf(v, r, acc_r[a]);
+                        const float vn = v * isnull;
+                        acc_null[a] += vn;
+                        if constexpr (FUSED) {
+                            const float qj[5] = {(&q4[0].x)[j], (&q4[1].x)[j], (&q4[2].x)[j], (&q4[3].x)[j],
+                                                 (&q4[4].x)[j]};
+#pragma unroll
+                            for (int ap = 0; ap < 5; ++ap) acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                        }
+                    }
+                }
+            }
+#ifdef QV_TRACE
+            if (band == band0) {
+                __syncthreads();
+                QV_TRACE_MARK(tr, 12);
+            }
+#endif
+            // fold this band's register sums into the per-warp totals
+            {
+                float vals[NV];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    vals[a] = acc_null[a];
+                    vals[5 + a] = acc_r[a];
+                }
+                if constexpr (FUSED) {
+#pragma unroll
+                    for (int i = 0; i < 25; ++i) vals[10 + i] = acc_q[i];
+                }
+#pragma unroll
+                for (int i = 0; i < NV; ++i) {
+                    const float v = warp_sum(vals[i]);
+                    if (lane == 0) S.red[wid * 36 + i] += v;
+                }
+            }
+#ifdef QV_TRACE
+            if (band == band0) {
+                __syncthreads();
+                QV_TRACE_MARK(tr, 13);
+            }
+#endif
+            label_pass<FUSED>(er, S.sb, S.cw, S.q, r0, r1, S, Bm);
+#ifdef QV_TRACE
+            if (band == band0) {
+                __syncthreads();
+                QV_TRACE_MARK(tr, 14);
+            }
+#endif
+        }
+        QV_TRACE_MARK(tr, 4);
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            float t = 0.0f;
+            for (int k = 0; k < kWarps; ++k) t += S.red[k * 36 + threadIdx.x];
+            S.tot[threadIdx.x] = t;
+        }
+        if (threadIdx.x == 0) S.tot[35] = bgoal;  // zero unless this item holds the goal row
+        __syncthreads();
+        QV_TRACE_MARK(tr, 5);
+        const int iid = ep.inode_base[l] + local;
+        if (items > 1) {
+            // partial record of this work item: [hist 5B][histq 25B][tot 36]
+            if (w >= pl.n_part) {
+                if (threadIdx.x == 0) atomicOr(pl.status, kErrCapacity);
+                continue;
+            }
+            const int hq = FUSED ? 25 * B : 0;
+            const int nrec = 5 * B + hq + 36;
+            float *rec = pl.partials + static_cast<long long>(w) * pl.rec_len;
+            for (int i = threadIdx.x; i < nrec; i += blockDim.x) {
+                float v;
+                if (i < 5 * B) v = S.hist[(i / B) * Bm + (i % B)];
+                else if (i < 5 * B + hq) {
+                    const int k = i - 5 * B;
+                    v = S.histq[((k / 5) / B * Bm + (k / 5) % B) * 5 + k % 5];
+                } else v = S.tot[i - 5 * B - hq];
+                rec[i] = v;
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned prev = atomicAdd(pl.node_cnt + iid, 1u);
+                const int last = prev == static_cast<unsigned>(items - 1);
+                if (last) pl.node_cnt[iid] = 0u;
+                S.flags[0] = last;
+            }
+            __syncthreads();
+            QV_TRACE_MARK(tr, 6);
+            if (!S.flags[0]) {
+#ifdef QV_TRACE
+                trace_commit(tr, kTraceWords);
+#endif
+                continue;
+            }
+            __threadfence();
+            // the last item sums every record of the node in item order
+            const float *base = pl.partials + static_cast<long long>(w0e + local * items) * pl.rec_len;
+            for (int i = threadIdx.x; i < nrec; i += blockDim.x) {
+                float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+                int it = 0;
+                for (; it + 4 <= items; it += 4) {
+                    t0 += __ldcg(base + static_cast<long long>(it) * pl.rec_len + i);
+                    t1 += __ldcg(base + static_cast<long long>(it + 1) * pl.rec_len + i);
+                    t2 += __ldcg(base + static_cast<long long>(it + 2) * pl.rec_len + i);
+                    t3 += __ldcg(base + static_cast<long long>(it + 3) * pl.rec_len + i);
+                }
+                for (; it < items; ++it) t0 += __ldcg(base + static_cast<long long>(it) * pl.rec_len + i);
+                const float t = (t0 + t1) + (t2 + t3);
+                if (i < 5 * B) S.hist[(i / B) * Bm + (i % B)] = t;
+                else if (i < 5 * B + hq) {
+                    const int k = i - 5 * B;
+                    S.histq[((k / 5) / B * Bm + (k / 5) % B) * 5 + k % 5] = t;
+                } else S.tot[i - 5 * B - hq] = t;
+            }
+            __syncthreads();
+        }
+        QV_TRACE_MARK(tr, 7);
+        finalize_node(pl, ep, l, local, FUSED, S.tot[35], code, S);
+        QV_TRACE_MARK(tr, 8);
+        node_done(pl, l, e, ep, S);
+        QV_TRACE_MARK(tr, 9);
+#ifdef QV_TRACE
+        tr[0] |= 1ull << 56;  // this item finalised its node
+        trace_commit(tr, kTraceWords);
+#endif
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- update phase (Eq. 3)
+__device__ bool phase_update(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, unsigned &mphase, int &cur_e) {
+    const int E = pl.E, K = pl.K;
+    const int *wb = pl.wb_upd + l * (E + 1);
+    const int total = __ldcg(wb + E);
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int e = find_episode(wb, E, w);
+        load_ep(pl, e, S, cur_e);
+        const EpDev &ep = *S.ep;
+        const int items = __ldcg(pl.uitems + l * E + e);
+        const int rel = w - __ldcg(wb + e);
+        const int local = rel / items, item = rel - local * items;
+        const long long ia = static_cast<long long>(ep.inode_base[l] + local) * 5;
+        __syncthreads();
+        if (threadIdx.x < 5) {
+            S.u_n[threadIdx.x] = __ldcg(pl.nchild + ia + threadIdx.x);
+            S.u_off[threadIdx.x] = __ldcg(pl.choff + ia + threadIdx.x);
+        }
+        for (int t = threadIdx.x; t < 5 * K; t += blockDim.x) {
+            const int a = t / K, j = t - a * K;
+            const long long sbi = (ia + a) * K + j;
+            const float p = __ldcg(pl.slot_P + sbi);
+            S.u_z[t] = __ldcg(pl.slot_z + sbi);
+            S.u_sa[t] = ep.acc / p;
+            S.u_se[t] = ep.eta / p;
+        }
+        const float *b = node_belief(pl, ep, l, local);
+        float *child0 = pl.beliefs + ep.belief_off[l + 1];
+        const int cap = ep.cap[l + 1];
+        const int band0 = static_cast<int>((static_cast<long long>(item) * ep.bands) / items);
+        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * ep.bands) / items);
+        const EpReg er = ep_reg(ep);
+        const int P = er.P, P4 = P >> 2, goal = er.goal, band_rows = ep.band_rows, N = er.N;
+        const float slip = er.slip;
+        for (int band = band0; band < band1; ++band) {
+            const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows);
+            if (!stage_band(er, b, r0, r1, 1, S.sb, S.cw, nullptr, mbar, mphase, pl.status)) return false;
+            const int ng = (r1 - r0) * P4;
+            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+                const int rr = gi / P4, col = (gi - rr * P4) << 2;
+                const int y = (r0 + rr) * P + col;
+                Nbr4 n;
+                load_nbr(er, S.sb + (rr + 1) * P, S.cw + (rr + 1) * P, col, n);
+                float outs[4][5];
+                int lab[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float nb[4];
+                    inflow_nb(n, j, nb);
+                    predict_cell(nb, n.m[j + 1], n.cw[j], (y + j) == goal, slip, S.lut, outs[j]);
+                    lab[j] = QV_CELL_LABEL(n.cw[j]);
+                }
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    const int cn = S.u_n[a], off = S.u_off[a];
+                    for (int m = 0; m < cn; ++m) {
+                        const int c = off + m;
+                        if (c >= cap) break;
+                        const int t = a * K + m;
+                        const int z = S.u_z[t];
+                        const float sa = S.u_sa[t], se = S.u_se[t];
+                        float4 o;
+                        o.x = outs[0][a] * (lab[0] == z ? sa : se);
+                        o.y = outs[1][a] * (lab[1] == z ? sa : se);
+                        o.z = outs[2][a] * (lab[2] == z ? sa : se);
+                        o.w = outs[3][a] * (lab[3] == z ? sa : se);
+                        *reinterpret_cast<float4 *>(child0 + static_cast<long long>(c) * N + y) = o;
+                    }
+                }
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- leaf phase (Eq. 4)
+__device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
+    float(*s_red)[kLeafGroup * 5] = reinterpret_cast<float(*)[kLeafGroup * 5]>(S.red);
+    const int *wb = pl.wb_leaf;
+    const int total = __ldcg(wb + pl.E);
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int e = find_episode(wb, pl.E, w);
+        load_ep(pl, e, S, cur_e);
+        const EpDev &ep = *S.ep;
+        const int n = __ldcg(pl.count + l * pl.E + e);
+        const int first = (w - __ldcg(wb + e)) * kLeafGroup;
+        const int cnt = min(kLeafGroup, n - first);
+        float acc[kLeafGroup][5];
+#pragma unroll
+        for (int i = 0; i < kLeafGroup; ++i)
+#pragma unroll
+            for (int a = 0; a < 5; ++a) acc[i][a] = 0.0f;
+        const size_t plane = static_cast<size_t>(ep.N);
+        const int n4 = ep.N >> 2;
+        for (int i4 = threadIdx.x; i4 < n4; i4 += blockDim.x) {
+            float4 q[5];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) q[a] = __ldg(reinterpret_cast<const float4 *>(ep.Q + a * plane) + i4);
+#pragma unroll
+            for (int i = 0; i < kLeafGroup; ++i) {
+                if (i < cnt) {
+                    const float4 b = __ldcs(reinterpret_cast<const float4 *>(node_belief(pl, ep, l, first + i)) + i4);
+#pragma unroll
+                    for (int a = 0; a < 5; ++a)
+                        acc[i][a] = fmaf(b.x, q[a].x, fmaf(b.y, q[a].y, fmaf(b.z, q[a].z, fmaf(b.w, q[a].w, acc[i][a]))));
+                }
+            }
+        }
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kLeafGroup; ++i)
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                const float v = warp_sum(acc[i][a]);
+                if (lane == 0) s_red[wid][i * 5 + a] = v;
+            }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const int i = threadIdx.x;
+            float sums[5];
+            float best = -3.402823466e38f;
+            int ba = 0;
+            for (int a = 0; a < 5; ++a) {
+                float t = 0.0f;
+                for (int k = 0; k < kWarps; ++k) t += s_red[k][i * 5 + a];
+                sums[a] = t;
+                if (t > best) {
+                    best = t;
+                    ba = a;
+                }
+            }
+            pl.value[ep.node_base[l] + first + i] = best;
+            if (l == 0) {  // depth-0 plan: the root is the leaf
+                ResultDev r;
+                r.action = ba;
+                r.value = best;
+                for (int a = 0; a < 5; ++a) r.q[a] = sums[a];
+                r.pad = 0;
+                pl.result[e] = r;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- backup phase (Alg. 6, 7)
+// Records of the leaves, which nothing read before, from every (node,
+// action) pair of the deepest internal level.  `write_value`: fused leaves,
+// whose values live in the sample slots.
+__device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep, int l, int t, bool write_value) {
+    const int K = pl.K, nz = ep.B + 1;
+    const int node = t / 5, a = t - node * 5;
+    const long long ia = static_cast<long long>(ep.inode_base[l] + node) * 5 + a;
+    const int m = __ldcg(pl.nchild + ia), off = __ldcg(pl.choff + ia);
+    const long long sb = ia * K;
+    const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l] + node);
+    for (int j = 0; j < m; ++j) {
+        if (off + j >= ep.cap[l + 1]) break;
+        const int g = ep.node_base[l + 1] + off + j;
+        const int z = __ldcg(pl.slot_z + sb + j);
+        pl.parent[g] = node;
+        pl.action[g] = a;
+        pl.obs[g] = z;
+        pl.weight[g] = __ldcg(pl.slot_w + sb + j);
+        pl.pz[g] = __ldcg(pl.slot_P + sb + j);
+        pl.code[g] = (pcode * 5ull + a) * static_cast<unsigned long long>(nz) + z;
+        if (write_value) pl.value[g] = __ldcg(pl.slot_val + sb + j);
+    }
+}
+
+// Fused leaves: the deepest internal level already holds U_Q and U_V (from
+// its finalisation); every CTA writes leaf records, one CTA per episode backs
+// up the levels above.  Materialised leaves: one CTA per episode backs up
+// every level.  Each level handles its (node, action) pairs in parallel.
+__device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
+    const int K = pl.K, D = pl.depth;
+    const bool fused = pl.leaf_mode != QV_LEAF_MATERIALISE;
+    if (fused) {
+        for (int e = 0; e < pl.E; ++e) {
+            const EpDev &epg = pl.eps[e];
+            const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
+            for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += gridDim.x * blockDim.x)
+                leaf_records(pl, epg, D - 1, t, true);
+        }
+    }
+    for (int e = blockIdx.x; e < pl.E; e += gridDim.x) {
+        load_ep(pl, e, S, cur_e);
+        const EpDev &ep = *S.ep;
+        for (int l = fused ? D - 2 : D - 1; l >= 0; --l) {
+            const int n = __ldcg(pl.count + l * pl.E + e);
+            for (int t = threadIdx.x; t < 5 * n; t += blockDim.x) {
+                const int node = t / 5, a = t - node * 5;
+                const long long ia = static_cast<long long>(ep.inode_base[l] + node) * 5 + a;
+                const int m = __ldcg(pl.nchild + ia), off = __ldcg(pl.choff + ia);
+                const long long sb = ia * K;
+                float s = 0.0f;
+                for (int j = 0; j < m; ++j)
+                    s = fmaf(__ldcg(pl.slot_w + sb + j), __ldcg(pl.value + ep.node_base[l + 1] + off + j), s);
+                pl.UQ[ia] = fmaf(ep.gamma, s, __ldcg(pl.R + ia));
+                if (!fused && l == D - 1) leaf_records(pl, ep, l, t, false);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const long long ia = static_cast<long long>(ep.inode_base[l] + i) * 5;
+                float best = pl.UQ[ia];
+                for (int a = 1; a < 5; ++a) best = fmaxf(best, pl.UQ[ia + a]);
+                pl.value[ep.node_base[l] + i] = best;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const long long ia = static_cast<long long>(ep.inode_base[0]) * 5;
+            ResultDev r;
+            float q[5];
+            int best = 0;
+            for (int a = 0; a < 5; ++a) {
+                q[a] = __ldcg(pl.UQ + ia + a);
+                if (q[a] > q[best]) best = a;
+            }
+            r.action = best;
+            for (int a = 0; a < 5; ++a) r.q[a] = q[a];
+            r.value = __ldcg(pl.value + ep.node_base[0]);
+            r.pad = 0;
+            pl.result[e] = r;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- the plan kernel
+__global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    const SmemLayout L = SmemLayout::make(pl.sb_floats, pl.sp_floats, pl.q_floats, pl.Bmax, pl.K);
+    Smem S;
+    S.sb = reinterpret_cast<float *>(smem_raw + L.sb);
+    S.sp = reinterpret_cast<float *>(smem_raw + L.sp);
+    S.cw = reinterpret_cast<uint16_t *>(smem_raw + L.cw);
+    S.q = reinterpret_cast<float *>(smem_raw + L.q);
+    S.ep = reinterpret_cast<EpDev *>(smem_raw + L.ep);
+    S.bco = reinterpret_cast<int *>(smem_raw + L.bco);
+    S.hist = reinterpret_cast<float *>(smem_raw + L.hist);
+    S.histq = reinterpret_cast<float *>(smem_raw + L.histq);
+    S.tot = reinterpret_cast<float *>(smem_raw + L.tot);
+    S.red = reinterpret_cast<float *>(smem_raw + L.red);
+    S.P = reinterpret_cast<float *>(smem_raw + L.P);
+    S.C = reinterpret_cast<float *>(smem_raw + L.C);
+    S.cnt = reinterpret_cast<int *>(smem_raw + L.cnt);
+    S.T = reinterpret_cast<float *>(smem_raw + L.T);
+    S.uq = reinterpret_cast<float *>(smem_raw + L.uq);
+    S.lut = reinterpret_cast<float *>(smem_raw + L.lut);
+    S.u_n = reinterpret_cast<int *>(smem_raw + L.u_n);
+    S.u_off = reinterpret_cast<int *>(smem_raw + L.u_off);
+    S.u_z = reinterpret_cast<int *>(smem_raw + L.u_z);
+    S.u_sa = reinterpret_cast<float *>(smem_raw + L.u_sa);
+    S.u_se = reinterpret_cast<float *>(smem_raw + L.u_se);
+    S.scan = reinterpret_cast<int *>(smem_raw + L.scan);
+    S.flags = reinterpret_cast<int *>(smem_raw + L.flags);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    unsigned mphase = 0;
+    int cur_e = -1;
+    int slot = 0;
+    stamp(pl, slot++);
+    const int D = pl.depth;
+    const bool mat = pl.leaf_mode == QV_LEAF_MATERIALISE;
+    for (int l = 0; l < D; ++l) {
+        const bool fused = (l == D - 1) && !mat;
+        // a level's beliefs are stored when a later phase reads them
+        const bool store = l > 0 && (l < D - 1 || mat);
+        const bool ok = fused ? phase_expand<true>(pl, l, store, S, &mbar, mphase, cur_e)
+                              : phase_expand<false>(pl, l, store, S, &mbar, mphase, cur_e);
+        if (!ok && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
+#ifdef QV_TRACE
+        {
+            const unsigned long long t[3] = {static_cast<unsigned long long>(l) | (0xFFull << 8) |
+                                                 (static_cast<unsigned long long>(blockIdx.x) << 24),
+                                             0ull, globaltimer()};
+            trace_commit(t, 3);
+        }
+#endif
+        if (!grid_sync(pl)) return;
+        stamp(pl, slot++);
+    }
+    if (D > 0 && mat) {
+        if (!phase_update(pl, D - 1, S, &mbar, mphase, cur_e) && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
+        if (!grid_sync(pl)) return;
+        stamp(pl, slot++);
+    }
+    if (D == 0 || mat) {
+        phase_leaf(pl, D, S, cur_e);
+        if (!grid_sync(pl)) return;
+        stamp(pl, slot++);
+    }
+    if (D > 0) {
+        phase_backup(pl, S, cur_e);
+        stamp(pl, slot++);
+    }
+}
+
+}  // namespace qv

@@ -329,7 +329,7 @@ extern "C" qv_status mdp_value_iterate(const qv_model_t *m, int32_t dtype, doubl
                                        int32_t *sweeps_out, double *residual_out, qv_stream_t stream) {
     if (!m || !m->d_cell || !d_V || !d_Q || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: null pointer");
-    if (m->H < 1 || m->W < 1 || m->pitch != ((m->W + 3) / 4) * 4 || m->W > QV_MAX_WIDTH)
+    if (m->H < 1 || m->W < 1 || m->pitch != QV_PITCH(m->W) || m->W > QV_MAX_WIDTH)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: bad grid");
     if (!(m->discount > 0.0f && m->discount < 1.0f) || !(m->slip >= 0.0f && m->slip <= 0.5f))
         return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: discount or slip out of range");

@@ -245,6 +245,25 @@ def diff(seed: int = 0, H: int = 128, W: int = 128, depth: int = 3, K: int = 8,
         vi_truncated=sweeps, cost=cost)
 
 
+def episodes(w: Workload, R: int, seed: int = 0, first_episode: int = 0) -> List[Workload]:
+    """R planning requests on the map of `w`: the same grid, beacons, goal and
+    model, each with its own start cell (drawn from the goal's free
+    component), its own b0 of the same family as `w`, and its own Philox
+    episode word."""
+    rng = np.random.default_rng([6, seed, first_episode])
+    comp, _ = _components(w.occ)
+    cells = np.flatnonzero(comp.ravel() == comp.ravel()[w.goal])
+    cells = cells[cells != w.goal]
+    gaussian = np.count_nonzero(w.b0) > 9
+    out = []
+    for r in range(R):
+        start = int(rng.choice(cells))
+        b0 = _b0_gauss(w.occ, start) if gaussian else _b0_block(w.occ, start)
+        out.append(dataclasses.replace(w, name=f"{w.name}/ep{first_episode + r}", start=start, b0=b0,
+                                       episode=first_episode + r))
+    return out
+
+
 def custom(H, W, occ, beacons, sense_range, goal, start, slip, accuracy, discount,
            b0, depth=1, K=4, seed=0, episode=0, cost=None, name="custom"):
     """Wrap hand-made arrays (test fixtures) as a Workload."""

@@ -56,11 +56,12 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     from paper_1810_00204_gb300 import _native as N
     L = N.lib()
     assert L.qv_model_build(0, 5, 8, None, None, 1, 1, 0, None, None) == N.QV_ERR_INVALID
-    m = N.qv_model_t(4, 5, 7, 16, 1, 0, 0.1, 0.9, 0.95, None)    # bad pitch
+    # device pointers are never dereferenced by the sizing call: any non-null value
+    m = N.qv_model_t(4, 5, 7, 16, 1, 0, 0.1, 0.9, 0.95, None, 32, 3)    # bad pitch
     p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
     assert b"pitch" in L.qv_last_error()
-    m = N.qv_model_t(4, 5, 8, 16, 1, 0, 0.1, 0.9, 0.95, None)
+    m = N.qv_model_t(4, 5, 8, 16, 1, 0, 0.1, 0.9, 0.95, None, 32, 3)
     p = N.qv_plan_params_t(2, 0, 0, 0, 0, 0, None)                # K = 0
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
     p = N.qv_plan_params_t(N.QV_MAX_DEPTH + 1, 4, 0, 0, 0, 0, None)
