@@ -148,6 +148,26 @@ qv_status belief_correct(const qv_model_t *model, const float *d_bbar, int32_t z
                          float *d_bout, float *d_pz, void *d_ws, size_t ws_bytes,
                          qv_stream_t stream);
 
+/* belief_correct_noalloc: the same result as belief_correct, for callers that
+ * cannot allocate device memory -- for example a control loop that must not
+ * call cudaMalloc after start-up (an allocation can synchronise the device
+ * and stall the loop), or a host application that owns every device
+ * allocation and forbids libraries to make their own.  The paper has no
+ * counterpart: this is a deployment variant of the Eq. 3 correction.
+ *   - Takes no workspace: the reduction's scratch is a fixed array compiled
+ *     into the library (about 16 KB, resident on every device that loads
+ *     the library until the process exits).  Nothing is allocated.
+ *   - Grids are limited to QV_NOALLOC_MAX_CELLS cells (H * pitch); larger
+ *     ones return QV_ERR_INVALID with a message.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls whose GPU work
+ *     overlaps (other streams, other threads) race and must be serialised by
+ *     the caller.  Each call clears the part that must start at zero. */
+#define QV_NOALLOC_MAX_CELLS (4096 * 1024)
+qv_status belief_correct_noalloc(const qv_model_t *model, const float *d_bbar, int32_t z,
+                                 float *d_bout, float *d_pz, qv_stream_t stream);
+
 /* leaf_value: v[i] = max_a sum_y b_i(y) Q[a][y] for n beliefs stored at
  * d_b + i * H * pitch (Eq. 4 with the QMDP alpha-vectors; Alg. 5). */
 qv_status leaf_value(const qv_model_t *model, const float *d_Q, const float *d_b,

@@ -20,6 +20,7 @@ QV_MAX_DEPTH = 6
 QV_MAX_BEACONS = 126
 QV_MAX_K = 64
 QV_MAX_WIDTH = 2048
+QV_NOALLOC_MAX_CELLS = 4096 * 1024
 QV_F32, QV_F64 = 0, 1
 QV_WEIGHT_FREQ, QV_WEIGHT_MARGINAL = 0, 1
 QV_LEAF_FUSED, QV_LEAF_MATERIALISE = 0, 1
@@ -67,6 +68,7 @@ SIGNATURES = {
     "belief_predict": (C.c_int, [_M, _vp, _i32, _vp, _vp]),
     "belief_correct_workspace_bytes": (_sz, [_M]),
     "belief_correct": (C.c_int, [_M, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "belief_correct_noalloc": (C.c_int, [_M, _vp, _i32, _vp, _vp, _vp]),
     "leaf_value": (C.c_int, [_M, _vp, _vp, _i32, _vp, _vp]),
     "qv_plan_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_create": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(_vp), _vp]),

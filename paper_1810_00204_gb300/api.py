@@ -130,6 +130,16 @@ def belief_correct(model: Model, bbar: torch.Tensor, z: int, out=None, stream=No
     return out, pz
 
 
+def belief_correct_noalloc(model: Model, bbar: torch.Tensor, z: int, out: torch.Tensor, pz: torch.Tensor,
+                           stream=None):
+    """belief_correct without a workspace: the library keeps the reduction's
+    scratch in a fixed device array, so the call itself allocates nothing.
+    The caller provides `out` (like bbar) and `pz` (one float32 on the device)."""
+    check(lib().belief_correct_noalloc(C.byref(model.struct), _ptr(bbar), int(z), _ptr(out), _ptr(pz),
+                                       _stream(stream)), "belief_correct_noalloc")
+    return out, pz
+
+
 def leaf_value(model: Model, Q: torch.Tensor, b: torch.Tensor, stream=None):
     n = b.shape[0] if b.dim() == 3 else 1
     out = torch.empty(n, dtype=torch.float32, device=b.device)

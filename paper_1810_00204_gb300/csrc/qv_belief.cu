@@ -1,6 +1,8 @@
 // qv_belief.cu -- single-belief primitives: the predict step (numerator of
 // Eq. 3 with the blocked-move rule of Eq. 10), the Bayes correction with its
 // normaliser P(z | b, a) (Eq. 3), and QMDP leaf values (Eq. 4).
+#include <mutex>
+
 #include "qv_common.cuh"
 
 namespace qv {
@@ -189,6 +191,72 @@ extern "C" qv_status belief_correct(const qv_model_t *m, const float *d_bbar, in
     qv::k_obs_partial<<<grid, 256, 0, cs>>>(a, d_bbar, z, partials, counter, d_pz);
     qv::k_correct_scale<<<grid, 256, 0, cs>>>(a, d_bbar, z, d_pz, d_bout);
     return qv_check_cuda(cudaGetLastError(), "belief_correct launch");
+}
+
+// ---------------------------------------------------------------- no-allocation variant
+// belief_correct_noalloc runs the two kernels above with their scratch (the
+// per-block partial sums and the arrival counter) in a file-scope device
+// array instead of a caller workspace.  One block per kNoAllocCellsPerBlock
+// cells, so the array's kNoAllocBlocks partial sums bound the grid size.
+namespace qv {
+constexpr int kNoAllocBlocks = 4096;
+constexpr int kNoAllocCellsPerBlock = 1024;
+static_assert(static_cast<long long>(kNoAllocBlocks) * kNoAllocCellsPerBlock == QV_NOALLOC_MAX_CELLS,
+              "QV_NOALLOC_MAX_CELLS follows the scratch capacity");
+// [0, kNoAllocBlocks): partial sums; [kNoAllocBlocks]: the arrival counter.
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocBlocks + 64];
+}  // namespace qv
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kNoAllocMaxDevices = 64;
+float *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code cannot use the symbol itself as a device pointer).
+qv_status noalloc_scratch(float **out) {
+    int dev = 0;
+    if (qv_check_cuda(cudaGetDevice(&dev), "belief_correct_noalloc: cudaGetDevice") != QV_OK) return QV_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return qv_set_error(QV_ERR_INVALID, "belief_correct_noalloc: device ordinal %d unsupported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (qv_check_cuda(cudaGetSymbolAddress(&p, qv::g_noalloc_scratch),
+                          "belief_correct_noalloc: cudaGetSymbolAddress") != QV_OK)
+            return QV_ERR_CUDA;
+        g_noalloc_addr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return QV_OK;
+}
+}  // namespace
+
+extern "C" qv_status belief_correct_noalloc(const qv_model_t *m, const float *d_bbar, int32_t z, float *d_bout,
+                                            float *d_pz, qv_stream_t stream) {
+    qv_status st = qv::check_model(m, "belief_correct_noalloc");
+    if (st != QV_OK) return st;
+    if (!d_bbar || !d_bout || !d_pz) return qv_set_error(QV_ERR_INVALID, "belief_correct_noalloc: null pointer");
+    if (z < 0 || z > m->num_beacons) return qv_set_error(QV_ERR_INVALID, "belief_correct_noalloc: z %d", z);
+    const long long cells = static_cast<long long>(m->H) * m->pitch;
+    if (cells > QV_NOALLOC_MAX_CELLS)
+        return qv_set_error(QV_ERR_INVALID,
+                            "belief_correct_noalloc: %lld cells exceed the static scratch limit of %d cells",
+                            cells, QV_NOALLOC_MAX_CELLS);
+    float *scratch = nullptr;
+    st = noalloc_scratch(&scratch);
+    if (st != QV_OK) return st;
+    unsigned *counter = reinterpret_cast<unsigned *>(scratch + qv::kNoAllocBlocks);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    const qv::ModelArgs a = qv::model_args(m);
+    const int grid = static_cast<int>(std::max<long long>(
+        1, (cells + qv::kNoAllocCellsPerBlock - 1) / qv::kNoAllocCellsPerBlock));
+    // the arrival counter must start at zero; the partial sums are overwritten
+    if (qv_check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), cs), "belief_correct_noalloc memset") != QV_OK)
+        return QV_ERR_CUDA;
+    qv::k_obs_partial<<<grid, 256, 0, cs>>>(a, d_bbar, z, scratch, counter, d_pz);
+    qv::k_correct_scale<<<grid, 256, 0, cs>>>(a, d_bbar, z, d_pz, d_bout);
+    return qv_check_cuda(cudaGetLastError(), "belief_correct_noalloc launch");
 }
 
 extern "C" qv_status leaf_value(const qv_model_t *m, const float *d_Q, const float *d_b, int32_t n, float *d_value,
