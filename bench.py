@@ -51,7 +51,95 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched (256 uneven maps) and 512x512 sub-measurements")
+    ap.add_argument("--extra-steps", type=int, default=20)
     return ap.parse_args()
+
+
+def time_device(run, steps, flush, stream):
+    """Sum of per-step CUDA-event times of run(), L2 flushed before each step
+    outside the events."""
+    import torch
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 255)
+        ev0[k].record(stream)
+        run()
+        ev1[k].record(stream)
+    torch.cuda.synchronize()
+    return sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+
+
+def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
+    """Sub-measurements beside the headline: the step's requests as one
+    batched launch, the 256-episode batch of uneven maps, and the 512x512
+    configuration in both leaf modes with per-phase bandwidth."""
+    import torch
+    from paper_1810_00204_gb300 import _native as N
+    from paper_1810_00204_gb300 import api, workloads as WL
+    out = {}
+    K = max(3, args.extra_steps)
+    peak, _ = measured_peak()
+    # (1) the same R requests in one launch (E = R episodes on one map)
+    b0s = [model.to_grid(e.b0) for e in eps]
+    pb = api.Plan([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
+                  episode=eps[0].episode)
+    pb.capture_graph()
+    for _ in range(3):
+        pb.run()
+    ms = time_device(pb.run, K, flush, stream)
+    out["same_requests_one_launch"] = {"plans_per_s": len(eps) * K / (ms / 1e3), "E": len(eps),
+                                       "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s}
+    del pb
+    # (2) 256 independent episodes on maps of uneven size, one launch per step
+    ws = WL.batched(args.seed, E=256)
+    ms_ = [api.Model(x, device=dev) for x in ws]
+    Qs = [api.mdp_value_iterate(m, dtype="f32")["Q"] for m in ms_]
+    p3 = api.Plan(ms_, Qs, [m.b0() for m in ms_], depth=3, K=8, seed=args.seed, episode=0)
+    p3.capture_graph()
+    for _ in range(2):
+        p3.run()
+    res = p3.read()
+    ms3 = time_device(p3.run, K, flush, stream)
+    nodes = [sum(r["nodes_per_level"][1:]) for r in res]
+    out["batched_256_uneven"] = {"plans_per_s": 256 * K / (ms3 / 1e3), "ms_per_launch": ms3 / K,
+                                 "updates_per_s": sum(nodes) * K / (ms3 / 1e3),
+                                 "cells_mean": float(sum(x.H * x.W for x in ws) / 256),
+                                 "workspace_GB": p3.workspace_bytes / 1e9}
+    del p3, Qs, ms_
+    torch.cuda.empty_cache()
+    # (3) 512x512, one plan per launch, fused and materialised leaves
+    wl = WL.large(args.seed)
+    ml = api.Model(wl, device=dev)
+    Ql = api.mdp_value_iterate(ml, dtype="f32")["Q"]
+    Ncell = ml.H * ml.P
+    for mode_name, mode in (("fused", N.QV_LEAF_FUSED), ("materialise", N.QV_LEAF_MATERIALISE)):
+        p4 = api.Plan([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode)
+        p4.capture_graph()
+        for _ in range(2):
+            p4.run()
+        r4 = p4.read()[0]
+        ms4 = time_device(p4.run, K, flush, stream)
+        nodes = r4["nodes_per_level"]
+        phases = {}
+        prof_runs = [p4.profile() for _ in range(3)]
+        for it in prof_runs[0][1:]:
+            nm, lv = it["name"].split(":", 1)[1], it["level"]
+            t = statistics.mean(pr[i]["ms"] for pr in prof_runs for i in range(len(pr))
+                                if pr[i]["name"] == it["name"] and pr[i]["level"] == lv)
+            b = phase_bytes(nm, lv, nodes, Ncell, wl.depth, mode_name)
+            gbps = b / (t * 1e-3) / 1e9 if t > 0 else None
+            phases[f"{nm}[{lv}]"] = {"ms": t, "bytes": b, "GBps": gbps,
+                                     "frac_of_measured_hbm": (gbps / peak) if gbps else None}
+        out[f"large_512_{mode_name}"] = {"plans_per_s": K / (ms4 / 1e3), "ms_per_plan": ms4 / K,
+                                         "nodes_per_level": nodes,
+                                         "updates_per_s": sum(nodes[1:]) * K / (ms4 / 1e3), "phases": phases,
+                                         "workspace_GB": p4.workspace_bytes / 1e9}
+        del p4
+        torch.cuda.empty_cache()
+    return out
 
 
 def make_workload(name, seed):
@@ -384,6 +472,10 @@ def main():
         e2e = {"value": e2e_val, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": R * res_bytes,
                "steps": n_e2e}
 
+    extra = None
+    if not args.no_extra and args.workload == "mid":
+        extra = extra_measurements(args, dev, flush, stream, plans_per_s / world_size, model, Qd, eps, w)
+
     # oracle CPU baseline (rank 0, N = 1 only), bounded sample
     cpu = None
     if rank == 0 and world_size == 1 and not args.no_cpu:
@@ -415,6 +507,7 @@ def main():
                    "cell_sweeps_per_s": model.H * model.W * vi["sweeps"] / (vi_ms / 1e3),
                    "note": "offline, once per map; not part of plans/s"},
             "wall_s": wall,
+            "extra": extra,
         }
         print(json.dumps(line), flush=True)
     if world_size > 1:

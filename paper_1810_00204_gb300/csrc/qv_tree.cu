@@ -29,6 +29,7 @@ struct Layout {
     size_t off_eps, off_count, off_items, off_uitems, off_wbs, off_wbu, off_wbl, off_parent, off_action, off_obs,
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_ep_cnt, off_lvl_cnt, off_partials,
+        off_leaf_split, off_leaf_cnt,
         off_status, off_boundary, off_bar, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0;
@@ -189,6 +190,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_wbs = take(sizeof(int) * D1 * E1);
     L.off_wbu = take(sizeof(int) * D1 * E1);
     L.off_wbl = take(sizeof(int) * E1);
+    L.off_leaf_split = take(sizeof(int));
     L.off_parent = take(sizeof(int) * L.NT);
     L.off_action = take(sizeof(int) * L.NT);
     L.off_obs = take(sizeof(int) * L.NT);
@@ -214,6 +216,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_node_cnt = take(sizeof(unsigned) * L.NI);
     L.off_ep_cnt = take(sizeof(unsigned) * D1 * E);
     L.off_lvl_cnt = take(sizeof(unsigned) * D1);
+    L.off_leaf_cnt = take(sizeof(unsigned) * static_cast<size_t>(L.n_part));
     L.off_bar = take(sizeof(qv::GridBar));
     L.off_status = take(sizeof(unsigned) * 4);
     L.off_boundary = take(sizeof(unsigned long long));
@@ -314,6 +317,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.wb_stats = at<int>(ws, L.off_wbs);
     d.wb_upd = at<int>(ws, L.off_wbu);
     d.wb_leaf = at<int>(ws, L.off_wbl);
+    d.leaf_split = at<int>(ws, L.off_leaf_split);
+    d.leaf_cnt = at<unsigned>(ws, L.off_leaf_cnt);
     d.parent = at<int>(ws, L.off_parent);
     d.action = at<int>(ws, L.off_action);
     d.obs = at<int>(ws, L.off_obs);
@@ -350,6 +355,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     std::vector<float> one(E, 1.0f);
     std::vector<unsigned long long> zero64(E, 0ull);
     int s0 = 0, l0 = 0;
+    // a depth-0 plan streams each root as one leaf, split into leaf0_split chunks
+    const int leaf0_split = static_cast<int>(std::min<long long>(std::max<long long>((L.target + E - 1) / E, 1), 64));
     for (int e = 0; e < E; ++e) {
         const long long want = (L.target + E - 1) / E;
         it0[e] = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), L.eps[e].bands));
@@ -357,7 +364,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
         wbu[e] = s0;
         s0 += D > 0 ? it0[e] : 0;
         wbl[e] = l0;
-        l0 += 1;
+        l0 += leaf0_split;
     }
     wbs[E] = s0;
     wbu[E] = s0;
@@ -372,6 +379,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
         up(d.wb_stats, wbs.data(), sizeof(int) * (E + 1)) != QV_OK ||
         up(d.wb_upd, wbu.data(), sizeof(int) * (E + 1)) != QV_OK ||
         up(d.wb_leaf, wbl.data(), sizeof(int) * (E + 1)) != QV_OK ||
+        up(d.leaf_split, &leaf0_split, sizeof(int)) != QV_OK ||
         up(d.parent, neg.data(), sizeof(int) * E) != QV_OK || up(d.action, neg.data(), sizeof(int) * E) != QV_OK ||
         up(d.obs, neg.data(), sizeof(int) * E) != QV_OK || up(d.weight, one.data(), sizeof(float) * E) != QV_OK ||
         up(d.pz, one.data(), sizeof(float) * E) != QV_OK ||

@@ -117,6 +117,8 @@ struct PlanDev {
     int *wb_stats;     // [(d+1)][E+1] work-list prefixes
     int *wb_upd;       // [(d+1)][E+1]
     int *wb_leaf;      // [E+1]
+    int *leaf_split;   // chunks per group of leaves in the leaf phase
+    unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
     // per node (gid over every level)
     int *parent, *action, *obs;
     float *weight, *pz, *value;
@@ -427,16 +429,16 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
     const float eta = ep.eta, acc = ep.acc;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 5 * nz; i += blockDim.x) S.cnt[i] = 0;
-    if (fused && threadIdx.x >= 160 && threadIdx.x < 185) {
-        const int t = threadIdx.x - 160, a = t / 5, ap = t % 5;
-        float s = S.tot[10 + t];
-        for (int z = 0; z < B; ++z) s += S.histq[(a * Bm + z) * 5 + ap];
-        S.T[t] = s;
-    }
-    if (wid < 5 && lane == 0) {
+    if (fused)
+        for (int t = threadIdx.x; t < 25; t += blockDim.x) {
+            const int a = t / 5, ap = t % 5;
+            float s = S.tot[10 + t];
+            for (int z = 0; z < B; ++z) s += S.histq[(a * Bm + z) * 5 + ap];
+            S.T[t] = s;
+        }
+    for (int a = wid; a < 5 && lane == 0; a += kWarps) {
         // the cumulative sum runs in ascending z, in FP32, as the sampler's
         // inverse CDF is defined
-        const int a = wid;
         float Ssum = S.tot[a];
         for (int z = 0; z < B; ++z) Ssum += S.hist[a * Bm + z];
         float run = 0.0f;
@@ -476,8 +478,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
         atomicAdd(&S.cnt[a * nz + z], 1);
     }
     __syncthreads();
-    if (wid < 5) {
-        const int a = wid;
+    for (int a = wid; a < 5; a += kWarps) {
         const long long sb = (static_cast<long long>(iid) * 5 + a) * K;
         int base = 0;
         float psum = 0.0f;
@@ -582,6 +583,13 @@ __device__ void level_prefix(const PlanDev &pl, int l1) {
     long long T = 0;
     for (int e = 0; e < E; ++e) T += __ldcg(pl.count + l1 * E + e);
     const long long want = T > 0 ? (pl.target + T - 1) / T : 1;
+    int C = 1;  // leaf chunks per group of leaves
+    if (l1 == pl.depth) {
+        long long G = 0;
+        for (int e = 0; e < E; ++e) G += (__ldcg(pl.count + l1 * E + e) + kLeafGroup - 1) / kLeafGroup;
+        C = static_cast<int>(min(max(G > 0 ? (pl.target + G - 1) / G : 1LL, 1LL), 64LL));
+        *pl.leaf_split = C;
+    }
     int ws = 0, wu = 0, wl = 0;
     for (int e = 0; e < E; ++e) {
         const int c = __ldcg(pl.count + l1 * E + e);
@@ -594,7 +602,7 @@ __device__ void level_prefix(const PlanDev &pl, int l1) {
         if (l1 == pl.depth) pl.wb_leaf[e] = wl;
         if (l1 < pl.depth) ws += c * it;
         wu += c * it;
-        wl += (c + kLeafGroup - 1) / kLeafGroup;
+        wl += ((c + kLeafGroup - 1) / kLeafGroup) * C;
     }
     pl.wb_stats[l1 * (E + 1) + E] = ws;
     pl.wb_upd[l1 * (E + 1) + E] = wu;
@@ -1067,16 +1075,22 @@ __device__ bool phase_update(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, 
 }
 
 // ---------------------------------------------------------------- leaf phase (Eq. 4)
+// Work items are (group of kLeafGroup leaves, chunk of the grid); with more
+// than one chunk the partial sums go to per-item records and the last chunk
+// of a group adds them in chunk order.
 __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
     float(*s_red)[kLeafGroup * 5] = reinterpret_cast<float(*)[kLeafGroup * 5]>(S.red);
     const int *wb = pl.wb_leaf;
     const int total = __ldcg(wb + pl.E);
+    const int C = max(1, __ldcg(pl.leaf_split));
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int e = find_episode(wb, pl.E, w);
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
         const int n = __ldcg(pl.count + l * pl.E + e);
-        const int first = (w - __ldcg(wb + e)) * kLeafGroup;
+        const int rel = w - __ldcg(wb + e);
+        const int group = rel / C, chunk = rel - group * C;
+        const int first = group * kLeafGroup;
         const int cnt = min(kLeafGroup, n - first);
         float acc[kLeafGroup][5];
 #pragma unroll
@@ -1085,7 +1099,10 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             for (int a = 0; a < 5; ++a) acc[i][a] = 0.0f;
         const size_t plane = static_cast<size_t>(ep.N);
         const int n4 = ep.N >> 2;
-        for (int i4 = threadIdx.x; i4 < n4; i4 += blockDim.x) {
+        const int c0 = static_cast<int>((static_cast<long long>(chunk) * n4) / C);
+        const int c1 = static_cast<int>((static_cast<long long>(chunk + 1) * n4) / C);
+#pragma unroll 2
+        for (int i4 = c0 + threadIdx.x; i4 < c1; i4 += blockDim.x) {
             float4 q[5];
 #pragma unroll
             for (int a = 0; a < 5; ++a) q[a] = __ldg(reinterpret_cast<const float4 *>(ep.Q + a * plane) + i4);
@@ -1109,14 +1126,42 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 if (lane == 0) s_red[wid][i * 5 + a] = v;
             }
         __syncthreads();
+        if (threadIdx.x < kLeafGroup * 5) {
+            float t = 0.0f;
+            for (int k = 0; k < kWarps; ++k) t += s_red[k][threadIdx.x];
+            S.tot[threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (C > 1) {
+            float *rec = pl.partials + static_cast<long long>(w) * pl.rec_len;
+            if (threadIdx.x < kLeafGroup * 5) rec[threadIdx.x] = S.tot[threadIdx.x];
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned key = static_cast<unsigned>(w / C);
+                const unsigned prev = atomicAdd(pl.leaf_cnt + key, 1u);
+                const int last = prev == static_cast<unsigned>(C - 1);
+                if (last) pl.leaf_cnt[key] = 0u;
+                S.flags[3] = last;
+            }
+            __syncthreads();
+            if (!S.flags[3]) continue;
+            __threadfence();
+            if (threadIdx.x < kLeafGroup * 5) {
+                const float *base = pl.partials + static_cast<long long>(w - chunk) * pl.rec_len;
+                float t = 0.0f;
+                for (int c = 0; c < C; ++c) t += __ldcg(base + static_cast<long long>(c) * pl.rec_len + threadIdx.x);
+                S.tot[threadIdx.x] = t;
+            }
+            __syncthreads();
+        }
         if (threadIdx.x < cnt) {
             const int i = threadIdx.x;
             float sums[5];
             float best = -3.402823466e38f;
             int ba = 0;
             for (int a = 0; a < 5; ++a) {
-                float t = 0.0f;
-                for (int k = 0; k < kWarps; ++k) t += s_red[k][i * 5 + a];
+                const float t = S.tot[i * 5 + a];
                 sums[a] = t;
                 if (t > best) {
                     best = t;
