@@ -73,6 +73,13 @@ def lib():
                                    vp, vp, C.c_int] + [vp] * 16
         L.or_tree_plan.restype = C.c_int
         L.or_num_threads.restype = C.c_int
+        L.or_transition_row_dslip.argtypes = [P, C.c_int, C.c_int, vp, vp]
+        L.or_transition_row_dslip.restype = C.c_int
+        L.or_tree_backward.argtypes = [P, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       C.c_double, vp, vp, vp, vp, vp]
+        L.or_tree_backward.restype = C.c_int
+        L.or_vi_backward.argtypes = [P, C.c_int, vp, vp, vp, vp]
+        L.or_vi_backward.restype = C.c_int
         _lib = L
     return _lib
 
@@ -265,7 +272,9 @@ def tree_plan(w, Q, depth=None, K=None, seed=None, episode=None, weight_mode=FRE
         raise RuntimeError("oracle tree exceeded its level capacity")
     out = dict(root_action=ra.value, root_value=rv.value, root_q=rq, boundary_count=bc.value,
                n_level=n_level.copy(), off=off, depth=depth, K=K,
-               samples_flat=samples, boundary_flat=boundary)
+               samples_flat=samples, boundary_flat=boundary,
+               flat=dict(n_level=n_level, parent=parent, action=action, obs=obs, weight=weight,
+                         pz=pz, UQ=UQ, belief=belief, store_levels=store_levels))
     lv = {k: [] for k in ("parent", "action", "obs", "weight", "pz", "value", "R", "UQ",
                           "samples", "boundary", "belief")}
     for l in range(depth + 1):
@@ -284,6 +293,74 @@ def tree_plan(w, Q, depth=None, K=None, seed=None, episode=None, weight_mode=FRE
             lv["belief"].append(belief[s * p.n:(s + n) * p.n].reshape(n, p.n))
     out.update(lv)
     return out
+
+
+def transition_row_dslip(w, x, a):
+    """d T(x, a, y) / d eps for the targets y of row (x, a)."""
+    p = _prob(w)
+    y = np.zeros(4, np.int32)
+    d = np.zeros(4, np.float64)
+    m = lib().or_transition_row_dslip(p.ref, int(x), int(a), _p(y), _p(d))
+    return {int(y[i]): float(d[i]) for i in range(m)}
+
+
+def tree_backward(w, Q, tree, dL=1.0, **kw):
+    """Adjoint of the root value of `tree` (a tree_plan result with
+    store_levels >= depth - 1, FREQ weights).  Returns dict(Qbar [5][n],
+    Rbar [5][n], dslip, dacc, db0 [n])."""
+    p = _prob(w, **kw)
+    f = tree["flat"]
+    depth = tree["depth"]
+    if f["belief"] is None or f["store_levels"] < max(depth - 1, 0):
+        raise ValueError("tree_backward needs the beliefs of levels 0..depth-1")
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(A, p.n))
+    Qbar = np.zeros(A * p.n, np.float64)
+    Rbar = np.zeros(A * p.n, np.float64)
+    db0 = np.zeros(p.n, np.float64)
+    ds = C.c_double(0.0)
+    da = C.c_double(0.0)
+    lib().or_tree_backward(p.ref, _p(Q), depth, tree["K"], _p(tree["off"]), _p(f["n_level"]),
+                           _p(f["parent"]), _p(f["action"]), _p(f["obs"]), _p(f["weight"]),
+                           _p(f["UQ"]), _p(f["belief"]), float(dL), _p(Qbar), _p(Rbar),
+                           C.byref(ds), C.byref(da), _p(db0))
+    return dict(Qbar=Qbar.reshape(A, p.n), Rbar=Rbar.reshape(A, p.n), dslip=ds.value,
+                dacc=da.value, db0=db0)
+
+
+def vi_backward(w, sweeps, Qbar, Rbar=None, **kw):
+    """Adjoint of `sweeps` truncated VI sweeps and of R and Q.  Returns
+    dict(dslip, dcost [n], Rbar [5][n] after the Q and sweep terms)."""
+    p = _prob(w, **kw)
+    Qbar = np.ascontiguousarray(np.asarray(Qbar, np.float64).reshape(-1))
+    Rbar = np.zeros(A * p.n) if Rbar is None else np.array(Rbar, np.float64).reshape(-1)
+    dcost = np.zeros(p.n, np.float64)
+    ds = C.c_double(0.0)
+    lib().or_vi_backward(p.ref, int(sweeps), _p(Qbar), _p(Rbar), C.byref(ds), _p(dcost))
+    return dict(dslip=ds.value, dcost=dcost, Rbar=Rbar.reshape(A, p.n))
+
+
+def root_value(w, sweeps, depth=None, K=None, seed=None, episode=None, replay=None, b0=None, **kw):
+    """Root value of the plan on Q from `sweeps` truncated VI sweeps (FREQ
+    weights; `replay` fixes the sampled measurements)."""
+    p = _prob(w, **kw)
+    vi = value_iteration(p, truncated=sweeps)
+    t = tree_plan(p, vi["Q"], depth=depth, K=K, seed=seed, episode=episode, replay=replay, b0=b0)
+    return t["root_value"], t
+
+
+def root_value_grad(w, sweeps, depth=None, K=None, seed=None, episode=None, replay=None, b0=None,
+                    dL=1.0, **kw):
+    """Reverse mode of root_value: dict(value, dslip, dacc, dcost [n],
+    db0 [n], tree)."""
+    p = _prob(w, **kw)
+    depth = p.w.depth if depth is None else depth
+    vi = value_iteration(p, truncated=sweeps)
+    t = tree_plan(p, vi["Q"], depth=depth, K=K, seed=seed, episode=episode, replay=replay, b0=b0,
+                  store_levels=max(depth - 1, 0))
+    tb = tree_backward(p, vi["Q"], t, dL=dL)
+    vb = vi_backward(p, sweeps, tb["Qbar"], tb["Rbar"])
+    return dict(value=t["root_value"], dslip=tb["dslip"] + vb["dslip"], dacc=tb["dacc"],
+                dcost=vb["dcost"], db0=tb["db0"], tree=t, Q=vi["Q"])
 
 
 def num_threads():

@@ -439,3 +439,233 @@ int or_tree_plan(const or_problem *p, const double *Q, const double *b0,
     free(lev_b); free(code); free(label); free(Rt);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode (adjoint) of the root value.  The plan's value is a function
+ * of the slip eps (through T, Sec. II and Eq. 10), the sensor accuracy alpha
+ * (through O) and the cost map c (through r and so R and Q).  Everything the
+ * forward pass decided is held fixed: the sampled measurements, the FREQ
+ * weights f/K, every max over actions (Alg. 7, Eq. 4 over the leaf's
+ * alpha-vectors, the Bellman max of each sweep), ties to the lowest index.
+ * Only the FREQ weighting is handled: its weights do not depend on the
+ * parameters.                                                               */
+
+/* d T(x, a, y) / d eps on the targets of or_transition_row: the intended
+ * move (weight 1 - 2 eps) gives -2, each perpendicular slip (eps) gives +1;
+ * Eq. 10 folds blocked moves onto x exactly as in the forward row.  Rows of
+ * absorbing cells and of the stay action do not depend on eps.             */
+int or_transition_row_dslip(const or_problem *p, int x, int a, int *y, double *dpr) {
+    int n = 0;
+    if (p->occ[x] || x == p->goal || a == 4) {
+        y[0] = x; dpr[0] = 0.0;
+        return 1;
+    }
+    int r = x / p->W, c = x % p->W;
+    int dirs[3] = {a, (a + 1) % 4, (a + 3) % 4};
+    double w[3] = {-2.0, 1.0, 1.0};
+    for (int i = 0; i < 3; ++i) {
+        int rr = r + DR[dirs[i]], cc = c + DC[dirs[i]];
+        int t = is_free(p, rr, cc) ? rr * p->W + cc : x;
+        int j;
+        for (j = 0; j < n; ++j)
+            if (y[j] == t) { dpr[j] += w[i]; break; }
+        if (j == n) { y[n] = t; dpr[n] = w[i]; ++n; }
+    }
+    return n;
+}
+
+/* d O(x', z) / d alpha: 1 on the cell's own label, -1/B elsewhere.         */
+static double obs_lik_dacc(const or_problem *p, const int *label, int x, int z) {
+    return label[x] == z ? 1.0 : -1.0 / (double)p->B;
+}
+
+static int argmax5(const double *q) {
+    int best = 0;
+    for (int a = 1; a < OR_NUM_ACTIONS; ++a)
+        if (q[a] > q[best]) best = a;
+    return best;
+}
+
+int or_tree_backward(const or_problem *p, const double *Q, int depth, int K, const long *off,
+                     const int *n_level, const int *parent, const int *action, const int *obs,
+                     const double *weight, const double *UQ, const double *belief, double dL_dV,
+                     double *Qbar, double *Rbar, double *dslip, double *dacc, double *db0) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS;
+    (void)K;
+    double qa[OR_NUM_ACTIONS];
+    if (depth == 0) {
+        /* the root is the leaf: U_V(b0) = max_a sum_x b0(x) Q(a, x) (Eq. 4) */
+        const double *b = belief;
+        or_leaf_value(p, Q, b, qa);
+        const int ap = argmax5(qa);
+        for (int x = 0; x < n; ++x) {
+            if (p->occ[x]) continue;
+            Qbar[ap * n + x] += dL_dV * b[x];
+            if (db0) db0[x] += dL_dV * Q[ap * n + x];
+        }
+        return 0;
+    }
+    int *label = (int *)malloc(sizeof(int) * n);
+    double *Rt = (double *)malloc(sizeof(double) * A * n);
+    or_labels(p, label);
+    or_reward_table(p, Rt);
+    /* adjoint of every V-node's value, top down: Alg. 7 passes it to the
+     * chosen action only, Alg. 6 to that action's children times gamma f/K */
+    double *u = (double *)calloc((size_t)off[depth + 1], sizeof(double));
+    int *best = (int *)calloc((size_t)off[depth + 1], sizeof(int));
+    u[off[0]] = dL_dV;
+    for (int l = 0; l < depth; ++l) {
+        for (int i = 0; i < n_level[l]; ++i) best[off[l] + i] = argmax5(UQ + (off[l] + i) * A);
+        for (int j = 0; j < n_level[l + 1]; ++j) {
+            const long t = off[l + 1] + j;
+            const long pi = off[l] + parent[t];
+            if (action[t] == best[pi]) u[t] = p->gamma * weight[t] * u[pi];
+        }
+    }
+    /* adjoint of the belief of every V-node of the level below */
+    double *beta_below = NULL;
+    double *bbar = (double *)malloc(sizeof(double) * n);
+    double *bc = (double *)malloc(sizeof(double) * n);
+    double *betac = (double *)malloc(sizeof(double) * n);
+    double *g = (double *)malloc(sizeof(double) * n);
+    for (int l = depth - 1; l >= 0; --l) {
+        double *beta = (double *)calloc((size_t)(n_level[l] > 0 ? n_level[l] : 1) * n, sizeof(double));
+        for (int i = 0; i < n_level[l]; ++i) {
+            const long si = off[l] + i;
+            const double ui = u[si];
+            if (ui == 0.0) continue;
+            const double *b = belief + (size_t)si * n;
+            const int a = best[si];
+            or_predict(p, b, a, bbar);                     /* Eq. 3 numerator */
+            for (int y = 0; y < n; ++y) g[y] = 0.0;
+            for (int j = 0; j < n_level[l + 1]; ++j) {
+                const long t = off[l + 1] + j;
+                if (parent[t] != i || action[t] != a) continue;
+                const int z = obs[t];
+                const double P = or_correct(p, label, bbar, z, bc);   /* Eq. 3 */
+                if (l + 1 == depth) {
+                    /* leaf: V(b') = sum_y b'(y) Q(a', y) with a' its argmax */
+                    or_leaf_value(p, Q, bc, qa);
+                    const int ap = argmax5(qa);
+                    for (int y = 0; y < n; ++y) {
+                        betac[y] = p->occ[y] ? 0.0 : u[t] * Q[ap * n + y];
+                        if (!p->occ[y]) Qbar[ap * n + y] += u[t] * bc[y];
+                    }
+                } else {
+                    memcpy(betac, beta_below + (size_t)j * n, sizeof(double) * n);
+                }
+                /* b' = O_z bbar / P(z):  dL/dbbar = O_z (beta' - <beta', b'>) / P,
+                 * dL/dO_z(y) = bbar(y) (beta'(y) - <beta', b'>) / P           */
+                double s = 0.0;
+                for (int y = 0; y < n; ++y) s += betac[y] * bc[y];
+                for (int y = 0; y < n; ++y) {
+                    const double d = (betac[y] - s) / P;
+                    g[y] += or_obs_lik(p, label, y, z) * d;
+                    *dacc += bbar[y] * d * obs_lik_dacc(p, label, y, z);
+                }
+            }
+            /* U_Q(b, a) = R(b, a) + ...:  R(b, a) = sum_x R(x, a) b(x), and
+             * bbar = T_a^T b:  dL/db(x) = u R(x, a) + sum_y T(x, a, y) g(y) */
+            double *bi = beta + (size_t)i * n;
+            for (int x = 0; x < n; ++x) {
+                if (p->occ[x]) continue;
+                int ys[3]; double pr[3];
+                int m = or_transition_row(p, x, a, ys, pr);
+                double s = 0.0;
+                for (int k = 0; k < m; ++k) s += pr[k] * g[ys[k]];
+                bi[x] = ui * Rt[a * n + x] + s;
+                Rbar[a * n + x] += ui * b[x];
+                m = or_transition_row_dslip(p, x, a, ys, pr);
+                double ds = 0.0;
+                for (int k = 0; k < m; ++k) ds += pr[k] * g[ys[k]];
+                *dslip += b[x] * ds;
+            }
+        }
+        free(beta_below);
+        beta_below = beta;
+    }
+    if (db0)
+        for (int x = 0; x < n; ++x) db0[x] += beta_below[x];
+    free(beta_below); free(bbar); free(bc); free(betac); free(g);
+    free(u); free(best); free(label); free(Rt);
+    return 0;
+}
+
+int or_vi_backward(const or_problem *p, int sweeps, const double *Qbar, double *Rbar,
+                   double *dslip, double *dcost) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS;
+    double *R = (double *)malloc(sizeof(double) * A * n);
+    double *V = (double *)calloc((size_t)(sweeps + 1) * n, sizeof(double));  /* V_0 .. V_S */
+    int *astar = (int *)malloc(sizeof(int) * (size_t)(sweeps > 0 ? sweeps : 1) * n);
+    or_reward_table(p, R);
+    /* the forward sweeps of or_value_iteration, every V_k and argmax kept */
+    for (int k = 0; k < sweeps; ++k) {
+        const double *Vk = V + (size_t)k * n;
+        double *Vn = V + (size_t)(k + 1) * n;
+        for (int x = 0; x < n; ++x) {
+            astar[(size_t)k * n + x] = -1;
+            if (p->occ[x] || x == p->goal) { Vn[x] = 0.0; continue; }
+            double best = -HUGE_VAL;
+            for (int a = 0; a < A; ++a) {
+                int y[3]; double pr[3];
+                int m = or_transition_row(p, x, a, y, pr);
+                double s = 0.0;
+                for (int j = 0; j < m; ++j) s += pr[j] * Vk[y[j]];
+                double q = R[a * n + x] + p->gamma * s;
+                if (q > best) { best = q; astar[(size_t)k * n + x] = a; }
+            }
+            Vn[x] = best;
+        }
+    }
+    double *lam = (double *)calloc(n, sizeof(double));
+    double *lam_prev = (double *)calloc(n, sizeof(double));
+    /* Q(a, x) = R(x, a) + gamma sum_y T(x, a, y) V_S(y) */
+    const double *VS = V + (size_t)sweeps * n;
+    for (int x = 0; x < n; ++x) {
+        if (p->occ[x] || x == p->goal) continue;
+        for (int a = 0; a < A; ++a) {
+            const double qb = Qbar[a * n + x];
+            if (qb == 0.0) continue;
+            Rbar[a * n + x] += qb;
+            int y[3]; double pr[3];
+            int m = or_transition_row(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j) lam[y[j]] += p->gamma * qb * pr[j];
+            m = or_transition_row_dslip(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j) *dslip += p->gamma * qb * pr[j] * VS[y[j]];
+        }
+    }
+    /* V_{k+1}(x) = R(x, a*) + gamma sum_y T(x, a*, y) V_k(y), k = S-1 .. 0 */
+    for (int k = sweeps - 1; k >= 0; --k) {
+        const double *Vk = V + (size_t)k * n;
+        for (int y = 0; y < n; ++y) lam_prev[y] = 0.0;
+        for (int x = 0; x < n; ++x) {
+            if (p->occ[x] || x == p->goal) continue;
+            const double lx = lam[x];
+            if (lx == 0.0) continue;
+            const int a = astar[(size_t)k * n + x];
+            Rbar[a * n + x] += lx;
+            int y[3]; double pr[3];
+            int m = or_transition_row(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j) lam_prev[y[j]] += p->gamma * lx * pr[j];
+            m = or_transition_row_dslip(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j) *dslip += p->gamma * lx * pr[j] * Vk[y[j]];
+        }
+        double *t = lam; lam = lam_prev; lam_prev = t;
+    }
+    /* R(x, a) = sum_y T(x, a, y) r(y), r(y) = -1 - c(y) off the goal */
+    for (int x = 0; x < n; ++x) {
+        if (p->occ[x] || x == p->goal) continue;
+        for (int a = 0; a < A; ++a) {
+            const double rb = Rbar[a * n + x];
+            if (rb == 0.0) continue;
+            int y[3]; double pr[3];
+            int m = or_transition_row_dslip(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j) *dslip += rb * pr[j] * stage_reward(p, y[j]);
+            m = or_transition_row(p, x, a, y, pr);
+            for (int j = 0; j < m; ++j)
+                if (y[j] != p->goal && dcost) dcost[y[j]] -= rb * pr[j];
+        }
+    }
+    free(R); free(V); free(astar); free(lam); free(lam_prev);
+    return 0;
+}

@@ -80,6 +80,24 @@ int or_tree_plan(const or_problem *p, const double *Q, const double *b0,
                  double *belief, int *root_action, double *root_value,
                  double *root_q, long *boundary_count);
 
+/* ---- reverse mode (FREQ weights; samples and every argmax held fixed) ---- */
+/* d T(x, a, .) / d eps on the targets of or_transition_row.                */
+int or_transition_row_dslip(const or_problem *p, int x, int a, int *y, double *dpr);
+/* Adjoint of the root value of an or_tree_plan tree (its flat arrays, with
+ * belief holding levels 0..depth-1).  Accumulates (+=) into Qbar[5n] (dL/dQ),
+ * Rbar[5n] (dL/dR(x, a) of the internal nodes' R(b, a)), *dslip (through T
+ * in every prediction), *dacc (through O in every correction) and db0[n]
+ * (nullable).                                                              */
+int or_tree_backward(const or_problem *p, const double *Q, int depth, int K, const long *off,
+                     const int *n_level, const int *parent, const int *action, const int *obs,
+                     const double *weight, const double *UQ, const double *belief, double dL_dV,
+                     double *Qbar, double *Rbar, double *dslip, double *dacc, double *db0);
+/* Adjoint of `sweeps` truncated Jacobi sweeps from V_0 = 0 and of
+ * Q = R + gamma T V_sweeps and R(x, a) = sum_y T r: given Qbar and Rbar
+ * (Rbar updated in place), accumulates *dslip and dcost[n] (nullable).     */
+int or_vi_backward(const or_problem *p, int sweeps, const double *Qbar, double *Rbar,
+                   double *dslip, double *dcost);
+
 int or_num_threads(void);
 
 #endif
