@@ -135,6 +135,33 @@ qv_status mdp_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
                             void *d_ws, size_t ws_bytes, int32_t *sweeps_out,
                             double *residual_out, qv_stream_t stream);
 
+/* mdp_value_iterate_checkpointed: exactly `sweeps` FP64 Jacobi sweeps of the
+ * same operator from V_0 = 0 (d_V is zeroed first), for the adjoint below.
+ * Also stores V_k for k = 0, every, 2*every, ... < sweeps into d_Vckpt
+ * ([ceil(sweeps / every)][H][pitch] FP64).  Writes V_sweeps to d_V and Q
+ * (FP32) as mdp_value_iterate does.  Workspace:
+ * mdp_value_iterate_workspace_bytes(model, QV_F64).  Synchronises. */
+qv_status mdp_value_iterate_checkpointed(const qv_model_t *model, int32_t sweeps, int32_t every,
+                                         double *d_V, float *d_Q, double *d_Vckpt,
+                                         void *d_ws, size_t ws_bytes, qv_stream_t stream);
+
+/* mdp_value_backward: reverse mode of mdp_value_iterate_checkpointed (the
+ * derivatives of Eq. 2's Bellman sweeps and of Eq. 10's transition model).
+ * Given d_Qbar = dL/dQ[a][y] (FP64 [5][H][pitch]), accumulates (+=)
+ *   *d_dslip       dL/d slip   (device FP64 scalar),
+ *   d_dcost[y]     dL/d c(y)   (FP64 [H][pitch], nullable),
+ * through Q = R + gamma T V_sweeps, every sweep V_{k+1} = max_a [R + gamma T
+ * V_k] with its argmax held fixed (ties to the lowest action index, as the
+ * forward takes them), and R(x, a) = sum_y T(x, a, y) r(y), r(y) = -1 - c(y)
+ * off the goal.  The sweeps are recomputed segment by segment from the
+ * checkpoints of the forward call (same model, sweeps and every), so memory
+ * holds `every` sweeps at a time.  One persistent cooperative launch with a
+ * bounded grid barrier; QV_ERR_TIMEOUT if a wait gives up.  Synchronises. */
+size_t mdp_value_backward_workspace_bytes(const qv_model_t *model, int32_t every);
+qv_status mdp_value_backward(const qv_model_t *model, int32_t sweeps, int32_t every,
+                             const double *d_Vckpt, const double *d_Qbar, double *d_dslip,
+                             double *d_dcost, void *d_ws, size_t ws_bytes, qv_stream_t stream);
+
 /* ---------------------------------------------------------------- belief update (Eq. 3)
  * belief_predict: bbar(y) = sum_x T(x, action, y) b(x), the numerator of
  * Eq. 3.  Values stored on occupied cells of b are read as 0. */
@@ -226,8 +253,33 @@ typedef struct {
     const int32_t *d_nchild;   /* [cap][5] unique children per action                  */
     const int32_t *d_samples;  /* [cap][5][K] raw sampled z                            */
     const float *d_belief;     /* [cap][H][pitch] or NULL                              */
+    const int32_t *d_leaf_arg; /* leaves: argmax a' of sum_y b(y) Q(a', y), else NULL  */
 } qv_level_view_t;
 qv_status qv_plan_level(const qv_plan_t *plan, int32_t e, int32_t level, qv_level_view_t *view);
+
+/* ---------------------------------------------------------------- adjoint of the plan
+ * qv_tree_backward: reverse mode of the root value U_V(b0) of episode e of a
+ * plan that has run (stream order), by the derivatives of Alg. 6 and 7
+ * (backup), Eq. 4 (leaf values), Eq. 3 (prediction, correction and its
+ * normalisation) and R(b, a).  Held fixed: the sampled measurements, the
+ * FREQ weights f/K, and every max (Alg. 7 over actions, Eq. 4 over a leaf's
+ * alpha-vectors; ties to the lowest index).  MARGINAL weights depend on the
+ * parameters and are refused (QV_ERR_INVALID).  With seed adjoint dL_dV,
+ * accumulates (+=) into FP64 device buffers:
+ *   d_Qbar   [5][H][pitch]  dL/dQ (feed to mdp_value_backward)
+ *   d_dslip  scalar         dL/d slip through every T_a in the tree
+ *   d_dacc   scalar         dL/d accuracy through every O(., z)
+ *   d_dcost  [H][pitch]     dL/d c(y) through every R(b, a)   (nullable)
+ *   d_db0    [H][pitch]     dL/d b0(y)                        (nullable)
+ * Only the V-nodes on the chosen actions carry a nonzero adjoint; their
+ * beliefs come from the plan (the deepest internal level of the fused mode
+ * is recomputed from its parents).  Asynchronous, allocation-free and
+ * capturable; the workspace is the caller's (contents need no clearing).
+ * Contributions to d_Qbar and d_dcost are summed with FP64 atomics. */
+size_t qv_tree_backward_workspace_bytes(const qv_plan_t *plan, int32_t e);
+qv_status qv_tree_backward(const qv_plan_t *plan, int32_t e, double dL_dV, double *d_Qbar,
+                           double *d_dslip, double *d_dacc, double *d_dcost, double *d_db0,
+                           void *d_ws, size_t ws_bytes, qv_stream_t stream);
 
 /* One plan from b0 to the chosen action: create + run + read + destroy.
  * Synchronises the stream. */

@@ -47,7 +47,8 @@ class qv_level_view_t(C.Structure):
     _fields_ = [("cap", C.c_int32), ("d_count", C.c_void_p), ("d_parent", C.c_void_p),
                 ("d_action", C.c_void_p), ("d_obs", C.c_void_p), ("d_weight", C.c_void_p),
                 ("d_pz", C.c_void_p), ("d_value", C.c_void_p), ("d_R", C.c_void_p), ("d_UQ", C.c_void_p),
-                ("d_nchild", C.c_void_p), ("d_samples", C.c_void_p), ("d_belief", C.c_void_p)]
+                ("d_nchild", C.c_void_p), ("d_samples", C.c_void_p), ("d_belief", C.c_void_p),
+                ("d_leaf_arg", C.c_void_p)]
 
 
 class qv_launch_time_t(C.Structure):
@@ -65,6 +66,9 @@ SIGNATURES = {
     "mdp_value_iterate_workspace_bytes": (_sz, [_M, _i32]),
     "mdp_value_iterate": (C.c_int, [_M, _i32, C.c_double, _i32, _i32, _vp, _vp, _vp, _sz,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_double), _vp]),
+    "mdp_value_iterate_checkpointed": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "mdp_value_backward_workspace_bytes": (_sz, [_M, _i32]),
+    "mdp_value_backward": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "belief_predict": (C.c_int, [_M, _vp, _i32, _vp, _vp]),
     "belief_correct_workspace_bytes": (_sz, [_M]),
     "belief_correct": (C.c_int, [_M, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
@@ -78,6 +82,8 @@ SIGNATURES = {
     "qv_plan_destroy": (None, [_vp]),
     "qv_plan_profile": (C.c_int, [_vp, C.POINTER(qv_launch_time_t), _i32, C.POINTER(C.c_int32), _vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
+    "qv_tree_backward_workspace_bytes": (_sz, [_vp, _i32]),
+    "qv_tree_backward": (C.c_int, [_vp, _i32, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qv_tree_plan": (C.c_int, [_M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
     "qv_tree_plan_batched": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
 }

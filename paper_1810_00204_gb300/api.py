@@ -16,8 +16,9 @@ import torch
 from . import _native as N
 from ._native import check, lib
 
-__all__ = ["Model", "Plan", "qv_model_build", "mdp_value_iterate", "belief_predict", "belief_correct",
-           "leaf_value", "qv_tree_plan", "qv_tree_plan_batched", "pitch_of"]
+__all__ = ["Model", "Plan", "qv_model_build", "mdp_value_iterate", "mdp_value_iterate_checkpointed",
+           "mdp_value_backward", "belief_predict", "belief_correct", "leaf_value", "qv_tree_plan",
+           "qv_tree_plan_batched", "qv_tree_backward", "pitch_of"]
 
 
 def pitch_of(W: int) -> int:
@@ -60,7 +61,7 @@ class Model:
         qv_model_build(self.H, self.W, self.P, self.occ, self.beacons, self.B, w.sense_range, self.goal,
                        self.cell, stream)
         c = w.cost if isinstance(cost, str) else cost
-        self.cost = None if c is None else self.to_grid(np.asarray(c, np.float32))
+        self.cost = None if c is None else self.to_grid(c if torch.is_tensor(c) else np.asarray(c, np.float32))
         self.slip = float(w.slip if slip is None else slip)
         self.accuracy = float(w.accuracy if accuracy is None else accuracy)
         self.discount = float(w.discount)
@@ -111,6 +112,35 @@ def mdp_value_iterate(model: Model, dtype="f32", tol=None, max_sweeps=100000, tr
     if st not in (N.QV_OK, N.QV_ERR_NOT_CONVERGED):
         check(st, "mdp_value_iterate")
     return dict(V=V, Q=Q, sweeps=sweeps.value, residual=res.value, status=st)
+
+
+def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
+    """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
+    is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),
+    Q (FP32 [5][H][pitch]), ckpt (FP64 [ceil(sweeps/every)][H][pitch]),
+    sweeps, every)."""
+    J = (int(sweeps) + int(every) - 1) // int(every)
+    V = torch.empty((model.H, model.P), dtype=torch.float64, device=model.device)
+    Q = torch.empty((5, model.H, model.P), dtype=torch.float32, device=model.device)
+    ck = torch.empty((J, model.H, model.P), dtype=torch.float64, device=model.device)
+    nbytes = lib().mdp_value_iterate_workspace_bytes(C.byref(model.struct), N.QV_F64)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.device)
+    check(lib().mdp_value_iterate_checkpointed(C.byref(model.struct), int(sweeps), int(every), _ptr(V), _ptr(Q),
+                                               _ptr(ck), _ptr(ws), nbytes, _stream(stream)),
+          "mdp_value_iterate_checkpointed")
+    return dict(V=V, Q=Q, ckpt=ck, sweeps=int(sweeps), every=int(every))
+
+
+def mdp_value_backward(model: Model, vi: dict, Qbar: torch.Tensor, dslip: torch.Tensor,
+                       dcost: Optional[torch.Tensor] = None, stream=None):
+    """Accumulates dL/dslip (FP64 device scalar) and dL/dc (FP64 [H][pitch])
+    through the checkpointed sweeps `vi`, given Qbar = dL/dQ (FP64 [5][H][pitch])."""
+    nbytes = lib().mdp_value_backward_workspace_bytes(C.byref(model.struct), vi["every"])
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.device)
+    check(lib().mdp_value_backward(C.byref(model.struct), vi["sweeps"], vi["every"], _ptr(vi["ckpt"]),
+                                   _ptr(Qbar.contiguous()), _ptr(dslip), _ptr(dcost), _ptr(ws), nbytes,
+                                   _stream(stream)), "mdp_value_backward")
+    return dslip, dcost
 
 
 def belief_predict(model: Model, b: torch.Tensor, action: int, out=None, stream=None):
@@ -192,6 +222,14 @@ class Plan:
     def workspace_bytes(self):
         return self.ws.numel()
 
+    def backward_workspace(self, nbytes: int) -> torch.Tensor:
+        """Device scratch for qv_tree_backward, kept with the plan."""
+        ws = getattr(self, "_bws", None)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.models[0].device)
+            self._bws = ws
+        return ws
+
     def run(self, stream=None):
         check(lib().qv_plan_run(self.handle, _stream(stream)), "qv_plan_run")
 
@@ -242,6 +280,8 @@ class Plan:
             out[key] = None if t is None else t[:n]
         t = self._view(v.d_samples, cap * 5 * self.K, torch.int32, (cap, 5, self.K)) if v.d_samples else None
         out["samples"] = None if t is None else t[:n]
+        t = self._view(v.d_leaf_arg, cap, torch.int32) if v.d_leaf_arg else None
+        out["leaf_arg"] = None if t is None else t[:n]
         if l == 0:
             out["belief"] = self.b0s[e].view(1, m.H, m.P)
         else:
@@ -254,6 +294,30 @@ class Plan:
         if h is not None and h.value:
             lib().qv_plan_destroy(h)
             self.handle = C.c_void_p()
+
+
+def qv_tree_backward(plan: Plan, e: int = 0, dL: float = 1.0, Qbar=None, dslip=None, dacc=None, dcost=None,
+                     db0=None, want_db0=True, stream=None):
+    """Adjoint of episode e's root value (FREQ weights; samples and every
+    argmax held fixed).  Accumulates into FP64 device tensors, created zeroed
+    when not given: Qbar [5][H][pitch], dslip [1], dacc [1], dcost [H][pitch],
+    db0 [H][pitch].  Asynchronous: nothing is read back."""
+    m = plan.models[e]
+    dev = m.device
+    f64 = dict(dtype=torch.float64, device=dev)
+    Qbar = torch.zeros((5, m.H, m.P), **f64) if Qbar is None else Qbar
+    dslip = torch.zeros(1, **f64) if dslip is None else dslip
+    dacc = torch.zeros(1, **f64) if dacc is None else dacc
+    dcost = torch.zeros((m.H, m.P), **f64) if dcost is None else dcost
+    if db0 is None and want_db0:
+        db0 = torch.zeros((m.H, m.P), **f64)
+    nbytes = lib().qv_tree_backward_workspace_bytes(plan.handle, int(e))
+    if nbytes == 0:
+        raise N.QVError(N.QV_ERR_INVALID, "qv_tree_backward_workspace_bytes")
+    ws = plan.backward_workspace(nbytes)
+    check(lib().qv_tree_backward(plan.handle, int(e), float(dL), _ptr(Qbar), _ptr(dslip), _ptr(dacc), _ptr(dcost),
+                                 _ptr(db0), _ptr(ws), nbytes, _stream(stream)), "qv_tree_backward")
+    return dict(Qbar=Qbar, dslip=dslip, dacc=dacc, dcost=dcost, db0=db0)
 
 
 def qv_tree_plan(model: Model, Q: torch.Tensor, b0: torch.Tensor, depth=2, K=4, seed=0, episode=0,

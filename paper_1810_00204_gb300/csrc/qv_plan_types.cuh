@@ -1,0 +1,133 @@
+// qv_plan_types.cuh -- the plan's data structures, shared by the search
+// kernel (qv_tree_device.cuh), its host side (qv_tree.cu) and the adjoint
+// (qv_adjoint.cu): per-episode descriptors, the device view of a plan's
+// workspace, and the host handle.
+#pragma once
+
+#include <vector>
+
+#include "qv_common.cuh"
+
+namespace qv {
+
+constexpr int kMaxD = QV_MAX_DEPTH;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kLeafGroup = 4;
+constexpr int kBandCells = 2048;
+constexpr float kBoundaryEps = 1e-6f;
+constexpr int kStamps = 4 * kMaxD + 8;
+
+struct __align__(16) EpDev {
+    int H, W, P, N;          // N = H * P
+    int B, goal;
+    float slip, acc, eta, gamma;
+    const uint16_t *cell;
+    const float *cost;
+    const float *Q;          // [5][N]
+    const float *b0;         // [N]
+    const int *beacons;      // [B] beacon cells (row * P + col)
+    int range;               // Manhattan sensing range
+    int band_rows, bands;
+    uint32_t episode;
+    int cap[kMaxD + 1];         // node capacity of each level
+    int node_base[kMaxD + 1];   // gid of local node 0 of level l
+    int inode_base[kMaxD + 1];  // iid of local node 0 of internal level l < d
+    int pad2;
+    long long belief_off[kMaxD + 1];  // float offset of stored level-l beliefs, -1 when not stored
+};
+static_assert(sizeof(EpDev) % 16 == 0, "EpDev is copied to smem in 16-byte words");
+
+// The scalars the band loops read, held in registers for the duration of a
+// work item (reading them from the shared-memory descriptor inside the loops
+// would reload them after every shared-memory store).
+struct EpReg {
+    int H, W, P, N, B, goal, range;
+    float slip;
+    const uint16_t *cell;
+    const float *cost, *Q;
+};
+__device__ __forceinline__ EpReg ep_reg(const EpDev &e) {
+    EpReg r;
+    r.H = e.H;
+    r.W = e.W;
+    r.P = e.P;
+    r.N = e.N;
+    r.B = e.B;
+    r.goal = e.goal;
+    r.range = e.range;
+    r.slip = e.slip;
+    r.cell = e.cell;
+    r.cost = e.cost;
+    r.Q = e.Q;
+    return r;
+}
+
+struct ResultDev {
+    int action;
+    float value;
+    float q[5];
+    int pad;
+};
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+struct PlanDev {
+    int E, depth, K, weight_mode, leaf_mode, Bmax, rec_len, target, n_part;
+    int sb_floats, sp_floats, q_floats;  // shared-memory band buffers
+    uint64_t seed;
+    const EpDev *eps;
+    float *beliefs;
+    int *count;        // [(d+1)][E] nodes per level
+    int *items;        // [(d+1)][E] expand work items per node
+    int *uitems;       // [(d+1)][E] update work items per node
+    int *wb_stats;     // [(d+1)][E+1] work-list prefixes
+    int *wb_upd;       // [(d+1)][E+1]
+    int *wb_leaf;      // [E+1]
+    int *leaf_split;   // chunks per group of leaves in the leaf phase
+    unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
+    // per node (gid over every level)
+    int *parent, *action, *obs;
+    float *weight, *pz, *value;
+    unsigned long long *code;
+    long long *src_slot;  // slot of the node in its parent's sample arrays
+    // per internal node (iid over levels < d)
+    unsigned *node_cnt;
+    float *R, *UQ;     // [iid][5]
+    int *nchild, *choff;
+    int *samples;      // [iid][5][K]
+    int *slot_z, *slot_cnt;
+    float *slot_P, *slot_w, *slot_val;
+    int *slot_arg;     // [iid][5][K] argmax action of a fused leaf's value (Eq. 4)
+    int *leaf_arg;     // per node: argmax action of a leaf's value (ties to the lowest index)
+    // arrival counters and scratch
+    unsigned *ep_cnt;  // [(d+1)][E]
+    unsigned *lvl_cnt; // [d+1]
+    float *partials;   // [n_part][rec_len]
+    unsigned *status;
+    unsigned long long *boundary;
+    GridBar *bar;
+    unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
+    ResultDev *result; // [E]
+    const int *replay;
+};
+
+}  // namespace qv
+
+// Host handle of a plan (qv_plan_t in the C ABI).
+struct qv_plan {
+    int E = 0;
+    qv_plan_params_t params{};
+    std::vector<qv::EpDev> eps;
+    qv::PlanDev dev{};
+    char *ws = nullptr;
+    size_t bytes = 0;
+    int grid = 0;
+    size_t smem = 0;
+    size_t reset_off = 0, reset_bytes = 0;  // counters zeroed when a run failed
+    bool dirty = false;
+    cudaGraphExec_t graph = nullptr;
+};

@@ -8,27 +8,13 @@
 #include "qv_tree_device.cuh"
 
 // ======================================================================== host side
-struct qv_plan {
-    int E = 0;
-    qv_plan_params_t params{};
-    std::vector<qv::EpDev> eps;
-    qv::PlanDev dev{};
-    char *ws = nullptr;
-    size_t bytes = 0;
-    int grid = 0;
-    size_t smem = 0;
-    size_t reset_off = 0, reset_bytes = 0;  // counters zeroed when a run failed
-    bool dirty = false;
-    cudaGraphExec_t graph = nullptr;
-};
-
 namespace {
 
 struct Layout {
     size_t total = 0;
     size_t off_eps, off_count, off_items, off_uitems, off_wbs, off_wbu, off_wbl, off_parent, off_action, off_obs,
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
-        off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_ep_cnt, off_lvl_cnt, off_partials,
+        off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
         off_status, off_boundary, off_bar, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
@@ -209,6 +195,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_slot_P = take(sizeof(float) * L.NI * 5 * K);
     L.off_slot_w = take(sizeof(float) * L.NI * 5 * K);
     L.off_slot_val = take(sizeof(float) * L.NI * 5 * K);
+    L.off_slot_arg = take(sizeof(int) * L.NI * 5 * K);
+    L.off_leaf_arg = take(sizeof(int) * L.NT);
     L.off_partials = take(sizeof(float) * static_cast<size_t>(L.n_part) * L.rec_len);
     L.off_result = take(sizeof(qv::ResultDev) * E);
     L.off_stamps = take(sizeof(unsigned long long) * qv::kStamps);
@@ -338,6 +326,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.slot_P = at<float>(ws, L.off_slot_P);
     d.slot_w = at<float>(ws, L.off_slot_w);
     d.slot_val = at<float>(ws, L.off_slot_val);
+    d.slot_arg = at<int>(ws, L.off_slot_arg);
+    d.leaf_arg = at<int>(ws, L.off_leaf_arg);
     d.ep_cnt = at<unsigned>(ws, L.off_ep_cnt);
     d.lvl_cnt = at<unsigned>(ws, L.off_lvl_cnt);
     d.partials = at<float>(ws, L.off_partials);
@@ -546,6 +536,7 @@ extern "C" qv_status qv_plan_level(const qv_plan_t *pl, int32_t e, int32_t l, qv
         v->d_nchild = d.nchild + i * 5;
         v->d_samples = d.samples + i * 5 * K;
     }
+    if (l == pl->params.depth) v->d_leaf_arg = d.leaf_arg + g;
     if (l == 0) v->d_belief = ep.b0;
     else if (ep.belief_off[l] >= 0) v->d_belief = d.beliefs + ep.belief_off[l];
     return QV_OK;

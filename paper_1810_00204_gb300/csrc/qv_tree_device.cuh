@@ -36,112 +36,9 @@
 // waits for a level.
 #pragma once
 
-#include "qv_common.cuh"
+#include "qv_plan_types.cuh"
 
 namespace qv {
-
-constexpr int kMaxD = QV_MAX_DEPTH;
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kLeafGroup = 4;
-constexpr int kBandCells = 2048;
-constexpr float kBoundaryEps = 1e-6f;
-constexpr int kStamps = 4 * kMaxD + 8;
-
-struct __align__(16) EpDev {
-    int H, W, P, N;          // N = H * P
-    int B, goal;
-    float slip, acc, eta, gamma;
-    const uint16_t *cell;
-    const float *cost;
-    const float *Q;          // [5][N]
-    const float *b0;         // [N]
-    const int *beacons;      // [B] beacon cells (row * P + col)
-    int range;               // Manhattan sensing range
-    int band_rows, bands;
-    uint32_t episode;
-    int cap[kMaxD + 1];         // node capacity of each level
-    int node_base[kMaxD + 1];   // gid of local node 0 of level l
-    int inode_base[kMaxD + 1];  // iid of local node 0 of internal level l < d
-    int pad2;
-    long long belief_off[kMaxD + 1];  // float offset of stored level-l beliefs, -1 when not stored
-};
-static_assert(sizeof(EpDev) % 16 == 0, "EpDev is copied to smem in 16-byte words");
-
-// The scalars the band loops read, held in registers for the duration of a
-// work item (reading them from the shared-memory descriptor inside the loops
-// would reload them after every shared-memory store).
-struct EpReg {
-    int H, W, P, N, B, goal, range;
-    float slip;
-    const uint16_t *cell;
-    const float *cost, *Q;
-};
-__device__ __forceinline__ EpReg ep_reg(const EpDev &e) {
-    EpReg r;
-    r.H = e.H;
-    r.W = e.W;
-    r.P = e.P;
-    r.N = e.N;
-    r.B = e.B;
-    r.goal = e.goal;
-    r.range = e.range;
-    r.slip = e.slip;
-    r.cell = e.cell;
-    r.cost = e.cost;
-    r.Q = e.Q;
-    return r;
-}
-
-struct ResultDev {
-    int action;
-    float value;
-    float q[5];
-    int pad;
-};
-
-struct GridBar {
-    unsigned count;
-    unsigned gen;
-};
-
-struct PlanDev {
-    int E, depth, K, weight_mode, leaf_mode, Bmax, rec_len, target, n_part;
-    int sb_floats, sp_floats, q_floats;  // shared-memory band buffers
-    uint64_t seed;
-    const EpDev *eps;
-    float *beliefs;
-    int *count;        // [(d+1)][E] nodes per level
-    int *items;        // [(d+1)][E] expand work items per node
-    int *uitems;       // [(d+1)][E] update work items per node
-    int *wb_stats;     // [(d+1)][E+1] work-list prefixes
-    int *wb_upd;       // [(d+1)][E+1]
-    int *wb_leaf;      // [E+1]
-    int *leaf_split;   // chunks per group of leaves in the leaf phase
-    unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
-    // per node (gid over every level)
-    int *parent, *action, *obs;
-    float *weight, *pz, *value;
-    unsigned long long *code;
-    long long *src_slot;  // slot of the node in its parent's sample arrays
-    // per internal node (iid over levels < d)
-    unsigned *node_cnt;
-    float *R, *UQ;     // [iid][5]
-    int *nchild, *choff;
-    int *samples;      // [iid][5][K]
-    int *slot_z, *slot_cnt;
-    float *slot_P, *slot_w, *slot_val;
-    // arrival counters and scratch
-    unsigned *ep_cnt;  // [(d+1)][E]
-    unsigned *lvl_cnt; // [d+1]
-    float *partials;   // [n_part][rec_len]
-    unsigned *status;
-    unsigned long long *boundary;
-    GridBar *bar;
-    unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
-    ResultDev *result; // [E]
-    const int *replay;
-};
 
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
@@ -494,12 +391,17 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
                 pl.slot_P[sb + pos] = p;
                 if (fused) {
                     float best = -3.402823466e38f;
+                    int barg = 0;
                     for (int ap = 0; ap < 5; ++ap) {
                         const float mq = z < B ? S.histq[(a * Bm + z) * 5 + ap] : S.tot[10 + a * 5 + ap];
                         const float v = fmaf(acc - eta, mq, eta * S.T[a * 5 + ap]) / p;
-                        best = v > best ? v : best;
+                        if (v > best) {
+                            best = v;
+                            barg = ap;
+                        }
                     }
                     pl.slot_val[sb + pos] = best;
+                    pl.slot_arg[sb + pos] = barg;
                 }
             }
             psum += warp_sum(c > 0 ? p : 0.0f);
@@ -1169,6 +1071,7 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 }
             }
             pl.value[ep.node_base[l] + first + i] = best;
+            pl.leaf_arg[ep.node_base[l] + first + i] = ba;
             if (l == 0) {  // depth-0 plan: the root is the leaf
                 ResultDev r;
                 r.action = ba;
@@ -1203,7 +1106,10 @@ __device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep,
         pl.weight[g] = __ldcg(pl.slot_w + sb + j);
         pl.pz[g] = __ldcg(pl.slot_P + sb + j);
         pl.code[g] = (pcode * 5ull + a) * static_cast<unsigned long long>(nz) + z;
-        if (write_value) pl.value[g] = __ldcg(pl.slot_val + sb + j);
+        if (write_value) {
+            pl.value[g] = __ldcg(pl.slot_val + sb + j);
+            pl.leaf_arg[g] = __ldcg(pl.slot_arg + sb + j);
+        }
     }
 }
 

@@ -13,16 +13,10 @@
 // barrier whose waits are bounded (timeout -> status bit, every CTA exits).
 #include <algorithm>
 
-#include "qv_common.cuh"
+#include "qv_vi_cell.cuh"
 
 namespace qv {
 
-struct VIWork {
-    unsigned bar_count;
-    unsigned bar_gen;
-    unsigned status;
-    unsigned pad;
-};
 
 template <typename T>
 struct VIArgs {
@@ -43,64 +37,9 @@ struct VIArgs {
     int *sweeps_out;     // device: number of sweeps
     T *residual_out;     // device: last residual
     int chunk_rows;      // rows staged per smem chunk
+    T *ckpt;             // nullable: V_k stored at every k % every == 0, k < sweeps
+    int every;
 };
-
-// Bounded grid barrier (all CTAs co-resident through a cooperative launch).
-__device__ bool grid_barrier(VIWork *w, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *gen = &w->bar_gen;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(&w->bar_count, 1u) == nblocks - 1) {
-            atomicExch(&w->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&w->bar_gen, 1u);
-        } else {
-            unsigned i = 0;
-            while (*gen == g) {
-                if (++i > kSpinLimit || (*((volatile unsigned *)&w->status) & kErrTimeout)) {
-                    atomicOr(&w->status, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-template <typename T>
-__device__ __forceinline__ T arrive_value(const VIArgs<T> &a, int y, const T *Vs_row, int col) {
-    // r(y) + gamma V(y) for a free cell y
-    const float c = a.cost ? __ldg(a.cost + y) : 0.0f;
-    const T r = (y == a.goal) ? T(100) : T(-1) - T(c);
-    return r + a.gamma * Vs_row[col];
-}
-
-// Q_a(x) for the 5 actions of a free, non-goal cell, V staged in smem rows
-// (row stride P) where `rowp` points at x's row.
-template <typename T>
-__device__ __forceinline__ void cell_q(const VIArgs<T> &a, int y, int col, unsigned cw, const T *rowp,
-                                       T q[5]) {
-    const unsigned blk = QV_CELL_BLOCKED(cw);
-    const T wx = arrive_value(a, y, rowp, col);
-    T wn[4];
-    wn[kDirN] = (blk & 1u) ? wx : arrive_value(a, y - a.P, rowp - a.P, col);
-    wn[kDirE] = (blk & 2u) ? wx : arrive_value(a, y + 1, rowp, col + 1);
-    wn[kDirS] = (blk & 4u) ? wx : arrive_value(a, y + a.P, rowp + a.P, col);
-    wn[kDirW] = (blk & 8u) ? wx : arrive_value(a, y - 1, rowp, col - 1);
-    const T fwd = T(1) - T(2) * T(a.slip), eps = T(a.slip);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) q[d] = fwd * wn[d] + eps * (wn[(d + 1) & 3] + wn[(d + 3) & 3]);
-    q[4] = wx;
-}
 
 // Stage grid rows [c0-1, c1+1) of `src` (clipped to the grid) into smem rows
 // 0.. of Vs with one bulk copy.  False when the wait ran out (after a second
@@ -151,6 +90,10 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     while (k < limit) {
         const T *Vk = (k & 1) ? a.V1 : a.V0;
         T *Vn = (k & 1) ? a.V0 : a.V1;
+        if (a.ckpt && k % a.every == 0) {  // this CTA's rows of V_k, complete since the last barrier
+            T *dst = a.ckpt + static_cast<size_t>(k / a.every) * a.H * a.P;
+            for (int i = r_begin * a.P + threadIdx.x; i < r_end * a.P; i += blockDim.x) dst[i] = Vk[i];
+        }
         T local = T(0);
         for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
             const int c1 = min(r_end, c0 + a.chunk_rows);
@@ -237,7 +180,8 @@ size_t vi_ws_bytes(int H, int P, int nslots) {
 
 template <typename T>
 qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated, T *d_V, float *d_Q,
-                 void *d_ws, size_t ws_bytes, int *sweeps_out, double *residual_out, cudaStream_t st) {
+                 void *d_ws, size_t ws_bytes, int *sweeps_out, double *residual_out, cudaStream_t st,
+                 T *d_ckpt = nullptr, int every = 1) {
     const int H = m->H, P = m->pitch;
     // rows staged per chunk: (chunk + 2) rows within a 40 KB budget (at least
     // three rows, with the opt-in for large dynamic shared memory)
@@ -293,6 +237,8 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     a.sweeps_out = d_sweeps;
     a.residual_out = d_res;
     a.chunk_rows = chunk;
+    a.ckpt = d_ckpt;
+    a.every = every;
     void *args[] = {&a};
     if (qv_check_cuda(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_value_iteration<T>), grid, 256,
                                                   args, smem, st),
@@ -345,4 +291,25 @@ extern "C" qv_status mdp_value_iterate(const qv_model_t *m, int32_t dtype, doubl
         return qv::run_vi<float>(m, tol, max_sweeps, truncated, static_cast<float *>(d_V), d_Q, d_ws, ws_bytes,
                                  sweeps_out, residual_out, st);
     return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: dtype %d", dtype);
+}
+
+extern "C" qv_status mdp_value_iterate_checkpointed(const qv_model_t *m, int32_t sweeps, int32_t every, double *d_V,
+                                                    float *d_Q, double *d_Vckpt, void *d_ws, size_t ws_bytes,
+                                                    qv_stream_t stream) {
+    if (!m || !m->d_cell || !d_V || !d_Q || !d_Vckpt || !d_ws)
+        return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: null pointer");
+    if (m->H < 1 || m->W < 1 || m->pitch != QV_PITCH(m->W) || m->W > QV_MAX_WIDTH)
+        return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: bad grid");
+    if (!(m->discount > 0.0f && m->discount < 1.0f) || !(m->slip >= 0.0f && m->slip <= 0.5f))
+        return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: discount or slip out of range");
+    if (sweeps < 1 || every < 1)
+        return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: sweeps %d every %d", sweeps, every);
+    if ((reinterpret_cast<uintptr_t>(d_V) | reinterpret_cast<uintptr_t>(d_ws)) & 15)
+        return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: buffers must be 16-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // V_0 = 0
+    if (qv_check_cuda(cudaMemsetAsync(d_V, 0, sizeof(double) * m->H * m->pitch, st), "memset") != QV_OK)
+        return QV_ERR_CUDA;
+    return qv::run_vi<double>(m, 0.0, sweeps, sweeps, d_V, d_Q, d_ws, ws_bytes, nullptr, nullptr, st, d_Vckpt,
+                              every);
 }

@@ -26,7 +26,8 @@ def libpath():
 def test_header_declares_the_paper_calls():
     names = _declared()
     for n in ("qv_model_build", "mdp_value_iterate", "belief_predict", "belief_correct", "leaf_value",
-              "qv_tree_plan", "qv_tree_plan_batched", "qv_plan_create", "qv_plan_run", "qv_plan_read"):
+              "qv_tree_plan", "qv_tree_plan_batched", "qv_plan_create", "qv_plan_run", "qv_plan_read",
+              "qv_tree_backward", "mdp_value_iterate_checkpointed", "mdp_value_backward"):
         assert n in names
 
 
@@ -70,3 +71,15 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
     m.num_beacons = N.QV_MAX_BEACONS + 1
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+
+
+def test_adjoint_arguments_are_rejected_without_gpu(libpath):
+    from paper_1810_00204_gb300 import _native as N
+    L = N.lib()
+    assert L.qv_tree_backward_workspace_bytes(None, 0) == 0
+    assert L.qv_tree_backward(None, 0, 1.0, None, None, None, None, None, None, 0, None) == N.QV_ERR_INVALID
+    m = N.qv_model_t(4, 5, 8, 16, 1, 0, 0.1, 0.9, 0.95, None, 32, 3)
+    assert L.mdp_value_backward_workspace_bytes(ctypes.byref(m), 0) == 0
+    assert L.mdp_value_backward_workspace_bytes(ctypes.byref(m), 16) > 0
+    assert L.mdp_value_backward(ctypes.byref(m), 200, 16, None, None, None, None, None, 0, None) == N.QV_ERR_INVALID
+    assert L.mdp_value_iterate_checkpointed(ctypes.byref(m), 0, 16, 16, 16, 16, 16, 0, None) == N.QV_ERR_INVALID
