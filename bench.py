@@ -139,7 +139,55 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
                                          "workspace_GB": p4.workspace_bytes / 1e9}
         del p4
         torch.cuda.empty_cache()
+    # (4) the gradient of the root value on the 128x128 differentiation workload
+    out["gradient_diff_128"] = gradient_measurement(args, dev, K, peak)
     return out
+
+
+def gradient_measurement(args, dev, K, peak):
+    """Forward (checkpointed FP64 value iteration + one plan) and backward
+    (tree adjoint + value-iteration adjoint) of the root value on the
+    128x128, depth-3, K=8, 200-sweep workload, each part timed with CUDA
+    events; one full gradient = the four parts in sequence."""
+    import torch
+    from paper_1810_00204_gb300 import api, workloads as WL
+    w = WL.diff(args.seed)
+    m = api.Model(w, device=dev)
+    S, every = 200, 16
+    times = {"vi_forward": [], "plan_forward": [], "tree_backward": [], "vi_backward": []}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for it in range(K + 2):
+        torch.cuda.synchronize()
+        ev[0].record()
+        vi = api.mdp_value_iterate_checkpointed(m, S, every)
+        ev[1].record()
+        plan = api.Plan([m], [vi["Q"]], [m.b0()], depth=3, K=8, seed=w.seed, episode=w.episode)
+        plan.run()
+        ev[2].record()
+        tb = api.qv_tree_backward(plan, 0, dL=1.0)
+        ev[3].record()
+        api.mdp_value_backward(m, vi, tb["Qbar"], tb["dslip"], tb["dcost"])
+        ev[4].record()
+        torch.cuda.synchronize()
+        if it >= 2:
+            for i, k in enumerate(times):
+                times[k].append(ev[i].elapsed_time(ev[i + 1]))
+    res = plan.read()[0]
+    ms = {k: statistics.median(v) for k, v in times.items()}
+    total = sum(ms.values())
+    N = m.H * m.P
+    # value-iteration adjoint, bytes per sweep if every array went to DRAM once:
+    # recompute (V_k read, V_k+1 write, argmax write, cell words) and reverse
+    # step (lambda read/write, V_k, argmax, dcost read-modify-write, cell words)
+    vib = S * N * ((8 + 8 + 1 + 2) + (8 + 8 + 8 + 1 + 16 + 2))
+    return {"gradients_per_s": 1e3 / total, "ms_per_gradient": total, "ms": ms,
+            "nodes_per_level": res["nodes_per_level"], "sweeps": S, "checkpoint_every": every,
+            "dslip": float(tb["dslip"][0]), "dacc": float(tb["dacc"][0]),
+            "vi_backward_us_per_sweep": 1e3 * ms["vi_backward"] / S,
+            "vi_backward_GBps_if_dram": vib / (ms["vi_backward"] * 1e-3) / 1e9,
+            "vi_backward_frac_of_measured_hbm": vib / (ms["vi_backward"] * 1e-3) / 1e9 / peak,
+            "note": "128x128 state fits L2 (the value-iteration adjoint's working set is about 2.5 MB): "
+                    "bound by its 2 grid barriers per sweep, not by HBM"}
 
 
 def make_workload(name, seed):
@@ -486,6 +534,17 @@ def main():
         cpu = {"value": n / el, "unit": "plans/s", "cores": O.num_threads(), "kind": "oracle",
                "sample": f"{n} plans of this workload (same map, {len(eps)} start cells cycled), "
                          f"{el:.1f} s, FP64 C oracle with OpenMP over tree nodes"}
+        if extra is not None and "gradient_diff_128" in extra:
+            # the oracle's reverse mode on the same differentiation workload, one gradient
+            from paper_1810_00204_gb300 import workloads as WLd
+            wd = WLd.diff(args.seed)
+            t0 = time.perf_counter()
+            O.root_value_grad(wd, 200, depth=3, K=8)
+            el = time.perf_counter() - t0
+            extra["gradient_diff_128"]["cpu_baseline"] = {
+                "value": 1.0 / el, "unit": "gradients/s", "cores": O.num_threads(), "kind": "oracle",
+                "sample": "one FP64 reverse-mode gradient (200 VI sweeps, depth-3 K=8 tree, tree adjoint "
+                          "single-threaded)"}
 
     if rank == 0:
         line = {
