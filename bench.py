@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuner)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched (256 uneven maps) and 512x512 sub-measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
@@ -84,6 +85,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     peak, _ = measured_peak()
     # (1) the same R requests in one launch (E = R episodes on one map)
     b0s = [model.to_grid(e.b0) for e in eps]
+    best1, _ = api.autotune([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
+                            episode=eps[0].episode, reps=5)
     pb = api.Plan([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
                   episode=eps[0].episode)
     pb.capture_graph()
@@ -91,13 +94,22 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
         pb.run()
     ms = time_device(pb.run, K, flush, stream)
     out["same_requests_one_launch"] = {"plans_per_s": len(eps) * K / (ms / 1e3), "E": len(eps),
-                                       "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s}
+                                       "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s,
+                                       "tuning": pb.tuning}
     del pb
     # (2) 256 independent episodes on maps of uneven size, one launch per step
     ws = WL.batched(args.seed, E=256)
     ms_ = [api.Model(x, device=dev) for x in ws]
     Qs = [api.mdp_value_iterate(m, dtype="f32")["Q"] for m in ms_]
-    p3 = api.Plan(ms_, Qs, [m.b0() for m in ms_], depth=3, K=8, seed=args.seed, episode=0)
+    b3 = [m.b0() for m in ms_]
+    p3d = api.Plan(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0, band_cells=2048, items_per_cta=2)
+    p3d.capture_graph()
+    for _ in range(2):
+        p3d.run()
+    ms3d = time_device(p3d.run, K, flush, stream)
+    del p3d
+    api.autotune(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0, reps=3)
+    p3 = api.Plan(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0)
     p3.capture_graph()
     for _ in range(2):
         p3.run()
@@ -105,6 +117,7 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     ms3 = time_device(p3.run, K, flush, stream)
     nodes = [sum(r["nodes_per_level"][1:]) for r in res]
     out["batched_256_uneven"] = {"plans_per_s": 256 * K / (ms3 / 1e3), "ms_per_launch": ms3 / K,
+                                 "tuning": p3.tuning, "default_shape_plans_per_s": 256 * K / (ms3d / 1e3),
                                  "updates_per_s": sum(nodes) * K / (ms3 / 1e3),
                                  "cells_mean": float(sum(x.H * x.W for x in ws) / 256),
                                  "workspace_GB": p3.workspace_bytes / 1e9}
@@ -116,6 +129,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     Ql = api.mdp_value_iterate(ml, dtype="f32")["Q"]
     Ncell = ml.H * ml.P
     for mode_name, mode in (("fused", N.QV_LEAF_FUSED), ("materialise", N.QV_LEAF_MATERIALISE)):
+        api.autotune([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode, reps=3)
+        torch.cuda.empty_cache()
         p4 = api.Plan([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode)
         p4.capture_graph()
         for _ in range(2):
@@ -136,6 +151,7 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
         out[f"large_512_{mode_name}"] = {"plans_per_s": K / (ms4 / 1e3), "ms_per_plan": ms4 / K,
                                          "nodes_per_level": nodes,
                                          "updates_per_s": sum(nodes[1:]) * K / (ms4 / 1e3), "phases": phases,
+                                         "tuning": p4.tuning,
                                          "workspace_GB": p4.workspace_bytes / 1e9}
         del p4
         torch.cuda.empty_cache()
@@ -416,6 +432,15 @@ def main():
     Qd = vi["Q"]
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
     b0s = [model.to_grid(e.b0) for e in eps]
+    # launch-shape autotuner (offline, like the value iteration): the choice is
+    # cached in the library and taken by the plans created below
+    tune = None
+    if not args.no_tune:
+        best, table = api.autotune([model], [Qd], [b0s[0]], depth=w.depth, K=w.K, seed=w.seed,
+                                   episode=eps[0].episode, leaf_mode=leaf_mode, reps=5)
+        dflt = [t["ms"] for t in table if t["band_cells"] == 2048 and t["items_per_cta"] == 2]
+        tune = {"band_cells": best["band_cells"], "items_per_cta": best["items_per_cta"],
+                "tuned_ms": best["ms"], "default_ms": dflt[0] if dflt else None, "candidates": len(table)}
     plans = [api.Plan([model], [Qd], [b0s[i]], depth=w.depth, K=w.K, seed=w.seed, episode=e.episode,
                       leaf_mode=leaf_mode) for i, e in enumerate(eps)]
     use_graph = not args.no_graph
@@ -555,6 +580,7 @@ def main():
                        "leaf_mode": args.leaf_mode, "cuda_graph": use_graph,
                        "l2": "flushed before every step (256 MiB device write outside the timed events)",
                        "parallelism": "replicas" if world_size > 1 else "single GPU",
+                       "autotune": tune,
                        "nodes_per_level": nodes_per_plan[0]},
             "updates_per_s": updates_per_s,
             "roofline": roofline,

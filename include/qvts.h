@@ -94,6 +94,10 @@ typedef struct {
     const int32_t *d_replay;   /* nullable: observation samples to use instead of
                                   Philox draws, laid out like the samples array of
                                   qv_plan_level (per level, [node][action][K])         */
+    int32_t band_cells;        /* cells per work item (a band of whole rows), 0 = the
+                                  autotuner's choice for this shape, else 2048         */
+    int32_t items_per_cta;     /* work items aimed at per co-resident CTA in a phase,
+                                  0 = the autotuner's choice for this shape, else 2    */
 } qv_plan_params_t;
 
 typedef struct {
@@ -233,6 +237,37 @@ typedef struct {
 qv_status qv_plan_profile(qv_plan_t *plan, qv_launch_time_t *h_out, int32_t max_launches,
                           int32_t *n_out, qv_stream_t stream);
 void qv_plan_destroy(qv_plan_t *plan);
+
+/* ---------------------------------------------------------------- autotuner
+ * The plan kernel's two launch-shape knobs: the band of rows one work item
+ * covers (band_cells, the tile) and the work items a phase aims at per
+ * co-resident CTA (items_per_cta, nodes per CTA).  qv_plan_autotune times
+ * every candidate pair on the caller's inputs (each a full plan run,
+ * `reps` timed runs after two warm-up runs, CUDA events on `stream`), keeps
+ * the fastest in a process-wide cache under the inputs' shape class (E,
+ * depth, K, leaf and weight modes, largest B, and the power-of-two classes of
+ * the widest pitch and the mean cell count) and returns it.  Plans created
+ * later with band_cells = 0 / items_per_cta = 0 and the same shape class
+ * take the cached pair.  Candidates whose shared memory does not fit are
+ * skipped.  The workspace must hold qv_plan_autotune_workspace_bytes.
+ * Synchronises; not capturable.  Results of a tuned plan equal the default
+ * plan's up to FP32 summation order. */
+typedef struct {
+    int32_t band_cells;
+    int32_t items_per_cta;
+    float ms;                  /* mean time of one plan run                           */
+} qv_tune_t;
+size_t qv_plan_autotune_workspace_bytes(int32_t E, const qv_model_t *models,
+                                        const qv_plan_params_t *params);
+qv_status qv_plan_autotune(int32_t E, const qv_model_t *models, const float *const *d_Q,
+                           const float *const *d_b0, const qv_plan_params_t *params,
+                           void *d_ws, size_t ws_bytes, int32_t reps, qv_tune_t *h_best,
+                           qv_tune_t *h_all, int32_t max_all, int32_t *n_all,
+                           qv_stream_t stream);
+/* The knobs a plan was created with. */
+qv_status qv_plan_tuning(const qv_plan_t *plan, qv_tune_t *h_out);
+/* Forget every cached choice. */
+void qv_tune_clear(void);
 
 /* Device views of one level of episode e after a run (for inspection and
  * tests).  Level l nodes are ordered by (parent, action, z ascending).

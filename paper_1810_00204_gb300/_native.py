@@ -35,7 +35,12 @@ class qv_model_t(C.Structure):
 
 class qv_plan_params_t(C.Structure):
     _fields_ = [("depth", C.c_int32), ("K", C.c_int32), ("seed", C.c_uint64), ("episode", C.c_uint32),
-                ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p)]
+                ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p),
+                ("band_cells", C.c_int32), ("items_per_cta", C.c_int32)]
+
+
+class qv_tune_t(C.Structure):
+    _fields_ = [("band_cells", C.c_int32), ("items_per_cta", C.c_int32), ("ms", C.c_float)]
 
 
 class qv_plan_result_t(C.Structure):
@@ -82,6 +87,11 @@ SIGNATURES = {
     "qv_plan_destroy": (None, [_vp]),
     "qv_plan_profile": (C.c_int, [_vp, C.POINTER(qv_launch_time_t), _i32, C.POINTER(C.c_int32), _vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
+    "qv_plan_autotune_workspace_bytes": (_sz, [_i32, _M, _PP]),
+    "qv_plan_autotune": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, _i32, C.POINTER(qv_tune_t),
+                                   C.POINTER(qv_tune_t), _i32, C.POINTER(C.c_int32), _vp]),
+    "qv_plan_tuning": (C.c_int, [_vp, C.POINTER(qv_tune_t)]),
+    "qv_tune_clear": (None, []),
     "qv_tree_backward_workspace_bytes": (_sz, [_vp, _i32]),
     "qv_tree_backward": (C.c_int, [_vp, _i32, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qv_tree_plan": (C.c_int, [_M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),

@@ -18,7 +18,7 @@ from ._native import check, lib
 
 __all__ = ["Model", "Plan", "qv_model_build", "mdp_value_iterate", "mdp_value_iterate_checkpointed",
            "mdp_value_backward", "belief_predict", "belief_correct", "leaf_value", "qv_tree_plan",
-           "qv_tree_plan_batched", "qv_tree_backward", "pitch_of"]
+           "qv_tree_plan_batched", "qv_tree_backward", "autotune", "tune_clear", "pitch_of"]
 
 
 def pitch_of(W: int) -> int:
@@ -178,9 +178,9 @@ def leaf_value(model: Model, Q: torch.Tensor, b: torch.Tensor, stream=None):
     return out
 
 
-def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay):
+def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells=0, items_per_cta=0):
     return N.qv_plan_params_t(int(depth), int(K), int(seed), int(episode), int(weight_mode), int(leaf_mode),
-                              None if replay is None else replay.data_ptr())
+                              None if replay is None else replay.data_ptr(), int(band_cells), int(items_per_cta))
 
 
 def _result_dict(r: N.qv_plan_result_t, depth: int):
@@ -199,14 +199,14 @@ class Plan:
 
     def __init__(self, models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor],
                  depth=2, K=4, seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED,
-                 replay: Optional[torch.Tensor] = None, stream=None):
+                 replay: Optional[torch.Tensor] = None, stream=None, band_cells=0, items_per_cta=0):
         self.models = list(models)
         self.E = len(self.models)
         self.depth, self.K = int(depth), int(K)
         self.Qs = [q.contiguous() for q in Qs]
         self.b0s = [b.contiguous() for b in b0s]
         self.replay = replay
-        self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay)
+        self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells, items_per_cta)
         self.mstructs = (N.qv_model_t * self.E)(*[m.struct for m in self.models])
         self.qptrs = (C.c_void_p * self.E)(*[q.data_ptr() for q in self.Qs])
         self.bptrs = (C.c_void_p * self.E)(*[b.data_ptr() for b in self.b0s])
@@ -221,6 +221,13 @@ class Plan:
     @property
     def workspace_bytes(self):
         return self.ws.numel()
+
+    @property
+    def tuning(self) -> dict:
+        """The launch-shape knobs this plan was created with."""
+        t = N.qv_tune_t()
+        check(lib().qv_plan_tuning(self.handle, C.byref(t)), "qv_plan_tuning")
+        return dict(band_cells=int(t.band_cells), items_per_cta=int(t.items_per_cta))
 
     def backward_workspace(self, nbytes: int) -> torch.Tensor:
         """Device scratch for qv_tree_backward, kept with the plan."""
@@ -294,6 +301,33 @@ class Plan:
         if h is not None and h.value:
             lib().qv_plan_destroy(h)
             self.handle = C.c_void_p()
+
+
+def autotune(models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor], depth=2, K=4,
+             seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED, reps=5, stream=None):
+    """qv_plan_autotune: time every (band_cells, items_per_cta) candidate on
+    these inputs; the best is cached in the library for plans of the same
+    shape class created with the knobs left at 0.  Returns (best, all)."""
+    E = len(models)
+    ms = (N.qv_model_t * E)(*[m.struct for m in models])
+    qp = (C.c_void_p * E)(*[q.data_ptr() for q in Qs])
+    bp = (C.c_void_p * E)(*[b.data_ptr() for b in b0s])
+    params = _params(depth, K, seed, episode, weight_mode, leaf_mode, None)
+    nbytes = lib().qv_plan_autotune_workspace_bytes(E, ms, C.byref(params))
+    if nbytes == 0:
+        raise N.QVError(N.QV_ERR_INVALID, "qv_plan_autotune_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=models[0].device)
+    best = N.qv_tune_t()
+    allv = (N.qv_tune_t * 64)()
+    n = C.c_int32(0)
+    check(lib().qv_plan_autotune(E, ms, qp, bp, C.byref(params), _ptr(ws), nbytes, int(reps), C.byref(best), allv,
+                                 64, C.byref(n), _stream(stream)), "qv_plan_autotune")
+    conv = lambda t: dict(band_cells=int(t.band_cells), items_per_cta=int(t.items_per_cta), ms=float(t.ms))  # noqa: E731
+    return conv(best), [conv(allv[i]) for i in range(n.value)]
+
+
+def tune_clear():
+    lib().qv_tune_clear()
 
 
 def qv_tree_backward(plan: Plan, e: int = 0, dL: float = 1.0, Qbar=None, dslip=None, dacc=None, dcost=None,

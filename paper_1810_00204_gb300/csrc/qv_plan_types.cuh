@@ -14,7 +14,6 @@ constexpr int kMaxD = QV_MAX_DEPTH;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kLeafGroup = 4;
-constexpr int kBandCells = 2048;
 constexpr float kBoundaryEps = 1e-6f;
 constexpr int kStamps = 4 * kMaxD + 8;
 

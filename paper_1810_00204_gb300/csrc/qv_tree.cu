@@ -1,8 +1,12 @@
 // qv_tree.cu -- host side of the QV-tree search: workspace layout, plan
 // creation, launch (eager or as a CUDA graph), profiling and result read-back.
 // The device side (the persistent plan kernel) is in qv_tree_device.cuh.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "qv_tree_device.cuh"
@@ -19,6 +23,7 @@ struct Layout {
         off_status, off_boundary, off_bar, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0;
+    int band_cells = 0, items_per_cta = 0;  // the launch-shape knobs in effect
     int sb_floats = 0, sp_floats = 0, q_floats = 0;
     size_t smem = 0;
     std::vector<qv::EpDev> eps;
@@ -28,6 +33,45 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Upper bound on co-resident k_plan CTAs (8 per SM on 152 SMs).
 constexpr int kMaxGridSizing = 8 * 152;
+
+// ---- autotuner cache: shape class -> (band_cells, items_per_cta)
+constexpr int kDefaultBandCells = 2048;
+constexpr int kDefaultItemsPerCta = 2;
+constexpr int kMaxItemsPerCta = 8;
+
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, qv_tune_t> g_tune;
+
+int log2_class(double v) { return v <= 1.0 ? 0 : static_cast<int>(std::ceil(std::log2(v))); }
+
+TuneKey tune_key(int E, const qv_model_t *models, const qv_plan_params_t *p) {
+    int Bmax = 1, Pmax = 1;
+    double cells = 0.0;
+    for (int e = 0; e < E; ++e) {
+        Bmax = std::max(Bmax, models[e].num_beacons);
+        Pmax = std::max(Pmax, models[e].pitch);
+        cells += static_cast<double>(models[e].H) * models[e].pitch;
+    }
+    return TuneKey(E, p->depth, p->K, p->leaf_mode, p->weight_mode, Bmax, log2_class(Pmax), log2_class(cells / E));
+}
+
+// The knobs a plan uses: explicit values, else the cached choice for its
+// shape class, else the defaults.
+void resolve_tuning(int E, const qv_model_t *models, const qv_plan_params_t *p, int &bc, int &ipc) {
+    bc = p->band_cells;
+    ipc = p->items_per_cta;
+    if (bc <= 0 || ipc <= 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(tune_key(E, models, p));
+        if (it != g_tune.end()) {
+            if (bc <= 0) bc = it->second.band_cells;
+            if (ipc <= 0) ipc = it->second.items_per_cta;
+        }
+    }
+    if (bc <= 0) bc = kDefaultBandCells;
+    if (ipc <= 0) ipc = kDefaultItemsPerCta;
+}
 
 qv_status validate(int E, const qv_model_t *models, const qv_plan_params_t *p) {
     if (E < 1) return qv_set_error(QV_ERR_INVALID, "plan: E=%d", E);
@@ -39,6 +83,10 @@ qv_status validate(int E, const qv_model_t *models, const qv_plan_params_t *p) {
     if (p->leaf_mode != QV_LEAF_FUSED && p->leaf_mode != QV_LEAF_MATERIALISE)
         return qv_set_error(QV_ERR_INVALID, "plan: leaf_mode %d", p->leaf_mode);
     if (p->d_replay && E != 1) return qv_set_error(QV_ERR_INVALID, "plan: replay needs E = 1");
+    if (p->band_cells < 0 || p->band_cells > (1 << 16))
+        return qv_set_error(QV_ERR_INVALID, "plan: band_cells %d", p->band_cells);
+    if (p->items_per_cta < 0 || p->items_per_cta > kMaxItemsPerCta)
+        return qv_set_error(QV_ERR_INVALID, "plan: items_per_cta %d", p->items_per_cta);
     for (int e = 0; e < E; ++e) {
         const qv_model_t &m = models[e];
         if (!m.d_cell) return qv_set_error(QV_ERR_INVALID, "plan: episode %d has no cell words", e);
@@ -82,6 +130,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     if (st != QV_OK) return st;
     const int D = p->depth, K = p->K;
     L.eps.assign(E, qv::EpDev{});
+    resolve_tuning(E, models, p, L.band_cells, L.items_per_cta);
     L.Bmax = 1;
     for (int e = 0; e < E; ++e) L.Bmax = std::max(L.Bmax, models[e].num_beacons);
     long long NB[QV_MAX_DEPTH + 1] = {};
@@ -103,7 +152,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
         ep.beacons = m.d_beacons;
         ep.range = m.sense_range;
         ep.episode = p->episode + static_cast<uint32_t>(e);
-        ep.band_rows = std::max(1, std::min(m.H, qv::kBandCells / m.pitch));
+        ep.band_rows = std::max(1, std::min(m.H, L.band_cells / m.pitch));
         ep.bands = (m.H + ep.band_rows - 1) / ep.band_rows;
         const long long br = std::min<long long>(K, m.num_beacons + 1) * 5;
         long long c = 1;
@@ -124,8 +173,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     // work items per phase aimed at: two per co-resident CTA.  Band splits
     // keep every phase below 2 * target items, and the partial records are
     // sized for the largest possible grid so that sizing needs no device.
-    L.target = 2 * std::max(L.grid, 1);
-    L.n_part = 2 * 2 * kMaxGridSizing;
+    L.target = L.items_per_cta * std::max(L.grid, 1);
+    L.n_part = 2 * L.items_per_cta * kMaxGridSizing;
     long long gbase = 0, ibase = 0;
     long long run_g[QV_MAX_DEPTH + 1], run_i[QV_MAX_DEPTH + 1];
     for (int l = 0; l <= D; ++l) {
@@ -282,6 +331,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     pl->bytes = L.total;
     pl->grid = L.grid;
     pl->smem = L.smem;
+    pl->params.band_cells = L.band_cells;
+    pl->params.items_per_cta = L.items_per_cta;
     pl->dev.sb_floats = L.sb_floats;
     pl->dev.sp_floats = L.sp_floats;
     pl->dev.q_floats = L.q_floats;
@@ -558,6 +609,101 @@ extern "C" qv_status qv_tree_plan(const qv_model_t *model, const float *d_Q, con
                                   const qv_plan_params_t *params, void *d_ws, size_t ws_bytes,
                                   qv_plan_result_t *h_result, qv_stream_t stream) {
     return qv_tree_plan_batched(1, model, &d_Q, &d_b0, params, d_ws, ws_bytes, h_result, stream);
+}
+
+extern "C" qv_status qv_plan_tuning(const qv_plan_t *pl, qv_tune_t *out) {
+    if (!pl || !out) return qv_set_error(QV_ERR_INVALID, "qv_plan_tuning: null pointer");
+    out->band_cells = pl->params.band_cells;
+    out->items_per_cta = pl->params.items_per_cta;
+    out->ms = 0.0f;
+    return QV_OK;
+}
+
+extern "C" void qv_tune_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+namespace {
+const int kTuneBand[] = {1024, 2048, 4096, 8192};
+const int kTuneItems[] = {1, 2, 4, 8};
+}  // namespace
+
+extern "C" size_t qv_plan_autotune_workspace_bytes(int32_t E, const qv_model_t *models,
+                                                   const qv_plan_params_t *params) {
+    if (!params) return 0;
+    size_t best = 0;
+    for (int bc : kTuneBand)
+        for (int ipc : kTuneItems) {
+            qv_plan_params_t p = *params;
+            p.band_cells = bc;
+            p.items_per_cta = ipc;
+            Layout L;
+            if (make_layout(E, models, &p, L, false) == QV_OK) best = std::max(best, L.total);
+        }
+    return best;
+}
+
+extern "C" qv_status qv_plan_autotune(int32_t E, const qv_model_t *models, const float *const *d_Q,
+                                      const float *const *d_b0, const qv_plan_params_t *params, void *d_ws,
+                                      size_t ws_bytes, int32_t reps, qv_tune_t *best, qv_tune_t *all, int32_t max_all,
+                                      int32_t *n_all, qv_stream_t stream) {
+    if (!params || !best) return qv_set_error(QV_ERR_INVALID, "qv_plan_autotune: null pointer");
+    if (reps < 1) return qv_set_error(QV_ERR_INVALID, "qv_plan_autotune: reps %d", reps);
+    qv_status st = validate(E, models, params);
+    if (st != QV_OK) return st;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (qv_check_cuda(cudaEventCreate(&e0), "event") != QV_OK) return QV_ERR_CUDA;
+    if (qv_check_cuda(cudaEventCreate(&e1), "event") != QV_OK) {
+        cudaEventDestroy(e0);
+        return QV_ERR_CUDA;
+    }
+    qv_tune_t win{0, 0, 0.0f};
+    int n = 0;
+    st = QV_OK;
+    for (int bc : kTuneBand) {
+        for (int ipc : kTuneItems) {
+            qv_plan_params_t p = *params;
+            p.band_cells = bc;
+            p.items_per_cta = ipc;
+            Layout L;
+            if (make_layout(E, models, &p, L, true) != QV_OK || L.total > ws_bytes) continue;  // does not fit
+            qv_plan_t *pl = nullptr;
+            st = qv_plan_create(E, models, d_Q, d_b0, &p, d_ws, ws_bytes, &pl, stream);
+            if (st != QV_OK) break;
+            for (int w = 0; w < 2 && st == QV_OK; ++w) st = launch_plan(pl, cs);
+            if (st == QV_OK) st = qv_check_cuda(cudaEventRecord(e0, cs), "event");
+            for (int r = 0; r < reps && st == QV_OK; ++r) st = launch_plan(pl, cs);
+            if (st == QV_OK) st = qv_check_cuda(cudaEventRecord(e1, cs), "event");
+            if (st == QV_OK) st = qv_check_cuda(cudaEventSynchronize(e1), "autotune");
+            unsigned status = 0;
+            if (st == QV_OK)
+                st = qv_check_cuda(cudaMemcpy(&status, pl->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost),
+                                   "status");
+            qv_plan_destroy(pl);
+            if (st != QV_OK) break;
+            if (status) continue;  // a candidate that ran out of capacity or timed out is not a choice
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const qv_tune_t t{bc, ipc, ms / reps};
+            if (all && n < max_all) all[n] = t;
+            ++n;
+            if (win.band_cells == 0 || t.ms < win.ms) win = t;
+        }
+        if (st != QV_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (n_all) *n_all = std::min(n, std::max(max_all, 0));
+    if (st != QV_OK) return st;
+    if (win.band_cells == 0) return qv_set_error(QV_ERR_INVALID, "qv_plan_autotune: no candidate fits");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(E, models, params)] = win;
+    }
+    *best = win;
+    return QV_OK;
 }
 
 #ifdef QV_TRACE

@@ -69,6 +69,13 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
     p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 9)          # items_per_cta above 8
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 4096, 4)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
+    assert L.qv_plan_autotune_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) >= \
+        L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p))
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
     m.num_beacons = N.QV_MAX_BEACONS + 1
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
 
