@@ -134,9 +134,7 @@ __device__ __forceinline__ float predicted(const float *b, int y, int P, unsigne
     nb[kDirE] = (inf & 2u) ? __ldg(b + y + 1) : 0.0f;
     nb[kDirS] = (inf & 4u) ? __ldg(b + y + P) : 0.0f;
     nb[kDirW] = (inf & 8u) ? __ldg(b + y - 1) : 0.0f;
-    float out[5];
-    predict_cell(nb, __ldg(b + y), cw, is_goal, slip, lut, out);
-    return out[a];
+    return predict_one(nb, __ldg(b + y), cw, is_goal, slip, lut, a);
 }
 
 // ---------------------------------------------------------------- tree adjoint kernels

@@ -86,6 +86,24 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+// Reduce-scatter over a warp: on entry every lane holds 32 values v[0..31];
+// on exit v[0] of lane i is the sum over the 32 lanes of their v[i].  Each
+// halving step swaps half of the live values with the partner lane, so the
+// whole reduction takes 31 shuffles instead of 32 separate 5-shuffle sums.
+__device__ __forceinline__ void warp_reduce_scatter32(float v[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
@@ -163,6 +181,22 @@ __device__ __forceinline__ void predict_cell(const float nb[4], float self, unsi
         for (int a = 0; a < 4; ++a) out[a] = fmaf(self_lut[a * 16 + blk], s, out[a]);
     }
     out[4] = s;
+}
+
+// Predicted mass at one cell for one action a (uniform across the warp):
+// the same arithmetic as predict_cell's out[a], without the other four.
+__device__ __forceinline__ float predict_one(const float nb[4], float self, unsigned cw, bool is_goal, float slip,
+                                             const float *self_lut, int a) {
+    const float s = QV_CELL_FREE(cw) ? self : 0.0f;
+    if (a == 4) return s;
+    const float fwd = 1.0f - 2.0f * slip;
+    // intended move from the neighbour opposite a's step, slips from the two
+    // perpendicular ones (in predict_cell's order of summation)
+    const float n_in = a == 0 ? nb[kDirS] : a == 1 ? nb[kDirW] : a == 2 ? nb[kDirN] : nb[kDirE];
+    const float n_p1 = (a & 1) ? nb[kDirN] : nb[kDirE];
+    const float n_p2 = (a & 1) ? nb[kDirS] : nb[kDirW];
+    const float v = fmaf(fwd, n_in, slip * (n_p1 + n_p2));
+    return is_goal ? v + s : fmaf(self_lut[a * 16 + QV_CELL_BLOCKED(cw)], s, v);
 }
 
 // Stage reward of arriving in a cell: +100 at the goal, -1 - c(y) otherwise.

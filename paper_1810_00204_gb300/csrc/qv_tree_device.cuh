@@ -479,36 +479,57 @@ __device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e
 
 // The next level's work lists: band split per node from the actual level
 // size (about `target` items in all), then the per-episode prefix sums.
-__device__ void level_prefix(const PlanDev &pl, int l1) {
-    if (threadIdx.x != 0) return;
+__device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
+    // every thread of the CTA: one episode per thread per pass, block-wide
+    // sums and exclusive scans instead of a serial loop over the episodes
     const int E = pl.E;
-    long long T = 0;
-    for (int e = 0; e < E; ++e) T += __ldcg(pl.count + l1 * E + e);
-    const long long want = T > 0 ? (pl.target + T - 1) / T : 1;
+    int T = 0, G = 0;
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        const int c = __ldcg(pl.count + l1 * E + e);
+        T += c;
+        G += (c + kLeafGroup - 1) / kLeafGroup;
+    }
+    int Tt, Gt;
+    block_exclusive_scan(T, S.scan, Tt);
+    block_exclusive_scan(G, S.scan, Gt);
+    const long long want = Tt > 0 ? (static_cast<long long>(pl.target) + Tt - 1) / Tt : 1;
     int C = 1;  // leaf chunks per group of leaves
     if (l1 == pl.depth) {
-        long long G = 0;
-        for (int e = 0; e < E; ++e) G += (__ldcg(pl.count + l1 * E + e) + kLeafGroup - 1) / kLeafGroup;
-        C = static_cast<int>(min(max(G > 0 ? (pl.target + G - 1) / G : 1LL, 1LL), 64LL));
-        *pl.leaf_split = C;
+        C = static_cast<int>(min(max(Gt > 0 ? (static_cast<long long>(pl.target) + Gt - 1) / Gt : 1LL, 1LL), 64LL));
+        if (threadIdx.x == 0) *pl.leaf_split = C;
     }
     int ws = 0, wu = 0, wl = 0;
-    for (int e = 0; e < E; ++e) {
-        const int c = __ldcg(pl.count + l1 * E + e);
-        const int bands = __ldg(&pl.eps[e].bands);
-        const int it = static_cast<int>(min(max(want, 1LL), static_cast<long long>(bands)));
-        pl.items[l1 * E + e] = it;
-        pl.uitems[l1 * E + e] = it;
-        pl.wb_stats[l1 * (E + 1) + e] = ws;
-        pl.wb_upd[l1 * (E + 1) + e] = wu;
-        if (l1 == pl.depth) pl.wb_leaf[e] = wl;
-        if (l1 < pl.depth) ws += c * it;
-        wu += c * it;
-        wl += ((c + kLeafGroup - 1) / kLeafGroup) * C;
+    for (int base = 0; base < E; base += blockDim.x) {
+        const int e = base + threadIdx.x;
+        int vs = 0, vu = 0, vl = 0, it = 0;
+        if (e < E) {
+            const int c = __ldcg(pl.count + l1 * E + e);
+            const int bands = __ldg(&pl.eps[e].bands);
+            it = static_cast<int>(min(max(want, 1LL), static_cast<long long>(bands)));
+            vs = l1 < pl.depth ? c * it : 0;
+            vu = c * it;
+            vl = ((c + kLeafGroup - 1) / kLeafGroup) * C;
+        }
+        int ts, tu, tl;
+        const int xs = block_exclusive_scan(vs, S.scan, ts);
+        const int xu = block_exclusive_scan(vu, S.scan, tu);
+        const int xl = block_exclusive_scan(vl, S.scan, tl);
+        if (e < E) {
+            pl.items[l1 * E + e] = it;
+            pl.uitems[l1 * E + e] = it;
+            pl.wb_stats[l1 * (E + 1) + e] = ws + xs;
+            pl.wb_upd[l1 * (E + 1) + e] = wu + xu;
+            if (l1 == pl.depth) pl.wb_leaf[e] = wl + xl;
+        }
+        ws += ts;
+        wu += tu;
+        wl += tl;
     }
-    pl.wb_stats[l1 * (E + 1) + E] = ws;
-    pl.wb_upd[l1 * (E + 1) + E] = wu;
-    if (l1 == pl.depth) pl.wb_leaf[E] = wl;
+    if (threadIdx.x == 0) {
+        pl.wb_stats[l1 * (E + 1) + E] = ws;
+        pl.wb_upd[l1 * (E + 1) + E] = wu;
+        if (l1 == pl.depth) pl.wb_leaf[E] = wl;
+    }
     __threadfence();
 }
 
@@ -535,7 +556,7 @@ __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem
     __syncthreads();
     if (!S.flags[2]) return;
     __threadfence();
-    level_prefix(pl, l + 1);
+    level_prefix(pl, l + 1, S);
     __syncthreads();
 }
 
@@ -557,12 +578,9 @@ __device__ __forceinline__ void build_band(const EpReg &ep, const float *sp, con
             float v[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float nb[4], out[5];
+                float nb[4];
                 inflow_nb(n, j, nb);
-                predict_cell(nb, n.m[j + 1], n.cw[j], (y + j) == ep.goal, ep.slip, lut, out);
-                float pa = out[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) pa = (a == q) ? out[q] : pa;
+                const float pa = predict_one(nb, n.m[j + 1], n.cw[j], (y + j) == ep.goal, ep.slip, lut, a);
                 v[j] = pa * (static_cast<int>(QV_CELL_LABEL(n.cw[j])) == z ? sa : se);
             }
             o = make_float4(v[0], v[1], v[2], v[3]);
@@ -638,16 +656,23 @@ __device__ __forceinline__ void label_pass(const EpReg &ep, const float *sb, con
                     for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
             }
         }
-#pragma unroll
-        for (int a = 0; a < 5; ++a) {
-            const float t = warp_sum(la[a]);
-            if (lane == 0) S.hist[a * Bm + k] += t;
-        }
         if constexpr (FUSED) {
+            // lane i ends with the warp total of value i: 0..4 the label
+            // masses, 5..29 the Q-weighted ones
+            float v[32];
 #pragma unroll
-            for (int i = 0; i < 25; ++i) {
-                const float t = warp_sum(lq[i]);
-                if (lane == 0) S.histq[((i / 5) * Bm + k) * 5 + i % 5] += t;
+            for (int a = 0; a < 5; ++a) v[a] = la[a];
+#pragma unroll
+            for (int i = 0; i < 25; ++i) v[5 + i] = lq[i];
+            v[30] = v[31] = 0.0f;
+            warp_reduce_scatter32(v);
+            if (lane < 5) S.hist[lane * Bm + k] += v[0];
+            else if (lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] += v[0];
+        } else {
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                const float t = warp_sum(la[a]);
+                if (lane == 0) S.hist[a * Bm + k] += t;
             }
         }
     }
@@ -724,6 +749,14 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
         const float *cost = er.cost;
         const int grow = goal / P;
         QV_TRACE_MARK(tr, 3);
+        // null-label mass, rewards and (fused) Q-weighted null mass in
+        // registers over every band of the item; labelled cells only add
+        // their reward here
+        float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
         for (int band = band0; band < band1; ++band) {
             const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows);
             const int qstride = (r1 - r0) * P;
@@ -738,13 +771,6 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
             }
             if (band == band0) QV_TRACE_MARK(tr, 11);
             if (grow >= r0 && grow < r1) bgoal = S.sb[(grow - r0 + 1) * P + goal % P];
-            // null-label mass, rewards and (fused) Q-weighted null mass in
-            // registers; labelled cells only add their reward here
-            float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
-#pragma unroll
-            for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
             const int ng = (r1 - r0) * P4;
             for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
                 const int rr = gi / P4, col = (gi - rr * P4) << 2;
@@ -789,24 +815,6 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
                 QV_TRACE_MARK(tr, 12);
             }
 #endif
-            // fold this band's register sums into the per-warp totals
-            {
-                float vals[NV];
-#pragma unroll
-                for (int a = 0; a < 5; ++a) {
-                    vals[a] = acc_null[a];
-                    vals[5 + a] = acc_r[a];
-                }
-                if constexpr (FUSED) {
-#pragma unroll
-                    for (int i = 0; i < 25; ++i) vals[10 + i] = acc_q[i];
-                }
-#pragma unroll
-                for (int i = 0; i < NV; ++i) {
-                    const float v = warp_sum(vals[i]);
-                    if (lane == 0) S.red[wid * 36 + i] += v;
-                }
-            }
 #ifdef QV_TRACE
             if (band == band0) {
                 __syncthreads();
@@ -820,6 +828,38 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
                 QV_TRACE_MARK(tr, 14);
             }
 #endif
+        }
+        // fold the item's register sums into the per-warp totals
+        if constexpr (FUSED) {
+            // values 0..31 by a reduce-scatter (lane i gets value i), 32..34
+            // by plain warp sums
+            float v[32];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                v[a] = acc_null[a];
+                v[5 + a] = acc_r[a];
+            }
+#pragma unroll
+            for (int i = 0; i < 22; ++i) v[10 + i] = acc_q[i];
+            warp_reduce_scatter32(v);
+            S.red[wid * 36 + lane] += v[0];
+#pragma unroll
+            for (int i = 22; i < 25; ++i) {
+                const float t = warp_sum(acc_q[i]);
+                if (lane == 0) S.red[wid * 36 + 10 + i] += t;
+            }
+        } else {
+            float vals[NV];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                vals[a] = acc_null[a];
+                vals[5 + a] = acc_r[a];
+            }
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                const float v = warp_sum(vals[i]);
+                if (lane == 0) S.red[wid * 36 + i] += v;
+            }
         }
         QV_TRACE_MARK(tr, 4);
         __syncthreads();
@@ -1020,13 +1060,18 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
         }
         const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
         __syncthreads();
+        {
+            static_assert(kLeafGroup * 5 <= 32, "one reduce-scatter covers a leaf group");
+            float v[32];
 #pragma unroll
-        for (int i = 0; i < kLeafGroup; ++i)
+            for (int i = 0; i < kLeafGroup; ++i)
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                const float v = warp_sum(acc[i][a]);
-                if (lane == 0) s_red[wid][i * 5 + a] = v;
-            }
+                for (int a = 0; a < 5; ++a) v[i * 5 + a] = acc[i][a];
+#pragma unroll
+            for (int i = kLeafGroup * 5; i < 32; ++i) v[i] = 0.0f;
+            warp_reduce_scatter32(v);
+            if (lane < kLeafGroup * 5) s_red[wid][lane] = v[0];
+        }
         __syncthreads();
         if (threadIdx.x < kLeafGroup * 5) {
             float t = 0.0f;
