@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuner)")
+    ap.add_argument("--gradient-only", action="store_true",
+                    help="only time the gradient of the root value on the differentiation workload")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched (256 uneven maps) and 512x512 sub-measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
@@ -417,6 +419,13 @@ def main():
     replicas.barrier(dev)
     N.lib()
     stream = torch.cuda.current_stream()
+    if args.gradient_only:
+        # the differentiation workload alone (forward + adjoint), for profiling
+        if rank == 0:
+            peak, _ = measured_peak()
+            print(json.dumps({"gradient_diff_128": gradient_measurement(args, dev, max(3, args.extra_steps), peak)}),
+                  flush=True)
+        return
 
     w, desc = make_workload(args.workload, args.seed)
     R = args.plans_per_step

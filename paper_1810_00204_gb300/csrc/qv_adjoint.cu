@@ -403,6 +403,7 @@ struct VIBack {
     double *dslip;        // scalar
     double *red;          // [gridDim.x]
     VIWork *work;
+    unsigned *done;       // [gridDim.x] steps completed per CTA
 };
 
 __device__ __forceinline__ double self_weight_d(int a, unsigned blk, double slip) {
@@ -433,26 +434,33 @@ __device__ __forceinline__ void arrive4(const VIBack &a, int x, unsigned cw, con
     wn[kDirW] = (blk & 8u) ? wx : arrive_value(a, x - 1, row, col - 1);
 }
 
+// Each CTA owns a band of whole rows; every step reads one row into the
+// neighbouring bands, so consecutive steps are ordered by the neighbours'
+// progress flags only (publish_step / wait_neighbours).
 __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
     const unsigned nblocks = gridDim.x;
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows_per_cta = (a.H + nblocks - 1) / nblocks;
+    const int r_begin = min(a.H, static_cast<int>(blockIdx.x) * rows_per_cta);
+    const int r_end = min(a.H, r_begin + rows_per_cta);
+    const int y0 = r_begin * a.P, y1 = r_end * a.P;
     const int N = a.N, c = a.every, S = a.sweeps;
     const double slip = a.slip, fwd = 1.0 - 2.0 * slip;
     const int J = (S + c - 1) / c;
     double eps = 0.0;
     double *lam = a.lam0, *lam_next = a.lam1;
+    unsigned step = 0;
+    // V_{k0 + i} of the current segment: the checkpoint for i = 0
+    auto slot = [&](int j, int i) -> const double * {
+        return i == 0 ? a.ckpt + static_cast<size_t>(j) * N : a.segV + static_cast<size_t>(i) * N;
+    };
     for (int j = J - 1; j >= 0; --j) {
         const int k0 = j * c, Lseg = min(S, k0 + c) - k0;
-        const double *src = a.ckpt + static_cast<size_t>(j) * N;
-        for (int y = t0; y < N; y += stride) a.segV[y] = src[y];
-        if (!grid_barrier(a.work, nblocks)) return;
         // recompute sweeps k0 .. k0 + Lseg - 1 with the forward's arithmetic
         for (int i = 0; i < Lseg; ++i) {
-            const double *Vk = a.segV + static_cast<size_t>(i) * N;
+            const double *Vk = slot(j, i);
             double *Vn = a.segV + static_cast<size_t>(i + 1) * N;
             unsigned char *Ak = a.segA + static_cast<size_t>(i) * N;
-            for (int y = t0; y < N; y += stride) {
+            for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
                 const unsigned cw = __ldg(a.cell + y);
                 double v = 0.0;
                 int arg = 0;
@@ -470,12 +478,13 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                 Vn[y] = v;
                 Ak[y] = static_cast<unsigned char>(arg);
             }
-            if (!grid_barrier(a.work, nblocks)) return;
+            publish_step(a.done, ++step);
+            if (!wait_neighbours(a.done, step, &a.work->status)) return;
         }
         if (j == J - 1) {
             // Q = sum_y T (r + gamma V_S): lambda_S = gamma T^T Qbar
-            const double *VS = a.segV + static_cast<size_t>(Lseg) * N;
-            for (int y = t0; y < N; y += stride) {
+            const double *VS = slot(j, Lseg);
+            for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
                 const unsigned cw = __ldg(a.cell + y);
                 double rho = 0.0;
                 if (QV_CELL_FREE(cw)) {
@@ -484,7 +493,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                         double wn[4], wx;
                         arrive4(a, y, cw, VS, wn, wx);
                         for (int q = 0; q < 5; ++q) {
-                            const double qb = a.Qbar[static_cast<size_t>(q) * N + y];
+                            const double qb = __ldg(a.Qbar + static_cast<size_t>(q) * N + y);
                             rho += qb * (q == 4 ? 1.0 : self_weight_d(q, blk, slip));
                             if (q < 4) eps += qb * (-2.0 * wn[q] + wn[(q + 1) & 3] + wn[(q + 3) & 3]);
                         }
@@ -493,27 +502,28 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                     for (int D = 0; D < 4; ++D) {
                         if (!((inf >> D) & 1u)) continue;
                         const int x = D == kDirN ? y - a.P : D == kDirE ? y + 1 : D == kDirS ? y + a.P : y - 1;
-                        rho += fwd * a.Qbar[static_cast<size_t>((D + 2) & 3) * N + x] +
-                               slip * (a.Qbar[static_cast<size_t>((D + 1) & 3) * N + x] +
-                                       a.Qbar[static_cast<size_t>((D + 3) & 3) * N + x]);
+                        rho += fwd * __ldg(a.Qbar + static_cast<size_t>((D + 2) & 3) * N + x) +
+                               slip * (__ldg(a.Qbar + static_cast<size_t>((D + 1) & 3) * N + x) +
+                                       __ldg(a.Qbar + static_cast<size_t>((D + 3) & 3) * N + x));
                     }
                     if (a.dcost && y != a.goal) a.dcost[y] -= rho;
                 }
                 lam[y] = a.gamma * rho;
             }
-            if (!grid_barrier(a.work, nblocks)) return;
+            publish_step(a.done, ++step);
+            if (!wait_neighbours(a.done, step, &a.work->status)) return;
         }
         // sweeps k = k0 + Lseg - 1 .. k0: lam holds lambda_{k+1}
         for (int i = Lseg - 1; i >= 0; --i) {
-            const double *Vk = a.segV + static_cast<size_t>(i) * N;
+            const double *Vk = slot(j, i);
             const unsigned char *Ak = a.segA + static_cast<size_t>(i) * N;
-            for (int y = t0; y < N; y += stride) {
+            for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
                 const unsigned cw = __ldg(a.cell + y);
                 double rho = 0.0;
                 if (QV_CELL_FREE(cw)) {
                     if (y != a.goal) {
-                        const int act = Ak[y];
-                        const double ly = lam[y];
+                        const int act = __ldcg(Ak + y);
+                        const double ly = __ldcg(lam + y);
                         rho += ly * (act == 4 ? 1.0 : self_weight_d(act, QV_CELL_BLOCKED(cw), slip));
                         if (act < 4 && ly != 0.0) {
                             double wn[4], wx;
@@ -525,13 +535,14 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                     for (int D = 0; D < 4; ++D) {
                         if (!((inf >> D) & 1u)) continue;
                         const int x = D == kDirN ? y - a.P : D == kDirE ? y + 1 : D == kDirS ? y + a.P : y - 1;
-                        rho += lam[x] * inflow_weight(Ak[x], D, fwd, slip);
+                        rho += __ldcg(lam + x) * inflow_weight(__ldcg(Ak + x), D, fwd, slip);
                     }
                     if (a.dcost && y != a.goal) a.dcost[y] -= rho;
                 }
                 lam_next[y] = a.gamma * rho;
             }
-            if (!grid_barrier(a.work, nblocks)) return;
+            publish_step(a.done, ++step);
+            if (!wait_neighbours(a.done, step, &a.work->status)) return;
             double *t = lam;
             lam = lam_next;
             lam_next = t;
@@ -540,11 +551,20 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
     double z1 = 0.0, z2 = 0.0;
     block_sum3(eps, z1, z2);
     if (threadIdx.x == 0) a.red[blockIdx.x] = eps;
-    __threadfence();
-    if (!grid_barrier(a.work, nblocks)) return;
+    publish_step(a.done, ++step);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         double s = 0.0;
-        for (unsigned b = 0; b < nblocks; ++b) s += a.red[b];
+        for (unsigned b = 0; b < nblocks; ++b) {
+            unsigned it = 0;
+            while (ld_acquire(a.done + b) < step) {
+                if (++it > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                    atomicOr(&a.work->status, kErrTimeout);
+                    return;
+                }
+                __nanosleep(32);
+            }
+            s += *((volatile double *)(a.red + b));
+        }
         *a.dslip += s;
     }
 }
@@ -687,7 +707,7 @@ extern "C" qv_status qv_tree_backward(const qv_plan_t *pl, int32_t e, double dL_
 
 // ---------------------------------------------------------------- value-iteration adjoint host side
 namespace {
-size_t vib_bytes(int H, int P, int every, int nslots, size_t offs[6]) {
+size_t vib_bytes(int H, int P, int every, int nslots, size_t offs[7]) {
     const size_t N = static_cast<size_t>(H) * P;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -702,6 +722,7 @@ size_t vib_bytes(int H, int P, int every, int nslots, size_t offs[6]) {
     offs[3] = take(sizeof(double) * N);
     offs[4] = take(sizeof(double) * N);
     offs[5] = take(sizeof(double) * nslots);
+    offs[6] = take(sizeof(unsigned) * nslots);
     return qv::a256(o);
 }
 constexpr int kViBackMaxGrid = 4096;
@@ -709,7 +730,7 @@ constexpr int kViBackMaxGrid = 4096;
 
 extern "C" size_t mdp_value_backward_workspace_bytes(const qv_model_t *m, int32_t every) {
     if (!m || every < 1 || m->H < 1 || m->pitch < 1) return 0;
-    size_t offs[6];
+    size_t offs[7];
     return vib_bytes(m->H, m->pitch, every, kViBackMaxGrid, offs);
 }
 
@@ -725,7 +746,7 @@ extern "C" qv_status mdp_value_backward(const qv_model_t *m, int32_t sweeps, int
         return qv_set_error(QV_ERR_INVALID, "mdp_value_backward: sweeps %d every %d", sweeps, every);
     if (reinterpret_cast<uintptr_t>(d_ws) & 255)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_backward: workspace must be 256-byte aligned");
-    size_t offs[6];
+    size_t offs[7];
     const size_t need = vib_bytes(m->H, m->pitch, every, kViBackMaxGrid, offs);
     if (ws_bytes < need)
         return qv_set_error(QV_ERR_WORKSPACE, "mdp_value_backward: workspace %zu < %zu bytes", ws_bytes, need);
@@ -751,6 +772,7 @@ extern "C" qv_status mdp_value_backward(const qv_model_t *m, int32_t sweeps, int
     a.lam0 = reinterpret_cast<double *>(ws + offs[3]);
     a.lam1 = reinterpret_cast<double *>(ws + offs[4]);
     a.red = reinterpret_cast<double *>(ws + offs[5]);
+    a.done = reinterpret_cast<unsigned *>(ws + offs[6]);
     a.dcost = d_dcost;
     a.dslip = d_dslip;
     int per_sm = 0;
@@ -758,9 +780,14 @@ extern "C" qv_status mdp_value_backward(const qv_model_t *m, int32_t sweeps, int
                       "occupancy") != QV_OK)
         return QV_ERR_CUDA;
     if (per_sm < 1) return qv_set_error(QV_ERR_INVALID, "mdp_value_backward: kernel does not fit an SM");
+    // bands of whole rows, at least one row and about one CTA's threads of cells each
     int grid = std::min(per_sm * qv_num_sms(), (a.N + kAdjThreads - 1) / kAdjThreads);
-    grid = std::max(1, std::min(grid, kViBackMaxGrid));
-    if (qv_check_cuda(cudaMemsetAsync(a.work, 0, sizeof(VIWork), st), "memset") != QV_OK) return QV_ERR_CUDA;
+    grid = std::max(1, std::min(std::min(grid, kViBackMaxGrid), a.H));
+    const int rows_per_cta = (a.H + grid - 1) / grid;
+    grid = (a.H + rows_per_cta - 1) / rows_per_cta;
+    if (qv_check_cuda(cudaMemsetAsync(a.work, 0, sizeof(VIWork), st), "memset") != QV_OK ||
+        qv_check_cuda(cudaMemsetAsync(a.done, 0, sizeof(unsigned) * grid, st), "memset") != QV_OK)
+        return QV_ERR_CUDA;
     void *args[] = {&a};
     if (qv_check_cuda(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_vi_backward), grid, kAdjThreads, args,
                                                   0, st),

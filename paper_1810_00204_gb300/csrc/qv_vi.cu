@@ -39,6 +39,7 @@ struct VIArgs {
     int chunk_rows;      // rows staged per smem chunk
     T *ckpt;             // nullable: V_k stored at every k % every == 0, k < sweeps
     int every;
+    unsigned *done;      // [gridDim.x] sweeps completed per CTA (truncated mode)
 };
 
 // Stage grid rows [c0-1, c1+1) of `src` (clipped to the grid) into smem rows
@@ -168,6 +169,108 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     }
 }
 
+// Truncated mode: exactly `truncated` sweeps, no stopping test, so a CTA
+// needs only its two neighbours' halo rows of V_k before sweep k; the
+// residual is taken on the last sweep only.
+template <typename T>
+__global__ void __launch_bounds__(256) k_value_iteration_trunc(VIArgs<T> a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ T s_red[8];
+    T *Vs = reinterpret_cast<T *>(smem_raw);
+    const unsigned nblocks = gridDim.x;
+    const int rows_per_cta = (a.H + nblocks - 1) / nblocks;
+    const int r_begin = min(a.H, (int)blockIdx.x * rows_per_cta);
+    const int r_end = min(a.H, r_begin + rows_per_cta);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const int S = a.truncated;
+    T local = T(0);
+    for (int k = 0; k < S; ++k) {
+        const T *Vk = (k & 1) ? a.V1 : a.V0;
+        T *Vn = (k & 1) ? a.V0 : a.V1;
+        if (k > 0 && !wait_neighbours(a.done, k, &a.work->status)) return;
+        if (a.ckpt && k % a.every == 0) {
+            T *dst = a.ckpt + static_cast<size_t>(k / a.every) * a.H * a.P;
+            for (int i = r_begin * a.P + threadIdx.x; i < r_end * a.P; i += blockDim.x) dst[i] = Vk[i];
+        }
+        for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
+            const int c1 = min(r_end, c0 + a.chunk_rows);
+            if (!stage_rows(a, Vs, Vk, c0, c1, &bar, phase)) return;
+            const int ncell = (c1 - c0) * a.P;
+            for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+                const int rr = i / a.P, col = i - rr * a.P;
+                const int y = (c0 + rr) * a.P + col;
+                const unsigned cw = __ldg(a.cell + y);
+                T v = T(0);
+                if (QV_CELL_FREE(cw) && y != a.goal) {
+                    T q[5];
+                    cell_q(a, y, col, cw, Vs + (rr + 1) * a.P, q);
+                    v = q[0];
+#pragma unroll
+                    for (int d = 1; d < 5; ++d) v = q[d] > v ? q[d] : v;
+                }
+                Vn[y] = v;
+                if (k == S - 1) {
+                    const T diff = fabs(v - Vs[(rr + 1) * a.P + col]);
+                    local = diff > local ? diff : local;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        publish_step(a.done, k + 1);
+    }
+    local = warp_max(local);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T m = T(0);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w] > m ? s_red[w] : m;
+        a.res_slots[blockIdx.x] = m;
+    }
+    publish_step(a.done, S + 1);  // the residual slot is written
+    if (!wait_neighbours(a.done, S + 1, &a.work->status)) return;
+    const T *Vf = (S & 1) ? a.V1 : a.V0;
+    const size_t plane = static_cast<size_t>(a.H) * a.P;
+    for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
+        const int c1 = min(r_end, c0 + a.chunk_rows);
+        if (!stage_rows(a, Vs, Vf, c0, c1, &bar, phase)) return;
+        const int ncell = (c1 - c0) * a.P;
+        for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+            const int rr = i / a.P, col = i - rr * a.P;
+            const int y = (c0 + rr) * a.P + col;
+            const unsigned cw = __ldg(a.cell + y);
+            T q[5] = {T(0), T(0), T(0), T(0), T(0)};
+            if (QV_CELL_FREE(cw) && y != a.goal) cell_q(a, y, col, cw, Vs + (rr + 1) * a.P, q);
+#pragma unroll
+            for (int d = 0; d < 5; ++d) a.Q[d * plane + y] = static_cast<float>(q[d]);
+            if (S & 1) a.V0[y] = Vs[(rr + 1) * a.P + col];  // the result lives in the caller's buffer
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // every CTA's residual slot, after its flag says it is written
+        T m = T(0);
+        for (unsigned b = 0; b < nblocks; ++b) {
+            unsigned i = 0;
+            while (ld_acquire(a.done + b) < static_cast<unsigned>(S + 1)) {
+                if (++i > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                    atomicOr(&a.work->status, kErrTimeout);
+                    return;
+                }
+                __nanosleep(32);
+            }
+            const T v = *((volatile T *)&a.res_slots[b]);
+            m = v > m ? v : m;
+        }
+        *a.sweeps_out = S;
+        *a.residual_out = m;
+    }
+}
+
 template <typename T>
 size_t vi_ws_bytes(int H, int P, int nslots) {
     size_t b = sizeof(VIWork);
@@ -175,6 +278,8 @@ size_t vi_ws_bytes(int H, int P, int nslots) {
     b += static_cast<size_t>(H) * P * sizeof(T);  // second V buffer
     b = (b + 255) & ~size_t(255);
     b += nslots * sizeof(T) + sizeof(int) + sizeof(T) + 64;
+    b = (b + 255) & ~size_t(255);
+    b += nslots * sizeof(unsigned);  // progress flags
     return (b + 255) & ~size_t(255);
 }
 
@@ -189,14 +294,16 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     int chunk = static_cast<int>(budget / (P * sizeof(T))) - 2;
     if (chunk < 1) return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: pitch %d too wide", P);
     size_t smem = static_cast<size_t>(chunk + 2) * P * sizeof(T);
+    // truncated runs have no stopping test: neighbour-synchronised sweeps
+    void *kern = truncated > 0 ? reinterpret_cast<void *>(k_value_iteration_trunc<T>)
+                               : reinterpret_cast<void *>(k_value_iteration<T>);
     if (smem > 40 * 1024 &&
-        qv_check_cuda(cudaFuncSetAttribute(k_value_iteration<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem)),
+        qv_check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                       "smem attr") != QV_OK)
         return QV_ERR_CUDA;
     int per_sm = 0;
-    if (qv_check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_value_iteration<T>, 256, smem),
-                      "occupancy") != QV_OK)
+    if (qv_check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem), "occupancy") !=
+        QV_OK)
         return QV_ERR_CUDA;
     if (per_sm < 1) return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: kernel does not fit an SM");
     int grid = std::min(per_sm * qv_num_sms(), 1024);
@@ -216,7 +323,11 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     T *slots = reinterpret_cast<T *>(ws + off);
     int *d_sweeps = reinterpret_cast<int *>(slots + 1024);
     T *d_res = reinterpret_cast<T *>(reinterpret_cast<char *>(d_sweeps) + 16);
-    if (qv_check_cuda(cudaMemsetAsync(work, 0, sizeof(VIWork), st), "memset") != QV_OK) return QV_ERR_CUDA;
+    const size_t off_flags = (off + 1024 * sizeof(T) + sizeof(int) + sizeof(T) + 64 + 255) & ~size_t(255);
+    unsigned *flags = reinterpret_cast<unsigned *>(ws + off_flags);
+    if (qv_check_cuda(cudaMemsetAsync(work, 0, sizeof(VIWork), st), "memset") != QV_OK ||
+        qv_check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned) * grid, st), "memset") != QV_OK)
+        return QV_ERR_CUDA;
     VIArgs<T> a;
     a.H = H;
     a.W = m->W;
@@ -239,10 +350,10 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     a.chunk_rows = chunk;
     a.ckpt = d_ckpt;
     a.every = every;
+    a.done = flags;
     void *args[] = {&a};
-    if (qv_check_cuda(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_value_iteration<T>), grid, 256,
-                                                  args, smem, st),
-                      "value iteration launch") != QV_OK)
+    if (qv_check_cuda(cudaLaunchCooperativeKernel(kern, grid, 256, args, smem, st), "value iteration launch") !=
+        QV_OK)
         return QV_ERR_CUDA;
     VIWork hw;
     int hs = 0;

@@ -47,6 +47,52 @@ static __device__ bool grid_barrier(VIWork *w, unsigned nblocks) {
     return s_ok != 0;
 }
 
+// Progress flags of a row-band decomposition (one band per CTA, in CTA
+// order): CTA i publishes how many steps it has completed; a step whose
+// reads reach one row into the neighbouring bands waits only for CTAs i - 1
+// and i + 1 to have completed the step before.  That also keeps every CTA
+// within one step of its neighbours, so a step may overwrite a buffer its
+// neighbours read two steps back.
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+static __device__ void publish_step(unsigned *done, unsigned step) {
+    __syncthreads();  // every thread's writes of the step precede thread 0's release
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(done + blockIdx.x, step);
+    }
+}
+// Bounded wait for CTAs blockIdx.x +- 1 to reach `step`; false (status bit
+// set, every CTA then leaves) when the limit ran out.
+static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsigned *status) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        for (int d = -1; d <= 1 && ok; d += 2) {
+            const int nb = static_cast<int>(blockIdx.x) + d;
+            if (nb < 0 || nb >= static_cast<int>(gridDim.x)) continue;
+            unsigned i = 0;
+            while (ld_acquire(done + nb) < step) {
+                if (++i > kSpinLimit || (*((volatile unsigned *)status) & kErrTimeout)) {
+                    atomicOr(status, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 template <typename T, typename Args>
 __device__ __forceinline__ T arrive_value(const Args &a, int y, const T *Vs_row, int col) {
     // r(y) + gamma V(y) for a free cell y
