@@ -39,8 +39,13 @@ struct VIArgs {
     int chunk_rows;      // rows staged per smem chunk
     T *ckpt;             // nullable: V_k stored at every k % every == 0, k < sweeps
     int every;
-    unsigned *done;      // [gridDim.x] sweeps completed per CTA (truncated mode)
+    unsigned *done;      // [gridDim.x] sweeps completed per CTA
+    unsigned *arrive;    // [kResRing] cumulative residual postings per ring slot
 };
+
+// Residual slots are a ring of this many sweeps: a slot is rewritten four
+// sweeps later, after every CTA has passed the test that read it.
+constexpr int kResRing = 4;
 
 // Stage grid rows [c0-1, c1+1) of `src` (clipped to the grid) into smem rows
 // 0.. of Vs with one bulk copy.  False when the wait ran out (after a second
@@ -68,12 +73,60 @@ __device__ bool stage_rows(const VIArgs<T> &a, T *Vs, const T *src, int c0, int 
     return failed == 0;
 }
 
+// Largest residual of sweep j over every CTA: wait until all CTAs have
+// posted it (a cumulative arrival count per ring slot), then every thread
+// reads the slots.  Same value in every CTA.
+template <typename T>
+__device__ bool sweep_residual(const VIArgs<T> &a, int j, T &res) {
+    __shared__ int s_ok;
+    __shared__ T s_m[8];
+    const unsigned nblocks = gridDim.x;
+    if (threadIdx.x == 0) {
+        // every sweep posts when there is a stopping test; a truncated run
+        // posts its last sweep only
+        const unsigned want = a.truncated > 0 ? nblocks : nblocks * static_cast<unsigned>(j / kResRing + 1);
+        unsigned i = 0;
+        int ok = 1;
+        while (ld_acquire(a.arrive + j % kResRing) < want) {
+            if (++i > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                atomicOr(&a.work->status, kErrTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    T m = T(0);
+    const T *slot = a.res_slots + static_cast<size_t>(j % kResRing) * nblocks;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const T v = __ldcg(slot + b);
+        m = v > m ? v : m;
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = T(0);
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = s_m[w] > m ? s_m[w] : m;
+    __syncthreads();
+    res = m;
+    return true;
+}
+
+// Jacobi sweeps by bands of rows, one band per CTA.  Sweep k reads one halo
+// row of each neighbouring band, so it waits only for CTAs i - 1 and i + 1
+// to finish sweep k - 1 (progress flags).  The stopping test of sweep j
+// needs every CTA's residual; it is taken before sweep j + 2, the first
+// sweep that overwrites V_{j+1}, so one sweep may run speculatively past the
+// one that converged and is discarded: the result is exactly the first
+// V_{k+1} with |V_{k+1} - V_k| < tol.  Truncated runs skip the test.
 template <typename T>
 __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ T s_red[8];
-    __shared__ int s_stop;
     T *Vs = reinterpret_cast<T *>(smem_raw);  // smem row s holds grid row c0 - 1 + s
     const unsigned nblocks = gridDim.x;
     const int rows_per_cta = (a.H + nblocks - 1) / nblocks;
@@ -85,13 +138,24 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     }
     __syncthreads();
     unsigned phase = 0;
-    int k = 0;
-    const int limit = a.truncated > 0 ? a.truncated : a.max_sweeps;
-    T res = T(0);
-    while (k < limit) {
+    const bool trunc = a.truncated > 0;
+    const int limit = trunc ? a.truncated : a.max_sweeps;
+    int F = -1;    // sweeps in the result, once known
+    T res = T(0);  // residual of sweep F - 1
+    for (int k = 0; k < limit; ++k) {
+        if (!trunc && k >= 2) {
+            T r;
+            if (!sweep_residual(a, k - 2, r)) return;
+            if (r < a.tol) {
+                F = k - 1;
+                res = r;
+                break;
+            }
+        }
         const T *Vk = (k & 1) ? a.V1 : a.V0;
         T *Vn = (k & 1) ? a.V0 : a.V1;
-        if (a.ckpt && k % a.every == 0) {  // this CTA's rows of V_k, complete since the last barrier
+        if (k > 0 && !wait_neighbours(a.done, k, &a.work->status)) return;
+        if (a.ckpt && k % a.every == 0) {  // this CTA's rows of V_k
             T *dst = a.ckpt + static_cast<size_t>(k / a.every) * a.H * a.P;
             for (int i = r_begin * a.P + threadIdx.x; i < r_end * a.P; i += blockDim.x) dst[i] = Vk[i];
         }
@@ -118,123 +182,42 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
             }
         }
         asm volatile("fence.proxy.async.global;" ::: "memory");
-        // block max -> per-CTA slot
-        local = warp_max(local);
-        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            T m = T(0);
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w] > m ? s_red[w] : m;
-            a.res_slots[blockIdx.x] = m;
-        }
-        __threadfence();
-        if (!grid_barrier(a.work, nblocks)) return;
-        ++k;
-        // every CTA reads every slot and takes the same decision
-        if (threadIdx.x == 0) {
-            T m = T(0);
-            for (unsigned b = 0; b < nblocks; ++b) {
-                const T v = *((volatile T *)&a.res_slots[b]);
-                m = v > m ? v : m;
-            }
-            res = m;
-            s_stop = (a.truncated <= 0 && m < a.tol) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_stop) break;
-        // the slots are rewritten next sweep: everybody must have read them
-        if (!grid_barrier(a.work, nblocks)) return;
-    }
-    // V_final is the buffer the last sweep wrote; Q = sum_y T (r + gamma V_final)
-    const T *Vf = (k & 1) ? a.V1 : a.V0;
-    const size_t plane = static_cast<size_t>(a.H) * a.P;
-    for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
-        const int c1 = min(r_end, c0 + a.chunk_rows);
-        if (!stage_rows(a, Vs, Vf, c0, c1, &bar, phase)) return;
-        const int ncell = (c1 - c0) * a.P;
-        for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
-            const int rr = i / a.P, col = i - rr * a.P;
-            const int y = (c0 + rr) * a.P + col;
-            const unsigned cw = __ldg(a.cell + y);
-            T q[5] = {T(0), T(0), T(0), T(0), T(0)};
-            if (QV_CELL_FREE(cw) && y != a.goal) cell_q(a, y, col, cw, Vs + (rr + 1) * a.P, q);
-#pragma unroll
-            for (int d = 0; d < 5; ++d) a.Q[d * plane + y] = static_cast<float>(q[d]);
-            if (k & 1) a.V0[y] = Vs[(rr + 1) * a.P + col];  // the result lives in the caller's buffer
-        }
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *a.sweeps_out = k;
-        *a.residual_out = res;
-    }
-}
-
-// Truncated mode: exactly `truncated` sweeps, no stopping test, so a CTA
-// needs only its two neighbours' halo rows of V_k before sweep k; the
-// residual is taken on the last sweep only.
-template <typename T>
-__global__ void __launch_bounds__(256) k_value_iteration_trunc(VIArgs<T> a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ T s_red[8];
-    T *Vs = reinterpret_cast<T *>(smem_raw);
-    const unsigned nblocks = gridDim.x;
-    const int rows_per_cta = (a.H + nblocks - 1) / nblocks;
-    const int r_begin = min(a.H, (int)blockIdx.x * rows_per_cta);
-    const int r_end = min(a.H, r_begin + rows_per_cta);
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    unsigned phase = 0;
-    const int S = a.truncated;
-    T local = T(0);
-    for (int k = 0; k < S; ++k) {
-        const T *Vk = (k & 1) ? a.V1 : a.V0;
-        T *Vn = (k & 1) ? a.V0 : a.V1;
-        if (k > 0 && !wait_neighbours(a.done, k, &a.work->status)) return;
-        if (a.ckpt && k % a.every == 0) {
-            T *dst = a.ckpt + static_cast<size_t>(k / a.every) * a.H * a.P;
-            for (int i = r_begin * a.P + threadIdx.x; i < r_end * a.P; i += blockDim.x) dst[i] = Vk[i];
-        }
-        for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
-            const int c1 = min(r_end, c0 + a.chunk_rows);
-            if (!stage_rows(a, Vs, Vk, c0, c1, &bar, phase)) return;
-            const int ncell = (c1 - c0) * a.P;
-            for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
-                const int rr = i / a.P, col = i - rr * a.P;
-                const int y = (c0 + rr) * a.P + col;
-                const unsigned cw = __ldg(a.cell + y);
-                T v = T(0);
-                if (QV_CELL_FREE(cw) && y != a.goal) {
-                    T q[5];
-                    cell_q(a, y, col, cw, Vs + (rr + 1) * a.P, q);
-                    v = q[0];
-#pragma unroll
-                    for (int d = 1; d < 5; ++d) v = q[d] > v ? q[d] : v;
-                }
-                Vn[y] = v;
-                if (k == S - 1) {
-                    const T diff = fabs(v - Vs[(rr + 1) * a.P + col]);
-                    local = diff > local ? diff : local;
-                }
+        if (!trunc || k == limit - 1) {
+            // post this CTA's residual of sweep k
+            local = warp_max(local);
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                T m = T(0);
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w] > m ? s_red[w] : m;
+                a.res_slots[static_cast<size_t>(k % kResRing) * nblocks + blockIdx.x] = m;
+                __threadfence();
+                atomicAdd(a.arrive + k % kResRing, 1u);
             }
         }
-        asm volatile("fence.proxy.async.global;" ::: "memory");
         publish_step(a.done, k + 1);
     }
-    local = warp_max(local);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = local;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        T m = T(0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = s_red[w] > m ? s_red[w] : m;
-        a.res_slots[blockIdx.x] = m;
+    if (F < 0) {
+        // the loop ran to its limit: the last two sweeps' tests are still open
+        if (!trunc && limit >= 2) {
+            T r;
+            if (!sweep_residual(a, limit - 2, r)) return;
+            if (r < a.tol) {
+                F = limit - 1;
+                res = r;
+            }
+        }
+        if (F < 0) {
+            T r;
+            if (!sweep_residual(a, limit - 1, r)) return;
+            F = limit;
+            res = r;
+        }
     }
-    publish_step(a.done, S + 1);  // the residual slot is written
-    if (!wait_neighbours(a.done, S + 1, &a.work->status)) return;
-    const T *Vf = (S & 1) ? a.V1 : a.V0;
+    // V_F and its neighbours' halo rows are complete (every CTA finished
+    // sweep F - 1); Q = sum_y T (r + gamma V_F)
+    if (!wait_neighbours(a.done, F, &a.work->status)) return;
+    const T *Vf = (F & 1) ? a.V1 : a.V0;
     const size_t plane = static_cast<size_t>(a.H) * a.P;
     for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
         const int c1 = min(r_end, c0 + a.chunk_rows);
@@ -248,26 +231,12 @@ __global__ void __launch_bounds__(256) k_value_iteration_trunc(VIArgs<T> a) {
             if (QV_CELL_FREE(cw) && y != a.goal) cell_q(a, y, col, cw, Vs + (rr + 1) * a.P, q);
 #pragma unroll
             for (int d = 0; d < 5; ++d) a.Q[d * plane + y] = static_cast<float>(q[d]);
-            if (S & 1) a.V0[y] = Vs[(rr + 1) * a.P + col];  // the result lives in the caller's buffer
+            if (F & 1) a.V0[y] = Vs[(rr + 1) * a.P + col];  // the result lives in the caller's buffer
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        // every CTA's residual slot, after its flag says it is written
-        T m = T(0);
-        for (unsigned b = 0; b < nblocks; ++b) {
-            unsigned i = 0;
-            while (ld_acquire(a.done + b) < static_cast<unsigned>(S + 1)) {
-                if (++i > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
-                    atomicOr(&a.work->status, kErrTimeout);
-                    return;
-                }
-                __nanosleep(32);
-            }
-            const T v = *((volatile T *)&a.res_slots[b]);
-            m = v > m ? v : m;
-        }
-        *a.sweeps_out = S;
-        *a.residual_out = m;
+        *a.sweeps_out = F;
+        *a.residual_out = res;
     }
 }
 
@@ -277,9 +246,9 @@ size_t vi_ws_bytes(int H, int P, int nslots) {
     b = (b + 255) & ~size_t(255);
     b += static_cast<size_t>(H) * P * sizeof(T);  // second V buffer
     b = (b + 255) & ~size_t(255);
-    b += nslots * sizeof(T) + sizeof(int) + sizeof(T) + 64;
+    b += kResRing * nslots * sizeof(T) + sizeof(int) + sizeof(T) + 64;
     b = (b + 255) & ~size_t(255);
-    b += nslots * sizeof(unsigned);  // progress flags
+    b += nslots * sizeof(unsigned) + 64;  // progress flags, residual arrival counters
     return (b + 255) & ~size_t(255);
 }
 
@@ -294,9 +263,7 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     int chunk = static_cast<int>(budget / (P * sizeof(T))) - 2;
     if (chunk < 1) return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: pitch %d too wide", P);
     size_t smem = static_cast<size_t>(chunk + 2) * P * sizeof(T);
-    // truncated runs have no stopping test: neighbour-synchronised sweeps
-    void *kern = truncated > 0 ? reinterpret_cast<void *>(k_value_iteration_trunc<T>)
-                               : reinterpret_cast<void *>(k_value_iteration<T>);
+    void *kern = reinterpret_cast<void *>(k_value_iteration<T>);
     if (smem > 40 * 1024 &&
         qv_check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)),
                       "smem attr") != QV_OK)
@@ -321,12 +288,14 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     T *V1 = reinterpret_cast<T *>(ws + off);
     off = (off + static_cast<size_t>(H) * P * sizeof(T) + 255) & ~size_t(255);
     T *slots = reinterpret_cast<T *>(ws + off);
-    int *d_sweeps = reinterpret_cast<int *>(slots + 1024);
+    int *d_sweeps = reinterpret_cast<int *>(slots + kResRing * 1024);
     T *d_res = reinterpret_cast<T *>(reinterpret_cast<char *>(d_sweeps) + 16);
-    const size_t off_flags = (off + 1024 * sizeof(T) + sizeof(int) + sizeof(T) + 64 + 255) & ~size_t(255);
+    const size_t off_flags =
+        (off + kResRing * 1024 * sizeof(T) + sizeof(int) + sizeof(T) + 64 + 255) & ~size_t(255);
     unsigned *flags = reinterpret_cast<unsigned *>(ws + off_flags);
+    unsigned *arrive = flags + 1024;
     if (qv_check_cuda(cudaMemsetAsync(work, 0, sizeof(VIWork), st), "memset") != QV_OK ||
-        qv_check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned) * grid, st), "memset") != QV_OK)
+        qv_check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned) * (1024 + 16), st), "memset") != QV_OK)
         return QV_ERR_CUDA;
     VIArgs<T> a;
     a.H = H;
@@ -351,6 +320,7 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     a.ckpt = d_ckpt;
     a.every = every;
     a.done = flags;
+    a.arrive = arrive;
     void *args[] = {&a};
     if (qv_check_cuda(cudaLaunchCooperativeKernel(kern, grid, 256, args, smem, st), "value iteration launch") !=
         QV_OK)
