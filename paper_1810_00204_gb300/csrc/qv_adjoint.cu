@@ -404,6 +404,7 @@ struct VIBack {
     double *red;          // [gridDim.x]
     VIWork *work;
     unsigned *done;       // [gridDim.x] steps completed per CTA
+    unsigned spin_limit;  // polls before a wait on other CTAs gives up
 };
 
 __device__ __forceinline__ double self_weight_d(int a, unsigned blk, double slip) {
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                 Ak[y] = static_cast<unsigned char>(arg);
             }
             publish_step(a.done, ++step);
-            if (!wait_neighbours(a.done, step, &a.work->status)) return;
+            if (!wait_neighbours(a.done, step, &a.work->status, a.spin_limit)) return;
         }
         if (j == J - 1) {
             // Q = sum_y T (r + gamma V_S): lambda_S = gamma T^T Qbar
@@ -511,7 +512,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                 lam[y] = a.gamma * rho;
             }
             publish_step(a.done, ++step);
-            if (!wait_neighbours(a.done, step, &a.work->status)) return;
+            if (!wait_neighbours(a.done, step, &a.work->status, a.spin_limit)) return;
         }
         // sweeps k = k0 + Lseg - 1 .. k0: lam holds lambda_{k+1}
         for (int i = Lseg - 1; i >= 0; --i) {
@@ -542,7 +543,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
                 lam_next[y] = a.gamma * rho;
             }
             publish_step(a.done, ++step);
-            if (!wait_neighbours(a.done, step, &a.work->status)) return;
+            if (!wait_neighbours(a.done, step, &a.work->status, a.spin_limit)) return;
             double *t = lam;
             lam = lam_next;
             lam_next = t;
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_vi_backward(VIBack a) {
         for (unsigned b = 0; b < nblocks; ++b) {
             unsigned it = 0;
             while (ld_acquire(a.done + b) < step) {
-                if (++it > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                if (++it > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
                     atomicOr(&a.work->status, kErrTimeout);
                     return;
                 }
@@ -773,6 +774,7 @@ extern "C" qv_status mdp_value_backward(const qv_model_t *m, int32_t sweeps, int
     a.lam1 = reinterpret_cast<double *>(ws + offs[4]);
     a.red = reinterpret_cast<double *>(ws + offs[5]);
     a.done = reinterpret_cast<unsigned *>(ws + offs[6]);
+    a.spin_limit = qv_cross_spin_limit();
     a.dcost = d_dcost;
     a.dslip = d_dslip;
     int per_sm = 0;

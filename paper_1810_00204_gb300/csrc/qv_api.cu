@@ -1,6 +1,8 @@
 // qv_api.cu -- error reporting and device queries shared by the entry points.
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 
 #include "qv_common.cuh"
 
@@ -19,6 +21,11 @@ qv_status qv_set_error(qv_status st, const char *fmt, ...) {
 qv_status qv_check_cuda(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return QV_OK;
     return qv_set_error(QV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+unsigned qv_cross_spin_limit() {
+    const char *f = std::getenv("QVTS_FAULT");
+    return (f && std::strcmp(f, "timeout") == 0) ? 0u : qv::kSpinLimit;
 }
 
 int qv_num_sms() {

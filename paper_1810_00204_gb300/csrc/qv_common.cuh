@@ -33,6 +33,9 @@ constexpr unsigned kErrCapacity = 2u;
 constexpr unsigned kErrInput = 4u;
 
 // Bounded spin: after this many polls a wait gives up and reports a timeout.
+// Waits on the CTA's own bulk copies always use it; waits on other CTAs (grid
+// barriers, progress flags) use the limit the host passes in, which is this
+// one unless a timeout is injected (qv_cross_spin_limit).
 constexpr unsigned kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -210,3 +213,8 @@ __device__ __forceinline__ float stage_reward(bool free_cell, bool is_goal, floa
 qv_status qv_set_error(qv_status st, const char *fmt, ...);
 qv_status qv_check_cuda(cudaError_t e, const char *what);
 int qv_num_sms();
+// Poll limit for waits on other CTAs: kSpinLimit, or 0 when the environment
+// variable QVTS_FAULT is "timeout" (host-side fault injection: every such wait
+// that is not already satisfied gives up at once and reports QV_ERR_TIMEOUT,
+// so the timeout path runs without a real hang).
+unsigned qv_cross_spin_limit();

@@ -112,6 +112,7 @@ struct PlanDev {
     unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
     ResultDev *result; // [E]
     const int *replay;
+    unsigned spin_limit;  // polls before a wait on other CTAs gives up
 };
 
 }  // namespace qv

@@ -268,6 +268,7 @@ T *at(char *ws, size_t off) {
 }
 
 qv_status launch_plan(qv_plan_t *pl, cudaStream_t st) {
+    pl->dev.spin_limit = qv_cross_spin_limit();
     if (pl->dirty) {
         if (qv_check_cuda(cudaMemsetAsync(pl->ws + pl->reset_off, 0, pl->reset_bytes, st), "counter reset") != QV_OK)
             return QV_ERR_CUDA;

@@ -161,7 +161,7 @@ __device__ bool grid_sync(const PlanDev &pl) {
         } else {
             unsigned i = 0;
             while (*gen == g) {
-                if (++i > kSpinLimit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+                if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
                     atomicOr(pl.status, kErrTimeout);
                     ok = 0;
                     break;

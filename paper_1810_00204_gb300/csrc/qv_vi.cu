@@ -41,6 +41,7 @@ struct VIArgs {
     int every;
     unsigned *done;      // [gridDim.x] sweeps completed per CTA
     unsigned *arrive;    // [kResRing] cumulative residual postings per ring slot
+    unsigned spin_limit; // polls before a wait on other CTAs gives up
 };
 
 // Residual slots are a ring of this many sweeps: a slot is rewritten four
@@ -88,7 +89,7 @@ __device__ bool sweep_residual(const VIArgs<T> &a, int j, T &res) {
         unsigned i = 0;
         int ok = 1;
         while (ld_acquire(a.arrive + j % kResRing) < want) {
-            if (++i > kSpinLimit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+            if (++i > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
                 atomicOr(&a.work->status, kErrTimeout);
                 ok = 0;
                 break;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
         }
         const T *Vk = (k & 1) ? a.V1 : a.V0;
         T *Vn = (k & 1) ? a.V0 : a.V1;
-        if (k > 0 && !wait_neighbours(a.done, k, &a.work->status)) return;
+        if (k > 0 && !wait_neighbours(a.done, k, &a.work->status, a.spin_limit)) return;
         if (a.ckpt && k % a.every == 0) {  // this CTA's rows of V_k
             T *dst = a.ckpt + static_cast<size_t>(k / a.every) * a.H * a.P;
             for (int i = r_begin * a.P + threadIdx.x; i < r_end * a.P; i += blockDim.x) dst[i] = Vk[i];
@@ -216,7 +217,7 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     }
     // V_F and its neighbours' halo rows are complete (every CTA finished
     // sweep F - 1); Q = sum_y T (r + gamma V_F)
-    if (!wait_neighbours(a.done, F, &a.work->status)) return;
+    if (!wait_neighbours(a.done, F, &a.work->status, a.spin_limit)) return;
     const T *Vf = (F & 1) ? a.V1 : a.V0;
     const size_t plane = static_cast<size_t>(a.H) * a.P;
     for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
@@ -321,6 +322,7 @@ qv_status run_vi(const qv_model_t *m, double tol, int max_sweeps, int truncated,
     a.every = every;
     a.done = flags;
     a.arrive = arrive;
+    a.spin_limit = qv_cross_spin_limit();
     void *args[] = {&a};
     if (qv_check_cuda(cudaLaunchCooperativeKernel(kern, grid, 256, args, smem, st), "value iteration launch") !=
         QV_OK)

@@ -16,37 +16,6 @@ struct VIWork {
     unsigned pad;
 };
 
-// Bounded grid barrier (all CTAs co-resident through a cooperative launch).
-static __device__ bool grid_barrier(VIWork *w, unsigned nblocks) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        volatile unsigned *gen = &w->bar_gen;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(&w->bar_count, 1u) == nblocks - 1) {
-            atomicExch(&w->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&w->bar_gen, 1u);
-        } else {
-            unsigned i = 0;
-            while (*gen == g) {
-                if (++i > kSpinLimit || (*((volatile unsigned *)&w->status) & kErrTimeout)) {
-                    atomicOr(&w->status, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Progress flags of a row-band decomposition (one band per CTA, in CTA
 // order): CTA i publishes how many steps it has completed; a step whose
 // reads reach one row into the neighbouring bands waits only for CTAs i - 1
@@ -70,7 +39,7 @@ static __device__ void publish_step(unsigned *done, unsigned step) {
 }
 // Bounded wait for CTAs blockIdx.x +- 1 to reach `step`; false (status bit
 // set, every CTA then leaves) when the limit ran out.
-static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsigned *status) {
+static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsigned *status, unsigned limit) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -79,7 +48,7 @@ static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsi
             if (nb < 0 || nb >= static_cast<int>(gridDim.x)) continue;
             unsigned i = 0;
             while (ld_acquire(done + nb) < step) {
-                if (++i > kSpinLimit || (*((volatile unsigned *)status) & kErrTimeout)) {
+                if (++i > limit || (*((volatile unsigned *)status) & kErrTimeout)) {
                     atomicOr(status, kErrTimeout);
                     ok = 0;
                     break;
