@@ -144,23 +144,29 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 // Bounded grid barrier; every CTA of the cooperative launch calls it the
-// same number of times.  False (for every CTA) once any wait gave up.
+// same number of times.  False (for every CTA) once any wait gave up.  The
+// arrival is an acquire-release add on the counter (after the CTA barrier,
+// so it publishes every thread's writes); the last arriver releases the
+// generation word, which the others acquire.
 __device__ bool grid_sync(const PlanDev &pl) {
     __shared__ int s_ok;
     fence_proxy_async_global();
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *gen = &pl.bar->gen;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(&pl.bar->count, 1u) == gridDim.x - 1) {
-            atomicExch(&pl.bar->count, 0u);
-            __threadfence();
-            atomicAdd(&pl.bar->gen, 1u);
+        unsigned g;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&pl.bar->gen) : "memory");
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&pl.bar->count) : "memory");
+        if (prev == gridDim.x - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&pl.bar->count) : "memory");
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&pl.bar->gen), "r"(g + 1u) : "memory");
         } else {
             unsigned i = 0;
-            while (*gen == g) {
+            for (;;) {
+                unsigned cur;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&pl.bar->gen) : "memory");
+                if (cur != g) break;
                 if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
                     atomicOr(pl.status, kErrTimeout);
                     ok = 0;
@@ -169,7 +175,6 @@ __device__ bool grid_sync(const PlanDev &pl) {
                 __nanosleep(32);
             }
         }
-        __threadfence();
         if (*((volatile unsigned *)pl.status) & kErrTimeout) ok = 0;
         s_ok = ok;
     }
