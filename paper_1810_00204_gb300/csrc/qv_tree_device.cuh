@@ -1171,12 +1171,18 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
     const int K = pl.K, D = pl.depth;
     const bool fused = pl.leaf_mode != QV_LEAF_MATERIALISE;
     if (fused) {
-        for (int e = 0; e < pl.E; ++e) {
-            const EpDev &epg = pl.eps[e];
-            const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
-            for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n; t += gridDim.x * blockDim.x)
-                leaf_records(pl, epg, D - 1, t, true);
-        }
+        // the CTAs that back up an episode (blockIdx.x < E) write no leaf
+        // records when there are other CTAs to write them
+        const int skip = gridDim.x > pl.E ? pl.E : 0;
+        const int nb = gridDim.x - skip;
+        const int b = static_cast<int>(blockIdx.x) - skip;
+        if (b >= 0)
+            for (int e = 0; e < pl.E; ++e) {
+                const EpDev &epg = pl.eps[e];
+                const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
+                for (int t = b * blockDim.x + threadIdx.x; t < 5 * n; t += nb * blockDim.x)
+                    leaf_records(pl, epg, D - 1, t, true);
+            }
     }
     for (int e = blockIdx.x; e < pl.E; e += gridDim.x) {
         load_ep(pl, e, S, cur_e);
