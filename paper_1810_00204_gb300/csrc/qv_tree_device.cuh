@@ -1139,27 +1139,36 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
 // Records of the leaves, which nothing read before, from every (node,
 // action) pair of the deepest internal level.  `write_value`: fused leaves,
 // whose values live in the sample slots.
+// One leaf record per call: t indexes the (node, action, sample slot)
+// triples of level l, so every slot's loads are independent of the others.
 __device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep, int l, int t, bool write_value) {
     const int K = pl.K, nz = ep.B + 1;
-    const int node = t / 5, a = t - node * 5;
+    const int node = t / (5 * K), a = (t / K) % 5, j = t % K;
     const long long ia = static_cast<long long>(ep.inode_base[l] + node) * 5 + a;
-    const int m = __ldcg(pl.nchild + ia), off = __ldcg(pl.choff + ia);
-    const long long sb = ia * K;
+    const int m = __ldcg(pl.nchild + ia);
+    if (j >= m) return;
+    const int off = __ldcg(pl.choff + ia);
+    if (off + j >= ep.cap[l + 1]) return;
+    const long long sb = ia * K + j;
     const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l] + node);
-    for (int j = 0; j < m; ++j) {
-        if (off + j >= ep.cap[l + 1]) break;
-        const int g = ep.node_base[l + 1] + off + j;
-        const int z = __ldcg(pl.slot_z + sb + j);
-        pl.parent[g] = node;
-        pl.action[g] = a;
-        pl.obs[g] = z;
-        pl.weight[g] = __ldcg(pl.slot_w + sb + j);
-        pl.pz[g] = __ldcg(pl.slot_P + sb + j);
-        pl.code[g] = (pcode * 5ull + a) * static_cast<unsigned long long>(nz) + z;
-        if (write_value) {
-            pl.value[g] = __ldcg(pl.slot_val + sb + j);
-            pl.leaf_arg[g] = __ldcg(pl.slot_arg + sb + j);
-        }
+    const int z = __ldcg(pl.slot_z + sb);
+    const float w = __ldcg(pl.slot_w + sb), p = __ldcg(pl.slot_P + sb);
+    float v = 0.0f;
+    int arg = 0;
+    if (write_value) {
+        v = __ldcg(pl.slot_val + sb);
+        arg = __ldcg(pl.slot_arg + sb);
+    }
+    const int g = ep.node_base[l + 1] + off + j;
+    pl.parent[g] = node;
+    pl.action[g] = a;
+    pl.obs[g] = z;
+    pl.weight[g] = w;
+    pl.pz[g] = p;
+    pl.code[g] = (pcode * 5ull + a) * static_cast<unsigned long long>(nz) + z;
+    if (write_value) {
+        pl.value[g] = v;
+        pl.leaf_arg[g] = arg;
     }
 }
 
@@ -1180,7 +1189,7 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
             for (int e = 0; e < pl.E; ++e) {
                 const EpDev &epg = pl.eps[e];
                 const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
-                for (int t = b * blockDim.x + threadIdx.x; t < 5 * n; t += nb * blockDim.x)
+                for (int t = b * blockDim.x + threadIdx.x; t < 5 * K * n; t += nb * blockDim.x)
                     leaf_records(pl, epg, D - 1, t, true);
             }
     }
@@ -1194,11 +1203,23 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
                 const long long ia = static_cast<long long>(ep.inode_base[l] + node) * 5 + a;
                 const int m = __ldcg(pl.nchild + ia), off = __ldcg(pl.choff + ia);
                 const long long sb = ia * K;
+                const float *vals = pl.value + ep.node_base[l + 1] + off;
                 float s = 0.0f;
-                for (int j = 0; j < m; ++j)
-                    s = fmaf(__ldcg(pl.slot_w + sb + j), __ldcg(pl.value + ep.node_base[l + 1] + off + j), s);
+                // loads of a batch of children issued together, summed in order
+                for (int j0 = 0; j0 < m; j0 += 8) {
+                    float wv[8], vv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        wv[i] = j0 + i < m ? __ldcg(pl.slot_w + sb + j0 + i) : 0.0f;
+                        vv[i] = j0 + i < m ? __ldcg(vals + j0 + i) : 0.0f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (j0 + i < m) s = fmaf(wv[i], vv[i], s);
+                }
                 pl.UQ[ia] = fmaf(ep.gamma, s, __ldcg(pl.R + ia));
-                if (!fused && l == D - 1) leaf_records(pl, ep, l, t, false);
+                if (!fused && l == D - 1)
+                    for (int j = 0; j < K; ++j) leaf_records(pl, ep, l, t * K + j, false);
             }
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
