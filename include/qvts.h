@@ -273,7 +273,10 @@ void qv_tune_clear(void);
  * tests).  Level l nodes are ordered by (parent, action, z ascending).
  * Arrays with a NULL out-pointer are skipped.  Per-node arrays have
  * capacity cap; per-(node, action) arrays are [cap][5]; samples [cap][5][K].
- * belief is NULL for levels that hold no beliefs (fused leaves). */
+ * belief is NULL for levels that hold no beliefs (fused leaves).  In the
+ * fused mode the leaves' per-node records are written on demand: asking for
+ * the leaf level synchronises the device, writes them (one small launch)
+ * and synchronises again. */
 typedef struct {
     int32_t cap;               /* capacity of the level (worst case)                   */
     const int32_t *d_count;    /* device scalar: nodes in the level                    */

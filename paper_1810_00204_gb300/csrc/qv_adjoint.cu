@@ -650,6 +650,8 @@ extern "C" qv_status qv_tree_backward(const qv_plan_t *pl, int32_t e, double dL_
         return qv_set_error(QV_ERR_INVALID, "qv_tree_backward: workspace must be 256-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int D = pl->params.depth;
+    // the leaves' records (observations, P(z), values, argmax) in stream order
+    if (qv_plan_leaf_records(const_cast<qv_plan_t *>(pl), st, false) != QV_OK) return QV_ERR_CUDA;
     char *ws = static_cast<char *>(d_ws);
     AdjArgs a;
     std::memset(&a, 0, sizeof(a));

@@ -118,6 +118,10 @@ struct PlanDev {
 }  // namespace qv
 
 // Host handle of a plan (qv_plan_t in the C ABI).
+struct qv_plan;
+// Writes the fused mode's leaf records after a run (no-op otherwise);
+// sync_device: wait for the whole device before and after (inspection).
+qv_status qv_plan_leaf_records(qv_plan *pl, cudaStream_t st, bool sync_device);
 struct qv_plan {
     int E = 0;
     qv_plan_params_t params{};
@@ -129,5 +133,6 @@ struct qv_plan {
     size_t smem = 0;
     size_t reset_off = 0, reset_bytes = 0;  // counters zeroed when a run failed
     bool dirty = false;
+    bool records_fresh = false;  // the fused mode's leaf records match the last run
     cudaGraphExec_t graph = nullptr;
 };

@@ -269,6 +269,7 @@ T *at(char *ws, size_t off) {
 
 qv_status launch_plan(qv_plan_t *pl, cudaStream_t st) {
     pl->dev.spin_limit = qv_cross_spin_limit();
+    pl->records_fresh = false;
     if (pl->dirty) {
         if (qv_check_cuda(cudaMemsetAsync(pl->ws + pl->reset_off, 0, pl->reset_bytes, st), "counter reset") != QV_OK)
             return QV_ERR_CUDA;
@@ -438,6 +439,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
 extern "C" qv_status qv_plan_run(qv_plan_t *pl, qv_stream_t stream) {
     if (!pl) return qv_set_error(QV_ERR_INVALID, "qv_plan_run: null plan");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pl->records_fresh = false;
     if (pl->graph && !pl->dirty) return qv_check_cuda(cudaGraphLaunch(pl->graph, st), "qv_plan_run graph launch");
     return launch_plan(pl, st);
 }
@@ -564,10 +566,28 @@ extern "C" void qv_plan_destroy(qv_plan_t *pl) {
     delete pl;
 }
 
-extern "C" qv_status qv_plan_level(const qv_plan_t *pl, int32_t e, int32_t l, qv_level_view_t *v) {
-    if (!pl || !v) return qv_set_error(QV_ERR_INVALID, "qv_plan_level: null pointer");
-    if (e < 0 || e >= pl->E || l < 0 || l > pl->params.depth)
+// The fused mode writes its leaves' records on demand, after the run that
+// `stream` (or, with a null stream, the whole device) has finished or holds.
+qv_status qv_plan_leaf_records(qv_plan_t *pl, cudaStream_t st, bool sync_device) {
+    if (pl->params.leaf_mode == QV_LEAF_MATERIALISE || pl->params.depth == 0 || pl->records_fresh) return QV_OK;
+    if (sync_device && qv_check_cuda(cudaDeviceSynchronize(), "leaf records") != QV_OK) return QV_ERR_CUDA;
+    const int blocks = std::max(1, std::min(4 * qv_num_sms(), 1 << 16));
+    qv::k_leaf_records<<<blocks, 256, 0, st>>>(pl->dev);
+    if (qv_check_cuda(cudaGetLastError(), "leaf records launch") != QV_OK) return QV_ERR_CUDA;
+    if (sync_device && qv_check_cuda(cudaDeviceSynchronize(), "leaf records") != QV_OK) return QV_ERR_CUDA;
+    pl->records_fresh = true;
+    return QV_OK;
+}
+
+extern "C" qv_status qv_plan_level(const qv_plan_t *cpl, int32_t e, int32_t l, qv_level_view_t *v) {
+    if (!cpl || !v) return qv_set_error(QV_ERR_INVALID, "qv_plan_level: null pointer");
+    if (e < 0 || e >= cpl->E || l < 0 || l > cpl->params.depth)
         return qv_set_error(QV_ERR_INVALID, "qv_plan_level: episode %d level %d out of range", e, l);
+    qv_plan_t *pl = const_cast<qv_plan_t *>(cpl);
+    if (l == pl->params.depth) {
+        const qv_status rs = qv_plan_leaf_records(pl, nullptr, true);
+        if (rs != QV_OK) return rs;
+    }
     const qv::EpDev &ep = pl->eps[e];
     const qv::PlanDev &d = pl->dev;
     const int K = pl->params.K;

@@ -936,7 +936,9 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
         QV_TRACE_MARK(tr, 7);
         finalize_node(pl, ep, l, local, FUSED, S.tot[35], code, S);
         QV_TRACE_MARK(tr, 8);
-        node_done(pl, l, e, ep, S);
+        // the fused level's children are leaves: they are numbered in the
+        // backup phase, beside the backup, and need no work lists
+        if constexpr (!FUSED) node_done(pl, l, e, ep, S);
         QV_TRACE_MARK(tr, 9);
 #ifdef QV_TRACE
         tr[0] |= 1ull << 56;  // this item finalised its node
@@ -1180,18 +1182,16 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
     const int K = pl.K, D = pl.depth;
     const bool fused = pl.leaf_mode != QV_LEAF_MATERIALISE;
     if (fused) {
-        // the CTAs that back up an episode (blockIdx.x < E) write no leaf
-        // records when there are other CTAs to write them
-        const int skip = gridDim.x > pl.E ? pl.E : 0;
-        const int nb = gridDim.x - skip;
-        const int b = static_cast<int>(blockIdx.x) - skip;
-        if (b >= 0)
-            for (int e = 0; e < pl.E; ++e) {
-                const EpDev &epg = pl.eps[e];
-                const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
-                for (int t = b * blockDim.x + threadIdx.x; t < 5 * K * n; t += nb * blockDim.x)
-                    leaf_records(pl, epg, D - 1, t, true);
-            }
+        // number the leaves of every episode (the children of the fused
+        // level), on CTAs other than those that back the episode up when
+        // there are enough; their records are written on demand
+        // (k_leaf_records)
+        const int first = gridDim.x >= 2 * pl.E ? pl.E : 0;
+        for (int e = static_cast<int>(blockIdx.x) - first; e >= 0 && e < pl.E;
+             e += static_cast<int>(gridDim.x) - first) {
+            load_ep(pl, e, S, cur_e);
+            compact_episode(pl, D - 1, *S.ep, e, S);
+        }
     }
     for (int e = blockIdx.x; e < pl.E; e += gridDim.x) {
         load_ep(pl, e, S, cur_e);
@@ -1320,6 +1320,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     if (D > 0) {
         phase_backup(pl, S, cur_e);
         stamp(pl, slot++);
+    }
+}
+
+// Records (parent, action, observation, weight, P(z), path code, value,
+// argmax) of the fused mode's leaves, written on demand after a run: one
+// thread per (episode, node, action, sample slot) of the deepest internal
+// level.
+__global__ void __launch_bounds__(256) k_leaf_records(PlanDev pl) {
+    const int D = pl.depth, K = pl.K;
+    for (int e = 0; e < pl.E; ++e) {
+        const EpDev &ep = pl.eps[e];
+        const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 5 * K * n; t += gridDim.x * blockDim.x)
+            leaf_records(pl, ep, D - 1, t, true);
     }
 }
 
