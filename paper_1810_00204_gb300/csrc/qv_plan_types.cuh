@@ -132,6 +132,7 @@ struct qv_plan {
     int grid = 0;
     size_t smem = 0;
     size_t reset_off = 0, reset_bytes = 0;  // counters zeroed when a run failed
+    size_t read_off = 0, read_bytes = 0;    // counts, results, status, boundary: one copy back
     bool dirty = false;
     bool records_fresh = false;  // the fused mode's leaf records match the last run
     cudaGraphExec_t graph = nullptr;

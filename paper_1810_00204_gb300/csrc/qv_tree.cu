@@ -219,7 +219,6 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     };
     const long long E1 = E + 1, D1 = D + 1;
     L.off_eps = take(sizeof(qv::EpDev) * E);
-    L.off_count = take(sizeof(int) * D1 * E);
     L.off_items = take(sizeof(int) * D1 * E);
     L.off_uitems = take(sizeof(int) * D1 * E);
     L.off_wbs = take(sizeof(int) * D1 * E1);
@@ -247,16 +246,19 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_slot_arg = take(sizeof(int) * L.NI * 5 * K);
     L.off_leaf_arg = take(sizeof(int) * L.NT);
     L.off_partials = take(sizeof(float) * static_cast<size_t>(L.n_part) * L.rec_len);
-    L.off_result = take(sizeof(qv::ResultDev) * E);
     L.off_stamps = take(sizeof(unsigned long long) * qv::kStamps);
+    // what qv_plan_read copies back, contiguous: level sizes, root results,
+    // then (first in the zeroed region) the status word and boundary count
+    L.off_count = take(sizeof(int) * D1 * E);
+    L.off_result = take(sizeof(qv::ResultDev) * E);
     // counters and status words: one contiguous region, zeroed at create
+    L.off_status = take(sizeof(unsigned) * 4);
+    L.off_boundary = take(sizeof(unsigned long long));
     L.off_node_cnt = take(sizeof(unsigned) * L.NI);
     L.off_ep_cnt = take(sizeof(unsigned) * D1 * E);
     L.off_lvl_cnt = take(sizeof(unsigned) * D1);
     L.off_leaf_cnt = take(sizeof(unsigned) * static_cast<size_t>(L.n_part));
     L.off_bar = take(sizeof(qv::GridBar));
-    L.off_status = take(sizeof(unsigned) * 4);
-    L.off_boundary = take(sizeof(unsigned long long));
     L.off_beliefs = take(sizeof(float) * std::max<long long>(L.n_belief, 4));
     L.total = align_up(o, 256);
     return QV_OK;
@@ -275,11 +277,9 @@ qv_status launch_plan(qv_plan_t *pl, cudaStream_t st) {
             return QV_ERR_CUDA;
         pl->dirty = false;
     }
-    // per-run status word and boundary count
-    if (qv_check_cuda(cudaMemsetAsync(pl->dev.status, 0, 4 * sizeof(unsigned), st), "status reset") != QV_OK ||
-        qv_check_cuda(cudaMemsetAsync(pl->dev.boundary, 0, sizeof(unsigned long long), st), "boundary reset") !=
-            QV_OK)
-        return QV_ERR_CUDA;
+    // per-run status word and boundary count (adjacent: one memset)
+    const size_t sb_bytes = reinterpret_cast<char *>(pl->dev.boundary + 1) - reinterpret_cast<char *>(pl->dev.status);
+    if (qv_check_cuda(cudaMemsetAsync(pl->dev.status, 0, sb_bytes, st), "status reset") != QV_OK) return QV_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(pl->grid);
     cfg.blockDim = dim3(qv::kThreads);
@@ -390,8 +390,10 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
-    pl->reset_off = L.off_node_cnt;
-    pl->reset_bytes = L.off_beliefs - L.off_node_cnt;
+    pl->reset_off = L.off_status;
+    pl->reset_bytes = L.off_beliefs - L.off_status;
+    pl->read_off = L.off_count;
+    pl->read_bytes = L.off_boundary + sizeof(unsigned long long) - L.off_count;
     // static state: descriptors, the root of every episode, level-0 work lists
     const int D = params->depth;
     std::vector<int> cnt0(E, 1), it0(E), wbs(E + 1), wbu(E + 1), wbl(E + 1), neg(E, -1);
@@ -531,20 +533,21 @@ extern "C" qv_status qv_plan_read(qv_plan_t *pl, qv_plan_result_t *h, qv_stream_
     if (!pl || !h) return qv_set_error(QV_ERR_INVALID, "qv_plan_read: null pointer");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int E = pl->E, D = pl->params.depth;
-    std::vector<qv::ResultDev> r(E);
-    std::vector<int> cnt((D + 1) * E);
-    unsigned status = 0;
-    unsigned long long bnd = 0;
-    if (qv_check_cuda(cudaMemcpyAsync(r.data(), pl->dev.result, sizeof(qv::ResultDev) * E, cudaMemcpyDeviceToHost, st),
+    // level sizes, root results, status and boundary count in one copy
+    std::vector<char> buf(pl->read_bytes);
+    if (qv_check_cuda(cudaMemcpyAsync(buf.data(), pl->ws + pl->read_off, pl->read_bytes, cudaMemcpyDeviceToHost, st),
                       "read results") != QV_OK ||
-        qv_check_cuda(cudaMemcpyAsync(cnt.data(), pl->dev.count, sizeof(int) * cnt.size(), cudaMemcpyDeviceToHost, st),
-                      "read counts") != QV_OK ||
-        qv_check_cuda(cudaMemcpyAsync(&status, pl->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost, st),
-                      "read status") != QV_OK ||
-        qv_check_cuda(cudaMemcpyAsync(&bnd, pl->dev.boundary, sizeof(bnd), cudaMemcpyDeviceToHost, st),
-                      "read boundary") != QV_OK ||
         qv_check_cuda(cudaStreamSynchronize(st), "qv_plan_read") != QV_OK)
         return QV_ERR_CUDA;
+    auto at_host = [&](const void *dev_ptr) {
+        return buf.data() + (static_cast<const char *>(dev_ptr) - (pl->ws + pl->read_off));
+    };
+    const qv::ResultDev *r = reinterpret_cast<const qv::ResultDev *>(at_host(pl->dev.result));
+    const int *cnt = reinterpret_cast<const int *>(at_host(pl->dev.count));
+    unsigned status;
+    unsigned long long bnd;
+    std::memcpy(&status, at_host(pl->dev.status), sizeof(status));
+    std::memcpy(&bnd, at_host(pl->dev.boundary), sizeof(bnd));
     for (int e = 0; e < E; ++e) {
         qv_plan_result_t &o = h[e];
         std::memset(&o, 0, sizeof(o));
