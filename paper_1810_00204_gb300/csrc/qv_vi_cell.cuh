@@ -32,31 +32,31 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
 }
 static __device__ void publish_step(unsigned *done, unsigned step) {
     __syncthreads();  // every thread's writes of the step precede thread 0's release
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(done + blockIdx.x, step);
-    }
+    if (threadIdx.x == 0) st_release(done + blockIdx.x, step);
 }
-// Bounded wait for CTAs blockIdx.x +- 1 to reach `step`; false (status bit
-// set, every CTA then leaves) when the limit ran out.
+// Bounded wait for CTAs blockIdx.x +- 1 to reach `step` (lanes 0 and 1 of
+// warp 0 watch one each); false (status bit set, every CTA then leaves) when
+// the limit ran out.
 static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsigned *status, unsigned limit) {
     __shared__ int s_ok;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         int ok = 1;
-        for (int d = -1; d <= 1 && ok; d += 2) {
-            const int nb = static_cast<int>(blockIdx.x) + d;
-            if (nb < 0 || nb >= static_cast<int>(gridDim.x)) continue;
-            unsigned i = 0;
-            while (ld_acquire(done + nb) < step) {
-                if (++i > limit || (*((volatile unsigned *)status) & kErrTimeout)) {
-                    atomicOr(status, kErrTimeout);
-                    ok = 0;
-                    break;
+        if (threadIdx.x < 2) {
+            const int nb = static_cast<int>(blockIdx.x) + (threadIdx.x == 0 ? -1 : 1);
+            if (nb >= 0 && nb < static_cast<int>(gridDim.x)) {
+                unsigned i = 0;
+                while (ld_acquire(done + nb) < step) {
+                    if (++i > limit || (*((volatile unsigned *)status) & kErrTimeout)) {
+                        atomicOr(status, kErrTimeout);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
                 }
-                __nanosleep(32);
             }
         }
-        s_ok = ok;
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
