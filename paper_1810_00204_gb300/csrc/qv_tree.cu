@@ -403,7 +403,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     // a depth-0 plan streams each root as one leaf, split into leaf0_split chunks
     const int leaf0_split = static_cast<int>(std::min<long long>(std::max<long long>((L.target + E - 1) / E, 1), 64));
     for (int e = 0; e < E; ++e) {
-        const long long want = (L.target + E - 1) / E;
+        const long long want = std::max<long long>(L.target / E, 1);
         it0[e] = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), L.eps[e].bands));
         wbs[e] = s0;
         wbu[e] = s0;

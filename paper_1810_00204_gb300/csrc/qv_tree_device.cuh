@@ -497,7 +497,9 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
     int Tt, Gt;
     block_exclusive_scan(T, S.scan, Tt);
     block_exclusive_scan(G, S.scan, Gt);
-    const long long want = Tt > 0 ? (static_cast<long long>(pl.target) + Tt - 1) / Tt : 1;
+    // items per node: the target rounded down, so that a phase's items fill
+    // at most the target (one wave of the grid per item aimed at per CTA)
+    const long long want = Tt > 0 ? max(static_cast<long long>(pl.target) / Tt, 1LL) : 1;
     int C = 1;  // leaf chunks per group of leaves
     if (l1 == pl.depth) {
         C = static_cast<int>(min(max(Gt > 0 ? (static_cast<long long>(pl.target) + Gt - 1) / Gt : 1LL, 1LL), 64LL));
