@@ -401,7 +401,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     std::vector<unsigned long long> zero64(E, 0ull);
     int s0 = 0, l0 = 0;
     // a depth-0 plan streams each root as one leaf, split into leaf0_split chunks
-    const int leaf0_split = static_cast<int>(std::min<long long>(std::max<long long>((L.target + E - 1) / E, 1), 64));
+    const int leaf0_split = static_cast<int>(std::min<long long>(std::max<long long>(L.target / E, 1), 64));
     for (int e = 0; e < E; ++e) {
         const long long want = std::max<long long>(L.target / E, 1);
         it0[e] = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), L.eps[e].bands));

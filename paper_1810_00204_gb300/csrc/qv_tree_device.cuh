@@ -502,7 +502,7 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
     const long long want = Tt > 0 ? max(static_cast<long long>(pl.target) / Tt, 1LL) : 1;
     int C = 1;  // leaf chunks per group of leaves
     if (l1 == pl.depth) {
-        C = static_cast<int>(min(max(Gt > 0 ? (static_cast<long long>(pl.target) + Gt - 1) / Gt : 1LL, 1LL), 64LL));
+        C = static_cast<int>(min(max(Gt > 0 ? static_cast<long long>(pl.target) / Gt : 1LL, 1LL), 64LL));
         if (threadIdx.x == 0) *pl.leaf_split = C;
     }
     int ws = 0, wu = 0, wl = 0;
