@@ -1052,18 +1052,36 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
         const int n4 = ep.N >> 2;
         const int c0 = static_cast<int>((static_cast<long long>(chunk) * n4) / C);
         const int c1 = static_cast<int>((static_cast<long long>(chunk + 1) * n4) / C);
-#pragma unroll 2
-        for (int i4 = c0 + threadIdx.x; i4 < c1; i4 += blockDim.x) {
-            float4 q[5];
+        // the group's leaf beliefs (streamed once from HBM) against Q (L2):
+        // every load of kLeafUnroll consecutive float4 columns is issued
+        // before the arithmetic that consumes them
+        const float4 *bl[kLeafGroup];
 #pragma unroll
-            for (int a = 0; a < 5; ++a) q[a] = __ldg(reinterpret_cast<const float4 *>(ep.Q + a * plane) + i4);
+        for (int i = 0; i < kLeafGroup; ++i)
+            bl[i] = reinterpret_cast<const float4 *>(node_belief(pl, ep, l, first + min(i, cnt - 1)));
+        const float4 *q4 = reinterpret_cast<const float4 *>(ep.Q);
+        const int n4p = static_cast<int>(plane >> 2);
+        constexpr int kLeafUnroll = 4;
+        for (int i4 = c0 + threadIdx.x; i4 < c1; i4 += kLeafUnroll * blockDim.x) {
+            float4 bv[kLeafUnroll][kLeafGroup];
 #pragma unroll
-            for (int i = 0; i < kLeafGroup; ++i) {
-                if (i < cnt) {
-                    const float4 b = __ldcs(reinterpret_cast<const float4 *>(node_belief(pl, ep, l, first + i)) + i4);
+            for (int u = 0; u < kLeafUnroll; ++u) {
+                const int j4 = i4 + u * blockDim.x;
 #pragma unroll
-                    for (int a = 0; a < 5; ++a)
-                        acc[i][a] = fmaf(b.x, q[a].x, fmaf(b.y, q[a].y, fmaf(b.z, q[a].z, fmaf(b.w, q[a].w, acc[i][a]))));
+                for (int i = 0; i < kLeafGroup; ++i)
+                    bv[u][i] = (j4 < c1 && i < cnt) ? __ldcs(bl[i] + j4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kLeafUnroll; ++u) {
+                const int j4 = i4 + u * blockDim.x;
+                if (j4 >= c1) break;
+#pragma unroll
+                for (int a = 0; a < 5; ++a) {
+                    const float4 q = __ldg(q4 + a * n4p + j4);
+#pragma unroll
+                    for (int i = 0; i < kLeafGroup; ++i)
+                        acc[i][a] = fmaf(bv[u][i].x, q.x,
+                                         fmaf(bv[u][i].y, q.y, fmaf(bv[u][i].z, q.z, fmaf(bv[u][i].w, q.w, acc[i][a]))));
                 }
             }
         }
