@@ -159,7 +159,62 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
         torch.cuda.empty_cache()
     # (4) the gradient of the root value on the 128x128 differentiation workload
     out["gradient_diff_128"] = gradient_measurement(args, dev, K, peak)
+    # (5) the single-belief primitives of the C ABI on inputs larger than L2
+    out["primitives"] = primitive_measurement(args, dev, K, peak)
     return out
+
+
+def primitive_measurement(args, dev, K, peak):
+    """belief_predict and belief_correct on one 16384x2048 belief (128 MiB,
+    larger than L2), leaf_value on 256 beliefs of 512x512 (256 MiB): device
+    time per call with CUDA events, algorithmic bytes / time against the
+    measured HBM bandwidth."""
+    import torch
+    from paper_1810_00204_gb300 import api, workloads as WL
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    res = {}
+    w = WL.tiny(args.seed, H=16384, W=2048)
+    m = api.Model(w, device=dev)
+    N = m.H * m.P
+    b = torch.rand((m.H, m.P), device=dev) * (m.occ == 0)
+    b /= b.sum()
+    out = torch.empty_like(b)
+    ms = timed(lambda: api.belief_predict(m, b, 1, out), K)
+    nbytes = N * (4 + 4 + 2)  # belief in, predicted belief out, cell words
+    res["belief_predict"] = {"cells": N, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
+                             "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
+    pz = torch.empty(1, dtype=torch.float32, device=dev)
+    ms = timed(lambda: api.belief_correct_noalloc(m, out, 2, b, pz) if N <= 4096 * 1024
+               else api.belief_correct(m, out, 2, b), K)
+    nbytes = N * (4 + 2) * 2 + N * 4  # P(z) pass and scale pass read bbar and the cell words; b' written
+    res["belief_correct"] = {"cells": N, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
+                             "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
+    del b, out
+    torch.cuda.empty_cache()
+    wl = WL.large(args.seed)
+    ml = api.Model(wl, device=dev)
+    Ql = api.mdp_value_iterate(ml, dtype="f32")["Q"]
+    n = 256
+    bl = torch.rand((n, ml.H, ml.P), device=dev) * (ml.occ == 0)
+    bl /= bl.sum(dim=(1, 2), keepdim=True)
+    Nl = ml.H * ml.P
+    ms = timed(lambda: api.leaf_value(ml, Ql, bl), K)
+    nbytes = n * Nl * 4 + 20 * Nl
+    res["leaf_value"] = {"beliefs": n, "cells": Nl, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
+                         "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
+    return res
 
 
 def gradient_measurement(args, dev, K, peak):

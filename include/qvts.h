@@ -173,7 +173,8 @@ qv_status belief_predict(const qv_model_t *model, const float *d_b, int32_t acti
                          float *d_bbar, qv_stream_t stream);
 
 /* belief_correct: b'(y) = O(y, z) bbar(y) / P(z), P(z) = sum_y O(y, z) bbar(y)
- * (Eq. 3); writes P(z) to the device scalar d_pz. */
+ * (Eq. 3); writes P(z) to the device scalar d_pz.  d_bbar and d_bout are
+ * 16-byte aligned (QV_ERR_INVALID otherwise). */
 size_t belief_correct_workspace_bytes(const qv_model_t *model);
 qv_status belief_correct(const qv_model_t *model, const float *d_bbar, int32_t z,
                          float *d_bout, float *d_pz, void *d_ws, size_t ws_bytes,

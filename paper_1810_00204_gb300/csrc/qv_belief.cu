@@ -64,6 +64,18 @@ __global__ void __launch_bounds__(256) k_predict(ModelArgs m, const float *__res
     }
 }
 
+// O(y, z) bbar(y) for the four cells of a float4 group (0 off the free cells).
+__device__ __forceinline__ float4 weigh4(const ModelArgs &m, float4 v, ushort4 c, int z) {
+    float4 o;
+    o.x = QV_CELL_FREE(c.x) ? v.x * (static_cast<int>(QV_CELL_LABEL(c.x)) == z ? m.acc : m.eta) : 0.0f;
+    o.y = QV_CELL_FREE(c.y) ? v.y * (static_cast<int>(QV_CELL_LABEL(c.y)) == z ? m.acc : m.eta) : 0.0f;
+    o.z = QV_CELL_FREE(c.z) ? v.z * (static_cast<int>(QV_CELL_LABEL(c.z)) == z ? m.acc : m.eta) : 0.0f;
+    o.w = QV_CELL_FREE(c.w) ? v.w * (static_cast<int>(QV_CELL_LABEL(c.w)) == z ? m.acc : m.eta) : 0.0f;
+    return o;
+}
+
+constexpr int kStreamUnroll = 4;  // float4 groups whose loads a thread issues together
+
 // P(z) = sum_y O(y, z) bbar(y): per-CTA partial sums, the last CTA adds them
 // in CTA order and writes the scalar.
 __global__ void __launch_bounds__(256) k_obs_partial(ModelArgs m, const float *__restrict__ bbar, int z,
@@ -71,11 +83,24 @@ __global__ void __launch_bounds__(256) k_obs_partial(ModelArgs m, const float *_
                                                      float *__restrict__ pz) {
     __shared__ float s_red[8];
     __shared__ int s_last;
+    const float4 *b4 = reinterpret_cast<const float4 *>(bbar);
+    const ushort4 *c4 = reinterpret_cast<const ushort4 *>(m.cell);
+    const int ng = m.N >> 2, stride = gridDim.x * blockDim.x;
     float acc = 0.0f;
-    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < m.N; y += gridDim.x * blockDim.x) {
-        const unsigned cw = __ldg(m.cell + y);
-        const float v = QV_CELL_FREE(cw) ? __ldg(bbar + y) : 0.0f;
-        acc = fmaf(static_cast<int>(QV_CELL_LABEL(cw)) == z ? m.acc : m.eta, v, acc);
+    for (int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < ng; g0 += kStreamUnroll * stride) {
+        float4 v[kStreamUnroll];
+        ushort4 c[kStreamUnroll];
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const int g = g0 + u * stride;
+            v[u] = g < ng ? __ldcs(b4 + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+            c[u] = g < ng ? __ldg(c4 + g) : make_ushort4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const float4 o = weigh4(m, v[u], c[u], z);
+            acc += (o.x + o.y) + (o.z + o.w);
+        }
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
@@ -100,26 +125,56 @@ __global__ void __launch_bounds__(256) k_obs_partial(ModelArgs m, const float *_
 __global__ void __launch_bounds__(256) k_correct_scale(ModelArgs m, const float *__restrict__ bbar, int z,
                                                        const float *__restrict__ pz, float *__restrict__ out) {
     const float inv = 1.0f / __ldcg(pz);
-    for (int y = blockIdx.x * blockDim.x + threadIdx.x; y < m.N; y += gridDim.x * blockDim.x) {
-        const unsigned cw = __ldg(m.cell + y);
-        const float v = QV_CELL_FREE(cw) ? __ldg(bbar + y) : 0.0f;
-        out[y] = v * (static_cast<int>(QV_CELL_LABEL(cw)) == z ? m.acc : m.eta) * inv;
+    const float4 *b4 = reinterpret_cast<const float4 *>(bbar);
+    const ushort4 *c4 = reinterpret_cast<const ushort4 *>(m.cell);
+    float4 *o4 = reinterpret_cast<float4 *>(out);
+    const int ng = m.N >> 2, stride = gridDim.x * blockDim.x;
+    for (int g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < ng; g0 += kStreamUnroll * stride) {
+        float4 v[kStreamUnroll];
+        ushort4 c[kStreamUnroll];
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const int g = g0 + u * stride;
+            v[u] = g < ng ? __ldcs(b4 + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+            c[u] = g < ng ? __ldg(c4 + g) : make_ushort4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const int g = g0 + u * stride;
+            if (g < ng) {
+                const float4 o = weigh4(m, v[u], c[u], z);
+                __stcs(o4 + g, make_float4(o.x * inv, o.y * inv, o.z * inv, o.w * inv));
+            }
+        }
     }
 }
 
-// One CTA per belief: max_a sum_y b(y) Q[a][y].
-__global__ void __launch_bounds__(256) k_leaf_prim(ModelArgs m, const float *__restrict__ Q,
-                                                   const float *__restrict__ b, float *__restrict__ value) {
-    __shared__ float s_red[8][5];
-    const float *bi = b + static_cast<long long>(blockIdx.x) * m.N;
+// One CTA of kLeafThreads per belief: max_a sum_y b(y) Q[a][y], with the
+// loads of kStreamUnroll float4 columns issued before their arithmetic.
+constexpr int kLeafThreads = 1024;
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_prim(ModelArgs m, const float *__restrict__ Q,
+                                                            const float *__restrict__ b, float *__restrict__ value) {
+    __shared__ float s_red[kLeafThreads / 32][5];
+    const float4 *bi = reinterpret_cast<const float4 *>(b + static_cast<long long>(blockIdx.x) * m.N);
+    const float4 *q4 = reinterpret_cast<const float4 *>(Q);
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int n4 = m.N >> 2;
-    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(bi) + i);
+    for (int i0 = threadIdx.x; i0 < n4; i0 += kStreamUnroll * blockDim.x) {
+        float4 v[kStreamUnroll];
 #pragma unroll
-        for (int a = 0; a < 5; ++a) {
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(Q + static_cast<long long>(a) * m.N) + i);
-            acc[a] = fmaf(v.x, q.x, fmaf(v.y, q.y, fmaf(v.z, q.z, fmaf(v.w, q.w, acc[a]))));
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const int i = i0 + u * blockDim.x;
+            v[u] = i < n4 ? __ldcs(bi + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < kStreamUnroll; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= n4) break;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) {
+                const float4 q = __ldg(q4 + static_cast<long long>(a) * n4 + i);
+                acc[a] = fmaf(v[u].x, q.x, fmaf(v[u].y, q.y, fmaf(v[u].z, q.z, fmaf(v[u].w, q.w, acc[a]))));
+            }
         }
     }
 #pragma unroll
@@ -179,6 +234,9 @@ extern "C" qv_status belief_correct(const qv_model_t *m, const float *d_bbar, in
     if (st != QV_OK) return st;
     if (!d_bbar || !d_bout || !d_pz || !d_ws) return qv_set_error(QV_ERR_INVALID, "belief_correct: null pointer");
     if (z < 0 || z > m->num_beacons) return qv_set_error(QV_ERR_INVALID, "belief_correct: z %d", z);
+    if (((reinterpret_cast<uintptr_t>(d_bbar) | reinterpret_cast<uintptr_t>(d_bout)) & 15) ||
+        (reinterpret_cast<uintptr_t>(m->d_cell) & 7))
+        return qv_set_error(QV_ERR_INVALID, "belief_correct: beliefs must be 16-byte aligned, cell words 8-byte");
     if (ws_bytes < belief_correct_workspace_bytes(m))
         return qv_set_error(QV_ERR_WORKSPACE, "belief_correct: workspace %zu bytes too small", ws_bytes);
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -238,6 +296,10 @@ extern "C" qv_status belief_correct_noalloc(const qv_model_t *m, const float *d_
     if (st != QV_OK) return st;
     if (!d_bbar || !d_bout || !d_pz) return qv_set_error(QV_ERR_INVALID, "belief_correct_noalloc: null pointer");
     if (z < 0 || z > m->num_beacons) return qv_set_error(QV_ERR_INVALID, "belief_correct_noalloc: z %d", z);
+    if (((reinterpret_cast<uintptr_t>(d_bbar) | reinterpret_cast<uintptr_t>(d_bout)) & 15) ||
+        (reinterpret_cast<uintptr_t>(m->d_cell) & 7))
+        return qv_set_error(QV_ERR_INVALID,
+                            "belief_correct_noalloc: beliefs must be 16-byte aligned, cell words 8-byte");
     const long long cells = static_cast<long long>(m->H) * m->pitch;
     if (cells > QV_NOALLOC_MAX_CELLS)
         return qv_set_error(QV_ERR_INVALID,
@@ -268,6 +330,7 @@ extern "C" qv_status leaf_value(const qv_model_t *m, const float *d_Q, const flo
     if (n == 0) return QV_OK;
     if ((reinterpret_cast<uintptr_t>(d_Q) | reinterpret_cast<uintptr_t>(d_b)) & 15)
         return qv_set_error(QV_ERR_INVALID, "leaf_value: buffers must be 16-byte aligned");
-    qv::k_leaf_prim<<<n, 256, 0, static_cast<cudaStream_t>(stream)>>>(qv::model_args(m), d_Q, d_b, d_value);
+    qv::k_leaf_prim<<<n, qv::kLeafThreads, 0, static_cast<cudaStream_t>(stream)>>>(qv::model_args(m), d_Q, d_b,
+                                                                                     d_value);
     return qv_check_cuda(cudaGetLastError(), "leaf_value launch");
 }
