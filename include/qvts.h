@@ -226,6 +226,14 @@ qv_status qv_plan_run(qv_plan_t *plan, qv_stream_t stream);
  * later qv_plan_run calls launch the graph. */
 qv_status qv_plan_capture_graph(qv_plan_t *plan, qv_stream_t stream);
 qv_status qv_plan_read(qv_plan_t *plan, qv_plan_result_t *h_results, qv_stream_t stream);
+/* The same read in two steps, so that many plans' results come back with one
+ * synchronisation: qv_plan_read_async enqueues the copy of the plan's
+ * qv_plan_readback_bytes result bytes into h_buf (pinned host memory for the
+ * copy to be asynchronous); once the stream has passed it, qv_plan_decode
+ * turns them into the E results and the run's status, as qv_plan_read does. */
+size_t qv_plan_readback_bytes(const qv_plan_t *plan);
+qv_status qv_plan_read_async(const qv_plan_t *plan, void *h_buf, qv_stream_t stream);
+qv_status qv_plan_decode(qv_plan_t *plan, const void *h_buf, qv_plan_result_t *h_results);
 
 /* Run the plan once without the graph, with a CUDA event recorded on
  * `stream` before the first launch and after every launch; returns for each

@@ -84,6 +84,9 @@ SIGNATURES = {
     "qv_plan_run": (C.c_int, [_vp, _vp]),
     "qv_plan_capture_graph": (C.c_int, [_vp, _vp]),
     "qv_plan_read": (C.c_int, [_vp, C.POINTER(qv_plan_result_t), _vp]),
+    "qv_plan_readback_bytes": (_sz, [_vp]),
+    "qv_plan_read_async": (C.c_int, [_vp, _vp, _vp]),
+    "qv_plan_decode": (C.c_int, [_vp, _vp, C.POINTER(qv_plan_result_t)]),
     "qv_plan_destroy": (None, [_vp]),
     "qv_plan_profile": (C.c_int, [_vp, C.POINTER(qv_launch_time_t), _i32, C.POINTER(C.c_int32), _vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),

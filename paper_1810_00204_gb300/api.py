@@ -251,6 +251,21 @@ class Plan:
         check(lib().qv_plan_read(self.handle, res, _stream(stream)), "qv_plan_read")
         return [_result_dict(res[e], self.depth) for e in range(self.E)]
 
+    def readback_buffer(self) -> torch.Tensor:
+        """Pinned host bytes for read_async."""
+        return torch.empty(lib().qv_plan_readback_bytes(self.handle), dtype=torch.uint8).pin_memory()
+
+    def read_async(self, buf: torch.Tensor, stream=None):
+        """Enqueue the copy of this plan's results into `buf` (no synchronisation)."""
+        check(lib().qv_plan_read_async(self.handle, C.c_void_p(buf.data_ptr()), _stream(stream)),
+              "qv_plan_read_async")
+
+    def decode(self, buf: torch.Tensor) -> List[dict]:
+        """Results from a buffer filled by read_async, once the stream has passed the copy."""
+        res = (N.qv_plan_result_t * self.E)()
+        check(lib().qv_plan_decode(self.handle, C.c_void_p(buf.data_ptr()), res), "qv_plan_decode")
+        return [_result_dict(res[e], self.depth) for e in range(self.E)]
+
     def profile(self, stream=None) -> List[dict]:
         """One eager run with a CUDA event after every launch (synchronises)."""
         out = (N.qv_launch_time_t * 64)()

@@ -529,18 +529,21 @@ extern "C" qv_status qv_plan_capture_graph(qv_plan_t *pl, qv_stream_t stream) {
     return qv_check_cuda(ie, "graph instantiate");
 }
 
-extern "C" qv_status qv_plan_read(qv_plan_t *pl, qv_plan_result_t *h, qv_stream_t stream) {
-    if (!pl || !h) return qv_set_error(QV_ERR_INVALID, "qv_plan_read: null pointer");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+extern "C" size_t qv_plan_readback_bytes(const qv_plan_t *pl) { return pl ? pl->read_bytes : 0; }
+
+extern "C" qv_status qv_plan_read_async(const qv_plan_t *pl, void *h_buf, qv_stream_t stream) {
+    if (!pl || !h_buf) return qv_set_error(QV_ERR_INVALID, "qv_plan_read_async: null pointer");
+    return qv_check_cuda(cudaMemcpyAsync(h_buf, pl->ws + pl->read_off, pl->read_bytes, cudaMemcpyDeviceToHost,
+                                         static_cast<cudaStream_t>(stream)),
+                         "qv_plan_read_async");
+}
+
+extern "C" qv_status qv_plan_decode(qv_plan_t *pl, const void *h_buf, qv_plan_result_t *h) {
+    if (!pl || !h_buf || !h) return qv_set_error(QV_ERR_INVALID, "qv_plan_decode: null pointer");
     const int E = pl->E, D = pl->params.depth;
-    // level sizes, root results, status and boundary count in one copy
-    std::vector<char> buf(pl->read_bytes);
-    if (qv_check_cuda(cudaMemcpyAsync(buf.data(), pl->ws + pl->read_off, pl->read_bytes, cudaMemcpyDeviceToHost, st),
-                      "read results") != QV_OK ||
-        qv_check_cuda(cudaStreamSynchronize(st), "qv_plan_read") != QV_OK)
-        return QV_ERR_CUDA;
+    const char *buf = static_cast<const char *>(h_buf);
     auto at_host = [&](const void *dev_ptr) {
-        return buf.data() + (static_cast<const char *>(dev_ptr) - (pl->ws + pl->read_off));
+        return buf + (static_cast<const char *>(dev_ptr) - (pl->ws + pl->read_off));
     };
     const qv::ResultDev *r = reinterpret_cast<const qv::ResultDev *>(at_host(pl->dev.result));
     const int *cnt = reinterpret_cast<const int *>(at_host(pl->dev.count));
@@ -561,6 +564,15 @@ extern "C" qv_status qv_plan_read(qv_plan_t *pl, qv_plan_result_t *h, qv_stream_
     if (status & qv::kErrTimeout) return qv_set_error(QV_ERR_TIMEOUT, "qv_plan: a bounded device wait timed out");
     if (status & qv::kErrCapacity) return qv_set_error(QV_ERR_CAPACITY, "qv_plan: a level outgrew its capacity");
     return QV_OK;
+}
+
+extern "C" qv_status qv_plan_read(qv_plan_t *pl, qv_plan_result_t *h, qv_stream_t stream) {
+    if (!pl || !h) return qv_set_error(QV_ERR_INVALID, "qv_plan_read: null pointer");
+    std::vector<char> buf(pl->read_bytes);
+    if (qv_plan_read_async(pl, buf.data(), stream) != QV_OK ||
+        qv_check_cuda(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "qv_plan_read") != QV_OK)
+        return QV_ERR_CUDA;
+    return qv_plan_decode(pl, buf.data(), h);
 }
 
 extern "C" void qv_plan_destroy(qv_plan_t *pl) {

@@ -298,3 +298,21 @@ def test_batched_matches_plain(api):
         if o["boundary_count"] == 0:
             assert batch[e]["nodes_per_level"] == [int(x) for x in o["n_level"]]
             assert abs(batch[e]["value"] - o["root_value"]) <= REL * max(1.0, abs(o["root_value"]))
+
+
+def test_async_readback_matches_read(api):
+    w = WL.mid(0)
+    m = api.Model(w)
+    Qd = m.to_grid(_oracle_Q(w).reshape(5, w.H, w.W))
+    plans = [api.Plan([m], [Qd], [m.b0()], depth=3, K=8, seed=0, episode=e) for e in range(3)]
+    bufs = [p.readback_buffer() for p in plans]
+    for p, b in zip(plans, bufs):
+        p.run()
+        p.read_async(b)
+    torch.cuda.current_stream().synchronize()
+    got = [p.decode(b)[0] for p, b in zip(plans, bufs)]
+    ref = [p.read()[0] for p in plans]
+    for g, r in zip(got, ref):
+        assert g["nodes_per_level"] == r["nodes_per_level"]
+        assert g["value"] == r["value"] and g["action"] == r["action"]
+        assert np.array_equal(g["q"], r["q"])
