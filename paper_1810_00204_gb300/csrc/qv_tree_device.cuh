@@ -1016,7 +1016,7 @@ __device__ bool phase_update(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, 
                         o.y = outs[1][a] * (lab[1] == z ? sa : se);
                         o.z = outs[2][a] * (lab[2] == z ? sa : se);
                         o.w = outs[3][a] * (lab[3] == z ? sa : se);
-                        *reinterpret_cast<float4 *>(child0 + static_cast<long long>(c) * N + y) = o;
+                        __stcs(reinterpret_cast<float4 *>(child0 + static_cast<long long>(c) * N + y), o);
                     }
                 }
             }
