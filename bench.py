@@ -634,9 +634,16 @@ def main():
         O.build()
         oq = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)
         n, el = oracle_plans(eps, oq, args.cpu_seconds)
-        cpu = {"value": n / el, "unit": "plans/s", "cores": O.num_threads(), "kind": "oracle",
+        cores = O.num_threads()
+        # the same oracle on one thread, on a quarter of the time budget
+        O.set_threads(1)
+        n1, el1 = oracle_plans(eps, oq, max(args.cpu_seconds / 4, 0.1))
+        O.set_threads(cores)
+        cpu = {"value": n / el, "unit": "plans/s", "cores": cores, "kind": "oracle",
+               "single_thread_value": n1 / el1,
                "sample": f"{n} plans of this workload (same map, {len(eps)} start cells cycled), "
-                         f"{el:.1f} s, FP64 C oracle with OpenMP over tree nodes"}
+                         f"{el:.1f} s, FP64 C oracle with OpenMP over tree nodes; single thread: {n1} plans "
+                         f"in {el1:.1f} s"}
         if extra is not None and "gradient_diff_128" in extra:
             # the oracle's reverse mode on the same differentiation workload, one gradient
             from paper_1810_00204_gb300 import workloads as WLd

@@ -73,6 +73,8 @@ def lib():
                                    vp, vp, C.c_int] + [vp] * 16
         L.or_tree_plan.restype = C.c_int
         L.or_num_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
+        L.or_set_threads.restype = None
         L.or_transition_row_dslip.argtypes = [P, C.c_int, C.c_int, vp, vp]
         L.or_transition_row_dslip.restype = C.c_int
         L.or_tree_backward.argtypes = [P, vp, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -365,3 +367,8 @@ def root_value_grad(w, sweeps, depth=None, K=None, seed=None, episode=None, repl
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops from now on."""
+    lib().or_set_threads(int(n))

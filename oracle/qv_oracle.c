@@ -27,6 +27,16 @@ int or_num_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops from now on (timing single- and
+ * multi-threaded runs of the same process). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 static int is_free(const or_problem *p, int r, int c) {
     if (r < 0 || r >= p->H || c < 0 || c >= p->W) return 0;  /* outside = occupied */
     return p->occ[r * p->W + c] == 0;

@@ -99,5 +99,6 @@ int or_vi_backward(const or_problem *p, int sweeps, const double *Qbar, double *
                    double *dslip, double *dcost);
 
 int or_num_threads(void);
+void or_set_threads(int n);
 
 #endif
