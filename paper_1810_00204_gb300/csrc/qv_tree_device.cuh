@@ -137,6 +137,15 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Arrival on a last-arriver counter: an acquire-release add, so that (after
+// a CTA barrier) it publishes the CTA's writes and, for the last arriver,
+// makes the earlier arrivals' writes visible.
+__device__ __forceinline__ unsigned arrive_acq_rel(unsigned *p) {
+    unsigned prev;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(p) : "memory");
+    return prev;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -444,7 +453,6 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
         for (int a = 1; a < 5; ++a) best = fmaxf(best, S.uq[a]);
         pl.value[ep.node_base[l] + local] = best;
     }
-    __threadfence();
     __syncthreads();
 }
 
@@ -478,7 +486,6 @@ __device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e
         nn = cap;
     }
     if (threadIdx.x == 0) pl.count[(l + 1) * pl.E + e] = nn;
-    __threadfence();
     __syncthreads();
 }
 
@@ -537,7 +544,6 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         pl.wb_upd[l1 * (E + 1) + E] = wu;
         if (l1 == pl.depth) pl.wb_leaf[E] = wl;
     }
-    __threadfence();
 }
 
 // A node of episode e at level l is final: the last one numbers the
@@ -545,24 +551,24 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
 __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem &S) {
     if (threadIdx.x == 0) {
         const int n = __ldcg(pl.count + l * pl.E + e);
-        const unsigned prev = atomicAdd(pl.ep_cnt + l * pl.E + e, 1u);
+        const unsigned prev = arrive_acq_rel(pl.ep_cnt + l * pl.E + e);
         const int last = prev == static_cast<unsigned>(n - 1);
         if (last) pl.ep_cnt[l * pl.E + e] = 0u;
         S.flags[1] = last;
     }
     __syncthreads();
     if (!S.flags[1]) return;
-    __threadfence();
     compact_episode(pl, l, ep, e, S);
-    if (threadIdx.x == 0) {
-        const unsigned prev = atomicAdd(pl.lvl_cnt + l, 1u);
-        const int last = prev == static_cast<unsigned>(pl.E - 1);
-        if (last) pl.lvl_cnt[l] = 0u;
-        S.flags[2] = last;
+    if (pl.E > 1) {  // with one episode its last node is the level's last
+        if (threadIdx.x == 0) {
+            const unsigned prev = arrive_acq_rel(pl.lvl_cnt + l);
+            const int last = prev == static_cast<unsigned>(pl.E - 1);
+            if (last) pl.lvl_cnt[l] = 0u;
+            S.flags[2] = last;
+        }
+        __syncthreads();
+        if (!S.flags[2]) return;
     }
-    __syncthreads();
-    if (!S.flags[2]) return;
-    __threadfence();
     level_prefix(pl, l + 1, S);
     __syncthreads();
 }
@@ -897,10 +903,9 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
                 } else v = S.tot[i - 5 * B - hq];
                 rec[i] = v;
             }
-            __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
-                const unsigned prev = atomicAdd(pl.node_cnt + iid, 1u);
+                const unsigned prev = arrive_acq_rel(pl.node_cnt + iid);
                 const int last = prev == static_cast<unsigned>(items - 1);
                 if (last) pl.node_cnt[iid] = 0u;
                 S.flags[0] = last;
@@ -913,7 +918,6 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
 #endif
                 continue;
             }
-            __threadfence();
             // the last item sums every record of the node in item order
             const float *base = pl.partials + static_cast<long long>(w0e + local * items) * pl.rec_len;
             for (int i = threadIdx.x; i < nrec; i += blockDim.x) {
@@ -1109,18 +1113,16 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
         if (C > 1) {
             float *rec = pl.partials + static_cast<long long>(w) * pl.rec_len;
             if (threadIdx.x < kLeafGroup * 5) rec[threadIdx.x] = S.tot[threadIdx.x];
-            __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
                 const unsigned key = static_cast<unsigned>(w / C);
-                const unsigned prev = atomicAdd(pl.leaf_cnt + key, 1u);
+                const unsigned prev = arrive_acq_rel(pl.leaf_cnt + key);
                 const int last = prev == static_cast<unsigned>(C - 1);
                 if (last) pl.leaf_cnt[key] = 0u;
                 S.flags[3] = last;
             }
             __syncthreads();
             if (!S.flags[3]) continue;
-            __threadfence();
             if (threadIdx.x < kLeafGroup * 5) {
                 const float *base = pl.partials + static_cast<long long>(w - chunk) * pl.rec_len;
                 float t = 0.0f;
