@@ -113,6 +113,7 @@ struct PlanDev {
     ResultDev *result; // [E]
     const int *replay;
     unsigned spin_limit;  // polls before a wait on other CTAs gives up
+    EpDev ep0;            // the descriptor of a one-episode plan, in parameter space
 };
 
 }  // namespace qv

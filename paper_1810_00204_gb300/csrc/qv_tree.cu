@@ -390,6 +390,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
+    d.ep0 = L.eps[0];
     pl->reset_off = L.off_status;
     pl->reset_bytes = L.off_beliefs - L.off_status;
     pl->read_off = L.off_count;

@@ -118,9 +118,14 @@ __device__ __forceinline__ void fill_self_lut(float *lut, float slip) {
 __device__ __forceinline__ void load_ep(const PlanDev &pl, int e, Smem &S, int &cur_e) {
     if (e == cur_e) return;
     __syncthreads();
-    const int4 *src = reinterpret_cast<const int4 *>(pl.eps + e);
     int4 *dst = reinterpret_cast<int4 *>(S.ep);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(EpDev) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    if (pl.E == 1) {  // from the kernel's parameters, no global round trip
+        const int4 *src = reinterpret_cast<const int4 *>(&pl.ep0);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(EpDev) / 16); i += blockDim.x) dst[i] = src[i];
+    } else {
+        const int4 *src = reinterpret_cast<const int4 *>(pl.eps + e);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(EpDev) / 16); i += blockDim.x) dst[i] = __ldg(src + i);
+    }
     __syncthreads();
     const EpDev &ep = *S.ep;
     for (int k = threadIdx.x; k < ep.B; k += blockDim.x) {
