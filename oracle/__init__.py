@@ -82,6 +82,10 @@ def lib():
         L.or_tree_backward.restype = C.c_int
         L.or_vi_backward.argtypes = [P, C.c_int, vp, vp, vp, vp]
         L.or_vi_backward.restype = C.c_int
+        L.or_fib_sweep.argtypes = [P, vp, vp, vp, vp]
+        L.or_fib_sweep.restype = C.c_double
+        L.or_fib_iteration.argtypes = [P, C.c_double, C.c_int, C.c_int, vp, vp, vp, vp]
+        L.or_fib_iteration.restype = C.c_int
         _lib = L
     return _lib
 
@@ -152,6 +156,35 @@ def value_iteration(w, tol=None, max_sweeps=100000, truncated=None, **kw):
                                   C.byref(sw), C.byref(res), _p(hist))
     return dict(V=V, Q=Q.reshape(A, p.n), sweeps=sw.value, residual=res.value,
                 hist=hist[:sw.value].copy(), converged=(st == 0))
+
+
+def fib_iteration(w, tol=None, max_sweeps=100000, truncated=None, **kw):
+    """Fast Informed Bound alpha-vectors (Sec. IV-A, Eq. 7) by Jacobi sweeps
+    from alpha_0 = 0.  Returns dict(alpha [5][n], sweeps, residual, hist,
+    converged).  V_FIB(b) (Eq. 6's value) is leaf_value(w, alpha, b)."""
+    p = _prob(w, **kw)
+    ww = p.w
+    tol = ww.vi_tol if tol is None else tol
+    truncated = ww.vi_truncated if truncated is None else truncated
+    alpha = np.zeros(A * p.n, np.float64)
+    sw = C.c_int(0)
+    res = C.c_double(0)
+    hist = np.zeros(max(truncated, max_sweeps) + 1, np.float64)
+    st = lib().or_fib_iteration(p.ref, tol, max_sweeps, truncated, _p(alpha), C.byref(sw),
+                                C.byref(res), _p(hist))
+    return dict(alpha=alpha.reshape(A, p.n), sweeps=sw.value, residual=res.value,
+                hist=hist[:sw.value].copy(), converged=(st == 0))
+
+
+def fib_sweep(w, alpha, **kw):
+    """One application of Eq. 7 to alpha [5][n]; returns (alpha', max change)."""
+    p = _prob(w, **kw)
+    label = labels(p)
+    R = np.ascontiguousarray(reward_table(p).reshape(-1))
+    a = np.ascontiguousarray(np.asarray(alpha, np.float64).reshape(-1))
+    out = np.zeros(A * p.n, np.float64)
+    res = lib().or_fib_sweep(p.ref, _p(label), _p(R), _p(a), _p(out))
+    return out.reshape(A, p.n), res
 
 
 def predict(w, b, a):

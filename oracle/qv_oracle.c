@@ -679,3 +679,75 @@ int or_vi_backward(const or_problem *p, int sweeps, const double *Qbar, double *
     free(R); free(V); free(astar); free(lam); free(lam_prev);
     return 0;
 }
+
+/* ---- Fast Informed Bound (Sec. IV-A) ---------------------------------- */
+
+/* One application of the FIB alpha-vector Bellman operator, Eq. 7:
+ *   alpha'^a(x) = R(x, a) + gamma sum_z max_a' sum_x' O(x', z) T(x, a, x') alpha^a'(x')
+ * for every free, non-goal cell x and action a; the sum over x' runs over
+ * the support of T(x, a, .) (every other term is zero) and z over all B + 1
+ * observations.  The goal and occupied cells keep alpha = 0, as V does in
+ * the value iteration (absorbing, nothing earned there).  alpha, out: [5*n],
+ * action-major.  Returns max |out - alpha| over every (a, x).              */
+double or_fib_sweep(const or_problem *p, const int *label, const double *R, const double *alpha,
+                    double *out) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS, nz = p->B + 1;
+    double res = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : res)
+    for (int x = 0; x < n; ++x) {
+        for (int a = 0; a < A; ++a) {
+            double v = 0.0;
+            if (!p->occ[x] && x != p->goal) {
+                int y[3]; double pr[3];
+                const int m = or_transition_row(p, x, a, y, pr);
+                double sz = 0.0;
+                for (int z = 0; z < nz; ++z) {
+                    double best = -HUGE_VAL;
+                    for (int b = 0; b < A; ++b) {
+                        double s = 0.0;
+                        for (int j = 0; j < m; ++j)
+                            s += or_obs_lik(p, label, y[j], z) * pr[j] * alpha[b * n + y[j]];
+                        if (s > best) best = s;
+                    }
+                    sz += best;
+                }
+                v = R[a * n + x] + p->gamma * sz;
+            }
+            out[a * n + x] = v;
+            const double d = fabs(v - alpha[a * n + x]);
+            if (d > res) res = d;
+        }
+    }
+    return res;
+}
+
+/* FIB value iteration (Sec. IV-A: Eq. 7 is a monotone contraction, so Jacobi
+ * sweeps converge): alpha_0 = 0, alpha_{k+1} = Eq. 7 applied to alpha_k;
+ * stops at the first sweep whose max-abs change is below tol, or after
+ * exactly `truncated` sweeps when truncated > 0.  Returns 0, or 1 when
+ * max_sweeps ran out first.  alpha: [5*n]; residual_hist nullable.        */
+int or_fib_iteration(const or_problem *p, double tol, int max_sweeps, int truncated, double *alpha,
+                     int *sweeps, double *residual, double *residual_hist) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS;
+    int *label = (int *)malloc(sizeof(int) * n);
+    double *R = (double *)malloc(sizeof(double) * A * n);
+    double *next = (double *)malloc(sizeof(double) * A * n);
+    or_labels(p, label);
+    or_reward_table(p, R);
+    for (int i = 0; i < A * n; ++i) alpha[i] = 0.0;
+    const int limit = truncated > 0 ? truncated : max_sweeps;
+    int k = 0, status = 1;
+    double res = 0.0;
+    while (k < limit) {
+        res = or_fib_sweep(p, label, R, alpha, next);
+        memcpy(alpha, next, sizeof(double) * A * n);
+        if (residual_hist) residual_hist[k] = res;
+        ++k;
+        if (truncated <= 0 && res < tol) { status = 0; break; }
+    }
+    if (truncated > 0) status = 0;
+    *sweeps = k;
+    *residual = res;
+    free(label); free(R); free(next);
+    return status;
+}

@@ -98,6 +98,16 @@ int or_tree_backward(const or_problem *p, const double *Q, int depth, int K, con
 int or_vi_backward(const or_problem *p, int sweeps, const double *Qbar, double *Rbar,
                    double *dslip, double *dcost);
 
+/* ---- Fast Informed Bound (Sec. IV-A, Eq. 6-7) ---- */
+/* One application of Eq. 7 to alpha [5*n] -> out [5*n]; R from
+ * or_reward_table, label from or_labels.  Returns max |out - alpha|.       */
+double or_fib_sweep(const or_problem *p, const int *label, const double *R, const double *alpha,
+                    double *out);
+/* Jacobi iteration of Eq. 7 from alpha_0 = 0 (same stopping rule as
+ * or_value_iteration).  alpha [5*n]; residual_hist nullable.               */
+int or_fib_iteration(const or_problem *p, double tol, int max_sweeps, int truncated, double *alpha,
+                     int *sweeps, double *residual, double *residual_hist);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
