@@ -31,6 +31,11 @@ if ROOT not in sys.path:
 
 METRIC = "QV-Tree plans/sec and belief-state updates/sec (1 GB300) and % HBM peak"
 L2_FLUSH_BYTES = 256 << 20
+# algorithmic bytes of one offline sweep per cell (FP32, no cost map): the
+# value iteration reads and writes V and reads the cell word; the FIB
+# iteration reads and writes five alpha planes and reads the cell word
+VI_BYTES_PER_CELL = 4 + 4 + 2
+FIB_BYTES_PER_CELL = 5 * 4 + 5 * 4 + 2
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -73,6 +78,36 @@ def time_device(run, steps, flush, stream):
         ev1[k].record(stream)
     torch.cuda.synchronize()
     return sum(ev0[k].elapsed_time(ev1[k]) for k in range(steps))
+
+
+def time_offline(solve):
+    """(result, first-call ms, median ms of three later calls) of a solver
+    that synchronises (the value iteration, the FIB iteration)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = solve()
+    torch.cuda.synchronize()
+    first = 1e3 * (time.perf_counter() - t0)
+    runs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        r = solve()
+        torch.cuda.synchronize()
+        runs.append(1e3 * (time.perf_counter() - t0))
+    return r, first, statistics.median(runs)
+
+
+def offline_line(r, first_ms, ms, model, bytes_per_cell, peak):
+    """Sweeps, time and per-sweep bandwidth of an offline solve; the
+    algorithmic bytes of one sweep are `bytes_per_cell` for every cell of the
+    padded grid (values in and out, the cell word)."""
+    cells = model.H * model.P
+    sweep_s = ms / 1e3 / max(r["sweeps"], 1)
+    gbps = cells * bytes_per_cell / sweep_s / 1e9
+    return {"sweeps": r["sweeps"], "ms": ms, "first_call_ms": first_ms, "cells": model.H * model.W,
+            "us_per_sweep": 1e6 * sweep_s, "cell_sweeps_per_s": model.H * model.W * r["sweeps"] / (ms / 1e3),
+            "bytes_per_cell_sweep": bytes_per_cell, "GBps": gbps, "frac_of_measured_hbm": gbps / peak}
 
 
 def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
@@ -128,7 +163,12 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     # (3) 512x512, one plan per launch, fused and materialised leaves
     wl = WL.large(args.seed)
     ml = api.Model(wl, device=dev)
-    Ql = api.mdp_value_iterate(ml, dtype="f32")["Q"]
+    r, f, t = time_offline(lambda: api.mdp_value_iterate(ml, dtype="f32"))
+    Ql = r["Q"]
+    out["offline_512"] = {"vi": offline_line(r, f, t, ml, VI_BYTES_PER_CELL, peak)}
+    r, f, t = time_offline(lambda: api.fib_value_iterate(ml, dtype="f32", want_alpha=False))
+    out["offline_512"]["fib"] = offline_line(r, f, t, ml, FIB_BYTES_PER_CELL, peak)
+    del r
     Ncell = ml.H * ml.P
     for mode_name, mode in (("fused", N.QV_LEAF_FUSED), ("materialise", N.QV_LEAF_MATERIALISE)):
         api.autotune([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode, reps=3)
@@ -490,18 +530,8 @@ def main():
     # offline value iteration (once per map), timed on its own
     # (the first call in a process also loads the library's kernels: timed
     # apart from the steady-state solve)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    vi = api.mdp_value_iterate(model, dtype="f32")
-    torch.cuda.synchronize()
-    vi_first_ms = 1e3 * (time.perf_counter() - t0)
-    vi_runs = []
-    for _ in range(3):
-        t0 = time.perf_counter()
-        vi = api.mdp_value_iterate(model, dtype="f32")
-        torch.cuda.synchronize()
-        vi_runs.append(1e3 * (time.perf_counter() - t0))
-    vi_ms = statistics.median(vi_runs)
+    vi, vi_first_ms, vi_ms = time_offline(lambda: api.mdp_value_iterate(model, dtype="f32"))
+    fib, fib_first_ms, fib_ms = time_offline(lambda: api.fib_value_iterate(model, dtype="f32", want_alpha=False))
     Qd = vi["Q"]
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
     b0s = [model.to_grid(e.b0) for e in eps]
@@ -673,9 +703,10 @@ def main():
             "e2e": e2e,
             "gpu_launches": launches_per_plan * R * K,
             "clocks": clocks,
-            "vi": {"sweeps": vi["sweeps"], "ms": vi_ms, "first_call_ms": vi_first_ms, "cells": model.H * model.W,
-                   "cell_sweeps_per_s": model.H * model.W * vi["sweeps"] / (vi_ms / 1e3),
-                   "note": "offline, once per map; not part of plans/s; ms = median of 3 calls after the first"},
+            "vi": dict(offline_line(vi, vi_first_ms, vi_ms, model, VI_BYTES_PER_CELL, peak),
+                       note="offline, once per map; not part of plans/s; ms = median of 3 calls after the first"),
+            "fib": dict(offline_line(fib, fib_first_ms, fib_ms, model, FIB_BYTES_PER_CELL, peak),
+                        note="Fast Informed Bound alpha-vectors (Eq. 7), FP32; offline like vi"),
             "wall_s": wall,
             "extra": extra,
         }

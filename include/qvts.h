@@ -166,6 +166,28 @@ qv_status mdp_value_backward(const qv_model_t *model, int32_t sweeps, int32_t ev
                              const double *d_Vckpt, const double *d_Qbar, double *d_dslip,
                              double *d_dcost, void *d_ws, size_t ws_bytes, qv_stream_t stream);
 
+/* ---------------------------------------------------------------- FIB bound (Sec. IV-A)
+ * fib_value_iterate: the Fast Informed Bound alpha-vectors, one per action,
+ * by Jacobi sweeps of Eq. 7 from alpha_0 = 0:
+ *   alpha^a(x) = R(x, a) + gamma sum_z max_a' sum_x' O(x', z) T(x, a, x') alpha^a'(x'),
+ * with the same T, O and R as the rest of the library and alpha = 0 on the
+ * goal and on occupied cells.  Stops at the first sweep with
+ * max_{a,x} |alpha_{k+1} - alpha_k| < tol, or after exactly `truncated`
+ * sweeps when truncated > 0.  Outputs:
+ *   d_alpha  [5][H][pitch] in `dtype` (QV_F32 or QV_F64), nullable, 16-byte aligned
+ *   d_Q      [5][H][pitch] FP32 copy, the layout the tree search takes as its
+ *            leaf alpha-vectors: with it the leaf value max_a sum_x b(x) Q is
+ *            V_FIB(b) of Eq. 6, the upper bound U_V of Alg. 5.
+ * Synchronises the stream.  Returns QV_ERR_NOT_CONVERGED when max_sweeps ran
+ * out first, QV_ERR_INVALID for a pitch too wide to stage three rows of the
+ * five planes in shared memory (FP64 above pitch 1928; FP32 fits every
+ * width), QV_ERR_TIMEOUT when a wait on another CTA gave up. */
+size_t fib_value_iterate_workspace_bytes(const qv_model_t *model, int32_t dtype);
+qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
+                            int32_t max_sweeps, int32_t truncated, void *d_alpha, float *d_Q,
+                            void *d_ws, size_t ws_bytes, int32_t *sweeps_out,
+                            double *residual_out, qv_stream_t stream);
+
 /* ---------------------------------------------------------------- belief update (Eq. 3)
  * belief_predict: bbar(y) = sum_x T(x, action, y) b(x), the numerator of
  * Eq. 3.  Values stored on occupied cells of b are read as 0. */

@@ -71,6 +71,9 @@ SIGNATURES = {
     "mdp_value_iterate_workspace_bytes": (_sz, [_M, _i32]),
     "mdp_value_iterate": (C.c_int, [_M, _i32, C.c_double, _i32, _i32, _vp, _vp, _vp, _sz,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_double), _vp]),
+    "fib_value_iterate_workspace_bytes": (_sz, [_M, _i32]),
+    "fib_value_iterate": (C.c_int, [_M, _i32, C.c_double, _i32, _i32, _vp, _vp, _vp, _sz,
+                                    C.POINTER(_i32), C.POINTER(C.c_double), _vp]),
     "mdp_value_iterate_checkpointed": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mdp_value_backward_workspace_bytes": (_sz, [_M, _i32]),
     "mdp_value_backward": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),

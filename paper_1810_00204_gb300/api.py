@@ -114,6 +114,32 @@ def mdp_value_iterate(model: Model, dtype="f32", tol=None, max_sweeps=100000, tr
     return dict(V=V, Q=Q, sweeps=sweeps.value, residual=res.value, status=st)
 
 
+def fib_value_iterate(model: Model, dtype="f32", tol=None, max_sweeps=100000, truncated=None, want_alpha=True,
+                      stream=None):
+    """The Fast Informed Bound alpha-vectors (Eq. 7).  Returns dict(alpha
+    [5][H][pitch] in `dtype` or None, Q [5][H][pitch] float32 -- the leaf
+    alpha-vectors of a plan whose leaves take V_FIB -- sweeps, residual, status)."""
+    w = model.w
+    tol = w.vi_tol if tol is None else tol
+    truncated = w.vi_truncated if truncated is None else truncated
+    dt = N.QV_F64 if dtype in ("f64", torch.float64) else N.QV_F32
+    alpha = None
+    if want_alpha:
+        alpha = torch.empty((5, model.H, model.P), dtype=torch.float64 if dt == N.QV_F64 else torch.float32,
+                            device=model.device)
+    Q = torch.empty((5, model.H, model.P), dtype=torch.float32, device=model.device)
+    nbytes = lib().fib_value_iterate_workspace_bytes(C.byref(model.struct), dt)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=model.device)
+    sweeps = C.c_int32(0)
+    res = C.c_double(0)
+    st = lib().fib_value_iterate(C.byref(model.struct), dt, float(tol), int(max_sweeps), int(truncated),
+                                 _ptr(alpha), _ptr(Q), _ptr(ws), nbytes, C.byref(sweeps), C.byref(res),
+                                 _stream(stream))
+    if st not in (N.QV_OK, N.QV_ERR_NOT_CONVERGED):
+        check(st, "fib_value_iterate")
+    return dict(alpha=alpha, Q=Q, sweeps=sweeps.value, residual=res.value, status=st)
+
+
 def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
     """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
     is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),

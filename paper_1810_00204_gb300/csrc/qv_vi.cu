@@ -44,78 +44,6 @@ struct VIArgs {
     unsigned spin_limit; // polls before a wait on other CTAs gives up
 };
 
-// Residual slots are a ring of this many sweeps: a slot is rewritten four
-// sweeps later, after every CTA has passed the test that read it.
-constexpr int kResRing = 4;
-
-// Stage grid rows [c0-1, c1+1) of `src` (clipped to the grid) into smem rows
-// 0.. of Vs with one bulk copy.  False when the wait ran out (after a second
-// bounded wait for the copy still in flight).
-template <typename T>
-__device__ bool stage_rows(const VIArgs<T> &a, T *Vs, const T *src, int c0, int c1, uint64_t *bar,
-                           unsigned &phase) {
-    const int lo = max(0, c0 - 1), hi = min(a.H, c1 + 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        fence_proxy_async();
-        const unsigned bytes = static_cast<unsigned>((hi - lo) * a.P * sizeof(T));
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_copy_g2s(Vs + (lo - (c0 - 1)) * a.P, src + static_cast<size_t>(lo) * a.P, bytes, bar);
-    }
-    const bool ok = mbar_wait_bounded(bar, phase);
-    // one decision for the whole CTA, so an early exit never splits it
-    const int failed = __syncthreads_or(ok ? 0 : 1);
-    if (failed) {
-        if (threadIdx.x == 0) atomicOr(&a.work->status, kErrTimeout);
-        if (!ok) mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
-    }
-    phase ^= 1u;
-    return failed == 0;
-}
-
-// Largest residual of sweep j over every CTA: wait until all CTAs have
-// posted it (a cumulative arrival count per ring slot), then every thread
-// reads the slots.  Same value in every CTA.
-template <typename T>
-__device__ bool sweep_residual(const VIArgs<T> &a, int j, T &res) {
-    __shared__ int s_ok;
-    __shared__ T s_m[8];
-    const unsigned nblocks = gridDim.x;
-    if (threadIdx.x == 0) {
-        // every sweep posts when there is a stopping test; a truncated run
-        // posts its last sweep only
-        const unsigned want = a.truncated > 0 ? nblocks : nblocks * static_cast<unsigned>(j / kResRing + 1);
-        unsigned i = 0;
-        int ok = 1;
-        while (ld_acquire(a.arrive + j % kResRing) < want) {
-            if (++i > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
-                atomicOr(&a.work->status, kErrTimeout);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return false;
-    T m = T(0);
-    const T *slot = a.res_slots + static_cast<size_t>(j % kResRing) * nblocks;
-    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const T v = __ldcg(slot + b);
-        m = v > m ? v : m;
-    }
-    m = warp_max(m);
-    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
-    __syncthreads();
-    m = T(0);
-    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = s_m[w] > m ? s_m[w] : m;
-    __syncthreads();
-    res = m;
-    return true;
-}
-
 // Jacobi sweeps by bands of rows, one band per CTA.  Sweep k reads one halo
 // row of each neighbouring band, so it waits only for CTAs i - 1 and i + 1
 // to finish sweep k - 1 (progress flags).  The stopping test of sweep j
@@ -163,7 +91,7 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
         T local = T(0);
         for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
             const int c1 = min(r_end, c0 + a.chunk_rows);
-            if (!stage_rows(a, Vs, Vk, c0, c1, &bar, phase)) return;
+            if (!stage_rows(a, Vs, Vk, c0, c1, a.P, &bar, phase)) return;
             const int ncell = (c1 - c0) * a.P;
             for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
                 const int rr = i / a.P, col = i - rr * a.P;
@@ -222,7 +150,7 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
     const size_t plane = static_cast<size_t>(a.H) * a.P;
     for (int c0 = r_begin; c0 < r_end; c0 += a.chunk_rows) {
         const int c1 = min(r_end, c0 + a.chunk_rows);
-        if (!stage_rows(a, Vs, Vf, c0, c1, &bar, phase)) return;
+        if (!stage_rows(a, Vs, Vf, c0, c1, a.P, &bar, phase)) return;
         const int ncell = (c1 - c0) * a.P;
         for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
             const int rr = i / a.P, col = i - rr * a.P;

@@ -1,8 +1,9 @@
 // qv_vi_cell.cuh -- the per-cell Bellman backup of the value iteration and
-// its bounded grid barrier, shared by the forward sweeps (qv_vi.cu) and the
-// sweeps the adjoint recomputes from checkpoints (qv_adjoint.cu), so both run
-// the same arithmetic.  `Args` provides P (row pitch), cost, goal, slip and
-// gamma (of type T).
+// the bounded cross-CTA waits of row-band sweeps, shared by the forward
+// sweeps (qv_vi.cu), the sweeps the adjoint recomputes from checkpoints
+// (qv_adjoint.cu) and the FIB iteration (qv_fib.cu), so all run the same
+// arithmetic and the same synchronisation.  For the cell backup `Args`
+// provides P (row pitch), cost, goal, slip and gamma (of type T).
 #pragma once
 
 #include "qv_common.cuh"
@@ -60,6 +61,83 @@ static __device__ bool wait_neighbours(const unsigned *done, unsigned step, unsi
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Row-band sweeps (the value iteration, the FIB iteration) share the two
+// pieces below.  `Args` provides H, work, truncated, res_slots, arrive and
+// spin_limit.
+
+// Residual slots are a ring of this many sweeps: a slot is rewritten four
+// sweeps later, after every CTA has passed the test that read it.
+constexpr int kResRing = 4;
+
+// Stage grid rows [c0-1, c1+1) of `src` (clipped to the grid; `row_elems`
+// elements a row) into smem rows 0.. of Vs with one bulk copy.  False when
+// the wait ran out (after a second bounded wait for the copy still in
+// flight).
+template <typename T, typename Args>
+__device__ bool stage_rows(const Args &a, T *Vs, const T *src, int c0, int c1, int row_elems, uint64_t *bar,
+                           unsigned &phase) {
+    const int lo = max(0, c0 - 1), hi = min(a.H, c1 + 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        fence_proxy_async();
+        const unsigned bytes = static_cast<unsigned>((hi - lo) * row_elems * sizeof(T));
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_copy_g2s(Vs + (lo - (c0 - 1)) * row_elems, src + static_cast<size_t>(lo) * row_elems, bytes, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase);
+    // one decision for the whole CTA, so an early exit never splits it
+    const int failed = __syncthreads_or(ok ? 0 : 1);
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(&a.work->status, kErrTimeout);
+        if (!ok) mbar_wait_bounded(bar, phase);  // let the copy in flight land before leaving
+    }
+    phase ^= 1u;
+    return failed == 0;
+}
+
+// Largest residual of sweep j over every CTA: wait until all CTAs have
+// posted it (a cumulative arrival count per ring slot), then every thread
+// reads the slots.  Same value in every CTA.
+template <typename T, typename Args>
+__device__ bool sweep_residual(const Args &a, int j, T &res) {
+    __shared__ int s_ok;
+    __shared__ T s_m[8];
+    const unsigned nblocks = gridDim.x;
+    if (threadIdx.x == 0) {
+        // every sweep posts when there is a stopping test; a truncated run
+        // posts its last sweep only
+        const unsigned want = a.truncated > 0 ? nblocks : nblocks * static_cast<unsigned>(j / kResRing + 1);
+        unsigned i = 0;
+        int ok = 1;
+        while (ld_acquire(a.arrive + j % kResRing) < want) {
+            if (++i > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                atomicOr(&a.work->status, kErrTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    T m = T(0);
+    const T *slot = a.res_slots + static_cast<size_t>(j % kResRing) * nblocks;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const T v = __ldcg(slot + b);
+        m = v > m ? v : m;
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = T(0);
+    for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) m = s_m[w] > m ? s_m[w] : m;
+    __syncthreads();
+    res = m;
+    return true;
 }
 
 template <typename T, typename Args>

@@ -1,0 +1,189 @@
+"""GPU parity of the Fast Informed Bound (Eq. 7): fib_value_iterate through
+the C ABI against the oracle's FIB iteration on the same inputs, sweep for
+sweep; at the full workload sizes, the oracle's own Eq. 7 sweep applied to the
+GPU's alpha-vectors (a fixed-point check cell by cell) and FIB <= QMDP; a plan
+whose leaves take V_FIB against the oracle's plan with the oracle's FIB
+alpha-vectors; the width limit of the FP64 path, the not-converged status and
+the bounded waits.
+
+Tolerances: FP64 alpha |d| <= 1e-10 * max(|ref|, 1) (rounding order only);
+FP32 alpha |d| <= 1e-5 * max(|ref|, 1), as for the value iteration."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1810_00204_gb300 import workloads as WL
+from test_gpu_parity import _close, compare_tree
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1810_00204_gb300 import api as A
+    return A
+
+
+def _alpha(m, t):
+    return m.from_grid(t).reshape(5, -1).astype(np.float64)
+
+
+CASES = [
+    lambda: WL.tiny(0),
+    lambda: WL.tiny(3, H=13, W=17),          # ragged width (pitch 24) and height
+    lambda: WL.mid(1, H=67, W=45),           # several CTAs, 16 beacons
+    lambda: WL.diff(0, H=40, W=36),          # cost map
+    lambda: WL.batched(2, E=1, lo=40, hi=90)[0],
+]
+
+
+@pytest.mark.parametrize("make", CASES)
+def test_fib_f64_truncated_matches_oracle(api, make):
+    w = make()
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f64", truncated=60)
+    assert r["status"] == 0 and r["sweeps"] == 60
+    o = O.fib_iteration(w, truncated=60)
+    _close(_alpha(m, r["alpha"]), o["alpha"], rel=1e-10, floor=1.0, what="alpha f64")
+    assert abs(r["residual"] - o["residual"]) <= 1e-10 * max(1.0, o["residual"])
+    _close(_alpha(m, r["Q"]), o["alpha"], rel=1e-6, floor=1.0, what="Q f64->f32")
+    # padding columns, occupied cells and the goal hold 0
+    a = r["alpha"].cpu().numpy()
+    assert np.all(a[:, :, w.W:] == 0.0)
+    dead = w.occ.ravel().astype(bool).copy()
+    dead[w.goal] = True
+    assert np.all(_alpha(m, r["alpha"])[:, dead] == 0.0)
+
+
+@pytest.mark.parametrize("make", [lambda: WL.tiny(1), lambda: WL.tiny(4, H=29, W=31)])
+def test_fib_f64_converged(api, make):
+    w = make()
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f64", tol=1e-9)
+    assert r["status"] == 0 and r["residual"] < 1e-9
+    o = O.fib_iteration(w, tol=1e-9)
+    assert abs(o["sweeps"] - r["sweeps"]) <= 1
+    ot = O.fib_iteration(w, truncated=r["sweeps"])
+    _close(_alpha(m, r["alpha"]), ot["alpha"], rel=1e-10, floor=1.0, what="alpha f64")
+
+
+@pytest.mark.parametrize("make", [lambda: WL.mid(0), lambda: WL.tiny(2, H=31, W=29)])
+def test_fib_f32_sweep_for_sweep(api, make):
+    w = make()
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f32", tol=1e-5)
+    assert r["status"] == 0 and r["residual"] < 1e-5
+    o = O.fib_iteration(w, truncated=r["sweeps"])
+    _close(_alpha(m, r["alpha"]), o["alpha"], floor=1.0, what="alpha f32")
+    _close(_alpha(m, r["Q"]), o["alpha"], floor=1.0, what="Q f32")
+
+
+@pytest.mark.parametrize("make", [lambda: WL.mid(0), lambda: WL.large(0)])
+def test_fib_full_size_fixed_point_and_bound(api, make):
+    # the configurations the benchmark times: the oracle applies Eq. 7 once
+    # to the GPU's converged alpha-vectors; the change is the GPU's last
+    # residual plus FP32 rounding of values of size <= 100
+    w = make()
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f32")
+    assert r["status"] == 0 and r["residual"] < w.vi_tol
+    al = _alpha(m, r["alpha"])
+    _, change = O.fib_sweep(w, al)
+    assert change < 1e-4, change
+    q = api.mdp_value_iterate(m, dtype="f32")
+    Qm = _alpha(m, q["Q"])
+    assert np.all(al <= Qm + 1e-4)
+    assert (Qm - al).max() > 1e-2  # partial sensing: strictly tighter somewhere
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("leaf_mode", [0, 1])
+def test_plan_with_fib_leaves(api, seed, leaf_mode):
+    # U_V = V_FIB(b) at the leaves (Alg. 5): the plan takes the FIB
+    # alpha-vectors as its leaf alpha-vectors
+    w = WL.tiny(seed)
+    Qf = O.fib_iteration(w)["alpha"].astype(np.float32)
+    compare_tree(api, w, w.depth, w.K, leaf_mode, Qf=Qf)
+
+
+def test_plan_with_gpu_fib_leaves_mid(api):
+    # the full mid configuration with the GPU's own FIB alpha-vectors
+    w = WL.mid(0)
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f32")
+    res, _ = api.qv_tree_plan(m, r["Q"], m.b0(), depth=w.depth, K=w.K, seed=w.seed, keep=True)
+    Qf = _alpha(m, r["Q"])
+    o = O.tree_plan(w, Qf, depth=w.depth, K=w.K, seed=w.seed)
+    if o["boundary_count"] == 0:
+        assert res["nodes_per_level"] == [int(x) for x in o["n_level"]]
+        _close(res["value"], o["root_value"], floor=1.0, what="root value")
+        _close(res["q"], o["root_q"], floor=1.0, what="root q")
+    # the samples do not depend on the leaf alpha-vectors, so both plans grow
+    # the same tree; V_FIB <= V_QMDP at every leaf and the backup is monotone
+    # in the leaf values, so every root Q-value can only go down
+    qm = api.mdp_value_iterate(m, dtype="f32")["Q"]
+    res_m, _ = api.qv_tree_plan(m, qm, m.b0(), depth=w.depth, K=w.K, seed=w.seed, keep=True)
+    assert res_m["nodes_per_level"] == res["nodes_per_level"]
+    assert np.all(np.asarray(res["q"]) <= np.asarray(res_m["q"]) + 1e-5 * max(1.0, abs(res_m["value"])))
+
+
+def test_fib_not_converged_is_reported(api):
+    w = WL.tiny(1)
+    m = api.Model(w)
+    r = api.fib_value_iterate(m, dtype="f32", tol=1e-5, max_sweeps=5)
+    assert r["status"] == 5 and r["sweeps"] == 5
+
+
+def test_fib_single_row_and_column(api):
+    for H, W in ((1, 16), (2, 9), (16, 1)):
+        occ = np.zeros((H, W), np.uint8)
+        b0 = np.zeros(H * W)
+        b0[-1] = 1.0
+        w = WL.custom(H, W, occ, [H * W - 1], 2, 0, H * W - 1, 0.1, 0.9, 0.95, b0)
+        m = api.Model(w)
+        r = api.fib_value_iterate(m, dtype="f64", truncated=30)
+        o = O.fib_iteration(w, truncated=30)
+        _close(_alpha(m, r["alpha"]), o["alpha"], rel=1e-10, floor=1.0, what=f"alpha {H}x{W}")
+
+
+def test_fib_widest_grids(api):
+    from paper_1810_00204_gb300 import _native as N
+    rng = np.random.default_rng(3)
+    # FP64 stages three rows of five planes: pitch 1928 fits, 2048 does not
+    for W, ok in ((1928, True), (2048, False)):
+        H = 3
+        occ = (rng.random((H, W)) < 0.1).astype(np.uint8)
+        free = np.flatnonzero(occ.ravel() == 0)
+        b0 = np.zeros(H * W)
+        b0[free[-1]] = 1.0
+        w = WL.custom(H, W, occ, free[1:9], 40, int(free[0]), int(free[-1]), 0.1, 0.9, 0.95, b0)
+        m = api.Model(w)
+        if ok:
+            r = api.fib_value_iterate(m, dtype="f64", truncated=4)
+            o = O.fib_iteration(w, truncated=4)
+            _close(_alpha(m, r["alpha"]), o["alpha"], rel=1e-10, floor=1.0, what="alpha wide f64")
+        else:
+            with pytest.raises(N.QVError) as ei:
+                api.fib_value_iterate(m, dtype="f64", truncated=4)
+            assert ei.value.status == N.QV_ERR_INVALID
+            r = api.fib_value_iterate(m, dtype="f32", truncated=4)
+            o = O.fib_iteration(w, truncated=4)
+            _close(_alpha(m, r["alpha"]), o["alpha"], floor=1.0, what="alpha wide f32")
+
+
+@pytest.mark.parametrize("truncated", [0, 50])
+def test_fib_timeout_is_reported(api, monkeypatch, truncated):
+    from paper_1810_00204_gb300 import _native as N
+    w = WL.mid(0)
+    m = api.Model(w)
+    monkeypatch.setenv("QVTS_FAULT", "timeout")
+    with pytest.raises(N.QVError) as ei:
+        api.fib_value_iterate(m, dtype="f32", truncated=truncated)
+    assert ei.value.status == N.QV_ERR_TIMEOUT
+    monkeypatch.delenv("QVTS_FAULT")
+    assert torch.ones(4, device="cuda").sum().item() == 4.0
+    r = api.fib_value_iterate(m, dtype="f32", truncated=truncated)
+    assert r["status"] == N.QV_OK

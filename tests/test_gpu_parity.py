@@ -151,11 +151,12 @@ def _oracle_Q(w):
     return vi["Q"].astype(np.float32)
 
 
-def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_beliefs=True):
-    """Run both sides on the same inputs; return (gpu result, oracle tree)."""
+def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_beliefs=True, Qf=None):
+    """Run both sides on the same inputs (leaf alpha-vectors Qf, float32
+    [5][n], the oracle's QMDP ones by default); return (gpu result, oracle tree)."""
     seed = w.seed if seed is None else seed
     m = api.Model(w)
-    Qf = _oracle_Q(w)
+    Qf = _oracle_Q(w) if Qf is None else Qf
     Qd = m.to_grid(Qf.reshape(5, w.H, w.W))
     b0 = m.b0()
     o = O.tree_plan(w, Qf.astype(np.float64), depth=depth, K=K, seed=seed, weight_mode=weight_mode,
