@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuner)")
     ap.add_argument("--gradient-only", action="store_true",
                     help="only time the gradient of the root value on the differentiation workload")
+    ap.add_argument("--offline-only", action="store_true",
+                    help="only time the offline solves (value iteration, FIB) on the workload's map")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched (256 uneven maps) and 512x512 sub-measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
@@ -523,6 +525,17 @@ def main():
         return
 
     w, desc = make_workload(args.workload, args.seed)
+    if args.offline_only:
+        # the offline alpha-vector solves alone, for profiling
+        if rank == 0:
+            peak, _ = measured_peak()
+            model = api.Model(w, device=dev)
+            vi, f, t = time_offline(lambda: api.mdp_value_iterate(model, dtype="f32"))
+            out = {"workload": desc, "vi": offline_line(vi, f, t, model, VI_BYTES_PER_CELL, peak)}
+            fib, f, t = time_offline(lambda: api.fib_value_iterate(model, dtype="f32", want_alpha=False))
+            out["fib"] = offline_line(fib, f, t, model, FIB_BYTES_PER_CELL, peak)
+            print(json.dumps(out), flush=True)
+        return
     R = args.plans_per_step
     ep_ids = replicas.episode_range(rank, world_size, R)
     eps = WL.episodes(w, R, seed=args.seed, first_episode=ep_ids.start)
