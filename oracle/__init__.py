@@ -86,6 +86,12 @@ def lib():
         L.or_fib_sweep.restype = C.c_double
         L.or_fib_iteration.argtypes = [P, C.c_double, C.c_int, C.c_int, vp, vp, vp, vp]
         L.or_fib_iteration.restype = C.c_int
+        L.or_pbvi_init.argtypes = [P, vp]
+        L.or_pbvi_init.restype = None
+        L.or_pbvi_expand.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, vp, vp, vp, vp]
+        L.or_pbvi_expand.restype = C.c_int
+        L.or_pbvi_backup.argtypes = [P, vp, C.c_int, vp, C.c_int, vp, vp, vp, vp, vp, vp]
+        L.or_pbvi_backup.restype = C.c_int
         _lib = L
     return _lib
 
@@ -185,6 +191,74 @@ def fib_sweep(w, alpha, **kw):
     out = np.zeros(A * p.n, np.float64)
     res = lib().or_fib_sweep(p.ref, _p(label), _p(R), _p(a), _p(out))
     return out.reshape(A, p.n), res
+
+
+def pbvi_init(w, **kw):
+    """The pessimistic PBVI start alpha_0 [n] (R_min / (1 - gamma))."""
+    p = _prob(w, **kw)
+    out = np.zeros(p.n, np.float64)
+    lib().or_pbvi_init(p.ref, _p(out))
+    return out
+
+
+def pbvi_expand(w, B, rnd, seed=None, **kw):
+    """One round of belief set expansion (Sec. IV-B): a new point from each
+    point of B [nB][n].  Returns dict(points [nB][n], action, obs, boundary)."""
+    p = _prob(w, **kw)
+    seed = p.w.seed if seed is None else seed
+    B = np.ascontiguousarray(np.asarray(B, np.float64).reshape(-1, p.n))
+    nB = B.shape[0]
+    out = np.zeros_like(B)
+    a = np.zeros(nB, np.int32)
+    z = np.zeros(nB, np.int32)
+    bd = np.zeros(nB, np.int32)
+    lib().or_pbvi_expand(p.ref, _p(B), nB, int(rnd), int(seed), _p(out), _p(a), _p(z), _p(bd))
+    return dict(points=out, action=a, obs=z, boundary=bd)
+
+
+def pbvi_backup(w, B, G, want_score=False, **kw):
+    """One Eq. 8 backup at every point of B [nB][n] given Gamma G [nG][n].
+    Returns dict(G [nB][n], value, astar, best [nB][nz], q [nB][5], score
+    [nB][5][nz][nG] or None)."""
+    p = _prob(w, **kw)
+    B = np.ascontiguousarray(np.asarray(B, np.float64).reshape(-1, p.n))
+    G = np.ascontiguousarray(np.asarray(G, np.float64).reshape(-1, p.n))
+    nB, nG, nz = B.shape[0], G.shape[0], p.B + 1
+    Gout = np.zeros((nB, p.n), np.float64)
+    value = np.zeros(nB, np.float64)
+    astar = np.zeros(nB, np.int32)
+    best = np.zeros((nB, nz), np.int32)
+    q = np.zeros((nB, A), np.float64)
+    score = np.zeros((nB, A, nz, nG), np.float64) if want_score else None
+    lib().or_pbvi_backup(p.ref, _p(B), nB, _p(G), nG, _p(Gout), _p(value), _p(astar), _p(best), _p(q),
+                         None if score is None else _p(score))
+    return dict(G=Gout, value=value, astar=astar, best=best, q=q, score=score)
+
+
+def pbvi_value(G, b):
+    """V_PBVI(b) = max over the alpha-vectors of Gamma of alpha . b (Eq. 4's
+    form with Gamma_PBVI); b [n] or [m][n]."""
+    G = np.asarray(G, np.float64)
+    return (np.asarray(b, np.float64) @ G.T).max(axis=-1)
+
+
+def pbvi_solve(w, rounds, iters, seed=None, b0=None, **kw):
+    """The PBVI schedule of this build: from B = {b0} and Gamma = {alpha_0},
+    `rounds` times (`iters` backups of Eq. 8, then one expansion round),
+    then `iters` more backups.  Returns dict(B, G, value, history)."""
+    p = _prob(w, **kw)
+    b = (p.w.b0.reshape(-1) if b0 is None else np.asarray(b0).reshape(-1)).astype(np.float64)
+    B = b[None, :].copy()
+    G = pbvi_init(p)[None, :]
+    hist = []
+    for r in range(rounds + 1):
+        for _ in range(iters):
+            bk = pbvi_backup(p, B, G)
+            G = bk["G"]
+            hist.append(bk["value"].copy())
+        if r < rounds:
+            B = np.concatenate([B, pbvi_expand(p, B, r, seed)["points"]])
+    return dict(B=B, G=G, value=pbvi_value(G, B), history=hist)
 
 
 def predict(w, b, a):

@@ -751,3 +751,129 @@ int or_fib_iteration(const or_problem *p, double tol, int max_sweeps, int trunca
     free(label); free(R); free(next);
     return status;
 }
+
+/* ---- Point-based value iteration (Sec. IV-B) --------------------------- */
+
+/* Pessimistic start of the PBVI alpha-vectors: every policy earns at least
+ * R_min = min over free, non-goal x and a of R(x, a) per step, so
+ * alpha_0 = R_min / (1 - gamma) on those cells (0 on the goal and occupied
+ * cells) is below V* everywhere.  alpha0: [n].                            */
+void or_pbvi_init(const or_problem *p, double *alpha0) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS;
+    double *R = (double *)malloc(sizeof(double) * A * n);
+    or_reward_table(p, R);
+    double rmin = HUGE_VAL;
+    for (int x = 0; x < n; ++x) {
+        if (p->occ[x] || x == p->goal) continue;
+        for (int a = 0; a < A; ++a)
+            if (R[a * n + x] < rmin) rmin = R[a * n + x];
+    }
+    for (int x = 0; x < n; ++x) alpha0[x] = (p->occ[x] || x == p->goal) ? 0.0 : rmin / (1.0 - p->gamma);
+    free(R);
+}
+
+/* Belief set expansion (Sec. IV-B): every point b_j of the set yields one
+ * new point by forward sampling one action-observation step from it: the
+ * action uniformly, a = floor(5 u_a), then z ~ P(z | b_j, a) by the inverse
+ * CDF of Alg. 3-4's reading, then b' = tau(b_j, a, z) (Eq. 3).  The uniforms
+ * are the Philox stream of the tree search with level code 255 (never a tree
+ * level), episode word = the expansion round, path = j: u_a is its word 0,
+ * u_z its word 1.  B: [nB][n]; out: [nB][n]; action, obs, boundary: [nB].  */
+int or_pbvi_expand(const or_problem *p, const double *B, int nB, int round, uint64_t seed, double *out,
+                   int *action, int *obs, int *boundary) {
+    const int n = p->H * p->W, nz = p->B + 1;
+    int *label = (int *)malloc(sizeof(int) * n);
+    or_labels(p, label);
+#pragma omp parallel for schedule(dynamic)
+    for (int j = 0; j < nB; ++j) {
+        double *bbar = (double *)malloc(sizeof(double) * n);
+        double *P = (double *)malloc(sizeof(double) * nz);
+        const float ua = or_uniform(seed, (uint32_t)round, 255, (uint64_t)j, 0);
+        int a = (int)floor((double)ua * 5.0);
+        if (a > 4) a = 4;
+        or_predict(p, B + (size_t)j * n, a, bbar);
+        or_obs_marginal(p, label, bbar, P);
+        const float uz = or_uniform(seed, (uint32_t)round, 255, (uint64_t)j, 1);
+        const int z = or_sample_obs(P, nz, uz);
+        or_correct(p, label, bbar, z, out + (size_t)j * n);
+        action[j] = a;
+        obs[j] = z;
+        boundary[j] = or_is_boundary(P, nz, uz);
+        free(bbar); free(P);
+    }
+    free(label);
+    return 0;
+}
+
+/* One PBVI alpha-vector backup, Eq. 8, at every point b of B given the set
+ * Gamma (nG vectors of n values):
+ *   for each action a and observation z, the vector of Gamma maximising
+ *     sum_x sum_x' O(x', z) T(x, a, x') alpha(x') b(x)          (ties: lowest index),
+ *   Q_b(a) = R(b, a) + gamma sum_z (that maximum),
+ *   a*(b) = argmax_a Q_b(a)                                      (ties: lowest a),
+ * and the new vector of b is
+ *   alpha_b(x) = R(x, a*) + gamma sum_z sum_x' O(x', z) T(x, a*, x') alpha_{i*(z)}(x')
+ * on free, non-goal x, 0 on the goal and occupied cells (their value is 0
+ * under every policy).  Gout: [nB][n]; value[b] = Q_b(a*) = sum_x b(x) alpha_b(x);
+ * astar[b]; best: [nB][nz] the maximising indices for a*; q: [nB][5]
+ * (nullable) every Q_b(a); score: [nB][5][nz][nG] (nullable) every sum.   */
+int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G, int nG, double *Gout,
+                   double *value, int *astar, int *best, double *q, double *score) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS, nz = p->B + 1;
+    int *label = (int *)malloc(sizeof(int) * n);
+    double *R = (double *)malloc(sizeof(double) * A * n);
+    or_labels(p, label);
+    or_reward_table(p, R);
+#pragma omp parallel for schedule(dynamic)
+    for (int j = 0; j < nB; ++j) {
+        const double *b = B + (size_t)j * n;
+        int *bi = (int *)malloc(sizeof(int) * A * nz);
+        double qa[OR_NUM_ACTIONS];
+        for (int a = 0; a < A; ++a) {
+            double qv = 0.0;
+            for (int x = 0; x < n; ++x) qv += R[a * n + x] * b[x];   /* R(b, a) */
+            for (int z = 0; z < nz; ++z) {
+                double mx = -HUGE_VAL;
+                int arg = 0;
+                for (int i = 0; i < nG; ++i) {
+                    const double *al = G + (size_t)i * n;
+                    double s = 0.0;
+                    for (int x = 0; x < n; ++x) {
+                        if (b[x] == 0.0) continue;
+                        int y[3]; double pr[3];
+                        const int m = or_transition_row(p, x, a, y, pr);
+                        for (int t = 0; t < m; ++t)
+                            s += or_obs_lik(p, label, y[t], z) * pr[t] * al[y[t]] * b[x];
+                    }
+                    if (score) score[(((size_t)j * A + a) * nz + z) * nG + i] = s;
+                    if (s > mx) { mx = s; arg = i; }
+                }
+                bi[a * nz + z] = arg;
+                qv += p->gamma * mx;
+            }
+            qa[a] = qv;
+            if (q) q[(size_t)j * A + a] = qv;
+        }
+        int as = 0;
+        for (int a = 1; a < A; ++a)
+            if (qa[a] > qa[as]) as = a;
+        astar[j] = as;
+        value[j] = qa[as];
+        for (int z = 0; z < nz; ++z) best[(size_t)j * nz + z] = bi[as * nz + z];
+        double *out = Gout + (size_t)j * n;
+        for (int x = 0; x < n; ++x) {
+            if (p->occ[x] || x == p->goal) { out[x] = 0.0; continue; }
+            int y[3]; double pr[3];
+            const int m = or_transition_row(p, x, as, y, pr);
+            double s = 0.0;
+            for (int z = 0; z < nz; ++z) {
+                const double *al = G + (size_t)bi[as * nz + z] * n;
+                for (int t = 0; t < m; ++t) s += or_obs_lik(p, label, y[t], z) * pr[t] * al[y[t]];
+            }
+            out[x] = R[as * n + x] + p->gamma * s;
+        }
+        free(bi);
+    }
+    free(label); free(R);
+    return 0;
+}

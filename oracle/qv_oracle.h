@@ -108,6 +108,16 @@ double or_fib_sweep(const or_problem *p, const int *label, const double *R, cons
 int or_fib_iteration(const or_problem *p, double tol, int max_sweeps, int truncated, double *alpha,
                      int *sweeps, double *residual, double *residual_hist);
 
+/* ---- Point-based value iteration (Sec. IV-B, Eq. 8) ---- */
+/* Pessimistic alpha_0 = R_min / (1 - gamma) on free, non-goal cells.       */
+void or_pbvi_init(const or_problem *p, double *alpha0);
+/* One round of belief set expansion: a new point from every point.        */
+int or_pbvi_expand(const or_problem *p, const double *B, int nB, int round, uint64_t seed, double *out,
+                   int *action, int *obs, int *boundary);
+/* One Eq. 8 backup at every point of B given Gamma [nG][n].                */
+int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G, int nG, double *Gout,
+                   double *value, int *astar, int *best, double *q, double *score);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
