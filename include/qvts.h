@@ -188,6 +188,62 @@ qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
                             void *d_ws, size_t ws_bytes, int32_t *sweeps_out,
                             double *residual_out, qv_stream_t stream);
 
+/* ---------------------------------------------------------------- PBVI bound (Sec. IV-B)
+ * Point-based value iteration: alpha-vectors, one per point of a belief set,
+ * backed up with Eq. 8 at the points; V_PBVI(b) = max_alpha alpha . b is a
+ * lower bound of the optimal value (the L_V of Alg. 5) when the vectors start
+ * from qv_pbvi_init.  Every belief and alpha-vector is FP32 [H][pitch] (sets
+ * of them [count][H][pitch]); every alpha-vector is 0 on the goal and on
+ * occupied cells.
+ *
+ * qv_pbvi_init: alpha_0 = R_min / (1 - gamma) on free, non-goal cells, with
+ * R_min the least R(x, a) there (a lower bound on every policy's value).
+ *
+ * qv_pbvi_expand: one round of belief set expansion (Sec. IV-B): from point
+ * j of d_B, an action a = floor(5 u_a) and an observation z drawn from
+ * P(z | b_j, a) by the inverse CDF (FP32, ascending z, as the tree search
+ * draws), giving d_out[j] = tau(b_j, a, z) (Eq. 3).  u_a and u_z are words 0
+ * and 1 of the Philox4x32-10 stream with key `seed` and counter
+ * {0, round, j, 255 << 24} (the tree's counter layout with level code 255).
+ * d_action, d_obs, d_boundary [nB] record a, z and whether u_z lay within
+ * 1e-6 of a CDF step.  One CTA per point.
+ *
+ * qv_pbvi_create builds a handle for one model (reads its cell words back,
+ * so it synchronises): the live cells (free, not the goal) ordered label by
+ * label for the contraction of Eq. 8.  The handle keeps host tables only;
+ * device state lives in the caller's workspace of qv_pbvi_workspace_bytes,
+ * which the later calls take from qv_pbvi_set_points.
+ * qv_pbvi_set_points: the belief set (1..max_points points, d_B is read
+ * during this call only): its five predicted beliefs per point and R(b, a).
+ * qv_pbvi_backup: one Eq. 8 backup of every point of the set given nG
+ * vectors d_G (nG <= max_points); writes one new vector per point to d_Gout
+ * (must not overlap d_G), and, where not NULL, the backed-up value at the
+ * point d_value [nB] (= d_Gout[b] . b), the chosen action d_astar [nB] (ties
+ * to the lowest), the winning vector of each observation for that action
+ * d_best [nB][B + 1] (ties to the lowest index), d_q [nB][5] every Q_b(a).
+ * qv_pbvi_value: V_PBVI(b) and its maximising vector for nb <= max_points
+ * beliefs d_b given nG vectors d_G.
+ * The host may upload small tables (pageable copies) on the stream; none of
+ * these calls synchronises except qv_pbvi_create. */
+typedef struct qv_pbvi qv_pbvi_t;
+qv_status qv_pbvi_init(const qv_model_t *model, float *d_alpha0, qv_stream_t stream);
+qv_status qv_pbvi_expand(const qv_model_t *model, const float *d_B, int32_t nB, int32_t round,
+                         uint64_t seed, float *d_out, int32_t *d_action, int32_t *d_obs,
+                         int32_t *d_boundary, qv_stream_t stream);
+qv_status qv_pbvi_create(const qv_model_t *model, int32_t max_points, qv_pbvi_t **out);
+size_t qv_pbvi_workspace_bytes(const qv_pbvi_t *pbvi);
+/* Length of the label-ordered cell axis (each label's run padded to a
+ * multiple of 16); seg_out (nullable, B + 2 entries) gets the runs' starts. */
+int32_t qv_pbvi_layout(const qv_pbvi_t *pbvi, int32_t *seg_out);
+qv_status qv_pbvi_set_points(qv_pbvi_t *pbvi, const float *d_B, int32_t nB, void *d_ws,
+                             size_t ws_bytes, qv_stream_t stream);
+qv_status qv_pbvi_backup(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, float *d_Gout,
+                         float *d_value, int32_t *d_astar, int32_t *d_best, float *d_q,
+                         qv_stream_t stream);
+qv_status qv_pbvi_value(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, const float *d_b,
+                        int32_t nb, float *d_value, int32_t *d_arg, qv_stream_t stream);
+void qv_pbvi_destroy(qv_pbvi_t *pbvi);
+
 /* ---------------------------------------------------------------- belief update (Eq. 3)
  * belief_predict: bbar(y) = sum_x T(x, action, y) b(x), the numerator of
  * Eq. 3.  Values stored on occupied cells of b are read as 0. */

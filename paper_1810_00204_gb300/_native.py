@@ -74,6 +74,15 @@ SIGNATURES = {
     "fib_value_iterate_workspace_bytes": (_sz, [_M, _i32]),
     "fib_value_iterate": (C.c_int, [_M, _i32, C.c_double, _i32, _i32, _vp, _vp, _vp, _sz,
                                     C.POINTER(_i32), C.POINTER(C.c_double), _vp]),
+    "qv_pbvi_init": (C.c_int, [_M, _vp, _vp]),
+    "qv_pbvi_expand": (C.c_int, [_M, _vp, _i32, _i32, C.c_uint64, _vp, _vp, _vp, _vp, _vp]),
+    "qv_pbvi_create": (C.c_int, [_M, _i32, C.POINTER(_vp)]),
+    "qv_pbvi_workspace_bytes": (_sz, [_vp]),
+    "qv_pbvi_layout": (_i32, [_vp, _vp]),
+    "qv_pbvi_set_points": (C.c_int, [_vp, _vp, _i32, _vp, _sz, _vp]),
+    "qv_pbvi_backup": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "qv_pbvi_value": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "qv_pbvi_destroy": (None, [_vp]),
     "mdp_value_iterate_checkpointed": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mdp_value_backward_workspace_bytes": (_sz, [_M, _i32]),
     "mdp_value_backward": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),

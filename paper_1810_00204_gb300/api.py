@@ -140,6 +140,110 @@ def fib_value_iterate(model: Model, dtype="f32", tol=None, max_sweeps=100000, tr
     return dict(alpha=alpha, Q=Q, sweeps=sweeps.value, residual=res.value, status=st)
 
 
+def pbvi_init(model: Model, stream=None) -> torch.Tensor:
+    """The pessimistic PBVI start alpha_0 (R_min / (1 - gamma)), [H][pitch]."""
+    a0 = torch.empty((model.H, model.P), dtype=torch.float32, device=model.device)
+    check(lib().qv_pbvi_init(C.byref(model.struct), _ptr(a0), _stream(stream)), "qv_pbvi_init")
+    return a0
+
+
+def pbvi_expand(model: Model, B: torch.Tensor, rnd: int, seed: int, out=None, stream=None):
+    """One round of belief set expansion: a new point from each of the nB
+    points of B [nB][H][pitch].  Returns dict(points, action, obs, boundary)."""
+    nB = B.shape[0]
+    out = torch.empty_like(B) if out is None else out
+    a = torch.empty(nB, dtype=torch.int32, device=B.device)
+    z = torch.empty(nB, dtype=torch.int32, device=B.device)
+    bd = torch.empty(nB, dtype=torch.int32, device=B.device)
+    check(lib().qv_pbvi_expand(C.byref(model.struct), _ptr(B.contiguous()), nB, int(rnd), int(seed), _ptr(out),
+                               _ptr(a), _ptr(z), _ptr(bd), _stream(stream)), "qv_pbvi_expand")
+    return dict(points=out, action=a, obs=z, boundary=bd)
+
+
+class Pbvi:
+    """Point-based value iteration on one model (Eq. 8): a belief set of up
+    to `max_points` points and the C ABI handle with its workspace."""
+
+    def __init__(self, model: Model, max_points: int):
+        self.model = model
+        self.max_points = int(max_points)
+        h = C.c_void_p()
+        check(lib().qv_pbvi_create(C.byref(model.struct), self.max_points, C.byref(h)), "qv_pbvi_create")
+        self.handle = h
+        self.ws_bytes = lib().qv_pbvi_workspace_bytes(h)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=model.device)
+        off = (-self.ws.data_ptr()) % 256
+        self.ws_ptr = C.c_void_p(self.ws.data_ptr() + off)
+        self.nB = 0
+
+    def layout(self):
+        seg = (C.c_int32 * (self.model.B + 2))()
+        Kp = lib().qv_pbvi_layout(self.handle, seg)
+        return Kp, list(seg)
+
+    def set_points(self, B: torch.Tensor, stream=None):
+        self.B = B.contiguous()
+        self.nB = self.B.shape[0]
+        check(lib().qv_pbvi_set_points(self.handle, _ptr(self.B), self.nB, self.ws_ptr, self.ws_bytes,
+                                       _stream(stream)), "qv_pbvi_set_points")
+
+    def backup(self, G: torch.Tensor, out=None, stream=None):
+        """One Eq. 8 backup at every point of the set given G [nG][H][pitch].
+        Returns dict(G [nB][H][pitch], value, astar, best [nB][B+1], q [nB][5])."""
+        nB, m = self.nB, self.model
+        out = torch.empty((nB, m.H, m.P), dtype=torch.float32, device=m.device) if out is None else out
+        value = torch.empty(nB, dtype=torch.float32, device=m.device)
+        astar = torch.empty(nB, dtype=torch.int32, device=m.device)
+        best = torch.empty((nB, m.B + 1), dtype=torch.int32, device=m.device)
+        q = torch.empty((nB, 5), dtype=torch.float32, device=m.device)
+        check(lib().qv_pbvi_backup(self.handle, _ptr(G.contiguous()), G.shape[0], _ptr(out), _ptr(value), _ptr(astar),
+                                   _ptr(best), _ptr(q), _stream(stream)), "qv_pbvi_backup")
+        return dict(G=out, value=value, astar=astar, best=best, q=q)
+
+    def value(self, G: torch.Tensor, b: torch.Tensor, stream=None):
+        """V_PBVI(b) and the maximising vector's index for beliefs b [nb][H][pitch]."""
+        nb = b.shape[0]
+        v = torch.empty(nb, dtype=torch.float32, device=b.device)
+        arg = torch.empty(nb, dtype=torch.int32, device=b.device)
+        check(lib().qv_pbvi_value(self.handle, _ptr(G.contiguous()), G.shape[0], _ptr(b.contiguous()), nb, _ptr(v),
+                                  _ptr(arg), _stream(stream)), "qv_pbvi_value")
+        return v, arg
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().qv_pbvi_destroy(h)
+            self.handle = None
+
+
+def pbvi_solve(model: Model, rounds: int, iters: int, seed: int = 0, b0: Optional[torch.Tensor] = None,
+               stream=None):
+    """The PBVI schedule the oracle's pbvi_solve follows: from B = {b0} and
+    Gamma = {alpha_0}, `rounds` times (`iters` Eq. 8 backups, then one
+    expansion round), then `iters` more backups.  Returns dict(B, G, value,
+    pbvi) with value = V_PBVI at every point."""
+    nmax = 1 << rounds
+    m = model
+    B = torch.zeros((nmax, m.H, m.P), dtype=torch.float32, device=m.device)
+    B[0] = m.b0() if b0 is None else b0
+    pb = Pbvi(m, nmax)
+    G = torch.zeros((nmax, m.H, m.P), dtype=torch.float32, device=m.device)
+    G[0] = pbvi_init(m, stream)
+    G2 = torch.empty_like(G)
+    nB, nG = 1, 1
+    for r in range(rounds + 1):
+        pb.set_points(B[:nB], stream)
+        for _ in range(iters):
+            pb.backup(G[:nG], out=G2[:nB], stream=stream)
+            G, G2 = G2, G
+            nG = nB
+        if r < rounds:
+            pbvi_expand(m, B[:nB], r, seed, out=B[nB:2 * nB], stream=stream)
+            nB *= 2
+    v, _ = pb.value(G[:nG], B[:nB], stream)
+    return dict(B=B[:nB], G=G[:nG], value=v, pbvi=pb)
+
+
 def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
     """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
     is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),

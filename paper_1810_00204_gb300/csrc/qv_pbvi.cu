@@ -1,0 +1,818 @@
+// qv_pbvi.cu -- point-based value iteration, the lower bound of Sec. IV-B.
+//
+// Belief set expansion: every point b_j of the set yields tau(b_j, a, z)
+// with a drawn uniformly and z ~ P(z | b_j, a) (one CTA per point).
+//
+// The Eq. 8 backup at a point b needs, for every action a, observation z and
+// alpha-vector alpha_i of Gamma,
+//   s(b, a, z, i) = sum_x sum_x' O(x', z) T(x, a, x') alpha_i(x') b(x)
+//                 = sum_x' O(x', z) bbar_{b,a}(x') alpha_i(x'),
+// with bbar_{b,a} = T_a^T b the predicted belief.  O(x', z) is eta plus
+// (accuracy - eta) on the cells labelled z, so with
+//   D_z(m, i) = sum over the cells x' labelled z of bbar_m(x') alpha_i(x'),   m = (b, a),
+// s = eta sum_z' D_z'(m, i) + (accuracy - eta) D_z(m, i).  D is one dense
+// contraction over the cells, split by label: the cells are ordered label by
+// label (each label's run padded to a multiple of 16 with zeros, the goal and
+// occupied cells left out because every alpha-vector is 0 there), so D_z is
+// a matrix product over one contiguous range of that order.  Long ranges are
+// cut into pieces so the grid fills the GPU; a piece's partial product is one
+// slab, and the selection kernel adds the slabs of a label in piece order.
+// The products run on the FP32 pipes, register-blocked 4x4 per thread on
+// 64x64 tiles with 16-deep shared-memory stages.
+//
+// The selection kernel takes, per point, every (a, z) argmax over Gamma, the
+// action a* maximising Q_b(a) = R(b, a) + gamma sum_z max_i s, and the set of
+// distinct winning vectors with their multiplicities; the update kernel then
+// forms alpha_b(x) = sum_{x'} T(x, a*, x') [r(x') + gamma c_b(x')] with
+//   c_b(x') = eta sum_z alpha_{i*(z)}(x') + (accuracy - eta) alpha_{i*(label(x'))}(x'),
+// band by band with c_b staged in shared memory.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qv_common.cuh"
+#include "qv_plan_types.cuh"  // kBoundaryEps, the window of a boundary draw
+
+struct qv_pbvi;
+
+namespace qv {
+namespace {
+
+constexpr int kPbThreads = 256;
+constexpr int kKC = 16;          // K depth of one contraction stage; label runs are padded to it
+constexpr int kTM = 64, kTN = 64;
+constexpr int kPiecesExtra = 64; // pieces beyond one per label
+
+struct PbModel {
+    int H, W, P, N, B, nz, goal;
+    float slip, acc, eta, gamma;
+    const uint16_t *cell;
+    const float *cost;
+};
+
+PbModel pb_model(const qv_model_t *m) {
+    PbModel a;
+    a.H = m->H;
+    a.W = m->W;
+    a.P = m->pitch;
+    a.N = m->H * m->pitch;
+    a.B = m->num_beacons;
+    a.nz = m->num_beacons + 1;
+    a.goal = m->goal;
+    a.slip = m->slip;
+    a.acc = m->accuracy;
+    a.eta = (1.0f - m->accuracy) / static_cast<float>(m->num_beacons);
+    a.gamma = m->discount;
+    a.cell = m->d_cell;
+    a.cost = m->d_cost;
+    return a;
+}
+
+__device__ __forceinline__ float pb_reward(const PbModel &m, int y) {
+    const unsigned cw = __ldg(m.cell + y);
+    return stage_reward(QV_CELL_FREE(cw) != 0, y == m.goal, m.cost ? __ldg(m.cost + y) : 0.0f);
+}
+
+// The (at most three) cells a free, non-goal cell x reaches under action a,
+// with their probabilities (Sec. II, Eq. 10: a blocked move stays on x).
+__device__ __forceinline__ int pb_successors(const PbModel &m, int x, unsigned cw, int a, int y[3], float p[3]) {
+    if (a == 4) {
+        y[0] = x;
+        p[0] = 1.0f;
+        return 1;
+    }
+    const unsigned blk = QV_CELL_BLOCKED(cw);
+    const int step[4] = {-m.P, 1, m.P, -1};
+    const int d[3] = {a, (a + 1) & 3, (a + 3) & 3};
+    const float w[3] = {1.0f - 2.0f * m.slip, m.slip, m.slip};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        y[i] = ((blk >> d[i]) & 1u) ? x : x + step[d[i]];
+        p[i] = w[i];
+    }
+    return 3;
+}
+
+// ---------------------------------------------------------------- expansion
+// One CTA per point j: pass 1 writes the predicted belief of the drawn action
+// into out_j and sums its mass per label (one shared-memory column per
+// thread, added in a fixed order, so the sums are reproducible); thread 0
+// draws z from P(z) by the FP32 inverse CDF of the tree search; pass 2
+// rescales out_j in place by O(., z) / P(z).
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_expand(PbModel m, const float *__restrict__ B, int round,
+                                                            uint64_t seed, float *__restrict__ out,
+                                                            int *__restrict__ action, int *__restrict__ obs,
+                                                            int *__restrict__ boundary) {
+    extern __shared__ float hist[];  // [nz][kPbThreads]
+    __shared__ float lut[64];
+    __shared__ float s_P[QV_MAX_BEACONS + 1], s_C[QV_MAX_BEACONS + 1];
+    __shared__ int s_z;
+    const int j = blockIdx.x, tid = threadIdx.x;
+    const float *b = B + static_cast<size_t>(j) * m.N;
+    float *o = out + static_cast<size_t>(j) * m.N;
+    for (int i = tid; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, m.slip);
+    for (int z = 0; z < m.nz; ++z) hist[z * kPbThreads + tid] = 0.0f;
+    // the action: word 0 of the point's stream, a = floor(5 u) in exact arithmetic
+    const float ua = sample_uniform(seed, static_cast<uint32_t>(round), 255, static_cast<uint64_t>(j), 0);
+    const int a = min(4, static_cast<int>(floor(static_cast<double>(ua) * 5.0)));
+    __syncthreads();
+    for (int y = tid; y < m.N; y += blockDim.x) {
+        const unsigned cw = __ldg(m.cell + y);
+        const unsigned in = QV_CELL_INFLOW(cw);
+        float nb[4];
+        nb[kDirN] = (in & 1u) ? __ldg(b + y - m.P) : 0.0f;
+        nb[kDirE] = (in & 2u) ? __ldg(b + y + 1) : 0.0f;
+        nb[kDirS] = (in & 4u) ? __ldg(b + y + m.P) : 0.0f;
+        nb[kDirW] = (in & 8u) ? __ldg(b + y - 1) : 0.0f;
+        const float v = predict_one(nb, __ldg(b + y), cw, y == m.goal, m.slip, lut, a);
+        o[y] = v;
+        if (QV_CELL_FREE(cw)) hist[QV_CELL_LABEL(cw) * kPbThreads + tid] += v;
+    }
+    __syncthreads();
+    for (int z = tid; z < m.nz; z += blockDim.x) {
+        float s = 0.0f;
+        for (int t = 0; t < kPbThreads; ++t) s += hist[z * kPbThreads + t];
+        s_P[z] = s;  // mass on label z, turned into P(z) below
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // P(z) = eta * total + (accuracy - eta) * mass(z), the total summed as
+        // the tree search sums it (null label first, then z ascending)
+        float tot = s_P[m.B];
+        for (int z = 0; z < m.B; ++z) tot += s_P[z];
+        float run = 0.0f;
+        for (int z = 0; z < m.nz; ++z) {
+            const float p = fmaf(m.acc - m.eta, s_P[z], m.eta * tot);
+            s_P[z] = p;
+            run = run + p;
+            s_C[z] = run;
+        }
+        const float uz = sample_uniform(seed, static_cast<uint32_t>(round), 255, static_cast<uint64_t>(j), 1);
+        const float t_u = uz * s_C[m.B];
+        int lo = 0, hi = m.B;  // first z with t_u < C[z]
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (t_u < s_C[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        const float inv = 1.0f / s_C[m.B];
+        const bool near = (lo < m.B && fabsf(uz - s_C[lo] * inv) < kBoundaryEps) ||
+                          (lo > 0 && fabsf(uz - s_C[lo - 1] * inv) < kBoundaryEps);
+        s_z = lo;
+        action[j] = a;
+        obs[j] = lo;
+        boundary[j] = near ? 1 : 0;
+    }
+    __syncthreads();
+    const int z = s_z;
+    const float inv = 1.0f / s_P[z];
+    for (int y = tid; y < m.N; y += blockDim.x) {
+        const unsigned cw = __ldg(m.cell + y);
+        const float w = QV_CELL_FREE(cw) ? (static_cast<int>(QV_CELL_LABEL(cw)) == z ? m.acc : m.eta) : 0.0f;
+        o[y] = o[y] * w * inv;
+    }
+}
+
+// ---------------------------------------------------------------- the pessimistic start
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_init(PbModel m, float *__restrict__ alpha0) {
+    __shared__ float s_min[kPbThreads / 32];
+    __shared__ float s_v;
+    float mn = INFINITY;
+    for (int x = threadIdx.x; x < m.N; x += blockDim.x) {
+        const unsigned cw = __ldg(m.cell + x);
+        if (!QV_CELL_FREE(cw) || x == m.goal) continue;
+        for (int a = 0; a < 5; ++a) {
+            int y[3];
+            float p[3];
+            const int n = pb_successors(m, x, cw, a, y, p);
+            float R = 0.0f;
+            for (int i = 0; i < n; ++i) R = fmaf(p[i], pb_reward(m, y[i]), R);
+            mn = fminf(mn, R);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = s_min[0];
+        for (int w = 1; w < kPbThreads / 32; ++w) v = fminf(v, s_min[w]);
+        s_v = v / (1.0f - m.gamma);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < m.N; x += blockDim.x) {
+        const unsigned cw = __ldg(m.cell + x);
+        alpha0[x] = (QV_CELL_FREE(cw) && x != m.goal) ? s_v : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------- predicted beliefs of the set
+// Grid (bands, points): every action's predicted belief of point b on the
+// band's cells, scattered into the label order (row b * 5 + a of Bp), and the
+// band's share of sum_y bbar_a(y) r(y).
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_predict(PbModel m, const float *__restrict__ Bset,
+                                                             const int *__restrict__ pos, int Kp, int band_cells,
+                                                             float *__restrict__ Bp, float *__restrict__ rpart) {
+    __shared__ float lut[64];
+    __shared__ float s_r[kPbThreads / 32][5];
+    const int b = blockIdx.y, band = blockIdx.x;
+    const float *bel = Bset + static_cast<size_t>(b) * m.N;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, m.slip);
+    __syncthreads();
+    float rs[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int y0 = band * band_cells, y1 = min(m.N, y0 + band_cells);
+    for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
+        const unsigned cw = __ldg(m.cell + y);
+        const unsigned in = QV_CELL_INFLOW(cw);
+        float nb[4], o[5];
+        nb[kDirN] = (in & 1u) ? __ldg(bel + y - m.P) : 0.0f;
+        nb[kDirE] = (in & 2u) ? __ldg(bel + y + 1) : 0.0f;
+        nb[kDirS] = (in & 4u) ? __ldg(bel + y + m.P) : 0.0f;
+        nb[kDirW] = (in & 8u) ? __ldg(bel + y - 1) : 0.0f;
+        predict_cell(nb, __ldg(bel + y), cw, y == m.goal, m.slip, lut, o);
+        const int k = __ldg(pos + y);
+        if (k >= 0) {
+#pragma unroll
+            for (int a = 0; a < 5; ++a) Bp[(static_cast<size_t>(b) * 5 + a) * Kp + k] = o[a];
+        }
+        if (QV_CELL_FREE(cw)) {
+            const float r = stage_reward(true, y == m.goal, m.cost ? __ldg(m.cost + y) : 0.0f);
+#pragma unroll
+            for (int a = 0; a < 5; ++a) rs[a] = fmaf(o[a], r, rs[a]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        float v = rs[a];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5][a] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        float v = 0.0f;
+        for (int w = 0; w < kPbThreads / 32; ++w) v += s_r[w][threadIdx.x];
+        rpart[(static_cast<size_t>(b) * gridDim.x + band) * 5 + threadIdx.x] = v;
+    }
+}
+
+// R(b, a) = sum_y bbar_a(y) r(y) - 100 b(goal): the mass already on the goal
+// stays there and earns nothing (R(goal, a) = 0).  Bands added in order.
+__global__ void k_pbvi_reward(PbModel m, const float *__restrict__ Bset, int nB, int nbands,
+                              const float *__restrict__ rpart, float *__restrict__ RB) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nB * 5) return;
+    const int b = t / 5, a = t - b * 5;
+    float v = 0.0f;
+    for (int k = 0; k < nbands; ++k) v += rpart[(static_cast<size_t>(b) * nbands + k) * 5 + a];
+    RB[t] = v - 100.0f * Bset[static_cast<size_t>(b) * m.N + m.goal];
+}
+
+// ---------------------------------------------------------------- Gamma in the label order
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restrict__ G, int nG, int N,
+                                                            const int *__restrict__ perm, int Kp,
+                                                            float *__restrict__ Gp) {
+    const size_t total = static_cast<size_t>(nG) * Kp;
+    for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int i = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<size_t>(i) * Kp);
+        const int y = __ldg(perm + k);
+        Gp[t] = y >= 0 ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
+    }
+}
+
+// ---------------------------------------------------------------- the contraction
+// slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k]; grid (M tiles, N
+// tiles, pieces); both operands K-contiguous rows of Kp floats.
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
+                                                            int M, int N, int Kp, const int *__restrict__ piece,
+                                                            float *__restrict__ slab) {
+    __shared__ __align__(16) float As[kKC][kTM + 4];
+    __shared__ __align__(16) float Bs[kKC][kTN + 4];
+    const int p = blockIdx.z;
+    const int k0 = __ldg(piece + 3 * p), k1 = __ldg(piece + 3 * p + 1);
+    const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // loader: row lr of the tile, 4 consecutive k at lk
+    const int lr = tid >> 2, lk = (tid & 3) * 4;
+    const bool a_ok = m0 + lr < M, b_ok = n0 + lr < N;
+    const float *ap = A + static_cast<size_t>(m0 + lr) * Kp + lk;
+    const float *bp = Bm + static_cast<size_t>(n0 + lr) * Kp + lk;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k = k0; k < k1; k += kKC) {
+        const float4 av = a_ok ? __ldg(reinterpret_cast<const float4 *>(ap + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 bv = b_ok ? __ldg(reinterpret_cast<const float4 *>(bp + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        As[lk + 0][lr] = av.x;
+        As[lk + 1][lr] = av.y;
+        As[lk + 2][lr] = av.z;
+        As[lk + 3][lr] = av.w;
+        Bs[lk + 0][lr] = bv.x;
+        Bs[lk + 1][lr] = bv.y;
+        Bs[lk + 2][lr] = bv.z;
+        Bs[lk + 3][lr] = bv.w;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKC; ++kk) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
+            const float ar[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float br[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        }
+    }
+    float *out = slab + static_cast<size_t>(p) * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int mm = m0 + ty * 4 + i;
+        if (mm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int nn = n0 + tx * 4 + j;
+            if (nn < N) out[static_cast<size_t>(mm) * N + nn] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- selection
+// One CTA per point b.  For each action: D(i) = the sum of every slab row
+// (pieces in order), then one warp per observation z takes
+// argmax_i eta D(i) + (accuracy - eta) D_z(i) (ties to the lowest i).  Then
+// a* and the distinct winners of a* with their multiplicities.
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_select(PbModel m, int nB, int nG, int npieces,
+                                                            const int *__restrict__ piece,
+                                                            const float *__restrict__ slab,
+                                                            const float *__restrict__ RB, float *__restrict__ value,
+                                                            int *__restrict__ astar, int *__restrict__ best,
+                                                            float *__restrict__ q, int *__restrict__ uniq,
+                                                            int *__restrict__ mult, int *__restrict__ nuniq) {
+    extern __shared__ float D[];  // [nG]
+    __shared__ float s_val[QV_MAX_BEACONS + 1];
+    __shared__ int s_arg[5][QV_MAX_BEACONS + 1];
+    __shared__ float s_q[5];
+    __shared__ int s_first[QV_MAX_BEACONS + 2];  // first piece of each label, label order
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int M = nB * 5;
+    const size_t slab_elems = static_cast<size_t>(M) * nG;
+    // pieces are stored label by label; s_first[z] .. s_first[z + 1] are z's
+    if (tid == 0) {
+        int p = 0;
+        for (int z = 0; z <= m.nz; ++z) {
+            while (p < npieces && __ldg(piece + 3 * p + 2) < z) ++p;
+            s_first[z] = p;
+        }
+    }
+    for (int a = 0; a < 5; ++a) {
+        const size_t row = static_cast<size_t>(b * 5 + a) * nG;
+        __syncthreads();
+        for (int i = tid; i < nG; i += blockDim.x) {
+            float s = 0.0f;
+            for (int p = 0; p < npieces; ++p) s += __ldg(slab + p * slab_elems + row + i);
+            D[i] = s;
+        }
+        __syncthreads();
+        for (int z = wid; z < m.nz; z += kPbThreads / 32) {
+            const int p0 = s_first[z], p1 = s_first[z + 1];
+            float bv = -INFINITY;
+            int bi = 0x7fffffff;
+            for (int i = lane; i < nG; i += 32) {
+                float dz = 0.0f;
+                for (int p = p0; p < p1; ++p) dz += __ldg(slab + p * slab_elems + row + i);
+                const float s = fmaf(m.acc - m.eta, dz, m.eta * D[i]);
+                if (s > bv) {  // i ascends within a lane: strict > keeps the lowest index
+                    bv = s;
+                    bi = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                s_val[z] = bv;
+                s_arg[a][z] = bi < nG ? bi : 0;  // no candidate compared above -inf (NaN input)
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float s = 0.0f;
+            for (int z = 0; z < m.nz; ++z) s += s_val[z];
+            s_q[a] = fmaf(m.gamma, s, __ldg(RB + b * 5 + a));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int as = 0;
+        for (int a = 1; a < 5; ++a)
+            if (s_q[a] > s_q[as]) as = a;
+        astar[b] = as;
+        value[b] = s_q[as];
+        if (q)
+            for (int a = 0; a < 5; ++a) q[b * 5 + a] = s_q[a];
+        int n = 0;
+        for (int z = 0; z < m.nz; ++z) {
+            const int i = s_arg[as][z];
+            best[b * m.nz + z] = i;
+            int t = 0;
+            while (t < n && uniq[b * m.nz + t] != i) ++t;
+            if (t == n) {
+                uniq[b * m.nz + n] = i;
+                mult[b * m.nz + n] = 0;
+                ++n;
+            }
+            ++mult[b * m.nz + t];
+        }
+        nuniq[b] = n;
+    }
+}
+
+// ---------------------------------------------------------------- the new alpha-vectors
+// Grid (bands of rows, points).  c_b on the band's rows and one halo row on
+// each side goes to shared memory, then alpha_b(x) = sum over x's successors
+// under a* of T [r(x') + gamma c_b(x')] on free, non-goal cells, 0 elsewhere.
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_alpha(PbModel m, int band_rows, const float *__restrict__ G,
+                                                           const int *__restrict__ astar, const int *__restrict__ best,
+                                                           const int *__restrict__ uniq, const int *__restrict__ mult,
+                                                           const int *__restrict__ nuniq, float *__restrict__ Gout) {
+    extern __shared__ float cs[];  // (band_rows + 2) rows of P
+    const int b = blockIdx.y;
+    const int r0 = blockIdx.x * band_rows, r1 = min(m.H, r0 + band_rows);
+    const int lo = max(0, r0 - 1), hi = min(m.H, r1 + 1);
+    const int nu = nuniq[b];
+    const int *ub = uniq + b * m.nz;
+    const int *mb = mult + b * m.nz;
+    const int *bb = best + b * m.nz;
+    const float dl = m.acc - m.eta;
+    for (int t = threadIdx.x; t < (hi - lo) * m.P; t += blockDim.x) {
+        const int y = lo * m.P + t;
+        const unsigned cw = __ldg(m.cell + y);
+        float c = 0.0f;
+        if (QV_CELL_FREE(cw) && y != m.goal) {
+            float s = 0.0f;
+            for (int u = 0; u < nu; ++u) s = fmaf(static_cast<float>(__ldg(mb + u)), __ldg(G + static_cast<size_t>(__ldg(ub + u)) * m.N + y), s);
+            const int own = __ldg(bb + QV_CELL_LABEL(cw));
+            c = fmaf(dl, __ldg(G + static_cast<size_t>(own) * m.N + y), m.eta * s);
+        }
+        cs[(lo - (r0 - 1)) * m.P + t] = c;
+    }
+    __syncthreads();
+    const int as = astar[b];
+    float *out = Gout + static_cast<size_t>(b) * m.N;
+    for (int t = threadIdx.x; t < (r1 - r0) * m.P; t += blockDim.x) {
+        const int x = r0 * m.P + t;
+        const unsigned cw = __ldg(m.cell + x);
+        float v = 0.0f;
+        if (QV_CELL_FREE(cw) && x != m.goal) {
+            int y[3];
+            float p[3];
+            const int n = pb_successors(m, x, cw, as, y, p);
+            for (int i = 0; i < n; ++i) {
+                const float cy = cs[y[i] - (r0 - 1) * m.P];
+                v = fmaf(p[i], fmaf(m.gamma, cy, pb_reward(m, y[i])), v);
+            }
+        }
+        out[x] = v;
+    }
+}
+
+// ---------------------------------------------------------------- V_PBVI(b) = max_i alpha_i . b
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_scatter_points(const float *__restrict__ Bset, int nb, int N,
+                                                                    const int *__restrict__ perm, int Kp,
+                                                                    float *__restrict__ Ap) {
+    const size_t total = static_cast<size_t>(nb) * Kp;
+    for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+         t += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int j = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<size_t>(j) * Kp);
+        const int y = __ldg(perm + k);
+        Ap[t] = y >= 0 ? __ldg(Bset + static_cast<size_t>(j) * N + y) : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int npieces, const float *__restrict__ slab,
+                                                            float *__restrict__ value, int *__restrict__ arg) {
+    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ float s_v[kPbThreads / 32];
+    __shared__ int s_i[kPbThreads / 32];
+    const size_t slab_elems = static_cast<size_t>(nb) * nG;
+    float bv = -INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < nG; i += blockDim.x) {
+        float s = 0.0f;
+        for (int p = 0; p < npieces; ++p) s += __ldg(slab + p * slab_elems + static_cast<size_t>(j) * nG + i);
+        if (s > bv) {
+            bv = s;
+            bi = i;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > bv || (ov == bv && oi < bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    if (lane == 0) {
+        s_v[wid] = bv;
+        s_i[wid] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float v = s_v[0];
+        int ii = s_i[0];
+        for (int w = 1; w < kPbThreads / 32; ++w)
+            if (s_v[w] > v || (s_v[w] == v && s_i[w] < ii)) {
+                v = s_v[w];
+                ii = s_i[w];
+            }
+        value[j] = v;
+        if (arg) arg[j] = ii < nG ? ii : 0;
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+}  // namespace qv
+
+// ------------------------------------------------------------------ host side
+struct qv_pbvi {
+    qv_model_t model;
+    int max_points, max_vectors;
+    int Kp, nz, max_pieces;
+    std::vector<int> perm;       // Kp: grid index of each position, -1 for padding
+    std::vector<int> pos;        // H * pitch: position of each cell, -1 off the live cells
+    std::vector<int> seg;        // nz + 1: label z occupies [seg[z], seg[z + 1])
+    std::vector<int> pieces;     // last uploaded piece table (k0, k1, label) triples
+    size_t off_pos, off_perm, off_piece, off_Bp, off_RB, off_rpart, off_Gp, off_Ap, off_slab;
+    size_t off_best, off_uniq, off_mult, off_nuniq, off_astar, off_val;
+    size_t ws_bytes;
+    void *ws;                    // workspace the tables live in (set by qv_pbvi_set_points)
+    int nB;                      // points of the current set
+    int nbands;                  // bands of k_pbvi_predict
+    int band_cells;
+};
+
+namespace {
+
+using qv::align256;
+
+// Pieces of the label runs: each run [seg[z], seg[z+1]) is cut into pieces of
+// at most L positions (a multiple of kKC), L chosen so that tiles x pieces
+// fills the GPU a few times over and there are at most max_pieces pieces.
+void make_pieces(const qv_pbvi &h, int tiles, int total_len, bool by_label, std::vector<int> &out) {
+    out.clear();
+    const int target = 4 * qv_num_sms();
+    const int want_pieces = std::max(1, (target + tiles - 1) / tiles);
+    int L = std::max(qv::kKC, ((total_len / want_pieces + qv::kKC - 1) / qv::kKC) * qv::kKC);
+    for (;;) {
+        out.clear();
+        if (by_label) {
+            for (int z = 0; z < h.nz; ++z)
+                for (int k = h.seg[z]; k < h.seg[z + 1]; k += L) out.insert(out.end(), {k, std::min(h.seg[z + 1], k + L), z});
+        } else {
+            for (int k = 0; k < total_len; k += L) out.insert(out.end(), {k, std::min(total_len, k + L), 0});
+        }
+        if (static_cast<int>(out.size() / 3) <= h.max_pieces) break;
+        L *= 2;
+    }
+}
+
+qv_status upload_pieces(qv_pbvi *h, const std::vector<int> &pc, cudaStream_t st) {
+    if (pc == h->pieces) return QV_OK;
+    h->pieces = pc;
+    return qv_check_cuda(cudaMemcpyAsync(static_cast<char *>(h->ws) + h->off_piece, h->pieces.data(),
+                                         h->pieces.size() * sizeof(int), cudaMemcpyHostToDevice, st),
+                         "piece table");
+}
+
+}  // namespace
+
+extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_pbvi **out) {
+    if (!m || !m->d_cell || !out) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_create: null pointer");
+    *out = nullptr;
+    if (m->H < 1 || m->W < 1 || m->pitch != QV_PITCH(m->W) || m->W > QV_MAX_WIDTH || m->num_beacons < 1 ||
+        m->num_beacons > QV_MAX_BEACONS || m->goal < 0 || m->goal >= m->H * m->pitch)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_create: bad model");
+    if (max_points < 1 || max_points > (1 << 16))
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_create: max_points %d outside 1..65536", max_points);
+    const int N = m->H * m->pitch, nz = m->num_beacons + 1;
+    std::vector<uint16_t> cell(N);
+    if (qv_check_cuda(cudaMemcpy(cell.data(), m->d_cell, N * sizeof(uint16_t), cudaMemcpyDeviceToHost),
+                      "cell words") != QV_OK)
+        return QV_ERR_CUDA;
+    qv_pbvi *h = new qv_pbvi();
+    h->model = *m;
+    h->max_points = max_points;
+    h->max_vectors = max_points;
+    h->nz = nz;
+    // live cells (free, not the goal) in label order, grid order within a label
+    std::vector<int> count(nz, 0);
+    for (int y = 0; y < N; ++y)
+        if (QV_CELL_FREE(cell[y]) && y != m->goal) ++count[QV_CELL_LABEL(cell[y])];
+    h->seg.assign(nz + 1, 0);
+    for (int z = 0; z < nz; ++z) h->seg[z + 1] = h->seg[z] + ((count[z] + qv::kKC - 1) / qv::kKC) * qv::kKC;
+    h->Kp = std::max(h->seg[nz], qv::kKC);
+    h->perm.assign(h->Kp, -1);
+    h->pos.assign(N, -1);
+    std::vector<int> fill(h->seg.begin(), h->seg.end() - 1);
+    for (int y = 0; y < N; ++y)
+        if (QV_CELL_FREE(cell[y]) && y != m->goal) {
+            const int k = fill[QV_CELL_LABEL(cell[y])]++;
+            h->perm[k] = y;
+            h->pos[y] = k;
+        }
+    h->max_pieces = nz + qv::kPiecesExtra;
+    h->band_cells = 4096;
+    h->nbands = (N + h->band_cells - 1) / h->band_cells;
+    const size_t P = max_points, G = h->max_vectors, Kp = h->Kp;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    h->off_pos = take(N * sizeof(int));
+    h->off_perm = take(Kp * sizeof(int));
+    h->off_piece = take(3 * h->max_pieces * sizeof(int));
+    h->off_Bp = take(5 * P * Kp * sizeof(float));
+    h->off_RB = take(5 * P * sizeof(float));
+    h->off_rpart = take(5 * P * h->nbands * sizeof(float));
+    h->off_Gp = take(G * Kp * sizeof(float));
+    h->off_Ap = take(P * Kp * sizeof(float));
+    h->off_slab = take(static_cast<size_t>(h->max_pieces) * 5 * P * std::max(G, P) * sizeof(float));
+    h->off_best = take(P * nz * sizeof(int));
+    h->off_uniq = take(P * nz * sizeof(int));
+    h->off_mult = take(P * nz * sizeof(int));
+    h->off_nuniq = take(P * sizeof(int));
+    h->off_astar = take(P * sizeof(int));
+    h->off_val = take(P * sizeof(float));
+    h->ws_bytes = off;
+    h->ws = nullptr;
+    h->nB = 0;
+    *out = h;
+    return QV_OK;
+}
+
+extern "C" void qv_pbvi_destroy(qv_pbvi *h) { delete h; }
+
+extern "C" size_t qv_pbvi_workspace_bytes(const qv_pbvi *h) { return h ? h->ws_bytes : 0; }
+
+extern "C" int32_t qv_pbvi_layout(const qv_pbvi *h, int32_t *seg_out) {
+    if (!h) return 0;
+    if (seg_out)
+        for (int z = 0; z <= h->nz; ++z) seg_out[z] = h->seg[z];
+    return h->Kp;
+}
+
+extern "C" qv_status qv_pbvi_init(const qv_model_t *m, float *d_alpha0, qv_stream_t stream) {
+    if (!m || !m->d_cell || !d_alpha0) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_init: null pointer");
+    if (!(m->discount > 0.0f && m->discount < 1.0f) || m->num_beacons < 1)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_init: bad model");
+    qv::k_pbvi_init<<<1, qv::kPbThreads, 0, static_cast<cudaStream_t>(stream)>>>(qv::pb_model(m), d_alpha0);
+    return qv_check_cuda(cudaGetLastError(), "qv_pbvi_init launch");
+}
+
+extern "C" qv_status qv_pbvi_expand(const qv_model_t *m, const float *d_B, int32_t nB, int32_t round, uint64_t seed,
+                                    float *d_out, int32_t *d_action, int32_t *d_obs, int32_t *d_boundary,
+                                    qv_stream_t stream) {
+    if (!m || !m->d_cell || !d_B || !d_out || !d_action || !d_obs || !d_boundary)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_expand: null pointer");
+    if (nB < 0 || round < 0 || m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_expand: bad arguments");
+    if (nB == 0) return QV_OK;
+    const size_t smem = static_cast<size_t>(m->num_beacons + 1) * qv::kPbThreads * sizeof(float);
+    if (smem > 48 * 1024 &&
+        qv_check_cuda(cudaFuncSetAttribute(qv::k_pbvi_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem)),
+                      "smem attr") != QV_OK)
+        return QV_ERR_CUDA;
+    qv::k_pbvi_expand<<<nB, qv::kPbThreads, smem, static_cast<cudaStream_t>(stream)>>>(
+        qv::pb_model(m), d_B, round, seed, d_out, d_action, d_obs, d_boundary);
+    return qv_check_cuda(cudaGetLastError(), "qv_pbvi_expand launch");
+}
+
+extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB, void *d_ws, size_t ws_bytes,
+                                        qv_stream_t stream) {
+    if (!h || !d_B || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_set_points: null pointer");
+    if (nB < 1 || nB > h->max_points)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_set_points: %d points outside 1..%d", nB, h->max_points);
+    if (ws_bytes < h->ws_bytes)
+        return qv_set_error(QV_ERR_WORKSPACE, "qv_pbvi_set_points: workspace %zu < %zu bytes", ws_bytes, h->ws_bytes);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_set_points: workspace must be 256-byte aligned");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(d_ws);
+    if (h->ws != d_ws) {
+        h->ws = d_ws;
+        h->pieces.clear();
+        if (qv_check_cuda(cudaMemcpyAsync(ws + h->off_pos, h->pos.data(), h->pos.size() * sizeof(int),
+                                          cudaMemcpyHostToDevice, st), "pos table") != QV_OK ||
+            qv_check_cuda(cudaMemcpyAsync(ws + h->off_perm, h->perm.data(), h->perm.size() * sizeof(int),
+                                          cudaMemcpyHostToDevice, st), "perm table") != QV_OK)
+            return QV_ERR_CUDA;
+    }
+    h->nB = nB;
+    float *Bp = reinterpret_cast<float *>(ws + h->off_Bp);
+    if (qv_check_cuda(cudaMemsetAsync(Bp, 0, static_cast<size_t>(5) * nB * h->Kp * sizeof(float), st), "memset") !=
+        QV_OK)
+        return QV_ERR_CUDA;
+    const qv::PbModel pm = qv::pb_model(&h->model);
+    qv::k_pbvi_predict<<<dim3(h->nbands, nB), qv::kPbThreads, 0, st>>>(
+        pm, d_B, reinterpret_cast<const int *>(ws + h->off_pos), h->Kp, h->band_cells, Bp,
+        reinterpret_cast<float *>(ws + h->off_rpart));
+    qv::k_pbvi_reward<<<(nB * 5 + 127) / 128, 128, 0, st>>>(pm, d_B, nB, h->nbands,
+                                                             reinterpret_cast<const float *>(ws + h->off_rpart),
+                                                             reinterpret_cast<float *>(ws + h->off_RB));
+    return qv_check_cuda(cudaGetLastError(), "qv_pbvi_set_points launch");
+}
+
+extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, float *d_Gout, float *d_value,
+                                    int32_t *d_astar, int32_t *d_best, float *d_q, qv_stream_t stream) {
+    if (!h || !d_G || !d_Gout) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: null pointer");
+    if (!h->ws || h->nB < 1) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: no point set (qv_pbvi_set_points)");
+    if (nG < 1 || nG > h->max_vectors)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: %d vectors outside 1..%d", nG, h->max_vectors);
+    const size_t N = static_cast<size_t>(h->model.H) * h->model.pitch;
+    if (d_G < d_Gout + N * h->nB && d_Gout < d_G + N * nG)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: d_G and d_Gout overlap");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(h->ws);
+    const int nB = h->nB, M = 5 * nB, Kp = h->Kp;
+    const int Mt = (M + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
+    std::vector<int> pc;
+    make_pieces(*h, Mt * Nt, Kp, true, pc);
+    if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
+    const int npieces = static_cast<int>(pc.size() / 3);
+    const int *piece = reinterpret_cast<const int *>(ws + h->off_piece);
+    float *Gp = reinterpret_cast<float *>(ws + h->off_Gp);
+    float *slab = reinterpret_cast<float *>(ws + h->off_slab);
+    const int gthreads = 256, gblocks = std::min<long long>((static_cast<long long>(nG) * Kp + gthreads - 1) / gthreads,
+                                                            8LL * qv_num_sms());
+    qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
+                                                    reinterpret_cast<const int *>(ws + h->off_perm), Kp, Gp);
+    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
+        reinterpret_cast<const float *>(ws + h->off_Bp), Gp, M, nG, Kp, piece, slab);
+    const qv::PbModel pm = qv::pb_model(&h->model);
+    int *best = d_best ? d_best : reinterpret_cast<int *>(ws + h->off_best);
+    int *astar = d_astar ? d_astar : reinterpret_cast<int *>(ws + h->off_astar);
+    float *value = d_value ? d_value : reinterpret_cast<float *>(ws + h->off_val);
+    int *uniq = reinterpret_cast<int *>(ws + h->off_uniq), *mult = reinterpret_cast<int *>(ws + h->off_mult);
+    int *nuniq = reinterpret_cast<int *>(ws + h->off_nuniq);
+    const size_t sel_smem = static_cast<size_t>(nG) * sizeof(float);
+    if (sel_smem > 48 * 1024 &&
+        qv_check_cuda(cudaFuncSetAttribute(qv::k_pbvi_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(sel_smem)),
+                      "smem attr") != QV_OK)
+        return QV_ERR_CUDA;
+    qv::k_pbvi_select<<<nB, qv::kPbThreads, sel_smem, st>>>(pm, nB, nG, npieces, piece, slab,
+                                                             reinterpret_cast<const float *>(ws + h->off_RB), value,
+                                                             astar, best, d_q, uniq, mult, nuniq);
+    const int band_rows = std::max(1, 4096 / h->model.pitch);
+    const int nbands = (h->model.H + band_rows - 1) / band_rows;
+    const size_t a_smem = static_cast<size_t>(band_rows + 2) * h->model.pitch * sizeof(float);
+    if (a_smem > 48 * 1024 &&
+        qv_check_cuda(cudaFuncSetAttribute(qv::k_pbvi_alpha, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(a_smem)),
+                      "smem attr") != QV_OK)
+        return QV_ERR_CUDA;
+    qv::k_pbvi_alpha<<<dim3(nbands, nB), qv::kPbThreads, a_smem, st>>>(pm, band_rows, d_G, astar, best, uniq, mult,
+                                                                        nuniq, d_Gout);
+    return qv_check_cuda(cudaGetLastError(), "qv_pbvi_backup launch");
+}
+
+extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, const float *d_b, int32_t nb,
+                                   float *d_value, int32_t *d_arg, qv_stream_t stream) {
+    if (!h || !d_G || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: null pointer");
+    if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: no workspace yet (qv_pbvi_set_points)");
+    if (nG < 1 || nG > h->max_vectors || nb < 1 || nb > h->max_points)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: %d vectors, %d beliefs", nG, nb);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(h->ws);
+    const int Kp = h->Kp, N = h->model.H * h->model.pitch;
+    const int Mt = (nb + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
+    std::vector<int> pc;
+    make_pieces(*h, Mt * Nt, Kp, false, pc);
+    if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
+    const int npieces = static_cast<int>(pc.size() / 3);
+    float *Ap = reinterpret_cast<float *>(ws + h->off_Ap);
+    float *Gp = reinterpret_cast<float *>(ws + h->off_Gp);
+    float *slab = reinterpret_cast<float *>(ws + h->off_slab);
+    const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
+    const int gb = 8 * qv_num_sms();
+    qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b, nb, N, perm, Kp, Ap);
+    qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, Kp, Gp);
+    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
+        Ap, Gp, nb, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab);
+    qv::k_pbvi_rowmax<<<nb, qv::kPbThreads, 0, st>>>(nb, nG, npieces, slab, d_value, d_arg);
+    return qv_check_cuda(cudaGetLastError(), "qv_pbvi_value launch");
+}

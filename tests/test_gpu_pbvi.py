@@ -1,0 +1,232 @@
+"""GPU parity of the PBVI lower bound (Sec. IV-B, Eq. 8): the pessimistic
+start, belief set expansion, one backup, V_PBVI and the whole schedule
+through the C ABI against the oracle on the same inputs.
+
+Decisions taken by an argmax (a*, the winning vector of each observation,
+V_PBVI's vector) must match the oracle's wherever the oracle's best and
+second-best candidates are more than 1e-4 * scale apart; elsewhere the
+GPU's choice must score within that margin of the oracle's maximum.  Values
+|d| <= 1e-5 * max(|ref|, 1) (FP32 against FP64) for one backup, 1e-4 after a
+schedule of many backups.  Sampled observations match except at draws the
+oracle flags as lying within 1e-6 of a CDF step."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1810_00204_gb300 import workloads as WL
+from test_gpu_parity import _close
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+GAP = 1e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1810_00204_gb300 import api as A
+    return A
+
+
+def _dead(w):
+    d = w.occ.ravel().astype(bool).copy()
+    d[w.goal] = True
+    return d
+
+
+def _beliefs(w, m, seed, support=None):
+    """m random FP32 beliefs on the free cells (dense, or on `support` cells)."""
+    rng = np.random.default_rng(seed)
+    free = np.flatnonzero(w.occ.ravel() == 0)
+    out = np.zeros((m, w.H * w.W), np.float32)
+    for j in range(m):
+        idx = free if support is None else rng.choice(free, size=min(support, len(free)), replace=False)
+        out[j, idx] = rng.random(len(idx)).astype(np.float32)
+        out[j] /= out[j].sum()
+    return out
+
+
+def _vectors(w, m, seed):
+    rng = np.random.default_rng([5, seed])
+    G = rng.normal(-10.0, 15.0, (m, w.H * w.W)).astype(np.float32)
+    G[:, _dead(w)] = 0.0
+    return G
+
+
+def _grid(m, a):
+    a = np.asarray(a, np.float32)
+    return m.to_grid(a.reshape(-1, m.H, m.W))
+
+
+def _flat(m, t):
+    return m.from_grid(t).reshape(t.shape[0], -1).astype(np.float64)
+
+
+def _check_argmax(got, scores, scale, what):
+    """got: chosen index; scores: the oracle's candidates (FP64)."""
+    s = np.sort(scores)
+    top = s[-1]
+    if len(s) > 1 and top - s[-2] > GAP * scale:
+        assert got == int(np.argmax(scores)), f"{what}: {got} vs {int(np.argmax(scores))}"
+    else:
+        assert scores[got] >= top - GAP * scale, f"{what}: pick {got} scores {scores[got]} < max {top}"
+
+
+def test_init_matches_oracle(api):
+    for w in (WL.tiny(0), WL.diff(0, H=40, W=36), WL.mid(1, H=67, W=45)):
+        m = api.Model(w)
+        got = m.from_grid(api.pbvi_init(m)).reshape(-1)
+        _close(got, O.pbvi_init(w), rel=1e-6, floor=1.0, what="alpha0")
+
+
+@pytest.mark.parametrize("make", [lambda: WL.tiny(0), lambda: WL.tiny(3, H=13, W=17),
+                                  lambda: WL.mid(1, H=67, W=45), lambda: WL.large(0, H=96, W=80)])
+def test_expand_matches_oracle(api, make):
+    w = make()
+    m = api.Model(w)
+    B = _beliefs(w, 24, 1)
+    B[0] = w.b0.ravel()
+    for rnd in (0, 5):
+        g = api.pbvi_expand(m, _grid(m, B), rnd, seed=7)
+        o = O.pbvi_expand(w, B.astype(np.float64), rnd, seed=7)
+        assert np.array_equal(g["action"].cpu().numpy(), o["action"])
+        gz = g["obs"].cpu().numpy()
+        bad = (gz != o["obs"]) & (o["boundary"] == 0)
+        assert not bad.any(), f"{int(bad.sum())} observations differ away from a CDF step"
+        gp = _flat(m, g["points"])
+        for j in np.flatnonzero(gz == o["obs"]):
+            _close(gp[j], o["points"][j], what=f"point {j}")
+
+
+def _backup_case(api, w, nB, nG, seed, support=None):
+    m = api.Model(w)
+    B = _beliefs(w, nB, seed, support)
+    G = _vectors(w, nG, seed)
+    pb = api.Pbvi(m, max(nB, nG))
+    pb.set_points(_grid(m, B))
+    r = pb.backup(_grid(m, G))
+    torch.cuda.synchronize()
+    o = O.pbvi_backup(w, B.astype(np.float64), G.astype(np.float64), want_score=True)
+    scale = max(1.0, float(np.abs(o["q"]).max()))
+    gv = r["value"].cpu().numpy()
+    ga = r["astar"].cpu().numpy()
+    gb = r["best"].cpu().numpy()
+    gq = r["q"].cpu().numpy()
+    _close(gq, o["q"], floor=scale, what="Q_b(a)")
+    _close(gv, o["value"], floor=scale, what="value")
+    GG = _flat(m, r["G"])
+    clean = 0
+    for j in range(nB):
+        _check_argmax(int(ga[j]), o["q"][j], scale, f"a* of point {j}")
+        a = int(ga[j])
+        amb = False
+        for z in range(w.B + 1):
+            sc = o["score"][j, a, z]
+            _check_argmax(int(gb[j, z]), sc, scale, f"best of point {j} z {z}")
+            srt = np.sort(sc)
+            amb |= len(srt) > 1 and srt[-1] - srt[-2] <= GAP * scale
+        if a == o["astar"][j] and not amb:
+            _close(GG[j], o["G"][j], floor=scale, what=f"alpha of point {j}")
+            clean += 1
+        # the new vector gives the backed-up value at its own point
+        assert abs(GG[j] @ B[j].astype(np.float64) - gv[j]) <= REL * scale * 10
+        assert np.all(GG[j][_dead(w)] == 0.0)
+    assert clean >= nB // 2
+    return m, pb
+
+
+@pytest.mark.parametrize("make,nB,nG", [(lambda: WL.tiny(0), 5, 4), (lambda: WL.tiny(2, H=13, W=17), 7, 3),
+                                       (lambda: WL.diff(1, H=24, W=20), 6, 6)])
+def test_backup_matches_oracle(api, make, nB, nG):
+    _backup_case(api, make(), nB, nG, 3)
+
+
+def test_backup_many_tiles_and_pieces(api):
+    # 330 rows (6 tiles of 64) by 65 vectors (2 tiles), 17 labels, sparse
+    # beliefs so the oracle's literal sums stay short
+    w = WL.mid(2, H=67, W=45)
+    _backup_case(api, w, 66, 65, 4, support=40)
+
+
+def test_value_matches_oracle(api):
+    w = WL.mid(1, H=40, W=52)
+    m = api.Model(w)
+    G = _vectors(w, 70, 2)
+    b = _beliefs(w, 90, 2, support=60)
+    pb = api.Pbvi(m, 96)
+    pb.set_points(_grid(m, b[:1]))
+    v, arg = pb.value(_grid(m, G), _grid(m, b))
+    s = b.astype(np.float64) @ G.astype(np.float64).T
+    scale = max(1.0, float(np.abs(s).max()))
+    _close(v.cpu().numpy(), s.max(axis=1), floor=scale, what="V_PBVI")
+    for j, a in enumerate(arg.cpu().numpy()):
+        _check_argmax(int(a), s[j], scale, f"V_PBVI vector of belief {j}")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_solve_matches_oracle_schedule(api, seed):
+    w = WL.tiny(seed, H=10, W=11)
+    m = api.Model(w)
+    g = api.pbvi_solve(m, rounds=3, iters=12, seed=seed)
+    o = O.pbvi_solve(w, rounds=3, iters=12, seed=seed)
+    gB = _flat(m, g["B"])
+    assert gB.shape == o["B"].shape
+    _close(gB, o["B"], rel=1e-4, what="belief set")
+    scale = max(1.0, float(np.abs(o["value"]).max()))
+    _close(g["value"].cpu().numpy(), o["value"], rel=1e-4, floor=scale, what="V_PBVI at the points")
+
+
+def test_full_size_lower_bound_and_sampled_backups(api):
+    # the mid map: 64 points after six expansion rounds; V_PBVI below V_FIB
+    # at every point, and the oracle's own Eq. 8 backup at sampled points
+    # from the GPU's final vectors gives the GPU's backed-up values
+    w = WL.mid(0)
+    m = api.Model(w)
+    g = api.pbvi_solve(m, rounds=6, iters=8, seed=3)
+    fib = api.fib_value_iterate(m, dtype="f32")["Q"]
+    B = _flat(m, g["B"])
+    Gv = _flat(m, g["G"])
+    F = m.from_grid(fib).reshape(5, -1).astype(np.float64)
+    vf = (B @ F.T).max(axis=1)
+    vp = g["value"].cpu().numpy()
+    assert np.all(vp <= vf + 1e-4 * np.maximum(1.0, np.abs(vf)))
+    r = g["pbvi"].backup(g["G"])
+    gv = r["value"].cpu().numpy()
+    for j in (0, 37):
+        o = O.pbvi_backup(w, B[j:j + 1], Gv)
+        assert abs(gv[j] - o["value"][0]) <= REL * max(1.0, abs(o["value"][0])) * 10
+
+
+def test_large_map_one_round(api):
+    w = WL.large(1)
+    m = api.Model(w)
+    g = api.pbvi_solve(m, rounds=2, iters=3, seed=1)
+    B = _flat(m, g["B"])
+    Gv = _flat(m, g["G"])
+    r = g["pbvi"].backup(g["G"])
+    gv = r["value"].cpu().numpy()
+    o = O.pbvi_backup(w, B[3:4], Gv)
+    assert abs(gv[3] - o["value"][0]) <= REL * max(1.0, abs(o["value"][0])) * 10
+
+
+def test_errors(api):
+    from paper_1810_00204_gb300 import _native as N
+    w = WL.tiny(0)
+    m = api.Model(w)
+    pb = api.Pbvi(m, 4)
+    G = torch.zeros((8, m.H, m.P), dtype=torch.float32, device="cuda")
+    with pytest.raises(N.QVError) as ei:
+        pb.backup(G[:1])                      # no point set yet
+    assert ei.value.status == N.QV_ERR_INVALID
+    with pytest.raises(N.QVError):
+        pb.set_points(G[:5])                  # more points than the handle holds
+    pb.set_points(_grid(m, _beliefs(w, 2, 0)))
+    with pytest.raises(N.QVError):
+        pb.backup(G[:5])                      # more vectors than the handle holds
+    with pytest.raises(N.QVError):
+        pb.backup(G[:2], out=G[1:3])          # output overlaps the input
+    r = pb.backup(G[:2])
+    assert torch.isfinite(r["value"]).all()
