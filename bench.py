@@ -36,6 +36,9 @@ L2_FLUSH_BYTES = 256 << 20
 # iteration reads and writes five alpha planes and reads the cell word
 VI_BYTES_PER_CELL = 4 + 4 + 2
 FIB_BYTES_PER_CELL = 5 * 4 + 5 * 4 + 2
+# FP32 pipe peak of the GPU for the PBVI contraction (CUDA cores, FMA = 2
+# flops): 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -110,6 +113,56 @@ def offline_line(r, first_ms, ms, model, bytes_per_cell, peak):
     return {"sweeps": r["sweeps"], "ms": ms, "first_call_ms": first_ms, "cells": model.H * model.W,
             "us_per_sweep": 1e6 * sweep_s, "cell_sweeps_per_s": model.H * model.W * r["sweeps"] / (ms / 1e3),
             "bytes_per_cell_sweep": bytes_per_cell, "GBps": gbps, "frac_of_measured_hbm": gbps / peak}
+
+
+def pbvi_measurement(args, dev, K, flush, stream, with_cpu=True):
+    """The PBVI lower bound (Eq. 8) on the mid map: belief sets of 256 and
+    1024 points grown by the expansion rounds from b0, then one Eq. 8 backup
+    of every point timed with CUDA events (L2 flushed before each), with the
+    contraction's flops against the FP32 pipes' peak."""
+    import torch
+    import oracle as O
+    from paper_1810_00204_gb300 import api, workloads as WL
+    w = WL.mid(args.seed)
+    m = api.Model(w, device=dev)
+    out = {}
+    for rounds in (8, 10):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = api.pbvi_solve(m, rounds=rounds, iters=4, seed=args.seed)
+        torch.cuda.synchronize()
+        solve_ms = 1e3 * (time.perf_counter() - t0)
+        pb, G = g["pbvi"], g["G"]
+        nB, nG = g["B"].shape[0], G.shape[0]
+        Gout = torch.empty_like(G)
+        for _ in range(3):
+            pb.backup(G, out=Gout)
+        ms = time_device(lambda: pb.backup(G, out=Gout), K, flush, stream) / K
+        Kp, _ = pb.layout()
+        flops = 2.0 * 5 * nB * nG * Kp
+        tfl = flops / (ms * 1e-3) / 1e12
+        line = {"points": nB, "vectors": nG, "backup_ms": ms, "point_backups_per_s": nB / (ms * 1e-3),
+                "solve_ms": solve_ms, "solve_schedule": f"{rounds} expansion rounds, 4 backups after each",
+                "contraction": {"flops_per_backup": flops, "label_ordered_cells": Kp,
+                                "achieved_tflops_whole_backup": tfl, "fp32_alu_peak_tflops": FP32_ALU_PEAK_TFLOPS,
+                                "frac": tfl / FP32_ALU_PEAK_TFLOPS, "bound": "alu"},
+                "v_pbvi_b0": float(g["value"][0])}
+        if with_cpu and rounds == 8:
+            # the oracle's Eq. 8 backup of a few points against the same vectors
+            Bh = m.from_grid(g["B"]).reshape(nB, -1).astype("float64")
+            Gh = m.from_grid(G).reshape(nG, -1).astype("float64")
+            npts = max(1, min(O.num_threads(), 8))
+            t0 = time.perf_counter()
+            O.pbvi_backup(w, Bh[:npts], Gh)
+            el = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": npts / el, "unit": "point backups/s", "cores": O.num_threads(),
+                                    "kind": "oracle",
+                                    "sample": f"{npts} of the {nB} points backed up against all {nG} vectors, "
+                                              f"{el:.1f} s, FP64 C oracle with OpenMP over points"}
+        out[f"points_{nB}"] = line
+        del g, pb, G, Gout
+        torch.cuda.empty_cache()
+    return out
 
 
 def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
@@ -203,6 +256,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     out["gradient_diff_128"] = gradient_measurement(args, dev, K, peak)
     # (5) the single-belief primitives of the C ABI on inputs larger than L2
     out["primitives"] = primitive_measurement(args, dev, K, peak)
+    # (6) the PBVI lower bound (Eq. 8) on the mid map
+    out["pbvi_mid"] = pbvi_measurement(args, dev, K, flush, stream, with_cpu=not args.no_cpu)
     return out
 
 
@@ -534,6 +589,10 @@ def main():
             out = {"workload": desc, "vi": offline_line(vi, f, t, model, VI_BYTES_PER_CELL, peak)}
             fib, f, t = time_offline(lambda: api.fib_value_iterate(model, dtype="f32", want_alpha=False))
             out["fib"] = offline_line(fib, f, t, model, FIB_BYTES_PER_CELL, peak)
+            if args.workload == "mid":
+                flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+                out["pbvi"] = pbvi_measurement(args, dev, max(3, args.extra_steps), flush, stream,
+                                               with_cpu=not args.no_cpu)
             print(json.dumps(out), flush=True)
         return
     R = args.plans_per_step

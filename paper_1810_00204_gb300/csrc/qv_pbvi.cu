@@ -17,8 +17,8 @@
 // a matrix product over one contiguous range of that order.  Long ranges are
 // cut into pieces so the grid fills the GPU; a piece's partial product is one
 // slab, and the selection kernel adds the slabs of a label in piece order.
-// The products run on the FP32 pipes, register-blocked 4x4 per thread on
-// 64x64 tiles with 16-deep shared-memory stages.
+// The products run on the FP32 pipes, register-blocked 8x8 per thread on
+// 128x128 tiles with double-buffered 16-deep shared-memory stages.
 //
 // The selection kernel takes, per point, every (a, z) argmax over Gamma, the
 // action a* maximising Q_b(a) = R(b, a) + gamma sum_z max_i s, and the set of
@@ -40,7 +40,7 @@ namespace {
 
 constexpr int kPbThreads = 256;
 constexpr int kKC = 16;          // K depth of one contraction stage; label runs are padded to it
-constexpr int kTM = 64, kTN = 64;
+constexpr int kTM = 128, kTN = 128;
 constexpr int kPiecesExtra = 64; // pieces beyond one per label
 
 struct PbModel {
@@ -281,59 +281,97 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restr
 
 // ---------------------------------------------------------------- the contraction
 // slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k]; grid (M tiles, N
-// tiles, pieces); both operands K-contiguous rows of Kp floats.
-__global__ void __launch_bounds__(kPbThreads) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
-                                                            int M, int N, int Kp, const int *__restrict__ piece,
-                                                            float *__restrict__ slab) {
-    __shared__ __align__(16) float As[kKC][kTM + 4];
-    __shared__ __align__(16) float Bs[kKC][kTN + 4];
+// tiles, pieces); both operands are K-contiguous rows of Kp floats.  A CTA
+// computes a 128 x 128 tile, each thread an 8 x 8 block (rows ty*4 + i and
+// 64 + ty*4 + i, columns likewise), from 16-deep stages held k-major in
+// shared memory.  The next stage's global loads are issued into registers
+// before the current stage's arithmetic and stored to the other buffer after
+// it (one barrier per stage).  A warp loads 32 consecutive rows of one
+// 4-wide k group, so its transposing stores hit 32 consecutive words.
+__global__ void __launch_bounds__(kPbThreads, 2) k_pbvi_scores(const float *__restrict__ A,
+                                                               const float *__restrict__ Bm, int M, int N, int Kp,
+                                                               const int *__restrict__ piece,
+                                                               float *__restrict__ slab) {
+    __shared__ __align__(16) float As[2][kKC][kTM + 4];
+    __shared__ __align__(16) float Bs[2][kKC][kTN + 4];
     const int p = blockIdx.z;
     const int k0 = __ldg(piece + 3 * p), k1 = __ldg(piece + 3 * p + 1);
     const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    // loader: row lr of the tile, 4 consecutive k at lk
-    const int lr = tid >> 2, lk = (tid & 3) * 4;
-    const bool a_ok = m0 + lr < M, b_ok = n0 + lr < N;
-    const float *ap = A + static_cast<size_t>(m0 + lr) * Kp + lk;
-    const float *bp = Bm + static_cast<size_t>(n0 + lr) * Kp + lk;
-    float acc[4][4];
+    // loader: float4 number t = tid + 256 h covers row (t & 31) + 32 (t >> 7)
+    // of the tile and k group (t >> 5) & 3, i.e. rows lrow and lrow + 64 of
+    // one k group
+    const int lrow = (tid & 31) + 32 * (tid >> 7), lk = ((tid >> 5) & 3) * 4;
+    const bool aok0 = m0 + lrow < M, aok1 = m0 + lrow + 64 < M;
+    const bool bok0 = n0 + lrow < N, bok1 = n0 + lrow + 64 < N;
+    const float *ap = A + static_cast<size_t>(aok0 ? m0 + lrow : 0) * Kp + lk;
+    const float *bp = Bm + static_cast<size_t>(bok0 ? n0 + lrow : 0) * Kp + lk;
+    const size_t far = static_cast<size_t>(64) * Kp;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 ra0, ra1, rb0, rb1;
+    auto load = [&](int k) {
+        ra0 = aok0 ? __ldg(reinterpret_cast<const float4 *>(ap + k)) : zero4;
+        ra1 = aok1 ? __ldg(reinterpret_cast<const float4 *>(ap + far + k)) : zero4;
+        rb0 = bok0 ? __ldg(reinterpret_cast<const float4 *>(bp + k)) : zero4;
+        rb1 = bok1 ? __ldg(reinterpret_cast<const float4 *>(bp + far + k)) : zero4;
+    };
+    auto store = [&](int buf) {
+        As[buf][lk + 0][lrow] = ra0.x;
+        As[buf][lk + 1][lrow] = ra0.y;
+        As[buf][lk + 2][lrow] = ra0.z;
+        As[buf][lk + 3][lrow] = ra0.w;
+        As[buf][lk + 0][lrow + 64] = ra1.x;
+        As[buf][lk + 1][lrow + 64] = ra1.y;
+        As[buf][lk + 2][lrow + 64] = ra1.z;
+        As[buf][lk + 3][lrow + 64] = ra1.w;
+        Bs[buf][lk + 0][lrow] = rb0.x;
+        Bs[buf][lk + 1][lrow] = rb0.y;
+        Bs[buf][lk + 2][lrow] = rb0.z;
+        Bs[buf][lk + 3][lrow] = rb0.w;
+        Bs[buf][lk + 0][lrow + 64] = rb1.x;
+        Bs[buf][lk + 1][lrow + 64] = rb1.y;
+        Bs[buf][lk + 2][lrow + 64] = rb1.z;
+        Bs[buf][lk + 3][lrow + 64] = rb1.w;
+    };
+    float acc[8][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    int buf = 0;
+    if (k0 < k1) {
+        load(k0);
+        store(0);
+    }
+    __syncthreads();
     for (int k = k0; k < k1; k += kKC) {
-        const float4 av = a_ok ? __ldg(reinterpret_cast<const float4 *>(ap + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 bv = b_ok ? __ldg(reinterpret_cast<const float4 *>(bp + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        As[lk + 0][lr] = av.x;
-        As[lk + 1][lr] = av.y;
-        As[lk + 2][lr] = av.z;
-        As[lk + 3][lr] = av.w;
-        Bs[lk + 0][lr] = bv.x;
-        Bs[lk + 1][lr] = bv.y;
-        Bs[lk + 2][lr] = bv.z;
-        Bs[lk + 3][lr] = bv.w;
-        __syncthreads();
+        const bool more = k + kKC < k1;
+        if (more) load(k + kKC);
 #pragma unroll
         for (int kk = 0; kk < kKC; ++kk) {
-            const float4 a4 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-            const float ar[4] = {a4.x, a4.y, a4.z, a4.w};
-            const float br[4] = {b4.x, b4.y, b4.z, b4.w};
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
         }
+        if (more) store(buf ^ 1);  // the other buffer: last read before the previous barrier
+        __syncthreads();
+        buf ^= 1;
     }
     float *out = slab + static_cast<size_t>(p) * M * N;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int mm = m0 + ty * 4 + i;
+    for (int i = 0; i < 8; ++i) {
+        const int mm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
         if (mm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int nn = n0 + tx * 4 + j;
+        for (int j = 0; j < 8; ++j) {
+            const int nn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
             if (nn < N) out[static_cast<size_t>(mm) * N + nn] = acc[i][j];
         }
     }
