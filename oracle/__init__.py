@@ -92,6 +92,8 @@ def lib():
         L.or_pbvi_expand.restype = C.c_int
         L.or_pbvi_backup.argtypes = [P, vp, C.c_int, vp, C.c_int, vp, vp, vp, vp, vp, vp]
         L.or_pbvi_backup.restype = C.c_int
+        L.or_tree_bounds.argtypes = [C.c_int] + [vp] * 9 + [C.c_double] + [vp] * 6
+        L.or_tree_bounds.restype = C.c_int
         _lib = L
     return _lib
 
@@ -383,7 +385,7 @@ def tree_plan(w, Q, depth=None, K=None, seed=None, episode=None, weight_mode=FRE
                n_level=n_level.copy(), off=off, depth=depth, K=K,
                samples_flat=samples, boundary_flat=boundary,
                flat=dict(n_level=n_level, parent=parent, action=action, obs=obs, weight=weight,
-                         pz=pz, UQ=UQ, belief=belief, store_levels=store_levels))
+                         pz=pz, UQ=UQ, R=R, value=value, belief=belief, store_levels=store_levels))
     lv = {k: [] for k in ("parent", "action", "obs", "weight", "pz", "value", "R", "UQ",
                           "samples", "boundary", "belief")}
     for l in range(depth + 1):
@@ -401,6 +403,37 @@ def tree_plan(w, Q, depth=None, K=None, seed=None, episode=None, weight_mode=FRE
         if belief is not None and l <= store_levels:
             lv["belief"].append(belief[s * p.n:(s + n) * p.n].reshape(n, p.n))
     out.update(lv)
+    return out
+
+
+def tree_bounds(tree, Lleaf, gamma):
+    """AEMS bookkeeping of Alg. 5-7 and Eq. 9 over a tree_plan tree given the
+    lower bound of every leaf (Lleaf [n_leaves]).  Returns per-level lists
+    LV, HV, EV (EV: index of a leaf in the deepest level) and LQ, HQ, EQ
+    ([n][5], internal levels)."""
+    f = tree["flat"]
+    depth, off = tree["depth"], np.ascontiguousarray(tree["off"], np.int64)
+    tot = int(off[-1])
+    Ll = np.ascontiguousarray(np.asarray(Lleaf, np.float64).reshape(-1))
+    assert Ll.size == int(f["n_level"][depth])
+    LV = np.zeros(tot, np.float64)
+    HV = np.zeros(tot, np.float64)
+    EV = np.full(tot, -1, np.int32)
+    LQ = np.zeros(tot * A, np.float64)
+    HQ = np.zeros(tot * A, np.float64)
+    EQ = np.full(tot * A, -1, np.int32)
+    lib().or_tree_bounds(depth, _p(off), _p(f["n_level"]), _p(f["parent"]), _p(f["action"]), _p(f["weight"]),
+                         _p(f["R"]), _p(f["UQ"]), _p(f["value"]), _p(Ll), float(gamma), _p(LV), _p(HV), _p(EV),
+                         _p(LQ), _p(HQ), _p(EQ))
+    out = {k: [] for k in ("LV", "HV", "EV", "LQ", "HQ", "EQ")}
+    for l in range(depth + 1):
+        s, n = int(off[l]), int(f["n_level"][l])
+        out["LV"].append(LV[s:s + n])
+        out["HV"].append(HV[s:s + n])
+        out["EV"].append(EV[s:s + n])
+        out["LQ"].append(LQ[s * A:(s + n) * A].reshape(n, A))
+        out["HQ"].append(HQ[s * A:(s + n) * A].reshape(n, A))
+        out["EQ"].append(EQ[s * A:(s + n) * A].reshape(n, A))
     return out
 
 

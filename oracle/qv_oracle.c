@@ -877,3 +877,70 @@ int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G
     free(label); free(R);
     return 0;
 }
+
+/* ---- AEMS bookkeeping over a tree (Alg. 5-7, Eq. 9) --------------------- */
+
+/* Lower bounds, heuristics and the V-node to expand, bottom-up over the
+ * flat arrays of an or_tree_plan tree (level l at [off[l], off[l] + n_level[l]),
+ * children ordered by (parent, action, z)).  Leaves (level depth, Alg. 5):
+ * L_V = Lleaf[j] (V_PBVI of the leaf belief), H_V = U_V - L_V, E_V = the
+ * leaf itself (its index within the leaf level).  Q-node (Alg. 6, discounted
+ * like U_Q): L_Q = R + gamma sum_children weight L_V; the child maximising
+ * gamma weight H_V (ties: the first in order) gives H_Q = gamma weight H_V
+ * and E_Q = its E_V.  V-node (Alg. 7 with Eq. 9's H(b, a) = 1 for the action
+ * maximising U_Q, ties to the lowest): L_V = max_a L_Q, H_V = H_Q and
+ * E_V = E_Q of that action.  A Q-node without children keeps L_Q = R,
+ * H_Q = 0, E_Q = -1.  Outputs: LV, HV, EV [tot]; LQ, HQ, EQ [tot * 5]
+ * (internal nodes).                                                       */
+int or_tree_bounds(int depth, const long *off, const int *n_level, const int *parent, const int *action,
+                   const double *weight, const double *R, const double *UQ, const double *value,
+                   const double *Lleaf, double gamma, double *LV, double *HV, int *EV, double *LQ,
+                   double *HQ, int *EQ) {
+    const int A = OR_NUM_ACTIONS;
+    const long s = off[depth];
+    for (int j = 0; j < n_level[depth]; ++j) {
+        LV[s + j] = Lleaf[j];
+        HV[s + j] = value[s + j] - Lleaf[j];
+        EV[s + j] = j;
+    }
+    for (int l = depth - 1; l >= 0; --l) {
+        const long sl = off[l], sc = off[l + 1];
+        const int n = n_level[l], nc = n_level[l + 1];
+        for (int i = 0; i < n; ++i)
+            for (int a = 0; a < A; ++a) {
+                const long q = (sl + i) * A + a;
+                LQ[q] = R[q];
+                HQ[q] = 0.0;
+                EQ[q] = -1;
+            }
+        double *sum = (double *)calloc((size_t)n * A, sizeof(double));
+        int *have = (int *)calloc((size_t)n * A, sizeof(int));
+        for (int j = 0; j < nc; ++j) {
+            const int i = parent[sc + j], a = action[sc + j];
+            const long q = (sl + i) * A + a;
+            const double w = weight[sc + j];
+            sum[(long)i * A + a] += w * LV[sc + j];
+            const double h = gamma * w * HV[sc + j];
+            if (!have[(long)i * A + a] || h > HQ[q]) {
+                HQ[q] = h;
+                EQ[q] = EV[sc + j];
+                have[(long)i * A + a] = 1;
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            double lmax = -HUGE_VAL;
+            int au = 0;
+            for (int a = 0; a < A; ++a) {
+                const long q = (sl + i) * A + a;
+                if (have[(long)i * A + a]) LQ[q] = R[q] + gamma * sum[(long)i * A + a];
+                if (LQ[q] > lmax) lmax = LQ[q];
+                if (UQ[q] > UQ[(sl + i) * A + au]) au = a;
+            }
+            LV[sl + i] = lmax;
+            HV[sl + i] = HQ[(sl + i) * A + au];
+            EV[sl + i] = EQ[(sl + i) * A + au];
+        }
+        free(sum); free(have);
+    }
+    return 0;
+}

@@ -118,6 +118,12 @@ int or_pbvi_expand(const or_problem *p, const double *B, int nB, int round, uint
 int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G, int nG, double *Gout,
                    double *value, int *astar, int *best, double *q, double *score);
 
+/* ---- AEMS bookkeeping (Alg. 5-7, Eq. 9) ---- */
+int or_tree_bounds(int depth, const long *off, const int *n_level, const int *parent, const int *action,
+                   const double *weight, const double *R, const double *UQ, const double *value,
+                   const double *Lleaf, double gamma, double *LV, double *HV, int *EV, double *LQ,
+                   double *HQ, int *EQ);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
