@@ -221,8 +221,9 @@ qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
  * point d_value [nB] (= d_Gout[b] . b), the chosen action d_astar [nB] (ties
  * to the lowest), the winning vector of each observation for that action
  * d_best [nB][B + 1] (ties to the lowest index), d_q [nB][5] every Q_b(a).
- * qv_pbvi_value: V_PBVI(b) and its maximising vector for nb <= max_points
- * beliefs d_b given nG vectors d_G.
+ * qv_pbvi_value: V_PBVI(b) and its maximising vector (ties to the lowest
+ * index) for nb beliefs d_b given nG <= max_points vectors d_G (the beliefs
+ * go through in chunks of max_points).
  * The host may upload small tables (pageable copies) on the stream; none of
  * these calls synchronises except qv_pbvi_create. */
 typedef struct qv_pbvi qv_pbvi_t;
@@ -381,6 +382,38 @@ typedef struct {
     const int32_t *d_leaf_arg; /* leaves: argmax a' of sum_y b(y) Q(a', y), else NULL  */
 } qv_level_view_t;
 qv_status qv_plan_level(const qv_plan_t *plan, int32_t e, int32_t level, qv_level_view_t *view);
+
+/* ---------------------------------------------------------------- AEMS fields (Alg. 5-7, Eq. 9)
+ * qv_plan_bounds: the lower bound L, heuristic H and V-node to expand E of
+ * every node of episode e of a plan that has run, bottom-up from the lower
+ * bound of every leaf, d_leaf_L [leaves] (for example V_PBVI of the leaf
+ * beliefs from qv_pbvi_value; the leaf level's order is qv_plan_level's):
+ *   leaf     L_V = d_leaf_L, H_V = U_V - L_V, E_V = its own index
+ *   Q-node   L_Q = R(b, a) + gamma sum_children w L_V; the child maximising
+ *            gamma w H_V (ties: first in (parent, action, z) order) gives
+ *            H_Q = gamma w H_V and E_Q = its E_V; no children: L_Q = R,
+ *            H_Q = 0, E_Q = -1
+ *   V-node   L_V = max_a L_Q; H_V, E_V = H_Q, E_Q of the action maximising
+ *            U_Q (H(b, a) of Eq. 9; ties to the lowest)
+ * E values index the leaf level.  The root's E is the V-node the paper's
+ * search would expand next.  Results live in the caller's workspace of
+ * qv_plan_bounds_workspace_bytes (256-byte aligned); qv_plan_bounds_view
+ * gives level l's arrays ([cap] per node, [cap][5] per Q-node, Q arrays NULL
+ * at the leaf level).  Asynchronous, except that a fused-mode plan's leaf
+ * records are written first (qv_plan_level's synchronisation). */
+typedef struct {
+    float *d_LV;
+    float *d_HV;
+    int32_t *d_EV;
+    float *d_LQ;
+    float *d_HQ;
+    int32_t *d_EQ;
+} qv_bounds_view_t;
+size_t qv_plan_bounds_workspace_bytes(const qv_plan_t *plan, int32_t e);
+qv_status qv_plan_bounds(const qv_plan_t *plan, int32_t e, const float *d_leaf_L, void *d_ws,
+                         size_t ws_bytes, qv_stream_t stream);
+qv_status qv_plan_bounds_view(const qv_plan_t *plan, int32_t e, int32_t level, void *d_ws,
+                              qv_bounds_view_t *view);
 
 /* ---------------------------------------------------------------- adjoint of the plan
  * qv_tree_backward: reverse mode of the root value U_V(b0) of episode e of a

@@ -56,6 +56,11 @@ class qv_level_view_t(C.Structure):
                 ("d_leaf_arg", C.c_void_p)]
 
 
+class qv_bounds_view_t(C.Structure):
+    _fields_ = [("d_LV", C.c_void_p), ("d_HV", C.c_void_p), ("d_EV", C.c_void_p), ("d_LQ", C.c_void_p),
+                ("d_HQ", C.c_void_p), ("d_EQ", C.c_void_p)]
+
+
 class qv_launch_time_t(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("level", C.c_int32), ("ms", C.c_float)]
 
@@ -101,6 +106,9 @@ SIGNATURES = {
     "qv_plan_decode": (C.c_int, [_vp, _vp, C.POINTER(qv_plan_result_t)]),
     "qv_plan_destroy": (None, [_vp]),
     "qv_plan_profile": (C.c_int, [_vp, C.POINTER(qv_launch_time_t), _i32, C.POINTER(C.c_int32), _vp]),
+    "qv_plan_bounds_workspace_bytes": (_sz, [_vp, _i32]),
+    "qv_plan_bounds": (C.c_int, [_vp, _i32, _vp, _vp, _sz, _vp]),
+    "qv_plan_bounds_view": (C.c_int, [_vp, _i32, _i32, _vp, C.POINTER(qv_bounds_view_t)]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
     "qv_plan_autotune_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_autotune": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, _i32, C.POINTER(qv_tune_t),

@@ -441,6 +441,39 @@ class Plan:
             out["belief"] = None if t is None else t[:n]
         return out
 
+    def bounds(self, leaf_L: torch.Tensor, e: int = 0, stream=None) -> List[dict]:
+        """AEMS fields of episode e (Alg. 5-7, Eq. 9) from the lower bound of
+        every leaf (leaf_L [leaves], float32): per level dict(LV, HV, EV and,
+        below the leaves, LQ, HQ, EQ [n][5]); EV/EQ index the leaf level."""
+        nbytes = lib().qv_plan_bounds_workspace_bytes(self.handle, e)
+        ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.models[e].device)
+        ptr = C.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+        check(lib().qv_plan_bounds(self.handle, e, _ptr(leaf_L.contiguous()), ptr, nbytes, _stream(stream)),
+              "qv_plan_bounds")
+        out = []
+        for l in range(self.depth + 1):
+            v = N.qv_bounds_view_t()
+            check(lib().qv_plan_bounds_view(self.handle, e, l, ptr, C.byref(v)), "qv_plan_bounds_view")
+            lv = N.qv_level_view_t()
+            check(lib().qv_plan_level(self.handle, e, l, C.byref(lv)), "qv_plan_level")
+            cap = lv.cap
+            n = int(self._view(lv.d_count, 1, torch.int32).item())
+            d = dict(count=n)
+
+            def view(p_, count, dt):
+                off = p_ - ws.data_ptr()
+                return ws[off:off + 4 * count].view(dt)
+
+            for key, p_, dt in (("LV", v.d_LV, torch.float32), ("HV", v.d_HV, torch.float32),
+                                ("EV", v.d_EV, torch.int32)):
+                d[key] = view(p_, cap, dt)[:n]
+            for key, p_, dt in (("LQ", v.d_LQ, torch.float32), ("HQ", v.d_HQ, torch.float32),
+                                ("EQ", v.d_EQ, torch.int32)):
+                d[key] = view(p_, cap * 5, dt).view(cap, 5)[:n] if p_ else None
+            out.append(d)
+        out[0]["_ws"] = ws  # keeps the workspace the views point into alive
+        return out
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h is not None and h.value:

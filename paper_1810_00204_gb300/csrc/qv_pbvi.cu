@@ -832,25 +832,30 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
                                    float *d_value, int32_t *d_arg, qv_stream_t stream) {
     if (!h || !d_G || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: null pointer");
     if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: no workspace yet (qv_pbvi_set_points)");
-    if (nG < 1 || nG > h->max_vectors || nb < 1 || nb > h->max_points)
+    if (nG < 1 || nG > h->max_vectors || nb < 0)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: %d vectors, %d beliefs", nG, nb);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(h->ws);
     const int Kp = h->Kp, N = h->model.H * h->model.pitch;
-    const int Mt = (nb + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
-    std::vector<int> pc;
-    make_pieces(*h, Mt * Nt, Kp, false, pc);
-    if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
-    const int npieces = static_cast<int>(pc.size() / 3);
     float *Ap = reinterpret_cast<float *>(ws + h->off_Ap);
     float *Gp = reinterpret_cast<float *>(ws + h->off_Gp);
     float *slab = reinterpret_cast<float *>(ws + h->off_slab);
     const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
     const int gb = 8 * qv_num_sms();
-    qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b, nb, N, perm, Kp, Ap);
     qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, Kp, Gp);
-    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
-        Ap, Gp, nb, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab);
-    qv::k_pbvi_rowmax<<<nb, qv::kPbThreads, 0, st>>>(nb, nG, npieces, slab, d_value, d_arg);
+    // beliefs in chunks of up to max_points (the size of the Ap region)
+    for (int c0 = 0; c0 < nb; c0 += h->max_points) {
+        const int nc = std::min(h->max_points, nb - c0);
+        const int Mt = (nc + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
+        std::vector<int> pc;
+        make_pieces(*h, Mt * Nt, Kp, false, pc);
+        if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
+        const int npieces = static_cast<int>(pc.size() / 3);
+        qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, Kp, Ap);
+        qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
+            Ap, Gp, nc, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab);
+        qv::k_pbvi_rowmax<<<nc, qv::kPbThreads, 0, st>>>(nc, nG, npieces, slab, d_value + c0,
+                                                         d_arg ? d_arg + c0 : nullptr);
+    }
     return qv_check_cuda(cudaGetLastError(), "qv_pbvi_value launch");
 }
