@@ -165,6 +165,55 @@ def pbvi_measurement(args, dev, K, flush, stream, with_cpu=True):
     return out
 
 
+def aems_measurement(args, dev, K, stream):
+    """The paper's node fields on the mid map (Alg. 5-7, Eq. 9): U from FIB
+    leaf alpha-vectors, L from PBVI at the materialised leaf beliefs (256
+    points), then L, H and E up to the root.  Times each stage with CUDA
+    events (inputs resident, after warm-up)."""
+    import torch
+    from paper_1810_00204_gb300 import _native as N
+    from paper_1810_00204_gb300 import api, workloads as WL
+    w = WL.mid(args.seed)
+    m = api.Model(w, device=dev)
+    Q = api.fib_value_iterate(m, dtype="f32", want_alpha=False)["Q"]
+    g = api.pbvi_solve(m, rounds=8, iters=4, seed=args.seed)
+    plan = api.Plan([m], [Q], [m.b0()], depth=w.depth, K=w.K, seed=w.seed, episode=w.episode,
+                    leaf_mode=N.QV_LEAF_MATERIALISE)
+    plan.run()
+    leaves = plan.level(0, w.depth)
+    nleaf = leaves["count"]
+    lb = leaves["belief"]
+    L = torch.empty(nleaf, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(K):
+            fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / K
+
+    ms_plan = timed(plan.run)
+    ms_leafL = timed(lambda: L.copy_(g["pbvi"].value(g["G"], lb)[0]))
+    b = plan.bounds(L)
+    ms_bounds = timed(lambda: plan.bounds(L))
+    b = plan.bounds(L)
+    res = plan.read()[0]
+    Kp, _ = g["pbvi"].layout()
+    nG = g["G"].shape[0]
+    return {"leaves": nleaf, "pbvi_vectors": nG, "plan_ms": ms_plan, "leaf_pbvi_value_ms": ms_leafL,
+            "leaf_pbvi_tflops": 2.0 * nleaf * nG * Kp / (ms_leafL * 1e-3) / 1e12,
+            "bounds_ms_incl_host": ms_bounds,
+            "root": {"U": res["value"], "L": float(b[0]["LV"][0]), "H": float(b[0]["HV"][0]),
+                     "E_leaf": int(b[0]["EV"][0])},
+            "note": "plan in the materialised mode with FIB leaves; bounds_ms includes the host-side level "
+                    "views and the per-level launches"}
+
+
 def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
     """Sub-measurements beside the headline: the step's requests as one
     batched launch, the 256-episode batch of uneven maps, and the 512x512
@@ -258,6 +307,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     out["primitives"] = primitive_measurement(args, dev, K, peak)
     # (6) the PBVI lower bound (Eq. 8) on the mid map
     out["pbvi_mid"] = pbvi_measurement(args, dev, K, flush, stream, with_cpu=not args.no_cpu)
+    # (7) the paper's node fields U, L, H, E on the mid map
+    out["aems_fields_mid"] = aems_measurement(args, dev, K, stream)
     return out
 
 
@@ -593,6 +644,7 @@ def main():
                 flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
                 out["pbvi"] = pbvi_measurement(args, dev, max(3, args.extra_steps), flush, stream,
                                                with_cpu=not args.no_cpu)
+                out["aems_fields"] = aems_measurement(args, dev, max(3, args.extra_steps), stream)
             print(json.dumps(out), flush=True)
         return
     R = args.plans_per_step
