@@ -94,6 +94,9 @@ def lib():
         L.or_pbvi_backup.restype = C.c_int
         L.or_tree_bounds.argtypes = [C.c_int] + [vp] * 9 + [C.c_double] + [vp] * 6
         L.or_tree_bounds.restype = C.c_int
+        L.or_bestfirst.argtypes = ([P, vp, vp, C.c_int, vp, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
+                                    C.c_int, vp, vp] + [vp] * 18)
+        L.or_bestfirst.restype = C.c_int
         _lib = L
     return _lib
 
@@ -434,6 +437,47 @@ def tree_bounds(tree, Lleaf, gamma):
         out["LQ"].append(LQ[s * A:(s + n) * A].reshape(n, A))
         out["HQ"].append(HQ[s * A:(s + n) * A].reshape(n, A))
         out["EQ"].append(EQ[s * A:(s + n) * A].reshape(n, A))
+    return out
+
+
+def bestfirst(w, Qu, G, iters, K=None, seed=None, episode=None, max_depth=6, max_nodes=None, b0=None, **kw):
+    """Alg. 1's best-first planning loop: `iters` expansions of the V-node the
+    root's E points at, U from the upper-bound alpha-vectors Qu [5][n] (FIB),
+    L from the PBVI vectors G [nG][n].  Returns dict with per-node arrays
+    (parent, action, obs, depth, weight, U, L, H, E, belief), per Q-node
+    arrays [nodes][5] (R, UQ, LQ, HQ, EQ, first, count), expanded [iters],
+    iterations, nodes, boundary, root_action."""
+    p = _prob(w, **kw)
+    ww = p.w
+    K = ww.K if K is None else K
+    seed = ww.seed if seed is None else seed
+    episode = ww.episode if episode is None else episode
+    nz = p.B + 1
+    max_nodes = 1 + iters * A * min(K, nz) if max_nodes is None else max_nodes
+    Qu = np.ascontiguousarray(np.asarray(Qu, np.float64).reshape(A, p.n))
+    G = np.ascontiguousarray(np.asarray(G, np.float64).reshape(-1, p.n))
+    b0 = ww.b0 if b0 is None else b0
+    b0 = np.ascontiguousarray(np.asarray(b0, np.float64).reshape(-1))
+    bel = np.zeros((max_nodes, p.n), np.float64)
+    i32 = lambda m: np.zeros(m, np.int32)
+    f64 = lambda m: np.zeros(m, np.float64)
+    o = dict(expanded=i32(iters), parent=i32(max_nodes), action=i32(max_nodes), obs=i32(max_nodes),
+             depth=i32(max_nodes), weight=f64(max_nodes), U=f64(max_nodes), L=f64(max_nodes), H=f64(max_nodes),
+             E=i32(max_nodes), R=f64(max_nodes * A), UQ=f64(max_nodes * A), LQ=f64(max_nodes * A),
+             HQ=f64(max_nodes * A), EQ=i32(max_nodes * A), first=i32(max_nodes * A), count=i32(max_nodes * A))
+    nn = C.c_int(0)
+    bd = C.c_long(0)
+    it = lib().or_bestfirst(p.ref, _p(Qu), _p(G), G.shape[0], _p(b0), int(K), int(seed), int(episode), int(iters),
+                            int(max_depth), int(max_nodes), _p(bel), C.byref(nn), _p(o["expanded"]),
+                            _p(o["parent"]), _p(o["action"]), _p(o["obs"]), _p(o["depth"]), _p(o["weight"]),
+                            _p(o["U"]), _p(o["L"]), _p(o["H"]), _p(o["E"]), _p(o["R"]), _p(o["UQ"]), _p(o["LQ"]),
+                            _p(o["HQ"]), _p(o["EQ"]), _p(o["first"]), _p(o["count"]), C.byref(bd))
+    m = nn.value
+    out = {k: v[:m] for k, v in o.items() if k != "expanded" and v.size == max_nodes}
+    for k in ("R", "UQ", "LQ", "HQ", "EQ", "first", "count"):
+        out[k] = o[k][:m * A].reshape(m, A)
+    out.update(expanded=o["expanded"], iterations=it, nodes=m, boundary=bd.value, belief=bel[:m],
+               root_action=int(np.argmax(out["UQ"][0])) if out["count"][0].sum() else -1)
     return out
 
 

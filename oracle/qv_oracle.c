@@ -944,3 +944,139 @@ int or_tree_bounds(int depth, const long *off, const int *n_level, const int *pa
     }
     return 0;
 }
+
+/* ---- Best-first QV-Tree Search (Alg. 1 inner loop, Alg. 2-7, Eq. 9) ----- */
+
+/* Recompute Q-node (v, a) from its children (Alg. 6) and V-node v from its
+ * Q-nodes (Alg. 7 with Eq. 9's H(b, a)); the same rules as or_tree_bounds. */
+static void bf_update_node(int v, double gamma, const int *cbeg, const int *ccnt, const double *Rq,
+                           const double *w, double *U, double *L, double *Hh, int *E, double *UQ, double *LQ,
+                           double *HQ, int *EQ) {
+    const int A = OR_NUM_ACTIONS;
+    for (int a = 0; a < A; ++a) {
+        const int q = v * A + a;
+        double su = 0.0, sl = 0.0, bh = 0.0;
+        int be = -1;
+        for (int c = cbeg[q]; c < cbeg[q] + ccnt[q]; ++c) {
+            su += w[c] * U[c];
+            sl += w[c] * L[c];
+            const double h = gamma * w[c] * Hh[c];
+            if (be < 0 || h > bh) { bh = h; be = E[c]; }
+        }
+        UQ[q] = Rq[q] + gamma * su;
+        LQ[q] = Rq[q] + gamma * sl;
+        HQ[q] = bh;
+        EQ[q] = be;
+    }
+    int au = 0;
+    double lmax = LQ[v * A];
+    for (int a = 1; a < A; ++a) {
+        if (UQ[v * A + a] > UQ[v * A + au]) au = a;
+        if (LQ[v * A + a] > lmax) lmax = LQ[v * A + a];
+    }
+    U[v] = UQ[v * A + au];
+    L[v] = lmax;
+    Hh[v] = HQ[v * A + au];
+    E[v] = EQ[v * A + au];
+}
+
+/* Alg. 1's planning loop: starting from the root V-node of b0 (U = V_U(b0)
+ * with the upper-bound alpha-vectors Qu, e.g. FIB; L = V_PBVI(b0) =
+ * max_i G_i . b0; H = U - L; E = root), each iteration expands the V-node
+ * the root's E points at (Alg. 2: all five actions; Alg. 3: K forward
+ * samples of z, the unique ones with frequencies f, children tau(b, a, z)
+ * with weight f / K, Alg. 5: U, L, H, E of each child) and updates it and
+ * its ancestors (Alg. 6-7).  Node ids are assigned in creation order,
+ * children of a Q-node in ascending z.  The samples of (V-node, a) are the
+ * Philox stream of the level-synchronous tree: level = depth, path = the
+ * node's mixed-radix code * 5 + a.  A node created at max_depth is closed:
+ * its H is 0, so the search turns elsewhere.  Planning stops early when the
+ * node to expand lies at max_depth (every open gap is 0) or the next
+ * expansion could overflow max_nodes.
+ * Outputs per node: parent, action, obs, depth, weight, U, L, H, E; per
+ * Q-node (v * 5 + a): R, U_Q, L_Q, H_Q, E_Q, first child, children;
+ * expanded[it] the node expanded at iteration it (-1 after a stop);
+ * *n_nodes; *boundary draws within 1e-6 of a CDF step.  Returns the
+ * iterations run.  belief: [max_nodes][n] scratch.                        */
+int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG, const double *b0, int K,
+                 uint64_t seed, uint32_t episode, int iters, int max_depth, int max_nodes, double *belief,
+                 int *n_nodes, int *expanded, int *vparent, int *vaction, int *vobs, int *vdepth, double *vweight,
+                 double *U, double *L, double *Hh, int *E, double *Rq, double *UQ, double *LQ, double *HQ, int *EQ,
+                 int *cbeg, int *ccnt, long *boundary) {
+    const int n = p->H * p->W, nz = p->B + 1, A = OR_NUM_ACTIONS;
+    int *label = (int *)malloc(sizeof(int) * n);
+    double *Rt = (double *)malloc(sizeof(double) * A * n);
+    double *bbar = (double *)malloc(sizeof(double) * n);
+    double *P = (double *)malloc(sizeof(double) * nz);
+    int *cnt = (int *)malloc(sizeof(int) * nz);
+    uint64_t *code = (uint64_t *)malloc(sizeof(uint64_t) * max_nodes);
+    or_labels(p, label);
+    or_reward_table(p, Rt);
+    *boundary = 0;
+    for (int i = 0; i < max_nodes * A; ++i) { cbeg[i] = 0; ccnt[i] = 0; Rq[i] = UQ[i] = LQ[i] = HQ[i] = 0.0; EQ[i] = -1; }
+    /* the root */
+    for (int x = 0; x < n; ++x) belief[x] = p->occ[x] ? 0.0 : b0[x];
+    vparent[0] = -1; vaction[0] = -1; vobs[0] = -1; vdepth[0] = 0; vweight[0] = 1.0; code[0] = 0;
+    U[0] = or_leaf_value(p, Qu, belief, NULL);
+    {
+        double best = -HUGE_VAL;
+        for (int i = 0; i < nG; ++i) {
+            double s = 0.0;
+            for (int x = 0; x < n; ++x) s += G[(size_t)i * n + x] * belief[x];
+            if (s > best) best = s;
+        }
+        L[0] = best;
+    }
+    Hh[0] = U[0] - L[0];
+    E[0] = 0;
+    int nn = 1, it = 0;
+    for (; it < iters; ++it) {
+        const int v = E[0];
+        const int room = A * (K < nz ? K : nz);
+        if (vdepth[v] >= max_depth || nn + room > max_nodes) break;
+        const double *b = belief + (size_t)v * n;
+        for (int a = 0; a < A; ++a) {
+            const int q = v * A + a;
+            Rq[q] = or_belief_reward(p, Rt, b, a);
+            or_predict(p, b, a, bbar);
+            or_obs_marginal(p, label, bbar, P);
+            const uint64_t path = code[v] * A + (uint64_t)a;
+            for (int z = 0; z < nz; ++z) cnt[z] = 0;
+            for (int k = 0; k < K; ++k) {
+                const float u = or_uniform(seed, episode, vdepth[v], path, k);
+                cnt[or_sample_obs(P, nz, u)] += 1;
+                *boundary += or_is_boundary(P, nz, u);
+            }
+            cbeg[q] = nn;
+            for (int z = 0; z < nz; ++z) {
+                if (!cnt[z]) continue;
+                const int c = nn++;
+                double *bc = belief + (size_t)c * n;
+                or_correct(p, label, bbar, z, bc);
+                vparent[c] = v; vaction[c] = a; vobs[c] = z; vdepth[c] = vdepth[v] + 1;
+                vweight[c] = (double)cnt[z] / (double)K;
+                code[c] = path * (uint64_t)nz + (uint64_t)z;
+                U[c] = or_leaf_value(p, Qu, bc, NULL);
+                double best = -HUGE_VAL;
+                for (int i = 0; i < nG; ++i) {
+                    double s = 0.0;
+                    for (int x = 0; x < n; ++x) s += G[(size_t)i * n + x] * bc[x];
+                    if (s > best) best = s;
+                }
+                L[c] = best;
+                /* a node at the depth limit is closed: no gap left to draw the search */
+                Hh[c] = vdepth[c] < max_depth ? U[c] - L[c] : 0.0;
+                E[c] = c;
+            }
+            ccnt[q] = nn - cbeg[q];
+        }
+        /* the expanded node, then its ancestors up to the root */
+        for (int u = v; u >= 0; u = vparent[u])
+            bf_update_node(u, p->gamma, cbeg, ccnt, Rq, vweight, U, L, Hh, E, UQ, LQ, HQ, EQ);
+        expanded[it] = v;
+    }
+    for (int t = it; t < iters; ++t) expanded[t] = -1;
+    *n_nodes = nn;
+    free(label); free(Rt); free(bbar); free(P); free(cnt); free(code);
+    return it;
+}

@@ -124,6 +124,13 @@ int or_tree_bounds(int depth, const long *off, const int *n_level, const int *pa
                    const double *Lleaf, double gamma, double *LV, double *HV, int *EV, double *LQ,
                    double *HQ, int *EQ);
 
+/* ---- Best-first QV-Tree Search (Alg. 1 inner loop) ---- */
+int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG, const double *b0, int K,
+                 uint64_t seed, uint32_t episode, int iters, int max_depth, int max_nodes, double *belief,
+                 int *n_nodes, int *expanded, int *vparent, int *vaction, int *vobs, int *vdepth, double *vweight,
+                 double *U, double *L, double *Hh, int *E, double *Rq, double *UQ, double *LQ, double *HQ, int *EQ,
+                 int *cbeg, int *ccnt, long *boundary);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
