@@ -415,6 +415,58 @@ qv_status qv_plan_bounds(const qv_plan_t *plan, int32_t e, const float *d_leaf_L
 qv_status qv_plan_bounds_view(const qv_plan_t *plan, int32_t e, int32_t level, void *d_ws,
                               qv_bounds_view_t *view);
 
+/* ---------------------------------------------------------------- best-first search (Alg. 1)
+ * The planning loop of Alg. 1: each iteration expands the V-node the root's
+ * E points at (Alg. 2-5: every action, K forward samples, the unique
+ * observations with frequencies f, children tau(b, a, z) of weight f / K,
+ * U = max_a sum b Qu (d_Qu: upper-bound alpha-vectors, FP32 [5][H][pitch],
+ * e.g. fib_value_iterate's), L = V_PBVI (qv_pbvi_value with the nG vectors
+ * d_G, whose handle must have a workspace), H = U - L, E = the child) and
+ * updates it and its ancestors (Alg. 6-7 with H(b, a) of Eq. 9).  A node
+ * created at max_depth is closed (H = 0).  The samples of (V-node, a) are
+ * the level-synchronous tree's: level = the node's depth, path = its
+ * mixed-radix code * 5 + a, so every node is the node of the same path in
+ * that tree.  Node ids follow creation order (action, then z ascending).
+ * Planning stops (later iterations do nothing) when the node to expand lies
+ * at max_depth or the next expansion could overflow max_nodes.
+ *   qv_bf_create   checks sizes (max_depth 0..8, (5 |Z|)^max_depth < 2^56)
+ *   qv_bf_reset    the root from d_b0 in the caller's workspace (256-byte
+ *                  aligned, qv_bf_workspace_bytes; one belief per node)
+ *   qv_bf_run      `iters` iterations, launches only (no host waits)
+ *   qv_bf_read     synchronises; root fields, iterations, nodes, stop flag
+ *   qv_bf_view     device arrays of the tree (per node; per Q-node [n][5];
+ *                  expanded [max_nodes]: the node of each iteration, -1 after) */
+typedef struct qv_bf qv_bf_t;
+typedef struct {
+    int32_t iterations;        /* expansions done                                     */
+    int32_t nodes;             /* V-nodes in the tree                                 */
+    int32_t stopped;           /* 1 once planning stopped                             */
+    int32_t root_action;       /* argmax_a U_Q(root, a), ties to the lowest; -1 unexpanded */
+    float U, L, H;             /* the root's fields                                   */
+    int32_t E;                 /* the V-node the next iteration expands               */
+    float q[QV_NUM_ACTIONS];   /* U_Q(root, a)                                        */
+    int64_t boundary_samples;  /* draws whose uniform fell within 1e-6 of a CDF step  */
+} qv_bf_result_t;
+typedef struct {
+    int32_t max_nodes;
+    const int32_t *d_parent, *d_action, *d_obs, *d_depth;
+    const float *d_weight, *d_U, *d_L, *d_H;
+    const int32_t *d_E;
+    const float *d_R, *d_UQ, *d_LQ, *d_HQ;
+    const int32_t *d_EQ, *d_first, *d_count;
+    const float *d_belief;
+    const int32_t *d_expanded;
+} qv_bf_view_t;
+qv_status qv_bf_create(const qv_model_t *model, const float *d_Qu, qv_pbvi_t *pbvi, const float *d_G,
+                       int32_t nG, int32_t K, uint64_t seed, uint32_t episode, int32_t max_depth,
+                       int32_t max_nodes, qv_bf_t **out);
+size_t qv_bf_workspace_bytes(const qv_bf_t *bf);
+qv_status qv_bf_reset(qv_bf_t *bf, const float *d_b0, void *d_ws, size_t ws_bytes, qv_stream_t stream);
+qv_status qv_bf_run(qv_bf_t *bf, int32_t iters, qv_stream_t stream);
+qv_status qv_bf_read(qv_bf_t *bf, qv_bf_result_t *h_result, qv_stream_t stream);
+qv_status qv_bf_view(const qv_bf_t *bf, qv_bf_view_t *view);
+void qv_bf_destroy(qv_bf_t *bf);
+
 /* ---------------------------------------------------------------- adjoint of the plan
  * qv_tree_backward: reverse mode of the root value U_V(b0) of episode e of a
  * plan that has run (stream order), by the derivatives of Alg. 6 and 7

@@ -997,12 +997,16 @@ static void bf_update_node(int v, double gamma, const int *cbeg, const int *ccnt
  * Q-node (v * 5 + a): R, U_Q, L_Q, H_Q, E_Q, first child, children;
  * expanded[it] the node expanded at iteration it (-1 after a stop);
  * *n_nodes; *boundary draws within 1e-6 of a CDF step.  Returns the
- * iterations run.  belief: [max_nodes][n] scratch.                        */
+ * iterations run.  belief: [max_nodes][n] scratch.  force (nullable):
+ * force[it] >= 0 expands that node instead of the root's E (to follow
+ * another implementation's choices), with best_h, forced_h and slack
+ * (nullable, [iters]) recording how each forced choice compares.        */
 int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG, const double *b0, int K,
                  uint64_t seed, uint32_t episode, int iters, int max_depth, int max_nodes, double *belief,
                  int *n_nodes, int *expanded, int *vparent, int *vaction, int *vobs, int *vdepth, double *vweight,
                  double *U, double *L, double *Hh, int *E, double *Rq, double *UQ, double *LQ, double *HQ, int *EQ,
-                 int *cbeg, int *ccnt, long *boundary) {
+                 int *cbeg, int *ccnt, long *boundary, const int *force, double *best_h, double *forced_h,
+                 double *slack) {
     const int n = p->H * p->W, nz = p->B + 1, A = OR_NUM_ACTIONS;
     int *label = (int *)malloc(sizeof(int) * n);
     double *Rt = (double *)malloc(sizeof(double) * A * n);
@@ -1031,9 +1035,28 @@ int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG,
     E[0] = 0;
     int nn = 1, it = 0;
     for (; it < iters; ++it) {
-        const int v = E[0];
+        int v = E[0];
         const int room = A * (K < nz ? K : nz);
         if (vdepth[v] >= max_depth || nn + room > max_nodes) break;
+        if (force && force[it] >= 0) {
+            /* follow a given choice (a leaf of the current tree), and report
+             * how it compares with this tree's own: the heuristic product
+             * along its path against the root's H, and the largest shortfall
+             * of a taken action's U_Q below its node's best                  */
+            const int f = force[it];
+            double h = vdepth[f] < max_depth ? U[f] - L[f] : 0.0, gap = 0.0;
+            for (int u = f; vparent[u] >= 0; u = vparent[u]) {
+                const int pv = vparent[u], a = vaction[u];
+                h *= p->gamma * vweight[u];
+                double best = UQ[pv * A];
+                for (int b = 1; b < A; ++b) if (UQ[pv * A + b] > best) best = UQ[pv * A + b];
+                if (best - UQ[pv * A + a] > gap) gap = best - UQ[pv * A + a];
+            }
+            if (best_h) best_h[it] = Hh[0];
+            if (forced_h) forced_h[it] = h;
+            if (slack) slack[it] = gap;
+            v = f;
+        }
         const double *b = belief + (size_t)v * n;
         for (int a = 0; a < A; ++a) {
             const int q = v * A + a;

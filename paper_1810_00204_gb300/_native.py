@@ -61,6 +61,18 @@ class qv_bounds_view_t(C.Structure):
                 ("d_HQ", C.c_void_p), ("d_EQ", C.c_void_p)]
 
 
+class qv_bf_result_t(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("nodes", C.c_int32), ("stopped", C.c_int32),
+                ("root_action", C.c_int32), ("U", C.c_float), ("L", C.c_float), ("H", C.c_float),
+                ("E", C.c_int32), ("q", C.c_float * QV_NUM_ACTIONS), ("boundary_samples", C.c_int64)]
+
+
+class qv_bf_view_t(C.Structure):
+    _fields_ = [("max_nodes", C.c_int32)] + [(k, C.c_void_p) for k in (
+        "d_parent", "d_action", "d_obs", "d_depth", "d_weight", "d_U", "d_L", "d_H", "d_E", "d_R", "d_UQ", "d_LQ",
+        "d_HQ", "d_EQ", "d_first", "d_count", "d_belief", "d_expanded")]
+
+
 class qv_launch_time_t(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("level", C.c_int32), ("ms", C.c_float)]
 
@@ -109,6 +121,13 @@ SIGNATURES = {
     "qv_plan_bounds_workspace_bytes": (_sz, [_vp, _i32]),
     "qv_plan_bounds": (C.c_int, [_vp, _i32, _vp, _vp, _sz, _vp]),
     "qv_plan_bounds_view": (C.c_int, [_vp, _i32, _i32, _vp, C.POINTER(qv_bounds_view_t)]),
+    "qv_bf_create": (C.c_int, [_M, _vp, _vp, _vp, _i32, _i32, C.c_uint64, C.c_uint32, _i32, _i32, C.POINTER(_vp)]),
+    "qv_bf_workspace_bytes": (_sz, [_vp]),
+    "qv_bf_reset": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
+    "qv_bf_run": (C.c_int, [_vp, _i32, _vp]),
+    "qv_bf_read": (C.c_int, [_vp, C.POINTER(qv_bf_result_t), _vp]),
+    "qv_bf_view": (C.c_int, [_vp, C.POINTER(qv_bf_view_t)]),
+    "qv_bf_destroy": (None, [_vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
     "qv_plan_autotune_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_autotune": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, _i32, C.POINTER(qv_tune_t),

@@ -244,6 +244,69 @@ def pbvi_solve(model: Model, rounds: int, iters: int, seed: int = 0, b0: Optiona
     return dict(B=B[:nB], G=G[:nG], value=v, pbvi=pb)
 
 
+class BestFirst:
+    """Alg. 1's best-first planning loop on one model: U from the upper-bound
+    alpha-vectors Qu (FP32 [5][H][pitch], e.g. FIB), L from PBVI (a Pbvi
+    handle with its vectors G), K forward samples per (V-node, action)."""
+
+    def __init__(self, model: Model, Qu: torch.Tensor, pbvi: "Pbvi", G: torch.Tensor, K=8, seed=0, episode=0,
+                 max_depth=6, max_nodes=4096):
+        self.model, self.Qu, self.pbvi, self.G = model, Qu, pbvi, G.contiguous()
+        h = C.c_void_p()
+        check(lib().qv_bf_create(C.byref(model.struct), _ptr(Qu), pbvi.handle, _ptr(self.G), self.G.shape[0],
+                                 int(K), int(seed), int(episode), int(max_depth), int(max_nodes), C.byref(h)),
+              "qv_bf_create")
+        self.handle = h
+        self.ws_bytes = lib().qv_bf_workspace_bytes(h)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=model.device)
+        self.ws_ptr = C.c_void_p(self.ws.data_ptr() + (-self.ws.data_ptr()) % 256)
+
+    def reset(self, b0: Optional[torch.Tensor] = None, stream=None):
+        b = self.model.b0() if b0 is None else b0.contiguous()
+        self._b0 = b
+        check(lib().qv_bf_reset(self.handle, _ptr(b), self.ws_ptr, self.ws_bytes, _stream(stream)), "qv_bf_reset")
+
+    def run(self, iters: int, stream=None):
+        check(lib().qv_bf_run(self.handle, int(iters), _stream(stream)), "qv_bf_run")
+
+    def read(self, stream=None) -> dict:
+        r = N.qv_bf_result_t()
+        check(lib().qv_bf_read(self.handle, C.byref(r), _stream(stream)), "qv_bf_read")
+        return dict(iterations=r.iterations, nodes=r.nodes, stopped=r.stopped, root_action=r.root_action,
+                    U=r.U, L=r.L, H=r.H, E=r.E, q=list(r.q), boundary_samples=r.boundary_samples)
+
+    def tree(self) -> dict:
+        """Host copies of the tree's arrays (the first `nodes` entries)."""
+        n = self.read()["nodes"]
+        v = N.qv_bf_view_t()
+        check(lib().qv_bf_view(self.handle, C.byref(v)), "qv_bf_view")
+        base = self.ws.data_ptr()
+
+        def arr(ptr, count, dt):
+            off = ptr - base
+            esz = torch.tensor([], dtype=dt).element_size()
+            return self.ws[off:off + count * esz].view(dt)
+
+        m = self.model
+        out = {}
+        for k, dt in (("parent", torch.int32), ("action", torch.int32), ("obs", torch.int32), ("depth", torch.int32),
+                      ("weight", torch.float32), ("U", torch.float32), ("L", torch.float32), ("H", torch.float32),
+                      ("E", torch.int32)):
+            out[k] = arr(getattr(v, "d_" + k), n, dt).cpu().numpy()
+        for k, dt in (("R", torch.float32), ("UQ", torch.float32), ("LQ", torch.float32), ("HQ", torch.float32),
+                      ("EQ", torch.int32), ("first", torch.int32), ("count", torch.int32)):
+            out[k] = arr(getattr(v, "d_" + k), n * 5, dt).view(n, 5).cpu().numpy()
+        out["expanded"] = arr(v.d_expanded, v.max_nodes, torch.int32).cpu().numpy()
+        out["belief"] = arr(v.d_belief, n * m.H * m.P, torch.float32).view(n, m.H, m.P)
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().qv_bf_destroy(h)
+            self.handle = None
+
+
 def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
     """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
     is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),

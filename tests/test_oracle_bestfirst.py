@@ -90,3 +90,21 @@ def test_root_pointer_path_and_bounds(seed):
     assert v == r["E"][0]
     gap = r["U"][v] - r["L"][v] if r["depth"][v] < 6 else 0.0
     assert r["H"][0] == pytest.approx(prod * gap, rel=1e-12, abs=1e-15)
+
+
+def test_forcing_its_own_choices_changes_nothing():
+    w, Qu, G = _setup(7)
+    r = O.bestfirst(w, Qu, G, 14, max_depth=5)
+    f = O.bestfirst(w, Qu, G, 14, max_depth=5, force=r["expanded"])
+    assert f["nodes"] == r["nodes"] and np.array_equal(f["expanded"], r["expanded"])
+    assert np.array_equal(f["U"], r["U"]) and np.array_equal(f["E"], r["E"])
+    it = r["iterations"]
+    assert np.array_equal(f["forced_h"][:it], f["best_h"][:it])
+    assert np.all(f["slack"][:it] == 0.0)
+    # any other leaf either scores below the root's H along greedy actions or
+    # hangs under a non-greedy action (a positive U_Q shortfall)
+    for leaf in range(1, r["count"][0].sum() + 1):
+        g = O.bestfirst(w, Qu, G, 2, max_depth=5, force=[0, leaf])
+        assert g["forced_h"][1] <= g["best_h"][1] or g["slack"][1] > 0.0
+        if leaf != r["expanded"][1]:
+            assert g["forced_h"][1] < g["best_h"][1] or g["slack"][1] > 0.0
