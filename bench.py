@@ -214,6 +214,50 @@ def aems_measurement(args, dev, K, stream):
                     "views and the per-level launches"}
 
 
+def bestfirst_measurement(args, dev, stream, iters=400):
+    """Alg. 1's best-first planning loop on the mid map: U from FIB, L from a
+    256-point PBVI, K = 8; `iters` expansions timed with CUDA events (the
+    tree resident on the device, one reset before the timed run), with the
+    oracle's loop on a bounded sample as the CPU baseline."""
+    import torch
+    import oracle as O
+    from paper_1810_00204_gb300 import api, workloads as WL
+    w = WL.mid(args.seed)
+    m = api.Model(w, device=dev)
+    Q = api.fib_value_iterate(m, dtype="f32", want_alpha=False)["Q"]
+    g = api.pbvi_solve(m, rounds=8, iters=4, seed=args.seed)
+    nz = w.B + 1
+    bf = api.BestFirst(m, Q, g["pbvi"], g["G"], K=w.K, seed=w.seed, episode=w.episode, max_depth=6,
+                       max_nodes=1 + iters * 5 * min(w.K, nz))
+    bf.reset()
+    bf.run(20)  # warm-up
+    bf.read()
+    bf.reset()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    bf.run(iters)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    r = bf.read()
+    out = {"iterations": r["iterations"], "requested": iters, "stopped": r["stopped"], "nodes": r["nodes"],
+           "ms": ms, "expansions_per_s": r["iterations"] / (ms * 1e-3), "us_per_expansion": 1e3 * ms / max(1, r["iterations"]),
+           "root": {"U": r["U"], "L": r["L"], "H": r["H"], "action": r["root_action"]},
+           "launches_per_expansion": 8,
+           "pbvi_vectors": int(g["G"].shape[0])}
+    if not args.no_cpu:
+        Qh = m.from_grid(Q).reshape(5, -1).astype("float64")
+        Gh = m.from_grid(g["G"]).reshape(g["G"].shape[0], -1).astype("float64")
+        n = 20
+        t0 = time.perf_counter()
+        ro = O.bestfirst(w, Qh, Gh, n, K=w.K, max_depth=6)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": ro["iterations"] / el, "unit": "expansions/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the oracle's first {n} expansions of the same loop, {el:.1f} s, one thread"}
+    return out
+
+
 def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
     """Sub-measurements beside the headline: the step's requests as one
     batched launch, the 256-episode batch of uneven maps, and the 512x512
@@ -309,6 +353,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     out["pbvi_mid"] = pbvi_measurement(args, dev, K, flush, stream, with_cpu=not args.no_cpu)
     # (7) the paper's node fields U, L, H, E on the mid map
     out["aems_fields_mid"] = aems_measurement(args, dev, K, stream)
+    # (8) the best-first planning loop of Alg. 1 on the mid map
+    out["bestfirst_mid"] = bestfirst_measurement(args, dev, stream)
     return out
 
 
@@ -645,6 +691,7 @@ def main():
                 out["pbvi"] = pbvi_measurement(args, dev, max(3, args.extra_steps), flush, stream,
                                                with_cpu=not args.no_cpu)
                 out["aems_fields"] = aems_measurement(args, dev, max(3, args.extra_steps), stream)
+                out["bestfirst"] = bestfirst_measurement(args, dev, stream)
             print(json.dumps(out), flush=True)
         return
     R = args.plans_per_step
