@@ -223,7 +223,10 @@ qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
  * d_best [nB][B + 1] (ties to the lowest index), d_q [nB][5] every Q_b(a).
  * qv_pbvi_value: V_PBVI(b) and its maximising vector (ties to the lowest
  * index) for nb beliefs d_b given nG <= max_points vectors d_G (the beliefs
- * go through in chunks of max_points).
+ * go through in chunks of max_points).  d_G = NULL reuses the vectors of the
+ * previous qv_pbvi_value call (same nG) unless a backup has run since
+ * (QV_ERR_INVALID then): a caller asking about many beliefs against fixed
+ * vectors skips their reordering.
  * The host may upload small tables (pageable copies) on the stream; none of
  * these calls synchronises except qv_pbvi_create. */
 typedef struct qv_pbvi qv_pbvi_t;

@@ -4,18 +4,22 @@
 // 5-7) and updates it and its ancestors.  The tree lives on the device
 // (node arrays, per-Q-node arrays, one belief per V-node); the host only
 // issues launches, so an iteration never waits for the host:
-//   k_bf_expand    one CTA per action of the chosen node v (read from the
-//                  root's E on the device): the predicted belief, R(b, a),
-//                  P(z | b, a), K forward samples (the level-synchronous
+//   k_bf_predict   grid (action, band of cells) on the chosen node v (read
+//                  from the root's E on the device): the predicted belief
+//                  and each band's mass per label and share of R(b, a)
+//   k_bf_sample    one CTA per action: P(z | b, a) from the bands' sums (in
+//                  band order), K forward samples (the level-synchronous
 //                  tree's Philox stream: level = depth of v, path = code of
-//                  v * 5 + a), the unique z with their frequencies, and the
-//                  children's beliefs tau(b, a, z) in a scratch area
+//                  v * 5 + a), the unique z with their frequencies, R(b, a)
+//   k_bf_children  grid (child slot, band): tau(b, a, z) into a scratch area
 //   leaf_value     U of every scratch child (the upper-bound alpha-vectors)
-//   qv_pbvi_value  L of every scratch child (the PBVI vectors)
+//   qv_pbvi_value  L of every scratch child (the PBVI vectors, reordered
+//                  once per search)
 //   k_bf_update    one warp: the children's ids (creation order: a, then z
-//                  ascending), their fields (Alg. 5; a child at the depth
-//                  limit is closed, H = 0), the Q-nodes of v (Alg. 6) and v
-//                  and every ancestor (Alg. 7 with H(b, a) of Eq. 9)
+//                  ascending) and fields (Alg. 5; a child at the depth limit
+//                  is closed, H = 0), then the Q-nodes (Alg. 6, one lane per
+//                  action) and fields (Alg. 7 with H(b, a) of Eq. 9) of v and
+//                  every ancestor
 //   k_bf_commit    the children's beliefs from the scratch area to their ids
 // Planning stops (a device flag; later iterations do nothing) when the node
 // to expand lies at the depth limit or the tree could outgrow max_nodes.
@@ -46,41 +50,43 @@ struct BfDev {
     int *EQ, *first, *count;  // [max_nodes][5]
     float *belief;            // [max_nodes][N]
     // scratch of one expansion
-    float *sbelief;           // [5 * cmax][N]
-    float *sU, *sL;           // [5 * cmax]
+    float *sbelief;           // [5 * cmax][N] children
+    float *sbbar;             // [5][N] predicted beliefs
+    float *spart;             // [5][nbands][nz + 1] band sums: mass per label, then R's share
+    float *sU, *sL, *sP;      // [5 * cmax]: U, L, P(z) of each child
     int *sz, *sf, *sm;        // [5][cmax] z, frequency; [5] unique count
     float *sR;                // [5]
+    int band_cells, nbands;
 };
 
-// One CTA per action of the node the root's E points at.
-__global__ void __launch_bounds__(kBfThreads) k_bf_expand(BfDev d) {
-    extern __shared__ float hist[];  // [nz][kBfThreads]
+// The node to expand, or -1 when planning has stopped (every CTA of a
+// launch reaches the same answer; CTA 0 records a new stop).
+__device__ __forceinline__ int bf_node(const BfDev &d, bool record) {
+    const int v = d.E[0];
+    const bool stop = d.state[2] != 0 || d.depth[v] >= d.max_depth || d.state[0] + 5 * d.cmax > d.max_nodes;
+    if (stop && record) d.state[2] = 1;
+    return stop ? -1 : v;
+}
+
+// Grid (action, band): the predicted belief of the band's cells, and the
+// band's mass per label and share of sum_y bbar(y) r(y) (one shared-memory
+// column per thread, added in a fixed order).
+__global__ void __launch_bounds__(kBfThreads) k_bf_predict(BfDev d) {
+    extern __shared__ float hist[];  // [nz + 1][kBfThreads]; row nz: reward
     __shared__ float lut[64];
-    __shared__ float s_red[kBfThreads / 32];
-    __shared__ float s_P[QV_MAX_BEACONS + 1], s_C[QV_MAX_BEACONS + 1];
-    __shared__ int s_cnt[QV_MAX_BEACONS + 1];
-    __shared__ int s_go, s_v, s_m;
-    const int a = blockIdx.x, tid = threadIdx.x;
-    if (tid == 0) {
-        const int v = d.E[0];
-        const int n = d.state[0];
-        const bool stop = d.state[2] != 0 || d.depth[v] >= d.max_depth || n + 5 * d.cmax > d.max_nodes;
-        s_go = stop ? 0 : 1;
-        s_v = v;
-    }
+    __shared__ int s_v;
+    const int a = blockIdx.x, band = blockIdx.y, tid = threadIdx.x;
+    if (tid == 0) s_v = bf_node(d, a == 0 && band == 0);
     for (int i = tid; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, d.slip);
-    for (int z = 0; z < d.nz; ++z) hist[z * kBfThreads + tid] = 0.0f;
-    for (int z = tid; z < d.nz; z += blockDim.x) s_cnt[z] = 0;
+    for (int z = 0; z <= d.nz; ++z) hist[z * kBfThreads + tid] = 0.0f;
     __syncthreads();
-    if (!s_go) {
-        if (a == 0 && tid == 0) d.state[2] = 1;
-        return;
-    }
     const int v = s_v;
+    if (v < 0) return;
     const float *b = d.belief + static_cast<size_t>(v) * d.N;
-    float *bbar = d.sbelief + static_cast<size_t>(a) * d.cmax * d.N;  // first child slot holds bbar
+    float *bbar = d.sbbar + static_cast<size_t>(a) * d.N;
+    const int y0 = band * d.band_cells, y1 = min(d.N, y0 + d.band_cells);
     float rs = 0.0f;
-    for (int y = tid; y < d.N; y += blockDim.x) {
+    for (int y = y0 + tid; y < y1; y += blockDim.x) {
         const unsigned cw = __ldg(d.cell + y);
         const unsigned in = QV_CELL_INFLOW(cw);
         float nb[4];
@@ -95,19 +101,36 @@ __global__ void __launch_bounds__(kBfThreads) k_bf_expand(BfDev d) {
             rs = fmaf(p, stage_reward(true, y == d.goal, d.cost ? __ldg(d.cost + y) : 0.0f), rs);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-    if ((tid & 31) == 0) s_red[tid >> 5] = rs;
+    hist[d.nz * kBfThreads + tid] = rs;
     __syncthreads();
-    for (int z = tid; z < d.nz; z += blockDim.x) {
+    float *out = d.spart + (static_cast<size_t>(a) * d.nbands + band) * (d.nz + 1);
+    for (int z = tid; z <= d.nz; z += blockDim.x) {
         float s = 0.0f;
         for (int t = 0; t < kBfThreads; ++t) s += hist[z * kBfThreads + t];
-        s_P[z] = s;
+        out[z] = s;
+    }
+}
+
+// One CTA per action: P(z) from the band sums, the K samples, the unique z
+// with their frequencies, R(b, a).
+__global__ void __launch_bounds__(128) k_bf_sample(BfDev d) {
+    __shared__ float s_P[QV_MAX_BEACONS + 2], s_C[QV_MAX_BEACONS + 1];
+    __shared__ int s_cnt[QV_MAX_BEACONS + 1];
+    __shared__ int s_v;
+    const int a = blockIdx.x, tid = threadIdx.x;
+    if (tid == 0) s_v = bf_node(d, false);
+    for (int z = tid; z < d.nz; z += blockDim.x) s_cnt[z] = 0;
+    __syncthreads();
+    const int v = s_v;
+    if (v < 0) return;
+    for (int z = tid; z <= d.nz; z += blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < d.nbands; ++k) s += d.spart[(static_cast<size_t>(a) * d.nbands + k) * (d.nz + 1) + z];
+        s_P[z] = s;  // mass of label z; s_P[nz]: sum_y bbar(y) r(y)
     }
     __syncthreads();
     if (tid == 0) {
-        float r = 0.0f;
-        for (int w = 0; w < kBfThreads / 32; ++w) r += s_red[w];
-        d.sR[a] = r - 100.0f * b[d.goal];  // the goal's own mass stays and earns nothing
+        d.sR[a] = s_P[d.nz] - 100.0f * d.belief[static_cast<size_t>(v) * d.N + d.goal];  // the goal's own mass earns nothing
         float tot = s_P[d.B];
         for (int z = 0; z < d.B; ++z) tot += s_P[z];
         float run = 0.0f;
@@ -142,31 +165,35 @@ __global__ void __launch_bounds__(kBfThreads) k_bf_expand(BfDev d) {
             if (s_cnt[z]) {
                 d.sz[a * d.cmax + m] = z;
                 d.sf[a * d.cmax + m] = s_cnt[z];
+                d.sP[a * d.cmax + m] = s_P[z];
                 ++m;
             }
         d.sm[a] = m;
-        s_m = m;
-    }
-    __syncthreads();
-    // children tau(b, a, z) = O(., z) bbar / P(z); the last child first, so
-    // the first slot (which holds bbar) is rewritten last
-    for (int j = s_m - 1; j >= 0; --j) {
-        const int z = d.sz[a * d.cmax + j];
-        const float inv = 1.0f / s_P[z];
-        float *out = d.sbelief + (static_cast<size_t>(a) * d.cmax + j) * d.N;
-        for (int y = tid; y < d.N; y += blockDim.x) {
-            const unsigned cw = __ldg(d.cell + y);
-            const float w = QV_CELL_FREE(cw) ? (static_cast<int>(QV_CELL_LABEL(cw)) == z ? d.acc : d.eta) : 0.0f;
-            out[y] = bbar[y] * w * inv;
-        }
-        __syncthreads();
     }
 }
 
-// Alg. 6 for the five Q-nodes of u and Alg. 7 for u (lane 0 of one warp).
-__device__ void bf_update_node(const BfDev &d, int u) {
-    for (int a = 0; a < 5; ++a) {
-        const int q = u * 5 + a;
+// Grid (child slot, band): tau(b, a, z) = O(., z) bbar / P(z) on the band.
+__global__ void __launch_bounds__(kBfThreads) k_bf_children(BfDev d) {
+    const int s = blockIdx.x, band = blockIdx.y;
+    const int a = s / d.cmax, j = s - a * d.cmax;
+    if (d.state[2] || j >= d.sm[a]) return;
+    const int z = d.sz[s];
+    const float inv = 1.0f / d.sP[s];
+    const float *bbar = d.sbbar + static_cast<size_t>(a) * d.N;
+    float *out = d.sbelief + static_cast<size_t>(s) * d.N;
+    const int y0 = band * d.band_cells, y1 = min(d.N, y0 + d.band_cells);
+    for (int y = y0 + threadIdx.x; y < y1; y += blockDim.x) {
+        const unsigned cw = __ldg(d.cell + y);
+        const float w = QV_CELL_FREE(cw) ? (static_cast<int>(QV_CELL_LABEL(cw)) == z ? d.acc : d.eta) : 0.0f;
+        out[y] = bbar[y] * w * inv;
+    }
+}
+
+// Alg. 6 for the five Q-nodes of u (lane a of the warp takes action a) and
+// Alg. 7 for u (lane 0).
+__device__ void bf_update_node(const BfDev &d, int u, int lane) {
+    if (lane < 5) {
+        const int q = u * 5 + lane;
         const int c0 = d.first[q], nc = d.count[q];
         float su = 0.0f, sl = 0.0f, bh = 0.0f;
         int be = -1;
@@ -184,59 +211,72 @@ __device__ void bf_update_node(const BfDev &d, int u) {
         d.HQ[q] = bh;
         d.EQ[q] = be;
     }
-    int au = 0;
-    float lmax = d.LQ[u * 5];
-    for (int a = 1; a < 5; ++a) {
-        if (d.UQ[u * 5 + a] > d.UQ[u * 5 + au]) au = a;
-        lmax = fmaxf(lmax, d.LQ[u * 5 + a]);
+    __syncwarp();
+    if (lane == 0) {
+        int au = 0;
+        float lmax = d.LQ[u * 5];
+        for (int a = 1; a < 5; ++a) {
+            if (d.UQ[u * 5 + a] > d.UQ[u * 5 + au]) au = a;
+            lmax = fmaxf(lmax, d.LQ[u * 5 + a]);
+        }
+        d.U[u] = d.UQ[u * 5 + au];
+        d.L[u] = lmax;
+        d.Hh[u] = d.HQ[u * 5 + au];
+        d.E[u] = d.EQ[u * 5 + au];
     }
-    d.U[u] = d.UQ[u * 5 + au];
-    d.L[u] = lmax;
-    d.Hh[u] = d.HQ[u * 5 + au];
-    d.E[u] = d.EQ[u * 5 + au];
+    __syncwarp();
 }
 
-__global__ void k_bf_update(BfDev d) {
-    if (threadIdx.x != 0 || d.state[2]) return;
+// One warp: the children's ids and fields, then v and its ancestors.
+__global__ void __launch_bounds__(32) k_bf_update(BfDev d) {
+    const int lane = threadIdx.x;
+    if (d.state[2]) return;
     const int v = d.E[0];
-    int n = d.state[0];
-    d.state[3] = n;  // the first child's id, for k_bf_commit
-    for (int a = 0; a < 5; ++a) {
-        const int q = v * 5 + a;
-        d.R[q] = d.sR[a];
-        d.first[q] = n;
-        d.count[q] = d.sm[a];
-        for (int j = 0; j < d.sm[a]; ++j) {
-            const int c = n++;
-            const int z = d.sz[a * d.cmax + j], s = a * d.cmax + j;
-            d.parent[c] = v;
-            d.action[c] = a;
-            d.obs[c] = z;
-            d.depth[c] = d.depth[v] + 1;
-            d.weight[c] = static_cast<float>(d.sf[s]) / static_cast<float>(d.K);
-            d.code[c] = (d.code[v] * 5ull + static_cast<unsigned long long>(a)) * static_cast<unsigned long long>(d.nz) +
-                        static_cast<unsigned long long>(z);
-            d.U[c] = d.sU[s];
-            d.L[c] = d.sL[s];
-            d.Hh[c] = d.depth[c] < d.max_depth ? d.sU[s] - d.sL[s] : 0.0f;
-            d.E[c] = c;
-            for (int t = c * 5; t < c * 5 + 5; ++t) {  // a leaf's Q-nodes: empty until it is expanded
-                d.first[t] = 0;
-                d.count[t] = 0;
-                d.R[t] = d.UQ[t] = d.LQ[t] = d.HQ[t] = 0.0f;
-                d.EQ[t] = -1;
-            }
+    const int n = d.state[0];
+    int base[6];
+    base[0] = 0;
+    for (int a = 0; a < 5; ++a) base[a + 1] = base[a] + d.sm[a];
+    const int total = base[5];
+    for (int t = lane; t < total; t += 32) {
+        int a = 0;
+        while (t >= base[a + 1]) ++a;
+        const int j = t - base[a], s = a * d.cmax + j;
+        const int c = n + t, z = d.sz[s];
+        d.parent[c] = v;
+        d.action[c] = a;
+        d.obs[c] = z;
+        d.depth[c] = d.depth[v] + 1;
+        d.weight[c] = static_cast<float>(d.sf[s]) / static_cast<float>(d.K);
+        d.code[c] = (d.code[v] * 5ull + static_cast<unsigned long long>(a)) * static_cast<unsigned long long>(d.nz) +
+                    static_cast<unsigned long long>(z);
+        d.U[c] = d.sU[s];
+        d.L[c] = d.sL[s];
+        d.Hh[c] = d.depth[v] + 1 < d.max_depth ? d.sU[s] - d.sL[s] : 0.0f;
+        d.E[c] = c;
+        for (int q = c * 5; q < c * 5 + 5; ++q) {  // a leaf's Q-nodes: empty until it is expanded
+            d.first[q] = 0;
+            d.count[q] = 0;
+            d.R[q] = d.UQ[q] = d.LQ[q] = d.HQ[q] = 0.0f;
+            d.EQ[q] = -1;
         }
     }
-    d.state[0] = n;
-    for (int u = v; u >= 0; u = d.parent[u]) bf_update_node(d, u);
-    d.expanded[d.state[1]] = v;
-    d.state[1] += 1;
+    if (lane < 5) {
+        d.R[v * 5 + lane] = d.sR[lane];
+        d.first[v * 5 + lane] = n + base[lane];
+        d.count[v * 5 + lane] = d.sm[lane];
+    }
+    __syncwarp();
+    for (int u = v; u >= 0; u = d.parent[u]) bf_update_node(d, u, lane);
+    if (lane == 0) {
+        d.state[3] = n;  // the first child's id, for k_bf_commit
+        d.state[0] = n + total;
+        d.expanded[d.state[1]] = v;
+        d.state[1] += 1;
+    }
 }
 
 // One CTA per scratch child: copy its belief to its id.
-__global__ void __launch_bounds__(kBfThreads) k_bf_commit(BfDev d, int stopped_before) {
-    (void)stopped_before;
+__global__ void __launch_bounds__(kBfThreads) k_bf_commit(BfDev d) {
     const int s = blockIdx.x, a = s / d.cmax, j = s - a * d.cmax;
     __shared__ int s_id;
     if (threadIdx.x == 0) {
@@ -298,7 +338,38 @@ struct qv_bf {
     size_t bytes;
     size_t off[32];
     bool ready;
+    void *ws;                           // workspace the device pointers point into
+    cudaStream_t gs = nullptr;          // private stream the iteration graph replays on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph = nullptr;    // one iteration, captured for the workspace `ws`
 };
+
+namespace {
+
+void bf_drop_graph(qv_bf *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+// One iteration's launches.  regather: reorder the PBVI vectors again (the
+// first iteration of every qv_bf_run call does, so that calls on the PBVI
+// handle in between cannot leave stale vectors or piece tables behind).
+qv_status bf_issue(qv_bf *h, cudaStream_t st, bool regather) {
+    qv::BfDev &d = h->dev;
+    const int S = 5 * d.cmax;
+    const size_t smem = static_cast<size_t>(d.nz + 1) * qv::kBfThreads * sizeof(float);
+    qv::k_bf_predict<<<dim3(5, d.nbands), qv::kBfThreads, smem, st>>>(d);
+    qv::k_bf_sample<<<5, 128, 0, st>>>(d);
+    qv::k_bf_children<<<dim3(S, d.nbands), qv::kBfThreads, 0, st>>>(d);
+    qv_status s = leaf_value(&h->model, h->Qu, d.sbelief, S, d.sU, st);
+    if (s == QV_OK) s = qv_pbvi_value(h->pbvi, regather ? h->G : nullptr, h->nG, d.sbelief, S, d.sL, nullptr, st);
+    if (s != QV_OK) return s;
+    qv::k_bf_update<<<1, 32, 0, st>>>(d);
+    qv::k_bf_commit<<<S, qv::kBfThreads, 0, st>>>(d);
+    return qv_check_cuda(cudaGetLastError(), "qv_bf_run launch");
+}
+
+}  // namespace
 
 extern "C" qv_status qv_bf_create(const qv_model_t *m, const float *d_Qu, qv_pbvi_t *pbvi, const float *d_G,
                                   int32_t nG, int32_t K, uint64_t seed, uint32_t episode, int32_t max_depth,
@@ -341,6 +412,8 @@ extern "C" qv_status qv_bf_create(const qv_model_t *m, const float *d_Qu, qv_pbv
     d.episode = episode;
     d.cell = m->d_cell;
     d.cost = m->d_cost;
+    d.band_cells = 4096;
+    d.nbands = (d.N + d.band_cells - 1) / d.band_cells;
     const size_t Mn = max_nodes, N = d.N, S = 5 * cmax;
     size_t off = 0;
     int k = 0;
@@ -376,6 +449,9 @@ extern "C" qv_status qv_bf_create(const qv_model_t *m, const float *d_Qu, qv_pbv
     take(S * sizeof(int));                  // 25 sf
     take(8 * sizeof(int));                  // 26 sm
     take(8 * sizeof(float));                // 27 sR
+    take(5 * N * sizeof(float));            // 28 sbbar
+    take(5 * static_cast<size_t>(d.nbands) * (nz + 1) * sizeof(float));  // 29 spart
+    take(S * sizeof(float));                // 30 sP
     h->bytes = off;
     h->ready = false;
     *out = h;
@@ -384,7 +460,14 @@ extern "C" qv_status qv_bf_create(const qv_model_t *m, const float *d_Qu, qv_pbv
 
 extern "C" size_t qv_bf_workspace_bytes(const qv_bf_t *h) { return h ? h->bytes : 0; }
 
-extern "C" void qv_bf_destroy(qv_bf_t *h) { delete h; }
+extern "C" void qv_bf_destroy(qv_bf_t *h) {
+    if (!h) return;
+    bf_drop_graph(h);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->gs) cudaStreamDestroy(h->gs);
+    delete h;
+}
 
 extern "C" qv_status qv_bf_reset(qv_bf_t *h, const float *d_b0, void *d_ws, size_t ws_bytes, qv_stream_t stream) {
     if (!h || !d_b0 || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_bf_reset: null pointer");
@@ -393,6 +476,8 @@ extern "C" qv_status qv_bf_reset(qv_bf_t *h, const float *d_b0, void *d_ws, size
     if (reinterpret_cast<uintptr_t>(d_ws) & 255)
         return qv_set_error(QV_ERR_INVALID, "qv_bf_reset: workspace must be 256-byte aligned");
     char *ws = static_cast<char *>(d_ws);
+    if (h->ws != d_ws) bf_drop_graph(h);  // the graph's pointers were the old workspace's
+    h->ws = d_ws;
     qv::BfDev &d = h->dev;
     auto P = [&](int i) { return ws + h->off[i]; };
     d.state = reinterpret_cast<int *>(P(0));
@@ -423,6 +508,9 @@ extern "C" qv_status qv_bf_reset(qv_bf_t *h, const float *d_b0, void *d_ws, size
     d.sf = reinterpret_cast<int *>(P(25));
     d.sm = reinterpret_cast<int *>(P(26));
     d.sR = reinterpret_cast<float *>(P(27));
+    d.sbbar = reinterpret_cast<float *>(P(28));
+    d.spart = reinterpret_cast<float *>(P(29));
+    d.sP = reinterpret_cast<float *>(P(30));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t bN = static_cast<size_t>(d.N) * sizeof(float);
     if (qv_check_cuda(cudaMemsetAsync(d.expanded, 0xff, static_cast<size_t>(d.max_nodes) * sizeof(int), st),
@@ -442,24 +530,52 @@ extern "C" qv_status qv_bf_run(qv_bf_t *h, int32_t iters, qv_stream_t stream) {
     if (!h) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: null pointer");
     if (!h->ready) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: no tree (qv_bf_reset)");
     if (iters < 0) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: iters %d", iters);
+    if (iters == 0) return QV_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     qv::BfDev &d = h->dev;
-    const int S = 5 * d.cmax;
-    const size_t smem = static_cast<size_t>(d.nz) * qv::kBfThreads * sizeof(float);
+    const size_t smem = static_cast<size_t>(d.nz + 1) * qv::kBfThreads * sizeof(float);
     if (smem > 48 * 1024 &&
-        qv_check_cuda(cudaFuncSetAttribute(qv::k_bf_expand, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        qv_check_cuda(cudaFuncSetAttribute(qv::k_bf_predict, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem)),
                       "smem attr") != QV_OK)
         return QV_ERR_CUDA;
-    for (int t = 0; t < iters; ++t) {
-        qv::k_bf_expand<<<5, qv::kBfThreads, smem, st>>>(d);
-        qv_status s = leaf_value(&h->model, h->Qu, d.sbelief, S, d.sU, stream);
-        if (s == QV_OK) s = qv_pbvi_value(h->pbvi, h->G, h->nG, d.sbelief, S, d.sL, nullptr, stream);
-        if (s != QV_OK) return s;
-        qv::k_bf_update<<<1, 32, 0, st>>>(d);
-        qv::k_bf_commit<<<S, qv::kBfThreads, 0, st>>>(d, 0);
+    // the first iteration eagerly on the caller's stream (it also restores the
+    // PBVI handle's reordered vectors and piece table the graph reads)
+    qv_status s = bf_issue(h, st, true);
+    if (s != QV_OK || iters == 1) return s;
+    if (!h->gs) {
+        if (qv_check_cuda(cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking), "stream") != QV_OK ||
+            qv_check_cuda(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "event") != QV_OK ||
+            qv_check_cuda(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "event") != QV_OK)
+            return QV_ERR_CUDA;
     }
-    return qv_check_cuda(cudaGetLastError(), "qv_bf_run launch");
+    if (qv_check_cuda(cudaEventRecord(h->ev_in, st), "event") != QV_OK ||
+        qv_check_cuda(cudaStreamWaitEvent(h->gs, h->ev_in, 0), "wait") != QV_OK)
+        return QV_ERR_CUDA;
+    if (!h->graph) {
+        cudaGraph_t g = nullptr;
+        if (qv_check_cuda(cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal), "capture") != QV_OK)
+            return QV_ERR_CUDA;
+        const qv_status cs = bf_issue(h, h->gs, false);
+        const cudaError_t ce = cudaStreamEndCapture(h->gs, &g);
+        if (cs != QV_OK) {
+            if (g) cudaGraphDestroy(g);
+            return cs;
+        }
+        if (qv_check_cuda(ce, "end capture") != QV_OK) return QV_ERR_CUDA;
+        const cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (qv_check_cuda(ie, "instantiate") != QV_OK) {
+            h->graph = nullptr;
+            return QV_ERR_CUDA;
+        }
+    }
+    for (int t = 1; t < iters; ++t)
+        if (qv_check_cuda(cudaGraphLaunch(h->graph, h->gs), "graph launch") != QV_OK) return QV_ERR_CUDA;
+    if (qv_check_cuda(cudaEventRecord(h->ev_out, h->gs), "event") != QV_OK ||
+        qv_check_cuda(cudaStreamWaitEvent(st, h->ev_out, 0), "wait") != QV_OK)
+        return QV_ERR_CUDA;
+    return QV_OK;
 }
 
 extern "C" qv_status qv_bf_read(qv_bf_t *h, qv_bf_result_t *r, qv_stream_t stream) {

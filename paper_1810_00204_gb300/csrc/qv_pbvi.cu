@@ -596,6 +596,8 @@ struct qv_pbvi {
     size_t ws_bytes;
     void *ws;                    // workspace the tables live in (set by qv_pbvi_set_points)
     int nB;                      // points of the current set
+    int gp_value_nG;             // vectors in Gp gathered by the last qv_pbvi_value call, 0 when a
+                                 // backup has overwritten Gp since
     int nbands;                  // bands of k_pbvi_predict
     int band_cells;
 };
@@ -697,6 +699,7 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
     h->ws_bytes = off;
     h->ws = nullptr;
     h->nB = 0;
+    h->gp_value_nG = 0;
     *out = h;
     return QV_OK;
 }
@@ -796,6 +799,7 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     float *slab = reinterpret_cast<float *>(ws + h->off_slab);
     const int gthreads = 256, gblocks = std::min<long long>((static_cast<long long>(nG) * Kp + gthreads - 1) / gthreads,
                                                             8LL * qv_num_sms());
+    h->gp_value_nG = 0;
     qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
                                                     reinterpret_cast<const int *>(ws + h->off_perm), Kp, Gp);
     qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
@@ -830,10 +834,12 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
 
 extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, const float *d_b, int32_t nb,
                                    float *d_value, int32_t *d_arg, qv_stream_t stream) {
-    if (!h || !d_G || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: null pointer");
+    if (!h || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: null pointer");
     if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: no workspace yet (qv_pbvi_set_points)");
     if (nG < 1 || nG > h->max_vectors || nb < 0)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: %d vectors, %d beliefs", nG, nb);
+    if (!d_G && h->gp_value_nG != nG)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: no vectors of this count kept from the last call");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(h->ws);
     const int Kp = h->Kp, N = h->model.H * h->model.pitch;
@@ -842,7 +848,10 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
     float *slab = reinterpret_cast<float *>(ws + h->off_slab);
     const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
     const int gb = 8 * qv_num_sms();
-    qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, Kp, Gp);
+    if (d_G) {
+        qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, Kp, Gp);
+        h->gp_value_nG = nG;
+    }
     // beliefs in chunks of up to max_points (the size of the Ap region)
     for (int c0 = 0; c0 < nb; c0 += h->max_points) {
         const int nc = std::min(h->max_points, nb - c0);
