@@ -200,13 +200,15 @@ class Pbvi:
                                    _ptr(best), _ptr(q), _stream(stream)), "qv_pbvi_backup")
         return dict(G=out, value=value, astar=astar, best=best, q=q)
 
-    def value(self, G: torch.Tensor, b: torch.Tensor, stream=None):
-        """V_PBVI(b) and the maximising vector's index for beliefs b [nb][H][pitch]."""
+    def value(self, G: Optional[torch.Tensor], b: torch.Tensor, nG: Optional[int] = None, stream=None):
+        """V_PBVI(b) and the maximising vector's index for beliefs b [nb][H][pitch].
+        G = None (with nG) reuses the vectors of the previous call."""
         nb = b.shape[0]
         v = torch.empty(nb, dtype=torch.float32, device=b.device)
         arg = torch.empty(nb, dtype=torch.int32, device=b.device)
-        check(lib().qv_pbvi_value(self.handle, _ptr(G.contiguous()), G.shape[0], _ptr(b.contiguous()), nb, _ptr(v),
-                                  _ptr(arg), _stream(stream)), "qv_pbvi_value")
+        n = G.shape[0] if G is not None else int(nG)
+        check(lib().qv_pbvi_value(self.handle, None if G is None else _ptr(G.contiguous()), n, _ptr(b.contiguous()),
+                                  nb, _ptr(v), _ptr(arg), _stream(stream)), "qv_pbvi_value")
         return v, arg
 
     def __del__(self):

@@ -230,3 +230,22 @@ def test_errors(api):
         pb.backup(G[:2], out=G[1:3])          # output overlaps the input
     r = pb.backup(G[:2])
     assert torch.isfinite(r["value"]).all()
+
+
+def test_value_reuses_its_vectors_until_a_backup(api):
+    from paper_1810_00204_gb300 import _native as N
+    w = WL.tiny(1)
+    m = api.Model(w)
+    G = _grid(m, _vectors(w, 6, 1))
+    b = _grid(m, _beliefs(w, 9, 1))
+    pb = api.Pbvi(m, 16)
+    pb.set_points(b[:3])
+    v1, a1 = pb.value(G, b)
+    v2, a2 = pb.value(None, b, nG=6)
+    assert torch.equal(v1, v2) and torch.equal(a1, a2)
+    with pytest.raises(N.QVError):
+        pb.value(None, b, nG=5)          # a different count was not kept
+    pb.backup(G)                          # reorders other vectors
+    with pytest.raises(N.QVError) as ei:
+        pb.value(None, b, nG=6)
+    assert ei.value.status == N.QV_ERR_INVALID
