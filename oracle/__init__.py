@@ -97,6 +97,10 @@ def lib():
         L.or_bestfirst.argtypes = ([P, vp, vp, C.c_int, vp, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
                                     C.c_int, vp, vp] + [vp] * 22)
         L.or_bestfirst.restype = C.c_int
+        L.or_env_step.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, vp]
+        L.or_env_step.restype = C.c_int
+        L.or_closed_loop.argtypes = [P, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_int] + [vp] * 8
+        L.or_closed_loop.restype = C.c_int
         _lib = L
     return _lib
 
@@ -487,6 +491,36 @@ def bestfirst(w, Qu, G, iters, K=None, seed=None, episode=None, max_depth=6, max
     out.update(expanded=o["expanded"], iterations=it, nodes=m, boundary=bd.value, belief=bel[:m],
                root_action=int(np.argmax(out["UQ"][0])) if out["count"][0].sum() else -1)
     return out
+
+
+def env_step(w, x, a, seed, e, step):
+    """The true system's step (motion outcome, then measurement): (x', z)."""
+    p = _prob(w)
+    z = C.c_int(0)
+    y = lib().or_env_step(p.ref, _p(labels(p)), int(x), int(a), int(seed), int(e), int(step), C.byref(z))
+    return y, z.value
+
+
+def closed_loop(w, Q, b0s, x0s, depth=None, K=None, seed=None, max_steps=50, **kw):
+    """E closed-loop episodes on the map of w (Alg. 1's outer loop): returns
+    dict(actions, obs [E][S], states [E][S+1], steps, success, ret, root_gap
+    [E][S], boundary [E][S])."""
+    p = _prob(w, **kw)
+    ww = p.w
+    depth = ww.depth if depth is None else depth
+    K = ww.K if K is None else K
+    seed = ww.seed if seed is None else seed
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(A, p.n))
+    b0s = np.ascontiguousarray(np.asarray(b0s, np.float64).reshape(-1, p.n))
+    x0s = np.ascontiguousarray(np.asarray(x0s, np.int32))
+    E, S = b0s.shape[0], int(max_steps)
+    o = dict(actions=np.zeros((E, S), np.int32), obs=np.zeros((E, S), np.int32),
+             states=np.zeros((E, S + 1), np.int32), steps=np.zeros(E, np.int32), success=np.zeros(E, np.int32),
+             ret=np.zeros(E, np.float64), root_gap=np.zeros((E, S), np.float64), boundary=np.zeros((E, S), np.int64))
+    lib().or_closed_loop(p.ref, _p(Q), E, _p(b0s), _p(x0s), int(depth), int(K), int(seed), S, _p(o["actions"]),
+                         _p(o["obs"]), _p(o["states"]), _p(o["steps"]), _p(o["success"]), _p(o["ret"]),
+                         _p(o["root_gap"]), _p(o["boundary"]))
+    return o
 
 
 def transition_row_dslip(w, x, a):

@@ -1103,3 +1103,110 @@ int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG,
     free(label); free(Rt); free(bbar); free(P); free(cnt); free(code);
     return it;
 }
+
+/* ---- Closed-loop episodes (Alg. 1 outer loop, Eq. 1) ------------------- */
+
+/* The true system's step: from x under action a, the motion outcome is
+ * drawn with u_m (word 0) and the measurement at the new cell with u_o
+ * (word 1) of the Philox stream {0, episode e, path = step, level code 254}.
+ * Motion: the intended move if u_m < 1 - 2 eps, the first perpendicular
+ * (a + 1) if u_m < 1 - eps, else the second (a + 3), in FP32 as the kernel
+ * decides; a blocked move stays (Eq. 10); stay, the goal and occupied
+ * cells stay.  Measurement: z from O(x', .) by the inverse CDF of
+ * or_sample_obs.                                                            */
+int or_env_step(const or_problem *p, const int *label, int x, int a, uint64_t seed, uint32_t e, int step, int *z_out) {
+    const float um = or_uniform(seed, e, 254, (uint64_t)step, 0);
+    const float uo = or_uniform(seed, e, 254, (uint64_t)step, 1);
+    int y = x;
+    if (!p->occ[x] && x != p->goal && a != 4) {
+        const float eps = (float)p->slip;
+        const float fwd = 1.0f - 2.0f * eps;
+        const int d = um < fwd ? a : (um < fwd + eps ? (a + 1) % 4 : (a + 3) % 4);
+        const int r = x / p->W + DR[d], c = x % p->W + DC[d];
+        if (is_free(p, r, c)) y = r * p->W + c;
+    }
+    const int nz = p->B + 1;
+    double *P = (double *)malloc(sizeof(double) * nz);
+    for (int z = 0; z < nz; ++z) P[z] = or_obs_lik(p, label, y, z);
+    *z_out = or_sample_obs(P, nz, uo);
+    free(P);
+    return y;
+}
+
+/* E episodes of the loop of Alg. 1 (its outer loop): plan from the belief
+ * (the level-synchronous tree, Philox episode word = step * E + e), execute
+ * the root action on the true state, receive a measurement, update the
+ * belief by Eq. 3, until the goal is reached or max_steps.  Inputs b0s
+ * [E][n], x0s [E].  Outputs: actions, obs [E][max_steps], states
+ * [E][max_steps + 1] (-1 after the end), steps [E] (moves made), success
+ * [E] (goal reached), ret [E] (sum of gamma^t r(x_{t+1}), Eq. 1), root_gap
+ * [E][max_steps] (the gap between the two best root Q-values, for deciding
+ * near-ties), boundary [E][max_steps] (draws near a CDF step in the plan).  */
+int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0s, const int *x0s, int depth, int K,
+                   uint64_t seed, int max_steps, int *actions, int *obs, int *states, int *steps, int *success,
+                   double *ret, double *root_gap, long *boundary) {
+    const int n = p->H * p->W, A = OR_NUM_ACTIONS, nz = p->B + 1;
+    int *label = (int *)malloc(sizeof(int) * n);
+    or_labels(p, label);
+    /* tree capacity (5 min(K, |Z|))^l per level */
+    long *off = (long *)malloc(sizeof(long) * (depth + 2));
+    off[0] = 0;
+    long cap = 1;
+    for (int l = 0; l <= depth; ++l) {
+        off[l + 1] = off[l] + cap;
+        cap *= A * (K < nz ? K : nz);
+    }
+    const long tot = off[depth + 1];
+    int *n_level = (int *)malloc(sizeof(int) * (depth + 1));
+    int *par = (int *)malloc(sizeof(int) * tot), *act = (int *)malloc(sizeof(int) * tot);
+    int *ob = (int *)malloc(sizeof(int) * tot);
+    double *wt = (double *)malloc(sizeof(double) * tot), *pz = (double *)malloc(sizeof(double) * tot);
+    double *val = (double *)malloc(sizeof(double) * tot);
+    double *R = (double *)malloc(sizeof(double) * tot * A), *UQ = (double *)malloc(sizeof(double) * tot * A);
+    int *samp = (int *)malloc(sizeof(int) * tot * A * K);
+    unsigned char *bd = (unsigned char *)malloc(tot * A * K);
+    double *b = (double *)malloc(sizeof(double) * n), *bbar = (double *)malloc(sizeof(double) * n);
+    for (int e = 0; e < E; ++e) {
+        for (int x = 0; x < n; ++x) b[x] = b0s[(size_t)e * n + x];
+        int x = x0s[e];
+        double g = 1.0, rsum = 0.0;
+        int t = 0, ok = 0;
+        states[(size_t)e * (max_steps + 1)] = x;
+        for (; t < max_steps && x != p->goal; ++t) {
+            int ra; double rv, rq[OR_NUM_ACTIONS]; long bc = 0;
+            or_tree_plan(p, Q, b, depth, K, seed, (uint32_t)(t * E + e), 0, NULL, off, -1, n_level, par, act, ob,
+                         wt, pz, val, R, UQ, samp, bd, NULL, &ra, &rv, rq, &bc);
+            double q1 = -HUGE_VAL, q2 = -HUGE_VAL;
+            for (int a = 0; a < A; ++a) {
+                if (rq[a] > q1) { q2 = q1; q1 = rq[a]; }
+                else if (rq[a] > q2) q2 = rq[a];
+            }
+            root_gap[(size_t)e * max_steps + t] = q1 - q2;
+            boundary[(size_t)e * max_steps + t] = bc;
+            int z;
+            const int y = or_env_step(p, label, x, ra, seed, (uint32_t)e, t, &z);
+            actions[(size_t)e * max_steps + t] = ra;
+            obs[(size_t)e * max_steps + t] = z;
+            rsum += g * (y == p->goal ? 100.0 : -1.0 - (p->cost ? p->cost[y] : 0.0));
+            g *= p->gamma;
+            or_predict(p, b, ra, bbar);
+            or_correct(p, label, bbar, z, b);
+            x = y;
+            states[(size_t)e * (max_steps + 1) + t + 1] = x;
+        }
+        ok = (x == p->goal);
+        for (int s = t; s < max_steps; ++s) {
+            actions[(size_t)e * max_steps + s] = -1;
+            obs[(size_t)e * max_steps + s] = -1;
+            root_gap[(size_t)e * max_steps + s] = 0.0;
+            boundary[(size_t)e * max_steps + s] = 0;
+            states[(size_t)e * (max_steps + 1) + s + 1] = -1;
+        }
+        steps[e] = t;
+        success[e] = ok;
+        ret[e] = rsum;
+    }
+    free(label); free(off); free(n_level); free(par); free(act); free(ob); free(wt); free(pz); free(val);
+    free(R); free(UQ); free(samp); free(bd); free(b); free(bbar);
+    return 0;
+}

@@ -132,6 +132,12 @@ int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG,
                  int *cbeg, int *ccnt, long *boundary, const int *force, double *best_h, double *forced_h,
                  double *slack);
 
+/* ---- Closed-loop episodes (Alg. 1 outer loop, Eq. 1) ---- */
+int or_env_step(const or_problem *p, const int *label, int x, int a, uint64_t seed, uint32_t e, int step, int *z_out);
+int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0s, const int *x0s, int depth, int K,
+                   uint64_t seed, int max_steps, int *actions, int *obs, int *states, int *steps, int *success,
+                   double *ret, double *root_gap, long *boundary);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
