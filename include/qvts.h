@@ -470,6 +470,35 @@ qv_status qv_bf_read(qv_bf_t *bf, qv_bf_result_t *h_result, qv_stream_t stream);
 qv_status qv_bf_view(const qv_bf_t *bf, qv_bf_view_t *view);
 void qv_bf_destroy(qv_bf_t *bf);
 
+/* ---------------------------------------------------------------- closed-loop episodes (Alg. 1)
+ * The outer loop of Alg. 1 for E episodes on one map: plan (a batched plan
+ * whose episode e plans from belief e), execute, measure, update.
+ * qv_plan_actions_device: the device address of episode 0's root action in
+ * a plan's results; episode e's is at e * *stride (int32 units).
+ * qv_env_step: the true system's step of every episode not yet at the goal
+ * (d_done[e] == 0): action a = d_action[e * action_stride] from state
+ * d_state[e] (a cell, row * pitch + col), the motion outcome drawn with u_m
+ * and the measurement at the new cell with u_o, words 0 and 1 of the Philox
+ * stream {0, e, step, 254 << 24} (key seed): the intended move if
+ * u_m < 1 - 2 eps, the first perpendicular (a + 1) if u_m < 1 - eps, else
+ * the second (a + 3), FP32 comparisons, a blocked move staying (Eq. 10); z
+ * by the FP32 inverse CDF of O(x', .) in ascending z.  Updates d_state,
+ * d_obs (-1 for finished episodes), d_steps (+1), d_return (+= gamma^step
+ * r(x'), Eq. 1), d_done (1 at the goal).
+ * qv_belief_update_batched: b_e <- tau(b_e, a_e, z_e) (Eq. 3) in place for
+ * every episode with d_obs[e] >= 0; d_B [E][H][pitch].  Workspace:
+ * qv_belief_update_batched_workspace_bytes (256-byte aligned). */
+const int32_t *qv_plan_actions_device(const qv_plan_t *plan, int32_t *stride);
+qv_status qv_env_step(const qv_model_t *model, int32_t E, const int32_t *d_action,
+                      int32_t action_stride, int32_t *d_state, uint64_t seed, int32_t step,
+                      int32_t *d_obs, int32_t *d_steps, float *d_return, int32_t *d_done,
+                      qv_stream_t stream);
+size_t qv_belief_update_batched_workspace_bytes(const qv_model_t *model, int32_t E);
+qv_status qv_belief_update_batched(const qv_model_t *model, int32_t E, float *d_B,
+                                   const int32_t *d_action, int32_t action_stride,
+                                   const int32_t *d_obs, void *d_ws, size_t ws_bytes,
+                                   qv_stream_t stream);
+
 /* ---------------------------------------------------------------- adjoint of the plan
  * qv_tree_backward: reverse mode of the root value U_V(b0) of episode e of a
  * plan that has run (stream order), by the derivatives of Alg. 6 and 7

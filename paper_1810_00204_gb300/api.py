@@ -309,6 +309,62 @@ class BestFirst:
             self.handle = None
 
 
+def run_episodes(model: Model, Q: torch.Tensor, b0s: Sequence[torch.Tensor], starts: Sequence[int], depth=3, K=8,
+                 seed=0, max_steps=100, check_every=8, history=False, stream=None) -> dict:
+    """Closed-loop episodes (Alg. 1's outer loop) of E = len(b0s) robots on
+    one map: each step one batched plan (episode e plans from belief e with
+    Philox episode word step * E + e), the true system's step (qv_env_step)
+    and the belief update (qv_belief_update_batched), with no host wait
+    inside a step; every `check_every` steps the host reads whether all
+    episodes ended.  starts: unpadded cells.  Returns dict(steps, success,
+    ret, states [E], steps_run) on the host; with history, also the states
+    [steps_run + 1][E] and measurements [steps_run][E] (-1 once ended),
+    copied on the device each step."""
+    E = len(b0s)
+    dev = model.device
+    B = torch.stack([b.contiguous() for b in b0s]).contiguous()
+    state = torch.tensor([model.pcell(int(s)) for s in starts], dtype=torch.int32, device=dev)
+    obs = torch.full((E,), -1, dtype=torch.int32, device=dev)
+    steps = torch.zeros(E, dtype=torch.int32, device=dev)
+    ret = torch.zeros(E, dtype=torch.float32, device=dev)
+    done = (state == model.goal).to(torch.int32)
+    nws = lib().qv_belief_update_batched_workspace_bytes(C.byref(model.struct), E)
+    ws = torch.empty(nws + 256, dtype=torch.uint8, device=dev)
+    wsp = C.c_void_p(ws.data_ptr() + (-ws.data_ptr()) % 256)
+    stride = C.c_int32(0)
+    hist_s = torch.full((max_steps + 1, E), -1, dtype=torch.int32, device=dev) if history else None
+    hist_z = torch.full((max_steps, E), -1, dtype=torch.int32, device=dev) if history else None
+    if history:
+        hist_s[0].copy_(state)
+    t = 0
+    for t in range(max_steps):
+        plan = Plan([model] * E, [Q] * E, [B[e] for e in range(E)], depth=depth, K=K, seed=seed, episode=t * E,
+                    stream=stream)
+        plan.run(stream)
+        act = lib().qv_plan_actions_device(plan.handle, C.byref(stride))
+        check(lib().qv_env_step(C.byref(model.struct), E, act, stride.value, _ptr(state), int(seed), t, _ptr(obs),
+                                _ptr(steps), _ptr(ret), _ptr(done), _stream(stream)), "qv_env_step")
+        check(lib().qv_belief_update_batched(C.byref(model.struct), E, _ptr(B), act, stride.value, _ptr(obs), wsp,
+                                             nws, _stream(stream)), "qv_belief_update_batched")
+        if history:
+            hist_s[t + 1].copy_(state)
+            hist_z[t].copy_(obs)
+        if (t + 1) % check_every == 0 and bool(done.all()):
+            t += 1
+            break
+    else:
+        t = max_steps
+    def unpad(a):
+        return np.where(a >= 0, (a // model.P) * model.W + a % model.P, -1)
+
+    out = dict(steps=steps.cpu().numpy(), success=done.cpu().numpy(), ret=ret.cpu().numpy(),
+               states=unpad(state.cpu().numpy().astype(np.int64)), steps_run=t, beliefs=B)
+    if history:
+        out["state_history"] = unpad(hist_s[:t + 1].cpu().numpy().astype(np.int64))
+        out["obs_history"] = hist_z[:t].cpu().numpy()
+    return out
+
+
 def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
     """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
     is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),
