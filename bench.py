@@ -261,6 +261,48 @@ def bestfirst_measurement(args, dev, stream, iters=400):
     return out
 
 
+def episodes_measurement(args, dev, stream, E=64, max_steps=200):
+    """Closed-loop episodes (Alg. 1's outer loop) on the mid map with its
+    planning configuration (d = 3, K = 8, QMDP leaves): E robots from
+    different start cells; each step one batched plan, the true system's
+    step and the belief update.  Timed with CUDA events (host check of the
+    end every 8 steps included)."""
+    import torch
+    import oracle as O
+    from paper_1810_00204_gb300 import api, workloads as WL
+    w = WL.mid(args.seed)
+    m = api.Model(w, device=dev)
+    Q = api.mdp_value_iterate(m, dtype="f32")["Q"]
+    eps = WL.episodes(w, E, seed=args.seed + 11)
+    b0s = [m.to_grid(e.b0) for e in eps]
+    starts = [e.start for e in eps]
+    api.run_episodes(m, Q, b0s[:4], starts[:4], depth=w.depth, K=w.K, seed=w.seed, max_steps=3)  # warm-up
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    g = api.run_episodes(m, Q, b0s, starts, depth=w.depth, K=w.K, seed=w.seed, max_steps=max_steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    robot_steps = int(g["steps"].sum())
+    ok = g["success"].astype(bool)
+    out = {"episodes": E, "max_steps": max_steps, "steps_run": g["steps_run"], "ms": ms,
+           "robot_steps": robot_steps, "robot_steps_per_s": robot_steps / (ms * 1e-3),
+           "plans_per_s": E * g["steps_run"] / (ms * 1e-3),
+           "success_rate": float(ok.mean()), "mean_steps_success": float(g["steps"][ok].mean()) if ok.any() else None,
+           "mean_return": float(g["ret"].mean()),
+           "note": "plans for finished episodes still run inside the batch (counted in plans_per_s)"}
+    if not args.no_cpu:
+        Qh = m.from_grid(Q).reshape(5, -1).astype("float64")
+        t0 = time.perf_counter()
+        ro = O.closed_loop(w, Qh, [eps[0].b0], [eps[0].start], max_steps=10)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": int(ro["steps"][0]) / el, "unit": "robot steps/s", "cores": O.num_threads(),
+                               "kind": "oracle",
+                               "sample": f"the oracle's first {int(ro['steps'][0])} steps of one episode, {el:.1f} s"}
+    return out
+
+
 def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
     """Sub-measurements beside the headline: the step's requests as one
     batched launch, the 256-episode batch of uneven maps, and the 512x512
@@ -358,6 +400,8 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     out["aems_fields_mid"] = aems_measurement(args, dev, K, stream)
     # (8) the best-first planning loop of Alg. 1 on the mid map
     out["bestfirst_mid"] = bestfirst_measurement(args, dev, stream)
+    # (9) closed-loop episodes (Alg. 1's outer loop) on the mid map
+    out["episodes_mid"] = episodes_measurement(args, dev, stream)
     return out
 
 
@@ -695,6 +739,7 @@ def main():
                                                with_cpu=not args.no_cpu)
                 out["aems_fields"] = aems_measurement(args, dev, max(3, args.extra_steps), stream)
                 out["bestfirst"] = bestfirst_measurement(args, dev, stream)
+                out["episodes"] = episodes_measurement(args, dev, stream)
             print(json.dumps(out), flush=True)
         return
     R = args.plans_per_step
