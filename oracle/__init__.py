@@ -101,6 +101,8 @@ def lib():
         L.or_env_step.restype = C.c_int
         L.or_closed_loop.argtypes = [P, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_int] + [vp] * 8
         L.or_closed_loop.restype = C.c_int
+        L.or_forward_sample.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_uint64, vp]
+        L.or_forward_sample.restype = None
         _lib = L
     return _lib
 
@@ -521,6 +523,16 @@ def closed_loop(w, Q, b0s, x0s, depth=None, K=None, seed=None, max_steps=50, **k
                          _p(o["obs"]), _p(o["states"]), _p(o["steps"]), _p(o["success"]), _p(o["ret"]),
                          _p(o["root_gap"]), _p(o["boundary"]))
     return o
+
+
+def forward_sample(w, b, a, K, seed=0, episode=0, level=0, path=0):
+    """K measurements for (b, a) by Alg. 4's ancestral sampler: x ~ b,
+    x' ~ T(x, a, .), z ~ O(x', .)."""
+    p = _prob(w)
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    z = np.zeros(K, np.int32)
+    lib().or_forward_sample(p.ref, _p(b), int(a), int(K), int(seed), int(episode), int(level), int(path), _p(z))
+    return z
 
 
 def transition_row_dslip(w, x, a):

@@ -1210,3 +1210,47 @@ int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0
     free(R); free(UQ); free(samp); free(bd); free(b); free(bbar);
     return 0;
 }
+
+/* ---- Ancestral forward sampling, Alg. 4 as written ---------------------- */
+
+/* K measurement samples for (b, a), each by Alg. 4's three stages: x ~ b
+ * (inverse CDF over the cells in index order), x' ~ T(x, a, .) (the
+ * system's motion rule of or_env_step), z ~ O(x', .) (or_sample_obs).  The
+ * uniforms of sample k are words 3k, 3k + 1, 3k + 2 of the Philox stream of
+ * (level, path); the CDF of b runs in FP32, as the sampler kernels' do.    */
+void or_forward_sample(const or_problem *p, const double *b, int a, int K, uint64_t seed, uint32_t episode,
+                       int level, uint64_t path, int *z) {
+    const int n = p->H * p->W, nz = p->B + 1;
+    int *label = (int *)malloc(sizeof(int) * n);
+    float *C = (float *)malloc(sizeof(float) * n);
+    double *P = (double *)malloc(sizeof(double) * nz);
+    or_labels(p, label);
+    float run = 0.0f;
+    for (int x = 0; x < n; ++x) {
+        run = run + (p->occ[x] ? 0.0f : (float)b[x]);
+        C[x] = run;
+    }
+    for (int k = 0; k < K; ++k) {
+        const float u1 = or_uniform(seed, episode, level, path, 3 * k);
+        const float u2 = or_uniform(seed, episode, level, path, 3 * k + 1);
+        const float u3 = or_uniform(seed, episode, level, path, 3 * k + 2);
+        /* x ~ b */
+        const float t = u1 * C[n - 1];
+        int x = n - 1;
+        for (int i = 0; i < n; ++i)
+            if (t < C[i]) { x = i; break; }
+        /* x' ~ T(x, a, .) */
+        int y = x;
+        if (!p->occ[x] && x != p->goal && a != 4) {
+            const float eps = (float)p->slip;
+            const float fwd = 1.0f - 2.0f * eps;
+            const int d = u2 < fwd ? a : (u2 < fwd + eps ? (a + 1) % 4 : (a + 3) % 4);
+            const int r = x / p->W + DR[d], c = x % p->W + DC[d];
+            if (is_free(p, r, c)) y = r * p->W + c;
+        }
+        /* z ~ O(x', .) */
+        for (int zz = 0; zz < nz; ++zz) P[zz] = or_obs_lik(p, label, y, zz);
+        z[k] = or_sample_obs(P, nz, u3);
+    }
+    free(label); free(C); free(P);
+}

@@ -138,6 +138,10 @@ int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0
                    uint64_t seed, int max_steps, int *actions, int *obs, int *states, int *steps, int *success,
                    double *ret, double *root_gap, long *boundary);
 
+/* ---- Ancestral forward sampling (Alg. 4) ---- */
+void or_forward_sample(const or_problem *p, const double *b, int a, int K, uint64_t seed, uint32_t episode,
+                       int level, uint64_t path, int *z);
+
 int or_num_threads(void);
 void or_set_threads(int n);
 
