@@ -499,6 +499,22 @@ qv_status qv_belief_update_batched(const qv_model_t *model, int32_t E, float *d_
                                    const int32_t *d_obs, void *d_ws, size_t ws_bytes,
                                    qv_stream_t stream);
 
+/* ---------------------------------------------------------------- ancestral sampler (Alg. 4)
+ * qv_forward_sample: K measurement samples for each of n (belief, action)
+ * pairs by Alg. 4 as written, one thread per sample: x ~ b (the inverse CDF
+ * of b over the cells in index order, FP32 prefix sums), x' ~ T(x, a, .)
+ * and z ~ O(x', .) by qv_env_step's rules.  Sample k of pair j uses words
+ * 3k, 3k + 1, 3k + 2 of the Philox stream {.., episode, d_path[j], level}.
+ * The tree search draws z from the exact marginal P(z | b, a) instead (one
+ * inverse CDF over z); both have the same law.  d_B [n][H][pitch],
+ * d_action [n], d_path [n], d_z [n][K]; workspace
+ * qv_forward_sample_workspace_bytes (the prefix sums). */
+size_t qv_forward_sample_workspace_bytes(const qv_model_t *model, int32_t n);
+qv_status qv_forward_sample(const qv_model_t *model, int32_t n, const float *d_B,
+                            const int32_t *d_action, const uint64_t *d_path, int32_t level,
+                            uint64_t seed, uint32_t episode, int32_t K, int32_t *d_z, void *d_ws,
+                            size_t ws_bytes, qv_stream_t stream);
+
 /* ---------------------------------------------------------------- adjoint of the plan
  * qv_tree_backward: reverse mode of the root value U_V(b0) of episode e of a
  * plan that has run (stream order), by the derivatives of Alg. 6 and 7

@@ -132,6 +132,8 @@ SIGNATURES = {
     "qv_env_step": (C.c_int, [_M, _i32, _vp, _i32, _vp, C.c_uint64, _i32, _vp, _vp, _vp, _vp, _vp]),
     "qv_belief_update_batched_workspace_bytes": (_sz, [_M, _i32]),
     "qv_belief_update_batched": (C.c_int, [_M, _i32, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "qv_forward_sample_workspace_bytes": (_sz, [_M, _i32]),
+    "qv_forward_sample": (C.c_int, [_M, _i32, _vp, _vp, _vp, _i32, C.c_uint64, C.c_uint32, _i32, _vp, _vp, _sz, _vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
     "qv_plan_autotune_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_autotune": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, _i32, C.POINTER(qv_tune_t),

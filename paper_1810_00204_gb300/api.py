@@ -365,6 +365,21 @@ def run_episodes(model: Model, Q: torch.Tensor, b0s: Sequence[torch.Tensor], sta
     return out
 
 
+def forward_sample(model: Model, B: torch.Tensor, actions, paths, K: int, level=0, seed=0, episode=0, stream=None):
+    """Alg. 4's ancestral sampler: K measurements for each (belief B[j],
+    action actions[j]) with Philox path paths[j].  Returns int32 [n][K]."""
+    n = B.shape[0]
+    a = torch.as_tensor(actions, dtype=torch.int32, device=B.device).contiguous()
+    pth = torch.as_tensor(paths, dtype=torch.int64, device=B.device).contiguous()
+    z = torch.empty((n, K), dtype=torch.int32, device=B.device)
+    nws = lib().qv_forward_sample_workspace_bytes(C.byref(model.struct), n)
+    ws = torch.empty(max(nws, 1), dtype=torch.uint8, device=B.device)
+    check(lib().qv_forward_sample(C.byref(model.struct), n, _ptr(B.contiguous()), _ptr(a), _ptr(pth), int(level),
+                                  int(seed), int(episode), int(K), _ptr(z), _ptr(ws), nws, _stream(stream)),
+          "qv_forward_sample")
+    return z
+
+
 def mdp_value_iterate_checkpointed(model: Model, sweeps: int, every: int = 16, stream=None):
     """Exactly `sweeps` FP64 sweeps from V_0 = 0, keeping V_k at every k that
     is a multiple of `every` for mdp_value_backward.  Returns dict(V (FP64),

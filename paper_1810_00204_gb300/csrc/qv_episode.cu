@@ -14,6 +14,9 @@
 //                 bands' sums added in band order
 // The plan between them is the batched level-synchronous plan; its root
 // actions are read on the device, so a whole step needs no host wait.
+// k_forward_sample is Alg. 4's ancestral sampler as written (x ~ b,
+// x' ~ T, z ~ O, one thread per sample) with the same motion and
+// measurement rules.
 #include <algorithm>
 
 #include "qv_plan_types.cuh"
@@ -48,6 +51,34 @@ EnvArgs env_args(const qv_model_t *m) {
     return a;
 }
 
+// One motion outcome of action a from cell x (Sec. II, Eq. 10): the
+// intended move if u < 1 - 2 eps, the first perpendicular (a + 1) if
+// u < 1 - eps, else the second (a + 3), in FP32; a blocked move, staying,
+// the goal and occupied cells keep x.
+__device__ __forceinline__ int system_move(const EnvArgs &m, int x, int a, float u) {
+    const unsigned cw = m.cell[x];
+    if (!QV_CELL_FREE(cw) || x == m.goal || a == 4) return x;
+    const float fwd = 1.0f - 2.0f * m.slip;
+    const int d = u < fwd ? a : (u < fwd + m.slip ? ((a + 1) & 3) : ((a + 3) & 3));
+    const int stepd[4] = {-m.P, 1, m.P, -1};
+    return ((QV_CELL_BLOCKED(cw) >> d) & 1u) ? x : x + stepd[d];
+}
+
+// One measurement at cell y: O(y, .) is the accuracy on y's label and eta
+// elsewhere, drawn by the FP32 inverse CDF in ascending z.
+__device__ __forceinline__ int system_measure(const EnvArgs &m, int y, float u) {
+    const int own = static_cast<int>(QV_CELL_LABEL(m.cell[y]));
+    float total = 0.0f;
+    for (int z = 0; z <= m.B; ++z) total = total + (z == own ? m.acc : m.eta);
+    const float t_u = u * total;
+    float run = 0.0f;
+    for (int k = 0; k <= m.B; ++k) {
+        run = run + (k == own ? m.acc : m.eta);
+        if (t_u < run) return k;
+    }
+    return m.B;
+}
+
 __global__ void k_env_step(EnvArgs m, int E, const int *__restrict__ action, int stride, int *__restrict__ state,
                            uint64_t seed, int step, int *__restrict__ obs, int *__restrict__ steps,
                            float *__restrict__ ret, int *__restrict__ done) {
@@ -61,29 +92,8 @@ __global__ void k_env_step(EnvArgs m, int E, const int *__restrict__ action, int
     const int a = min(max(action[static_cast<size_t>(e) * stride], 0), 4);
     const float um = sample_uniform(seed, static_cast<uint32_t>(e), kEnvLevel, static_cast<uint64_t>(step), 0);
     const float uo = sample_uniform(seed, static_cast<uint32_t>(e), kEnvLevel, static_cast<uint64_t>(step), 1);
-    const unsigned cw = m.cell[x];
-    int y = x;
-    if (QV_CELL_FREE(cw) && x != m.goal && a != 4) {
-        const float fwd = 1.0f - 2.0f * m.slip;
-        const int d = um < fwd ? a : (um < fwd + m.slip ? ((a + 1) & 3) : ((a + 3) & 3));
-        const int stepd[4] = {-m.P, 1, m.P, -1};
-        if (!((QV_CELL_BLOCKED(cw) >> d) & 1u)) y = x + stepd[d];
-    }
-    // the measurement at y: O(y, .) = accuracy on its label, eta elsewhere,
-    // drawn by the FP32 inverse CDF in ascending z
-    const int own = static_cast<int>(QV_CELL_LABEL(m.cell[y]));
-    float total = 0.0f;
-    for (int z = 0; z <= m.B; ++z) total = total + (z == own ? m.acc : m.eta);
-    const float t_u = uo * total;
-    float run = 0.0f;
-    int z = m.B;
-    for (int k = 0; k <= m.B; ++k) {
-        run = run + (k == own ? m.acc : m.eta);
-        if (t_u < run) {
-            z = k;
-            break;
-        }
-    }
+    const int y = system_move(m, x, a, um);
+    const int z = system_measure(m, y, uo);
     state[e] = y;
     obs[e] = z;
     const float r = (y == m.goal) ? 100.0f : -1.0f - (m.cost ? m.cost[y] : 0.0f);
@@ -173,8 +183,83 @@ __global__ void __launch_bounds__(kEpThreads) k_bu_correct(EnvArgs m, float *__r
 
 constexpr int kBandCells = 4096;
 
+// Alg. 4 as written, one CTA per (belief, action) and one thread per
+// sample: x ~ b by the inverse CDF over the cells in index order (a
+// block-wide FP32 prefix sum: per-thread chunks, then the chunk totals in
+// thread order), x' = system_move, z = system_measure.  Sample k uses
+// words 3k, 3k + 1, 3k + 2 of the stream of (level, path).
+__global__ void __launch_bounds__(kEpThreads) k_forward_sample(EnvArgs m, const float *__restrict__ Bset,
+                                                               const int *__restrict__ action,
+                                                               const unsigned long long *__restrict__ path,
+                                                               int level, uint64_t seed, uint32_t episode, int K,
+                                                               float *__restrict__ cdf, int *__restrict__ zout) {
+    __shared__ float s_base[kEpThreads];
+    const int j = blockIdx.x, tid = threadIdx.x;
+    const float *b = Bset + static_cast<size_t>(j) * m.N;
+    float *C = cdf + static_cast<size_t>(j) * m.N;
+    const int chunk = (m.N + kEpThreads - 1) / kEpThreads;
+    const int c0 = min(m.N, tid * chunk), c1 = min(m.N, c0 + chunk);
+    float s = 0.0f;
+    for (int y = c0; y < c1; ++y) s += QV_CELL_FREE(m.cell[y]) ? b[y] : 0.0f;
+    s_base[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        float run = 0.0f;
+        for (int t = 0; t < kEpThreads; ++t) {
+            const float v = s_base[t];
+            s_base[t] = run;
+            run = run + v;
+        }
+    }
+    __syncthreads();
+    float run = s_base[tid];
+    for (int y = c0; y < c1; ++y) {
+        run = run + (QV_CELL_FREE(m.cell[y]) ? b[y] : 0.0f);
+        C[y] = run;
+    }
+    __syncthreads();
+    const float total = C[m.N - 1];
+    const int a = min(max(action[j], 0), 4);
+    const unsigned long long pth = path[j];
+    for (int k = tid; k < K; k += blockDim.x) {
+        const float u1 = sample_uniform(seed, episode, level, pth, 3 * k);
+        const float u2 = sample_uniform(seed, episode, level, pth, 3 * k + 1);
+        const float u3 = sample_uniform(seed, episode, level, pth, 3 * k + 2);
+        const float t = u1 * total;
+        int lo = 0, hi = m.N - 1;  // first cell with t < C[cell]
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (t < C[mid]) hi = mid;
+            else lo = mid + 1;
+        }
+        const int y = system_move(m, lo, a, u2);
+        zout[static_cast<size_t>(j) * K + k] = system_measure(m, y, u3);
+    }
+}
+
 }  // namespace
 }  // namespace qv
+
+extern "C" size_t qv_forward_sample_workspace_bytes(const qv_model_t *m, int32_t n) {
+    if (!m || n < 1) return 0;
+    return static_cast<size_t>(n) * m->H * m->pitch * sizeof(float);
+}
+
+extern "C" qv_status qv_forward_sample(const qv_model_t *m, int32_t n, const float *d_B, const int32_t *d_action,
+                                       const uint64_t *d_path, int32_t level, uint64_t seed, uint32_t episode,
+                                       int32_t K, int32_t *d_z, void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    if (!m || !m->d_cell || !d_B || !d_action || !d_path || !d_z || !d_ws)
+        return qv_set_error(QV_ERR_INVALID, "qv_forward_sample: null pointer");
+    if (n < 0 || K < 0 || level < 0 || level > 255 || m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
+        return qv_set_error(QV_ERR_INVALID, "qv_forward_sample: bad arguments");
+    if (n == 0 || K == 0) return QV_OK;
+    if (ws_bytes < qv_forward_sample_workspace_bytes(m, n))
+        return qv_set_error(QV_ERR_WORKSPACE, "qv_forward_sample: workspace too small");
+    qv::k_forward_sample<<<n, qv::kEpThreads, 0, static_cast<cudaStream_t>(stream)>>>(
+        qv::env_args(m), d_B, d_action, reinterpret_cast<const unsigned long long *>(d_path), level, seed, episode, K,
+        static_cast<float *>(d_ws), d_z);
+    return qv_check_cuda(cudaGetLastError(), "qv_forward_sample launch");
+}
 
 extern "C" const int32_t *qv_plan_actions_device(const qv_plan_t *pl, int32_t *stride) {
     if (!pl) return nullptr;

@@ -1,0 +1,64 @@
+"""GPU parity of Alg. 4's ancestral sampler (qv_forward_sample): from a
+one-cell belief every draw is decided by FP32 comparisons on both sides, so
+the samples equal the oracle's exactly; from spread beliefs the samples
+follow the exact marginal P(z | b, a) (chi-square at the 1e-4 level), the
+law of the tree's inverse-CDF sampler."""
+import numpy as np
+import pytest
+from scipy.stats import chisquare
+
+import oracle as O
+from paper_1810_00204_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1810_00204_gb300 import api as A
+    return A
+
+
+def test_one_cell_beliefs_match_exactly(api):
+    w = WL.tiny(2, H=11, W=13)   # pitch 16: padded rows
+    m = api.Model(w)
+    free = np.flatnonzero(w.occ.ravel() == 0)
+    cells = [int(c) for c in free[::7] if c != w.goal][:8]
+    B = np.zeros((len(cells) * 5, w.H * w.W), np.float32)
+    acts, paths = [], []
+    for i, c in enumerate(cells):
+        for a in range(5):
+            B[i * 5 + a, c] = 1.0
+            acts.append(a)
+            paths.append(1000 + i * 5 + a)
+    z = api.forward_sample(m, m.to_grid(B.reshape(-1, w.H, w.W)), acts, paths, 64, level=3, seed=11,
+                           episode=2).cpu().numpy()
+    for j in range(len(acts)):
+        ref = O.forward_sample(w, B[j].astype(np.float64), acts[j], 64, seed=11, episode=2, level=3, path=paths[j])
+        assert np.array_equal(z[j], ref), j
+
+
+@pytest.mark.parametrize("a", [0, 1, 4])
+def test_spread_beliefs_follow_the_marginal(api, a):
+    w = WL.mid(1, H=67, W=45)
+    m = api.Model(w)
+    rng = np.random.default_rng(a)
+    free = np.flatnonzero(w.occ.ravel() == 0)
+    b = np.zeros(w.H * w.W, np.float32)
+    b[free] = rng.random(len(free))
+    b /= b.sum()
+    n, K = 4, 8192
+    B = np.repeat(b[None, :], n, axis=0)
+    z = api.forward_sample(m, m.to_grid(B.reshape(n, w.H, w.W)), [a] * n, list(range(n)), K, level=1,
+                           seed=5).cpu().numpy().ravel()
+    P = O.obs_marginal(w, O.predict(w, b.astype(np.float64), a))
+    P = P / P.sum()
+    keep = P * len(z) >= 5
+    cnt = np.bincount(z, minlength=w.B + 1)
+    fo = np.append(cnt[keep], cnt[~keep].sum())
+    fe = np.append(P[keep], P[~keep].sum()) * len(z)
+    if fe[-1] == 0:
+        fo, fe = fo[:-1], fe[:-1]
+    assert chisquare(fo, fe).pvalue > 1e-4
