@@ -455,6 +455,15 @@ def primitive_measurement(args, dev, K, peak):
     nbytes = n * Nl * 4 + 20 * Nl
     res["leaf_value"] = {"beliefs": n, "cells": Nl, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
                          "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
+    # Alg. 4's ancestral sampler: 256 (belief, action) pairs of 512x512, 64
+    # samples each; per pair it reads the belief and the cell words and
+    # writes the prefix sums (the samples' own reads are L2 hits)
+    Ks = 64
+    ms = timed(lambda: api.forward_sample(ml, bl, [k % 5 for k in range(n)], list(range(n)), Ks, level=1), K)
+    nbytes = n * Nl * (4 + 2 + 4)
+    res["forward_sample_ancestral"] = {"pairs": n, "samples_per_pair": Ks, "cells": Nl, "ms": ms,
+                                       "samples_per_s": n * Ks / (ms * 1e-3), "GBps": nbytes / (ms * 1e-3) / 1e9,
+                                       "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
     return res
 
 
