@@ -508,7 +508,8 @@ qv_status qv_belief_update_batched(const qv_model_t *model, int32_t E, float *d_
  * The tree search draws z from the exact marginal P(z | b, a) instead (one
  * inverse CDF over z); both have the same law.  d_B [n][H][pitch],
  * d_action [n], d_path [n], d_z [n][K]; workspace
- * qv_forward_sample_workspace_bytes (the prefix sums). */
+ * qv_forward_sample_workspace_bytes (the prefix sums); d_B and the
+ * workspace 16-byte aligned (QV_ERR_INVALID otherwise). */
 size_t qv_forward_sample_workspace_bytes(const qv_model_t *model, int32_t n);
 qv_status qv_forward_sample(const qv_model_t *model, int32_t n, const float *d_B,
                             const int32_t *d_action, const uint64_t *d_path, int32_t level,

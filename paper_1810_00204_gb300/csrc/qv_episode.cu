@@ -185,37 +185,57 @@ constexpr int kBandCells = 4096;
 
 // Alg. 4 as written, one CTA per (belief, action) and one thread per
 // sample: x ~ b by the inverse CDF over the cells in index order (a
-// block-wide FP32 prefix sum: per-thread chunks, then the chunk totals in
-// thread order), x' = system_move, z = system_measure.  Sample k uses
-// words 3k, 3k + 1, 3k + 2 of the stream of (level, path).
+// block-wide FP32 prefix sum over tiles of 1024 cells: four consecutive
+// cells per thread, warp shuffles, the warps' totals, a carry from tile to
+// tile), x' = system_move, z = system_measure.  Sample k uses words 3k,
+// 3k + 1, 3k + 2 of the stream of (level, path).
 __global__ void __launch_bounds__(kEpThreads) k_forward_sample(EnvArgs m, const float *__restrict__ Bset,
                                                                const int *__restrict__ action,
                                                                const unsigned long long *__restrict__ path,
                                                                int level, uint64_t seed, uint32_t episode, int K,
                                                                float *__restrict__ cdf, int *__restrict__ zout) {
-    __shared__ float s_base[kEpThreads];
-    const int j = blockIdx.x, tid = threadIdx.x;
+    __shared__ float s_warp[kEpThreads / 32];
+    __shared__ float s_carry;
+    const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const float *b = Bset + static_cast<size_t>(j) * m.N;
     float *C = cdf + static_cast<size_t>(j) * m.N;
-    const int chunk = (m.N + kEpThreads - 1) / kEpThreads;
-    const int c0 = min(m.N, tid * chunk), c1 = min(m.N, c0 + chunk);
-    float s = 0.0f;
-    for (int y = c0; y < c1; ++y) s += QV_CELL_FREE(m.cell[y]) ? b[y] : 0.0f;
-    s_base[tid] = s;
+    if (tid == 0) s_carry = 0.0f;
     __syncthreads();
-    if (tid == 0) {
-        float run = 0.0f;
-        for (int t = 0; t < kEpThreads; ++t) {
-            const float v = s_base[t];
-            s_base[t] = run;
-            run = run + v;
+    // m.N is a multiple of 8 (whole rows of pitch), so every group of four
+    // cells is inside the grid and 16-byte aligned
+    for (int base = 0; base < m.N; base += 4 * kEpThreads) {
+        const int i = base + 4 * tid;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (i < m.N) {
+            const float4 bv = *reinterpret_cast<const float4 *>(b + i);
+            const ushort4 cw = *reinterpret_cast<const ushort4 *>(m.cell + i);
+            v[0] = QV_CELL_FREE(cw.x) ? bv.x : 0.0f;
+            v[1] = QV_CELL_FREE(cw.y) ? bv.y : 0.0f;
+            v[2] = QV_CELL_FREE(cw.z) ? bv.z : 0.0f;
+            v[3] = QV_CELL_FREE(cw.w) ? bv.w : 0.0f;
         }
-    }
-    __syncthreads();
-    float run = s_base[tid];
-    for (int y = c0; y < c1; ++y) {
-        run = run + (QV_CELL_FREE(m.cell[y]) ? b[y] : 0.0f);
-        C[y] = run;
+        v[1] += v[0];
+        v[2] += v[1];
+        v[3] += v[2];
+        float incl = v[3];  // inclusive scan of the threads' totals within the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const float t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        float woff = s_carry;
+        for (int w = 0; w < wid; ++w) woff += s_warp[w];
+        const float off = woff + incl - v[3];
+        if (i < m.N)
+            *reinterpret_cast<float4 *>(C + i) = make_float4(off + v[0], off + v[1], off + v[2], off + v[3]);
+        __syncthreads();
+        if (tid == 0) {
+            float t = s_carry;
+            for (int w = 0; w < kEpThreads / 32; ++w) t += s_warp[w];
+            s_carry = t;
+        }
+        __syncthreads();
     }
     __syncthreads();
     const float total = C[m.N - 1];
@@ -255,6 +275,9 @@ extern "C" qv_status qv_forward_sample(const qv_model_t *m, int32_t n, const flo
     if (n == 0 || K == 0) return QV_OK;
     if (ws_bytes < qv_forward_sample_workspace_bytes(m, n))
         return qv_set_error(QV_ERR_WORKSPACE, "qv_forward_sample: workspace too small");
+    if ((reinterpret_cast<uintptr_t>(d_B) | reinterpret_cast<uintptr_t>(d_ws)) & 15 ||
+        reinterpret_cast<uintptr_t>(m->d_cell) & 7)
+        return qv_set_error(QV_ERR_INVALID, "qv_forward_sample: beliefs and workspace must be 16-byte aligned");
     qv::k_forward_sample<<<n, qv::kEpThreads, 0, static_cast<cudaStream_t>(stream)>>>(
         qv::env_args(m), d_B, d_action, reinterpret_cast<const unsigned long long *>(d_path), level, seed, episode, K,
         static_cast<float *>(d_ws), d_z);
