@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuner)")
+    ap.add_argument("--streams", type=int, default=8,
+                    help="streams the step's single-plan launches run on concurrently (each plan then takes "
+                         "1/streams of the co-resident CTAs); 0 = the fastest of 1, 4, 8 and 16 in a short trial")
     ap.add_argument("--gradient-only", action="store_true",
                     help="only time the gradient of the root value on the differentiation workload")
     ap.add_argument("--offline-only", action="store_true",
@@ -772,17 +775,69 @@ def main():
         dflt = [t["ms"] for t in table if t["band_cells"] == 2048 and t["items_per_cta"] == 2]
         tune = {"band_cells": best["band_cells"], "items_per_cta": best["items_per_cta"],
                 "tuned_ms": best["ms"], "default_ms": dflt[0] if dflt else None, "candidates": len(table)}
-    plans = [api.Plan([model], [Qd], [b0s[i]], depth=w.depth, K=w.K, seed=w.seed, episode=e.episode,
-                      leaf_mode=leaf_mode) for i, e in enumerate(eps)]
     use_graph = not args.no_graph
-    if use_graph:
-        for p in plans:
-            p.capture_graph()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    full_grid = api.Plan([model], [Qd], [b0s[0]], depth=w.depth, K=w.K, seed=w.seed, episode=eps[0].episode,
+                         leaf_mode=leaf_mode).grid
+    knobs = {}
+    if tune is not None:
+        knobs = dict(band_cells=tune["band_cells"], items_per_cta=tune["items_per_cta"])
+
+    def make_plans(S):
+        """The step's R single-plan launches, each on 1/S of the co-resident
+        CTAs (with the knobs tuned for the whole grid), spread over S streams."""
+        g = 0 if S == 1 else max(1, full_grid // S)
+        ps = [api.Plan([model], [Qd], [b0s[i]], depth=w.depth, K=w.K, seed=w.seed, episode=e.episode,
+                       leaf_mode=leaf_mode, grid_ctas=g, **knobs) for i, e in enumerate(eps)]
+        if use_graph:
+            for p in ps:
+                p.capture_graph()
+        return ps, [torch.cuda.Stream() for _ in range(S)] if S > 1 else [stream]
+
+    def run_step(ps, ss):
+        if len(ss) == 1:
+            for p in ps:
+                p.run()
+            return
+        for s_ in ss:
+            s_.wait_stream(stream)
+        for i, p in enumerate(ps):
+            p.run(ss[i % len(ss)])
+        for s_ in ss:
+            stream.wait_stream(s_)
+
+    # concurrency: independent plans on several streams overlap on the GPU
+    # (each launch is still one plan); a short trial picks the stream count
+    trial = {}
+    choices = [args.streams] if args.streams > 0 else [1, 4, 8, 16]
+    best_S, best_rate = choices[0], -1.0
+    for S in choices:
+        ps, ss = make_plans(S)
+        for k in range(3):
+            run_step(ps, ss)
+        n_trial = 10 if len(choices) > 1 else 0
+        if n_trial:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms_t = 0.0
+            for k in range(n_trial):
+                flush.fill_(k & 255)
+                e0.record(stream)
+                run_step(ps, ss)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_t += e0.elapsed_time(e1)
+            rate = R * n_trial / (ms_t * 1e-3)
+            trial[S] = rate
+        else:
+            rate = 0.0
+        if rate > best_rate:
+            best_S, best_rate = S, rate
+        del ps, ss
+    plans, streams = make_plans(best_S)
+    grid_ctas = plans[0].grid
 
     def step():
-        for p in plans:
-            p.run()
+        run_step(plans, streams)
 
     # warm-up
     for k in range(max(args.warmup, 0)):
@@ -849,6 +904,9 @@ def main():
                 "kernel_share": 1.0, "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": avg_ms,
                 "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
                 else "fallback 6800 GB/s",
+                "job_achieved_GBps": abytes * plans_per_s / 1e9,
+                "job_note": "the step's algorithmic bytes over its device time, plans overlapping on "
+                            f"{len(streams)} stream(s); achieved/frac are per launch (one plan alone)",
                 "phases": per_phase}
 
     # end to end through the public API with host buffers: pinned b0 -> device,
@@ -867,11 +925,16 @@ def main():
             flush.fill_(k & 255)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            for s_ in streams:
+                s_.wait_stream(stream)
             for i, p in enumerate(plans):
-                b0s[i].copy_(pinned[i], non_blocking=True)
-                p.run()
-                p.read_async(rbufs[i])
-            stream.synchronize()
+                s_ = streams[i % len(streams)]
+                with torch.cuda.stream(s_):
+                    b0s[i].copy_(pinned[i], non_blocking=True)
+                p.run(s_)
+                p.read_async(rbufs[i], s_)
+            for s_ in streams:
+                s_.synchronize()
             got = [p.decode(rbufs[i])[0] for i, p in enumerate(plans)]
             t_e2e += time.perf_counter() - t0
         assert all(g["nodes_per_level"][0] == 1 for g in got)
@@ -924,6 +987,8 @@ def main():
                        "l2": "flushed before every step (256 MiB device write outside the timed events)",
                        "parallelism": "replicas" if world_size > 1 else "single GPU",
                        "autotune": tune,
+                       "streams": best_S, "grid_ctas": grid_ctas, "full_grid": full_grid,
+                       "concurrency_trial_plans_per_s": trial,
                        "nodes_per_level": nodes_per_plan[0]},
             "updates_per_s": updates_per_s,
             "roofline": roofline,

@@ -98,6 +98,10 @@ typedef struct {
                                   autotuner's choice for this shape, else 2048         */
     int32_t items_per_cta;     /* work items aimed at per co-resident CTA in a phase,
                                   0 = the autotuner's choice for this shape, else 2    */
+    int32_t grid_ctas;         /* CTAs of the plan's launch, 0 = every CTA that can be
+                                  co-resident; fewer leave room for plans launched
+                                  concurrently on other streams (a latency-bound plan
+                                  barely slows, the GPU runs several at once)         */
 } qv_plan_params_t;
 
 typedef struct {
@@ -336,8 +340,8 @@ void qv_plan_destroy(qv_plan_t *plan);
  * every candidate pair on the caller's inputs (each a full plan run,
  * `reps` timed runs after two warm-up runs, CUDA events on `stream`), keeps
  * the fastest in a process-wide cache under the inputs' shape class (E,
- * depth, K, leaf and weight modes, largest B, and the power-of-two classes of
- * the widest pitch and the mean cell count) and returns it.  Plans created
+ * depth, K, leaf and weight modes, largest B, the power-of-two classes of
+ * the widest pitch and the mean cell count, and grid_ctas) and returns it.  Plans created
  * later with band_cells = 0 / items_per_cta = 0 and the same shape class
  * take the cached pair.  Candidates whose shared memory does not fit are
  * skipped.  The workspace must hold qv_plan_autotune_workspace_bytes.
@@ -357,6 +361,8 @@ qv_status qv_plan_autotune(int32_t E, const qv_model_t *models, const float *con
                            qv_stream_t stream);
 /* The knobs a plan was created with. */
 qv_status qv_plan_tuning(const qv_plan_t *plan, qv_tune_t *h_out);
+/* CTAs of the plan's launch (grid_ctas, or every co-resident CTA). */
+int32_t qv_plan_grid(const qv_plan_t *plan);
 /* Forget every cached choice. */
 void qv_tune_clear(void);
 

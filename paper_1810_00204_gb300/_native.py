@@ -36,7 +36,7 @@ class qv_model_t(C.Structure):
 class qv_plan_params_t(C.Structure):
     _fields_ = [("depth", C.c_int32), ("K", C.c_int32), ("seed", C.c_uint64), ("episode", C.c_uint32),
                 ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p),
-                ("band_cells", C.c_int32), ("items_per_cta", C.c_int32)]
+                ("band_cells", C.c_int32), ("items_per_cta", C.c_int32), ("grid_ctas", C.c_int32)]
 
 
 class qv_tune_t(C.Structure):
@@ -134,6 +134,7 @@ SIGNATURES = {
     "qv_belief_update_batched": (C.c_int, [_M, _i32, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
     "qv_forward_sample_workspace_bytes": (_sz, [_M, _i32]),
     "qv_forward_sample": (C.c_int, [_M, _i32, _vp, _vp, _vp, _i32, C.c_uint64, C.c_uint32, _i32, _vp, _vp, _sz, _vp]),
+    "qv_plan_grid": (_i32, [_vp]),
     "qv_plan_level": (C.c_int, [_vp, _i32, _i32, C.POINTER(qv_level_view_t)]),
     "qv_plan_autotune_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_autotune": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, _i32, C.POINTER(qv_tune_t),

@@ -444,9 +444,10 @@ def leaf_value(model: Model, Q: torch.Tensor, b: torch.Tensor, stream=None):
     return out
 
 
-def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells=0, items_per_cta=0):
+def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells=0, items_per_cta=0, grid_ctas=0):
     return N.qv_plan_params_t(int(depth), int(K), int(seed), int(episode), int(weight_mode), int(leaf_mode),
-                              None if replay is None else replay.data_ptr(), int(band_cells), int(items_per_cta))
+                              None if replay is None else replay.data_ptr(), int(band_cells), int(items_per_cta),
+                              int(grid_ctas))
 
 
 def _result_dict(r: N.qv_plan_result_t, depth: int):
@@ -465,14 +466,15 @@ class Plan:
 
     def __init__(self, models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor],
                  depth=2, K=4, seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED,
-                 replay: Optional[torch.Tensor] = None, stream=None, band_cells=0, items_per_cta=0):
+                 replay: Optional[torch.Tensor] = None, stream=None, band_cells=0, items_per_cta=0, grid_ctas=0):
         self.models = list(models)
         self.E = len(self.models)
         self.depth, self.K = int(depth), int(K)
         self.Qs = [q.contiguous() for q in Qs]
         self.b0s = [b.contiguous() for b in b0s]
         self.replay = replay
-        self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells, items_per_cta)
+        self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells, items_per_cta,
+                              grid_ctas)
         self.mstructs = (N.qv_model_t * self.E)(*[m.struct for m in self.models])
         self.qptrs = (C.c_void_p * self.E)(*[q.data_ptr() for q in self.Qs])
         self.bptrs = (C.c_void_p * self.E)(*[b.data_ptr() for b in self.b0s])
@@ -487,6 +489,11 @@ class Plan:
     @property
     def workspace_bytes(self):
         return self.ws.numel()
+
+    @property
+    def grid(self) -> int:
+        """CTAs of the plan's launch."""
+        return int(lib().qv_plan_grid(self.handle))
 
     @property
     def tuning(self) -> dict:
@@ -618,7 +625,8 @@ class Plan:
 
 
 def autotune(models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor], depth=2, K=4,
-             seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED, reps=5, stream=None):
+             seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED, reps=5, grid_ctas=0,
+             stream=None):
     """qv_plan_autotune: time every (band_cells, items_per_cta) candidate on
     these inputs; the best is cached in the library for plans of the same
     shape class created with the knobs left at 0.  Returns (best, all)."""
@@ -626,7 +634,7 @@ def autotune(models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[
     ms = (N.qv_model_t * E)(*[m.struct for m in models])
     qp = (C.c_void_p * E)(*[q.data_ptr() for q in Qs])
     bp = (C.c_void_p * E)(*[b.data_ptr() for b in b0s])
-    params = _params(depth, K, seed, episode, weight_mode, leaf_mode, None)
+    params = _params(depth, K, seed, episode, weight_mode, leaf_mode, None, grid_ctas=grid_ctas)
     nbytes = lib().qv_plan_autotune_workspace_bytes(E, ms, C.byref(params))
     if nbytes == 0:
         raise N.QVError(N.QV_ERR_INVALID, "qv_plan_autotune_workspace_bytes")

@@ -39,7 +39,7 @@ constexpr int kDefaultBandCells = 2048;
 constexpr int kDefaultItemsPerCta = 2;
 constexpr int kMaxItemsPerCta = 8;
 
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int>;
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, qv_tune_t> g_tune;
 
@@ -53,7 +53,8 @@ TuneKey tune_key(int E, const qv_model_t *models, const qv_plan_params_t *p) {
         Pmax = std::max(Pmax, models[e].pitch);
         cells += static_cast<double>(models[e].H) * models[e].pitch;
     }
-    return TuneKey(E, p->depth, p->K, p->leaf_mode, p->weight_mode, Bmax, log2_class(Pmax), log2_class(cells / E));
+    return TuneKey(E, p->depth, p->K, p->leaf_mode, p->weight_mode, Bmax, log2_class(Pmax), log2_class(cells / E),
+                   p->grid_ctas);
 }
 
 // The knobs a plan uses: explicit values, else the cached choice for its
@@ -170,6 +171,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     if (L.smem > 200 * 1024) return qv_set_error(QV_ERR_INVALID, "plan: %zu bytes of shared memory", L.smem);
     L.grid = need_grid ? plan_grid(L.smem) : 0;
     if (need_grid && L.grid < 1) return qv_set_error(QV_ERR_CUDA, "plan: k_plan does not fit an SM");
+    if (p->grid_ctas < 0) return qv_set_error(QV_ERR_INVALID, "plan: grid_ctas %d", p->grid_ctas);
+    if (need_grid && p->grid_ctas > 0) L.grid = std::min(L.grid, p->grid_ctas);
     // work items per phase aimed at: two per co-resident CTA.  Band splits
     // keep every phase below 2 * target items, and the partial records are
     // sized for the largest possible grid so that sizing needs no device.
@@ -647,6 +650,8 @@ extern "C" qv_status qv_tree_plan(const qv_model_t *model, const float *d_Q, con
                                   qv_plan_result_t *h_result, qv_stream_t stream) {
     return qv_tree_plan_batched(1, model, &d_Q, &d_b0, params, d_ws, ws_bytes, h_result, stream);
 }
+
+extern "C" int32_t qv_plan_grid(const qv_plan_t *pl) { return pl ? pl->grid : 0; }
 
 extern "C" qv_status qv_plan_tuning(const qv_plan_t *pl, qv_tune_t *out) {
     if (!pl || !out) return qv_set_error(QV_ERR_INVALID, "qv_plan_tuning: null pointer");
