@@ -219,6 +219,8 @@ qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
  * which the later calls take from qv_pbvi_set_points.
  * qv_pbvi_set_points: the belief set (1..max_points points, d_B is read
  * during this call only): its five predicted beliefs per point and R(b, a).
+ * The score contraction of Eq. 8 and of V_PBVI runs on the tensor cores
+ * (tcgen05, TF32 operands split into head and tail, FP32 accumulation).
  * qv_pbvi_backup: one Eq. 8 backup of every point of the set given nG
  * vectors d_G (nG <= max_points); writes one new vector per point to d_Gout
  * (must not overlap d_G), and, where not NULL, the backed-up value at the
@@ -250,6 +252,9 @@ qv_status qv_pbvi_backup(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, float *d
                          qv_stream_t stream);
 qv_status qv_pbvi_value(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, const float *d_b,
                         int32_t nb, float *d_value, int32_t *d_arg, qv_stream_t stream);
+/* qv_pbvi_check: synchronises; QV_ERR_TIMEOUT (once) if a bounded wait of
+ * the tensor-core contraction gave up since the last check, else QV_OK. */
+qv_status qv_pbvi_check(qv_pbvi_t *pbvi, qv_stream_t stream);
 void qv_pbvi_destroy(qv_pbvi_t *pbvi);
 
 /* ---------------------------------------------------------------- belief update (Eq. 3)

@@ -805,12 +805,26 @@ int or_pbvi_expand(const or_problem *p, const double *B, int nB, int round, uint
     return 0;
 }
 
+/* Eq. 8's argmaxes meet exact ties (at the pessimistic start every action
+ * of a point far from the goal is worth R_min / (1 - gamma)), which FP32 and
+ * FP64 sums would break differently; so candidates within 1e-5 * max(1, |best|)
+ * of the best count as tied and the lowest index among them is taken.     */
+static int pbvi_pick(const double *v, int n) {
+    double best = v[0];
+    for (int i = 1; i < n; ++i)
+        if (v[i] > best) best = v[i];
+    const double tol = 1e-5 * (fabs(best) > 1.0 ? fabs(best) : 1.0);
+    for (int i = 0; i < n; ++i)
+        if (v[i] >= best - tol) return i;
+    return 0;
+}
+
 /* One PBVI alpha-vector backup, Eq. 8, at every point b of B given the set
  * Gamma (nG vectors of n values):
  *   for each action a and observation z, the vector of Gamma maximising
- *     sum_x sum_x' O(x', z) T(x, a, x') alpha(x') b(x)          (ties: lowest index),
- *   Q_b(a) = R(b, a) + gamma sum_z (that maximum),
- *   a*(b) = argmax_a Q_b(a)                                      (ties: lowest a),
+ *     sum_x sum_x' O(x', z) T(x, a, x') alpha(x') b(x)          (ties: pbvi_pick),
+ *   Q_b(a) = R(b, a) + gamma sum_z (that vector's sum),
+ *   a*(b) = argmax_a Q_b(a)                                      (ties: pbvi_pick),
  * and the new vector of b is
  *   alpha_b(x) = R(x, a*) + gamma sum_z sum_x' O(x', z) T(x, a*, x') alpha_{i*(z)}(x')
  * on free, non-goal x, 0 on the goal and occupied cells (their value is 0
@@ -828,13 +842,12 @@ int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G
     for (int j = 0; j < nB; ++j) {
         const double *b = B + (size_t)j * n;
         int *bi = (int *)malloc(sizeof(int) * A * nz);
+        double *sc = (double *)malloc(sizeof(double) * (nG > 0 ? nG : 1));
         double qa[OR_NUM_ACTIONS];
         for (int a = 0; a < A; ++a) {
             double qv = 0.0;
             for (int x = 0; x < n; ++x) qv += R[a * n + x] * b[x];   /* R(b, a) */
             for (int z = 0; z < nz; ++z) {
-                double mx = -HUGE_VAL;
-                int arg = 0;
                 for (int i = 0; i < nG; ++i) {
                     const double *al = G + (size_t)i * n;
                     double s = 0.0;
@@ -846,17 +859,16 @@ int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G
                             s += or_obs_lik(p, label, y[t], z) * pr[t] * al[y[t]] * b[x];
                     }
                     if (score) score[(((size_t)j * A + a) * nz + z) * nG + i] = s;
-                    if (s > mx) { mx = s; arg = i; }
+                    sc[i] = s;
                 }
+                const int arg = pbvi_pick(sc, nG);
                 bi[a * nz + z] = arg;
-                qv += p->gamma * mx;
+                qv += p->gamma * sc[arg];
             }
             qa[a] = qv;
             if (q) q[(size_t)j * A + a] = qv;
         }
-        int as = 0;
-        for (int a = 1; a < A; ++a)
-            if (qa[a] > qa[as]) as = a;
+        const int as = pbvi_pick(qa, A);
         astar[j] = as;
         value[j] = qa[as];
         for (int z = 0; z < nz; ++z) best[(size_t)j * nz + z] = bi[as * nz + z];
@@ -872,7 +884,7 @@ int or_pbvi_backup(const or_problem *p, const double *B, int nB, const double *G
             }
             out[x] = R[as * n + x] + p->gamma * s;
         }
-        free(bi);
+        free(bi); free(sc);
     }
     free(label); free(R);
     return 0;

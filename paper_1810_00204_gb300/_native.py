@@ -99,6 +99,7 @@ SIGNATURES = {
     "qv_pbvi_set_points": (C.c_int, [_vp, _vp, _i32, _vp, _sz, _vp]),
     "qv_pbvi_backup": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "qv_pbvi_value": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "qv_pbvi_check": (C.c_int, [_vp, _vp]),
     "qv_pbvi_destroy": (None, [_vp]),
     "mdp_value_iterate_checkpointed": (C.c_int, [_M, _i32, _i32, _vp, _vp, _vp, _vp, _sz, _vp]),
     "mdp_value_backward_workspace_bytes": (_sz, [_M, _i32]),

@@ -39,7 +39,8 @@ namespace qv {
 namespace {
 
 constexpr int kPbThreads = 256;
-constexpr int kKC = 16;          // K depth of one contraction stage; label runs are padded to it
+constexpr int kKC = 32;          // K depth of one contraction stage (one 128-byte row of FP32);
+                                 // label runs are padded to it
 constexpr int kTM = 128, kTN = 128;
 constexpr int kPiecesExtra = 64; // pieces beyond one per label
 
@@ -91,6 +92,15 @@ __device__ __forceinline__ int pb_successors(const PbModel &m, int x, unsigned c
         p[i] = w[i];
     }
     return 3;
+}
+
+// x = hi + lo with hi = x rounded to TF32 (round to nearest, ties away) and
+// lo the exact FP32 remainder.
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    hi = __uint_as_float(h);
+    lo = x - hi;
 }
 
 // ---------------------------------------------------------------- expansion
@@ -280,108 +290,214 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restr
 }
 
 // ---------------------------------------------------------------- the contraction
-// slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k]; grid (M tiles, N
-// tiles, pieces); both operands are K-contiguous rows of Kp floats.  A CTA
-// computes a 128 x 128 tile, each thread an 8 x 8 block (rows ty*4 + i and
-// 64 + ty*4 + i, columns likewise), from 16-deep stages held k-major in
-// shared memory.  The next stage's global loads are issued into registers
-// before the current stage's arithmetic and stored to the other buffer after
-// it (one barrier per stage).  A warp loads 32 consecutive rows of one
-// 4-wide k group, so its transposing stores hit 32 consecutive words.
-__global__ void __launch_bounds__(kPbThreads, 2) k_pbvi_scores(const float *__restrict__ A,
-                                                               const float *__restrict__ Bm, int M, int N, int Kp,
-                                                               const int *__restrict__ piece,
-                                                               float *__restrict__ slab) {
-    __shared__ __align__(16) float As[2][kKC][kTM + 4];
-    __shared__ __align__(16) float Bs[2][kKC][kTN + 4];
+// slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k] on the 5th-generation
+// tensor cores: grid (M tiles, N tiles, pieces), one CTA of four warps per
+// 128 x 128 tile, the accumulator in tensor memory (128 lanes x 128 FP32
+// columns).  TF32 keeps 10 mantissa bits, too few for the argmax decisions
+// of Eq. 8, so every operand is split into a TF32 head and a TF32 tail
+// (x = hi + lo, hi = x rounded to TF32) and each product is formed as
+// hi.hi + hi.lo + lo.hi, which restores FP32-level accuracy (the dropped
+// lo.lo term is below 2^-22 of the product).  Stages of 32 values of K (one
+// 128-byte row) are staged K-major with the 128-byte swizzle, double
+// buffered: the threads load and split stage s + 1 while the tensor core
+// multiplies stage s (one thread issues the twelve MMAs of a stage, K = 8
+// each, and commits them to the stage buffer's mbarrier).  Every wait is
+// bounded; a wait that gives up sets *status, lets the work in flight land
+// and still frees the tensor memory.
+constexpr int kTcThreads = 128;
+constexpr int kTcStageFloats = 4 * kTM * kKC;  // A hi, A lo, B hi, B lo
+constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float) + 1024;
+
+__device__ __forceinline__ uint32_t tc_smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory descriptor of a K-major tile with the 128-byte swizzle:
+// start address, stride of 1024 bytes between groups of 8 rows, descriptor
+// version 1, layout code 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFF) | (static_cast<uint64_t>(1024 >> 4) << 32) |
+           (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(tc_smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
+                                                               int M, int N, int Kp, const int *__restrict__ piece,
+                                                               float *__restrict__ slab, int *__restrict__ status) {
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_tmem;
+    float *st = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
     const int p = blockIdx.z;
     const int k0 = __ldg(piece + 3 * p), k1 = __ldg(piece + 3 * p + 1);
     const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    // loader: float4 number t = tid + 256 h covers row (t & 31) + 32 (t >> 7)
-    // of the tile and k group (t >> 5) & 3, i.e. rows lrow and lrow + 64 of
-    // one k group
-    const int lrow = (tid & 31) + 32 * (tid >> 7), lk = ((tid >> 5) & 3) * 4;
-    const bool aok0 = m0 + lrow < M, aok1 = m0 + lrow + 64 < M;
-    const bool bok0 = n0 + lrow < N, bok1 = n0 + lrow + 64 < N;
-    const float *ap = A + static_cast<size_t>(aok0 ? m0 + lrow : 0) * Kp + lk;
-    const float *bp = Bm + static_cast<size_t>(bok0 ? n0 + lrow : 0) * Kp + lk;
-    const size_t far = static_cast<size_t>(64) * Kp;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 ra0, ra1, rb0, rb1;
-    auto load = [&](int k) {
-        ra0 = aok0 ? __ldg(reinterpret_cast<const float4 *>(ap + k)) : zero4;
-        ra1 = aok1 ? __ldg(reinterpret_cast<const float4 *>(ap + far + k)) : zero4;
-        rb0 = bok0 ? __ldg(reinterpret_cast<const float4 *>(bp + k)) : zero4;
-        rb1 = bok1 ? __ldg(reinterpret_cast<const float4 *>(bp + far + k)) : zero4;
-    };
-    auto store = [&](int buf) {
-        As[buf][lk + 0][lrow] = ra0.x;
-        As[buf][lk + 1][lrow] = ra0.y;
-        As[buf][lk + 2][lrow] = ra0.z;
-        As[buf][lk + 3][lrow] = ra0.w;
-        As[buf][lk + 0][lrow + 64] = ra1.x;
-        As[buf][lk + 1][lrow + 64] = ra1.y;
-        As[buf][lk + 2][lrow + 64] = ra1.z;
-        As[buf][lk + 3][lrow + 64] = ra1.w;
-        Bs[buf][lk + 0][lrow] = rb0.x;
-        Bs[buf][lk + 1][lrow] = rb0.y;
-        Bs[buf][lk + 2][lrow] = rb0.z;
-        Bs[buf][lk + 3][lrow] = rb0.w;
-        Bs[buf][lk + 0][lrow + 64] = rb1.x;
-        Bs[buf][lk + 1][lrow + 64] = rb1.y;
-        Bs[buf][lk + 2][lrow + 64] = rb1.z;
-        Bs[buf][lk + 3][lrow + 64] = rb1.w;
-    };
-    float acc[8][8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    int buf = 0;
-    if (k0 < k1) {
-        load(k0);
-        store(0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&bar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&bar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc_smem_u32(&s_tmem)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    for (int k = k0; k < k1; k += kKC) {
-        const bool more = k + kKC < k1;
-        if (more) load(k + kKC);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    // thread t stages row t of the A tile and row t of the B tile: 32 values
+    // each, split, swizzled (16-byte chunk c of row r lands at chunk c ^ (r & 7));
+    // the next stage's global loads are issued into registers before the
+    // current stage's MMAs, so their latency overlaps the tensor core's work
+    const bool a_ok = m0 + tid < M, b_ok = n0 + tid < N;
+    const float *arow = A + static_cast<size_t>(a_ok ? m0 + tid : 0) * Kp;
+    const float *brow = Bm + static_cast<size_t>(b_ok ? n0 + tid : 0) * Kp;
+    float4 ra[kKC / 4], rb[kKC / 4];
+    auto fetch = [&](int k) {
 #pragma unroll
-        for (int kk = 0; kk < kKC; ++kk) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
-            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
-            const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float br[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(ar[i], br[j], acc[i][j]);
+        for (int c = 0; c < kKC / 4; ++c) {
+            ra[c] = a_ok ? __ldg(reinterpret_cast<const float4 *>(arow + k) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            rb[c] = b_ok ? __ldg(reinterpret_cast<const float4 *>(brow + k) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (more) store(buf ^ 1);  // the other buffer: last read before the previous barrier
+    };
+    auto stage_in = [&](int buf) {
+        float *sa_hi = st + buf * kTcStageFloats, *sa_lo = sa_hi + kTM * kKC;
+        float *sb_hi = sa_lo + kTM * kKC, *sb_lo = sb_hi + kTN * kKC;
+#pragma unroll
+        for (int c = 0; c < kKC / 4; ++c) {
+            const int o = tid * kKC + ((c ^ (tid & 7)) << 2);
+            float4 ah, al, bh, bl;
+            tf32_split(ra[c].x, ah.x, al.x);
+            tf32_split(ra[c].y, ah.y, al.y);
+            tf32_split(ra[c].z, ah.z, al.z);
+            tf32_split(ra[c].w, ah.w, al.w);
+            tf32_split(rb[c].x, bh.x, bl.x);
+            tf32_split(rb[c].y, bh.y, bl.y);
+            tf32_split(rb[c].z, bh.z, bl.z);
+            tf32_split(rb[c].w, bh.w, bl.w);
+            *reinterpret_cast<float4 *>(sa_hi + o) = ah;
+            *reinterpret_cast<float4 *>(sa_lo + o) = al;
+            *reinterpret_cast<float4 *>(sb_hi + o) = bh;
+            *reinterpret_cast<float4 *>(sb_lo + o) = bl;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
+    };
+    // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 128, M = 128
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
+    uint32_t phase[2] = {0u, 0u};
+    const int nst = (k1 - k0) / kKC;
+    bool ok = true;
+    if (nst > 0) fetch(k0);
+    for (int s = 0; s < nst; ++s) {
+        const int buf = s & 1;
+        if (s >= 2) {  // the MMAs of stage s - 2 read this buffer
+            const bool w = tc_wait(&bar[buf], phase[buf]);
+            phase[buf] ^= 1u;
+            if (__syncthreads_or(w ? 0 : 1)) {
+                ok = false;
+                break;
+            }
+        }
+        stage_in(buf);
+        if (s + 1 < nst) fetch(k0 + (s + 1) * kKC);
+        asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        buf ^= 1;
-    }
-    float *out = slab + static_cast<size_t>(p) * M * N;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            float *sa_hi = st + buf * kTcStageFloats, *sa_lo = sa_hi + kTM * kKC;
+            float *sb_hi = sa_lo + kTM * kKC, *sb_lo = sb_hi + kTN * kKC;
+            const uint64_t ah = tc_desc(tc_smem_u32(sa_hi)), al = tc_desc(tc_smem_u32(sa_lo));
+            const uint64_t bh = tc_desc(tc_smem_u32(sb_hi)), bl = tc_desc(tc_smem_u32(sb_lo));
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int mm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
-        if (mm >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int nn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-            if (nn < N) out[static_cast<size_t>(mm) * N + nn] = acc[i][j];
+            for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
+                const uint64_t o = 2ull * kk;
+                const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ah + o), "l"(bh + o), "r"(idesc), "r"(first));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(ah + o),
+                             "l"(bl + o), "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(al + o),
+                             "l"(bh + o), "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tc_smem_u32(&bar[buf])));
         }
     }
+    // the last commit covers every MMA issued before it
+    if (nst > 0) {
+        const int lb = (nst - 1) & 1;
+        const bool w = ok ? tc_wait(&bar[lb], phase[lb]) : false;
+        if (__syncthreads_or(w ? 0 : 1)) {
+            ok = false;
+            if (tid == 0) atomicOr(status, 1);
+            tc_wait(&bar[lb], phase[lb]);  // let the work in flight land before the memory is freed
+        }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        float *out = slab + static_cast<size_t>(p) * M * N;
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < kTN; c0 += 16) {
+            uint32_t r[16];
+            if (nst > 0) {
+                const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) r[j] = 0u;
+            }
+            if (row < M) {
+                float *dst = out + static_cast<size_t>(row) * N + n0 + c0;
+                if (n0 + c0 + 16 <= N && (N & 3) == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
 }
 
 // ---------------------------------------------------------------- selection
+// Eq. 8's argmaxes meet exact ties (at the pessimistic start every action of
+// a point far from the goal is worth R_min / (1 - gamma)) that rounding
+// would break at random; candidates within 1e-5 * max(1, |best|) of the best
+// count as tied and the lowest index among them is taken.
+__device__ __forceinline__ float tie_tol(float best) { return 1e-5f * fmaxf(1.0f, fabsf(best)); }
+
 // One CTA per point b.  For each action: D(i) = the sum of every slab row
 // (pieces in order), then one warp per observation z takes
-// argmax_i eta D(i) + (accuracy - eta) D_z(i) (ties to the lowest i).  Then
-// a* and the distinct winners of a* with their multiplicities.
+// argmax_i eta D(i) + (accuracy - eta) D_z(i) (ties as above).  Then a* and
+// the distinct winners of a* with their multiplicities.
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_select(PbModel m, int nB, int nG, int npieces,
                                                             const int *__restrict__ piece,
                                                             const float *__restrict__ slab,
@@ -416,28 +532,38 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_select(PbModel m, int nB, i
         __syncthreads();
         for (int z = wid; z < m.nz; z += kPbThreads / 32) {
             const int p0 = s_first[z], p1 = s_first[z + 1];
-            float bv = -INFINITY;
-            int bi = 0x7fffffff;
-            for (int i = lane; i < nG; i += 32) {
+            auto score = [&](int i) {
                 float dz = 0.0f;
                 for (int p = p0; p < p1; ++p) dz += __ldg(slab + p * slab_elems + row + i);
-                const float s = fmaf(m.acc - m.eta, dz, m.eta * D[i]);
-                if (s > bv) {  // i ascends within a lane: strict > keeps the lowest index
-                    bv = s;
+                return fmaf(m.acc - m.eta, dz, m.eta * D[i]);
+            };
+            // the best score, then the lowest index within the tie tolerance of it
+            float bv = -INFINITY;
+            for (int i = lane; i < nG; i += 32) bv = fmaxf(bv, score(i));
+            for (int o = 16; o > 0; o >>= 1) bv = fmaxf(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+            const float floor_v = bv - tie_tol(bv);
+            int bi = 0x7fffffff;
+            float bs = 0.0f;
+            for (int i = lane; i < nG; i += 32) {
+                const float sv = score(i);
+                if (sv >= floor_v) {
                     bi = i;
+                    bs = sv;
+                    break;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov > bv || (ov == bv && oi < bi)) {
-                    bv = ov;
+                const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+                if (oi < bi) {
                     bi = oi;
+                    bs = os;
                 }
             }
             if (lane == 0) {
-                s_val[z] = bv;
-                s_arg[a][z] = bi < nG ? bi : 0;  // no candidate compared above -inf (NaN input)
+                const bool found = bi < nG;  // (none when every score is NaN)
+                s_val[z] = found ? bs : bv;
+                s_arg[a][z] = found ? bi : 0;
             }
         }
         __syncthreads();
@@ -449,9 +575,10 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_select(PbModel m, int nB, i
     }
     __syncthreads();
     if (tid == 0) {
+        float qmax = s_q[0];
+        for (int a = 1; a < 5; ++a) qmax = fmaxf(qmax, s_q[a]);
         int as = 0;
-        for (int a = 1; a < 5; ++a)
-            if (s_q[a] > s_q[as]) as = a;
+        while (as < 4 && !(s_q[as] >= qmax - tie_tol(qmax))) ++as;
         astar[b] = as;
         value[b] = s_q[as];
         if (q)
@@ -579,6 +706,13 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int 
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The contraction kernel's shared memory exceeds the 48 KB default.
+qv_status tc_prepare() {
+    return qv_check_cuda(cudaFuncSetAttribute(k_pbvi_scores, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(kTcSmem)),
+                         "smem attr");
+}
+
 }  // namespace
 }  // namespace qv
 
@@ -592,7 +726,7 @@ struct qv_pbvi {
     std::vector<int> seg;        // nz + 1: label z occupies [seg[z], seg[z + 1])
     std::vector<int> pieces;     // last uploaded piece table (k0, k1, label) triples
     size_t off_pos, off_perm, off_piece, off_Bp, off_RB, off_rpart, off_Gp, off_Ap, off_slab;
-    size_t off_best, off_uniq, off_mult, off_nuniq, off_astar, off_val;
+    size_t off_best, off_uniq, off_mult, off_nuniq, off_astar, off_val, off_status;
     size_t ws_bytes;
     void *ws;                    // workspace the tables live in (set by qv_pbvi_set_points)
     int nB;                      // points of the current set
@@ -696,6 +830,7 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
     h->off_nuniq = take(P * sizeof(int));
     h->off_astar = take(P * sizeof(int));
     h->off_val = take(P * sizeof(float));
+    h->off_status = take(sizeof(int));
     h->ws_bytes = off;
     h->ws = nullptr;
     h->nB = 0;
@@ -705,6 +840,22 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
 }
 
 extern "C" void qv_pbvi_destroy(qv_pbvi *h) { delete h; }
+
+extern "C" qv_status qv_pbvi_check(qv_pbvi *h, qv_stream_t stream) {
+    if (!h) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_check: null pointer");
+    if (!h->ws) return QV_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int flag = 0;
+    char *ws = static_cast<char *>(h->ws);
+    if (qv_check_cuda(cudaMemcpyAsync(&flag, ws + h->off_status, sizeof(int), cudaMemcpyDeviceToHost, st), "copy") !=
+            QV_OK ||
+        qv_check_cuda(cudaStreamSynchronize(st), "qv_pbvi_check") != QV_OK)
+        return QV_ERR_CUDA;
+    if (!flag) return QV_OK;
+    if (qv_check_cuda(cudaMemsetAsync(ws + h->off_status, 0, sizeof(int), st), "status reset") != QV_OK)
+        return QV_ERR_CUDA;
+    return qv_set_error(QV_ERR_TIMEOUT, "qv_pbvi: a tensor-core wait gave up");
+}
 
 extern "C" size_t qv_pbvi_workspace_bytes(const qv_pbvi *h) { return h ? h->ws_bytes : 0; }
 
@@ -756,6 +907,8 @@ extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB
     if (h->ws != d_ws) {
         h->ws = d_ws;
         h->pieces.clear();
+        if (qv_check_cuda(cudaMemsetAsync(ws + h->off_status, 0, sizeof(int), st), "status reset") != QV_OK)
+            return QV_ERR_CUDA;
         if (qv_check_cuda(cudaMemcpyAsync(ws + h->off_pos, h->pos.data(), h->pos.size() * sizeof(int),
                                           cudaMemcpyHostToDevice, st), "pos table") != QV_OK ||
             qv_check_cuda(cudaMemcpyAsync(ws + h->off_perm, h->perm.data(), h->perm.size() * sizeof(int),
@@ -802,8 +955,10 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     h->gp_value_nG = 0;
     qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
                                                     reinterpret_cast<const int *>(ws + h->off_perm), Kp, Gp);
-    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
-        reinterpret_cast<const float *>(ws + h->off_Bp), Gp, M, nG, Kp, piece, slab);
+    if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
+    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
+        reinterpret_cast<const float *>(ws + h->off_Bp), Gp, M, nG, Kp, piece, slab,
+        reinterpret_cast<int *>(ws + h->off_status));
     const qv::PbModel pm = qv::pb_model(&h->model);
     int *best = d_best ? d_best : reinterpret_cast<int *>(ws + h->off_best);
     int *astar = d_astar ? d_astar : reinterpret_cast<int *>(ws + h->off_astar);
@@ -861,8 +1016,10 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
         if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
         const int npieces = static_cast<int>(pc.size() / 3);
         qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, Kp, Ap);
-        qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kPbThreads, 0, st>>>(
-            Ap, Gp, nc, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab);
+        if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
+        qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
+            Ap, Gp, nc, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab,
+            reinterpret_cast<int *>(ws + h->off_status));
         qv::k_pbvi_rowmax<<<nc, qv::kPbThreads, 0, st>>>(nc, nG, npieces, slab, d_value + c0,
                                                          d_arg ? d_arg + c0 : nullptr);
     }
