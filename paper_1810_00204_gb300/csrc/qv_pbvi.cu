@@ -298,15 +298,17 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restr
 // (x = hi + lo, hi = x rounded to TF32) and each product is formed as
 // hi.hi + hi.lo + lo.hi, which restores FP32-level accuracy (the dropped
 // lo.lo term is below 2^-22 of the product).  Stages of 32 values of K (one
-// 128-byte row) are staged K-major with the 128-byte swizzle, double
-// buffered: the threads load and split stage s + 1 while the tensor core
-// multiplies stage s (one thread issues the twelve MMAs of a stage, K = 8
-// each, and commits them to the stage buffer's mbarrier).  Every wait is
+// 128-byte row) are staged K-major with the 128-byte swizzle in one buffer
+// of 64 KB, so three CTAs share an SM: the threads fetch stage s + 1 into
+// registers while the tensor core multiplies stage s, then wait for it and
+// store their split values (one thread issues the twelve MMAs of a stage,
+// K = 8 each, and commits them to the buffer's mbarrier).  Every wait is
 // bounded; a wait that gives up sets *status, lets the work in flight land
 // and still frees the tensor memory.
 constexpr int kTcThreads = 128;
 constexpr int kTcStageFloats = 4 * kTM * kKC;  // A hi, A lo, B hi, B lo
-constexpr size_t kTcSmem = 2 * kTcStageFloats * sizeof(float) + 1024;
+constexpr int kTcBuffers = 1;  // one stage buffer per CTA: three CTAs share an SM's tensor core
+constexpr size_t kTcSmem = kTcBuffers * kTcStageFloats * sizeof(float) + 1024;
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -333,7 +335,7 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
+__global__ void __launch_bounds__(kTcThreads, 3) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
                                                                int M, int N, int Kp, const int *__restrict__ piece,
                                                                float *__restrict__ slab, int *__restrict__ status) {
     extern __shared__ unsigned char tc_raw[];
@@ -401,8 +403,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
     bool ok = true;
     if (nst > 0) fetch(k0);
     for (int s = 0; s < nst; ++s) {
-        const int buf = s & 1;
-        if (s >= 2) {  // the MMAs of stage s - 2 read this buffer
+        const int buf = s % kTcBuffers;
+        if (s >= kTcBuffers) {  // the MMAs of stage s - kTcBuffers read this buffer
             const bool w = tc_wait(&bar[buf], phase[buf]);
             phase[buf] ^= 1u;
             if (__syncthreads_or(w ? 0 : 1)) {
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
     }
     // the last commit covers every MMA issued before it
     if (nst > 0) {
-        const int lb = (nst - 1) & 1;
+        const int lb = (nst - 1) % kTcBuffers;
         const bool w = ok ? tc_wait(&bar[lb], phase[lb]) : false;
         if (__syncthreads_or(w ? 0 : 1)) {
             ok = false;
