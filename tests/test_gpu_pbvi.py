@@ -145,7 +145,7 @@ def test_backup_matches_oracle(api, make, nB, nG):
 
 
 def test_backup_many_tiles_and_pieces(api):
-    # 330 rows (6 tiles of 64) by 65 vectors (2 tiles), 17 labels, sparse
+    # 330 rows (3 tiles of 128) by 65 vectors (one tile), 17 labels, sparse
     # beliefs so the oracle's literal sums stay short
     w = WL.mid(2, H=67, W=45)
     _backup_case(api, w, 66, 65, 4, support=40)
