@@ -36,9 +36,10 @@ L2_FLUSH_BYTES = 256 << 20
 # iteration reads and writes five alpha planes and reads the cell word
 VI_BYTES_PER_CELL = 4 + 4 + 2
 FIB_BYTES_PER_CELL = 5 * 4 + 5 * 4 + 2
-# FP32 pipe peak of the GPU for the PBVI contraction (CUDA cores, FMA = 2
-# flops): 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# nominal dense TF32 / BF16 tensor rates (1.1 and 2.25 PFLOP/s): the PBVI
+# contraction runs as TF32 MMAs, so its peak is the measured BF16 one
+# scaled by this ratio
+TF32_PER_BF16 = 1.1 / 2.25
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -144,11 +145,16 @@ def pbvi_measurement(args, dev, K, flush, stream, with_cpu=True):
         Kp, _ = pb.layout()
         flops = 2.0 * 5 * nB * nG * Kp
         tfl = flops / (ms * 1e-3) / 1e12
+        bf16, src = measured_peak("bf16_tflops")
+        tf32 = bf16 * TF32_PER_BF16
         line = {"points": nB, "vectors": nG, "backup_ms": ms, "point_backups_per_s": nB / (ms * 1e-3),
                 "solve_ms": solve_ms, "solve_schedule": f"{rounds} expansion rounds, 4 backups after each",
                 "contraction": {"flops_per_backup": flops, "label_ordered_cells": Kp,
-                                "achieved_tflops_whole_backup": tfl, "fp32_alu_peak_tflops": FP32_ALU_PEAK_TFLOPS,
-                                "frac": tfl / FP32_ALU_PEAK_TFLOPS, "bound": "alu"},
+                                "achieved_tflops_whole_backup": tfl, "bound": "tensor", "unit": "TFLOP/s",
+                                "peak": tf32, "peak_source": f"{src} bf16_tflops x {TF32_PER_BF16:.3f} (TF32)",
+                                "frac": tfl / tf32,
+                                # each product is three TF32 MMAs (hi.hi + hi.lo + lo.hi)
+                                "issued_tf32_tflops": 3.0 * tfl, "issued_frac": 3.0 * tfl / tf32},
                 "v_pbvi_b0": float(g["value"][0])}
         if with_cpu and rounds == 8:
             # the oracle's Eq. 8 backup of a few points against the same vectors
@@ -587,14 +593,14 @@ def gpu_index(local_rank):
 
 
 # ---------------------------------------------------------------- roofline helpers
-def measured_peak():
+def measured_peak(key="hbm_gbs"):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             j = json.load(f)
-        return float(j["hbm_gbs"]), "measured"
+        return float(j[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}[key], "fallback"
 
 
 def tree_sources_sha():
