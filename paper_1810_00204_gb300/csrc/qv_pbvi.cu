@@ -12,13 +12,14 @@
 //   D_z(m, i) = sum over the cells x' labelled z of bbar_m(x') alpha_i(x'),   m = (b, a),
 // s = eta sum_z' D_z'(m, i) + (accuracy - eta) D_z(m, i).  D is one dense
 // contraction over the cells, split by label: the cells are ordered label by
-// label (each label's run padded to a multiple of 16 with zeros, the goal and
+// label (each label's run padded to a multiple of 32 with zeros, the goal and
 // occupied cells left out because every alpha-vector is 0 there), so D_z is
 // a matrix product over one contiguous range of that order.  Long ranges are
 // cut into pieces so the grid fills the GPU; a piece's partial product is one
 // slab, and the selection kernel adds the slabs of a label in piece order.
-// The products run on the FP32 pipes, register-blocked 8x8 per thread on
-// 128x128 tiles with double-buffered 16-deep shared-memory stages.
+// The products run on the tcgen05 tensor cores as TF32 head x head + head x
+// tail + tail x head; both operands are stored split, in the tile image the
+// tensor core reads (see tiled_off).
 //
 // The selection kernel takes, per point, every (a, z) argmax over Gamma, the
 // action a* maximising Q_b(a) = R(b, a) + gamma sum_z max_i s, and the set of
@@ -41,7 +42,8 @@ namespace {
 constexpr int kPbThreads = 256;
 constexpr int kKC = 32;          // K depth of one contraction stage (one 128-byte row of FP32);
                                  // label runs are padded to it
-constexpr int kTM = 128, kTN = 128;
+constexpr int kTM = 128, kTN = 256;  // rows of A and of B (Gamma) per contraction CTA
+constexpr int kRowTile = 128;        // rows of one 16 KB block of the tiled operand layout
 constexpr int kPiecesExtra = 64; // pieces beyond one per label
 
 struct PbModel {
@@ -95,12 +97,49 @@ __device__ __forceinline__ int pb_successors(const PbModel &m, int x, unsigned c
 }
 
 // x = hi + lo with hi = x rounded to TF32 (round to nearest, ties away) and
-// lo the exact FP32 remainder.
+// lo the FP32 remainder rounded to TF32 in turn, so both halves are exact
+// TF32 values and hi + lo is x to about 2^-22 relative.
 __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
-    uint32_t h;
+    uint32_t h, l;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
     hi = __uint_as_float(h);
-    lo = x - hi;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+    lo = __uint_as_float(l);
+}
+
+// Tiled operand layout of the contraction.  An operand of R rows (R padded
+// to a multiple of 128, RT = R / 128 row tiles) over Kp positions (S = Kp / 32
+// stages) is two planes, the TF32 heads and then the tails, each S x RT
+// blocks of 128 rows x 32 positions (16 KB), stage-major so that the row
+// tiles of one stage are adjacent.  Inside a block, row r holds its 32 values
+// in eight 16-byte chunks, chunk c stored at slot c ^ (r & 7): the K-major,
+// 128-byte-swizzled image the tensor core reads, so one bulk copy moves a
+// block (or adjacent row tiles) from HBM into shared memory unchanged.
+__device__ __forceinline__ size_t tiled_off(int row, int k, int S, int RT) {
+    const int rt = row >> 7, r = row & 127, s = k >> 5, kin = k & 31;
+    return (static_cast<size_t>(s) * RT + rt) * (kRowTile * kKC) + r * kKC + ((((kin >> 2) ^ (r & 7))) << 2) +
+           (kin & 3);
+}
+__host__ __device__ __forceinline__ size_t tiled_plane(int S, int RT) {
+    return static_cast<size_t>(S) * RT * (kRowTile * kKC);
+}
+// Writes x split into the head and tail planes at tiled position (row, k).
+__device__ __forceinline__ void tiled_store(float *T, int row, int k, int S, int RT, float x) {
+    float hi, lo;
+    tf32_split(x, hi, lo);
+    const size_t o = tiled_off(row, k, S, RT);
+    T[o] = hi;
+    T[o + tiled_plane(S, RT)] = lo;
+}
+// Inverse of tiled_off over one plane: the (row, k) whose head lives at
+// offset u (u < tiled_plane(S, RT)).
+__device__ __forceinline__ void tiled_pos(size_t u, int RT, int &row, int &k) {
+    const size_t blk = u / (kRowTile * kKC);
+    const int q = static_cast<int>(u - blk * (kRowTile * kKC));
+    const int s = static_cast<int>(blk / RT), rt = static_cast<int>(blk - static_cast<size_t>(s) * RT);
+    const int r = q >> 5, slot = q & 31;
+    row = rt * kRowTile + r;
+    k = s * kKC + ((((slot >> 2) ^ (r & 7))) << 2) + (slot & 3);
 }
 
 // ---------------------------------------------------------------- expansion
@@ -217,11 +256,13 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_init(PbModel m, float *__re
 
 // ---------------------------------------------------------------- predicted beliefs of the set
 // Grid (bands, points): every action's predicted belief of point b on the
-// band's cells, scattered into the label order (row b * 5 + a of Bp), and the
-// band's share of sum_y bbar_a(y) r(y).
+// band's cells, scattered into the label order (row b * 5 + a of the tiled
+// operand Bp, S stages, RT row tiles), and the band's share of
+// sum_y bbar_a(y) r(y).
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_predict(PbModel m, const float *__restrict__ Bset,
-                                                             const int *__restrict__ pos, int Kp, int band_cells,
-                                                             float *__restrict__ Bp, float *__restrict__ rpart) {
+                                                             const int *__restrict__ pos, int S, int RT,
+                                                             int band_cells, float *__restrict__ Bp,
+                                                             float *__restrict__ rpart) {
     __shared__ float lut[64];
     __shared__ float s_r[kPbThreads / 32][5];
     const int b = blockIdx.y, band = blockIdx.x;
@@ -242,7 +283,7 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_predict(PbModel m, const fl
         const int k = __ldg(pos + y);
         if (k >= 0) {
 #pragma unroll
-            for (int a = 0; a < 5; ++a) Bp[(static_cast<size_t>(b) * 5 + a) * Kp + k] = o[a];
+            for (int a = 0; a < 5; ++a) tiled_store(Bp, b * 5 + a, k, S, RT, o[a]);
         }
         if (QV_CELL_FREE(cw)) {
             const float r = stage_reward(true, y == m.goal, m.cost ? __ldg(m.cost + y) : 0.0f);
@@ -277,38 +318,65 @@ __global__ void k_pbvi_reward(PbModel m, const float *__restrict__ Bset, int nB,
 }
 
 // ---------------------------------------------------------------- Gamma in the label order
-__global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restrict__ G, int nG, int N,
-                                                            const int *__restrict__ perm, int Kp,
-                                                            float *__restrict__ Gp) {
-    const size_t total = static_cast<size_t>(nG) * Kp;
+// Rows of grid-ordered vectors in the label order, tiled and split: row
+// i < nG of the operand is G_i at the live cells (0 at padding positions),
+// rows nG .. R - 1 (R a multiple of 128, at most the operand's RT x 128) are
+// 0.  One thread per head element, in the planes' own order (coalesced
+// stores).
+__device__ __forceinline__ void tiled_gather(const float *__restrict__ G, int nG, int N, const int *__restrict__ perm,
+                                             int S, int RT, int R, float *__restrict__ Gp) {
+    const size_t plane = tiled_plane(S, RT);
+    const size_t rows_blocks = static_cast<size_t>(R) / kRowTile;
+    const size_t total = static_cast<size_t>(S) * rows_blocks * (kRowTile * kKC);
     for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int i = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<size_t>(i) * Kp);
+        // t runs over the first R / 128 row tiles of every stage
+        const size_t blk = t / (kRowTile * kKC);
+        const size_t s = blk / rows_blocks, rt = blk - s * rows_blocks;
+        const size_t u = (s * RT + rt) * (kRowTile * kKC) + (t - blk * (kRowTile * kKC));
+        int i, k;
+        tiled_pos(u, RT, i, k);
         const int y = __ldg(perm + k);
-        Gp[t] = y >= 0 ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
+        const float x = (i < nG && y >= 0) ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
+        float hi, lo;
+        tf32_split(x, hi, lo);
+        Gp[u] = hi;
+        Gp[u + plane] = lo;
     }
+}
+
+// Gamma as the B operand of the contraction.
+__global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restrict__ G, int nG, int N,
+                                                            const int *__restrict__ perm, int S, int RT, int R,
+                                                            float *__restrict__ Gp) {
+    tiled_gather(G, nG, N, perm, S, RT, R, Gp);
 }
 
 // ---------------------------------------------------------------- the contraction
 // slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k] on the 5th-generation
-// tensor cores: grid (M tiles, N tiles, pieces), one CTA of four warps per
-// 128 x 128 tile, the accumulator in tensor memory (128 lanes x 128 FP32
-// columns).  TF32 keeps 10 mantissa bits, too few for the argmax decisions
-// of Eq. 8, so every operand is split into a TF32 head and a TF32 tail
-// (x = hi + lo, hi = x rounded to TF32) and each product is formed as
-// hi.hi + hi.lo + lo.hi, which restores FP32-level accuracy (the dropped
-// lo.lo term is below 2^-22 of the product).  Stages of 32 values of K (one
-// 128-byte row) are staged K-major with the 128-byte swizzle in one buffer
-// of 64 KB, so three CTAs share an SM: the threads fetch stage s + 1 into
-// registers while the tensor core multiplies stage s, then wait for it and
-// store their split values (one thread issues the twelve MMAs of a stage,
-// K = 8 each, and commits them to the buffer's mbarrier).  Every wait is
-// bounded; a wait that gives up sets *status, lets the work in flight land
-// and still frees the tensor memory.
+// tensor cores: grid (M tiles of 128, N tiles of 256, pieces), one CTA of
+// four warps per 128 x 256 tile, the accumulator in tensor memory (128 lanes
+// x 256 FP32 columns).  TF32 keeps 10 mantissa bits, too few for the argmax
+// decisions of Eq. 8, so both operands come split into TF32 heads and tails
+// (x = hi + lo) and each product is formed as hi.hi + hi.lo + lo.hi, which
+// restores FP32-level accuracy (the dropped lo.lo term is below 2^-21 of the
+// product).  The operands sit in HBM in the tiled layout (tiled_off), so a
+// stage of 32 positions is four bulk copies (A heads and tails, 16 KB each;
+// B heads and tails, 32 KB each) into one of two 96 KB shared-memory
+// buffers.  Lane 0 of warp 0 issues the copies and the twelve MMAs of a stage
+// (K = 8 each) and commits them to the buffer's "empty" barrier; the copy of
+// stage s + 1 goes out once the MMAs of stage s - 1 have released its
+// buffer, while those of stage s run.  The four warps then read the
+// accumulator back (warp w owns lanes 32w .. 32w + 31, one row each).  Every
+// wait is bounded; a wait that gives up sets *status, lets the copies and
+// MMAs in flight land and still frees the tensor memory.
 constexpr int kTcThreads = 128;
-constexpr int kTcStageFloats = 4 * kTM * kKC;  // A hi, A lo, B hi, B lo
-constexpr int kTcBuffers = 1;  // one stage buffer per CTA: three CTAs share an SM's tensor core
-constexpr size_t kTcSmem = kTcBuffers * kTcStageFloats * sizeof(float) + 1024;
+constexpr int kTcStages = 2;
+constexpr int kTcAFloats = kTM * kKC, kTcBFloats = kTN * kKC;  // one plane of one stage
+constexpr int kTcStageFloats = 2 * kTcAFloats + 2 * kTcBFloats;  // A hi, A lo, B hi, B lo: 96 KB
+constexpr unsigned kTcStageBytes = kTcStageFloats * sizeof(float);
+constexpr size_t kTcSmem = kTcStages * static_cast<size_t>(kTcStageBytes) + 1024;
+constexpr int kTcTmemCols = kTN;  // FP32 accumulator: one column per B row
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -322,6 +390,7 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
            (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
 }
 
+// Bounded wait for phase `parity` of `bar`, polled by the whole warp.
 __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     for (int it = 0; it < (1 << 24); ++it) {
         uint32_t done;
@@ -335,11 +404,12 @@ __device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 3) k_pbvi_scores(const float *__restrict__ A, const float *__restrict__ Bm,
-                                                               int M, int N, int Kp, const int *__restrict__ piece,
+__global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__restrict__ A, int RTa,
+                                                               const float *__restrict__ Bm, int RTb, int M, int N,
+                                                               int S, const int *__restrict__ piece,
                                                                float *__restrict__ slab, int *__restrict__ status) {
     extern __shared__ unsigned char tc_raw[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
     __shared__ uint32_t s_tmem;
     float *st = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
     const int p = blockIdx.z;
@@ -347,113 +417,111 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_pbvi_scores(const float *__re
     const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&bar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&bar[1])));
+        for (int i = 0; i < kTcStages; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&empty[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc_smem_u32(&s_tmem)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc_smem_u32(&s_tmem)),
+                     "n"(kTcTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
-    // thread t stages row t of the A tile and row t of the B tile: 32 values
-    // each, split, swizzled (16-byte chunk c of row r lands at chunk c ^ (r & 7));
-    // the next stage's global loads are issued into registers before the
-    // current stage's MMAs, so their latency overlaps the tensor core's work
-    const bool a_ok = m0 + tid < M, b_ok = n0 + tid < N;
-    const float *arow = A + static_cast<size_t>(a_ok ? m0 + tid : 0) * Kp;
-    const float *brow = Bm + static_cast<size_t>(b_ok ? n0 + tid : 0) * Kp;
-    float4 ra[kKC / 4], rb[kKC / 4];
-    auto fetch = [&](int k) {
+    const int s0 = k0 / kKC, nst = (k1 - k0) / kKC;
+    const size_t planeA = tiled_plane(S, RTa), planeB = tiled_plane(S, RTb);
+    const int rta = m0 / kRowTile, rtb = n0 / kRowTile;
+    int fail = 0;
+    if (warp == 0 && nst > 0) {
+        // stage s of this piece: the A row tile and the two B row tiles of
+        // global stage s0 + s, heads and tails
+        auto load = [&](int s) {
+            if (lane == 0) {
+                float *buf = st + (s % kTcStages) * kTcStageFloats;
+                uint64_t *bar = &full[s % kTcStages];
+                const size_t oa = (static_cast<size_t>(s0 + s) * RTa + rta) * (kRowTile * kKC);
+                const size_t ob = (static_cast<size_t>(s0 + s) * RTb + rtb) * (kRowTile * kKC);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)),
+                             "r"(kTcStageBytes)
+                             : "memory");
+                const void *src[4] = {A + oa, A + oa + planeA, Bm + ob, Bm + ob + planeB};
+                float *dst[4] = {buf, buf + kTcAFloats, buf + 2 * kTcAFloats, buf + 2 * kTcAFloats + kTcBFloats};
+                const unsigned bytes[4] = {kTcAFloats * 4u, kTcAFloats * 4u, kTcBFloats * 4u, kTcBFloats * 4u};
 #pragma unroll
-        for (int c = 0; c < kKC / 4; ++c) {
-            ra[c] = a_ok ? __ldg(reinterpret_cast<const float4 *>(arow + k) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            rb[c] = b_ok ? __ldg(reinterpret_cast<const float4 *>(brow + k) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    auto stage_in = [&](int buf) {
-        float *sa_hi = st + buf * kTcStageFloats, *sa_lo = sa_hi + kTM * kKC;
-        float *sb_hi = sa_lo + kTM * kKC, *sb_lo = sb_hi + kTN * kKC;
-#pragma unroll
-        for (int c = 0; c < kKC / 4; ++c) {
-            const int o = tid * kKC + ((c ^ (tid & 7)) << 2);
-            float4 ah, al, bh, bl;
-            tf32_split(ra[c].x, ah.x, al.x);
-            tf32_split(ra[c].y, ah.y, al.y);
-            tf32_split(ra[c].z, ah.z, al.z);
-            tf32_split(ra[c].w, ah.w, al.w);
-            tf32_split(rb[c].x, bh.x, bl.x);
-            tf32_split(rb[c].y, bh.y, bl.y);
-            tf32_split(rb[c].z, bh.z, bl.z);
-            tf32_split(rb[c].w, bh.w, bl.w);
-            *reinterpret_cast<float4 *>(sa_hi + o) = ah;
-            *reinterpret_cast<float4 *>(sa_lo + o) = al;
-            *reinterpret_cast<float4 *>(sb_hi + o) = bh;
-            *reinterpret_cast<float4 *>(sb_lo + o) = bl;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
-    };
-    // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 128, M = 128
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
-    uint32_t phase[2] = {0u, 0u};
-    const int nst = (k1 - k0) / kKC;
-    bool ok = true;
-    if (nst > 0) fetch(k0);
-    for (int s = 0; s < nst; ++s) {
-        const int buf = s % kTcBuffers;
-        if (s >= kTcBuffers) {  // the MMAs of stage s - kTcBuffers read this buffer
-            const bool w = tc_wait(&bar[buf], phase[buf]);
-            phase[buf] ^= 1u;
-            if (__syncthreads_or(w ? 0 : 1)) {
-                ok = false;
+                for (int i = 0; i < 4; ++i)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            tc_smem_u32(dst[i])),
+                        "l"(src[i]), "r"(bytes[i]), "r"(tc_smem_u32(bar))
+                        : "memory");
+            }
+            __syncwarp();
+        };
+        // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 256, M = 128
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
+        int loaded = 0, committed = 0;  // stages whose copies / MMAs were issued
+        for (; loaded < nst && loaded < kTcStages; ++loaded) load(loaded);
+        for (int s = 0; s < nst; ++s) {
+            const int buf = s % kTcStages;
+            if (!tc_wait(&full[buf], (s / kTcStages) & 1)) {
+                fail = 1;
                 break;
             }
-        }
-        stage_in(buf);
-        if (s + 1 < nst) fetch(k0 + (s + 1) * kKC);
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-            float *sa_hi = st + buf * kTcStageFloats, *sa_lo = sa_hi + kTM * kKC;
-            float *sb_hi = sa_lo + kTM * kKC, *sb_lo = sb_hi + kTN * kKC;
-            const uint64_t ah = tc_desc(tc_smem_u32(sa_hi)), al = tc_desc(tc_smem_u32(sa_lo));
-            const uint64_t bh = tc_desc(tc_smem_u32(sb_hi)), bl = tc_desc(tc_smem_u32(sb_lo));
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (lane == 0) {
+                const float *b = st + buf * kTcStageFloats;
+                const uint64_t ah = tc_desc(tc_smem_u32(b)), al = tc_desc(tc_smem_u32(b + kTcAFloats));
+                const uint64_t bh = tc_desc(tc_smem_u32(b + 2 * kTcAFloats));
+                const uint64_t bl = tc_desc(tc_smem_u32(b + 2 * kTcAFloats + kTcBFloats));
 #pragma unroll
-            for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
-                const uint64_t o = 2ull * kk;
-                const uint32_t first = (s == 0 && kk == 0) ? 0u : 1u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ah + o), "l"(bh + o), "r"(idesc), "r"(first));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(ah + o),
-                             "l"(bl + o), "r"(idesc));
-                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem), "l"(al + o),
-                             "l"(bh + o), "r"(idesc));
+                for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
+                    const uint64_t o = 2ull * kk;
+                    const uint32_t acc = (s == 0 && kk == 0) ? 0u : 1u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ah + o), "l"(bh + o), "r"(idesc), "r"(acc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem),
+                                 "l"(ah + o), "l"(bl + o), "r"(idesc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem),
+                                 "l"(al + o), "l"(bh + o), "r"(idesc));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem_u32(&empty[buf])));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tc_smem_u32(&bar[buf])));
+            __syncwarp();
+            committed = s + 1;
+            // the copy of the next stage that is not yet in flight reuses the
+            // buffer of stage s - 1: wait for that stage's MMAs first
+            if (loaded < nst && s >= 1) {
+                const int pb = (s - 1) % kTcStages;
+                if (!tc_wait(&empty[pb], ((s - 1) / kTcStages) & 1)) {
+                    fail = 1;
+                    break;
+                }
+                load(loaded++);
+            }
+        }
+        // the last commit covers every MMA issued before it
+        if (!fail && !tc_wait(&empty[(nst - 1) % kTcStages], ((nst - 1) / kTcStages) & 1)) fail = 1;
+        if (fail) {
+            if (lane == 0) atomicOr(status, 1);
+            // let the copies and MMAs in flight land before the memory is freed
+            for (int s = committed; s < loaded; ++s) tc_wait(&full[s % kTcStages], (s / kTcStages) & 1);
+            if (committed > 0) tc_wait(&empty[(committed - 1) % kTcStages], ((committed - 1) / kTcStages) & 1);
         }
     }
-    // the last commit covers every MMA issued before it
-    if (nst > 0) {
-        const int lb = (nst - 1) % kTcBuffers;
-        const bool w = ok ? tc_wait(&bar[lb], phase[lb]) : false;
-        if (__syncthreads_or(w ? 0 : 1)) {
-            ok = false;
-            if (tid == 0) atomicOr(status, 1);
-            tc_wait(&bar[lb], phase[lb]);  // let the work in flight land before the memory is freed
-        }
-    }
+    const bool ok = !__syncthreads_or(fail);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
         float *out = slab + static_cast<size_t>(p) * M * N;
         const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kTN; c0 += 16) {
+        for (int c0 = 0; c0 < kTN && n0 + c0 < N; c0 += 16) {
             uint32_t r[16];
             if (nst > 0) {
                 const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
@@ -486,7 +554,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) k_pbvi_scores(const float *__re
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcTmemCols));
 }
 
 // ---------------------------------------------------------------- selection
@@ -653,15 +721,9 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_alpha(PbModel m, int band_r
 
 // ---------------------------------------------------------------- V_PBVI(b) = max_i alpha_i . b
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_scatter_points(const float *__restrict__ Bset, int nb, int N,
-                                                                    const int *__restrict__ perm, int Kp,
-                                                                    float *__restrict__ Ap) {
-    const size_t total = static_cast<size_t>(nb) * Kp;
-    for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
-         t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        const int j = static_cast<int>(t / Kp), k = static_cast<int>(t - static_cast<size_t>(j) * Kp);
-        const int y = __ldg(perm + k);
-        Ap[t] = y >= 0 ? __ldg(Bset + static_cast<size_t>(j) * N + y) : 0.0f;
-    }
+                                                                    const int *__restrict__ perm, int S, int RT,
+                                                                    int R, float *__restrict__ Ap) {
+    tiled_gather(Bset, nb, N, perm, S, RT, R, Ap);
 }
 
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int npieces, const float *__restrict__ slab,
@@ -736,6 +798,9 @@ struct qv_pbvi {
                                  // backup has overwritten Gp since
     int nbands;                  // bands of k_pbvi_predict
     int band_cells;
+    int S;                       // contraction stages, Kp / 32
+    int RTa, RTb, RTp;           // row tiles of the tiled operands Bp (5 x max_points rows),
+                                 // Gp (max_vectors rows, an even count) and Ap (max_points rows)
 };
 
 namespace {
@@ -820,11 +885,15 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
     h->off_pos = take(N * sizeof(int));
     h->off_perm = take(Kp * sizeof(int));
     h->off_piece = take(3 * h->max_pieces * sizeof(int));
-    h->off_Bp = take(5 * P * Kp * sizeof(float));
+    h->S = h->Kp / qv::kKC;
+    h->RTa = static_cast<int>((5 * P + qv::kRowTile - 1) / qv::kRowTile);
+    h->RTb = static_cast<int>(2 * ((G + qv::kTN - 1) / qv::kTN));
+    h->RTp = static_cast<int>((P + qv::kRowTile - 1) / qv::kRowTile);
+    h->off_Bp = take(2 * qv::tiled_plane(h->S, h->RTa) * sizeof(float));
     h->off_RB = take(5 * P * sizeof(float));
     h->off_rpart = take(5 * P * h->nbands * sizeof(float));
-    h->off_Gp = take(G * Kp * sizeof(float));
-    h->off_Ap = take(P * Kp * sizeof(float));
+    h->off_Gp = take(2 * qv::tiled_plane(h->S, h->RTb) * sizeof(float));
+    h->off_Ap = take(2 * qv::tiled_plane(h->S, h->RTp) * sizeof(float));
     h->off_slab = take(static_cast<size_t>(h->max_pieces) * 5 * P * std::max(G, P) * sizeof(float));
     h->off_best = take(P * nz * sizeof(int));
     h->off_uniq = take(P * nz * sizeof(int));
@@ -919,12 +988,16 @@ extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB
     }
     h->nB = nB;
     float *Bp = reinterpret_cast<float *>(ws + h->off_Bp);
-    if (qv_check_cuda(cudaMemsetAsync(Bp, 0, static_cast<size_t>(5) * nB * h->Kp * sizeof(float), st), "memset") !=
-        QV_OK)
+    // zero the row tiles the contraction reads (both planes: 2 S stage rows
+    // of RTa blocks, the first Mt of each), then scatter the live cells
+    const size_t blk = static_cast<size_t>(qv::kRowTile) * qv::kKC * sizeof(float);
+    const int Mt = (5 * nB + qv::kRowTile - 1) / qv::kRowTile;
+    if (qv_check_cuda(cudaMemset2DAsync(Bp, h->RTa * blk, 0, Mt * blk, 2 * static_cast<size_t>(h->S), st),
+                      "memset") != QV_OK)
         return QV_ERR_CUDA;
     const qv::PbModel pm = qv::pb_model(&h->model);
     qv::k_pbvi_predict<<<dim3(h->nbands, nB), qv::kPbThreads, 0, st>>>(
-        pm, d_B, reinterpret_cast<const int *>(ws + h->off_pos), h->Kp, h->band_cells, Bp,
+        pm, d_B, reinterpret_cast<const int *>(ws + h->off_pos), h->S, h->RTa, h->band_cells, Bp,
         reinterpret_cast<float *>(ws + h->off_rpart));
     qv::k_pbvi_reward<<<(nB * 5 + 127) / 128, 128, 0, st>>>(pm, d_B, nB, h->nbands,
                                                              reinterpret_cast<const float *>(ws + h->off_rpart),
@@ -952,14 +1025,14 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     const int *piece = reinterpret_cast<const int *>(ws + h->off_piece);
     float *Gp = reinterpret_cast<float *>(ws + h->off_Gp);
     float *slab = reinterpret_cast<float *>(ws + h->off_slab);
-    const int gthreads = 256, gblocks = std::min<long long>((static_cast<long long>(nG) * Kp + gthreads - 1) / gthreads,
-                                                            8LL * qv_num_sms());
+    const int gthreads = 256, gblocks = 8 * qv_num_sms();
     h->gp_value_nG = 0;
     qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
-                                                    reinterpret_cast<const int *>(ws + h->off_perm), Kp, Gp);
+                                                    reinterpret_cast<const int *>(ws + h->off_perm), h->S, h->RTb,
+                                                    Nt * qv::kTN, Gp);
     if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
     qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
-        reinterpret_cast<const float *>(ws + h->off_Bp), Gp, M, nG, Kp, piece, slab,
+        reinterpret_cast<const float *>(ws + h->off_Bp), h->RTa, Gp, h->RTb, M, nG, h->S, piece, slab,
         reinterpret_cast<int *>(ws + h->off_status));
     const qv::PbModel pm = qv::pb_model(&h->model);
     int *best = d_best ? d_best : reinterpret_cast<int *>(ws + h->off_best);
@@ -1005,22 +1078,24 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
     float *slab = reinterpret_cast<float *>(ws + h->off_slab);
     const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
     const int gb = 8 * qv_num_sms();
+    const int Nt = (nG + qv::kTN - 1) / qv::kTN;
     if (d_G) {
-        qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, Kp, Gp);
+        qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, h->S, h->RTb, Nt * qv::kTN, Gp);
         h->gp_value_nG = nG;
     }
     // beliefs in chunks of up to max_points (the size of the Ap region)
     for (int c0 = 0; c0 < nb; c0 += h->max_points) {
         const int nc = std::min(h->max_points, nb - c0);
-        const int Mt = (nc + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
+        const int Mt = (nc + qv::kTM - 1) / qv::kTM;
         std::vector<int> pc;
         make_pieces(*h, Mt * Nt, Kp, false, pc);
         if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
         const int npieces = static_cast<int>(pc.size() / 3);
-        qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, Kp, Ap);
+        qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, h->S, h->RTp,
+                                                       Mt * qv::kTM, Ap);
         if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
         qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
-            Ap, Gp, nc, nG, Kp, reinterpret_cast<const int *>(ws + h->off_piece), slab,
+            Ap, h->RTp, Gp, h->RTb, nc, nG, h->S, reinterpret_cast<const int *>(ws + h->off_piece), slab,
             reinterpret_cast<int *>(ws + h->off_status));
         qv::k_pbvi_rowmax<<<nc, qv::kPbThreads, 0, st>>>(nc, nG, npieces, slab, d_value + c0,
                                                          d_arg ? d_arg + c0 : nullptr);
