@@ -564,83 +564,146 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
 // count as tied and the lowest index among them is taken.
 __device__ __forceinline__ float tie_tol(float best) { return 1e-5f * fmaxf(1.0f, fabsf(best)); }
 
-// One CTA per point b.  For each action: D(i) = the sum of every slab row
-// (pieces in order), then one warp per observation z takes
-// argmax_i eta D(i) + (accuracy - eta) D_z(i) (ties as above).  Then a* and
-// the distinct winners of a* with their multiplicities.
-__global__ void __launch_bounds__(kPbThreads) k_pbvi_select(PbModel m, int nB, int nG, int npieces,
-                                                            const int *__restrict__ piece,
-                                                            const float *__restrict__ slab,
-                                                            const float *__restrict__ RB, float *__restrict__ value,
-                                                            int *__restrict__ astar, int *__restrict__ best,
-                                                            float *__restrict__ q, int *__restrict__ uniq,
-                                                            int *__restrict__ mult, int *__restrict__ nuniq) {
-    extern __shared__ float D[];  // [nG]
-    __shared__ float s_val[QV_MAX_BEACONS + 1];
+// One CTA per point b.  For each action a the slab rows of (b, a) are read
+// once, a chunk of vectors at a time: D_z(i) (the label's pieces in order)
+// and D(i) (every piece in order) go to shared memory.  One warp per
+// observation z then takes argmax_i eta D(i) + (accuracy - eta) D_z(i): the
+// best score over every chunk first, then the lowest index within the tie
+// tolerance of it (a second read of the slabs only when nG spans more than
+// one chunk).  Then a* and the distinct winners of a* with their
+// multiplicities.
+constexpr int kSelThreads = 512;
+constexpr size_t kSelSmemBudget = 96 * 1024;  // D_z and D of one chunk, and the piece labels
+
+int select_chunk(int nz, int nG, int npieces) {
+    const size_t room = (kSelSmemBudget - (npieces + 1) * sizeof(int)) / sizeof(float) / (nz + 1);
+    int c = static_cast<int>(std::min<size_t>(room, static_cast<size_t>(nG)));
+    if (c < nG) c = std::max(32, c & ~31);
+    return c;
+}
+size_t select_smem(int nz, int chunk, int npieces) {
+    return static_cast<size_t>(nz + 1) * chunk * sizeof(float) + (npieces + 1) * sizeof(int);
+}
+
+__global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int nB, int nG, int chunk, int npieces,
+                                                                const int *__restrict__ piece,
+                                                                const float *__restrict__ slab,
+                                                                const float *__restrict__ RB, float *__restrict__ value,
+                                                                int *__restrict__ astar, int *__restrict__ best,
+                                                                float *__restrict__ q, int *__restrict__ uniq,
+                                                                int *__restrict__ mult, int *__restrict__ nuniq) {
+    extern __shared__ float sel_sm[];
+    float *Dz = sel_sm;                       // [nz][chunk]
+    float *D = sel_sm + m.nz * chunk;         // [chunk]
+    int *plabel = reinterpret_cast<int *>(D + chunk);  // [npieces + 1], -1 after the last
+    __shared__ float s_bv[QV_MAX_BEACONS + 1], s_bs[QV_MAX_BEACONS + 1];
+    __shared__ int s_bi[QV_MAX_BEACONS + 1];
     __shared__ int s_arg[5][QV_MAX_BEACONS + 1];
+    __shared__ float s_val[QV_MAX_BEACONS + 1];
     __shared__ float s_q[5];
-    __shared__ int s_first[QV_MAX_BEACONS + 2];  // first piece of each label, label order
+    __shared__ int s_empty[QV_MAX_BEACONS + 1];  // labels with no piece (D_z = 0)
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int M = nB * 5;
-    const size_t slab_elems = static_cast<size_t>(M) * nG;
-    // pieces are stored label by label; s_first[z] .. s_first[z + 1] are z's
-    if (tid == 0) {
-        int p = 0;
-        for (int z = 0; z <= m.nz; ++z) {
-            while (p < npieces && __ldg(piece + 3 * p + 2) < z) ++p;
-            s_first[z] = p;
+    constexpr int kWarps = kSelThreads / 32;
+    const size_t slab_elems = static_cast<size_t>(nB) * 5 * nG;
+    for (int p = tid; p <= npieces; p += kSelThreads) plabel[p] = p < npieces ? __ldg(piece + 3 * p + 2) : -1;
+    for (int z = tid; z < m.nz; z += kSelThreads) s_empty[z] = 1;
+    __syncthreads();
+    for (int p = tid; p < npieces; p += kSelThreads) s_empty[plabel[p]] = 0;
+    const int nchunks = (nG + chunk - 1) / chunk;
+    // D_z and D of vectors i0 .. i0 + n - 1 of row (b, a); pieces in batches
+    // of eight loads so each thread has several in flight
+    auto fill = [&](size_t row, int i0, int n) {
+        for (int i = tid; i < n; i += kSelThreads) {
+            const size_t col = row + i0 + i;
+            float d = 0.0f, dz = 0.0f;
+            for (int p0 = 0; p0 < npieces; p0 += 8) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = p0 + j < npieces ? __ldg(slab + static_cast<size_t>(p0 + j) * slab_elems + col) : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int p = p0 + j;
+                    if (p < npieces) {
+                        d += v[j];
+                        dz += v[j];
+                        if (plabel[p + 1] != plabel[p]) {
+                            Dz[plabel[p] * chunk + i] = dz;
+                            dz = 0.0f;
+                        }
+                    }
+                }
+            }
+            D[i] = d;
+            for (int z = 0; z < m.nz; ++z)
+                if (s_empty[z]) Dz[z * chunk + i] = 0.0f;
         }
-    }
+    };
     for (int a = 0; a < 5; ++a) {
         const size_t row = static_cast<size_t>(b * 5 + a) * nG;
-        __syncthreads();
-        for (int i = tid; i < nG; i += blockDim.x) {
-            float s = 0.0f;
-            for (int p = 0; p < npieces; ++p) s += __ldg(slab + p * slab_elems + row + i);
-            D[i] = s;
+        // pass 1: the best score of every z
+        for (int c = 0; c < nchunks; ++c) {
+            const int i0 = c * chunk, n = min(chunk, nG - i0);
+            __syncthreads();
+            fill(row, i0, n);
+            __syncthreads();
+            for (int z = wid; z < m.nz; z += kWarps) {
+                const float *dz = Dz + z * chunk;
+                float bv = -INFINITY;
+                for (int i = lane; i < n; i += 32) bv = fmaxf(bv, fmaf(m.acc - m.eta, dz[i], m.eta * D[i]));
+                for (int o = 16; o > 0; o >>= 1) bv = fmaxf(bv, __shfl_xor_sync(0xffffffffu, bv, o));
+                if (lane == 0) {
+                    s_bv[z] = c == 0 ? bv : fmaxf(s_bv[z], bv);
+                    if (c == 0) s_bi[z] = 0x7fffffff;
+                }
+            }
         }
-        __syncthreads();
-        for (int z = wid; z < m.nz; z += kPbThreads / 32) {
-            const int p0 = s_first[z], p1 = s_first[z + 1];
-            auto score = [&](int i) {
-                float dz = 0.0f;
-                for (int p = p0; p < p1; ++p) dz += __ldg(slab + p * slab_elems + row + i);
-                return fmaf(m.acc - m.eta, dz, m.eta * D[i]);
-            };
-            // the best score, then the lowest index within the tie tolerance of it
-            float bv = -INFINITY;
-            for (int i = lane; i < nG; i += 32) bv = fmaxf(bv, score(i));
-            for (int o = 16; o > 0; o >>= 1) bv = fmaxf(bv, __shfl_xor_sync(0xffffffffu, bv, o));
-            const float floor_v = bv - tie_tol(bv);
-            int bi = 0x7fffffff;
-            float bs = 0.0f;
-            for (int i = lane; i < nG; i += 32) {
-                const float sv = score(i);
-                if (sv >= floor_v) {
-                    bi = i;
-                    bs = sv;
-                    break;
-                }
+        // pass 2: the lowest index within the tie tolerance of the best
+        for (int c = 0; c < nchunks; ++c) {
+            const int i0 = c * chunk, n = min(chunk, nG - i0);
+            __syncthreads();
+            if (nchunks > 1) {
+                fill(row, i0, n);
+                __syncthreads();
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                const float os = __shfl_xor_sync(0xffffffffu, bs, o);
-                if (oi < bi) {
-                    bi = oi;
-                    bs = os;
+            for (int z = wid; z < m.nz; z += kWarps) {
+                if (s_bi[z] != 0x7fffffff) continue;  // found in an earlier chunk (warp-uniform)
+                const float *dz = Dz + z * chunk;
+                const float floor_v = s_bv[z] - tie_tol(s_bv[z]);
+                int bi = 0x7fffffff;
+                float bs = 0.0f;
+                for (int i = lane; i < n; i += 32) {
+                    const float sv = fmaf(m.acc - m.eta, dz[i], m.eta * D[i]);
+                    if (sv >= floor_v) {
+                        bi = i;
+                        bs = sv;
+                        break;
+                    }
                 }
-            }
-            if (lane == 0) {
-                const bool found = bi < nG;  // (none when every score is NaN)
-                s_val[z] = found ? bs : bv;
-                s_arg[a][z] = found ? bi : 0;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    const float os = __shfl_xor_sync(0xffffffffu, bs, o);
+                    if (oi < bi) {
+                        bi = oi;
+                        bs = os;
+                    }
+                }
+                if (lane == 0 && bi != 0x7fffffff) {
+                    s_bi[z] = i0 + bi;
+                    s_bs[z] = bs;
+                }
             }
         }
         __syncthreads();
         if (tid == 0) {
-            float s = 0.0f;
-            for (int z = 0; z < m.nz; ++z) s += s_val[z];
-            s_q[a] = fmaf(m.gamma, s, __ldg(RB + b * 5 + a));
+            float sum = 0.0f;
+            for (int z = 0; z < m.nz; ++z) {
+                const bool found = s_bi[z] != 0x7fffffff;  // (none when every score is NaN)
+                s_val[z] = found ? s_bs[z] : s_bv[z];
+                s_arg[a][z] = found ? s_bi[z] : 0;
+                sum += s_val[z];
+            }
+            s_q[a] = fmaf(m.gamma, sum, __ldg(RB + b * 5 + a));
         }
     }
     __syncthreads();
@@ -735,8 +798,17 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int 
     float bv = -INFINITY;
     int bi = 0x7fffffff;
     for (int i = tid; i < nG; i += blockDim.x) {
+        // pieces in order, in batches of eight loads in flight
+        const float *col = slab + static_cast<size_t>(j) * nG + i;
         float s = 0.0f;
-        for (int p = 0; p < npieces; ++p) s += __ldg(slab + p * slab_elems + static_cast<size_t>(j) * nG + i);
+        for (int p0 = 0; p0 < npieces; p0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = p0 + t < npieces ? __ldg(col + (p0 + t) * slab_elems) : 0.0f;
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (p0 + t < npieces) s += v[t];
+        }
         if (s > bv) {
             bv = s;
             bi = i;
@@ -784,7 +856,8 @@ qv_status tc_prepare() {
 struct qv_pbvi {
     qv_model_t model;
     int max_points, max_vectors;
-    int Kp, nz, max_pieces;
+    int Kp, nz, max_pieces;      // the slab region holds max_pieces x 5 max_points x max(vectors, points)
+    int piece_table;             // entries of the piece table (at least max_pieces)
     std::vector<int> perm;       // Kp: grid index of each position, -1 for padding
     std::vector<int> pos;        // H * pitch: position of each cell, -1 off the live cells
     std::vector<int> seg;        // nz + 1: label z occupies [seg[z], seg[z + 1])
@@ -809,12 +882,15 @@ using qv::align256;
 
 // Pieces of the label runs: each run [seg[z], seg[z+1]) is cut into pieces of
 // at most L positions (a multiple of kKC), L chosen so that tiles x pieces
-// fills the GPU a few times over and there are at most max_pieces pieces.
-void make_pieces(const qv_pbvi &h, int tiles, int total_len, bool by_label, std::vector<int> &out) {
+// fills the GPU (a few times over for the backup's many tiles, about once
+// for the few tiles of V_PBVI, with at least three stages a piece) and there
+// are at most `cap` pieces.
+void make_pieces(const qv_pbvi &h, int tiles, int total_len, bool by_label, int cap, std::vector<int> &out) {
     out.clear();
-    const int target = 4 * qv_num_sms();
+    const int target = (by_label ? 4 : 1) * qv_num_sms();
     const int want_pieces = std::max(1, (target + tiles - 1) / tiles);
-    int L = std::max(qv::kKC, ((total_len / want_pieces + qv::kKC - 1) / qv::kKC) * qv::kKC);
+    const int min_len = by_label ? qv::kKC : 3 * qv::kKC;
+    int L = std::max(min_len, ((total_len / want_pieces + qv::kKC - 1) / qv::kKC) * qv::kKC);
     for (;;) {
         out.clear();
         if (by_label) {
@@ -823,9 +899,15 @@ void make_pieces(const qv_pbvi &h, int tiles, int total_len, bool by_label, std:
         } else {
             for (int k = 0; k < total_len; k += L) out.insert(out.end(), {k, std::min(total_len, k + L), 0});
         }
-        if (static_cast<int>(out.size() / 3) <= h.max_pieces) break;
-        L *= 2;
+        if (static_cast<int>(out.size() / 3) <= cap) break;
+        L += qv::kKC * std::max(1, L / (8 * qv::kKC));  // about 12 % longer
     }
+}
+
+// Pieces the slab region and the piece table allow for an M x N product.
+int piece_cap(const qv_pbvi &h, size_t M, size_t N) {
+    const size_t slab = static_cast<size_t>(h.max_pieces) * 5 * h.max_points * std::max(h.max_vectors, h.max_points);
+    return static_cast<int>(std::min<size_t>(h.piece_table, slab / std::max<size_t>(1, M * N)));
 }
 
 qv_status upload_pieces(qv_pbvi *h, const std::vector<int> &pc, cudaStream_t st) {
@@ -873,6 +955,7 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
             h->pos[y] = k;
         }
     h->max_pieces = nz + qv::kPiecesExtra;
+    h->piece_table = std::max(h->max_pieces, 512);
     h->band_cells = 4096;
     h->nbands = (N + h->band_cells - 1) / h->band_cells;
     const size_t P = max_points, G = h->max_vectors, Kp = h->Kp;
@@ -884,7 +967,7 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
     };
     h->off_pos = take(N * sizeof(int));
     h->off_perm = take(Kp * sizeof(int));
-    h->off_piece = take(3 * h->max_pieces * sizeof(int));
+    h->off_piece = take(3 * h->piece_table * sizeof(int));
     h->S = h->Kp / qv::kKC;
     h->RTa = static_cast<int>((5 * P + qv::kRowTile - 1) / qv::kRowTile);
     h->RTb = static_cast<int>(2 * ((G + qv::kTN - 1) / qv::kTN));
@@ -1019,7 +1102,7 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     const int nB = h->nB, M = 5 * nB, Kp = h->Kp;
     const int Mt = (M + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
     std::vector<int> pc;
-    make_pieces(*h, Mt * Nt, Kp, true, pc);
+    make_pieces(*h, Mt * Nt, Kp, true, piece_cap(*h, M, nG), pc);
     if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
     const int npieces = static_cast<int>(pc.size() / 3);
     const int *piece = reinterpret_cast<const int *>(ws + h->off_piece);
@@ -1040,13 +1123,14 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     float *value = d_value ? d_value : reinterpret_cast<float *>(ws + h->off_val);
     int *uniq = reinterpret_cast<int *>(ws + h->off_uniq), *mult = reinterpret_cast<int *>(ws + h->off_mult);
     int *nuniq = reinterpret_cast<int *>(ws + h->off_nuniq);
-    const size_t sel_smem = static_cast<size_t>(nG) * sizeof(float);
+    const int chunk = qv::select_chunk(h->nz, nG, npieces);
+    const size_t sel_smem = qv::select_smem(h->nz, chunk, npieces);
     if (sel_smem > 48 * 1024 &&
         qv_check_cuda(cudaFuncSetAttribute(qv::k_pbvi_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(sel_smem)),
                       "smem attr") != QV_OK)
         return QV_ERR_CUDA;
-    qv::k_pbvi_select<<<nB, qv::kPbThreads, sel_smem, st>>>(pm, nB, nG, npieces, piece, slab,
+    qv::k_pbvi_select<<<nB, qv::kSelThreads, sel_smem, st>>>(pm, nB, nG, chunk, npieces, piece, slab,
                                                              reinterpret_cast<const float *>(ws + h->off_RB), value,
                                                              astar, best, d_q, uniq, mult, nuniq);
     const int band_rows = std::max(1, 4096 / h->model.pitch);
@@ -1088,7 +1172,7 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
         const int nc = std::min(h->max_points, nb - c0);
         const int Mt = (nc + qv::kTM - 1) / qv::kTM;
         std::vector<int> pc;
-        make_pieces(*h, Mt * Nt, Kp, false, pc);
+        make_pieces(*h, Mt * Nt, Kp, false, piece_cap(*h, nc, nG), pc);
         if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
         const int npieces = static_cast<int>(pc.size() / 3);
         qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, h->S, h->RTp,
