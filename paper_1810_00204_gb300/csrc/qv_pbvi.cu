@@ -131,16 +131,6 @@ __device__ __forceinline__ void tiled_store(float *T, int row, int k, int S, int
     T[o] = hi;
     T[o + tiled_plane(S, RT)] = lo;
 }
-// Inverse of tiled_off over one plane: the (row, k) whose head lives at
-// offset u (u < tiled_plane(S, RT)).
-__device__ __forceinline__ void tiled_pos(size_t u, int RT, int &row, int &k) {
-    const size_t blk = u / (kRowTile * kKC);
-    const int q = static_cast<int>(u - blk * (kRowTile * kKC));
-    const int s = static_cast<int>(blk / RT), rt = static_cast<int>(blk - static_cast<size_t>(s) * RT);
-    const int r = q >> 5, slot = q & 31;
-    row = rt * kRowTile + r;
-    k = s * kKC + ((((slot >> 2) ^ (r & 7))) << 2) + (slot & 3);
-}
 
 // ---------------------------------------------------------------- expansion
 // One CTA per point j: pass 1 writes the predicted belief of the drawn action
@@ -319,25 +309,25 @@ __global__ void k_pbvi_reward(PbModel m, const float *__restrict__ Bset, int nB,
 
 // ---------------------------------------------------------------- Gamma in the label order
 // Rows of grid-ordered vectors in the label order, tiled and split: row
-// i < nG of the operand is G_i at the live cells (0 at padding positions),
-// rows nG .. R - 1 (R a multiple of 128, at most the operand's RT x 128) are
-// 0.  One thread per head element, in the planes' own order (coalesced
-// stores).
-__device__ __forceinline__ void tiled_gather(const float *__restrict__ G, int nG, int N, const int *__restrict__ perm,
-                                             int S, int RT, int R, float *__restrict__ Gp) {
+// i < R of the operand is G_i at the live cells (0 at padding positions).
+// Rows R .. of the last row tile are left as they are: an MMA row (or
+// column) only feeds its own output row (or column), which the contraction
+// does not store.  One thread per head element, a row's 32 values of a stage
+// by 32 consecutive threads (one 128-byte segment per plane).
+__device__ __forceinline__ void tiled_gather(const float *__restrict__ G, int N, const int *__restrict__ perm, int S,
+                                             int RT, int R, float *__restrict__ Gp) {
     const size_t plane = tiled_plane(S, RT);
-    const size_t rows_blocks = static_cast<size_t>(R) / kRowTile;
-    const size_t total = static_cast<size_t>(S) * rows_blocks * (kRowTile * kKC);
+    const size_t per_stage = static_cast<size_t>(R) * kKC;
+    const size_t total = static_cast<size_t>(S) * per_stage;
     for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += static_cast<size_t>(gridDim.x) * blockDim.x) {
-        // t runs over the first R / 128 row tiles of every stage
-        const size_t blk = t / (kRowTile * kKC);
-        const size_t s = blk / rows_blocks, rt = blk - s * rows_blocks;
-        const size_t u = (s * RT + rt) * (kRowTile * kKC) + (t - blk * (kRowTile * kKC));
-        int i, k;
-        tiled_pos(u, RT, i, k);
+        const int s = static_cast<int>(t / per_stage);
+        const int rem = static_cast<int>(t - static_cast<size_t>(s) * per_stage);
+        const int i = rem >> 5, slot = rem & 31;
+        const int k = s * kKC + ((((slot >> 2) ^ (i & 7))) << 2) + (slot & 3);
+        const size_t u = (static_cast<size_t>(s) * RT + (i >> 7)) * (kRowTile * kKC) + (i & 127) * kKC + slot;
         const int y = __ldg(perm + k);
-        const float x = (i < nG && y >= 0) ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
+        const float x = y >= 0 ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
         float hi, lo;
         tf32_split(x, hi, lo);
         Gp[u] = hi;
@@ -347,9 +337,9 @@ __device__ __forceinline__ void tiled_gather(const float *__restrict__ G, int nG
 
 // Gamma as the B operand of the contraction.
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restrict__ G, int nG, int N,
-                                                            const int *__restrict__ perm, int S, int RT, int R,
+                                                            const int *__restrict__ perm, int S, int RT,
                                                             float *__restrict__ Gp) {
-    tiled_gather(G, nG, N, perm, S, RT, R, Gp);
+    tiled_gather(G, N, perm, S, RT, nG, Gp);
 }
 
 // ---------------------------------------------------------------- the contraction
@@ -785,8 +775,8 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_alpha(PbModel m, int band_r
 // ---------------------------------------------------------------- V_PBVI(b) = max_i alpha_i . b
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_scatter_points(const float *__restrict__ Bset, int nb, int N,
                                                                     const int *__restrict__ perm, int S, int RT,
-                                                                    int R, float *__restrict__ Ap) {
-    tiled_gather(Bset, nb, N, perm, S, RT, R, Ap);
+                                                                    float *__restrict__ Ap) {
+    tiled_gather(Bset, N, perm, S, RT, nb, Ap);
 }
 
 __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int npieces, const float *__restrict__ slab,
@@ -798,15 +788,15 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int 
     float bv = -INFINITY;
     int bi = 0x7fffffff;
     for (int i = tid; i < nG; i += blockDim.x) {
-        // pieces in order, in batches of eight loads in flight
+        // pieces in order, in batches of sixteen loads in flight
         const float *col = slab + static_cast<size_t>(j) * nG + i;
         float s = 0.0f;
-        for (int p0 = 0; p0 < npieces; p0 += 8) {
-            float v[8];
+        for (int p0 = 0; p0 < npieces; p0 += 16) {
+            float v[16];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) v[t] = p0 + t < npieces ? __ldg(col + (p0 + t) * slab_elems) : 0.0f;
+            for (int t = 0; t < 16; ++t) v[t] = p0 + t < npieces ? __ldg(col + (p0 + t) * slab_elems) : 0.0f;
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
+            for (int t = 0; t < 16; ++t)
                 if (p0 + t < npieces) s += v[t];
         }
         if (s > bv) {
@@ -1102,7 +1092,7 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     const int nB = h->nB, M = 5 * nB, Kp = h->Kp;
     const int Mt = (M + qv::kTM - 1) / qv::kTM, Nt = (nG + qv::kTN - 1) / qv::kTN;
     std::vector<int> pc;
-    make_pieces(*h, Mt * Nt, Kp, true, piece_cap(*h, M, nG), pc);
+    make_pieces(*h, Mt * Nt, Kp, true, std::min(h->max_pieces, piece_cap(*h, M, nG)), pc);
     if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
     const int npieces = static_cast<int>(pc.size() / 3);
     const int *piece = reinterpret_cast<const int *>(ws + h->off_piece);
@@ -1111,8 +1101,7 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     const int gthreads = 256, gblocks = 8 * qv_num_sms();
     h->gp_value_nG = 0;
     qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
-                                                    reinterpret_cast<const int *>(ws + h->off_perm), h->S, h->RTb,
-                                                    Nt * qv::kTN, Gp);
+                                                    reinterpret_cast<const int *>(ws + h->off_perm), h->S, h->RTb, Gp);
     if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
     qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
         reinterpret_cast<const float *>(ws + h->off_Bp), h->RTa, Gp, h->RTb, M, nG, h->S, piece, slab,
@@ -1164,7 +1153,7 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
     const int gb = 8 * qv_num_sms();
     const int Nt = (nG + qv::kTN - 1) / qv::kTN;
     if (d_G) {
-        qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, h->S, h->RTb, Nt * qv::kTN, Gp);
+        qv::k_pbvi_gather<<<gb, 256, 0, st>>>(d_G, nG, N, perm, h->S, h->RTb, Gp);
         h->gp_value_nG = nG;
     }
     // beliefs in chunks of up to max_points (the size of the Ap region)
@@ -1176,7 +1165,7 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
         if (upload_pieces(h, pc, st) != QV_OK) return QV_ERR_CUDA;
         const int npieces = static_cast<int>(pc.size() / 3);
         qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, h->S, h->RTp,
-                                                       Mt * qv::kTM, Ap);
+                                                       Ap);
         if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
         qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
             Ap, h->RTp, Gp, h->RTb, nc, nG, h->S, reinterpret_cast<const int *>(ws + h->off_piece), slab,
