@@ -40,7 +40,8 @@ namespace qv {
 namespace {
 
 constexpr int kPbThreads = 256;
-constexpr int kKC = 32;          // K depth of one contraction stage (one 128-byte row of FP32);
+constexpr int kSK = 16;          // K depth of one contraction stage (one 64-byte row of FP32)
+constexpr int kKC = 32;          // K granularity of the label runs and pieces (two stages);
                                  // label runs are padded to it
 constexpr int kTM = 128, kTN = 256;  // rows of A and of B (Gamma) per contraction CTA
 constexpr int kRowTile = 128;        // rows of one 16 KB block of the tiled operand layout
@@ -108,20 +109,21 @@ __device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
 }
 
 // Tiled operand layout of the contraction.  An operand of R rows (R padded
-// to a multiple of 128, RT = R / 128 row tiles) over Kp positions (S = Kp / 32
+// to a multiple of 128, RT = R / 128 row tiles) over Kp positions (S = Kp / 16
 // stages) is two planes, the TF32 heads and then the tails, each S x RT
-// blocks of 128 rows x 32 positions (16 KB), stage-major so that the row
-// tiles of one stage are adjacent.  Inside a block, row r holds its 32 values
-// in eight 16-byte chunks, chunk c stored at slot c ^ (r & 7): the K-major,
-// 128-byte-swizzled image the tensor core reads, so one bulk copy moves a
-// block (or adjacent row tiles) from HBM into shared memory unchanged.
+// blocks of 128 rows x 16 positions (8 KB), stage-major so that the row tiles
+// of one stage are adjacent.  Inside a block, row r holds its 16 values in
+// four 16-byte chunks, chunk c stored at slot c ^ ((r >> 1) & 3): the
+// K-major, 64-byte-swizzled image the tensor core reads (8-row groups of
+// 512 bytes), so one bulk copy moves a block (or adjacent row tiles) from
+// HBM into shared memory unchanged.
+__device__ __forceinline__ int tiled_slot(int r, int kin) { return (((kin >> 2) ^ ((r >> 1) & 3)) << 2) | (kin & 3); }
 __device__ __forceinline__ size_t tiled_off(int row, int k, int S, int RT) {
-    const int rt = row >> 7, r = row & 127, s = k >> 5, kin = k & 31;
-    return (static_cast<size_t>(s) * RT + rt) * (kRowTile * kKC) + r * kKC + ((((kin >> 2) ^ (r & 7))) << 2) +
-           (kin & 3);
+    const int rt = row >> 7, r = row & 127, s = k >> 4, kin = k & 15;
+    return (static_cast<size_t>(s) * RT + rt) * (kRowTile * kSK) + r * kSK + tiled_slot(r, kin);
 }
 __host__ __device__ __forceinline__ size_t tiled_plane(int S, int RT) {
-    return static_cast<size_t>(S) * RT * (kRowTile * kKC);
+    return static_cast<size_t>(S) * RT * (kRowTile * kSK);
 }
 // Writes x split into the head and tail planes at tiled position (row, k).
 __device__ __forceinline__ void tiled_store(float *T, int row, int k, int S, int RT, float x) {
@@ -312,20 +314,20 @@ __global__ void k_pbvi_reward(PbModel m, const float *__restrict__ Bset, int nB,
 // i < R of the operand is G_i at the live cells (0 at padding positions).
 // Rows R .. of the last row tile are left as they are: an MMA row (or
 // column) only feeds its own output row (or column), which the contraction
-// does not store.  One thread per head element, a row's 32 values of a stage
-// by 32 consecutive threads (one 128-byte segment per plane).
+// does not store.  One thread per head element, a row's 16 values of a stage
+// by 16 consecutive threads (one 64-byte segment per plane).
 __device__ __forceinline__ void tiled_gather(const float *__restrict__ G, int N, const int *__restrict__ perm, int S,
                                              int RT, int R, float *__restrict__ Gp) {
     const size_t plane = tiled_plane(S, RT);
-    const size_t per_stage = static_cast<size_t>(R) * kKC;
+    const size_t per_stage = static_cast<size_t>(R) * kSK;
     const size_t total = static_cast<size_t>(S) * per_stage;
     for (size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
          t += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const int s = static_cast<int>(t / per_stage);
         const int rem = static_cast<int>(t - static_cast<size_t>(s) * per_stage);
-        const int i = rem >> 5, slot = rem & 31;
-        const int k = s * kKC + ((((slot >> 2) ^ (i & 7))) << 2) + (slot & 3);
-        const size_t u = (static_cast<size_t>(s) * RT + (i >> 7)) * (kRowTile * kKC) + (i & 127) * kKC + slot;
+        const int i = rem >> 4, slot = rem & 15;
+        const int k = s * kSK + tiled_slot(i & 127, slot);  // the swizzle is its own inverse
+        const size_t u = (static_cast<size_t>(s) * RT + (i >> 7)) * (kRowTile * kSK) + (i & 127) * kSK + slot;
         const int y = __ldg(perm + k);
         const float x = y >= 0 ? __ldg(G + static_cast<size_t>(i) * N + y) : 0.0f;
         float hi, lo;
@@ -351,19 +353,19 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restr
 // (x = hi + lo) and each product is formed as hi.hi + hi.lo + lo.hi, which
 // restores FP32-level accuracy (the dropped lo.lo term is below 2^-21 of the
 // product).  The operands sit in HBM in the tiled layout (tiled_off), so a
-// stage of 32 positions is four bulk copies (A heads and tails, 16 KB each;
-// B heads and tails, 32 KB each) into one of two 96 KB shared-memory
-// buffers.  Lane 0 of warp 0 issues the copies and the twelve MMAs of a stage
+// stage of 16 positions is four bulk copies (A heads and tails, 8 KB each;
+// B heads and tails, 16 KB each) into one of four 48 KB shared-memory
+// buffers.  Lane 0 of warp 0 issues the copies and the six MMAs of a stage
 // (K = 8 each) and commits them to the buffer's "empty" barrier; the copy of
-// stage s + 1 goes out once the MMAs of stage s - 1 have released its
-// buffer, while those of stage s run.  The four warps then read the
+// stage s + 3 goes out once the MMAs of stage s - 1 have released its
+// buffer, so it has three stages of MMAs to land.  The four warps then read the
 // accumulator back (warp w owns lanes 32w .. 32w + 31, one row each).  Every
 // wait is bounded; a wait that gives up sets *status, lets the copies and
 // MMAs in flight land and still frees the tensor memory.
 constexpr int kTcThreads = 128;
-constexpr int kTcStages = 2;
-constexpr int kTcAFloats = kTM * kKC, kTcBFloats = kTN * kKC;  // one plane of one stage
-constexpr int kTcStageFloats = 2 * kTcAFloats + 2 * kTcBFloats;  // A hi, A lo, B hi, B lo: 96 KB
+constexpr int kTcStages = 4;
+constexpr int kTcAFloats = kTM * kSK, kTcBFloats = kTN * kSK;  // one plane of one stage
+constexpr int kTcStageFloats = 2 * kTcAFloats + 2 * kTcBFloats;  // A hi, A lo, B hi, B lo: 48 KB
 constexpr unsigned kTcStageBytes = kTcStageFloats * sizeof(float);
 constexpr size_t kTcSmem = kTcStages * static_cast<size_t>(kTcStageBytes) + 1024;
 constexpr int kTcTmemCols = kTN;  // FP32 accumulator: one column per B row
@@ -372,12 +374,12 @@ __device__ __forceinline__ uint32_t tc_smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory descriptor of a K-major tile with the 128-byte swizzle:
-// start address, stride of 1024 bytes between groups of 8 rows, descriptor
-// version 1, layout code 2 (128-byte swizzle).
+// Shared-memory descriptor of a K-major tile with the 64-byte swizzle:
+// start address, stride of 512 bytes between groups of 8 rows, descriptor
+// version 1, layout code 4 (64-byte swizzle).
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    return static_cast<uint64_t>((saddr >> 4) & 0x3FFF) | (static_cast<uint64_t>(1024 >> 4) << 32) |
-           (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(2) << 61);
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFF) | (static_cast<uint64_t>(512 >> 4) << 32) |
+           (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(4) << 61);
 }
 
 // Bounded wait for phase `parity` of `bar`, polled by the whole warp.
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
-    const int s0 = k0 / kKC, nst = (k1 - k0) / kKC;
+    const int s0 = k0 / kSK, nst = (k1 - k0) / kSK;
     const size_t planeA = tiled_plane(S, RTa), planeB = tiled_plane(S, RTb);
     const int rta = m0 / kRowTile, rtb = n0 / kRowTile;
     int fail = 0;
@@ -434,8 +436,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
             if (lane == 0) {
                 float *buf = st + (s % kTcStages) * kTcStageFloats;
                 uint64_t *bar = &full[s % kTcStages];
-                const size_t oa = (static_cast<size_t>(s0 + s) * RTa + rta) * (kRowTile * kKC);
-                const size_t ob = (static_cast<size_t>(s0 + s) * RTb + rtb) * (kRowTile * kKC);
+                const size_t oa = (static_cast<size_t>(s0 + s) * RTa + rta) * (kRowTile * kSK);
+                const size_t ob = (static_cast<size_t>(s0 + s) * RTb + rtb) * (kRowTile * kSK);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)),
                              "r"(kTcStageBytes)
                              : "memory");
@@ -469,7 +471,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
                 const uint64_t bh = tc_desc(tc_smem_u32(b + 2 * kTcAFloats));
                 const uint64_t bl = tc_desc(tc_smem_u32(b + 2 * kTcAFloats + kTcBFloats));
 #pragma unroll
-                for (int kk = 0; kk < kKC / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
+                for (int kk = 0; kk < kSK / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
                     const uint64_t o = 2ull * kk;
                     const uint32_t acc = (s == 0 && kk == 0) ? 0u : 1u;
                     asm volatile(
@@ -861,7 +863,7 @@ struct qv_pbvi {
                                  // backup has overwritten Gp since
     int nbands;                  // bands of k_pbvi_predict
     int band_cells;
-    int S;                       // contraction stages, Kp / 32
+    int S;                       // contraction stages, Kp / 16
     int RTa, RTb, RTp;           // row tiles of the tiled operands Bp (5 x max_points rows),
                                  // Gp (max_vectors rows, an even count) and Ap (max_points rows)
 };
@@ -958,7 +960,7 @@ extern "C" qv_status qv_pbvi_create(const qv_model_t *m, int32_t max_points, qv_
     h->off_pos = take(N * sizeof(int));
     h->off_perm = take(Kp * sizeof(int));
     h->off_piece = take(3 * h->piece_table * sizeof(int));
-    h->S = h->Kp / qv::kKC;
+    h->S = h->Kp / qv::kSK;
     h->RTa = static_cast<int>((5 * P + qv::kRowTile - 1) / qv::kRowTile);
     h->RTb = static_cast<int>(2 * ((G + qv::kTN - 1) / qv::kTN));
     h->RTp = static_cast<int>((P + qv::kRowTile - 1) / qv::kRowTile);
@@ -1063,7 +1065,7 @@ extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB
     float *Bp = reinterpret_cast<float *>(ws + h->off_Bp);
     // zero the row tiles the contraction reads (both planes: 2 S stage rows
     // of RTa blocks, the first Mt of each), then scatter the live cells
-    const size_t blk = static_cast<size_t>(qv::kRowTile) * qv::kKC * sizeof(float);
+    const size_t blk = static_cast<size_t>(qv::kRowTile) * qv::kSK * sizeof(float);
     const int Mt = (5 * nB + qv::kRowTile - 1) / qv::kRowTile;
     if (qv_check_cuda(cudaMemset2DAsync(Bp, h->RTa * blk, 0, Mt * blk, 2 * static_cast<size_t>(h->S), st),
                       "memset") != QV_OK)
