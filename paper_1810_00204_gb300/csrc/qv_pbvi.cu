@@ -602,33 +602,47 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
     __syncthreads();
     for (int p = tid; p < npieces; p += kSelThreads) s_empty[plabel[p]] = 0;
     const int nchunks = (nG + chunk - 1) / chunk;
-    // D_z and D of vectors i0 .. i0 + n - 1 of row (b, a); pieces in batches
-    // of eight loads so each thread has several in flight
+    // D_z and D of vectors i0 .. i0 + n - 1 of row (b, a): each thread takes
+    // two vectors at a time, pieces in batches of eight, sixteen loads in
+    // flight
     auto fill = [&](size_t row, int i0, int n) {
-        for (int i = tid; i < n; i += kSelThreads) {
-            const size_t col = row + i0 + i;
-            float d = 0.0f, dz = 0.0f;
+        for (int ia = tid; ia < n; ia += 2 * kSelThreads) {
+            const int ib = ia + kSelThreads;
+            const bool two = ib < n;
+            const float *ca = slab + row + i0 + ia, *cb = slab + row + i0 + (two ? ib : ia);
+            float d[2] = {0.0f, 0.0f}, dz[2] = {0.0f, 0.0f};
             for (int p0 = 0; p0 < npieces; p0 += 8) {
-                float v[8];
+                float v[2][8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = p0 + j < npieces ? __ldg(slab + static_cast<size_t>(p0 + j) * slab_elems + col) : 0.0f;
+                for (int j = 0; j < 8; ++j) {
+                    const bool in = p0 + j < npieces;
+                    const size_t o = static_cast<size_t>(p0 + j) * slab_elems;
+                    v[0][j] = in ? __ldg(ca + o) : 0.0f;
+                    v[1][j] = in && two ? __ldg(cb + o) : 0.0f;
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int p = p0 + j;
                     if (p < npieces) {
-                        d += v[j];
-                        dz += v[j];
+                        d[0] += v[0][j];
+                        d[1] += v[1][j];
+                        dz[0] += v[0][j];
+                        dz[1] += v[1][j];
                         if (plabel[p + 1] != plabel[p]) {
-                            Dz[plabel[p] * chunk + i] = dz;
-                            dz = 0.0f;
+                            Dz[plabel[p] * chunk + ia] = dz[0];
+                            if (two) Dz[plabel[p] * chunk + ib] = dz[1];
+                            dz[0] = dz[1] = 0.0f;
                         }
                     }
                 }
             }
-            D[i] = d;
+            D[ia] = d[0];
+            if (two) D[ib] = d[1];
             for (int z = 0; z < m.nz; ++z)
-                if (s_empty[z]) Dz[z * chunk + i] = 0.0f;
+                if (s_empty[z]) {
+                    Dz[z * chunk + ia] = 0.0f;
+                    if (two) Dz[z * chunk + ib] = 0.0f;
+                }
         }
     };
     for (int a = 0; a < 5; ++a) {
