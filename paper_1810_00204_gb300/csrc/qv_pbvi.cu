@@ -795,29 +795,57 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_scatter_points(const float 
     tiled_gather(Bset, N, perm, S, RT, nb, Ap);
 }
 
-__global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int npieces, const float *__restrict__ slab,
-                                                            float *__restrict__ value, int *__restrict__ arg) {
+// One CTA per belief j.  The threads form `groups` groups of cols =
+// blockDim / groups columns; group g adds a contiguous run of the pieces
+// (in order) for its columns, then the group sums are added in group order
+// and the CTA takes the best column (ties to the lowest index).
+constexpr int kRmThreads = 1024;
+// Piece groups and threads of one CTA: several groups when the beliefs are
+// too few to fill the GPU with one CTA each, one otherwise.
+void rowmax_shape(int nb, int nG, int &groups, int &threads) {
+    const int cols = std::max(32, (nG + 31) & ~31);
+    groups = nb >= qv_num_sms() ? 1 : std::max(1, std::min(8, kRmThreads / cols));
+    threads = std::min(kRmThreads, groups * cols);
+}
+
+__global__ void __launch_bounds__(kRmThreads) k_pbvi_rowmax(int nb, int nG, int npieces, int groups,
+                                                            const float *__restrict__ slab, float *__restrict__ value,
+                                                            int *__restrict__ arg) {
+    __shared__ float part[kRmThreads];
+    __shared__ float s_v[kRmThreads / 32];
+    __shared__ int s_i[kRmThreads / 32];
     const int j = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    __shared__ float s_v[kPbThreads / 32];
-    __shared__ int s_i[kPbThreads / 32];
+    const int cols = blockDim.x / groups, g = tid / cols, c = tid - g * cols;
+    const int per = (npieces + groups - 1) / groups;
+    const int p_lo = min(npieces, g * per), p_hi = min(npieces, p_lo + per);
     const size_t slab_elems = static_cast<size_t>(nb) * nG;
     float bv = -INFINITY;
     int bi = 0x7fffffff;
-    for (int i = tid; i < nG; i += blockDim.x) {
-        // pieces in order, in batches of sixteen loads in flight
-        const float *col = slab + static_cast<size_t>(j) * nG + i;
+    for (int i0 = 0; i0 < nG; i0 += cols) {
+        const int i = i0 + c;
         float s = 0.0f;
-        for (int p0 = 0; p0 < npieces; p0 += 16) {
-            float v[16];
+        if (i < nG && g < groups) {
+            // this group's pieces in order, sixteen loads in flight
+            const float *col = slab + static_cast<size_t>(j) * nG + i;
+            for (int p0 = p_lo; p0 < p_hi; p0 += 16) {
+                float v[16];
 #pragma unroll
-            for (int t = 0; t < 16; ++t) v[t] = p0 + t < npieces ? __ldg(col + (p0 + t) * slab_elems) : 0.0f;
+                for (int t = 0; t < 16; ++t) v[t] = p0 + t < p_hi ? __ldg(col + (p0 + t) * slab_elems) : 0.0f;
 #pragma unroll
-            for (int t = 0; t < 16; ++t)
-                if (p0 + t < npieces) s += v[t];
+                for (int t = 0; t < 16; ++t)
+                    if (p0 + t < p_hi) s += v[t];
+            }
         }
-        if (s > bv) {
-            bv = s;
-            bi = i;
+        __syncthreads();
+        if (g < groups) part[tid] = s;
+        __syncthreads();
+        if (g == 0 && i < nG) {
+            float t = part[c];
+            for (int h = 1; h < groups; ++h) t += part[h * cols + c];
+            if (t > bv) {
+                bv = t;
+                bi = i;
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -836,7 +864,7 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_rowmax(int nb, int nG, int 
     if (tid == 0) {
         float v = s_v[0];
         int ii = s_i[0];
-        for (int w = 1; w < kPbThreads / 32; ++w)
+        for (int w = 1; w < static_cast<int>(blockDim.x / 32); ++w)
             if (s_v[w] > v || (s_v[w] == v && s_i[w] < ii)) {
                 v = s_v[w];
                 ii = s_i[w];
@@ -1186,8 +1214,10 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
         qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
             Ap, h->RTp, Gp, h->RTb, nc, nG, h->S, reinterpret_cast<const int *>(ws + h->off_piece), slab,
             reinterpret_cast<int *>(ws + h->off_status));
-        qv::k_pbvi_rowmax<<<nc, qv::kPbThreads, 0, st>>>(nc, nG, npieces, slab, d_value + c0,
-                                                         d_arg ? d_arg + c0 : nullptr);
+        int groups, threads;
+        qv::rowmax_shape(nc, nG, groups, threads);
+        qv::k_pbvi_rowmax<<<nc, threads, 0, st>>>(nc, nG, npieces, groups, slab, d_value + c0,
+                                                  d_arg ? d_arg + c0 : nullptr);
     }
     return qv_check_cuda(cudaGetLastError(), "qv_pbvi_value launch");
 }
