@@ -151,6 +151,35 @@ def test_backup_many_tiles_and_pieces(api):
     _backup_case(api, w, 66, 65, 4, support=40)
 
 
+def test_backup_ragged_vector_tiles(api):
+    # 60 points (300 rows: 3 row tiles, the last ragged) by 300 vectors (two
+    # column tiles of 256, the second ragged), sparse beliefs
+    w = WL.mid(3, H=67, W=45)
+    _backup_case(api, w, 60, 300, 5, support=40)
+
+
+def test_backup_at_1024_points_sampled(api):
+    # the benchmarked size: 1024 points grown from b0 on the mid map, one
+    # backup against their 1024 vectors; the oracle's Eq. 8 backup at
+    # sampled points against the same vectors gives the same value and a*
+    w = WL.mid(0)
+    m = api.Model(w)
+    g = api.pbvi_solve(m, rounds=10, iters=1, seed=2)
+    assert g["B"].shape[0] == 1024 and g["G"].shape[0] == 1024
+    r = g["pbvi"].backup(g["G"])
+    torch.cuda.synchronize()
+    B = _flat(m, g["B"])
+    Gv = _flat(m, g["G"])
+    gv = r["value"].cpu().numpy()
+    ga = r["astar"].cpu().numpy()
+    pts = [0, 1023]  # one oracle call: its points run in parallel
+    o = O.pbvi_backup(w, B[pts], Gv)
+    for t, j in enumerate(pts):
+        scale = max(1.0, float(np.abs(o["q"][t]).max()))
+        assert abs(gv[j] - o["value"][t]) <= REL * scale * 10, j
+        _check_argmax(int(ga[j]), o["q"][t], scale, f"a* of point {j}")
+
+
 def test_value_matches_oracle(api):
     w = WL.mid(1, H=40, W=52)
     m = api.Model(w)
