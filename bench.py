@@ -123,7 +123,7 @@ def pbvi_measurement(args, dev, K, flush, stream, with_cpu=True):
     """The PBVI lower bound (Eq. 8) on the mid map: belief sets of 256 and
     1024 points grown by the expansion rounds from b0, then one Eq. 8 backup
     of every point timed with CUDA events (L2 flushed before each), with the
-    contraction's flops against the FP32 pipes' peak."""
+    contraction's flops against the TF32 tensor peak."""
     import torch
     import oracle as O
     from paper_1810_00204_gb300 import api, workloads as WL
