@@ -346,29 +346,35 @@ __global__ void __launch_bounds__(kPbThreads) k_pbvi_gather(const float *__restr
 
 // ---------------------------------------------------------------- the contraction
 // slab[p][m][n] = sum_{k in piece p} A[m][k] Bm[n][k] on the 5th-generation
-// tensor cores: grid (M tiles of 128, N tiles of 256, pieces), one CTA of
-// four warps per 128 x 256 tile, the accumulator in tensor memory (128 lanes
-// x 256 FP32 columns).  TF32 keeps 10 mantissa bits, too few for the argmax
-// decisions of Eq. 8, so both operands come split into TF32 heads and tails
-// (x = hi + lo) and each product is formed as hi.hi + hi.lo + lo.hi, which
-// restores FP32-level accuracy (the dropped lo.lo term is below 2^-21 of the
-// product).  The operands sit in HBM in the tiled layout (tiled_off), so a
-// stage of 16 positions is four bulk copies (A heads and tails, 8 KB each;
-// B heads and tails, 16 KB each) into one of four 48 KB shared-memory
-// buffers.  Lane 0 of warp 0 issues the copies and the six MMAs of a stage
-// (K = 8 each) and commits them to the buffer's "empty" barrier; the copy of
-// stage s + 3 goes out once the MMAs of stage s - 1 have released its
-// buffer, so it has three stages of MMAs to land.  The four warps then read the
-// accumulator back (warp w owns lanes 32w .. 32w + 31, one row each).  Every
-// wait is bounded; a wait that gives up sets *status, lets the copies and
-// MMAs in flight land and still frees the tensor memory.
-constexpr int kTcThreads = 128;
+// tensor cores, one 128 x 256 output tile (m tile, n tile, piece) at a time.
+// TF32 keeps 10 mantissa bits, too few for the argmax decisions of Eq. 8, so
+// both operands come split into TF32 heads and tails (x = hi + lo) and each
+// product is formed as hi.hi + hi.lo + lo.hi, which restores FP32-level
+// accuracy (the dropped lo.lo term is below 2^-21 of the product).  The
+// operands sit in HBM in the tiled layout (tiled_off), so a stage of 16
+// positions is four bulk copies (A heads and tails, 8 KB each; B heads and
+// tails, 16 KB each) into one of four 48 KB shared-memory buffers.
+//
+// The kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... with three roles.  Warp 0 issues the copies,
+// running up to four stages ahead across tile boundaries; warp 1 issues the
+// six MMAs of each stage (K = 8 each) into one of two TMEM accumulators of
+// 256 columns and commits them to the buffer's "empty" barrier, and each
+// finished tile to its accumulator's "full" barrier; warps 2-5 read a
+// finished accumulator back (warp w owns TMEM lanes 32 (w % 4) ..) and store
+// it, while the MMAs of the next tile run in the other accumulator.  Every
+// wait is bounded and also ends when another role has given up; a CTA that
+// gave up sets *status, lets its copies and MMAs in flight land and still
+// frees the tensor memory.
+constexpr int kTcThreads = 192;
 constexpr int kTcStages = 4;
 constexpr int kTcAFloats = kTM * kSK, kTcBFloats = kTN * kSK;  // one plane of one stage
 constexpr int kTcStageFloats = 2 * kTcAFloats + 2 * kTcBFloats;  // A hi, A lo, B hi, B lo: 48 KB
 constexpr unsigned kTcStageBytes = kTcStageFloats * sizeof(float);
 constexpr size_t kTcSmem = kTcStages * static_cast<size_t>(kTcStageBytes) + 1024;
-constexpr int kTcTmemCols = kTN;  // FP32 accumulator: one column per B row
+constexpr int kTcAccCols = kTN;                // FP32 accumulator: one column per B row
+constexpr int kTcTmemCols = 2 * kTcAccCols;    // two accumulators
+constexpr int kTcSpin = 1 << 24;               // polls of one wait before it gives up
 
 __device__ __forceinline__ uint32_t tc_smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -382,40 +388,77 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
            (static_cast<uint64_t>(1) << 46) | (static_cast<uint64_t>(4) << 61);
 }
 
-// Bounded wait for phase `parity` of `bar`, polled by the whole warp.
-__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(tc_smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+__device__ __forceinline__ bool tc_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(tc_smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`, polled by the whole warp (the
+// answer is made warp-uniform, so the warp stays converged); gives up (and
+// raises *fail) after kTcSpin polls, or as soon as *fail is raised.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *fail) {
+    for (int it = 0; it < kTcSpin; ++it) {
+        if (__any_sync(0xffffffffu, tc_try(bar, parity))) return true;
+        if ((it & 63) == 63 && __shfl_sync(0xffffffffu, *fail, 0)) return false;
     }
+    *fail = 1;
     return false;
+}
+
+// Bounded wait that ignores *fail: the clean-up after a role gave up.
+__device__ __forceinline__ void tc_drain(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 20); ++it)
+        if (__any_sync(0xffffffffu, tc_try(bar, parity))) return;
+}
+
+struct TcTile {
+    int m0, n0, p, s0, nst;
+};
+__device__ __forceinline__ TcTile tc_tile(int t, int Mt, int Nt, const int *piece) {
+    TcTile r;
+    const int mt = t % Mt, rest = t / Mt;
+    r.n0 = (rest % Nt) * kTN;
+    r.p = rest / Nt;
+    r.m0 = mt * kTM;
+    const int k0 = __ldg(piece + 3 * r.p), k1 = __ldg(piece + 3 * r.p + 1);
+    r.s0 = k0 / kSK;
+    r.nst = (k1 - k0) / kSK;
+    return r;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__restrict__ A, int RTa,
                                                                const float *__restrict__ Bm, int RTb, int M, int N,
-                                                               int S, const int *__restrict__ piece,
+                                                               int S, int Mt, int Nt, int ntiles,
+                                                               const int *__restrict__ piece,
                                                                float *__restrict__ slab, int *__restrict__ status) {
     extern __shared__ unsigned char tc_raw[];
-    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
+    __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    __shared__ int s_loaded, s_consumed;  // stages whose copies / MMAs were issued
     float *st = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
-    const int p = blockIdx.z;
-    const int k0 = __ldg(piece + 3 * p), k1 = __ldg(piece + 3 * p + 1);
-    const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int *fail = &s_fail;
     if (tid == 0) {
         for (int i = 0; i < kTcStages; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&full[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&empty[i])));
         }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(&acc_full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tc_smem_u32(&acc_empty[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
+        s_fail = 0;
+        s_loaded = 0;
+        s_consumed = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          tc_smem_u32(&s_tmem)),
                      "n"(kTcTmemCols));
@@ -425,128 +468,154 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = s_tmem;
-    const int s0 = k0 / kSK, nst = (k1 - k0) / kSK;
     const size_t planeA = tiled_plane(S, RTa), planeB = tiled_plane(S, RTb);
-    const int rta = m0 / kRowTile, rtb = n0 / kRowTile;
-    int fail = 0;
-    if (warp == 0 && nst > 0) {
-        // stage s of this piece: the A row tile and the two B row tiles of
-        // global stage s0 + s, heads and tails
-        auto load = [&](int s) {
-            if (lane == 0) {
-                float *buf = st + (s % kTcStages) * kTcStageFloats;
-                uint64_t *bar = &full[s % kTcStages];
-                const size_t oa = (static_cast<size_t>(s0 + s) * RTa + rta) * (kRowTile * kSK);
-                const size_t ob = (static_cast<size_t>(s0 + s) * RTb + rtb) * (kRowTile * kSK);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)),
-                             "r"(kTcStageBytes)
-                             : "memory");
-                const void *src[4] = {A + oa, A + oa + planeA, Bm + ob, Bm + ob + planeB};
-                float *dst[4] = {buf, buf + kTcAFloats, buf + 2 * kTcAFloats, buf + 2 * kTcAFloats + kTcBFloats};
-                const unsigned bytes[4] = {kTcAFloats * 4u, kTcAFloats * 4u, kTcBFloats * 4u, kTcBFloats * 4u};
+    if (warp == 0) {
+        // ---- copies
+        int g = 0;
+        for (int t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x) {
+            const TcTile tl = tc_tile(t, Mt, Nt, piece);
+            const int rta = tl.m0 / kRowTile, rtb = tl.n0 / kRowTile;
+            for (int s = 0; s < tl.nst; ++s, ++g) {
+                const int buf = g % kTcStages;
+                if (g >= kTcStages && !tc_wait(&empty[buf], ((g / kTcStages) - 1) & 1, fail)) break;
+                if (lane == 0) {
+                    float *b = st + buf * kTcStageFloats;
+                    uint64_t *bar = &full[buf];
+                    const size_t oa = (static_cast<size_t>(tl.s0 + s) * RTa + rta) * (kRowTile * kSK);
+                    const size_t ob = (static_cast<size_t>(tl.s0 + s) * RTb + rtb) * (kRowTile * kSK);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_smem_u32(bar)),
+                                 "r"(kTcStageBytes)
+                                 : "memory");
+                    const void *src[4] = {A + oa, A + oa + planeA, Bm + ob, Bm + ob + planeB};
+                    float *dst[4] = {b, b + kTcAFloats, b + 2 * kTcAFloats, b + 2 * kTcAFloats + kTcBFloats};
+                    const unsigned bytes[4] = {kTcAFloats * 4u, kTcAFloats * 4u, kTcBFloats * 4u, kTcBFloats * 4u};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            tc_smem_u32(dst[i])),
-                        "l"(src[i]), "r"(bytes[i]), "r"(tc_smem_u32(bar))
-                        : "memory");
-            }
-            __syncwarp();
-        };
-        // instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, N = 256, M = 128
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
-        int loaded = 0, committed = 0;  // stages whose copies / MMAs were issued
-        for (; loaded < nst && loaded < kTcStages; ++loaded) load(loaded);
-        for (int s = 0; s < nst; ++s) {
-            const int buf = s % kTcStages;
-            if (!tc_wait(&full[buf], (s / kTcStages) & 1)) {
-                fail = 1;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (lane == 0) {
-                const float *b = st + buf * kTcStageFloats;
-                const uint64_t ah = tc_desc(tc_smem_u32(b)), al = tc_desc(tc_smem_u32(b + kTcAFloats));
-                const uint64_t bh = tc_desc(tc_smem_u32(b + 2 * kTcAFloats));
-                const uint64_t bl = tc_desc(tc_smem_u32(b + 2 * kTcAFloats + kTcBFloats));
-#pragma unroll
-                for (int kk = 0; kk < kSK / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
-                    const uint64_t o = 2ull * kk;
-                    const uint32_t acc = (s == 0 && kk == 0) ? 0u : 1u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ah + o), "l"(bh + o), "r"(idesc), "r"(acc));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem),
-                                 "l"(ah + o), "l"(bl + o), "r"(idesc));
-                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(tmem),
-                                 "l"(al + o), "l"(bh + o), "r"(idesc));
+                    for (int i = 0; i < 4; ++i)
+                        asm volatile(
+                            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                            "[%3];" ::"r"(tc_smem_u32(dst[i])),
+                            "l"(src[i]), "r"(bytes[i]), "r"(tc_smem_u32(bar))
+                            : "memory");
+                    s_loaded = g + 1;
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    tc_smem_u32(&empty[buf])));
+                __syncwarp();
             }
-            __syncwarp();
-            committed = s + 1;
-            // the copy of the next stage that is not yet in flight reuses the
-            // buffer of stage s - 1: wait for that stage's MMAs first
-            if (loaded < nst && s >= 1) {
-                const int pb = (s - 1) % kTcStages;
-                if (!tc_wait(&empty[pb], ((s - 1) / kTcStages) & 1)) {
-                    fail = 1;
+        }
+    } else if (warp == 1) {
+        // ---- MMAs: FP32 accumulator, TF32 A and B, both K-major, N = 256, M = 128
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
+        int g = 0, j = 0;
+        for (int t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x, ++j) {
+            const TcTile tl = tc_tile(t, Mt, Nt, piece);
+            const int acc = j & 1;
+            // the epilogue of tile j - 2 has drained this accumulator
+            if (j >= 2 && !tc_wait(&acc_empty[acc], ((j >> 1) - 1) & 1, fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t d = tmem + static_cast<uint32_t>(acc * kTcAccCols);
+            bool ok = true;
+            for (int s = 0; s < tl.nst; ++s, ++g) {
+                const int buf = g % kTcStages;
+                if (!tc_wait(&full[buf], (g / kTcStages) & 1, fail)) {
+                    ok = false;
                     break;
                 }
-                load(loaded++);
-            }
-        }
-        // the last commit covers every MMA issued before it
-        if (!fail && !tc_wait(&empty[(nst - 1) % kTcStages], ((nst - 1) / kTcStages) & 1)) fail = 1;
-        if (fail) {
-            if (lane == 0) atomicOr(status, 1);
-            // let the copies and MMAs in flight land before the memory is freed
-            for (int s = committed; s < loaded; ++s) tc_wait(&full[s % kTcStages], (s / kTcStages) & 1);
-            if (committed > 0) tc_wait(&empty[(committed - 1) % kTcStages], ((committed - 1) / kTcStages) & 1);
-        }
-    }
-    const bool ok = !__syncthreads_or(fail);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
-        float *out = slab + static_cast<size_t>(p) * M * N;
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kTN && n0 + c0 < N; c0 += 16) {
-            uint32_t r[16];
-            if (nst > 0) {
-                const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                if (lane == 0) {
+                    const float *b = st + buf * kTcStageFloats;
+                    const uint64_t ah = tc_desc(tc_smem_u32(b)), al = tc_desc(tc_smem_u32(b + kTcAFloats));
+                    const uint64_t bh = tc_desc(tc_smem_u32(b + 2 * kTcAFloats));
+                    const uint64_t bl = tc_desc(tc_smem_u32(b + 2 * kTcAFloats + kTcBFloats));
 #pragma unroll
-                for (int j = 0; j < 16; ++j) r[j] = 0u;
+                    for (int kk = 0; kk < kSK / 8; ++kk) {  // K = 8 per MMA: 32 bytes further along the rows
+                        const uint64_t o = 2ull * kk;
+                        const uint32_t accum = (s == 0 && kk == 0) ? 0u : 1u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                            "l"(ah + o), "l"(bh + o), "r"(idesc), "r"(accum));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d),
+                                     "l"(ah + o), "l"(bl + o), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d),
+                                     "l"(al + o), "l"(bh + o), "r"(idesc));
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            tc_smem_u32(&empty[buf])));
+                    s_consumed = g + 1;
+                }
+                __syncwarp();
             }
-            if (row < M) {
-                float *dst = out + static_cast<size_t>(row) * N + n0 + c0;
-                if (n0 + c0 + 16 <= N && (N & 3) == 0) {
-#pragma unroll
-                    for (int j = 0; j < 16; j += 4)
-                        *reinterpret_cast<float4 *>(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+            if (!ok) break;
+            // every MMA of the tile done: the accumulator is ready
+            if (lane == 0)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tc_smem_u32(&acc_full[acc])));
+            __syncwarp();
+        }
+    } else {
+        // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) ..
+        const int q = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles && !*fail; t += gridDim.x, ++j) {
+            const TcTile tl = tc_tile(t, Mt, Nt, piece);
+            const int acc = j & 1;
+            if (!tc_wait(&acc_full[acc], (j >> 1) & 1, fail)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            float *out = slab + static_cast<size_t>(tl.p) * M * N;
+            const int row = tl.m0 + q * 32 + lane;
+            for (int c0 = 0; c0 < kTN && tl.n0 + c0 < N; c0 += 16) {
+                uint32_t r[16];
+                if (tl.nst > 0) {
+                    const uint32_t taddr = tmem + (static_cast<uint32_t>(q * 32) << 16) +
+                                           static_cast<uint32_t>(acc * kTcAccCols + c0);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                          "=r"(r[14]), "=r"(r[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (n0 + c0 + j < N) dst[j] = __uint_as_float(r[j]);
+                    for (int i = 0; i < 16; ++i) r[i] = 0u;
+                }
+                if (row < M) {
+                    float *dst = out + static_cast<size_t>(row) * N + tl.n0 + c0;
+                    if (tl.n0 + c0 + 16 <= N && (N & 3) == 0) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4 *>(dst + i) =
+                                make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+                                            __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (tl.n0 + c0 + i < N) dst[i] = __uint_as_float(r[i]);
+                    }
                 }
             }
+            // the accumulator may be overwritten once every epilogue warp has read it
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_smem_u32(&acc_empty[acc]))
+                             : "memory");
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcTmemCols));
+    if (s_fail) {
+        // let the copies and MMAs in flight land before the memory is freed
+        if (warp == 0) {
+            const int ld = s_loaded, cs = s_consumed;
+            for (int g = cs; g < ld; ++g) tc_drain(&full[g % kTcStages], (g / kTcStages) & 1);
+            if (cs > 0) tc_drain(&empty[(cs - 1) % kTcStages], ((cs - 1) / kTcStages) & 1);
+            if (lane == 0) atomicOr(status, 1);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTcTmemCols));
 }
 
 // ---------------------------------------------------------------- selection
@@ -1147,9 +1216,10 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
     qv::k_pbvi_gather<<<gblocks, gthreads, 0, st>>>(d_G, nG, static_cast<int>(N),
                                                     reinterpret_cast<const int *>(ws + h->off_perm), h->S, h->RTb, Gp);
     if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
-    qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
-        reinterpret_cast<const float *>(ws + h->off_Bp), h->RTa, Gp, h->RTb, M, nG, h->S, piece, slab,
-        reinterpret_cast<int *>(ws + h->off_status));
+    const int ntiles = Mt * Nt * npieces;
+    qv::k_pbvi_scores<<<std::min(ntiles, qv_num_sms()), qv::kTcThreads, qv::kTcSmem, st>>>(
+        reinterpret_cast<const float *>(ws + h->off_Bp), h->RTa, Gp, h->RTb, M, nG, h->S, Mt, Nt, ntiles, piece,
+        slab, reinterpret_cast<int *>(ws + h->off_status));
     const qv::PbModel pm = qv::pb_model(&h->model);
     int *best = d_best ? d_best : reinterpret_cast<int *>(ws + h->off_best);
     int *astar = d_astar ? d_astar : reinterpret_cast<int *>(ws + h->off_astar);
@@ -1211,9 +1281,10 @@ extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, con
         qv::k_pbvi_scatter_points<<<gb, 256, 0, st>>>(d_b + static_cast<size_t>(c0) * N, nc, N, perm, h->S, h->RTp,
                                                        Ap);
         if (qv::tc_prepare() != QV_OK) return QV_ERR_CUDA;
-        qv::k_pbvi_scores<<<dim3(Mt, Nt, npieces), qv::kTcThreads, qv::kTcSmem, st>>>(
-            Ap, h->RTp, Gp, h->RTb, nc, nG, h->S, reinterpret_cast<const int *>(ws + h->off_piece), slab,
-            reinterpret_cast<int *>(ws + h->off_status));
+        const int ntiles = Mt * Nt * npieces;
+        qv::k_pbvi_scores<<<std::min(ntiles, qv_num_sms()), qv::kTcThreads, qv::kTcSmem, st>>>(
+            Ap, h->RTp, Gp, h->RTb, nc, nG, h->S, Mt, Nt, ntiles, reinterpret_cast<const int *>(ws + h->off_piece),
+            slab, reinterpret_cast<int *>(ws + h->off_status));
         int groups, threads;
         qv::rowmax_shape(nc, nG, groups, threads);
         qv::k_pbvi_rowmax<<<nc, threads, 0, st>>>(nc, nG, npieces, groups, slab, d_value + c0,
