@@ -642,8 +642,20 @@ int select_chunk(int nz, int nG, int npieces) {
     if (c < nG) c = std::max(32, c & ~31);
     return c;
 }
+// Piece groups of the selection: when a chunk has fewer vectors than the
+// CTA has threads, groups of threads share the pieces (at most four, and as
+// many as the shared-memory budget holds: each group keeps its own D_z and
+// D).
+__host__ __device__ inline int select_groups(int nz, int chunk) {
+    const int cols = (chunk + 31) & ~31;
+    int g = kSelThreads / cols;
+    const int fit = static_cast<int>(kSelSmemBudget / (static_cast<size_t>(nz + 1) * chunk * sizeof(float)));
+    g = g < fit ? g : fit;
+    return cols >= kSelThreads ? 1 : (g < 1 ? 1 : (g > 4 ? 4 : g));
+}
 size_t select_smem(int nz, int chunk, int npieces) {
-    return static_cast<size_t>(nz + 1) * chunk * sizeof(float) + (npieces + 1) * sizeof(int);
+    return static_cast<size_t>(select_groups(nz, chunk)) * (nz + 1) * chunk * sizeof(float) +
+           (npieces + 1) * sizeof(int);
 }
 
 __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int nB, int nG, int chunk, int npieces,
@@ -654,9 +666,11 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
                                                                 float *__restrict__ q, int *__restrict__ uniq,
                                                                 int *__restrict__ mult, int *__restrict__ nuniq) {
     extern __shared__ float sel_sm[];
-    float *Dz = sel_sm;                       // [nz][chunk]
+    const int groups = select_groups(m.nz, chunk);
+    float *Dz = sel_sm;                       // [nz][chunk] (group 0's, and the sums over the groups)
     float *D = sel_sm + m.nz * chunk;         // [chunk]
-    int *plabel = reinterpret_cast<int *>(D + chunk);  // [npieces + 1], -1 after the last
+    int *plabel = reinterpret_cast<int *>(sel_sm + static_cast<size_t>(groups) * (m.nz + 1) * chunk);
+                                              // [npieces + 1], -1 after the last
     __shared__ float s_bv[QV_MAX_BEACONS + 1], s_bs[QV_MAX_BEACONS + 1];
     __shared__ int s_bi[QV_MAX_BEACONS + 1];
     __shared__ int s_arg[5][QV_MAX_BEACONS + 1];
@@ -671,10 +685,53 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
     __syncthreads();
     for (int p = tid; p < npieces; p += kSelThreads) s_empty[plabel[p]] = 0;
     const int nchunks = (nG + chunk - 1) / chunk;
-    // D_z and D of vectors i0 .. i0 + n - 1 of row (b, a): each thread takes
-    // two vectors at a time, pieces in batches of eight, sixteen loads in
-    // flight
+    // D_z and D of vectors i0 .. i0 + n - 1 of row (b, a).  One group: each
+    // thread takes two vectors at a time, pieces in batches of eight, sixteen
+    // loads in flight.  Several groups: group g adds its share of the pieces
+    // (in order) for one vector a thread, and the group sums are then added
+    // in group order.
+    auto fill_groups = [&](size_t row, int i0, int n) {
+        const int cols = (chunk + 31) & ~31, g = tid / cols, c = tid - g * cols;
+        const int per = (npieces + groups - 1) / groups;
+        const int p_lo = min(npieces, g * per), p_hi = min(npieces, p_lo + per);
+        if (g < groups && c < n) {
+            float *dzg = sel_sm + static_cast<size_t>(g) * (m.nz + 1) * chunk, *dg = dzg + m.nz * chunk;
+            for (int z = 0; z < m.nz; ++z) dzg[z * chunk + c] = 0.0f;
+            const float *col = slab + row + i0 + c;
+            float d = 0.0f, dz = 0.0f;
+            for (int p0 = p_lo; p0 < p_hi; p0 += 16) {
+                float v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    v[j] = p0 + j < p_hi ? __ldg(col + static_cast<size_t>(p0 + j) * slab_elems) : 0.0f;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int p = p0 + j;
+                    if (p < p_hi) {
+                        d += v[j];
+                        dz += v[j];
+                        if (p + 1 == p_hi || plabel[p + 1] != plabel[p]) {
+                            dzg[plabel[p] * chunk + c] = dz;
+                            dz = 0.0f;
+                        }
+                    }
+                }
+            }
+            dg[c] = d;
+        }
+        __syncthreads();
+        for (int t = tid; t < (m.nz + 1) * n; t += kSelThreads) {
+            const int z = t / n, i = t - z * n;
+            float v = sel_sm[static_cast<size_t>(z) * chunk + i];
+            for (int h = 1; h < groups; ++h) v += sel_sm[(static_cast<size_t>(h) * (m.nz + 1) + z) * chunk + i];
+            sel_sm[static_cast<size_t>(z) * chunk + i] = v;
+        }
+    };
     auto fill = [&](size_t row, int i0, int n) {
+        if (groups > 1) {
+            fill_groups(row, i0, n);
+            return;
+        }
         for (int ia = tid; ia < n; ia += 2 * kSelThreads) {
             const int ib = ia + kSelThreads;
             const bool two = ib < n;
