@@ -16,6 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qv_oracle.c")
+_SRC9 = os.path.join(_HERE, "qv_oracle9.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -25,11 +26,11 @@ A = 5
 
 def build(force: bool = False) -> str:
     """Compile qv_oracle.c into liboracle.so (gcc, OpenMP over tree nodes)."""
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
-            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "qv_oracle.h"))):
+    srcs = [_SRC, _SRC9, os.path.join(_HERE, "qv_oracle.h"), os.path.join(_HERE, "qv_oracle9.h")]
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(map(os.path.getmtime, srcs)):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, _SRC, _SRC9, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -103,8 +104,39 @@ def lib():
         L.or_closed_loop.restype = C.c_int
         L.or_forward_sample.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_uint64, vp]
         L.or_forward_sample.restype = None
+        P9 = C.POINTER(_Problem9)
+        L.or9_tprime_row.argtypes = [P9, C.c_int, C.c_int, vp, vp, vp]
+        L.or9_tprime_row.restype = C.c_int
+        L.or9_transition_row.argtypes = [P9, C.c_int, C.c_int, vp, vp]
+        L.or9_transition_row.restype = C.c_int
+        L.or9_reward_table.argtypes = [P9, vp]
+        L.or9_reward_table.restype = None
+        L.or9_pattern.argtypes = [P9, C.c_int]
+        L.or9_pattern.restype = C.c_int
+        L.or9_obs_lik.argtypes = [P9, C.c_int, C.c_int]
+        L.or9_obs_lik.restype = C.c_double
+        L.or9_value_iteration.argtypes = [P9, C.c_double, C.c_int, C.c_int, vp, vp, vp, vp]
+        L.or9_value_iteration.restype = C.c_int
+        L.or9_predict.argtypes = [P9, vp, C.c_int, vp]
+        L.or9_predict.restype = None
+        L.or9_obs_marginal.argtypes = [P9, vp, vp]
+        L.or9_obs_marginal.restype = None
+        L.or9_correct.argtypes = [P9, vp, C.c_int, vp]
+        L.or9_correct.restype = C.c_double
+        L.or9_belief_reward.argtypes = [P9, vp, vp, C.c_int]
+        L.or9_belief_reward.restype = C.c_double
+        L.or9_leaf_value.argtypes = [P9, vp, vp, vp]
+        L.or9_leaf_value.restype = C.c_double
+        L.or9_tree_plan.argtypes = ([P9, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, vp, C.c_int]
+                                    + [vp] * 15)
+        L.or9_tree_plan.restype = C.c_int
         _lib = L
     return _lib
+
+
+class _Problem9(C.Structure):
+    _fields_ = [("H", C.c_int), ("W", C.c_int), ("occ", C.c_void_p), ("goal", C.c_int),
+                ("slip", C.c_double), ("p_sensor", C.c_double), ("gamma", C.c_double)]
 
 
 def _p(a):
@@ -610,3 +642,162 @@ def num_threads():
 def set_threads(n):
     """Threads of the oracle's parallel loops from now on."""
     lib().or_set_threads(int(n))
+
+
+# ---------------------------------------------------------------------------
+# The paper's experimental model (Sec. V): nine actions, four occupancy
+# sensors (|Z| = 16), r in {-2, -1, 0}.  Thin wrappers over qv_oracle9.c.
+A9, NZ9 = 9, 16
+
+
+class Problem9:
+    """The Sec. V model built from a Workload: its map, goal, slip (each
+    45-degree slip), p_sensor and discount (arrays kept alive)."""
+
+    def __init__(self, w, slip=None, p_sensor=None, discount=None):
+        self.w = w
+        self.H, self.W, self.n = w.H, w.W, w.H * w.W
+        self.occ = np.ascontiguousarray(w.occ.reshape(-1).astype(np.uint8))
+        self.s = _Problem9(self.H, self.W, self.occ.ctypes.data_as(C.c_void_p), int(w.goal),
+                           float(w.slip if slip is None else slip),
+                           float(w.p_sensor if p_sensor is None else p_sensor),
+                           float(w.discount if discount is None else discount))
+        self.ref = C.byref(self.s)
+
+
+def _prob9(w, **kw):
+    return w if isinstance(w, Problem9) else Problem9(w, **kw)
+
+
+def tprime_row9(w, x, a, **kw):
+    """T'(x, a, .) of the Fig. 2 reading: list of ((row, col), prob)."""
+    p = _prob9(w, **kw)
+    rr, cc, pr = (C.c_int * 3)(), (C.c_int * 3)(), (C.c_double * 3)()
+    m = lib().or9_tprime_row(p.ref, int(x), int(a), rr, cc, pr)
+    return [((rr[j], cc[j]), pr[j]) for j in range(m)]
+
+
+def transition_row9(w, x, a, **kw):
+    """Row x of T(x, a, .) of Sec. V: dict target -> probability."""
+    p = _prob9(w, **kw)
+    y, pr = (C.c_int * 3)(), (C.c_double * 3)()
+    m = lib().or9_transition_row(p.ref, int(x), int(a), y, pr)
+    return {y[j]: pr[j] for j in range(m)}
+
+
+def reward_table9(w, **kw):
+    p = _prob9(w, **kw)
+    R = np.zeros(A9 * p.n)
+    lib().or9_reward_table(p.ref, _p(R))
+    return R.reshape(A9, p.n)
+
+
+def pattern9(w, x, **kw):
+    return lib().or9_pattern(_prob9(w, **kw).ref, int(x))
+
+
+def obs_lik9(w, x, z, **kw):
+    return lib().or9_obs_lik(_prob9(w, **kw).ref, int(x), int(z))
+
+
+def value_iteration9(w, tol=None, max_sweeps=100000, truncated=0, **kw):
+    """MDP value iteration on the Sec. V model: dict(V [n], Q [9][n], sweeps,
+    residual, converged)."""
+    p = _prob9(w, **kw)
+    tol = p.w.vi_tol if tol is None else tol
+    V = np.zeros(p.n)
+    Q = np.zeros(A9 * p.n)
+    sw = C.c_int(0)
+    res = C.c_double(0.0)
+    st = lib().or9_value_iteration(p.ref, float(tol), int(max_sweeps), int(truncated), _p(V), _p(Q),
+                                   C.byref(sw), C.byref(res))
+    return dict(V=V, Q=Q.reshape(A9, p.n), sweeps=sw.value, residual=res.value, converged=st == 0)
+
+
+def predict9(w, b, a, **kw):
+    p = _prob9(w, **kw)
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    out = np.zeros(p.n)
+    lib().or9_predict(p.ref, _p(b), int(a), _p(out))
+    return out
+
+
+def obs_marginal9(w, bbar, **kw):
+    p = _prob9(w, **kw)
+    bbar = np.ascontiguousarray(np.asarray(bbar, np.float64).reshape(-1))
+    P = np.zeros(NZ9)
+    lib().or9_obs_marginal(p.ref, _p(bbar), _p(P))
+    return P
+
+
+def correct9(w, bbar, z, **kw):
+    p = _prob9(w, **kw)
+    bbar = np.ascontiguousarray(np.asarray(bbar, np.float64).reshape(-1))
+    out = np.zeros(p.n)
+    pz = lib().or9_correct(p.ref, _p(bbar), int(z), _p(out))
+    return out, pz
+
+
+def leaf_value9(w, Q, b, **kw):
+    p = _prob9(w, **kw)
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(-1))
+    b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
+    qa = np.zeros(A9)
+    v = lib().or9_leaf_value(p.ref, _p(Q), _p(b), _p(qa))
+    return v, qa
+
+
+def level_capacity9(K, depth):
+    """Worst-case V-nodes per level of the nine-action tree."""
+    caps = [1]
+    for _ in range(depth):
+        caps.append(caps[-1] * A9 * min(K, NZ9))
+    return caps
+
+
+def tree_plan9(w, Q, depth=None, K=None, seed=None, episode=None, b0=None, store_levels=-1, **kw):
+    """The sampled tree (Alg. 2-7) on the Sec. V model; returns the node
+    arrays of every level (flat, level l at off[l]) and the root."""
+    p = _prob9(w, **kw)
+    ww = p.w
+    depth = ww.depth if depth is None else depth
+    K = ww.K if K is None else K
+    seed = ww.seed if seed is None else seed
+    episode = ww.episode if episode is None else episode
+    if depth > 3:
+        raise ValueError("tree_plan9: depth <= 3")
+    caps = level_capacity9(K, depth) + [0]
+    off = np.zeros(depth + 3, np.int64)
+    off[1:len(caps) + 1] = np.cumsum(caps)
+    off[len(caps) + 1:] = off[len(caps)]
+    total = int(off[depth + 1])
+    Q = np.ascontiguousarray(np.asarray(Q, np.float64).reshape(-1))
+    b = np.ascontiguousarray(np.asarray(ww.b0 if b0 is None else b0, np.float64).reshape(-1))
+    n_level = np.zeros(depth + 1, np.int32)
+    parent = np.full(total, -1, np.int32)
+    action = np.full(total, -1, np.int32)
+    obs = np.full(total, -1, np.int32)
+    weight = np.zeros(total)
+    pz = np.zeros(total)
+    value = np.zeros(total)
+    R = np.zeros(total * A9)
+    UQ = np.zeros(total * A9)
+    samples = np.full(total * A9 * K, -1, np.int32)
+    boundary = np.zeros(total * A9 * K, np.uint8)
+    nstore = int(off[min(store_levels, depth - 1) + 1]) if store_levels >= 0 and depth > 0 else 0
+    belief = np.zeros(max(nstore, 1) * p.n) if nstore else None
+    ra = C.c_int(0)
+    rv = C.c_double(0.0)
+    rq = np.zeros(A9)
+    bc = C.c_long(0)
+    st = lib().or9_tree_plan(p.ref, _p(Q), _p(b), int(depth), int(K), int(seed), int(episode), _p(off),
+                             int(store_levels), _p(n_level), _p(parent), _p(action), _p(obs), _p(weight), _p(pz),
+                             _p(value), _p(R), _p(UQ), _p(samples), _p(boundary),
+                             _p(belief) if belief is not None else None, C.byref(ra), C.byref(rv), _p(rq),
+                             C.byref(bc))
+    if st != 0:
+        raise RuntimeError("or9_tree_plan: capacity exceeded")
+    return dict(n_level=n_level, off=off, parent=parent, action=action, obs=obs, weight=weight, pz=pz,
+                value=value, R=R.reshape(-1, A9), UQ=UQ.reshape(-1, A9), samples=samples.reshape(-1, A9, K),
+                boundary=boundary.reshape(-1, A9, K), belief=None if belief is None else belief.reshape(-1, p.n),
+                root_action=ra.value, root_value=rv.value, root_q=rq, boundary_count=bc.value)

@@ -45,11 +45,12 @@ class Workload:
     vi_max_sweeps: int = 100000
     vi_truncated: int = 0      # >0: run exactly this many sweeps
     cost: Optional[np.ndarray] = None  # float32 [H][W] per-cell cost, or None
+    p_sensor: float = 0.95     # the nine-action model's occupancy sensors: P(reading right)
 
     def __setattr__(self, name, value):
         # The model parameters are float32 numbers (the C ABI carries them as
         # float); storing them rounded lets every consumer see the same value.
-        if name in ("slip", "accuracy", "discount"):
+        if name in ("slip", "accuracy", "discount", "p_sensor"):
             value = float(np.float32(value))
         object.__setattr__(self, name, value)
 
