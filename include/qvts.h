@@ -564,6 +564,94 @@ qv_status qv_tree_plan_batched(int32_t E, const qv_model_t *models, const float 
                                void *d_ws, size_t ws_bytes, qv_plan_result_t *h_results,
                                qv_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * The paper's experimental model (Sec. V), a second model family beside the
+ * beacon model above:
+ *   - Grids are unpadded row-major [H][W], cell y = row * W + col.
+ *   - Nine actions a = 0..8 move to the neighbour N_a(x) at (row + a/3 - 1,
+ *     col + a%3 - 1); N_4(x) = x is stay.  T' (Fig. 2, not in the text) is
+ *     read as: stay keeps the robot in place; any other action reaches N_a(x)
+ *     w.p. 1 - 2*slip and each of the two cells 45 degrees to either side
+ *     w.p. slip.  Mass that T' puts on an occupied or outside cell stays on x
+ *     (the Sec. V transition equation).  The goal is absorbing.
+ *   - Four sensors read the occupancy (outside = occupied) of N_1, N_3, N_5,
+ *     N_7 (up, left, right, down) as bits 0..3 of z, |Z| = 16; each is right
+ *     w.p. p_sensor, independently.
+ *   - Stage reward r = -2 on occupied (or outside) cells, 0 at the goal, -1
+ *     elsewhere; R(x, a) = -2 for stay off the goal, else sum_y r(y) T'(x, a,
+ *     y); R = 0 at the goal and on occupied cells.
+ * The tree is Alg. 2-7 as for the beacon model: full width to `depth`, K
+ * samples of z per (V-node, action) from the same Philox streams (path code
+ * = code * 9 + a, child code = path * 16 + z), FREQ weights f/K, leaves
+ * valued by Eq. 4 against Q(., a') of qv9_value_iterate, the root action the
+ * lowest index among the maxima. */
+#define QV9_NUM_ACTIONS 9
+#define QV9_NUM_OBS 16
+#define QV9_MAX_DEPTH 3
+#define QV9_MAX_K 16
+
+typedef struct {
+    int32_t H, W;             /* grid; W <= QV_MAX_WIDTH                               */
+    const uint8_t *d_occ;     /* [H][W] device, caller-owned: 1 occupied, 0 free       */
+    int32_t goal;             /* goal cell row * W + col, must be free                 */
+    float slip;               /* each 45-degree slip, in [0, 1/3]                      */
+    float p_sensor;           /* P(a sensor reads its cell right), in [0.5, 1]         */
+    float discount;           /* gamma in (0, 1)                                       */
+} qv9_model_t;
+
+typedef struct qv9 qv9_t;
+
+typedef struct {
+    int32_t action;           /* root action, lowest index among the maxima            */
+    float value;              /* U_V of the root                                       */
+    float q[QV9_NUM_ACTIONS]; /* U_Q of the root's actions                             */
+    int32_t nodes_per_level[QV9_MAX_DEPTH + 1];
+    int64_t boundary_samples; /* draws within 1e-6 of a step of the FP32 CDF           */
+} qv9_plan_result_t;
+
+/* One level of the last plan, device pointers into the workspace (valid
+ * until the next qv9_plan or qv9_value_iterate on the handle).  Nodes are in
+ * (parent, action, z) order; belief is [count][H][W] for the internal levels
+ * and NULL for the leaf level; R and UQ are [count][9] for the internal
+ * levels and NULL for the leaf level. */
+typedef struct {
+    int32_t count;
+    const int32_t *parent, *action, *obs;
+    const float *weight, *pz, *value;
+    const float *belief;
+    const float *R, *UQ;
+} qv9_level_view_t;
+
+/* qv9_create: a handle for one model and tree shape (1 <= depth <= 3,
+ * 1 <= K <= 16).  Reads the occupancy map back to the host to build the
+ * cell words and the sensor-pattern order of the cells.  Synchronises.
+ * qv9_workspace_bytes: device scratch the handle needs (the levels'
+ * beliefs and node arrays at their worst-case sizes (9 min(K, 16))^l).
+ * qv9_set_workspace: the caller's workspace (256-byte aligned, at least
+ * qv9_workspace_bytes) and the upload of the handle's tables into it. */
+qv_status qv9_create(const qv9_model_t *model, int32_t depth, int32_t K, qv9_t **out);
+size_t qv9_workspace_bytes(const qv9_t *h);
+qv_status qv9_set_workspace(qv9_t *h, void *d_ws, size_t ws_bytes, qv_stream_t stream);
+void qv9_destroy(qv9_t *h);
+
+/* MDP value iteration on the Sec. V model (Jacobi, from V = 0): stops at
+ * the first sweep whose max-abs change is below tol, or runs exactly
+ * `truncated` sweeps when truncated > 0; then Q = R + gamma T V.
+ *   d_V  [H][W] in dtype (QV_F32 or QV_F64), caller-owned
+ *   d_Q  [9][H][W] FP32, caller-owned
+ * max_sweeps <= 131072.  QV_ERR_NOT_CONVERGED when max_sweeps ran out.
+ * Synchronises (every 16 sweeps). */
+qv_status qv9_value_iterate(qv9_t *h, int32_t dtype, double tol, int32_t max_sweeps, int32_t truncated,
+                            void *d_V, float *d_Q, int32_t *sweeps_out, double *residual_out,
+                            qv_stream_t stream);
+
+/* One plan from d_b0 ([H][W] FP32, sums to 1; its occupied cells are
+ * ignored) with leaves valued against d_Q ([9][H][W] FP32).  Synchronises
+ * once per level (the next level's size is read back). */
+qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uint64_t seed, uint32_t episode,
+                   qv9_plan_result_t *h_result, qv_stream_t stream);
+qv_status qv9_level(const qv9_t *h, int32_t level, qv9_level_view_t *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,24 @@ class qv_launch_time_t(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("level", C.c_int32), ("ms", C.c_float)]
 
 
+QV9_NUM_ACTIONS, QV9_NUM_OBS, QV9_MAX_DEPTH, QV9_MAX_K = 9, 16, 3, 16
+
+
+class qv9_model_t(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("d_occ", C.c_void_p), ("goal", C.c_int32),
+                ("slip", C.c_float), ("p_sensor", C.c_float), ("discount", C.c_float)]
+
+
+class qv9_plan_result_t(C.Structure):
+    _fields_ = [("action", C.c_int32), ("value", C.c_float), ("q", C.c_float * QV9_NUM_ACTIONS),
+                ("nodes_per_level", C.c_int32 * (QV9_MAX_DEPTH + 1)), ("boundary_samples", C.c_int64)]
+
+
+class qv9_level_view_t(C.Structure):
+    _fields_ = [("count", C.c_int32)] + [(k, C.c_void_p) for k in (
+        "parent", "action", "obs", "weight", "pz", "value", "belief", "R", "UQ")]
+
+
 # every symbol include/qvts.h declares, with (restype, argtypes)
 _vp, _i32, _sz = C.c_void_p, C.c_int32, C.c_size_t
 _M = C.POINTER(qv_model_t)
@@ -146,6 +164,14 @@ SIGNATURES = {
     "qv_tree_backward": (C.c_int, [_vp, _i32, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "qv_tree_plan": (C.c_int, [_M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
     "qv_tree_plan_batched": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(qv_plan_result_t), _vp]),
+    "qv9_create": (C.c_int, [C.POINTER(qv9_model_t), _i32, _i32, C.POINTER(_vp)]),
+    "qv9_workspace_bytes": (_sz, [_vp]),
+    "qv9_set_workspace": (C.c_int, [_vp, _vp, _sz, _vp]),
+    "qv9_destroy": (None, [_vp]),
+    "qv9_value_iterate": (C.c_int, [_vp, _i32, C.c_double, _i32, _i32, _vp, _vp, C.POINTER(_i32),
+                                    C.POINTER(C.c_double), _vp]),
+    "qv9_plan": (C.c_int, [_vp, _vp, _vp, C.c_uint64, C.c_uint32, C.POINTER(qv9_plan_result_t), _vp]),
+    "qv9_level": (C.c_int, [_vp, _i32, C.POINTER(qv9_level_view_t)]),
 }
 
 _lib = None

@@ -690,3 +690,83 @@ def qv_tree_plan_batched(models, Qs, b0s, depth=3, K=8, seed=0, episode=0, weigh
     p = Plan(models, Qs, b0s, depth, K, seed, episode, weight_mode, leaf_mode, None, stream)
     p.run(stream)
     return p.read(stream)
+
+
+class Model9:
+    """The paper's experimental model (Sec. V) on one grid: nine actions,
+    four occupancy sensors, r in {-2, -1, 0}; its value iteration and plans
+    (tree shape fixed at creation: depth <= 3, K <= 16).  Grids are unpadded
+    [H][W] tensors on the model's device."""
+
+    def __init__(self, w, depth=None, K=None, device="cuda", stream=None):
+        self.w = w
+        self.H, self.W = w.H, w.W
+        self.device = torch.device(device)
+        self.depth = w.depth if depth is None else depth
+        self.K = w.K if K is None else K
+        self.occ = torch.from_numpy(np.ascontiguousarray(w.occ.astype(np.uint8))).to(self.device)
+        self.struct = N.qv9_model_t(int(w.H), int(w.W), _ptr(self.occ), int(w.goal), float(w.slip),
+                                    float(w.p_sensor), float(w.discount))
+        h = C.c_void_p()
+        check(lib().qv9_create(C.byref(self.struct), int(self.depth), int(self.K), C.byref(h)), "qv9_create")
+        self.handle = h
+        nbytes = lib().qv9_workspace_bytes(h)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = C.c_void_p(self.ws.data_ptr() + (-self.ws.data_ptr()) % 256)
+        check(lib().qv9_set_workspace(h, self.ws_ptr, nbytes, _stream(stream)), "qv9_set_workspace")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            lib().qv9_destroy(h)
+            self.handle = None
+
+    def b0(self):
+        return torch.from_numpy(np.ascontiguousarray(self.w.b0.astype(np.float32))).to(self.device)
+
+    def value_iterate(self, dtype="f32", tol=None, max_sweeps=100000, truncated=0, stream=None):
+        """dict(V [H][W] in dtype, Q [9][H][W] FP32, sweeps, residual)."""
+        tdt = torch.float64 if dtype == "f64" else torch.float32
+        V = torch.empty((self.H, self.W), dtype=tdt, device=self.device)
+        Q = torch.empty((9, self.H, self.W), dtype=torch.float32, device=self.device)
+        sw = C.c_int32(0)
+        res = C.c_double(0.0)
+        tol = self.w.vi_tol if tol is None else tol
+        check(lib().qv9_value_iterate(self.handle, N.QV_F64 if dtype == "f64" else N.QV_F32, float(tol),
+                                      int(max_sweeps), int(truncated), _ptr(V), _ptr(Q), C.byref(sw), C.byref(res),
+                                      _stream(stream)), "qv9_value_iterate")
+        return dict(V=V, Q=Q, sweeps=sw.value, residual=res.value)
+
+    def plan(self, Q, b0=None, seed=None, episode=None, stream=None):
+        """One plan: dict(action, value, q [9], nodes_per_level, boundary)."""
+        b0 = self.b0() if b0 is None else b0.contiguous()
+        r = N.qv9_plan_result_t()
+        check(lib().qv9_plan(self.handle, _ptr(Q.contiguous()), _ptr(b0), int(self.w.seed if seed is None else seed),
+                             int(self.w.episode if episode is None else episode), C.byref(r), _stream(stream)),
+              "qv9_plan")
+        return dict(action=r.action, value=r.value, q=np.array(r.q[:]),
+                    nodes_per_level=[int(r.nodes_per_level[l]) for l in range(self.depth + 1)],
+                    boundary=int(r.boundary_samples))
+
+    def _view(self, ptr, count, dtype, shape):
+        if not ptr or count == 0:
+            return None
+        esz = torch.tensor([], dtype=dtype).element_size()
+        off = ptr - self.ws.data_ptr()
+        return self.ws[off:off + count * esz].view(dtype).view(*shape)
+
+    def level(self, l):
+        """Level l of the last plan as device tensors (views of the workspace,
+        valid until the next plan): count, parent, action, obs, weight, pz,
+        value; belief [n][H][W], R and UQ [n][9] for the internal levels."""
+        v = N.qv9_level_view_t()
+        check(lib().qv9_level(self.handle, int(l), C.byref(v)), "qv9_level")
+        n = v.count
+        out = dict(count=n)
+        for key, dt in (("parent", torch.int32), ("action", torch.int32), ("obs", torch.int32),
+                        ("weight", torch.float32), ("pz", torch.float32), ("value", torch.float32)):
+            out[key] = self._view(getattr(v, key), n, dt, (n,))
+        out["belief"] = self._view(v.belief, n * self.H * self.W, torch.float32, (n, self.H, self.W))
+        out["R"] = self._view(v.R, n * 9, torch.float32, (n, 9))
+        out["UQ"] = self._view(v.UQ, n * 9, torch.float32, (n, 9))
+        return out

@@ -1,0 +1,162 @@
+"""GPU parity of the paper's experimental model (Sec. V: nine actions, four
+occupancy sensors) through the C ABI against the model-9 oracle: value
+iteration sweep for sweep (FP64) and at convergence (FP32), whole trees on
+small maps node by node, and at the mid map's planning configuration (d = 3,
+K = 8) sampled nodes that the oracle recomputes one by one from the GPU's
+own parent beliefs.  Tree shape, actions and measurements must match
+exactly; values |d| <= 1e-5 * max(|ref|, 1) (FP32 against FP64, summed over
+the whole tree: 1e-4)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_1810_00204_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1810_00204_gb300 import api as A
+    return A
+
+
+def _close(got, ref, rel, what):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = max(1.0, float(np.abs(ref).max())) if ref.size else 1.0
+    err = float(np.abs(got - ref).max()) if ref.size else 0.0
+    assert err <= rel * scale, f"{what}: max |d| {err:.3e} > {rel:.1e} x {scale:.3g}"
+
+
+@pytest.mark.parametrize("seed", [0, 4])
+def test_value_iteration_fp64_sweeps(api, seed):
+    w = WL.tiny(seed, H=17, W=23)
+    m = api.Model9(w, depth=1, K=1)
+    for k in (1, 9, 60):
+        g = m.value_iterate("f64", truncated=k)
+        o = O.value_iteration9(w, truncated=k)
+        assert g["sweeps"] == k
+        _close(g["V"].cpu().numpy().ravel(), o["V"], 1e-12, f"V after {k} sweeps")
+        _close(g["Q"].cpu().numpy().reshape(9, -1), o["Q"], 1e-6, f"Q after {k} sweeps")
+
+
+def test_value_iteration_fp32_converged(api):
+    w = WL.mid(1, H=64, W=48)
+    m = api.Model9(w, depth=1, K=1)
+    g = m.value_iterate("f32", tol=1e-4)
+    assert g["residual"] < 1e-4
+    o = O.value_iteration9(w, truncated=g["sweeps"])
+    _close(g["V"].cpu().numpy().ravel(), o["V"], 1e-5, "V")
+    # the oracle stops at the same sweep within the FP32 residual's noise
+    oc = O.value_iteration9(w, tol=1e-4)
+    assert abs(oc["sweeps"] - g["sweeps"]) <= 2
+
+
+def _compare_tree(api, w, depth, K):
+    m = api.Model9(w, depth=depth, K=K)
+    Qo = O.value_iteration9(w)["Q"]
+    Qf = Qo.astype(np.float32)
+    Q = torch.from_numpy(Qf.reshape(9, w.H, w.W)).cuda()
+    g = m.plan(Q)
+    o = O.tree_plan9(w, Qf.astype(np.float64), depth=depth, K=K, store_levels=depth - 1)
+    assert o["boundary_count"] == 0, "pick a case without draws on a CDF step"
+    assert g["nodes_per_level"] == [int(x) for x in o["n_level"]]
+    for l in range(depth + 1):
+        lv = m.level(l)
+        n = lv["count"]
+        s = slice(int(o["off"][l]), int(o["off"][l]) + n)
+        assert np.array_equal(lv["parent"].cpu().numpy(), o["parent"][s]), l
+        assert np.array_equal(lv["action"].cpu().numpy(), o["action"][s]), l
+        assert np.array_equal(lv["obs"].cpu().numpy(), o["obs"][s]), l
+        assert np.array_equal(lv["weight"].cpu().numpy(), o["weight"][s].astype(np.float32)), l
+        _close(lv["pz"].cpu().numpy(), o["pz"][s], 1e-5, f"P(z) level {l}")
+        _close(lv["value"].cpu().numpy(), o["value"][s], 1e-4, f"values level {l}")
+        if l < depth:
+            _close(lv["R"].cpu().numpy(), o["R"][s], 1e-5, f"R(b, a) level {l}")
+            _close(lv["UQ"].cpu().numpy(), o["UQ"][s], 1e-4, f"U_Q level {l}")
+            gb = lv["belief"].cpu().numpy().reshape(n, -1)
+            ob = o["belief"][s]
+            _close(gb, ob, 1e-5, f"beliefs level {l}")
+    assert g["action"] == o["root_action"] or abs(o["root_q"][g["action"]] - o["root_value"]) <= 1e-4 * max(
+        1.0, abs(o["root_value"]))
+    _close([g["value"]], [o["root_value"]], 1e-5, "root value")
+
+
+@pytest.mark.parametrize("seed,depth,K", [(0, 2, 4), (2, 2, 3), (1, 3, 2)])
+def test_tree_matches_oracle(api, seed, depth, K):
+    w = WL.tiny(seed, H=11, W=13)
+    _compare_tree(api, w, depth, K)
+
+
+def test_tree_with_obstacle_dense_map(api):
+    w = WL.mid(3, H=24, W=20)
+    _compare_tree(api, w, 2, 4)
+
+
+def test_full_size_sampled_nodes(api):
+    # the mid map's planning configuration: 128 x 128, d = 3, K = 8
+    w = WL.mid(0)
+    m = api.Model9(w)
+    vi = m.value_iterate("f32", tol=1e-4)
+    Q = vi["Q"]
+    g = m.plan(Q)
+    Qh = Q.cpu().numpy().reshape(9, -1).astype(np.float64)
+    lv = [m.level(l) for l in range(4)]
+    assert g["nodes_per_level"][0] == 1 and all(x > 0 for x in g["nodes_per_level"])
+    # the backup identity at every internal node, in FP64 on the GPU's arrays
+    for l in range(3):
+        nxt = lv[l + 1]
+        par, act = nxt["parent"].cpu().numpy(), nxt["action"].cpu().numpy()
+        wv = (nxt["weight"].cpu().numpy().astype(np.float64) * nxt["value"].cpu().numpy())
+        s = np.zeros((lv[l]["count"], 9))
+        np.add.at(s, (par, act), wv)
+        uq = lv[l]["R"].cpu().numpy() + w.discount * s
+        _close(lv[l]["UQ"].cpu().numpy(), uq, 1e-5, f"U_Q identity level {l}")
+        _close(lv[l]["value"].cpu().numpy(), uq.max(axis=1), 1e-5, f"U_V identity level {l}")
+    # sampled children recomputed by the oracle from the GPU parent's belief
+    rng = np.random.default_rng(0)
+    for l in (0, 1, 2):
+        nxt = lv[l + 1]
+        bel = lv[l]["belief"].cpu().numpy().reshape(lv[l]["count"], -1).astype(np.float64)
+        for j in rng.choice(nxt["count"], size=min(4, nxt["count"]), replace=False):
+            i, a, z = int(nxt["parent"][j]), int(nxt["action"][j]), int(nxt["obs"][j])
+            bbar = O.predict9(w, bel[i], a)
+            P = O.obs_marginal9(w, bbar)
+            _close([float(nxt["pz"][j])], [P[z]], 1e-5, f"P(z) of node {j} level {l + 1}")
+            bz, _ = O.correct9(w, bbar, z)
+            if l + 1 < 3:
+                _close(nxt["belief"][j].cpu().numpy().ravel(), bz, 1e-5, f"belief of node {j}")
+            else:
+                v, _ = O.leaf_value9(w, Qh, bz)
+                _close([float(nxt["value"][j])], [v], 1e-5, f"leaf value of node {j}")
+        # the samples of sampled (node, action) pairs: the oracle's draws on the
+        # marginal of the GPU's belief give the GPU's children (away from CDF steps)
+        for i in rng.choice(lv[l]["count"], size=min(2, lv[l]["count"]), replace=False):
+            for a in (0, 4, 7):
+                bbar = O.predict9(w, bel[i], a)
+                P = O.obs_marginal9(w, bbar)
+                code = 0
+                # the node's path code from its ancestors
+                node, ll, digits = int(i), l, []
+                while ll > 0:
+                    lvl = lv[ll]
+                    digits.append((int(lvl["action"][node]), int(lvl["obs"][node])))
+                    node = int(lvl["parent"][node])
+                    ll -= 1
+                for (aa, zz) in reversed(digits):
+                    code = (code * 9 + aa) * 16 + zz
+                path = code * 9 + a
+                zs, bd = [], False
+                for k in range(w.K):
+                    u = O.lib().or_uniform(w.seed, w.episode, l, path, k)
+                    zs.append(O.lib().or_sample_obs(P.ctypes.data_as(O.C.c_void_p), 16, u))
+                    bd |= bool(O.lib().or_is_boundary(P.ctypes.data_as(O.C.c_void_p), 16, u))
+                if bd:
+                    continue
+                sel = (nxt["parent"].cpu().numpy() == i) & (nxt["action"].cpu().numpy() == a)
+                assert list(nxt["obs"].cpu().numpy()[sel]) == sorted(set(zs)), (l, i, a)
+    _close([g["value"]], [lv[0]["value"][0].item()], 0.0, "root value read back")
