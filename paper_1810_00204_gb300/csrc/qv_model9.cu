@@ -35,16 +35,22 @@ namespace {
 constexpr int kA9 = QV9_NUM_ACTIONS, kZ9 = QV9_NUM_OBS;
 constexpr int kRec9 = kZ9 + kZ9 * kA9 + 1;  // M[16], H[16][9], R
 constexpr int kRun9 = 32;                    // pattern runs padded to whole warps
-constexpr int kChunk9 = 4096;                // positions per expansion CTA
+constexpr int kChunk9 = 8192;                // positions per expansion CTA at the deepest level
+constexpr int kChunkSmall9 = 1024;           // ... at the levels above it (few nodes, more CTAs)
 constexpr int kT9 = 256;                     // threads of the grid kernels
 constexpr int kW9 = kT9 / 32;
 constexpr int kBand9 = 4096;                 // cells per child-belief CTA
 constexpr int kVIResCap = 1 << 17;           // sweeps whose residual is kept
 
-// Move directions clockwise from straight up; a 45-degree slip of action a
-// moves one step along this ring.
-__constant__ int c_ring[8] = {1, 2, 5, 8, 7, 6, 3, 0};
-__constant__ int c_ring_pos[9] = {7, 0, 1, 6, -1, 2, 5, 4, 3};
+// Move directions clockwise from straight up (1, 2, 5, 8, 7, 6, 3, 0); a
+// 45-degree slip of action a moves one step along this ring.  Written as
+// functions so that they fold when a is known at compile time.
+__host__ __device__ constexpr int ring_at(int i) {
+    return i == 0 ? 1 : i == 1 ? 2 : i == 2 ? 5 : i == 3 ? 8 : i == 4 ? 7 : i == 5 ? 6 : i == 6 ? 3 : 0;
+}
+__host__ __device__ constexpr int ring_pos(int a) {
+    return a == 1 ? 0 : a == 2 ? 1 : a == 5 ? 2 : a == 8 ? 3 : a == 7 ? 4 : a == 6 ? 5 : a == 3 ? 6 : a == 0 ? 7 : -1;
+}
 
 struct M9 {
     int H, W, n, goal;
@@ -53,9 +59,9 @@ struct M9 {
 };
 
 __device__ __forceinline__ void slips9(int a, int &s1, int &s2) {
-    const int i = c_ring_pos[a];
-    s1 = c_ring[(i + 1) & 7];
-    s2 = c_ring[(i + 7) & 7];
+    const int i = ring_pos(a);
+    s1 = ring_at((i + 1) & 7);
+    s2 = ring_at((i + 7) & 7);
 }
 __device__ __forceinline__ int step9(const M9 &m, int t) { return (t / 3 - 1) * m.W + (t % 3 - 1); }
 __device__ __forceinline__ bool occ9(unsigned cw) { return (cw >> 4) & 1u; }
@@ -210,71 +216,132 @@ __global__ void __launch_bounds__(kT9) k9_root(M9 m, const float *__restrict__ b
     }
 }
 
-// Grid (chunks, 9 actions, nodes): the chunk's positions of the pattern
-// order for node i and action a: M[p] (and, at the deepest level, H[p][.])
-// over the chunk, and the chunk's share of R(b, a) = sum_x b(x) R(x, a).
-// Warp w takes a contiguous run of 32-position batches; a pattern's sums are
-// reduced over the warp when its run ends and kept per warp; the CTA then
-// adds the warps in order into the chunk's record.
+// Grid (chunks, nodes): the chunk's positions of the pattern order for node
+// i and every action at once (the cell's 3x3 neighbourhood, and at the
+// deepest level its nine Q values, are loaded once for the nine actions):
+// per action a, M_a[p] and the chunk's share of R(b, a) = sum_x b(x) R(x, a)
+// in registers, reduced over the warp when a pattern's run ends; at the
+// deepest level the 81 products bbar_a(y) Q(a', y) of each 32-position
+// batch are reduced over the warp at once (three reduce-scatters) into the
+// warp's H_a[p][a'] bins.  Warps keep their own bins; the CTA adds the warps
+// in order into the chunk's record [9][kRec9].
 template <bool LEAF>
-__global__ void __launch_bounds__(kT9) k9_expand(M9 m, const float *__restrict__ bel, const int *__restrict__ perm,
-                                                const signed char *__restrict__ bpat, int Kp, int nchunk,
-                                                const float *__restrict__ Q, float *__restrict__ rec) {
-    __shared__ float bins[kW9][kRec9];
-    const int c = blockIdx.x, a = blockIdx.y, i = blockIdx.z;
+__global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restrict__ bel, const int *__restrict__ perm,
+                                                   const uint16_t *__restrict__ cwp,
+                                                   const signed char *__restrict__ bpat, int Kp, int clen,
+                                                   int nchunk, const float *__restrict__ Q, float *__restrict__ rec) {
+    constexpr int NP = kA9 * kA9;  // products of one position at the deepest level
+    __shared__ float bins[kW9][kA9][kRec9];
+    const int c = blockIdx.x, i = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float *b = bel + static_cast<size_t>(i) * m.n;
-    for (int t = threadIdx.x; t < kW9 * kRec9; t += blockDim.x) (&bins[0][0])[t] = 0.0f;
+    for (int t = threadIdx.x; t < kW9 * kA9 * kRec9; t += blockDim.x) (&bins[0][0][0])[t] = 0.0f;
     __syncthreads();
-    const int k0 = c * kChunk9, k1 = min(Kp, k0 + kChunk9);
+    const int k0 = c * clen, k1 = min(Kp, k0 + clen);
     const int nb = (k1 - k0) / 32;
     const int b0 = (nb * w) / kW9, b1 = (nb * (w + 1)) / kW9;
     int cur = -1;
-    float accM = 0.0f, accR = 0.0f, accH[LEAF ? kA9 : 1];
+    float accM[kA9], accR[kA9];
 #pragma unroll
-    for (int j = 0; j < (LEAF ? kA9 : 1); ++j) accH[j] = 0.0f;
+    for (int a = 0; a < kA9; ++a) accM[a] = accR[a] = 0.0f;
     auto flush = [&]() {
         if (cur < 0) return;
-        const float s = warp_sum(accM);
-        if (lane == 0) bins[w][cur] += s;
-        if constexpr (LEAF) {
 #pragma unroll
-            for (int j = 0; j < kA9; ++j) {
-                const float h = warp_sum(accH[j]);
-                if (lane == 0) bins[w][kZ9 + cur * kA9 + j] += h;
-                accH[j] = 0.0f;
-            }
+        for (int a = 0; a < kA9; ++a) {
+            const float s = warp_sum(accM[a]);
+            if (lane == 0) bins[w][a][cur] += s;
+            accM[a] = 0.0f;
         }
-        accM = 0.0f;
     };
+    const float w0 = 1.0f - 2.0f * m.eps, w1 = m.eps;
+    // the cell index, cell word and pattern of the next batch are loaded
+    // while this batch is computed (they head the chain of dependent loads)
+    int y_next = b0 < b1 ? __ldg(perm + k0 + b0 * 32 + lane) : -1;
+    unsigned cw_next = b0 < b1 ? __ldg(cwp + k0 + b0 * 32 + lane) : 0u;
+    int p_next = b0 < b1 ? bpat[k0 / 32 + b0] : 0;
     for (int bt = b0; bt < b1; ++bt) {
         const int kb = k0 + bt * 32;
-        const int p = bpat[kb / 32];
+        const int p = p_next, y = y_next;
+        const unsigned cw = cw_next;
+        if (bt + 1 < b1) {
+            y_next = __ldg(perm + kb + 32 + lane);
+            cw_next = __ldg(cwp + kb + 32 + lane);
+            p_next = bpat[kb / 32 + 1];
+        }
         if (p != cur) {
             flush();
             cur = p;
         }
-        const int y = __ldg(perm + kb + lane);
+        float v[kA9], q[LEAF ? kA9 : 1];
+#pragma unroll
+        for (int a = 0; a < kA9; ++a) v[a] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < (LEAF ? kA9 : 1); ++j) q[j] = 0.0f;
         if (y >= 0) {
-            const unsigned cw = m.cw[y];
-            const float v = predict9(m, b, y, cw, a);
-            accM += v;
-            accR = fmaf(__ldg(b + y), reward9<float>(m, y, cw, a), accR);
+            const float self = __ldg(b + y);
+            // src[u]: the mass of N_u(y) that can move into y (free, not the goal)
+            float src[9];
+#pragma unroll
+            for (int u = 0; u < 9; ++u) {
+                src[u] = 0.0f;
+                if (u != 4 && !((cw >> u) & 1u)) {
+                    const int x = y + step9(m, u);
+                    src[u] = x == m.goal ? 0.0f : __ldg(b + x);
+                }
+            }
             if constexpr (LEAF) {
 #pragma unroll
-                for (int j = 0; j < kA9; ++j) accH[j] = fmaf(v, __ldg(Q + static_cast<size_t>(j) * m.n + y), accH[j]);
+                for (int j = 0; j < kA9; ++j) q[j] = __ldg(Q + static_cast<size_t>(j) * m.n + y);
+            }
+            const bool goal = y == m.goal;
+#pragma unroll
+            for (int a = 0; a < kA9; ++a) {
+                if (a == 4) {
+                    v[a] = self;
+                } else {
+                    int s1, s2;
+                    slips9(a, s1, s2);
+                    float t = fmaf(w0, src[8 - a], w1 * (src[8 - s1] + src[8 - s2]));
+                    if (goal) t += self;
+                    else {
+                        const float stay = w0 * static_cast<float>((cw >> a) & 1u) +
+                                           w1 * static_cast<float>(((cw >> s1) & 1u) + ((cw >> s2) & 1u));
+                        t = fmaf(stay, self, t);
+                    }
+                    v[a] = t;
+                }
+                accM[a] += v[a];
+                accR[a] = fmaf(self, reward9<float>(m, y, cw, a), accR[a]);
+            }
+        }
+        if constexpr (LEAF) {
+#pragma unroll
+            for (int g0 = 0; g0 < NP; g0 += 32) {
+                float pv[32];
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int idx = g0 + t;
+                    pv[t] = idx < NP ? v[(idx < NP ? idx : 0) / kA9] * q[(idx < NP ? idx : 0) % kA9] : 0.0f;
+                }
+                warp_reduce_scatter32(pv);
+                const int idx = g0 + lane;
+                if (idx < NP) bins[w][idx / kA9][kZ9 + p * kA9 + idx % kA9] += pv[0];
             }
         }
     }
     flush();
-    const float r = warp_sum(accR);
-    if (lane == 0) bins[w][kRec9 - 1] = r;
+#pragma unroll
+    for (int a = 0; a < kA9; ++a) {
+        const float r = warp_sum(accR[a]);
+        if (lane == 0) bins[w][a][kRec9 - 1] = r;
+    }
     __syncthreads();
-    float *out = rec + (static_cast<size_t>(i) * kA9 + a) * nchunk * kRec9 + static_cast<size_t>(c) * kRec9;
-    for (int t = threadIdx.x; t < kRec9; t += blockDim.x) {
-        if (!LEAF && t >= kZ9 && t < kRec9 - 1) continue;
+    float *out = rec + (static_cast<size_t>(i) * nchunk + c) * kA9 * kRec9;
+    for (int t = threadIdx.x; t < kA9 * kRec9; t += blockDim.x) {
+        const int a = t / kRec9, v = t - a * kRec9;
+        if (!LEAF && v >= kZ9 && v < kRec9 - 1) continue;
         float s = 0.0f;
-        for (int v = 0; v < kW9; ++v) s += bins[v][t];
+        for (int u = 0; u < kW9; ++u) s += bins[u][a][v];
         out[t] = s;
     }
 }
@@ -297,11 +364,12 @@ __global__ void __launch_bounds__(kT9) k9_finalise(M9 m, int l, int nl, int nchu
     const int g = blockIdx.x * kW9 + w;
     if (g >= nl * kA9) return;
     const int i = g / kA9, a = g - i * kA9;
-    const float *r = rec + static_cast<size_t>(g) * nchunk * kRec9;
+    // record of (node i, chunk c): [9][kRec9], action a's part at a * kRec9
+    const float *r = rec + static_cast<size_t>(i) * nchunk * kA9 * kRec9 + static_cast<size_t>(a) * kRec9;
     for (int v = lane; v < kRec9; v += 32) {
         if (!LEAF && v >= kZ9 && v < kRec9 - 1) continue;
         float s = 0.0f;
-        for (int c = 0; c < nchunk; ++c) s += r[static_cast<size_t>(c) * kRec9 + v];
+        for (int c = 0; c < nchunk; ++c) s += r[static_cast<size_t>(c) * kA9 * kRec9 + v];
         s_tot[w][v] = s;
     }
     __syncwarp();
@@ -475,14 +543,15 @@ M9 m9_of(const qv9_model_t &md, const uint16_t *cw) {
 
 struct qv9 {
     qv9_model_t model;
-    int depth, K, n, Kp, nchunk;
+    int depth, K, n, Kp, nchunk_leaf, nchunk_inner;  // expansion chunks of kChunk9 / kChunkSmall9 positions
     std::vector<uint16_t> cw;
     std::vector<int> perm;
     std::vector<signed char> bpat;
     long cap[QV9_MAX_DEPTH + 1];
     long node_off[QV9_MAX_DEPTH + 2];  // node arrays: level l at node_off[l]
     long total_nodes, internal_nodes;  // all levels; levels 0 .. depth - 1
-    size_t off_cw, off_perm, off_bpat, off_V0, off_V1, off_res, off_flags, off_bel;
+    std::vector<uint16_t> cwp;         // cell words in pattern order (0 at padding)
+    size_t off_cw, off_perm, off_cwp, off_bpat, off_V0, off_V1, off_res, off_flags, off_bel;
     size_t off_parent, off_action, off_obs, off_weight, off_pz, off_value, off_code;
     size_t off_R, off_UQ, off_un, off_coff, off_uz, off_uf, off_upz, off_uval, off_rec;
     size_t ws_bytes;
@@ -559,7 +628,11 @@ extern "C" qv_status qv9_create(const qv9_model_t *m, int32_t depth, int32_t K, 
         h->bpat.assign(1, 0);
     }
     h->Kp = static_cast<int>(h->perm.size());
-    h->nchunk = (h->Kp + qv::kChunk9 - 1) / qv::kChunk9;
+    h->cwp.assign(h->Kp, 0);
+    for (int k = 0; k < h->Kp; ++k)
+        if (h->perm[k] >= 0) h->cwp[k] = h->cw[h->perm[k]];
+    h->nchunk_leaf = (h->Kp + qv::kChunk9 - 1) / qv::kChunk9;
+    h->nchunk_inner = (h->Kp + qv::kChunkSmall9 - 1) / qv::kChunkSmall9;
     h->cap[0] = 1;
     for (int l = 1; l <= depth; ++l) h->cap[l] = h->cap[l - 1] * qv::kA9 * std::min(K, QV9_NUM_OBS);
     h->node_off[0] = 0;
@@ -575,6 +648,7 @@ extern "C" qv_status qv9_create(const qv9_model_t *m, int32_t depth, int32_t K, 
     const size_t NT = h->total_nodes, NI = h->internal_nodes;
     h->off_cw = take(n * sizeof(uint16_t));
     h->off_perm = take(h->Kp * sizeof(int));
+    h->off_cwp = take(h->Kp * sizeof(uint16_t));
     h->off_bpat = take(h->bpat.size());
     h->off_V0 = take(n * sizeof(double));
     h->off_V1 = take(n * sizeof(double));
@@ -596,7 +670,9 @@ extern "C" qv_status qv9_create(const qv9_model_t *m, int32_t depth, int32_t K, 
     h->off_uf = take(NI * qv::kA9 * K * sizeof(int));
     h->off_upz = take(NI * qv::kA9 * K * sizeof(float));
     h->off_uval = take(NI * qv::kA9 * K * sizeof(float));
-    h->off_rec = take(static_cast<size_t>(h->cap[depth - 1]) * qv::kA9 * h->nchunk * qv::kRec9 * sizeof(float));
+    const size_t rec_nodes = std::max(static_cast<size_t>(h->cap[depth - 1]) * h->nchunk_leaf,
+                                      depth > 1 ? static_cast<size_t>(h->cap[depth - 2]) * h->nchunk_inner : 0);
+    h->off_rec = take(rec_nodes * qv::kA9 * qv::kRec9 * sizeof(float));
     h->ws_bytes = off;
     h->ws = nullptr;
     h->planned = false;
@@ -621,6 +697,8 @@ extern "C" qv_status qv9_set_workspace(qv9_t *h, void *d_ws, size_t ws_bytes, qv
                                       cudaMemcpyHostToDevice, st), "cell words") != QV_OK ||
         qv_check_cuda(cudaMemcpyAsync(h->ws + h->off_perm, h->perm.data(), h->perm.size() * sizeof(int),
                                       cudaMemcpyHostToDevice, st), "pattern order") != QV_OK ||
+        qv_check_cuda(cudaMemcpyAsync(h->ws + h->off_cwp, h->cwp.data(), h->cwp.size() * sizeof(uint16_t),
+                                      cudaMemcpyHostToDevice, st), "pattern-order cell words") != QV_OK ||
         qv_check_cuda(cudaMemcpyAsync(h->ws + h->off_bpat, h->bpat.data(), h->bpat.size(),
                                       cudaMemcpyHostToDevice, st), "batch patterns") != QV_OK)
         return QV_ERR_CUDA;
@@ -705,6 +783,7 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
     char *ws = h->ws;
     const qv::M9 m = qv::m9_of(h->model, reinterpret_cast<const uint16_t *>(ws + h->off_cw));
     const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
+    const auto *cwp = reinterpret_cast<const uint16_t *>(ws + h->off_cwp);
     const auto *bpat = reinterpret_cast<const signed char *>(ws + h->off_bpat);
     auto *flags = reinterpret_cast<int *>(ws + h->off_flags);
     auto *bcount = reinterpret_cast<unsigned long long *>(ws + h->off_flags + 16);
@@ -726,19 +805,23 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
         const int nl = h->n_level[l];
         const bool leaf = l + 1 == D;
         const size_t q0 = static_cast<size_t>(h->node_off[l]) * qv::kA9;  // Q-node base of the level
-        const dim3 eg(h->nchunk, qv::kA9, nl);
+        const int nchunk = leaf ? h->nchunk_leaf : h->nchunk_inner;
+        const int clen = leaf ? qv::kChunk9 : qv::kChunkSmall9;
+        const dim3 eg(nchunk, nl);
         if (leaf)
-            qv::k9_expand<true><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, bpat, h->Kp, h->nchunk, d_Q, rec);
+            qv::k9_expand<true><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, cwp, bpat, h->Kp, clen, nchunk, d_Q,
+                                                         rec);
         else
-            qv::k9_expand<false><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, bpat, h->Kp, h->nchunk, d_Q, rec);
+            qv::k9_expand<false><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, cwp, bpat, h->Kp, clen, nchunk, d_Q,
+                                                          rec);
         const int fg = (nl * qv::kA9 + qv::kW9 - 1) / qv::kW9;
         const qv::Lvl9 L = level9(h, l);
         if (leaf)
-            qv::k9_finalise<true><<<fg, qv::kT9, 0, st>>>(m, l, nl, h->nchunk, K, rec, L.code, seed, episode, Rq + q0,
+            qv::k9_finalise<true><<<fg, qv::kT9, 0, st>>>(m, l, nl, nchunk, K, rec, L.code, seed, episode, Rq + q0,
                                                           un + q0, uz + q0 * K, uf + q0 * K, upz + q0 * K,
                                                           uval + q0 * K, bcount);
         else
-            qv::k9_finalise<false><<<fg, qv::kT9, 0, st>>>(m, l, nl, h->nchunk, K, rec, L.code, seed, episode, Rq + q0,
+            qv::k9_finalise<false><<<fg, qv::kT9, 0, st>>>(m, l, nl, nchunk, K, rec, L.code, seed, episode, Rq + q0,
                                                            un + q0, uz + q0 * K, uf + q0 * K, upz + q0 * K,
                                                            uval + q0 * K, bcount);
         qv::k9_scan<<<1, 1024, 0, st>>>(nl * qv::kA9, un + q0, coff + q0, flags + 2);
