@@ -160,3 +160,49 @@ def test_full_size_sampled_nodes(api):
                 sel = (nxt["parent"].cpu().numpy() == i) & (nxt["action"].cpu().numpy() == a)
                 assert list(nxt["obs"].cpu().numpy()[sel]) == sorted(set(zs)), (l, i, a)
     _close([g["value"]], [lv[0]["value"][0].item()], 0.0, "root value read back")
+
+
+def _edge(case):
+    w = WL.tiny({"depth1": 0, "K16": 1, "exact": 2, "goal": 3}[case], H=11, W=13)
+    depth, K = {"depth1": (1, 4), "K16": (2, 16), "exact": (2, 4), "goal": (2, 4)}[case]
+    if case == "exact":
+        w.slip, w.p_sensor = 0.0, 1.0
+    if case == "goal":
+        b = np.zeros((w.H, w.W), np.float32)
+        b.ravel()[w.goal] = 1.0
+        w.b0 = b
+    return w, depth, K
+
+
+@pytest.mark.parametrize("case", ["depth1", "K16", "exact", "goal"])
+def test_tree_edge_cases(api, case):
+    # the leaves one level below the root, the largest K, exact motion and
+    # sensing, all of b0 on the (absorbing) goal
+    w, depth, K = _edge(case)
+    _compare_tree(api, w, depth, K)
+
+
+def test_errors(api):
+    import ctypes as C
+    from paper_1810_00204_gb300 import _native as N
+    w = WL.tiny(0, H=11, W=13)
+    occ = torch.from_numpy(w.occ.astype(np.uint8)).cuda()
+
+    def create(depth=2, K=4, slip=0.1, ps=0.95, goal=None):
+        s = N.qv9_model_t(w.H, w.W, occ.data_ptr(), int(w.goal if goal is None else goal), slip, ps, 0.95)
+        h = C.c_void_p()
+        st = N.lib().qv9_create(C.byref(s), depth, K, C.byref(h))
+        if st == 0:
+            N.lib().qv9_destroy(h)
+        return st
+
+    assert create() == 0
+    for kw in (dict(depth=0), dict(depth=4), dict(K=0), dict(K=17), dict(slip=0.5), dict(ps=0.4),
+               dict(goal=int(np.flatnonzero(w.occ.ravel())[0]))):
+        assert create(**kw) == N.QV_ERR_INVALID, kw
+    m = api.Model9(w, depth=2, K=4)
+    v = N.qv9_level_view_t()
+    assert N.lib().qv9_level(m.handle, 0, C.byref(v)) == N.QV_ERR_INVALID  # no plan yet
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    p = small.data_ptr() + (-small.data_ptr()) % 256
+    assert N.lib().qv9_set_workspace(m.handle, C.c_void_p(p), 256, None) == N.QV_ERR_WORKSPACE
