@@ -218,19 +218,23 @@ __global__ void __launch_bounds__(kT9) k9_root(M9 m, const float *__restrict__ b
 
 // Grid (chunks, nodes): the chunk's positions of the pattern order for node
 // i and every action at once (the cell's 3x3 neighbourhood, and at the
-// deepest level its nine Q values, are loaded once for the nine actions):
-// per action a, M_a[p] and the chunk's share of R(b, a) = sum_x b(x) R(x, a)
-// in registers, reduced over the warp when a pattern's run ends; at the
-// deepest level the 81 products bbar_a(y) Q(a', y) of each 32-position
-// batch are reduced over the warp at once (three reduce-scatters) into the
-// warp's H_a[p][a'] bins.  Warps keep their own bins; the CTA adds the warps
-// in order into the chunk's record [9][kRec9].
+// deepest level its nine Q values, are loaded once for the nine actions).
+// Per action a, M_a[p], the chunk's share of R(b, a) = sum_x b(x) R(x, a)
+// and at the deepest level the 81 sums H_a[p][a'] of bbar_a(y) Q(a', y)
+// build up in registers over a warp's batches of one pattern and are
+// reduced over the warp (reduce-scatters of 32 values) when the pattern's
+// run ends.  Warps keep their own bins; the CTA adds the warps in order
+// into the chunk's record [9][kRec9].  (Reducing the 81 products of every
+// batch instead, to hold fewer registers, was 4 % slower.)
 template <bool LEAF>
-__global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restrict__ bel, const int *__restrict__ perm,
-                                                   const uint16_t *__restrict__ cwp,
-                                                   const signed char *__restrict__ bpat, int Kp, int clen,
-                                                   int nchunk, const float *__restrict__ Q, float *__restrict__ rec) {
-    constexpr int NP = kA9 * kA9;  // products of one position at the deepest level
+__global__ void __launch_bounds__(kT9, LEAF ? 1 : 2) k9_expand(M9 m, const float *__restrict__ bel,
+                                                              const int *__restrict__ perm,
+                                                              const uint16_t *__restrict__ cwp,
+                                                              const signed char *__restrict__ bpat, int Kp, int clen,
+                                                              int nchunk, const float *__restrict__ Q,
+                                                              float *__restrict__ rec) {
+    constexpr int NH = LEAF ? kA9 * kA9 : 1;
+    constexpr int NV = kA9 + (LEAF ? kA9 * kA9 : 0);  // values reduced when a pattern's run ends
     __shared__ float bins[kW9][kA9][kRec9];
     const int c = blockIdx.x, i = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -241,17 +245,34 @@ __global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restric
     const int nb = (k1 - k0) / 32;
     const int b0 = (nb * w) / kW9, b1 = (nb * (w + 1)) / kW9;
     int cur = -1;
-    float accM[kA9], accR[kA9];
+    float accM[kA9], accR[kA9], accH[NH];
 #pragma unroll
     for (int a = 0; a < kA9; ++a) accM[a] = accR[a] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NH; ++j) accH[j] = 0.0f;
     auto flush = [&]() {
         if (cur < 0) return;
+        // values: M_0..M_8, then H_a[.][a'] at 9 + a * 9 + a'
 #pragma unroll
-        for (int a = 0; a < kA9; ++a) {
-            const float s = warp_sum(accM[a]);
-            if (lane == 0) bins[w][a][cur] += s;
-            accM[a] = 0.0f;
+        for (int g0 = 0; g0 < NV; g0 += 32) {
+            float v[32];
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+                const int idx = g0 + t;
+                v[t] = idx < kA9 ? accM[idx < kA9 ? idx : 0] : (idx < NV ? accH[idx - kA9 < NH ? idx - kA9 : 0] : 0.0f);
+            }
+            warp_reduce_scatter32(v);
+            const int idx = g0 + lane;
+            if (idx < kA9) bins[w][idx][cur] += v[0];
+            else if (idx < NV) {
+                const int a = (idx - kA9) / kA9, j = (idx - kA9) - a * kA9;
+                bins[w][a][kZ9 + cur * kA9 + j] += v[0];
+            }
         }
+#pragma unroll
+        for (int a = 0; a < kA9; ++a) accM[a] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NH; ++j) accH[j] = 0.0f;
     };
     const float w0 = 1.0f - 2.0f * m.eps, w1 = m.eps;
     // the cell index, cell word and pattern of the next batch are loaded
@@ -272,11 +293,6 @@ __global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restric
             flush();
             cur = p;
         }
-        float v[kA9], q[LEAF ? kA9 : 1];
-#pragma unroll
-        for (int a = 0; a < kA9; ++a) v[a] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < (LEAF ? kA9 : 1); ++j) q[j] = 0.0f;
         if (y >= 0) {
             const float self = __ldg(b + y);
             // src[u]: the mass of N_u(y) that can move into y (free, not the goal)
@@ -289,6 +305,7 @@ __global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restric
                     src[u] = x == m.goal ? 0.0f : __ldg(b + x);
                 }
             }
+            float q[LEAF ? kA9 : 1];
             if constexpr (LEAF) {
 #pragma unroll
                 for (int j = 0; j < kA9; ++j) q[j] = __ldg(Q + static_cast<size_t>(j) * m.n + y);
@@ -296,36 +313,26 @@ __global__ void __launch_bounds__(kT9, 2) k9_expand(M9 m, const float *__restric
             const bool goal = y == m.goal;
 #pragma unroll
             for (int a = 0; a < kA9; ++a) {
+                float v;
                 if (a == 4) {
-                    v[a] = self;
+                    v = self;
                 } else {
                     int s1, s2;
                     slips9(a, s1, s2);
-                    float t = fmaf(w0, src[8 - a], w1 * (src[8 - s1] + src[8 - s2]));
-                    if (goal) t += self;
+                    v = fmaf(w0, src[8 - a], w1 * (src[8 - s1] + src[8 - s2]));
+                    if (goal) v += self;
                     else {
                         const float stay = w0 * static_cast<float>((cw >> a) & 1u) +
                                            w1 * static_cast<float>(((cw >> s1) & 1u) + ((cw >> s2) & 1u));
-                        t = fmaf(stay, self, t);
+                        v = fmaf(stay, self, v);
                     }
-                    v[a] = t;
                 }
-                accM[a] += v[a];
+                accM[a] += v;
                 accR[a] = fmaf(self, reward9<float>(m, y, cw, a), accR[a]);
-            }
-        }
-        if constexpr (LEAF) {
+                if constexpr (LEAF) {
 #pragma unroll
-            for (int g0 = 0; g0 < NP; g0 += 32) {
-                float pv[32];
-#pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const int idx = g0 + t;
-                    pv[t] = idx < NP ? v[(idx < NP ? idx : 0) / kA9] * q[(idx < NP ? idx : 0) % kA9] : 0.0f;
+                    for (int j = 0; j < kA9; ++j) accH[a * kA9 + j] = fmaf(v, q[j], accH[a * kA9 + j]);
                 }
-                warp_reduce_scatter32(pv);
-                const int idx = g0 + lane;
-                if (idx < NP) bins[w][idx / kA9][kZ9 + p * kA9 + idx % kA9] += pv[0];
             }
         }
     }
