@@ -90,3 +90,25 @@ def test_adjoint_arguments_are_rejected_without_gpu(libpath):
     assert L.mdp_value_backward_workspace_bytes(ctypes.byref(m), 16) > 0
     assert L.mdp_value_backward(ctypes.byref(m), 200, 16, None, None, None, None, None, 0, None) == N.QV_ERR_INVALID
     assert L.mdp_value_iterate_checkpointed(ctypes.byref(m), 0, 16, 16, 16, 16, 16, 0, None) == N.QV_ERR_INVALID
+
+
+def test_model9_arguments_rejected_without_gpu(libpath):
+    """qv9_create validates its arguments before it reads the map back."""
+    from paper_1810_00204_gb300 import _native as N
+    L = N.lib()
+    h = ctypes.c_void_p()
+    fake = 0x1000  # never dereferenced: every case below fails validation first
+
+    def create(H=10, W=10, goal=5, slip=0.1, ps=0.95, gamma=0.95, depth=2, K=4, null=False):
+        s = N.qv9_model_t(H, W, None if null else fake, goal, slip, ps, gamma)
+        return L.qv9_create(ctypes.byref(s), depth, K, ctypes.byref(h))
+
+    assert L.qv9_create(None, 2, 4, ctypes.byref(h)) == N.QV_ERR_INVALID
+    for kw in (dict(null=True), dict(H=0), dict(W=0), dict(goal=100), dict(goal=-1), dict(slip=0.4),
+               dict(ps=0.3), dict(ps=1.2), dict(gamma=1.0), dict(depth=0), dict(depth=4), dict(K=0), dict(K=17)):
+        assert create(**kw) == N.QV_ERR_INVALID, kw
+    assert L.qv9_workspace_bytes(None) == 0
+    v = N.qv9_level_view_t()
+    assert L.qv9_level(None, 0, ctypes.byref(v)) == N.QV_ERR_INVALID
+    r = N.qv9_plan_result_t()
+    assert L.qv9_plan(None, None, None, 0, 0, ctypes.byref(r), None) == N.QV_ERR_INVALID
