@@ -192,6 +192,15 @@ __global__ void __launch_bounds__(kT9) k9_vi_q(M9 m, const T *__restrict__ V, T 
     }
 }
 
+// R(x, a) for every cell and action, FP32 [9][H][W]: a model constant the
+// expansion reads instead of recomputing it per cell.
+__global__ void __launch_bounds__(kT9) k9_reward_table(M9 m, float *__restrict__ Rt) {
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < m.n; x += gridDim.x * blockDim.x) {
+        const unsigned cw = m.cw[x];
+        for (int a = 0; a < kA9; ++a) Rt[static_cast<size_t>(a) * m.n + x] = reward9<float>(m, x, cw, a);
+    }
+}
+
 // ---------------------------------------------------------------- the tree
 struct Lvl9 {  // one level's node arrays
     int *parent, *action, *obs;
@@ -220,19 +229,20 @@ __global__ void __launch_bounds__(kT9) k9_root(M9 m, const float *__restrict__ b
 // i and every action at once (the cell's 3x3 neighbourhood, and at the
 // deepest level its nine Q values, are loaded once for the nine actions).
 // Per action a, M_a[p], the chunk's share of R(b, a) = sum_x b(x) R(x, a)
-// and at the deepest level the 81 sums H_a[p][a'] of bbar_a(y) Q(a', y)
-// build up in registers over a warp's batches of one pattern and are
-// reduced over the warp (reduce-scatters of 32 values) when the pattern's
-// run ends.  Warps keep their own bins; the CTA adds the warps in order
-// into the chunk's record [9][kRec9].  (Reducing the 81 products of every
-// batch instead, to hold fewer registers, was 4 % slower.)
+// (R from the model's table) and at the deepest level the 81 sums
+// H_a[p][a'] of bbar_a(y) Q(a', y) build up in registers over a warp's
+// batches of one pattern and are reduced over the warp (reduce-scatters of
+// 32 values) when the pattern's run ends.  Warps keep their own bins; the
+// CTA adds the warps in order into the chunk's record [9][kRec9].
+// (Reducing the 81 products of every batch instead, to hold fewer
+// registers, was 4 % slower.)
 template <bool LEAF>
 __global__ void __launch_bounds__(kT9, LEAF ? 1 : 2) k9_expand(M9 m, const float *__restrict__ bel,
                                                               const int *__restrict__ perm,
                                                               const uint16_t *__restrict__ cwp,
                                                               const signed char *__restrict__ bpat, int Kp, int clen,
                                                               int nchunk, const float *__restrict__ Q,
-                                                              float *__restrict__ rec) {
+                                                              const float *__restrict__ Rt, float *__restrict__ rec) {
     constexpr int NH = LEAF ? kA9 * kA9 : 1;
     constexpr int NV = kA9 + (LEAF ? kA9 * kA9 : 0);  // values reduced when a pattern's run ends
     __shared__ float bins[kW9][kA9][kRec9];
@@ -328,7 +338,7 @@ __global__ void __launch_bounds__(kT9, LEAF ? 1 : 2) k9_expand(M9 m, const float
                     }
                 }
                 accM[a] += v;
-                accR[a] = fmaf(self, reward9<float>(m, y, cw, a), accR[a]);
+                accR[a] = fmaf(self, __ldg(Rt + static_cast<size_t>(a) * m.n + y), accR[a]);
                 if constexpr (LEAF) {
 #pragma unroll
                     for (int j = 0; j < kA9; ++j) accH[a * kA9 + j] = fmaf(v, q[j], accH[a * kA9 + j]);
@@ -558,7 +568,7 @@ struct qv9 {
     long node_off[QV9_MAX_DEPTH + 2];  // node arrays: level l at node_off[l]
     long total_nodes, internal_nodes;  // all levels; levels 0 .. depth - 1
     std::vector<uint16_t> cwp;         // cell words in pattern order (0 at padding)
-    size_t off_cw, off_perm, off_cwp, off_bpat, off_V0, off_V1, off_res, off_flags, off_bel;
+    size_t off_cw, off_perm, off_cwp, off_bpat, off_Rt, off_V0, off_V1, off_res, off_flags, off_bel;
     size_t off_parent, off_action, off_obs, off_weight, off_pz, off_value, off_code;
     size_t off_R, off_UQ, off_un, off_coff, off_uz, off_uf, off_upz, off_uval, off_rec;
     size_t ws_bytes;
@@ -657,6 +667,7 @@ extern "C" qv_status qv9_create(const qv9_model_t *m, int32_t depth, int32_t K, 
     h->off_perm = take(h->Kp * sizeof(int));
     h->off_cwp = take(h->Kp * sizeof(uint16_t));
     h->off_bpat = take(h->bpat.size());
+    h->off_Rt = take(static_cast<size_t>(qv::kA9) * n * sizeof(float));
     h->off_V0 = take(n * sizeof(double));
     h->off_V1 = take(n * sizeof(double));
     h->off_res = take(qv::kVIResCap * sizeof(unsigned long long));
@@ -709,6 +720,10 @@ extern "C" qv_status qv9_set_workspace(qv9_t *h, void *d_ws, size_t ws_bytes, qv
         qv_check_cuda(cudaMemcpyAsync(h->ws + h->off_bpat, h->bpat.data(), h->bpat.size(),
                                       cudaMemcpyHostToDevice, st), "batch patterns") != QV_OK)
         return QV_ERR_CUDA;
+    const qv::M9 m = qv::m9_of(h->model, reinterpret_cast<const uint16_t *>(h->ws + h->off_cw));
+    const int grid = std::max(1, std::min((h->n + qv::kT9 - 1) / qv::kT9, 4 * qv_num_sms()));
+    qv::k9_reward_table<<<grid, qv::kT9, 0, st>>>(m, reinterpret_cast<float *>(h->ws + h->off_Rt));
+    if (qv_check_cuda(cudaGetLastError(), "qv9 reward table") != QV_OK) return QV_ERR_CUDA;
     // the tables are read from pageable host memory: finish before returning
     return qv_check_cuda(cudaStreamSynchronize(st), "qv9_set_workspace");
 }
@@ -791,6 +806,7 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
     const qv::M9 m = qv::m9_of(h->model, reinterpret_cast<const uint16_t *>(ws + h->off_cw));
     const int *perm = reinterpret_cast<const int *>(ws + h->off_perm);
     const auto *cwp = reinterpret_cast<const uint16_t *>(ws + h->off_cwp);
+    const float *Rt = reinterpret_cast<const float *>(ws + h->off_Rt);
     const auto *bpat = reinterpret_cast<const signed char *>(ws + h->off_bpat);
     auto *flags = reinterpret_cast<int *>(ws + h->off_flags);
     auto *bcount = reinterpret_cast<unsigned long long *>(ws + h->off_flags + 16);
@@ -817,10 +833,10 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
         const dim3 eg(nchunk, nl);
         if (leaf)
             qv::k9_expand<true><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, cwp, bpat, h->Kp, clen, nchunk, d_Q,
-                                                         rec);
+                                                         Rt, rec);
         else
             qv::k9_expand<false><<<eg, qv::kT9, 0, st>>>(m, belief9(h, l), perm, cwp, bpat, h->Kp, clen, nchunk, d_Q,
-                                                          rec);
+                                                          Rt, rec);
         const int fg = (nl * qv::kA9 + qv::kW9 - 1) / qv::kW9;
         const qv::Lvl9 L = level9(h, l);
         if (leaf)
