@@ -737,9 +737,16 @@ class Model9:
                                       _stream(stream)), "qv9_value_iterate")
         return dict(V=V, Q=Q, sweeps=sw.value, residual=res.value)
 
+    def _check_grid(self, t, shape, what):
+        if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError(f"Model9: {what} must be a float32 CUDA tensor of shape {shape}, "
+                             f"got {tuple(t.shape)} {t.dtype} on {t.device}")
+
     def plan(self, Q, b0=None, seed=None, episode=None, stream=None):
         """One plan: dict(action, value, q [9], nodes_per_level, boundary)."""
+        self._check_grid(Q, (9, self.H, self.W), "Q")
         b0 = self.b0() if b0 is None else b0.contiguous()
+        self._check_grid(b0, (self.H, self.W), "b0")
         r = N.qv9_plan_result_t()
         check(lib().qv9_plan(self.handle, _ptr(Q.contiguous()), _ptr(b0), int(self.w.seed if seed is None else seed),
                              int(self.w.episode if episode is None else episode), C.byref(r), _stream(stream)),

@@ -112,3 +112,18 @@ def test_model9_arguments_rejected_without_gpu(libpath):
     assert L.qv9_level(None, 0, ctypes.byref(v)) == N.QV_ERR_INVALID
     r = N.qv9_plan_result_t()
     assert L.qv9_plan(None, None, None, 0, 0, ctypes.byref(r), None) == N.QV_ERR_INVALID
+
+
+def test_model9_binding_checks_tensor_shapes():
+    """The binding refuses Q and b0 of the wrong shape, type or place before
+    it calls the library (the C ABI cannot check sizes)."""
+    import torch
+    from paper_1810_00204_gb300 import api
+    m = object.__new__(api.Model9)   # no handle: the checks come first
+    m.H, m.W = 4, 5
+    with pytest.raises(ValueError):
+        m.plan(torch.zeros(9, 4, 5))                      # on the host
+    with pytest.raises(ValueError):
+        m._check_grid(torch.zeros(5, 4, 5), (9, 4, 5), "Q")
+    with pytest.raises(ValueError):
+        m._check_grid(torch.zeros(9, 4, 5, dtype=torch.float64), (9, 4, 5), "Q")
