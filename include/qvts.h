@@ -628,7 +628,8 @@ typedef struct {
  * qv9_workspace_bytes: device scratch the handle needs (the levels'
  * beliefs and node arrays at their worst-case sizes (9 min(K, 16))^l).
  * qv9_set_workspace: the caller's workspace (256-byte aligned, at least
- * qv9_workspace_bytes) and the upload of the handle's tables into it. */
+ * qv9_workspace_bytes): uploads the handle's tables into it and builds the
+ * R(x, a) table there.  Synchronises. */
 qv_status qv9_create(const qv9_model_t *model, int32_t depth, int32_t K, qv9_t **out);
 size_t qv9_workspace_bytes(const qv9_t *h);
 qv_status qv9_set_workspace(qv9_t *h, void *d_ws, size_t ws_bytes, qv_stream_t stream);
