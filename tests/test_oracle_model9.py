@@ -3,9 +3,10 @@ actions, four occupancy sensors, the paper's stage reward.  The oracle's
 per-cell rows are checked against the dense brute force of `brute9` (whole-
 grid shifts, a separate formulation of the same reading), its value
 iteration against the dense iteration and an exact policy-evaluation solve,
-its Bayes update against dense products, and its tree against a dense tree
-and the closed form that holds with exact motion and exact sensors.  None
-of these call the CUDA library."""
+its Bayes update against dense products, its tree against a dense tree
+and the closed form that holds with exact motion and exact sensors, and its
+value iteration on a corridor against the closed form of a walk to the
+goal.  None of these call the CUDA library."""
 import numpy as np
 import pytest
 
@@ -211,3 +212,23 @@ def test_exact_motion_and_sensors_give_the_mdp_value():
         assert list(t["n_level"]) == [9 ** l for l in range(d + 1)]
         assert t["root_value"] == pytest.approx(o["V"][w.start], abs=1e-9)
         assert t["root_q"][t["root_action"]] == pytest.approx(o["Q"][:, w.start].max(), abs=1e-9)
+
+
+def test_corridor_closed_form():
+    # one row, no slip, the goal at the east end: the best policy steps east
+    # (-1 per step, 0 for the step onto the goal), so a cell d steps away has
+    # V = -(1 - gamma^(d-1)) / (1 - gamma); every other move costs at least
+    # as much (into the outside: -2, staying: -2)
+    H, W = 1, 9
+    occ = np.zeros((H, W), np.uint8)
+    goal = W - 1
+    b0 = np.zeros((H, W), np.float32)
+    b0[0, 0] = 1.0
+    w = WL.custom(H, W, occ, np.array([0], np.int32), 1, goal, 0, 0.0, 0.9, 0.9, b0)
+    o = O.value_iteration9(w, tol=1e-14)
+    g = w.discount
+    for c in range(W - 1):
+        d = goal - c
+        assert o["V"][c] == pytest.approx(-(1 - g ** (d - 1)) / (1 - g), abs=1e-10), c
+    assert o["V"][goal] == 0.0
+    assert int(np.argmax(o["Q"][:, 0])) == 5   # east
