@@ -1,12 +1,14 @@
 #!/usr/bin/env python3
 """QV-Tree Search benchmark: plans/s and belief-state updates/s on GB300.
 
-Default workload: the 128x128 plain configuration (20 % rectangle obstacles,
-16 beacons with range 5 and accuracy 0.85, slip 0.1, discount 0.97, Gaussian
-b0 with sigma 4, depth 3, K = 8, FP32 beliefs and Q), one plan per launch
-sequence.  A step is R planning requests (different start cells on the same
-map), each a complete plan from b0 to the chosen action.  The offline value
-iteration is run once per map and reported separately.
+Default workload: the 512x512 plain configuration (rooms of 32 cells with
+1-cell walls and 3-wide doors plus random walls to 25 %, 64 beacons with
+range 8 and accuracy 0.8, slip 0.1, discount 0.97, Gaussian b0 with sigma 4,
+depth 3, K = 4, FP32 beliefs and Q), one plan per launch.  A step is R
+planning requests (different start cells on the same map), each a complete
+plan from b0 to the chosen action.  The offline value iteration is run once
+per map and reported separately.  The 128x128 configuration, the batched
+forms and the other parts of the method are timed as sub-measurements.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -51,19 +53,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "large", "tiny"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "large", "tiny"], default="large")
     ap.add_argument("--plans-per-step", type=int, default=32)
     ap.add_argument("--leaf-mode", choices=["fused", "materialise"], default="fused")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--reference-seconds", type=float, default=120.0,
+                    help="bound on the reference arm's timed plans (it stops early and reports the plans it timed)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuner)")
-    ap.add_argument("--streams", type=int, default=8,
+    ap.add_argument("--streams", type=int, default=0,
                     help="streams the step's single-plan launches run on concurrently (each plan then takes "
-                         "1/streams of the co-resident CTAs); 0 = the fastest of 1, 4, 8 and 16 in a short trial")
+                         "1/streams of the co-resident CTAs); 0 = the fastest of 1, 2, 4 and 8 in a short trial")
     ap.add_argument("--gradient-only", action="store_true",
                     help="only time the gradient of the root value on the differentiation workload")
     ap.add_argument("--offline-only", action="store_true",
@@ -312,41 +316,45 @@ def episodes_measurement(args, dev, stream, E=64, max_steps=200):
     return out
 
 
-def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, eps, w):
+def extra_measurements(args, dev, flush, stream, plain_plans_per_s, arm, model, Qd, eps, w):
     """Sub-measurements beside the headline: the step's requests as one
-    batched launch, the 256-episode batch of uneven maps, and the 512x512
-    configuration in both leaf modes with per-phase bandwidth."""
+    batched launch against the plain arm's one launch per plan (same
+    requests); the 256-episode batch of uneven maps as one launch against one
+    launch per episode (same episodes); the 128x128 configuration; the
+    512x512 plan with materialised leaves; the other parts of the method."""
     import torch
     from paper_1810_00204_gb300 import _native as N
     from paper_1810_00204_gb300 import api, workloads as WL
     out = {}
     K = max(3, args.extra_steps)
-    peak, _ = measured_peak()
+    peak, peak_kind = measured_peak()
+    leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
     # (1) the same R requests in one launch (E = R episodes on one map)
     b0s = [model.to_grid(e.b0) for e in eps]
-    best1, _ = api.autotune([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
-                            episode=eps[0].episode, reps=5)
+    api.autotune([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
+                 episode=eps[0].episode, leaf_mode=leaf_mode, reps=3)
     pb = api.Plan([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
-                  episode=eps[0].episode)
+                  episode=eps[0].episode, leaf_mode=leaf_mode)
     pb.capture_graph()
     for _ in range(3):
         pb.run()
     ms = time_device(pb.run, K, flush, stream)
-    out["same_requests_one_launch"] = {"plans_per_s": len(eps) * K / (ms / 1e3), "E": len(eps),
-                                       "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s,
-                                       "tuning": pb.tuning}
+    same = [r["nodes_per_level"] for r in pb.read()]
+    plain_nodes = [p.read()[0]["nodes_per_level"] for p in arm.plans]
+    out["same_requests_one_launch"] = {
+        "plans_per_s": len(eps) * K / (ms / 1e3), "E": len(eps), "plain_plans_per_s": plain_plans_per_s,
+        "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s, "tuning": pb.tuning,
+        "same_trees_as_plain": same == plain_nodes, "workspace_GB": pb.workspace_bytes / 1e9,
+        "note": "the headline's requests (same map, b0s, seeds and episode words) in one batched launch; the "
+                "plain figure is the headline's one launch per plan"}
     del pb
-    # (2) 256 independent episodes on maps of uneven size, one launch per step
+    torch.cuda.empty_cache()
+    # (2) 256 independent episodes on maps of uneven size: one launch per
+    # step against one launch per episode, the same episodes
     ws = WL.batched(args.seed, E=256)
     ms_ = [api.Model(x, device=dev) for x in ws]
     Qs = [api.mdp_value_iterate(m, dtype="f32")["Q"] for m in ms_]
     b3 = [m.b0() for m in ms_]
-    p3d = api.Plan(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0, band_cells=2048, items_per_cta=2)
-    p3d.capture_graph()
-    for _ in range(2):
-        p3d.run()
-    ms3d = time_device(p3d.run, K, flush, stream)
-    del p3d
     api.autotune(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0, reps=3)
     p3 = api.Plan(ms_, Qs, b3, depth=3, K=8, seed=args.seed, episode=0)
     p3.capture_graph()
@@ -355,27 +363,56 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
     res = p3.read()
     ms3 = time_device(p3.run, K, flush, stream)
     nodes = [sum(r["nodes_per_level"][1:]) for r in res]
-    out["batched_256_uneven"] = {"plans_per_s": 256 * K / (ms3 / 1e3), "ms_per_launch": ms3 / K,
-                                 "tuning": p3.tuning, "default_shape_plans_per_s": 256 * K / (ms3d / 1e3),
-                                 "updates_per_s": sum(nodes) * K / (ms3 / 1e3),
-                                 "cells_mean": float(sum(x.H * x.W for x in ws) / 256),
-                                 "workspace_GB": p3.workspace_bytes / 1e9}
-    del p3, Qs, ms_
+    tuning3 = p3.tuning
+    ws_gb = p3.workspace_bytes / 1e9
+    del p3
     torch.cuda.empty_cache()
-    # (3) 512x512, one plan per launch, fused and materialised leaves
-    wl = WL.large(args.seed)
-    ml = api.Model(wl, device=dev)
-    r, f, t = time_offline(lambda: api.mdp_value_iterate(ml, dtype="f32"))
-    Ql = r["Q"]
-    out["offline_512"] = {"vi": offline_line(r, f, t, ml, VI_BYTES_PER_CELL, peak)}
-    r, f, t = time_offline(lambda: api.fib_value_iterate(ml, dtype="f32", want_alpha=False))
-    out["offline_512"]["fib"] = offline_line(r, f, t, ml, FIB_BYTES_PER_CELL, peak)
-    del r
-    Ncell = ml.H * ml.P
-    for mode_name, mode in (("fused", N.QV_LEAF_FUSED), ("materialise", N.QV_LEAF_MATERIALISE)):
-        api.autotune([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode, reps=3)
+    arm3 = PlainArm(api, ms_, Qs, b3, list(range(256)), 3, 8, args.seed, N.QV_LEAF_FUSED, {}, True, flush, stream,
+                    [1, 4, 8, 16])
+    ms3p = arm3.time(K)
+    same3 = [p.read()[0]["nodes_per_level"] for p in arm3.plans] == [r["nodes_per_level"] for r in res]
+    out["batched_256_uneven"] = {"plans_per_s": 256 * K / (ms3 / 1e3), "ms_per_launch": ms3 / K,
+                                 "tuning": tuning3, "updates_per_s": sum(nodes) * K / (ms3 / 1e3),
+                                 "plain_plans_per_s": 256 * K / (ms3p / 1e3), "vs_plain": ms3p / ms3,
+                                 "plain_streams": arm3.S, "plain_trial_plans_per_s": arm3.trial,
+                                 "same_trees_as_plain": same3,
+                                 "cells_mean": float(sum(x.H * x.W for x in ws) / 256), "workspace_GB": ws_gb,
+                                 "note": "plain = one k_plan launch per episode from a CUDA graph, on streams"}
+    del arm3, Qs, ms_
+    torch.cuda.empty_cache()
+    # (3) the 128x128 configuration, one plan per launch
+    wm, descm = make_workload("mid", args.seed)
+    mm = api.Model(wm, device=dev)
+    r, f, t = time_offline(lambda: api.mdp_value_iterate(mm, dtype="f32"))
+    Qm = r["Q"]
+    mid = {"workload": descm, "vi": offline_line(r, f, t, mm, VI_BYTES_PER_CELL, peak)}
+    r, f, t = time_offline(lambda: api.fib_value_iterate(mm, dtype="f32", want_alpha=False))
+    mid["fib"] = offline_line(r, f, t, mm, FIB_BYTES_PER_CELL, peak)
+    epm = WL.episodes(wm, args.plans_per_step, seed=args.seed)
+    bm = [mm.to_grid(e.b0) for e in epm]
+    api.autotune([mm], [Qm], [bm[0]], depth=wm.depth, K=wm.K, seed=wm.seed, episode=epm[0].episode, reps=3)
+    armm = PlainArm(api, [mm] * len(epm), [Qm] * len(epm), bm, [e.episode for e in epm], wm.depth, wm.K, wm.seed,
+                    N.QV_LEAF_FUSED, {}, True, flush, stream, [1, 4, 8, 16])
+    msm = armm.time(K)
+    pps = len(epm) * K / (msm / 1e3)
+    ndm = [p.read()[0]["nodes_per_level"] for p in armm.plans]
+    nda = [sum(n[l] for n in ndm) / len(ndm) for l in range(wm.depth + 1)]
+    rl, _ = plan_roofline(api, mm, Qm, bm[0], epm[0], "fused", N.QV_LEAF_FUSED, {},
+                          armm.plans[0] if armm.S > 1 else None, flush, 5, peak, peak_kind, job_plans_per_s=pps,
+                          nodes_avg=nda)
+    mid.update({"plans_per_s": pps, "streams": armm.S, "trial_plans_per_s": armm.trial,
+                "updates_per_s": sum(sum(n[1:]) for n in ndm) * K / (msm / 1e3), "roofline": rl})
+    out["mid_128"] = mid
+    del armm
+    torch.cuda.empty_cache()
+    # (4) the headline map with materialised leaves, one plan per launch
+    if args.workload == "large":
+        Ncell = model.H * model.P
+        api.autotune([model], [Qd], [b0s[0]], depth=w.depth, K=w.K, seed=w.seed, episode=eps[0].episode,
+                     leaf_mode=N.QV_LEAF_MATERIALISE, reps=3)
         torch.cuda.empty_cache()
-        p4 = api.Plan([ml], [Ql], [ml.b0()], depth=wl.depth, K=wl.K, seed=wl.seed, leaf_mode=mode)
+        p4 = api.Plan([model], [Qd], [b0s[0]], depth=w.depth, K=w.K, seed=w.seed, episode=eps[0].episode,
+                      leaf_mode=N.QV_LEAF_MATERIALISE)
         p4.capture_graph()
         for _ in range(2):
             p4.run()
@@ -388,30 +425,32 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, model, Qd, e
             nm, lv = it["name"].split(":", 1)[1], it["level"]
             t = statistics.mean(pr[i]["ms"] for pr in prof_runs for i in range(len(pr))
                                 if pr[i]["name"] == it["name"] and pr[i]["level"] == lv)
-            b = phase_bytes(nm, lv, nodes, Ncell, wl.depth, mode_name)
+            b = phase_bytes(nm, lv, nodes, Ncell, w.depth, "materialise")
             gbps = b / (t * 1e-3) / 1e9 if t > 0 else None
             phases[f"{nm}[{lv}]"] = {"ms": t, "bytes": b, "GBps": gbps,
                                      "frac_of_measured_hbm": (gbps / peak) if gbps else None}
-        out[f"large_512_{mode_name}"] = {"plans_per_s": K / (ms4 / 1e3), "ms_per_plan": ms4 / K,
-                                         "nodes_per_level": nodes,
-                                         "updates_per_s": sum(nodes[1:]) * K / (ms4 / 1e3), "phases": phases,
-                                         "tuning": p4.tuning,
-                                         "workspace_GB": p4.workspace_bytes / 1e9}
+        sb = survey_bytes(nodes, Ncell, w.depth, "materialise")
+        out["large_512_materialise"] = {"plans_per_s": K / (ms4 / 1e3), "ms_per_plan": ms4 / K,
+                                        "nodes_per_level": nodes,
+                                        "updates_per_s": sum(nodes[1:]) * K / (ms4 / 1e3), "phases": phases,
+                                        "algorithmic_bytes_per_plan": sb,
+                                        "frac_of_measured_hbm": sb / (ms4 * 1e-3) / 1e9 / peak,
+                                        "tuning": p4.tuning, "workspace_GB": p4.workspace_bytes / 1e9}
         del p4
         torch.cuda.empty_cache()
-    # (4) the gradient of the root value on the 128x128 differentiation workload
+    # (5) the gradient of the root value on the 128x128 differentiation workload
     out["gradient_diff_128"] = gradient_measurement(args, dev, K, peak)
-    # (5) the single-belief primitives of the C ABI on inputs larger than L2
+    # (6) the single-belief primitives of the C ABI on inputs larger than L2
     out["primitives"] = primitive_measurement(args, dev, K, peak)
-    # (6) the PBVI lower bound (Eq. 8) on the mid map
+    # (7) the PBVI lower bound (Eq. 8) on the mid map
     out["pbvi_mid"] = pbvi_measurement(args, dev, K, flush, stream, with_cpu=not args.no_cpu)
-    # (7) the paper's node fields U, L, H, E on the mid map
+    # (8) the paper's node fields U, L, H, E on the mid map
     out["aems_fields_mid"] = aems_measurement(args, dev, K, stream)
-    # (8) the best-first planning loop of Alg. 1 on the mid map
+    # (9) the best-first planning loop of Alg. 1 on the mid map
     out["bestfirst_mid"] = bestfirst_measurement(args, dev, stream)
-    # (9) closed-loop episodes (Alg. 1's outer loop) on the mid map
+    # (10) closed-loop episodes (Alg. 1's outer loop) on the mid map
     out["episodes_mid"] = episodes_measurement(args, dev, stream)
-    # (10) the paper's experimental model (Sec. V) on the mid map
+    # (11) the paper's experimental model (Sec. V) on the mid map
     out["model9_mid"] = model9_measurement(args, dev, stream, with_cpu=not args.no_cpu)
     return out
 
@@ -502,13 +541,27 @@ def primitive_measurement(args, dev, K, peak):
     nbytes = N * (4 + 4 + 2)  # belief in, predicted belief out, cell words
     res["belief_predict"] = {"cells": N, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
                              "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
-    pz = torch.empty(1, dtype=torch.float32, device=dev)
-    ms = timed(lambda: api.belief_correct_noalloc(m, out, 2, b, pz) if N <= 4096 * 1024
-               else api.belief_correct(m, out, 2, b), K)
+    ms = timed(lambda: api.belief_correct(m, out, 2, b), K)
     nbytes = N * (4 + 2) * 2 + N * 4  # P(z) pass and scale pass read bbar and the cell words; b' written
     res["belief_correct"] = {"cells": N, "ms": ms, "GBps": nbytes / (ms * 1e-3) / 1e9,
                              "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peak}
     del b, out
+    torch.cuda.empty_cache()
+    # the no-allocation variant beside the workspace version, on the largest
+    # grid its fixed scratch takes (2048 x 2048 cells; 16 MiB beliefs, so
+    # both stay L2-resident between the back-to-back calls)
+    ws_ = WL.tiny(args.seed, H=2048, W=2048)
+    ms_ = api.Model(ws_, device=dev)
+    Ns = ms_.H * ms_.P
+    bs = torch.rand((ms_.H, ms_.P), device=dev) * (ms_.occ == 0)
+    bs /= bs.sum()
+    outs = torch.empty_like(bs)
+    pz = torch.empty(1, dtype=torch.float32, device=dev)
+    t_ws = timed(lambda: api.belief_correct(ms_, bs, 2, outs), K)
+    t_na = timed(lambda: api.belief_correct_noalloc(ms_, bs, 2, outs, pz), K)
+    res["belief_correct_noalloc"] = {"cells": Ns, "ms": t_na, "workspace_version_ms": t_ws,
+                                     "note": "same 2048x2048 grid for both; L2-resident"}
+    del bs, outs
     torch.cuda.empty_cache()
     wl = WL.large(args.seed)
     ml = api.Model(wl, device=dev)
@@ -593,6 +646,14 @@ def make_workload(name, seed):
         w = WL.tiny(seed)
         desc = "tiny 20x20, 15% iid obstacles, B=4 range 3 acc 0.9, depth 2, K=4"
     return w, desc
+
+
+def headline_config(args, w, desc, use_graph, world_size):
+    """The `config` object of the JSON line, the same for both arms."""
+    return {"workload": desc, "plans_per_step": args.plans_per_step, "depth": w.depth, "K": w.K,
+            "leaf_mode": args.leaf_mode, "cuda_graph": use_graph,
+            "l2": "flushed before every step (256 MiB device write outside the timed events)",
+            "parallelism": "replicas" if world_size > 1 else "single GPU"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -732,6 +793,10 @@ def oracle_plans(episodes, Q64, seconds, max_plans=None):
 
 
 def run_reference(args, rank):
+    """The reference arm: the FP64 oracle on the host cores, one plan of the
+    same workload per step (a bounded sample of the R-plan step), with the
+    same config object as our arm.  It stops early, after
+    --reference-seconds of timed plans, and then reports the plans it timed."""
     if rank != 0:
         return
     import numpy as np
@@ -739,33 +804,187 @@ def run_reference(args, rank):
     from paper_1810_00204_gb300 import workloads as WL
     O.build()
     w, desc = make_workload(args.workload, args.seed)
-    eps = WL.episodes(w, max(args.steps + args.warmup, 1), seed=args.seed)
+    eps = WL.episodes(w, max(args.plans_per_step, 1), seed=args.seed)
     Q64 = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)
     for i in range(args.warmup):
         O.tree_plan(eps[i % len(eps)], Q64)
-    t = 0.0
+    t, n = 0.0, 0
     for k in range(args.steps):
         t0 = time.perf_counter()
         O.tree_plan(eps[(args.warmup + k) % len(eps)], Q64)
         t += time.perf_counter() - t0
-    value = args.steps / t
+        n += 1
+        if t >= args.reference_seconds:
+            break
+    value = n / t
     cores = O.num_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "plans/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * t / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": desc, "plans_per_step": 1, "depth": w.depth, "K": w.K,
-                   "parallelism": "oracle on host cores"},
+        "config": headline_config(args, w, desc, not args.no_graph, 1),
         "cpu_baseline": {"value": value, "unit": "plans/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} plans of the workload, one per step, FP64 C oracle "
-                                   f"(OpenMP over tree nodes, {cores} threads)"},
+                         "sample": f"{n} plans of the workload (of the {args.steps} steps asked for), one per step, "
+                                   f"the step's start cells cycled, FP64 C oracle (OpenMP over tree nodes, "
+                                   f"{cores} threads)"},
         "e2e": {"value": value, "unit": "plans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------- our arm
+def survey_bytes(nodes, N, depth, leaf_mode):
+    """Algorithmic bytes of one plan in the paper's unfused form, with FP32
+    beliefs of 4 N bytes: every V-node whose children are materialised reads
+    its belief twice (once for P(z | b, a) and R(b, a), once for the Bayes
+    correction of its children) and each child is written once, 8 N + 4 N C
+    bytes for C children; a V-node of the deepest internal level reads its
+    belief once, 4 N bytes, and gets every leaf value from the factorised
+    leaf sums; materialised leaves are also written and read back once."""
+    b = 4 * N
+    if depth == 0:
+        return b
+    tot = 0
+    for lv in range(depth):
+        if lv < depth - 1 or leaf_mode == "materialise":
+            tot += 2 * nodes[lv] * b + nodes[lv + 1] * b
+        else:
+            tot += nodes[lv] * b
+    if leaf_mode == "materialise":
+        tot += nodes[depth] * b
+    return tot
+
+
+class PlainArm:
+    """R single-plan launches per step (the plain one-tree-per-launch form):
+    each request is its own plan and its own k_plan launch from a CUDA
+    graph; with S streams every launch takes 1/S of the co-resident CTAs so
+    that up to S plans overlap.  A short trial picks S among `choices`."""
+
+    def __init__(self, api, models, Qs, b0s, episodes, depth, K, seed, leaf_mode, knobs, use_graph, flush, stream,
+                 choices):
+        self.api, self.models, self.Qs, self.b0s = api, models, Qs, b0s
+        self.episodes, self.depth, self.K, self.seed = episodes, depth, K, seed
+        self.leaf_mode, self.knobs, self.use_graph = leaf_mode, knobs, use_graph
+        self.flush, self.stream = flush, stream
+        self.full_grid = api.Plan([models[0]], [Qs[0]], [b0s[0]], depth=depth, K=K, seed=seed, episode=episodes[0],
+                                  leaf_mode=leaf_mode, **knobs).grid
+        self.trial = {}
+        best_S, best_rate = choices[0], -1.0
+        for S in choices:
+            self._make(S)
+            for _ in range(3):
+                self.step()
+            if len(choices) > 1:
+                import torch
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ms_t = 0.0
+                for k in range(6):
+                    flush.fill_(k & 255)
+                    e0.record(stream)
+                    self.step()
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms_t += e0.elapsed_time(e1)
+                rate = len(models) * 6 / (ms_t * 1e-3)
+                self.trial[S] = rate
+            else:
+                rate = 0.0
+            if rate > best_rate:
+                best_S, best_rate = S, rate
+            self.plans = self.streams = None
+        self.S = best_S
+        self._make(best_S)
+
+    def _make(self, S):
+        import torch
+        g = 0 if S == 1 else max(1, self.full_grid // S)
+        self.plans = [self.api.Plan([m], [q], [b], depth=self.depth, K=self.K, seed=self.seed, episode=e,
+                                    leaf_mode=self.leaf_mode, grid_ctas=g, **self.knobs)
+                      for m, q, b, e in zip(self.models, self.Qs, self.b0s, self.episodes)]
+        if self.use_graph:
+            for p in self.plans:
+                p.capture_graph()
+        self.streams = [torch.cuda.Stream() for _ in range(S)] if S > 1 else [self.stream]
+
+    @property
+    def grid_ctas(self):
+        return self.plans[0].grid
+
+    def step(self):
+        ps, ss = self.plans, self.streams
+        if len(ss) == 1:
+            for p in ps:
+                p.run()
+            return
+        for s_ in ss:
+            s_.wait_stream(self.stream)
+        for i, p in enumerate(ps):
+            p.run(ss[i % len(ss)])
+        for s_ in ss:
+            self.stream.wait_stream(s_)
+
+    def time(self, steps):
+        """Device ms of `steps` steps (L2 flushed before each, outside the events)."""
+        return time_device(self.step, steps, self.flush, self.stream)
+
+
+def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_plan, flush, reps, peak, peak_kind,
+                  job_plans_per_s=None, nodes_avg=None):
+    """The dominant kernel (k_plan, the whole plan in one launch) against the
+    HBM roofline: algorithmic bytes of one plan (the unfused accounting of
+    survey_bytes) over the CUDA-event time of one launch alone on the whole
+    grid, L2 flushed before each launch; the same launch on the benchmark's
+    slice of the grid; the fused design's own minimum bytes beside it; the
+    per-phase device times of the full-grid launch."""
+    full = api.Plan([model], [Q], [b0], depth=w.depth, K=w.K, seed=w.seed, episode=w.episode,
+                    leaf_mode=leaf_mode, **knobs)
+    for _ in range(3):
+        full.run()
+    nodes = full.read()[0]["nodes_per_level"]
+    Ncell = model.H * model.P
+    ms_full, ms_slice, ph_ms = [], [], {}
+    for k in range(max(1, reps)):
+        flush.fill_(k & 255)
+        lst = full.profile()
+        ms_full.append(lst[0]["ms"])
+        for it in lst[1:]:
+            ph_ms.setdefault((it["name"].split(":", 1)[1], it["level"]), []).append(it["ms"])
+        if slice_plan is not None:
+            flush.fill_(k & 255)
+            ms_slice.append(slice_plan.profile()[0]["ms"])
+    nd = nodes if nodes_avg is None else nodes_avg
+    sbytes = survey_bytes(nd, Ncell, w.depth, leaf_mode_name)
+    fbytes = sum(phase_bytes(nm, lv, nd, Ncell, w.depth, leaf_mode_name) for nm, lv in plan_phases(w.depth, leaf_mode_name))
+    avg = statistics.mean(ms_full)
+    achieved = sbytes / (avg * 1e-3) / 1e9
+    per_phase = {}
+    for (nm, lv), v in ph_ms.items():
+        pb = phase_bytes(nm, lv, nodes, Ncell, w.depth, leaf_mode_name)
+        ms = statistics.mean(v)
+        per_phase[f"{nm}[{lv}]"] = {"ms": ms, "fused_design_bytes": pb,
+                                    "GBps": pb / (ms * 1e-3) / 1e9 if ms > 0 else None}
+    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": None, "kernel": "k_plan (whole plan, one launch)", "kernel_share": 1.0,
+           "algorithmic_bytes_per_launch": sbytes,
+           "bytes_rule": "per plan: 8N + 4N C per V-node with materialised children, 4N per leaf-parent "
+                         "V-node (N cells x 4 B beliefs)",
+           "nodes_per_level": nd,
+           "avg_launch_ms": avg, "launch": f"one plan alone on the whole grid ({full.grid} CTAs), L2 flushed",
+           "fused_design_bytes_per_launch": fbytes, "fused_design_frac": fbytes / (avg * 1e-3) / 1e9 / peak,
+           "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback 6800 GB/s",
+           "phases": per_phase}
+    if ms_slice:
+        s_avg = statistics.mean(ms_slice)
+        out["slice"] = {"avg_launch_ms": s_avg, "grid_ctas": slice_plan.grid, "achieved": sbytes / (s_avg * 1e-3) / 1e9,
+                        "frac": sbytes / (s_avg * 1e-3) / 1e9 / peak}
+    if job_plans_per_s is not None:
+        out["job_achieved_GBps"] = sbytes * job_plans_per_s / 1e9
+        out["job_frac"] = sbytes * job_plans_per_s / 1e9 / peak
+    return out, full
+
+
 def main():
     args = parse()
     from paper_1810_00204_gb300 import replicas
@@ -841,74 +1060,19 @@ def main():
                 "tuned_ms": best["ms"], "default_ms": dflt[0] if dflt else None, "candidates": len(table)}
     use_graph = not args.no_graph
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    full_grid = api.Plan([model], [Qd], [b0s[0]], depth=w.depth, K=w.K, seed=w.seed, episode=eps[0].episode,
-                         leaf_mode=leaf_mode).grid
     knobs = {}
     if tune is not None:
         knobs = dict(band_cells=tune["band_cells"], items_per_cta=tune["items_per_cta"])
-
-    def make_plans(S):
-        """The step's R single-plan launches, each on 1/S of the co-resident
-        CTAs (with the knobs tuned for the whole grid), spread over S streams."""
-        g = 0 if S == 1 else max(1, full_grid // S)
-        ps = [api.Plan([model], [Qd], [b0s[i]], depth=w.depth, K=w.K, seed=w.seed, episode=e.episode,
-                       leaf_mode=leaf_mode, grid_ctas=g, **knobs) for i, e in enumerate(eps)]
-        if use_graph:
-            for p in ps:
-                p.capture_graph()
-        return ps, [torch.cuda.Stream() for _ in range(S)] if S > 1 else [stream]
-
-    def run_step(ps, ss):
-        if len(ss) == 1:
-            for p in ps:
-                p.run()
-            return
-        for s_ in ss:
-            s_.wait_stream(stream)
-        for i, p in enumerate(ps):
-            p.run(ss[i % len(ss)])
-        for s_ in ss:
-            stream.wait_stream(s_)
-
-    # concurrency: independent plans on several streams overlap on the GPU
-    # (each launch is still one plan); a short trial picks the stream count
-    trial = {}
-    choices = [args.streams] if args.streams > 0 else [1, 4, 8, 16]
-    best_S, best_rate = choices[0], -1.0
-    for S in choices:
-        ps, ss = make_plans(S)
-        for k in range(3):
-            run_step(ps, ss)
-        n_trial = 10 if len(choices) > 1 else 0
-        if n_trial:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ms_t = 0.0
-            for k in range(n_trial):
-                flush.fill_(k & 255)
-                e0.record(stream)
-                run_step(ps, ss)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms_t += e0.elapsed_time(e1)
-            rate = R * n_trial / (ms_t * 1e-3)
-            trial[S] = rate
-        else:
-            rate = 0.0
-        if rate > best_rate:
-            best_S, best_rate = S, rate
-        del ps, ss
-    plans, streams = make_plans(best_S)
-    grid_ctas = plans[0].grid
-
-    def step():
-        run_step(plans, streams)
+    choices = [args.streams] if args.streams > 0 else [1, 2, 4, 8]
+    arm = PlainArm(api, [model] * R, [Qd] * R, b0s, [e.episode for e in eps], w.depth, w.K, w.seed, leaf_mode,
+                   knobs, use_graph, flush, stream, choices)
 
     # warm-up
     for k in range(max(args.warmup, 0)):
         flush.fill_(k & 255)
-        step()
+        arm.step()
     torch.cuda.synchronize()
-    results = [p.read()[0] for p in plans]
+    results = [p.read()[0] for p in arm.plans]
     nodes_per_plan = [r["nodes_per_level"] for r in results]
     updates_per_step = sum(sum(n[1:]) for n in nodes_per_plan)
 
@@ -926,7 +1090,7 @@ def main():
     for k in range(K):
         flush.fill_((k + 7) & 255)
         ev0[k].record(stream)
-        step()
+        arm.step()
         ev1[k].record(stream)
     torch.cuda.synchronize()
     replicas.barrier(dev)
@@ -938,40 +1102,14 @@ def main():
     plans_per_s = total_plans / (dev_ms_max / 1e3)
     updates_per_s = replicas.reduce_sum(updates_per_step * K, dev) / (dev_ms_max / 1e3)
 
-    # kernel profile: k_plan timed by CUDA events on the launching stream
-    # (L2 flushed before each plan), its phases by the device clock
-    Ncell = model.H * model.P
-    phases = plan_phases(w.depth, args.leaf_mode)
-    kplan_ms, ph_ms = [], {}
-    launches_per_plan = 1
-    for k in range(max(1, args.profile_steps)):
-        for p in plans:
-            flush.fill_(k & 255)
-            lst = p.profile()
-            kplan_ms.append(lst[0]["ms"])
-            for it in lst[1:]:
-                ph_ms.setdefault((it["name"].split(":", 1)[1], it["level"]), []).append(it["ms"])
-    abytes = sum(sum(phase_bytes(nm, lv, n, Ncell, w.depth, args.leaf_mode) for nm, lv in phases)
-                 for n in nodes_per_plan) \
-        / len(nodes_per_plan)
-    avg_ms = statistics.mean(kplan_ms)
+    # the dominant kernel against its roofline: one plan alone on the whole
+    # grid and on the step's slice, with the mean level sizes of the step
     peak, peak_kind = measured_peak()
-    achieved = abytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
-    traffic = recorded_traffic("k_plan", 0, args.workload)
-    per_phase = {}
-    for (nm, lv), v in ph_ms.items():
-        pb = sum(phase_bytes(nm, lv, n, Ncell, w.depth, args.leaf_mode) for n in nodes_per_plan) / len(nodes_per_plan)
-        ms = statistics.mean(v)
-        per_phase[f"{nm}[{lv}]"] = {"ms": ms, "bytes": pb, "GBps": pb / (ms * 1e-3) / 1e9 if ms > 0 else None}
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_plan (whole plan, one launch)",
-                "kernel_share": 1.0, "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": avg_ms,
-                "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
-                else "fallback 6800 GB/s",
-                "job_achieved_GBps": abytes * plans_per_s / 1e9,
-                "job_note": "the step's algorithmic bytes over its device time, plans overlapping on "
-                            f"{len(streams)} stream(s); achieved/frac are per launch (one plan alone)",
-                "phases": per_phase}
+    nodes_avg = [sum(n[l] for n in nodes_per_plan) / len(nodes_per_plan) for l in range(w.depth + 1)]
+    roofline, _ = plan_roofline(api, model, Qd, b0s[0], eps[0], args.leaf_mode, leaf_mode, knobs,
+                                arm.plans[0] if arm.S > 1 else None, flush, args.profile_steps, peak, peak_kind,
+                                job_plans_per_s=plans_per_s / world_size, nodes_avg=nodes_avg)
+    roofline["traffic"] = recorded_traffic("k_plan", 0, args.workload)
 
     # end to end through the public API with host buffers: pinned b0 -> device,
     # run, results -> host, every step
@@ -982,35 +1120,37 @@ def main():
         h2d = sum(p.numel() * 4 for p in pinned)
         # every plan's result bytes copied back asynchronously into pinned
         # memory, one synchronisation per step, then decoded
-        rbufs = [p.readback_buffer() for p in plans]
+        rbufs = [p.readback_buffer() for p in arm.plans]
         d2h = sum(b.numel() for b in rbufs)
         t_e2e = 0.0
-        for k in range(max(3, min(K, 200))):
+        n_e2e = max(3, min(K, 200))
+        for k in range(n_e2e):
             flush.fill_(k & 255)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            for s_ in streams:
+            for s_ in arm.streams:
                 s_.wait_stream(stream)
-            for i, p in enumerate(plans):
-                s_ = streams[i % len(streams)]
+            for i, p in enumerate(arm.plans):
+                s_ = arm.streams[i % len(arm.streams)]
                 with torch.cuda.stream(s_):
                     b0s[i].copy_(pinned[i], non_blocking=True)
                 p.run(s_)
                 p.read_async(rbufs[i], s_)
-            for s_ in streams:
+            for s_ in arm.streams:
                 s_.synchronize()
-            got = [p.decode(rbufs[i])[0] for i, p in enumerate(plans)]
+            got = [p.decode(rbufs[i])[0] for i, p in enumerate(arm.plans)]
             t_e2e += time.perf_counter() - t0
         assert all(g["nodes_per_level"][0] == 1 for g in got)
-        n_e2e = max(3, min(K, 200))
         e2e_val = R * n_e2e / t_e2e
         e2e_val = replicas.reduce_sum(e2e_val, dev) if world_size > 1 else e2e_val
         e2e = {"value": e2e_val, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": n_e2e}
 
+    launch = {"autotune": tune, "streams": arm.S, "grid_ctas": arm.grid_ctas, "full_grid": arm.full_grid,
+              "concurrency_trial_plans_per_s": arm.trial}
     extra = None
-    if not args.no_extra and args.workload == "mid":
-        extra = extra_measurements(args, dev, flush, stream, plans_per_s / world_size, model, Qd, eps, w)
+    if not args.no_extra and rank == 0:
+        extra = extra_measurements(args, dev, flush, stream, plans_per_s / world_size, arm, model, Qd, eps, w)
 
     # oracle CPU baseline (rank 0, N = 1 only), bounded sample
     cpu = None
@@ -1020,15 +1160,9 @@ def main():
         oq = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)
         n, el = oracle_plans(eps, oq, args.cpu_seconds)
         cores = O.num_threads()
-        # the same oracle on one thread, on a quarter of the time budget
-        O.set_threads(1)
-        n1, el1 = oracle_plans(eps, oq, max(args.cpu_seconds / 4, 0.1))
-        O.set_threads(cores)
         cpu = {"value": n / el, "unit": "plans/s", "cores": cores, "kind": "oracle",
-               "single_thread_value": n1 / el1,
-               "sample": f"{n} plans of this workload (same map, {len(eps)} start cells cycled), "
-                         f"{el:.1f} s, FP64 C oracle with OpenMP over tree nodes; single thread: {n1} plans "
-                         f"in {el1:.1f} s"}
+               "sample": f"{n} plans of this workload (same map, start cells cycled), {el:.1f} s, FP64 C oracle "
+                         f"with OpenMP over tree nodes"}
         if extra is not None and "gradient_diff_128" in extra:
             # the oracle's reverse mode on the same differentiation workload, one gradient
             from paper_1810_00204_gb300 import workloads as WLd
@@ -1046,19 +1180,14 @@ def main():
             "metric": METRIC, "value": plans_per_s, "unit": "plans/s", "n_gpus": world_size,
             "steps": K, "warmup": args.warmup, "ms_per_step": dev_ms_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": desc, "plans_per_step": R, "depth": w.depth, "K": w.K,
-                       "leaf_mode": args.leaf_mode, "cuda_graph": use_graph,
-                       "l2": "flushed before every step (256 MiB device write outside the timed events)",
-                       "parallelism": "replicas" if world_size > 1 else "single GPU",
-                       "autotune": tune,
-                       "streams": best_S, "grid_ctas": grid_ctas, "full_grid": full_grid,
-                       "concurrency_trial_plans_per_s": trial,
-                       "nodes_per_level": nodes_per_plan[0]},
+            "config": headline_config(args, w, desc, use_graph, world_size),
+            "launch": launch,
+            "nodes_per_level": nodes_per_plan[0],
             "updates_per_s": updates_per_s,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches_per_plan * R * K,
+            "gpu_launches": R * K,
             "clocks": clocks,
             "vi": dict(offline_line(vi, vi_first_ms, vi_ms, model, VI_BYTES_PER_CELL, peak),
                        note="offline, once per map; not part of plans/s; ms = median of 3 calls after the first"),

@@ -276,7 +276,7 @@ qv_status belief_correct(const qv_model_t *model, const float *d_bbar, int32_t z
  * call cudaMalloc after start-up (an allocation can synchronise the device
  * and stall the loop), or a host application that owns every device
  * allocation and forbids libraries to make their own.  The paper has no
- * counterpart: this is a deployment variant of the Eq. 3 correction.
+ * counterpart.
  *   - Takes no workspace: the reduction's scratch is a fixed array compiled
  *     into the library (about 16 KB, resident on every device that loads
  *     the library until the process exits).  Nothing is allocated.
@@ -284,6 +284,11 @@ qv_status belief_correct(const qv_model_t *model, const float *d_bbar, int32_t z
  *     ones return QV_ERR_INVALID with a message.
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
+ *     The address is kept for the life of the process and is valid only
+ *     while the device's context lives: after cudaDeviceReset (or any loss
+ *     of the primary context) the next call may use a stale address.  A
+ *     call that fails with a CUDA error forgets the address, so the call
+ *     after it looks it up again.
  *   - Every call on a device shares the one array: calls whose GPU work
  *     overlaps (other streams, other threads) race and must be serialised by
  *     the caller.  Each call clears the part that must start at zero. */

@@ -426,11 +426,34 @@ def belief_correct(model: Model, bbar: torch.Tensor, z: int, out=None, stream=No
     return out, pz
 
 
+def _check_tensor(t, shape, device, fn, what):
+    """Raise ValueError unless t is a contiguous float32 tensor on `device`
+    (a CUDA device) of the given shape, or of at least one element when
+    shape is None."""
+    want_dev = torch.device(device)
+    ok = (torch.is_tensor(t) and t.dtype == torch.float32 and t.is_cuda and t.is_contiguous()
+          and t.device.index == (want_dev.index if want_dev.index is not None else torch.cuda.current_device())
+          and t.numel() >= 1
+          and (shape is None or tuple(t.shape) == tuple(shape)))
+    if not ok:
+        desc = (f"{tuple(t.shape)} {t.dtype} on {t.device}, contiguous={t.is_contiguous()}"
+                if torch.is_tensor(t) else type(t).__name__)
+        want = f"shape {tuple(shape)}" if shape is not None else "at least one element"
+        raise ValueError(f"{fn}: {what} must be a contiguous float32 tensor on {device} with {want}, got {desc}")
+
+
 def belief_correct_noalloc(model: Model, bbar: torch.Tensor, z: int, out: torch.Tensor, pz: torch.Tensor,
                            stream=None):
     """belief_correct without a workspace: the library keeps the reduction's
     scratch in a fixed device array, so the call itself allocates nothing.
-    The caller provides `out` (like bbar) and `pz` (one float32 on the device)."""
+    The caller provides `out` (like bbar) and `pz` (one float32 on the device).
+    Every tensor is checked (float32, contiguous, on the model's device,
+    bbar and out of shape (H, pitch)) before the library is called: the C ABI
+    takes bare pointers and would write through a host or undersized one."""
+    dev = model.device
+    for t, what in ((bbar, "bbar"), (out, "out")):
+        _check_tensor(t, (model.H, model.P), dev, "belief_correct_noalloc", what)
+    _check_tensor(pz, None, dev, "belief_correct_noalloc", "pz")
     check(lib().belief_correct_noalloc(C.byref(model.struct), _ptr(bbar), int(z), _ptr(out), _ptr(pz),
                                        _stream(stream)), "belief_correct_noalloc")
     return out, pz

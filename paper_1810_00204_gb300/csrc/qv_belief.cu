@@ -288,6 +288,19 @@ qv_status noalloc_scratch(float **out) {
     *out = g_noalloc_addr[dev];
     return QV_OK;
 }
+
+// After a failed call the cached address may belong to a context that no
+// longer exists: drop it, so that the next call on the device looks it up
+// again.
+void noalloc_forget() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    g_noalloc_addr[dev] = nullptr;
+}
 }  // namespace
 
 extern "C" qv_status belief_correct_noalloc(const qv_model_t *m, const float *d_bbar, int32_t z, float *d_bout,
@@ -314,11 +327,15 @@ extern "C" qv_status belief_correct_noalloc(const qv_model_t *m, const float *d_
     const int grid = static_cast<int>(std::max<long long>(
         1, (cells + qv::kNoAllocCellsPerBlock - 1) / qv::kNoAllocCellsPerBlock));
     // the arrival counter must start at zero; the partial sums are overwritten
-    if (qv_check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), cs), "belief_correct_noalloc memset") != QV_OK)
+    if (qv_check_cuda(cudaMemsetAsync(counter, 0, sizeof(unsigned), cs), "belief_correct_noalloc memset") != QV_OK) {
+        noalloc_forget();
         return QV_ERR_CUDA;
+    }
     qv::k_obs_partial<<<grid, 256, 0, cs>>>(a, d_bbar, z, scratch, counter, d_pz);
     qv::k_correct_scale<<<grid, 256, 0, cs>>>(a, d_bbar, z, d_pz, d_bout);
-    return qv_check_cuda(cudaGetLastError(), "belief_correct_noalloc launch");
+    st = qv_check_cuda(cudaGetLastError(), "belief_correct_noalloc launch");
+    if (st != QV_OK) noalloc_forget();
+    return st;
 }
 
 extern "C" qv_status leaf_value(const qv_model_t *m, const float *d_Q, const float *d_b, int32_t n, float *d_value,

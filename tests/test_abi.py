@@ -127,3 +127,24 @@ def test_model9_binding_checks_tensor_shapes():
         m._check_grid(torch.zeros(5, 4, 5), (9, 4, 5), "Q")
     with pytest.raises(ValueError):
         m._check_grid(torch.zeros(9, 4, 5, dtype=torch.float64), (9, 4, 5), "Q")
+
+
+def test_noalloc_binding_checks_tensors_before_the_library():
+    """belief_correct_noalloc's binding refuses host, mistyped or wrongly
+    shaped tensors before it calls the library, whose C ABI takes bare
+    pointers and would write through them."""
+    import torch
+    from paper_1810_00204_gb300 import api
+
+    class _M:  # stands in for a Model: only its grid shape and device are read
+        H, P, device = 4, 8, torch.device("cuda", 0)
+    m = _M()
+    g = torch.zeros(4, 8)
+    with pytest.raises(ValueError):
+        api.belief_correct_noalloc(m, g, 0, g, torch.zeros(1))          # all on the host
+    with pytest.raises(ValueError):
+        api._check_tensor(torch.zeros(4, 5), (4, 8), "cpu", "f", "out")  # wrong shape (and place)
+    with pytest.raises(ValueError):
+        api._check_tensor(torch.zeros(1, dtype=torch.float64), None, "cpu", "f", "pz")
+    with pytest.raises(ValueError):
+        api._check_tensor(torch.zeros(8, 4).t(), (4, 8), "cpu", "f", "bbar")  # not contiguous

@@ -2,14 +2,15 @@
 allocate device memory (a loop that must not call cudaMalloc once running,
 or a host that owns every device allocation).  Its scratch is a fixed array
 inside the library, shared by every call, so these tests check it against
-the workspace-taking belief_correct on consecutive calls and check that an
-oversized grid is refused.  The file is named to run last."""
+the workspace-taking belief_correct and the oracle's Bayes update on
+consecutive calls, and check that an oversized grid is refused.  The file is named to run last."""
 import ctypes as C
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_1810_00204_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +57,10 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls(mods, make):
         assert np.abs(o - r).max() <= REL * np.abs(r).max(), f"call {call}"
         assert abs(pz.item() - ref_pz.item()) <= REL * abs(ref_pz.item()), f"call {call}"
         assert o[:, w.W:].max(initial=0.0) == 0.0  # padding columns stay empty
+        # and directly against the oracle's Bayes update of the same bbar
+        ob, opz = O.correct(w, m.from_grid(bbar).astype(np.float64), z)
+        assert np.abs(o[:, :w.W].ravel() - ob).max() <= REL * np.abs(ob).max(), f"call {call} vs oracle"
+        assert abs(pz.item() - opz) <= REL * abs(opz), f"call {call} P(z) vs oracle"
 
 
 def test_noalloc_refuses_grids_beyond_its_scratch(mods):
