@@ -224,9 +224,10 @@ qv_status fib_value_iterate(const qv_model_t *model, int32_t dtype, double tol,
  * qv_pbvi_backup: one Eq. 8 backup of every point of the set given nG
  * vectors d_G (nG <= max_points); writes one new vector per point to d_Gout
  * (must not overlap d_G), and, where not NULL, the backed-up value at the
- * point d_value [nB] (= d_Gout[b] . b), the chosen action d_astar [nB] (ties
- * to the lowest), the winning vector of each observation for that action
- * d_best [nB][B + 1] (ties to the lowest index), d_q [nB][5] every Q_b(a).
+ * point d_value [nB] (= d_Gout[b] . b), the chosen action d_astar [nB]
+ * (argmax of Q_b(a), exact ties to the lowest), the winning vector of each
+ * observation for that action d_best [nB][B + 1] (exact ties to the lowest
+ * index), d_q [nB][5] every Q_b(a).
  * qv_pbvi_value: V_PBVI(b) and its maximising vector (ties to the lowest
  * index) for nb beliefs d_b given nG <= max_points vectors d_G (the beliefs
  * go through in chunks of max_points).  d_G = NULL reuses the vectors of the
@@ -250,6 +251,17 @@ qv_status qv_pbvi_set_points(qv_pbvi_t *pbvi, const float *d_B, int32_t nB, void
 qv_status qv_pbvi_backup(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, float *d_Gout,
                          float *d_value, int32_t *d_astar, int32_t *d_best, float *d_q,
                          qv_stream_t stream);
+/* qv_pbvi_backup_fixed: qv_pbvi_backup with some of Eq. 8's decisions
+ * fixed by the caller (device arrays, nullable): a* of point b is
+ * d_fix_astar[b] when that is >= 0, and the winning vector of observation
+ * z for that a* is d_fix_best[b][z] (B + 1 per point) when that is >= 0;
+ * the fixed winner's own score enters Q_b(a*).  Entries < 0 leave the
+ * decision to the argmax.  Used to replay another implementation's choices
+ * at near-ties (d_fix_best needs d_fix_astar; QV_ERR_INVALID otherwise). */
+qv_status qv_pbvi_backup_fixed(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, float *d_Gout,
+                               float *d_value, int32_t *d_astar, int32_t *d_best, float *d_q,
+                               const int32_t *d_fix_astar, const int32_t *d_fix_best,
+                               qv_stream_t stream);
 qv_status qv_pbvi_value(qv_pbvi_t *pbvi, const float *d_G, int32_t nG, const float *d_b,
                         int32_t nb, float *d_value, int32_t *d_arg, qv_stream_t stream);
 /* qv_pbvi_check: synchronises; QV_ERR_TIMEOUT (once) if a bounded wait of
@@ -482,6 +494,13 @@ qv_status qv_bf_create(const qv_model_t *model, const float *d_Qu, qv_pbvi_t *pb
 size_t qv_bf_workspace_bytes(const qv_bf_t *bf);
 qv_status qv_bf_reset(qv_bf_t *bf, const float *d_b0, void *d_ws, size_t ws_bytes, qv_stream_t stream);
 qv_status qv_bf_run(qv_bf_t *bf, int32_t iters, qv_stream_t stream);
+/* qv_bf_set_replay: fix the node expanded at some iterations: at iteration
+ * t < n (counted from the last qv_bf_reset) with d_expand[t] >= 0 the loop
+ * expands node d_expand[t] (an id below the node count, else the root's E)
+ * instead of the root's E, to replay another implementation's choices
+ * where Eq. 9's comparisons are near-ties.  d_expand is a device array the
+ * caller keeps alive while runs use it; n = 0 clears the replay. */
+qv_status qv_bf_set_replay(qv_bf_t *bf, const int32_t *d_expand, int32_t n);
 qv_status qv_bf_read(qv_bf_t *bf, qv_bf_result_t *h_result, qv_stream_t stream);
 qv_status qv_bf_view(const qv_bf_t *bf, qv_bf_view_t *view);
 void qv_bf_destroy(qv_bf_t *bf);

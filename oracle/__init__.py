@@ -96,7 +96,7 @@ def lib():
         L.or_tree_bounds.argtypes = [C.c_int] + [vp] * 9 + [C.c_double] + [vp] * 6
         L.or_tree_bounds.restype = C.c_int
         L.or_bestfirst.argtypes = ([P, vp, vp, C.c_int, vp, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_int,
-                                    C.c_int, vp, vp] + [vp] * 22)
+                                    C.c_int, vp, vp] + [vp] * 19)
         L.or_bestfirst.restype = C.c_int
         L.or_env_step.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, vp]
         L.or_env_step.restype = C.c_int
@@ -478,16 +478,15 @@ def tree_bounds(tree, Lleaf, gamma):
     return out
 
 
-def bestfirst(w, Qu, G, iters, K=None, seed=None, episode=None, max_depth=6, max_nodes=None, b0=None, force=None,
-              **kw):
+def bestfirst(w, Qu, G, iters, K=None, seed=None, episode=None, max_depth=6, max_nodes=None, b0=None, **kw):
     """Alg. 1's best-first planning loop: `iters` expansions of the V-node the
     root's E points at, U from the upper-bound alpha-vectors Qu [5][n] (FIB),
     L from the PBVI vectors G [nG][n].  Returns dict with per-node arrays
     (parent, action, obs, depth, weight, U, L, H, E, belief), per Q-node
     arrays [nodes][5] (R, UQ, LQ, HQ, EQ, first, count), expanded [iters],
-    iterations, nodes, boundary, root_action.  force [iters]: expand these
-    nodes instead (then best_h, forced_h, slack per iteration compare each
-    choice with this tree's own)."""
+    margin [iters] (the smallest gap among the comparisons that chose each
+    iteration's node; inf while the root is a leaf), iterations, nodes,
+    boundary, root_action."""
     p = _prob(w, **kw)
     ww = p.w
     K = ww.K if K is None else K
@@ -508,20 +507,18 @@ def bestfirst(w, Qu, G, iters, K=None, seed=None, episode=None, max_depth=6, max
              HQ=f64(max_nodes * A), EQ=i32(max_nodes * A), first=i32(max_nodes * A), count=i32(max_nodes * A))
     nn = C.c_int(0)
     bd = C.c_long(0)
-    fc = None if force is None else np.ascontiguousarray(np.asarray(force, np.int32))
-    cmp_ = {k: np.zeros(iters, np.float64) for k in ("best_h", "forced_h", "slack")}
+    margin = np.full(iters, np.inf, np.float64)
     it = lib().or_bestfirst(p.ref, _p(Qu), _p(G), G.shape[0], _p(b0), int(K), int(seed), int(episode), int(iters),
                             int(max_depth), int(max_nodes), _p(bel), C.byref(nn), _p(o["expanded"]),
                             _p(o["parent"]), _p(o["action"]), _p(o["obs"]), _p(o["depth"]), _p(o["weight"]),
                             _p(o["U"]), _p(o["L"]), _p(o["H"]), _p(o["E"]), _p(o["R"]), _p(o["UQ"]), _p(o["LQ"]),
                             _p(o["HQ"]), _p(o["EQ"]), _p(o["first"]), _p(o["count"]), C.byref(bd),
-                            None if fc is None else _p(fc), _p(cmp_["best_h"]), _p(cmp_["forced_h"]),
-                            _p(cmp_["slack"]))
+                            _p(margin))
     m = nn.value
     out = {k: v[:m] for k, v in o.items() if k != "expanded" and v.size == max_nodes}
     for k in ("R", "UQ", "LQ", "HQ", "EQ", "first", "count"):
         out[k] = o[k][:m * A].reshape(m, A)
-    out.update(cmp_)
+    out["margin"] = margin
     out.update(expanded=o["expanded"], iterations=it, nodes=m, boundary=bd.value, belief=bel[:m],
                root_action=int(np.argmax(out["UQ"][0])) if out["count"][0].sum() else -1)
     return out

@@ -805,18 +805,13 @@ int or_pbvi_expand(const or_problem *p, const double *B, int nB, int round, uint
     return 0;
 }
 
-/* Eq. 8's argmaxes meet exact ties (at the pessimistic start every action
- * of a point far from the goal is worth R_min / (1 - gamma)), which FP32 and
- * FP64 sums would break differently; so candidates within 1e-5 * max(1, |best|)
- * of the best count as tied and the lowest index among them is taken.     */
+/* Eq. 8's argmax: the first index attaining the largest value (exact ties
+ * to the lowest index).                                                    */
 static int pbvi_pick(const double *v, int n) {
-    double best = v[0];
+    int best = 0;
     for (int i = 1; i < n; ++i)
-        if (v[i] > best) best = v[i];
-    const double tol = 1e-5 * (fabs(best) > 1.0 ? fabs(best) : 1.0);
-    for (int i = 0; i < n; ++i)
-        if (v[i] >= best - tol) return i;
-    return 0;
+        if (v[i] > v[best]) best = i;
+    return best;
 }
 
 /* One PBVI alpha-vector backup, Eq. 8, at every point b of B given the set
@@ -992,6 +987,37 @@ static void bf_update_node(int v, double gamma, const int *cbeg, const int *ccnt
     E[v] = EQ[v * A + au];
 }
 
+/* The smallest gap among the comparisons that point the root's E at the
+ * node to expand, following them down from the root: at every expanded
+ * V-node, the largest U_Q against each other action's (Alg. 7 and Eq. 9
+ * follow the action maximising U_Q), and among the children of that
+ * Q-node the largest gamma * weight * H_V against each other child's
+ * (Alg. 6).  HUGE_VAL when the root is still a leaf.                        */
+static double bf_margin(double gamma, const int *cbeg, const int *ccnt, const double *UQ, const double *w,
+                        const double *Hh) {
+    const int A = OR_NUM_ACTIONS;
+    double m = HUGE_VAL;
+    int u = 0;
+    while (ccnt[u * A] > 0) {
+        int au = 0;
+        for (int a = 1; a < A; ++a)
+            if (UQ[u * A + a] > UQ[u * A + au]) au = a;
+        for (int a = 0; a < A; ++a)
+            if (a != au && UQ[u * A + au] - UQ[u * A + a] < m) m = UQ[u * A + au] - UQ[u * A + a];
+        const int q = u * A + au;
+        int cb = -1;
+        double bh = 0.0;
+        for (int c = cbeg[q]; c < cbeg[q] + ccnt[q]; ++c) {
+            const double h = gamma * w[c] * Hh[c];
+            if (cb < 0 || h > bh) { bh = h; cb = c; }
+        }
+        for (int c = cbeg[q]; c < cbeg[q] + ccnt[q]; ++c)
+            if (c != cb && bh - gamma * w[c] * Hh[c] < m) m = bh - gamma * w[c] * Hh[c];
+        u = cb;
+    }
+    return m;
+}
+
 /* Alg. 1's planning loop: starting from the root V-node of b0 (U = V_U(b0)
  * with the upper-bound alpha-vectors Qu, e.g. FIB; L = V_PBVI(b0) =
  * max_i G_i . b0; H = U - L; E = root), each iteration expands the V-node
@@ -1009,16 +1035,15 @@ static void bf_update_node(int v, double gamma, const int *cbeg, const int *ccnt
  * Q-node (v * 5 + a): R, U_Q, L_Q, H_Q, E_Q, first child, children;
  * expanded[it] the node expanded at iteration it (-1 after a stop);
  * *n_nodes; *boundary draws within 1e-6 of a CDF step.  Returns the
- * iterations run.  belief: [max_nodes][n] scratch.  force (nullable):
- * force[it] >= 0 expands that node instead of the root's E (to follow
- * another implementation's choices), with best_h, forced_h and slack
- * (nullable, [iters]) recording how each forced choice compares.        */
+ * iterations run.  belief: [max_nodes][n] scratch.  margin (nullable,
+ * [iters]): for each iteration, the smallest gap among the comparisons that
+ * pointed the root's E at the node it expanded (bf_margin); a comparison
+ * whose gap is within rounding can order differently in another precision. */
 int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG, const double *b0, int K,
                  uint64_t seed, uint32_t episode, int iters, int max_depth, int max_nodes, double *belief,
                  int *n_nodes, int *expanded, int *vparent, int *vaction, int *vobs, int *vdepth, double *vweight,
                  double *U, double *L, double *Hh, int *E, double *Rq, double *UQ, double *LQ, double *HQ, int *EQ,
-                 int *cbeg, int *ccnt, long *boundary, const int *force, double *best_h, double *forced_h,
-                 double *slack) {
+                 int *cbeg, int *ccnt, long *boundary, double *margin) {
     const int n = p->H * p->W, nz = p->B + 1, A = OR_NUM_ACTIONS;
     int *label = (int *)malloc(sizeof(int) * n);
     double *Rt = (double *)malloc(sizeof(double) * A * n);
@@ -1050,25 +1075,7 @@ int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG,
         int v = E[0];
         const int room = A * (K < nz ? K : nz);
         if (vdepth[v] >= max_depth || nn + room > max_nodes) break;
-        if (force && force[it] >= 0) {
-            /* follow a given choice (a leaf of the current tree), and report
-             * how it compares with this tree's own: the heuristic product
-             * along its path against the root's H, and the largest shortfall
-             * of a taken action's U_Q below its node's best                  */
-            const int f = force[it];
-            double h = vdepth[f] < max_depth ? U[f] - L[f] : 0.0, gap = 0.0;
-            for (int u = f; vparent[u] >= 0; u = vparent[u]) {
-                const int pv = vparent[u], a = vaction[u];
-                h *= p->gamma * vweight[u];
-                double best = UQ[pv * A];
-                for (int b = 1; b < A; ++b) if (UQ[pv * A + b] > best) best = UQ[pv * A + b];
-                if (best - UQ[pv * A + a] > gap) gap = best - UQ[pv * A + a];
-            }
-            if (best_h) best_h[it] = Hh[0];
-            if (forced_h) forced_h[it] = h;
-            if (slack) slack[it] = gap;
-            v = f;
-        }
+        if (margin) margin[it] = bf_margin(p->gamma, cbeg, ccnt, UQ, vweight, Hh);
         const double *b = belief + (size_t)v * n;
         for (int a = 0; a < A; ++a) {
             const int q = v * A + a;

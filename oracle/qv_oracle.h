@@ -129,8 +129,7 @@ int or_bestfirst(const or_problem *p, const double *Qu, const double *G, int nG,
                  uint64_t seed, uint32_t episode, int iters, int max_depth, int max_nodes, double *belief,
                  int *n_nodes, int *expanded, int *vparent, int *vaction, int *vobs, int *vdepth, double *vweight,
                  double *U, double *L, double *Hh, int *E, double *Rq, double *UQ, double *LQ, double *HQ, int *EQ,
-                 int *cbeg, int *ccnt, long *boundary, const int *force, double *best_h, double *forced_h,
-                 double *slack);
+                 int *cbeg, int *ccnt, long *boundary, double *margin);
 
 /* ---- Closed-loop episodes (Alg. 1 outer loop, Eq. 1) ---- */
 int or_env_step(const or_problem *p, const int *label, int x, int a, uint64_t seed, uint32_t e, int step, int *z_out);

@@ -116,6 +116,7 @@ SIGNATURES = {
     "qv_pbvi_layout": (_i32, [_vp, _vp]),
     "qv_pbvi_set_points": (C.c_int, [_vp, _vp, _i32, _vp, _sz, _vp]),
     "qv_pbvi_backup": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "qv_pbvi_backup_fixed": (C.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "qv_pbvi_value": (C.c_int, [_vp, _vp, _i32, _vp, _i32, _vp, _vp, _vp]),
     "qv_pbvi_check": (C.c_int, [_vp, _vp]),
     "qv_pbvi_destroy": (None, [_vp]),
@@ -144,6 +145,7 @@ SIGNATURES = {
     "qv_bf_workspace_bytes": (_sz, [_vp]),
     "qv_bf_reset": (C.c_int, [_vp, _vp, _vp, _sz, _vp]),
     "qv_bf_run": (C.c_int, [_vp, _i32, _vp]),
+    "qv_bf_set_replay": (C.c_int, [_vp, _vp, _i32]),
     "qv_bf_read": (C.c_int, [_vp, C.POINTER(qv_bf_result_t), _vp]),
     "qv_bf_view": (C.c_int, [_vp, C.POINTER(qv_bf_view_t)]),
     "qv_bf_destroy": (None, [_vp]),

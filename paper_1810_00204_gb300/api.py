@@ -187,17 +187,26 @@ class Pbvi:
         check(lib().qv_pbvi_set_points(self.handle, _ptr(self.B), self.nB, self.ws_ptr, self.ws_bytes,
                                        _stream(stream)), "qv_pbvi_set_points")
 
-    def backup(self, G: torch.Tensor, out=None, stream=None):
+    def backup(self, G: torch.Tensor, out=None, stream=None, fix_astar=None, fix_best=None):
         """One Eq. 8 backup at every point of the set given G [nG][H][pitch].
-        Returns dict(G [nB][H][pitch], value, astar, best [nB][B+1], q [nB][5])."""
+        Returns dict(G [nB][H][pitch], value, astar, best [nB][B+1], q [nB][5]).
+        fix_astar [nB] / fix_best [nB][B+1] (int32 arrays, -1 = not fixed):
+        decisions taken as given (qv_pbvi_backup_fixed)."""
         nB, m = self.nB, self.model
         out = torch.empty((nB, m.H, m.P), dtype=torch.float32, device=m.device) if out is None else out
         value = torch.empty(nB, dtype=torch.float32, device=m.device)
         astar = torch.empty(nB, dtype=torch.int32, device=m.device)
         best = torch.empty((nB, m.B + 1), dtype=torch.int32, device=m.device)
         q = torch.empty((nB, 5), dtype=torch.float32, device=m.device)
-        check(lib().qv_pbvi_backup(self.handle, _ptr(G.contiguous()), G.shape[0], _ptr(out), _ptr(value), _ptr(astar),
-                                   _ptr(best), _ptr(q), _stream(stream)), "qv_pbvi_backup")
+        fa = fb = None
+        if fix_astar is not None:
+            fa = torch.as_tensor(np.ascontiguousarray(np.asarray(fix_astar, np.int32).reshape(nB))).to(m.device)
+        if fix_best is not None:
+            fb = torch.as_tensor(np.ascontiguousarray(np.asarray(fix_best, np.int32).reshape(nB, m.B + 1))).to(m.device)
+        self._fixed = (fa, fb)  # alive until the next backup (the launch reads them asynchronously)
+        check(lib().qv_pbvi_backup_fixed(self.handle, _ptr(G.contiguous()), G.shape[0], _ptr(out), _ptr(value),
+                                         _ptr(astar), _ptr(best), _ptr(q), _ptr(fa), _ptr(fb), _stream(stream)),
+              "qv_pbvi_backup_fixed")
         return dict(G=out, value=value, astar=astar, best=best, q=q)
 
     def value(self, G: Optional[torch.Tensor], b: torch.Tensor, nG: Optional[int] = None, stream=None):
@@ -270,6 +279,17 @@ class BestFirst:
 
     def run(self, iters: int, stream=None):
         check(lib().qv_bf_run(self.handle, int(iters), _stream(stream)), "qv_bf_run")
+
+    def set_replay(self, expand=None):
+        """Fix the node expanded at iteration t to expand[t] where that is >= 0
+        (qv_bf_set_replay); None clears it."""
+        if expand is None:
+            self._replay = None
+            check(lib().qv_bf_set_replay(self.handle, None, 0), "qv_bf_set_replay")
+            return
+        self._replay = torch.as_tensor(np.ascontiguousarray(np.asarray(expand, np.int32))).to(self.model.device)
+        check(lib().qv_bf_set_replay(self.handle, _ptr(self._replay), int(self._replay.numel())),
+              "qv_bf_set_replay")
 
     def read(self, stream=None) -> dict:
         r = N.qv_bf_result_t()

@@ -57,12 +57,26 @@ struct BfDev {
     int *sz, *sf, *sm;        // [5][cmax] z, frequency; [5] unique count
     float *sR;                // [5]
     int band_cells, nbands;
+    const int *replay;        // [n_replay] (nullable): node to expand at iteration t when >= 0
+    int n_replay;
 };
+
+// The V-node iteration t expands: the root's E (Eq. 9), unless the caller
+// fixed the choice of this iteration (replay of another implementation's
+// choices at near-ties); a fixed id must name an existing node.
+__device__ __forceinline__ int bf_target(const BfDev &d) {
+    const int t = d.state[1];
+    if (d.replay && t < d.n_replay) {
+        const int f = __ldg(d.replay + t);
+        if (f >= 0 && f < d.state[0]) return f;
+    }
+    return d.E[0];
+}
 
 // The node to expand, or -1 when planning has stopped (every CTA of a
 // launch reaches the same answer; CTA 0 records a new stop).
 __device__ __forceinline__ int bf_node(const BfDev &d, bool record) {
-    const int v = d.E[0];
+    const int v = bf_target(d);
     const bool stop = d.state[2] != 0 || d.depth[v] >= d.max_depth || d.state[0] + 5 * d.cmax > d.max_nodes;
     if (stop && record) d.state[2] = 1;
     return stop ? -1 : v;
@@ -231,7 +245,7 @@ __device__ void bf_update_node(const BfDev &d, int u, int lane) {
 __global__ void __launch_bounds__(32) k_bf_update(BfDev d) {
     const int lane = threadIdx.x;
     if (d.state[2]) return;
-    const int v = d.E[0];
+    const int v = bf_target(d);
     const int n = d.state[0];
     int base[6];
     base[0] = 0;
@@ -575,6 +589,15 @@ extern "C" qv_status qv_bf_run(qv_bf_t *h, int32_t iters, qv_stream_t stream) {
     if (qv_check_cuda(cudaEventRecord(h->ev_out, h->gs), "event") != QV_OK ||
         qv_check_cuda(cudaStreamWaitEvent(st, h->ev_out, 0), "wait") != QV_OK)
         return QV_ERR_CUDA;
+    return QV_OK;
+}
+
+extern "C" qv_status qv_bf_set_replay(qv_bf_t *h, const int32_t *d_expand, int32_t n) {
+    if (!h) return qv_set_error(QV_ERR_INVALID, "qv_bf_set_replay: null pointer");
+    if (n < 0 || (n > 0 && !d_expand)) return qv_set_error(QV_ERR_INVALID, "qv_bf_set_replay: n %d", n);
+    h->dev.replay = n > 0 ? d_expand : nullptr;
+    h->dev.n_replay = n;
+    bf_drop_graph(h);  // the captured iteration holds the old parameters
     return QV_OK;
 }
 

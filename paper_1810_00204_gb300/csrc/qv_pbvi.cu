@@ -619,20 +619,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_pbvi_scores(const float *__re
 }
 
 // ---------------------------------------------------------------- selection
-// Eq. 8's argmaxes meet exact ties (at the pessimistic start every action of
-// a point far from the goal is worth R_min / (1 - gamma)) that rounding
-// would break at random; candidates within 1e-5 * max(1, |best|) of the best
-// count as tied and the lowest index among them is taken.
-__device__ __forceinline__ float tie_tol(float best) { return 1e-5f * fmaxf(1.0f, fabsf(best)); }
-
 // One CTA per point b.  For each action a the slab rows of (b, a) are read
 // once, a chunk of vectors at a time: D_z(i) (the label's pieces in order)
 // and D(i) (every piece in order) go to shared memory.  One warp per
-// observation z then takes argmax_i eta D(i) + (accuracy - eta) D_z(i): the
-// best score over every chunk first, then the lowest index within the tie
-// tolerance of it (a second read of the slabs only when nG spans more than
-// one chunk).  Then a* and the distinct winners of a* with their
-// multiplicities.
+// observation z then takes Eq. 8's argmax_i eta D(i) + (accuracy - eta)
+// D_z(i): the best score over every chunk first, then the lowest index that
+// attains it (a second read of the slabs only when nG spans more than one
+// chunk).  Then a* = argmax_a Q_b(a) (ties to the lowest action) and the
+// distinct winners of a* with their multiplicities.
+// fix_astar / fix_best (nullable): decisions fixed by the caller, a* of
+// point b when fix_astar[b] >= 0 and the winner of observation z for that
+// a* when fix_best[b * nz + z] >= 0 (its own score then enters Q_b(a*)), so
+// that another implementation's choices at near-ties can be replayed.
 constexpr int kSelThreads = 512;
 constexpr size_t kSelSmemBudget = 96 * 1024;  // D_z and D of one chunk, and the piece labels
 
@@ -664,7 +662,9 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
                                                                 const float *__restrict__ RB, float *__restrict__ value,
                                                                 int *__restrict__ astar, int *__restrict__ best,
                                                                 float *__restrict__ q, int *__restrict__ uniq,
-                                                                int *__restrict__ mult, int *__restrict__ nuniq) {
+                                                                int *__restrict__ mult, int *__restrict__ nuniq,
+                                                                const int *__restrict__ fix_astar,
+                                                                const int *__restrict__ fix_best) {
     extern __shared__ float sel_sm[];
     const int groups = select_groups(m.nz, chunk);
     float *Dz = sel_sm;                       // [nz][chunk] (group 0's, and the sums over the groups)
@@ -771,6 +771,7 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
                 }
         }
     };
+    const int fa = fix_astar ? __ldg(fix_astar + b) : -1;
     for (int a = 0; a < 5; ++a) {
         const size_t row = static_cast<size_t>(b * 5 + a) * nG;
         // pass 1: the best score of every z
@@ -790,7 +791,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
                 }
             }
         }
-        // pass 2: the lowest index within the tie tolerance of the best
+        // pass 2: the lowest index that attains the best (or the caller's
+        // fixed winner, with its own score)
         for (int c = 0; c < nchunks; ++c) {
             const int i0 = c * chunk, n = min(chunk, nG - i0);
             __syncthreads();
@@ -799,9 +801,17 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
                 __syncthreads();
             }
             for (int z = wid; z < m.nz; z += kWarps) {
+                const int fz = (a == fa && fix_best) ? __ldg(fix_best + b * m.nz + z) : -1;
+                if (fz >= 0) {  // warp-uniform
+                    if (lane == 0 && fz >= i0 && fz < i0 + n) {
+                        s_bi[z] = fz;
+                        s_bs[z] = fmaf(m.acc - m.eta, Dz[z * chunk + (fz - i0)], m.eta * D[fz - i0]);
+                    }
+                    continue;
+                }
                 if (s_bi[z] != 0x7fffffff) continue;  // found in an earlier chunk (warp-uniform)
                 const float *dz = Dz + z * chunk;
-                const float floor_v = s_bv[z] - tie_tol(s_bv[z]);
+                const float floor_v = s_bv[z];
                 int bi = 0x7fffffff;
                 float bs = 0.0f;
                 for (int i = lane; i < n; i += 32) {
@@ -843,7 +853,8 @@ __global__ void __launch_bounds__(kSelThreads, 2) k_pbvi_select(PbModel m, int n
         float qmax = s_q[0];
         for (int a = 1; a < 5; ++a) qmax = fmaxf(qmax, s_q[a]);
         int as = 0;
-        while (as < 4 && !(s_q[as] >= qmax - tie_tol(qmax))) ++as;
+        while (as < 4 && !(s_q[as] >= qmax)) ++as;
+        if (fa >= 0 && fa < 5) as = fa;
         astar[b] = as;
         value[b] = s_q[as];
         if (q)
@@ -1250,7 +1261,15 @@ extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB
 
 extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, float *d_Gout, float *d_value,
                                     int32_t *d_astar, int32_t *d_best, float *d_q, qv_stream_t stream) {
+    return qv_pbvi_backup_fixed(h, d_G, nG, d_Gout, d_value, d_astar, d_best, d_q, nullptr, nullptr, stream);
+}
+
+extern "C" qv_status qv_pbvi_backup_fixed(qv_pbvi *h, const float *d_G, int32_t nG, float *d_Gout, float *d_value,
+                                          int32_t *d_astar, int32_t *d_best, float *d_q, const int32_t *d_fix_astar,
+                                          const int32_t *d_fix_best, qv_stream_t stream) {
     if (!h || !d_G || !d_Gout) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: null pointer");
+    if (d_fix_best && !d_fix_astar)
+        return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup_fixed: fixed winners need the fixed actions");
     if (!h->ws || h->nB < 1) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: no point set (qv_pbvi_set_points)");
     if (nG < 1 || nG > h->max_vectors)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: %d vectors outside 1..%d", nG, h->max_vectors);
@@ -1292,7 +1311,8 @@ extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, fl
         return QV_ERR_CUDA;
     qv::k_pbvi_select<<<nB, qv::kSelThreads, sel_smem, st>>>(pm, nB, nG, chunk, npieces, piece, slab,
                                                              reinterpret_cast<const float *>(ws + h->off_RB), value,
-                                                             astar, best, d_q, uniq, mult, nuniq);
+                                                             astar, best, d_q, uniq, mult, nuniq, d_fix_astar,
+                                                             d_fix_best);
     const int band_rows = std::max(1, 4096 / h->model.pitch);
     const int nbands = (h->model.H + band_rows - 1) / band_rows;
     const size_t a_smem = static_cast<size_t>(band_rows + 2) * h->model.pitch * sizeof(float);

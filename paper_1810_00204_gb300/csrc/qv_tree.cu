@@ -112,12 +112,31 @@ qv_status validate(int E, const qv_model_t *models, const qv_plan_params_t *p) {
     return QV_OK;
 }
 
+// The largest dynamic shared memory k_plan has been allowed on each device.
+// The attribute belongs to the kernel, not to a plan, so it only ever grows:
+// lowering it for a plan with small bands would make an earlier plan's
+// launch (or graph) with larger bands fail.
+std::mutex g_smem_mu;
+constexpr int kMaxDevices = 64;
+size_t g_smem_attr[kMaxDevices] = {};
+
+bool allow_smem(size_t smem) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return false;
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    if (smem <= g_smem_attr[dev]) return true;
+    if (cudaFuncSetAttribute(qv::k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
+        cudaSuccess)
+        return false;
+    g_smem_attr[dev] = smem;
+    return true;
+}
+
 // Co-resident CTAs of k_plan for a given dynamic smem size (0 when it does
 // not fit or there is no device).
 int plan_grid(size_t smem) {
     int per_sm = 0;
-    if (cudaFuncSetAttribute(qv::k_plan, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
-            cudaSuccess ||
+    if (!allow_smem(smem) ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qv::k_plan, qv::kThreads, smem) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();

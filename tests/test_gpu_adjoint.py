@@ -237,6 +237,16 @@ def test_autograd_function_on_the_differentiation_workload(api):
     assert r["value"] == pytest.approx(float(v.detach()), rel=1e-6)
     rep = _gpu_samples_flat(plan, 3, 8, w.B)
     p = _prob(w)
+    # the GPU's samples are the oracle's own Philox draws (the samples depend
+    # on the beliefs only, not on Q), except at draws the oracle flags as
+    # lying within 1e-6 of a CDF step
+    own = O.tree_plan(p, O.value_iteration(p, truncated=200)["Q"], depth=3, K=8, seed=w.seed, episode=w.episode)
+    assert own["n_level"].tolist() == r["nodes_per_level"] or own["boundary_count"] > 0
+    for l in range(3):
+        if plan.level(0, l)["count"] != own["n_level"][l]:
+            break
+        gs = plan.level(0, l)["samples"].cpu().numpy()
+        assert not ((gs != own["samples"][l]) & (own["boundary"][l] == 0)).any(), f"level {l} samples"
     ref = O.root_value_grad(p, 200, depth=3, K=8, replay=rep)
     assert ref["tree"]["n_level"].tolist() == r["nodes_per_level"]
     assert float(v.detach()) == pytest.approx(ref["value"], rel=1e-5)
@@ -254,6 +264,42 @@ def test_autograd_function_on_the_differentiation_workload(api):
     assert float(slip.grad) == pytest.approx(fd, rel=GRAD_REL)
     fd = (val(acc_v=float(w.accuracy) + h) - val(acc_v=float(w.accuracy) - h)) / (2 * h)
     assert float(acc.grad) == pytest.approx(fd, rel=GRAD_REL, abs=GRAD_ABS)
+
+
+def test_gradient_on_the_differentiation_workload_with_a_spread_belief(api):
+    """The differentiation workload (128x128, depth 3, K = 8, 200 truncated
+    sweeps with checkpoints every 16, its cost map) with b0 spread over every
+    free cell, so that the active beliefs straddle label regions and
+    d/d accuracy is far from zero: the GPU's gradient against the oracle's
+    reverse mode and central differences (h = 1e-6) at 1e-4 relative, with
+    no absolute floor."""
+    w = _spread(WL.diff(0))
+    S = 200
+    m, vi, p, Qf, o, r, plan = _tree_case(api, w, 3, 8, S, 0)
+    ds, da, dc, db = _full_grad_gpu(api, m, vi, plan)
+    rep = o["samples_flat"]
+    ref = O.root_value_grad(p, S, depth=3, K=8, replay=rep)
+    assert abs(ref["dacc"]) > 1e3 * GRAD_ABS
+    assert ds == pytest.approx(ref["dslip"], rel=GRAD_REL)
+    assert da == pytest.approx(ref["dacc"], rel=GRAD_REL)
+    _close(dc, ref["dcost"], GRAD_REL, what="dcost")
+    _close(db, ref["db0"], GRAD_REL, what="db0")
+    cost = w.cost.astype(np.float64).ravel()
+
+    def val(slip=float(w.slip), acc=float(w.accuracy), c=cost):
+        q = O.Problem(w, slip=slip, accuracy=acc, discount=float(w.discount), cost=c)
+        return O.root_value(q, S, depth=3, K=8, replay=rep)[0]
+
+    h = 1e-6
+    fd = (val(slip=float(w.slip) + h) - val(slip=float(w.slip) - h)) / (2 * h)
+    assert ds == pytest.approx(fd, rel=GRAD_REL)
+    fd = (val(acc=float(w.accuracy) + h) - val(acc=float(w.accuracy) - h)) / (2 * h)
+    assert da == pytest.approx(fd, rel=GRAD_REL)
+    for i in np.argsort(-np.abs(ref["dcost"]))[:3]:
+        e = np.zeros_like(cost)
+        e[i] = h
+        fd = (val(c=cost + e) - val(c=cost - e)) / (2 * h)
+        assert dc[i] == pytest.approx(fd, rel=GRAD_REL, abs=1e-8)
 
 
 def test_autograd_gradients_of_b0_and_accuracy(api):

@@ -1,12 +1,14 @@
 """GPU parity of the best-first planning loop (Alg. 1 with Alg. 2-7, Eq. 9):
 the qv_bf_* calls against the oracle's bestfirst on the same upper-bound
-alpha-vectors and PBVI vectors.  The oracle follows the GPU's choice of node
-at every iteration and each choice must be its own best up to 1e-4 * scale
-(the heuristic products and U_Q of FP32 and FP64 may order a near-tie
-differently); then the same tree (parents, actions, observations, depths,
-weights exactly), beliefs |d| <= 1e-5 max|ref|, fields |d| <= 1e-5
-max(|ref|, 1); the stop rules; and on the full mid map the same loop for 30
-iterations."""
+alpha-vectors and PBVI vectors.  The oracle runs its own loop.  At the
+iterations where it reports a near-tie among the comparisons that chose its
+node (margin within 1e-5 * scale: FP32 and FP64 may order those
+differently) the oracle's choice is replayed into the GPU loop
+(qv_bf_set_replay); at every other iteration the GPU chooses on its own and
+must expand the oracle's node.  Then the same tree (parents, actions,
+observations, depths, weights exactly), beliefs |d| <= 1e-5 max|ref|,
+fields |d| <= 1e-5 max(|ref|, 1); the stop rules; and on the full mid map
+the same loop for 30 iterations."""
 import numpy as np
 import pytest
 import torch
@@ -16,6 +18,8 @@ from paper_1810_00204_gb300 import workloads as WL
 from test_gpu_parity import _close
 
 pytestmark = pytest.mark.gpu
+
+TIE = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -41,16 +45,18 @@ def _run_both(api, w, iters, K, max_depth, max_nodes=None):
     Gd = m.to_grid(G.reshape(-1, w.H, w.W))
     nz = w.B + 1
     mn = max_nodes or 1 + iters * 5 * min(K, nz)
+    o = O.bestfirst(w, Qu.astype(np.float64), G.astype(np.float64), iters, K=K, max_depth=max_depth, max_nodes=mn)
+    scale = max(1.0, float(np.abs(o["U"]).max()), float(np.abs(o["L"]).max()))
+    it = o["iterations"]
+    near = np.zeros(iters, bool)
+    near[:it] = o["margin"][:it] <= TIE * scale
+    replay = np.where(near, o["expanded"], -1).astype(np.int32)
     bf = api.BestFirst(m, Qd, pb, Gd, K=K, seed=w.seed, episode=w.episode, max_depth=max_depth, max_nodes=mn)
+    bf.set_replay(replay)
     bf.reset()
     bf.run(iters)
     r = bf.read()
     t = bf.tree()
-    # the oracle follows the GPU's choices (a near-tie of the heuristic may
-    # order two expansions differently in FP32 and FP64) and reports how
-    # each compares with its own
-    o = O.bestfirst(w, Qu.astype(np.float64), G.astype(np.float64), iters, K=K, max_depth=max_depth, max_nodes=mn,
-                    force=t["expanded"][:iters])
     return m, bf, r, t, o
 
 
@@ -59,11 +65,8 @@ def _compare(m, r, t, o):
     assert r["iterations"] == o["iterations"]
     assert r["nodes"] == o["nodes"]
     it = o["iterations"]
+    # the GPU's own choices (every iteration not replayed) are the oracle's
     assert np.array_equal(t["expanded"][:it], o["expanded"][:it])
-    scale = max(1.0, float(np.abs(o["U"]).max()))
-    # every choice was the oracle's best up to a near-tie
-    assert np.all(o["forced_h"][:it] >= o["best_h"][:it] - 1e-4 * scale)
-    assert np.all(o["slack"][:it] <= 1e-4 * scale)
     for k in ("parent", "action", "obs", "depth"):
         assert np.array_equal(t[k], o[k]), k
     assert np.array_equal(t["weight"], o["weight"].astype(np.float32))

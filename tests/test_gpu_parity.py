@@ -299,6 +299,12 @@ def test_batched_matches_plain(api):
         if o["boundary_count"] == 0:
             assert batch[e]["nodes_per_level"] == [int(x) for x in o["n_level"]]
             assert abs(batch[e]["value"] - o["root_value"]) <= REL * max(1.0, abs(o["root_value"]))
+        else:
+            # a draw at a CDF step: the oracle's samples replayed give its tree
+            rp = api.qv_tree_plan(m, Qs[e], b0s[e], depth=3, K=8, seed=5, episode=e,
+                                  replay=torch.from_numpy(o["samples_flat"].copy()).cuda())
+            assert rp["nodes_per_level"] == [int(x) for x in o["n_level"]]
+            assert abs(rp["value"] - o["root_value"]) <= REL * max(1.0, abs(o["root_value"]))
 
 
 def test_async_readback_matches_read(api):

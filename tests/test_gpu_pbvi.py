@@ -2,13 +2,18 @@
 start, belief set expansion, one backup, V_PBVI and the whole schedule
 through the C ABI against the oracle on the same inputs.
 
-Decisions taken by an argmax (a*, the winning vector of each observation,
-V_PBVI's vector) must match the oracle's wherever the oracle's best and
-second-best candidates are more than 1e-4 * scale apart; elsewhere the
-GPU's choice must score within that margin of the oracle's maximum.  Values
-|d| <= 1e-5 * max(|ref|, 1) (FP32 against FP64) for one backup, 1e-4 after a
-schedule of many backups.  Sampled observations match except at draws the
-oracle flags as lying within 1e-6 of a CDF step."""
+The oracle takes Eq. 8's argmaxes as written (exact ties to the lowest
+index).  Where one of a point's decisions is a near-tie in the oracle's own
+scores (best and second-best candidates within 1e-4 * scale), FP32 and FP64
+may order the candidates differently, so the test replays the oracle's
+decisions for that point into the GPU backup (qv_pbvi_backup_fixed); every
+other decision is the GPU's own and must equal the oracle's.  Where only
+sampled points of a backup are recomputed by the oracle (or for V_PBVI's
+vector), a near-tie is reported instead: the GPU's pick must score within
+the margin of the oracle's best.  Values |d| <= 1e-5 * max(|ref|, 1) (FP32
+against FP64) for one backup, 1e-4 after a schedule of many backups.
+Sampled observations match except at draws the oracle flags as lying within
+1e-6 of a CDF step."""
 import numpy as np
 import pytest
 import torch
@@ -75,6 +80,27 @@ def _check_argmax(got, scores, scale, what):
         assert scores[got] >= top - GAP * scale, f"{what}: pick {got} scores {scores[got]} < max {top}"
 
 
+def _near(scores, scale):
+    s = np.sort(np.asarray(scores))
+    return len(s) > 1 and s[-1] - s[-2] <= GAP * scale
+
+
+def _oracle_fixes(o, scale):
+    """The oracle's a* and winners for every point with a near-tie among
+    its decisions (any action's Q, any observation's vectors); -1 elsewhere,
+    where the GPU decides on its own."""
+    nB, _, nz, _ = o["score"].shape
+    fa = np.full(nB, -1, np.int32)
+    fb = np.full((nB, nz), -1, np.int32)
+    for j in range(nB):
+        near = _near(o["q"][j], scale) or any(_near(o["score"][j, a, z], scale) for a in range(5)
+                                               for z in range(nz))
+        if near:
+            fa[j] = o["astar"][j]
+            fb[j] = o["best"][j]
+    return fa, fb
+
+
 def test_init_matches_oracle(api):
     for w in (WL.tiny(0), WL.diff(0, H=40, W=36), WL.mid(1, H=67, W=45)):
         m = api.Model(w)
@@ -107,35 +133,27 @@ def _backup_case(api, w, nB, nG, seed, support=None):
     G = _vectors(w, nG, seed)
     pb = api.Pbvi(m, max(nB, nG))
     pb.set_points(_grid(m, B))
-    r = pb.backup(_grid(m, G))
-    torch.cuda.synchronize()
     o = O.pbvi_backup(w, B.astype(np.float64), G.astype(np.float64), want_score=True)
     scale = max(1.0, float(np.abs(o["q"]).max()))
+    fa, fb = _oracle_fixes(o, scale)
+    r = pb.backup(_grid(m, G), fix_astar=fa, fix_best=fb)
+    torch.cuda.synchronize()
     gv = r["value"].cpu().numpy()
     ga = r["astar"].cpu().numpy()
     gb = r["best"].cpu().numpy()
     gq = r["q"].cpu().numpy()
     _close(gq, o["q"], floor=scale, what="Q_b(a)")
     _close(gv, o["value"], floor=scale, what="value")
+    # every decision, the GPU's own or replayed at a near-tie, is the oracle's
+    assert np.array_equal(ga, o["astar"]), "a*"
+    assert np.array_equal(gb, o["best"]), "winning vectors"
     GG = _flat(m, r["G"])
-    clean = 0
     for j in range(nB):
-        _check_argmax(int(ga[j]), o["q"][j], scale, f"a* of point {j}")
-        a = int(ga[j])
-        amb = False
-        for z in range(w.B + 1):
-            sc = o["score"][j, a, z]
-            _check_argmax(int(gb[j, z]), sc, scale, f"best of point {j} z {z}")
-            srt = np.sort(sc)
-            amb |= len(srt) > 1 and srt[-1] - srt[-2] <= GAP * scale
-        if a == o["astar"][j] and not amb:
-            _close(GG[j], o["G"][j], floor=scale, what=f"alpha of point {j}")
-            clean += 1
+        _close(GG[j], o["G"][j], floor=scale, what=f"alpha of point {j}")
         # the new vector gives the backed-up value at its own point
         assert abs(GG[j] @ B[j].astype(np.float64) - gv[j]) <= REL * scale * 10
         assert np.all(GG[j][_dead(w)] == 0.0)
-    assert clean >= nB // 2
-    return m, pb
+    return m, pb, int((fa >= 0).sum())
 
 
 @pytest.mark.parametrize("make,nB,nG", [(lambda: WL.tiny(0), 5, 4), (lambda: WL.tiny(2, H=13, W=17), 7, 3),
@@ -197,15 +215,50 @@ def test_value_matches_oracle(api):
 
 @pytest.mark.parametrize("seed", [0, 1])
 def test_solve_matches_oracle_schedule(api, seed):
+    # the schedule of pbvi_solve, run on both sides backup by backup: the
+    # oracle on its own FP64 chain, the GPU on its own FP32 chain with the
+    # oracle's decisions replayed at the points where they are near-ties
+    rounds, iters = 3, 12
     w = WL.tiny(seed, H=10, W=11)
     m = api.Model(w)
-    g = api.pbvi_solve(m, rounds=3, iters=12, seed=seed)
-    o = O.pbvi_solve(w, rounds=3, iters=12, seed=seed)
-    gB = _flat(m, g["B"])
-    assert gB.shape == o["B"].shape
-    _close(gB, o["B"], rel=1e-4, what="belief set")
-    scale = max(1.0, float(np.abs(o["value"]).max()))
-    _close(g["value"].cpu().numpy(), o["value"], rel=1e-4, floor=scale, what="V_PBVI at the points")
+    B = w.b0.ravel().astype(np.float64)[None].copy()
+    G = O.pbvi_init(w)[None]
+    nmax = 1 << rounds
+    Bg = torch.zeros((nmax, m.H, m.P), dtype=torch.float32, device="cuda")
+    Bg[0] = m.b0()
+    Gg = torch.zeros_like(Bg)
+    Gg[0] = api.pbvi_init(m)
+    G2 = torch.empty_like(Gg)
+    pb = api.Pbvi(m, nmax)
+    nB = nG = 1
+    replayed = 0
+    for r in range(rounds + 1):
+        pb.set_points(Bg[:nB])
+        for _ in range(iters):
+            o = O.pbvi_backup(w, B, G, want_score=True)
+            scale = max(1.0, float(np.abs(o["q"]).max()))
+            fa, fb = _oracle_fixes(o, scale)
+            replayed += int((fa >= 0).sum())
+            res = pb.backup(Gg[:nG], out=G2[:nB], fix_astar=fa, fix_best=fb)
+            assert np.array_equal(res["astar"].cpu().numpy(), o["astar"])
+            assert np.array_equal(res["best"].cpu().numpy(), o["best"])
+            Gg, G2 = G2, Gg
+            nG = nB
+            G = o["G"]
+        if r < rounds:
+            e = O.pbvi_expand(w, B, r, seed=seed)
+            assert int(e["boundary"].sum()) == 0
+            api.pbvi_expand(m, Bg[:nB], r, seed, out=Bg[nB:2 * nB])
+            B = np.concatenate([B, e["points"]])
+            nB *= 2
+    gB = _flat(m, Bg[:nB])
+    assert gB.shape == B.shape
+    _close(gB, B, rel=1e-4, what="belief set")
+    ov = O.pbvi_value(G, B)
+    scale = max(1.0, float(np.abs(ov).max()))
+    gv, _ = pb.value(Gg[:nG], Bg[:nB])
+    _close(gv.cpu().numpy(), ov, rel=1e-4, floor=scale, what="V_PBVI at the points")
+    _close(_flat(m, Gg[:nG]), G, rel=1e-4, floor=scale, what="alpha-vectors")
 
 
 def test_full_size_lower_bound_and_sampled_backups(api):

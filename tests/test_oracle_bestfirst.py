@@ -5,8 +5,9 @@ value); one expansion of the root is the depth-1 level-synchronous tree with
 its AEMS fields; each iteration expands the root's E of the tree before it;
 the root's E is reached by the greedy actions and the largest gamma w H_V
 children, with the root's H the product along that path; lower bounds stay
-below upper bounds; nodes at the depth limit are closed.  None of these call
-the CUDA library."""
+below upper bounds; nodes at the depth limit are closed; each iteration's
+margin is the smallest gap of the comparisons on the pointer path.  None of
+these call the CUDA library."""
 import numpy as np
 import pytest
 
@@ -92,19 +93,31 @@ def test_root_pointer_path_and_bounds(seed):
     assert r["H"][0] == pytest.approx(prod * gap, rel=1e-12, abs=1e-15)
 
 
-def test_forcing_its_own_choices_changes_nothing():
+def _path_margin(r, gamma):
+    """The gaps of the comparisons from the root down the pointer path, from
+    the fields of a finished run (numpy, independent of the C loop)."""
+    m, u = np.inf, 0
+    while r["count"][u].sum() > 0:
+        uq = r["UQ"][u]
+        au = int(np.argmax(uq))
+        m = min(m, min((uq[au] - uq[a] for a in range(5) if a != au), default=np.inf))
+        c0, n = int(r["first"][u][au]), int(r["count"][u][au])
+        ch = np.arange(c0, c0 + n)
+        h = gamma * r["weight"][ch] * r["H"][ch]
+        k = int(np.argmax(h))
+        if n > 1:
+            m = min(m, float(h[k] - np.delete(h, k).max()))
+        u = int(ch[k])
+    return m
+
+
+def test_margin_is_the_smallest_gap_on_the_pointer_path():
+    # margin[t] is taken on the tree of the first t expansions: recompute it
+    # from the fields of a run stopped after t iterations
     w, Qu, G = _setup(7)
-    r = O.bestfirst(w, Qu, G, 14, max_depth=5)
-    f = O.bestfirst(w, Qu, G, 14, max_depth=5, force=r["expanded"])
-    assert f["nodes"] == r["nodes"] and np.array_equal(f["expanded"], r["expanded"])
-    assert np.array_equal(f["U"], r["U"]) and np.array_equal(f["E"], r["E"])
-    it = r["iterations"]
-    assert np.array_equal(f["forced_h"][:it], f["best_h"][:it])
-    assert np.all(f["slack"][:it] == 0.0)
-    # any other leaf either scores below the root's H along greedy actions or
-    # hangs under a non-greedy action (a positive U_Q shortfall)
-    for leaf in range(1, r["count"][0].sum() + 1):
-        g = O.bestfirst(w, Qu, G, 2, max_depth=5, force=[0, leaf])
-        assert g["forced_h"][1] <= g["best_h"][1] or g["slack"][1] > 0.0
-        if leaf != r["expanded"][1]:
-            assert g["forced_h"][1] < g["best_h"][1] or g["slack"][1] > 0.0
+    full = O.bestfirst(w, Qu, G, 7, max_depth=5)
+    assert full["margin"][0] == np.inf and np.all(full["margin"][:full["iterations"]] >= 0.0)
+    for t in range(1, 7):
+        r = O.bestfirst(w, Qu, G, t, max_depth=5)
+        assert full["margin"][t] == pytest.approx(_path_margin(r, w.discount), rel=1e-12, abs=1e-12), t
+        assert full["expanded"][t] == r["E"][0]
