@@ -102,6 +102,15 @@ typedef struct {
                                   co-resident; fewer leave room for plans launched
                                   concurrently on other streams (a latency-bound plan
                                   barely slows, the GPU runs several at once)         */
+    double deadline_ms;        /* anytime stop (Sec. IV-C; Alg. 1 plans "while time
+                                  permits"): 0 = none; > 0 = a budget from the start of
+                                  the plan's kernel, checked each time a level is
+                                  final: once it has run out, that level's children
+                                  become the leaves (values by Eq. 4) and the backup
+                                  returns the best root action of the levels built so
+                                  far (depth_reached of the result; level 0 is always
+                                  built).  Needs QV_LEAF_FUSED; every level then also
+                                  sums its children's leaf values                     */
 } qv_plan_params_t;
 
 typedef struct {
@@ -110,6 +119,8 @@ typedef struct {
     float q[QV_NUM_ACTIONS];   /* U_Q(b0, a)                                            */
     int32_t nodes_per_level[QV_MAX_DEPTH + 1];
     int64_t boundary_samples;  /* draws whose uniform fell within 1e-6 of a CDF step    */
+    int32_t depth_reached;     /* depth of the tree the result comes from: the plan's
+                                  depth, or less when its deadline ran out            */
 } qv_plan_result_t;
 
 const char *qv_last_error(void);

@@ -36,7 +36,8 @@ class qv_model_t(C.Structure):
 class qv_plan_params_t(C.Structure):
     _fields_ = [("depth", C.c_int32), ("K", C.c_int32), ("seed", C.c_uint64), ("episode", C.c_uint32),
                 ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p),
-                ("band_cells", C.c_int32), ("items_per_cta", C.c_int32), ("grid_ctas", C.c_int32)]
+                ("band_cells", C.c_int32), ("items_per_cta", C.c_int32), ("grid_ctas", C.c_int32),
+                ("deadline_ms", C.c_double)]
 
 
 class qv_tune_t(C.Structure):
@@ -45,7 +46,8 @@ class qv_tune_t(C.Structure):
 
 class qv_plan_result_t(C.Structure):
     _fields_ = [("action", C.c_int32), ("value", C.c_float), ("q", C.c_float * QV_NUM_ACTIONS),
-                ("nodes_per_level", C.c_int32 * (QV_MAX_DEPTH + 1)), ("boundary_samples", C.c_int64)]
+                ("nodes_per_level", C.c_int32 * (QV_MAX_DEPTH + 1)), ("boundary_samples", C.c_int64),
+                ("depth_reached", C.c_int32)]
 
 
 class qv_level_view_t(C.Structure):

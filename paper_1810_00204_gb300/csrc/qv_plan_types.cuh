@@ -77,14 +77,28 @@ struct GridBar {
 struct PlanDev {
     int E, depth, K, weight_mode, leaf_mode, Bmax, rec_len, target, n_part;
     int sb_floats, sp_floats, q_floats;  // shared-memory band buffers
+    int cmax;          // children of one V-node at most: 5 min(K, Bmax + 1)
+    int n_xrec;        // per-(item, child) total records of multi-item groups
+    int n_frec;        // floats of the finalize chunk records
     uint64_t seed;
     const EpDev *eps;
     float *beliefs;
     int *count;        // [(d+1)][E] nodes per level
-    int *items;        // [(d+1)][E] expand work items per node
     int *uitems;       // [(d+1)][E] update work items per node
-    int *wb_stats;     // [(d+1)][E+1] work-list prefixes
     int *wb_upd;       // [(d+1)][E+1]
+    // expand work lists of level l: one group per V-node of level l - 1 with
+    // its children (at l = 0, the root of each episode), split into band
+    // ranges; group j of level l sits at gbase[l] + j
+    int *ngrp;         // [d] groups of level l
+    int *grp_off;      // [gbase[l] + l + j]: item prefix over the level's groups (G + 1 entries)
+    int *grp_rec;      // first record of a group with several items (-1: one item, totals in ntot)
+    int gbase[kMaxD + 1];
+    int *npre;         // [(d+1)][E+1] exclusive prefix of the level sizes over the episodes
+    int *fchunks;      // [d+1] beacon chunks per node of the finalize phase
+    int *wb_fin;       // [(d+1)][E+1] finalize work-list prefixes
+    float *ntot;       // [NI][kTot] per internal node totals
+    float *xrec;       // [n_xrec][kTot] per (item, child rank) totals
+    float *frec;       // [n_frec] label-histogram records of beacon chunks
     int *wb_leaf;      // [E+1]
     int *leaf_split;   // chunks per group of leaves in the leaf phase
     unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
@@ -112,6 +126,7 @@ struct PlanDev {
     unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
     ResultDev *result; // [E]
     const int *replay;
+    unsigned long long deadline_ns;  // anytime stop, 0 = none (status[1] set when it has run out)
     unsigned spin_limit;  // polls before a wait on other CTAs gives up
     EpDev ep0;            // the descriptor of a one-episode plan, in parameter space
 };

@@ -16,13 +16,17 @@ namespace {
 
 struct Layout {
     size_t total = 0;
-    size_t off_eps, off_count, off_items, off_uitems, off_wbs, off_wbu, off_wbl, off_parent, off_action, off_obs,
+    size_t off_eps, off_count, off_uitems, off_wbu, off_wbl, off_ngrp, off_grp_off, off_grp_rec, off_npre, off_fchunks,
+        off_wb_fin, off_ntot, off_xrec, off_frec, off_parent, off_action, off_obs,
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
         off_status, off_boundary, off_bar, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
-    int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0;
+    int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0, cmax = 0;
+    long long n_xrec = 0, n_frec = 0;
+    int gbase[QV_MAX_DEPTH + 1] = {};
+    long long ngrp_cap = 0;  // group slots over every level
     int band_cells = 0, items_per_cta = 0;  // the launch-shape knobs in effect
     int sb_floats = 0, sp_floats = 0, q_floats = 0;
     size_t smem = 0;
@@ -33,6 +37,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Upper bound on co-resident k_plan CTAs (8 per SM on 152 SMs).
 constexpr int kMaxGridSizing = 8 * 152;
+// SMs assumed when a workspace is sized without a device (GB300: 152).
+constexpr int kSizingSMs = 160;
 
 // ---- autotuner cache: shape class -> (band_cells, items_per_cta)
 constexpr int kDefaultBandCells = 2048;
@@ -84,6 +90,10 @@ qv_status validate(int E, const qv_model_t *models, const qv_plan_params_t *p) {
     if (p->leaf_mode != QV_LEAF_FUSED && p->leaf_mode != QV_LEAF_MATERIALISE)
         return qv_set_error(QV_ERR_INVALID, "plan: leaf_mode %d", p->leaf_mode);
     if (p->d_replay && E != 1) return qv_set_error(QV_ERR_INVALID, "plan: replay needs E = 1");
+    if (!(p->deadline_ms >= 0.0) || p->deadline_ms > 1e12)
+        return qv_set_error(QV_ERR_INVALID, "plan: deadline_ms %g", p->deadline_ms);
+    if (p->deadline_ms > 0.0 && p->leaf_mode != QV_LEAF_FUSED)
+        return qv_set_error(QV_ERR_INVALID, "plan: a deadline needs QV_LEAF_FUSED");
     if (p->band_cells < 0 || p->band_cells > (1 << 16))
         return qv_set_error(QV_ERR_INVALID, "plan: band_cells %d", p->band_cells);
     if (p->items_per_cta < 0 || p->items_per_cta > kMaxItemsPerCta)
@@ -186,7 +196,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
         L.sp_floats = std::max(L.sp_floats, (ep.band_rows + 4) * ep.P);
         if (p->leaf_mode == QV_LEAF_FUSED && D > 0) L.q_floats = std::max(L.q_floats, 5 * ep.band_rows * ep.P);
     }
-    L.smem = qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K).total;
+    L.cmax = 5 * std::min(K, L.Bmax + 1);
+    L.smem = qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax).total;
     if (L.smem > 200 * 1024) return qv_set_error(QV_ERR_INVALID, "plan: %zu bytes of shared memory", L.smem);
     L.grid = need_grid ? plan_grid(L.smem) : 0;
     if (need_grid && L.grid < 1) return qv_set_error(QV_ERR_CUDA, "plan: k_plan does not fit an SM");
@@ -197,6 +208,15 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     // sized for the largest possible grid so that sizing needs no device.
     L.target = L.items_per_cta * std::max(L.grid, 1);
     L.n_part = 2 * L.items_per_cta * kMaxGridSizing;
+    // per-(item, child) totals of groups with several items (those items
+    // number at most twice the target) and the beacon-chunk records of the
+    // finalize phase (several chunks per node only when a level's nodes
+    // times its chunks stay within the target, two or more chunks each);
+    // sized for the largest grid so that sizing needs no device
+    const long long per_sm = std::max<long long>(1, std::min<long long>(8, (228 * 1024) / std::max<size_t>(L.smem, 1)));
+    const long long tmax = static_cast<long long>(L.items_per_cta) * kSizingSMs * per_sm;
+    L.n_xrec = 2 * tmax * L.cmax;
+    L.n_frec = tmax * 30 * ((L.Bmax + 1) / 2) + 30LL * L.Bmax;
     long long gbase = 0, ibase = 0;
     long long run_g[QV_MAX_DEPTH + 1], run_i[QV_MAX_DEPTH + 1];
     for (int l = 0; l <= D; ++l) {
@@ -207,6 +227,13 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     }
     L.NT = gbase;
     L.NI = std::max<long long>(ibase, 1);
+    // expand groups of level l: the roots at l = 0, else the V-nodes of level l - 1
+    L.ngrp_cap = 0;
+    for (int l = 0; l <= D; ++l) {
+        L.gbase[l] = static_cast<int>(L.ngrp_cap);
+        L.ngrp_cap += l == 0 ? E : NB[l - 1];
+    }
+    if (L.ngrp_cap > (1LL << 30)) return qv_set_error(QV_ERR_INVALID, "plan: tree too large");
     if (L.NT > (1LL << 31) - 1 || L.NI * 5 * K > (1LL << 40))
         return qv_set_error(QV_ERR_INVALID, "plan: tree too large");
     const bool mat = p->leaf_mode == QV_LEAF_MATERIALISE || D == 0;
@@ -231,7 +258,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
                 ep.belief_off[l] = -1;
             }
         }
-    L.rec_len = 30 * L.Bmax + 36;
+    L.rec_len = qv::kLeafGroup * 5;  // the leaf phase's chunk records
     size_t o = 0;
     auto take = [&](size_t bytes) {
         o = align_up(o, 256);
@@ -241,10 +268,17 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     };
     const long long E1 = E + 1, D1 = D + 1;
     L.off_eps = take(sizeof(qv::EpDev) * E);
-    L.off_items = take(sizeof(int) * D1 * E);
     L.off_uitems = take(sizeof(int) * D1 * E);
-    L.off_wbs = take(sizeof(int) * D1 * E1);
     L.off_wbu = take(sizeof(int) * D1 * E1);
+    L.off_ngrp = take(sizeof(int) * D1);
+    L.off_grp_off = take(sizeof(int) * (L.ngrp_cap + D1));
+    L.off_grp_rec = take(sizeof(int) * L.ngrp_cap);
+    L.off_npre = take(sizeof(int) * D1 * E1);
+    L.off_fchunks = take(sizeof(int) * D1);
+    L.off_wb_fin = take(sizeof(int) * D1 * E1);
+    L.off_ntot = take(sizeof(float) * L.NI * qv::kTot);
+    L.off_xrec = take(sizeof(float) * L.n_xrec * qv::kTot);
+    L.off_frec = take(sizeof(float) * L.n_frec);
     L.off_wbl = take(sizeof(int) * E1);
     L.off_leaf_split = take(sizeof(int));
     L.off_parent = take(sizeof(int) * L.NT);
@@ -375,10 +409,21 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.eps = at<qv::EpDev>(ws, L.off_eps);
     d.beliefs = at<float>(ws, L.off_beliefs);
     d.count = at<int>(ws, L.off_count);
-    d.items = at<int>(ws, L.off_items);
     d.uitems = at<int>(ws, L.off_uitems);
-    d.wb_stats = at<int>(ws, L.off_wbs);
     d.wb_upd = at<int>(ws, L.off_wbu);
+    d.cmax = L.cmax;
+    d.n_xrec = static_cast<int>(std::min<long long>(L.n_xrec, (1LL << 31) - 1));
+    d.n_frec = static_cast<int>(std::min<long long>(L.n_frec, (1LL << 31) - 1));
+    d.ngrp = at<int>(ws, L.off_ngrp);
+    d.grp_off = at<int>(ws, L.off_grp_off);
+    d.grp_rec = at<int>(ws, L.off_grp_rec);
+    for (int l = 0; l <= params->depth; ++l) d.gbase[l] = L.gbase[l];
+    d.npre = at<int>(ws, L.off_npre);
+    d.fchunks = at<int>(ws, L.off_fchunks);
+    d.wb_fin = at<int>(ws, L.off_wb_fin);
+    d.ntot = at<float>(ws, L.off_ntot);
+    d.xrec = at<float>(ws, L.off_xrec);
+    d.frec = at<float>(ws, L.off_frec);
     d.wb_leaf = at<int>(ws, L.off_wbl);
     d.leaf_split = at<int>(ws, L.off_leaf_split);
     d.leaf_cnt = at<unsigned>(ws, L.off_leaf_cnt);
@@ -412,6 +457,9 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
+    d.deadline_ns = params->deadline_ms > 0.0
+                        ? std::max<unsigned long long>(1ull, static_cast<unsigned long long>(params->deadline_ms * 1e6))
+                        : 0ull;
     d.ep0 = L.eps[0];
     pl->reset_off = L.off_status;
     pl->reset_bytes = L.off_beliefs - L.off_status;
@@ -419,33 +467,48 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     pl->read_bytes = L.off_boundary + sizeof(unsigned long long) - L.off_count;
     // static state: descriptors, the root of every episode, level-0 work lists
     const int D = params->depth;
-    std::vector<int> cnt0(E, 1), it0(E), wbs(E + 1), wbu(E + 1), wbl(E + 1), neg(E, -1);
+    std::vector<int> cnt0(E, 1), it0(E), wbu(E + 1), wbl(E + 1), neg(E, -1), goff(E + 1), grec(E), npre(E + 1),
+        wbf(E + 1);
     std::vector<float> one(E, 1.0f);
     std::vector<unsigned long long> zero64(E, 0ull);
-    int s0 = 0, l0 = 0;
+    int s0 = 0, l0 = 0, g0 = 0, r0 = 0;
     // a depth-0 plan streams each root as one leaf, split into leaf0_split chunks
     const int leaf0_split = static_cast<int>(std::min<long long>(std::max<long long>(L.target / E, 1), 64));
+    const int fch0 = qv::finalize_chunks(E, L.target, L.Bmax);
     for (int e = 0; e < E; ++e) {
         const long long want = std::max<long long>(L.target / E, 1);
         it0[e] = static_cast<int>(std::min<long long>(std::max<long long>(want, 1), L.eps[e].bands));
-        wbs[e] = s0;
         wbu[e] = s0;
         s0 += D > 0 ? it0[e] : 0;
         wbl[e] = l0;
         l0 += leaf0_split;
+        // level 0's expand group of episode e: its root alone
+        const int gi = D > 0 ? qv::group_items(1, E, L.target, L.eps[e].bands) : 0;
+        goff[e] = g0;
+        g0 += gi;
+        grec[e] = gi >= 2 ? r0 : -1;
+        r0 += gi >= 2 ? gi : 0;
+        npre[e] = e;
+        wbf[e] = e * fch0;
     }
-    wbs[E] = s0;
     wbu[E] = s0;
     wbl[E] = l0;
+    goff[E] = g0;
+    npre[E] = E;
+    wbf[E] = E * fch0;
+    const int ngrp0 = E;
     auto up = [&](void *dst, const void *src, size_t bytes) {
         return qv_check_cuda(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, cs), "plan upload");
     };
     // root gids are 0..E-1 (level 0 is first in the node id space)
     if (up(const_cast<qv::EpDev *>(d.eps), L.eps.data(), sizeof(qv::EpDev) * E) != QV_OK ||
-        up(d.count, cnt0.data(), sizeof(int) * E) != QV_OK || up(d.items, it0.data(), sizeof(int) * E) != QV_OK ||
-        up(d.uitems, it0.data(), sizeof(int) * E) != QV_OK ||
-        up(d.wb_stats, wbs.data(), sizeof(int) * (E + 1)) != QV_OK ||
+        up(d.count, cnt0.data(), sizeof(int) * E) != QV_OK || up(d.uitems, it0.data(), sizeof(int) * E) != QV_OK ||
         up(d.wb_upd, wbu.data(), sizeof(int) * (E + 1)) != QV_OK ||
+        up(d.ngrp, &ngrp0, sizeof(int)) != QV_OK ||
+        up(d.grp_off + d.gbase[0], goff.data(), sizeof(int) * (E + 1)) != QV_OK ||
+        up(d.grp_rec + d.gbase[0], grec.data(), sizeof(int) * E) != QV_OK ||
+        up(d.npre, npre.data(), sizeof(int) * (E + 1)) != QV_OK || up(d.fchunks, &fch0, sizeof(int)) != QV_OK ||
+        up(d.wb_fin, wbf.data(), sizeof(int) * (E + 1)) != QV_OK ||
         up(d.wb_leaf, wbl.data(), sizeof(int) * (E + 1)) != QV_OK ||
         up(d.leaf_split, &leaf0_split, sizeof(int)) != QV_OK ||
         up(d.parent, neg.data(), sizeof(int) * E) != QV_OK || up(d.action, neg.data(), sizeof(int) * E) != QV_OK ||
@@ -508,7 +571,10 @@ extern "C" qv_status qv_plan_profile(qv_plan_t *pl, qv_launch_time_t *out, int32
             int level;
         };
         std::vector<Ph> ph;
-        for (int l = 0; l < D; ++l) ph.push_back({(l == D - 1 && !mat) ? "expand_fused" : "expand", l});
+        for (int l = 0; l < D; ++l) {
+            ph.push_back({(l == D - 1 && !mat) ? "expand_fused" : "expand", l});
+            ph.push_back({(l == D - 1 && !mat) ? "finalize_fused" : "finalize", l});
+        }
         if (D > 0 && mat) ph.push_back({"update", D - 1});
         if (D == 0 || mat) ph.push_back({"leaf", D});
         if (D > 0) ph.push_back({"backup", 0});
@@ -582,6 +648,7 @@ extern "C" qv_status qv_plan_decode(qv_plan_t *pl, const void *h_buf, qv_plan_re
         for (int a = 0; a < 5; ++a) o.q[a] = r[e].q[a];
         for (int l = 0; l <= D; ++l) o.nodes_per_level[l] = cnt[l * E + e];
         o.boundary_samples = static_cast<int64_t>(bnd);
+        o.depth_reached = r[e].pad;
     }
     if (status) pl->dirty = true;  // counters may be mid-way: the next run re-zeroes them
     if (status & qv::kErrTimeout) return qv_set_error(QV_ERR_TIMEOUT, "qv_plan: a bounded device wait timed out");

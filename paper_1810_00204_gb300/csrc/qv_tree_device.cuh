@@ -40,11 +40,22 @@
 
 namespace qv {
 
+// Per-warp buffers of the label histograms (phase_finalize): a tile of
+// kTileH x kTileW cells of the node's belief is formed from the parent's
+// belief with a two-cell rim, its cell words with a one-cell rim.
+constexpr int kTileH = 8, kTileW = 28;
+constexpr int kTileP = (kTileH + 4) * (kTileW + 4);   // parent values
+constexpr int kTileC = (kTileH + 2) * (kTileW + 2);   // node values, cell words
+constexpr int kTileFloats = kTileP + kTileC + (kTileC + 1) / 2;
+// Totals of one V-node per work item: [0, 5) null-label masses, [5, 10)
+// R(b, a) sums, [10, 35) Q-weighted null masses (fused level), [35] unused.
+constexpr int kTot = 36;
+
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
-    size_t sb, sp, cw, q, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, u_n, u_off, u_z, u_sa, u_se, scan,
-        flags, total;
-    __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K) {
+    size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, u_n, u_off, u_z, u_sa, u_se,
+        scan, flags, acc, c_pa, c_z, c_sa, c_se, total;
+    __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K, int cmax) {
         SmemLayout s;
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -57,12 +68,16 @@ struct SmemLayout {
         s.sp = take(sizeof(float) * sp_floats);      // parent band, two halo rows
         s.cw = take(sizeof(uint16_t) * sb_floats);   // cell words, one halo row
         s.q = take(sizeof(float) * q_floats);        // the band's rows of Q
+        // the label tiles of the finalize phase share the band buffers (the
+        // two phases are separated by grid barriers) when those are large enough
+        const size_t tile_bytes = sizeof(float) * kTileFloats * kWarps;
+        s.tile = (o - s.sb >= tile_bytes) ? s.sb : take(tile_bytes);
         s.ep = take(sizeof(EpDev));
         s.bco = take(sizeof(int) * 2 * Bm);          // beacon (row, col)
         s.hist = take(sizeof(float) * 5 * Bm);
         s.histq = take(sizeof(float) * 25 * Bm);
-        s.tot = take(sizeof(float) * 36);
-        s.red = take(sizeof(float) * kWarps * 36);
+        s.tot = take(sizeof(float) * kTot);
+        s.red = take(sizeof(float) * kWarps * kTot);
         s.P = take(sizeof(float) * 5 * (Bm + 1));
         s.C = take(sizeof(float) * 5 * (Bm + 1));
         s.cnt = take(sizeof(int) * 5 * (Bm + 1));
@@ -76,13 +91,18 @@ struct SmemLayout {
         s.u_se = take(sizeof(float) * 5 * K);
         s.scan = take(sizeof(int) * (kWarps + 4));
         s.flags = take(sizeof(int) * 8);
+        s.acc = take(sizeof(float) * kTot * cmax);   // per-child totals of a work item
+        s.c_pa = take(sizeof(int) * cmax);           // per child: action, observation, alpha / P, eta / P
+        s.c_z = take(sizeof(int) * cmax);
+        s.c_sa = take(sizeof(float) * cmax);
+        s.c_se = take(sizeof(float) * cmax);
         s.total = (o + 127) & ~size_t(127);
         return s;
     }
 };
 
 struct Smem {
-    float *sb, *sp, *q;
+    float *sb, *sp, *q, *tile;
     uint16_t *cw;
     EpDev *ep;
     int *bco;
@@ -91,6 +111,9 @@ struct Smem {
     int *u_n, *u_off, *u_z;
     float *u_sa, *u_se;
     int *scan, *flags;
+    float *acc;
+    int *c_pa, *c_z;
+    float *c_sa, *c_se;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -162,7 +185,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // arrival is an acquire-release add on the counter (after the CTA barrier,
 // so it publishes every thread's writes); the last arriver releases the
 // generation word, which the others acquire.
-__device__ bool grid_sync(const PlanDev &pl) {
+// With `deadline`, the last arriver also decides, once for every CTA,
+// whether the plan's time budget (from the kernel's first stamp) has run
+// out, and sets status[1] before it releases the others.
+__device__ bool grid_sync(const PlanDev &pl, bool deadline = false) {
     __shared__ int s_ok;
     fence_proxy_async_global();
     __syncthreads();
@@ -173,6 +199,8 @@ __device__ bool grid_sync(const PlanDev &pl) {
         unsigned prev;
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&pl.bar->count) : "memory");
         if (prev == gridDim.x - 1) {
+            if (deadline && globaltimer() - pl.stamps[0] >= pl.deadline_ns)
+                asm volatile("st.relaxed.gpu.global.u32 [%0], 1;" ::"l"(pl.status + 1) : "memory");
             asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&pl.bar->count) : "memory");
             asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&pl.bar->gen), "r"(g + 1u) : "memory");
         } else {
@@ -494,60 +522,126 @@ __device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e
     __syncthreads();
 }
 
-// The next level's work lists: band split per node from the actual level
-// size (about `target` items in all), then the per-episode prefix sums.
+// Finalize chunks per node of a level of n nodes: several beacon chunks
+// (at least one beacon per warp each) when the level holds fewer nodes than
+// the grid has work items, so that small levels spread their label
+// histograms over the grid.
+__host__ __device__ __forceinline__ int finalize_chunks(long long n, int target, int Bmax) {
+    if (n <= 0 || n * 2 > target) return 1;
+    const long long c = static_cast<long long>(target) / n;
+    const int cap = (Bmax + kWarps - 1) / kWarps;
+    return static_cast<int>(c < cap ? c : cap);
+}
+
+// Work items of one expand group: in proportion to its children, at least
+// one, at most one per band.
+__host__ __device__ __forceinline__ int group_items(int children, long long all_children, int target, int bands) {
+    if (children <= 0) return 0;
+    const long long want = (static_cast<long long>(target) * children + all_children - 1) / all_children;
+    return static_cast<int>(want < 1 ? 1 : (want > bands ? bands : want));
+}
+
+// The work lists of level l1 once every node of level l1 - 1 is final and
+// its children are numbered (one CTA):
+//  - npre[l1]: exclusive prefix of the level sizes over the episodes;
+//  - finalize (l1 < depth): fchunks[l1] beacon chunks per node, wb_fin[l1];
+//  - expand (l1 < depth): one group per V-node of level l1 - 1, its band
+//    ranges in proportion to its children (group_items), the item prefix
+//    and, for groups of several items, their first total record;
+//  - update (materialised leaves): about `target` items per level;
+//  - leaf (l1 = depth): groups of kLeafGroup leaves split into chunks.
 __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
-    // every thread of the CTA: one episode per thread per pass, block-wide
-    // sums and exclusive scans instead of a serial loop over the episodes
     const int E = pl.E;
-    int T = 0, G = 0;
+    // level sizes: totals, prefix over the episodes, leaf groups
+    int T = 0, Gl = 0;
     for (int e = threadIdx.x; e < E; e += blockDim.x) {
         const int c = __ldcg(pl.count + l1 * E + e);
         T += c;
-        G += (c + kLeafGroup - 1) / kLeafGroup;
+        Gl += (c + kLeafGroup - 1) / kLeafGroup;
     }
     int Tt, Gt;
     block_exclusive_scan(T, S.scan, Tt);
-    block_exclusive_scan(G, S.scan, Gt);
-    // items per node: the target rounded down, so that a phase's items fill
-    // at most the target (one wave of the grid per item aimed at per CTA)
+    block_exclusive_scan(Gl, S.scan, Gt);
     const long long want = Tt > 0 ? max(static_cast<long long>(pl.target) / Tt, 1LL) : 1;
     int C = 1;  // leaf chunks per group of leaves
     if (l1 == pl.depth) {
         C = static_cast<int>(min(max(Gt > 0 ? static_cast<long long>(pl.target) / Gt : 1LL, 1LL), 64LL));
         if (threadIdx.x == 0) *pl.leaf_split = C;
     }
-    int ws = 0, wu = 0, wl = 0;
+    const int fch = l1 < pl.depth ? finalize_chunks(Tt, pl.target, pl.Bmax) : 1;
+    if (threadIdx.x == 0 && l1 < pl.depth) pl.fchunks[l1] = fch;
+    int wn = 0, wu = 0, wl = 0;
     for (int base = 0; base < E; base += blockDim.x) {
         const int e = base + threadIdx.x;
-        int vs = 0, vu = 0, vl = 0, it = 0;
+        int vn = 0, vu = 0, vl = 0, it = 0;
         if (e < E) {
             const int c = __ldcg(pl.count + l1 * E + e);
             const int bands = __ldg(&pl.eps[e].bands);
             it = static_cast<int>(min(max(want, 1LL), static_cast<long long>(bands)));
-            vs = l1 < pl.depth ? c * it : 0;
+            vn = c;
             vu = c * it;
             vl = ((c + kLeafGroup - 1) / kLeafGroup) * C;
         }
-        int ts, tu, tl;
-        const int xs = block_exclusive_scan(vs, S.scan, ts);
+        int tn, tu, tl;
+        const int xn = block_exclusive_scan(vn, S.scan, tn);
         const int xu = block_exclusive_scan(vu, S.scan, tu);
         const int xl = block_exclusive_scan(vl, S.scan, tl);
         if (e < E) {
-            pl.items[l1 * E + e] = it;
+            pl.npre[l1 * (E + 1) + e] = wn + xn;
+            if (l1 < pl.depth) pl.wb_fin[l1 * (E + 1) + e] = (wn + xn) * fch;
             pl.uitems[l1 * E + e] = it;
-            pl.wb_stats[l1 * (E + 1) + e] = ws + xs;
             pl.wb_upd[l1 * (E + 1) + e] = wu + xu;
             if (l1 == pl.depth) pl.wb_leaf[e] = wl + xl;
         }
-        ws += ts;
+        wn += tn;
         wu += tu;
         wl += tl;
     }
     if (threadIdx.x == 0) {
-        pl.wb_stats[l1 * (E + 1) + E] = ws;
+        pl.npre[l1 * (E + 1) + E] = wn;
+        if (l1 < pl.depth) pl.wb_fin[l1 * (E + 1) + E] = wn * fch;
         pl.wb_upd[l1 * (E + 1) + E] = wu;
         if (l1 == pl.depth) pl.wb_leaf[E] = wl;
+    }
+    if (l1 >= pl.depth || l1 < 1) return;
+    // expand groups of level l1: the V-nodes of level l1 - 1 with their children
+    __syncthreads();
+    const int *np = pl.npre + (l1 - 1) * (E + 1);
+    const int G = __ldcg(np + E);
+    int *goff = pl.grp_off + pl.gbase[l1] + l1;
+    int *grec = pl.grp_rec + pl.gbase[l1];
+    auto children = [&](int j) {
+        const int e = find_episode(np, E, j);
+        const int lp = j - __ldcg(np + e);
+        const long long ia = static_cast<long long>(__ldg(&pl.eps[e].inode_base[l1 - 1]) + lp) * 5;
+        const int cnt = __ldcg(pl.count + l1 * E + e);
+        const int c0 = min(__ldcg(pl.choff + ia), cnt);
+        const int c1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
+        return make_int2(max(0, c1 - c0), __ldg(&pl.eps[e].bands));
+    };
+    int wi = 0, wr = 0;
+    for (int base = 0; base < G; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        int vi = 0, vr = 0;
+        if (j < G) {
+            const int2 cb = children(j);
+            vi = group_items(cb.x, Tt, pl.target, cb.y);
+            vr = vi >= 2 ? vi : 0;
+        }
+        int ti, tr;
+        const int xi = block_exclusive_scan(vi, S.scan, ti);
+        const int xr = block_exclusive_scan(vr, S.scan, tr);
+        if (j < G) {
+            goff[j] = wi + xi;
+            grec[j] = vr ? wr + xr : -1;
+        }
+        wi += ti;
+        wr += tr;
+    }
+    if (threadIdx.x == 0) {
+        goff[G] = wi;
+        pl.ngrp[l1] = G;
+        if (static_cast<long long>(wr) * pl.cmax > pl.n_xrec) atomicOr(pl.status, kErrCapacity);
     }
 }
 
@@ -609,155 +703,78 @@ __device__ __forceinline__ void build_band(const EpReg &ep, const float *sp, con
     __syncthreads();
 }
 
-// Integer floor(sqrt(t)) for 0 <= t < 2^24.
-__device__ __forceinline__ int isqrt_floor(int t) {
-    int i = static_cast<int>(sqrtf(static_cast<float>(t)));
-    while (i * i > t) --i;
-    while ((i + 1) * (i + 1) <= t) ++i;
-    return i;
-}
-
-// Cell t of the Manhattan diamond of radius R around (br, bc), counted row
-// by row from the top: rows i = 0..R hold 2i+1 cells (i^2 before row i), the
-// rows below mirror them.
-__device__ __forceinline__ void diamond_cell(int t, int R, int br, int bc, int &r, int &c) {
-    const int top = (R + 1) * (R + 1);
-    if (t < top) {
-        const int i = isqrt_floor(t);
-        r = br - R + i;
-        c = bc - i + (t - i * i);
-    } else {
-        const int t2 = (2 * R * R + 2 * R) - t;  // index counted from the last cell
-        const int i = isqrt_floor(t2);
-        r = br + R - i;
-        c = bc + i - (t2 - i * i);
-    }
-}
-
-// Label histograms of one staged band: every beacon's sensing diamond is
-// walked by one warp (lanes over the diamond's cells), cells whose label is
-// that beacon are summed in registers, then one warp reduction adds the
-// totals to the CTA's histograms.  Each beacon belongs to one warp, so no
-// two writers meet.
-template <bool FUSED>
-__device__ __forceinline__ void label_pass(const EpReg &ep, const float *sb, const uint16_t *cw, const float *q,
-                                           int r0, int r1, Smem &S, int Bm) {
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int R = ep.range;
-    const int ncell = 2 * R * R + 2 * R + 1;
-    const int qstride = (r1 - r0) * ep.P;
-    for (int k = wid; k < ep.B; k += kWarps) {
-        const int br = S.bco[2 * k], bc = S.bco[2 * k + 1];
-        if (br + R < r0 || br - R >= r1) continue;
-        float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float lq[FUSED ? 25 : 1];
-#pragma unroll
-        for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
-        for (int t = lane; t < ncell; t += 32) {
-            int r, c;
-            diamond_cell(t, R, br, bc, r, c);
-            if (r < r0 || r >= r1 || c < 0 || c >= ep.W) continue;
-            const int row = r - r0 + 1;
-            const unsigned cwv = cw[row * ep.P + c];
-            if (static_cast<int>(QV_CELL_LABEL(cwv)) != k) continue;
-            float out[5];
-            predict_at(ep, sb + row * ep.P, c, cwv, (r * ep.P + c) == ep.goal, S.lut, out);
-#pragma unroll
-            for (int a = 0; a < 5; ++a) la[a] += out[a];
-            if constexpr (FUSED) {
-                float qv[5];
-#pragma unroll
-                for (int ap = 0; ap < 5; ++ap) qv[ap] = q[ap * qstride + (r - r0) * ep.P + c];
-#pragma unroll
-                for (int a = 0; a < 5; ++a)
-#pragma unroll
-                    for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
-            }
-        }
-        if constexpr (FUSED) {
-            // lane i ends with the warp total of value i: 0..4 the label
-            // masses, 5..29 the Q-weighted ones
-            float v[32];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) v[a] = la[a];
-#pragma unroll
-            for (int i = 0; i < 25; ++i) v[5 + i] = lq[i];
-            v[30] = v[31] = 0.0f;
-            warp_reduce_scatter32(v);
-            if (lane < 5) S.hist[lane * Bm + k] += v[0];
-            else if (lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] += v[0];
-        } else {
-#pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                const float t = warp_sum(la[a]);
-                if (lane == 0) S.hist[a * Bm + k] += t;
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------- expand phase
+// Work items are (group, band range).  A group is one V-node of level l - 1
+// with all its children at level l (at l = 0, the root of one episode), so
+// the parent's band, the cell words and (fused level) Q are staged once per
+// band for every child.  Per band and child: the child's band Phi(parent, a,
+// z) (Eq. 3; written out when a later phase reads it), then on that band the
+// motion stencil for all five actions (Eq. 3 numerator, Eq. 10) and the sums
+// of the null-label cells and of the rewards (Sec. III), and at the fused
+// level the Q-weighted null sums.  The per-cell sums stay in registers; a
+// warp reduce-scatter per (child, band) and a fixed-order sum over the warps
+// add them into the child's totals in shared memory.  Cells with a beacon's
+// label enter through phase_finalize's tiles.
 template <bool FUSED>
-__device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S, uint64_t *mbar, unsigned &mphase,
+__device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
                              int &cur_e) {
-    const int E = pl.E, Bm = pl.Bmax, K = pl.K;
-    const int *wb = pl.wb_stats + l * (E + 1);
-    const int total = __ldcg(wb + E);
+    const int E = pl.E, K = pl.K;
+    const int G = __ldcg(pl.ngrp + l);
+    const int *goff = pl.grp_off + pl.gbase[l] + l;
+    const int *grec = pl.grp_rec + pl.gbase[l];
+    const int total = __ldcg(goff + G);
+    const int *np = l > 0 ? pl.npre + (l - 1) * (E + 1) : nullptr;
     constexpr int NV = FUSED ? 35 : 10;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
-#ifdef QV_TRACE
-        unsigned long long tr[kTraceWords] = {};
-#endif
-        QV_TRACE_MARK(tr, 2);
-        const int e = find_episode(wb, E, w);
+        const int j = find_episode(goff, G, w);
+        int e = j, lp = 0;
+        if (l > 0) {
+            e = find_episode(np, E, j);
+            lp = j - __ldcg(np + e);
+        }
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
-        const int items = __ldcg(pl.items + l * E + e);
-        const int w0e = __ldcg(wb + e);
-        const int rel = w - w0e;
-        const int local = rel / items, item = rel - local * items;
-#ifdef QV_TRACE
-        tr[0] = static_cast<unsigned long long>(l) | (static_cast<unsigned long long>(items) << 8) |
-                (static_cast<unsigned long long>(blockIdx.x) << 24);
-        tr[1] = static_cast<unsigned long long>(w);
-#endif
+        const int g0 = __ldcg(goff + j);
+        const int items = __ldcg(goff + j + 1) - g0, item = w - g0;
+        const int rec = __ldcg(grec + j);
         const int B = ep.B;
-        const int gid = ep.node_base[l] + local;
-        unsigned long long code = 0ull;
-        int pa = 0, pzv = 0;
-        float sa = 0.f, se = 0.f;
+        int c0 = 0, nc = 1;
         const float *src = ep.b0;
         if (l > 0) {
-            // the node's sample record in its parent's arrays: (iid_p * 5 + a) * K + j
-            const long long s = __ldcg(pl.src_slot + gid);
-            const int iid_p = static_cast<int>(s / (5LL * K));
-            pa = static_cast<int>((s / K) % 5);
-            const int par = iid_p - ep.inode_base[l - 1];
-            pzv = __ldcg(pl.slot_z + s);
-            const float p = __ldcg(pl.slot_P + s);
-            const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l - 1] + par);
-            code = (pcode * 5ull + pa) * static_cast<unsigned long long>(B + 1) + pzv;
-            sa = ep.acc / p;
-            se = ep.eta / p;
-            src = node_belief(pl, ep, l - 1, par);
-            if (item == 0 && threadIdx.x == 0) {
-                pl.parent[gid] = par;
-                pl.action[gid] = pa;
-                pl.obs[gid] = pzv;
-                pl.weight[gid] = __ldcg(pl.slot_w + s);
-                pl.pz[gid] = p;
-                pl.code[gid] = code;
+            const long long ia = static_cast<long long>(ep.inode_base[l - 1] + lp) * 5;
+            const int cnt = __ldcg(pl.count + l * E + e);
+            c0 = min(__ldcg(pl.choff + ia), cnt);
+            const int c1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
+            nc = min(max(0, c1 - c0), pl.cmax);
+            src = node_belief(pl, ep, l - 1, lp);
+        }
+        __syncthreads();  // the previous item's readers of the child table and totals are done
+        if (l > 0) {
+            for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+                const int gid = ep.node_base[l] + c0 + r;
+                // the child's sample record in its parent's arrays: (iid_p * 5 + a) * K + j
+                const long long s = __ldcg(pl.src_slot + gid);
+                const int a = static_cast<int>((s / K) % 5);
+                const int z = __ldcg(pl.slot_z + s);
+                const float p = __ldcg(pl.slot_P + s);
+                S.c_pa[r] = a;
+                S.c_z[r] = z;
+                S.c_sa[r] = ep.acc / p;
+                S.c_se[r] = ep.eta / p;
+                if (item == 0) {
+                    const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l - 1] + lp);
+                    pl.parent[gid] = lp;
+                    pl.action[gid] = a;
+                    pl.obs[gid] = z;
+                    pl.weight[gid] = __ldcg(pl.slot_w + s);
+                    pl.pz[gid] = p;
+                    pl.code[gid] = (pcode * 5ull + a) * static_cast<unsigned long long>(B + 1) + z;
+                }
             }
         }
-        float *dst = (l > 0 && write_node) ? pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N
-                                           : nullptr;
+        for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) S.acc[i] = 0.0f;
         __syncthreads();
-        for (int i = threadIdx.x; i < 5 * Bm; i += blockDim.x) S.hist[i] = 0.0f;
-        if (FUSED)
-            for (int i = threadIdx.x; i < 25 * Bm; i += blockDim.x) S.histq[i] = 0.0f;
-        for (int i = threadIdx.x; i < kWarps * 36; i += blockDim.x) S.red[i] = 0.0f;
-        float bgoal = 0.0f;
         const int band0 = static_cast<int>((static_cast<long long>(item) * ep.bands) / items);
         const int band1 = static_cast<int>((static_cast<long long>(item + 1) * ep.bands) / items);
         const int band_rows = ep.band_rows;
@@ -765,196 +782,359 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool write_node, Smem &S,
         const int P = er.P, P4 = P >> 2, goal = er.goal;
         const float slip = er.slip;
         const float *cost = er.cost;
-        const int grow = goal / P;
-        QV_TRACE_MARK(tr, 3);
-        // null-label mass, rewards and (fused) Q-weighted null mass in
-        // registers over every band of the item; labelled cells only add
-        // their reward here
-        float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
-#pragma unroll
-        for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
+        float *dst0 = (l > 0 && store) ? pl.beliefs + ep.belief_off[l] : nullptr;
         for (int band = band0; band < band1; ++band) {
             const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows);
             const int qstride = (r1 - r0) * P;
-            if (l == 0) {
-                if (!stage_band(er, src, r0, r1, 1, S.sb, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
-                    return false;
-            } else {
-                if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
-                    return false;
-                if (band == band0) QV_TRACE_MARK(tr, 10);
-                build_band(er, S.sp, S.cw, S.sb, r0, r1, pa, pzv, sa, se, S.lut, dst);
-            }
-            if (band == band0) QV_TRACE_MARK(tr, 11);
-            if (grow >= r0 && grow < r1) bgoal = S.sb[(grow - r0 + 1) * P + goal % P];
-            const int ng = (r1 - r0) * P4;
-            for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
-                const int rr = gi / P4, col = (gi - rr * P4) << 2;
-                const int y = (r0 + rr) * P + col;
-                Nbr4 n;
-                load_nbr(er, S.sb + (rr + 1) * P, S.cw + (rr + 1) * P, col, n);
-                float4 q4[5];
-                if constexpr (FUSED) {
+            if (!stage_band(er, src, r0, r1, l == 0 ? 1 : 2, l == 0 ? S.sb : S.sp, S.cw, FUSED ? S.q : nullptr, mbar,
+                            mphase, pl.status))
+                return false;
+            for (int r = 0; r < nc; ++r) {
+                if (l > 0)
+                    build_band(er, S.sp, S.cw, S.sb, r0, r1, S.c_pa[r], S.c_z[r], S.c_sa[r], S.c_se[r], S.lut,
+                               dst0 ? dst0 + static_cast<long long>(c0 + r) * er.N : nullptr);
+                float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
 #pragma unroll
-                    for (int ap = 0; ap < 5; ++ap)
-                        q4[ap] = *reinterpret_cast<const float4 *>(S.q + ap * qstride + rr * P + col);
-                }
-                float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (cost) c4 = __ldg(reinterpret_cast<const float4 *>(cost + y));
-                const float cst[4] = {c4.x, c4.y, c4.z, c4.w};
+                for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const unsigned cw = n.cw[j];
-                    float nb[4], out[5];
-                    inflow_nb(n, j, nb);
-                    predict_cell(nb, n.m[j + 1], cw, (y + j) == goal, slip, S.lut, out);
-                    const float r = stage_reward(QV_CELL_FREE(cw), (y + j) == goal, cst[j]);
-                    const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
+                for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
+                const int ng = (r1 - r0) * P4;
+                for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
+                    const int rr = gi / P4, col = (gi - rr * P4) << 2;
+                    const int y = (r0 + rr) * P + col;
+                    Nbr4 n;
+                    load_nbr(er, S.sb + (rr + 1) * P, S.cw + (rr + 1) * P, col, n);
+                    float4 q4[5];
+                    if constexpr (FUSED) {
 #pragma unroll
-                    for (int a = 0; a < 5; ++a) {
-                        const float v = out[a];
-                        acc_r[a] = fmaf(v, r, acc_r[a]);
-                        const float vn = v * isnull;
-                        acc_null[a] += vn;
-                        if constexpr (FUSED) {
-                            const float qj[5] = {(&q4[0].x)[j], (&q4[1].x)[j], (&q4[2].x)[j], (&q4[3].x)[j],
-                                                 (&q4[4].x)[j]};
+                        for (int ap = 0; ap < 5; ++ap)
+                            q4[ap] = *reinterpret_cast<const float4 *>(S.q + ap * qstride + rr * P + col);
+                    }
+                    float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (cost) c4 = __ldg(reinterpret_cast<const float4 *>(cost + y));
+                    const float cst[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                            for (int ap = 0; ap < 5; ++ap) acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const unsigned cw = n.cw[jj];
+                        float nb[4], out[5];
+                        inflow_nb(n, jj, nb);
+                        predict_cell(nb, n.m[jj + 1], cw, (y + jj) == goal, slip, S.lut, out);
+                        const float rw = stage_reward(QV_CELL_FREE(cw), (y + jj) == goal, cst[jj]);
+                        const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
+#pragma unroll
+                        for (int a = 0; a < 5; ++a) {
+                            const float v = out[a];
+                            acc_r[a] = fmaf(v, rw, acc_r[a]);
+                            const float vn = v * isnull;
+                            acc_null[a] += vn;
+                            if constexpr (FUSED) {
+                                const float qj[5] = {(&q4[0].x)[jj], (&q4[1].x)[jj], (&q4[2].x)[jj], (&q4[3].x)[jj],
+                                                     (&q4[4].x)[jj]};
+#pragma unroll
+                                for (int ap = 0; ap < 5; ++ap)
+                                    acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                            }
                         }
                     }
                 }
-            }
-#ifdef QV_TRACE
-            if (band == band0) {
+                // this (child, band)'s per-thread sums into the warp's slot:
+                // values 0..31 by a reduce-scatter (lane i gets value i),
+                // 32..34 by plain warp sums
+                {
+                    float v[32];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        v[a] = acc_null[a];
+                        v[5 + a] = acc_r[a];
+                    }
+#pragma unroll
+                    for (int i = 0; i < 22; ++i) {
+                        if constexpr (FUSED) v[10 + i] = acc_q[i];
+                        else v[10 + i] = 0.0f;
+                    }
+                    warp_reduce_scatter32(v);
+                    S.red[wid * kTot + lane] = v[0];
+                    if constexpr (FUSED) {
+#pragma unroll
+                        for (int i = 22; i < 25; ++i) {
+                            const float t = warp_sum(acc_q[i]);
+                            if (lane == 0) S.red[wid * kTot + 10 + i] = t;
+                        }
+                    }
+                }
                 __syncthreads();
-                QV_TRACE_MARK(tr, 12);
+                // the warps' slots in warp order into the child's totals (the
+                // next child's build touches neither S.red nor S.acc)
+                if (threadIdx.x < NV) {
+                    float t = 0.0f;
+                    for (int k = 0; k < kWarps; ++k) t += S.red[k * kTot + threadIdx.x];
+                    S.acc[r * kTot + threadIdx.x] += t;
+                }
             }
-#endif
-#ifdef QV_TRACE
-            if (band == band0) {
-                __syncthreads();
-                QV_TRACE_MARK(tr, 13);
-            }
-#endif
-            label_pass<FUSED>(er, S.sb, S.cw, S.q, r0, r1, S, Bm);
-#ifdef QV_TRACE
-            if (band == band0) {
-                __syncthreads();
-                QV_TRACE_MARK(tr, 14);
-            }
-#endif
         }
-        // fold the item's register sums into the per-warp totals
-        if constexpr (FUSED) {
-            // values 0..31 by a reduce-scatter (lane i gets value i), 32..34
-            // by plain warp sums
+        __syncthreads();
+        // the item's totals of every child: final when the group has one item,
+        // else one record per (item, child) that phase_finalize adds in order
+        for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
+            const int r = i / kTot, k = i - r * kTot;
+            const float v = S.acc[i];
+            if (rec < 0) {
+                pl.ntot[static_cast<long long>(ep.inode_base[l] + c0 + r) * kTot + k] = v;
+            } else {
+                const long long x = static_cast<long long>(rec + item) * pl.cmax + r;
+                if (x < pl.n_xrec) pl.xrec[x * kTot + k] = v;
+            }
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- label histograms
+// For one V-node (belief Phi(parent, a, z), or b0 at the root) and beacon
+// k: the five predicted masses sum_{y: label(y) = k} bbar_a(y) (Eq. 3
+// denominator) and, fused, the 25 Q-weighted ones sum bbar_a(y) Q(a', y),
+// into la / lq of the calling lane.  One warp: the beacon's sensing diamond
+// is covered by tiles of kTileH x kTileW cells; per tile the parent's values
+// with a two-cell rim and the cell words with a one-cell rim are read into
+// the warp's shared buffers, the node's belief is formed on the tile with a
+// one-cell rim, and the diamond's cells of label k predict from it.
+template <bool FUSED>
+__device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa, int zc, float sa, float se, int k,
+                            int br, int bc, float *tp, float *tc, uint16_t *tcw, const float *lut, float la[5],
+                            float lq[FUSED ? 25 : 1]) {
+    const int lane = threadIdx.x & 31;
+    const int R = ep.range, P = ep.P, H = ep.H, W = ep.W;
+    const int rlo = max(0, br - R), rhi = min(H - 1, br + R);
+    const int clo = max(0, bc - R), chi = min(W - 1, bc + R);
+    constexpr int PW = kTileW + 4, CW = kTileW + 2;
+    for (int y0 = rlo; y0 <= rhi; y0 += kTileH) {
+        for (int x0 = clo; x0 <= chi; x0 += kTileW) {
+            __syncwarp();
+            if (!root) {
+                for (int i = lane; i < kTileP; i += 32) {
+                    const int rr = i / PW, cc = i - rr * PW;
+                    const int r = y0 - 2 + rr, c = x0 - 2 + cc;
+                    tp[i] = (r >= 0 && r < H && c >= 0 && c < P) ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
+                }
+            }
+            for (int i = lane; i < kTileC; i += 32) {
+                const int rr = i / CW, cc = i - rr * CW;
+                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                tcw[i] = (r >= 0 && r < H && c >= 0 && c < P) ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
+                                                              : static_cast<uint16_t>(0);
+            }
+            __syncwarp();
+            // the node's belief on the tile and its rim
+            for (int i = lane; i < kTileC; i += 32) {
+                const int rr = i / CW, cc = i - rr * CW;
+                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                float v = 0.0f;
+                if (r >= 0 && r < H && c >= 0 && c < P) {
+                    const unsigned cw = tcw[i];
+                    if (root) {
+                        v = QV_CELL_FREE(cw) ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
+                    } else {
+                        const float *m = tp + (rr + 1) * PW + (cc + 1);
+                        const unsigned in = QV_CELL_INFLOW(cw);
+                        float nb[4];
+                        nb[kDirN] = (in & 1u) ? m[-PW] : 0.0f;
+                        nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
+                        nb[kDirS] = (in & 4u) ? m[PW] : 0.0f;
+                        nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
+                        const float p = predict_one(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, pa);
+                        v = p * (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+                    }
+                }
+                tc[i] = v;
+            }
+            __syncwarp();
+            // the diamond's cells of label k inside the tile
+            for (int i = lane; i < kTileH * kTileW; i += 32) {
+                const int rr = i / kTileW, cc = i - rr * kTileW;
+                const int r = y0 + rr, c = x0 + cc;
+                if (r > rhi || c > chi || abs(r - br) + abs(c - bc) > R) continue;
+                const unsigned cw = tcw[(rr + 1) * CW + cc + 1];
+                if (static_cast<int>(QV_CELL_LABEL(cw)) != k) continue;
+                const float *m = tc + (rr + 1) * CW + (cc + 1);
+                const unsigned in = QV_CELL_INFLOW(cw);
+                float nb[4], out[5];
+                nb[kDirN] = (in & 1u) ? m[-CW] : 0.0f;
+                nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
+                nb[kDirS] = (in & 4u) ? m[CW] : 0.0f;
+                nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
+                predict_cell(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, out);
+#pragma unroll
+                for (int a = 0; a < 5; ++a) la[a] += out[a];
+                if constexpr (FUSED) {
+                    float qv[5];
+#pragma unroll
+                    for (int ap = 0; ap < 5; ++ap) qv[ap] = __ldg(ep.Q + static_cast<size_t>(ap) * ep.N + r * P + c);
+#pragma unroll
+                    for (int a = 0; a < 5; ++a)
+#pragma unroll
+                        for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- finalize phase
+// Work items are (node of level l, beacon chunk).  Each item forms the
+// label histograms of its beacons (one warp per beacon, label_tiles); with
+// several chunks per node the items write records and the last to arrive
+// gathers them.  That item then adds the node's totals from its group's
+// work items in item order, takes the node's belief at the goal (for
+// R(b, a)), and finalises it: P(z | b, a), R(b, a), the K draws per action
+// (Alg. 3-4), the unique draws; at the fused level the leaf values and the
+// node's U_Q and U_V (Alg. 5-7).  At other levels the last node of an
+// episode numbers its children and the last episode publishes the next
+// level's work lists (NUMBER: every level but the fused deepest one).
+template <bool FUSED, bool NUMBER>
+__device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
+    const int E = pl.E, K = pl.K, Bm = pl.Bmax;
+    const int *wb = pl.wb_fin + l * (E + 1);
+    const int total = __ldcg(wb + E);
+    const int C = max(1, __ldcg(pl.fchunks + l));
+    const int stride = 30 * ((Bm + C - 1) / C);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tp = S.tile + wid * kTileFloats;
+    float *tc = tp + kTileP;
+    uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int e = find_episode(wb, E, w);
+        load_ep(pl, e, S, cur_e);
+        const EpDev &ep = *S.ep;
+        const int rel = w - __ldcg(wb + e);
+        const int local = rel / C, chunk = rel - local * C;
+        const int B = ep.B;
+        const int gid = ep.node_base[l] + local, iid = ep.inode_base[l] + local;
+        int pa = 0, zc = 0, lp = 0;
+        float sa = 1.0f, se = 1.0f;
+        const float *par = ep.b0;
+        if (l > 0) {
+            const long long s = __ldcg(pl.src_slot + gid);
+            const int iid_p = static_cast<int>(s / (5LL * K));
+            pa = static_cast<int>((s / K) % 5);
+            lp = iid_p - ep.inode_base[l - 1];
+            zc = __ldcg(pl.slot_z + s);
+            const float p = __ldcg(pl.slot_P + s);
+            sa = ep.acc / p;
+            se = ep.eta / p;
+            par = node_belief(pl, ep, l - 1, lp);
+        }
+        const EpReg er = ep_reg(ep);
+        const int bpc = (B + C - 1) / C;
+        const int k0 = min(B, chunk * bpc), k1 = min(B, k0 + bpc);
+        __syncthreads();  // the previous item's readers of the histograms are done
+        for (int k = k0 + wid; k < k1; k += kWarps) {
+            float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            float lq[FUSED ? 25 : 1];
+#pragma unroll
+            for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
+            label_tiles<FUSED>(er, par, l == 0, pa, zc, sa, se, k, S.bco[2 * k], S.bco[2 * k + 1], tp, tc, tcw, S.lut,
+                               la, lq);
+            // lane i ends with the warp total of value i: 0..4 the label
+            // masses, 5..29 the Q-weighted ones
             float v[32];
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                v[a] = acc_null[a];
-                v[5 + a] = acc_r[a];
-            }
+            for (int a = 0; a < 5; ++a) v[a] = la[a];
 #pragma unroll
-            for (int i = 0; i < 22; ++i) v[10 + i] = acc_q[i];
+            for (int i = 0; i < 25; ++i) {
+                if constexpr (FUSED) v[5 + i] = lq[i];
+                else v[5 + i] = 0.0f;
+            }
+            v[30] = v[31] = 0.0f;
             warp_reduce_scatter32(v);
-            S.red[wid * 36 + lane] += v[0];
-#pragma unroll
-            for (int i = 22; i < 25; ++i) {
-                const float t = warp_sum(acc_q[i]);
-                if (lane == 0) S.red[wid * 36 + 10 + i] += t;
-            }
-        } else {
-            float vals[NV];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                vals[a] = acc_null[a];
-                vals[5 + a] = acc_r[a];
-            }
-#pragma unroll
-            for (int i = 0; i < NV; ++i) {
-                const float v = warp_sum(vals[i]);
-                if (lane == 0) S.red[wid * 36 + i] += v;
-            }
+            if (lane < 5) S.hist[lane * Bm + k] = v[0];
+            else if (FUSED && lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] = v[0];
         }
-        QV_TRACE_MARK(tr, 4);
         __syncthreads();
-        if (threadIdx.x < NV) {
-            float t = 0.0f;
-            for (int k = 0; k < kWarps; ++k) t += S.red[k * 36 + threadIdx.x];
-            S.tot[threadIdx.x] = t;
-        }
-        if (threadIdx.x == 0) S.tot[35] = bgoal;  // zero unless this item holds the goal row
-        __syncthreads();
-        QV_TRACE_MARK(tr, 5);
-        const int iid = ep.inode_base[l] + local;
-        if (items > 1) {
-            // partial record of this work item: [hist 5B][histq 25B][tot 36]
-            if (w >= pl.n_part) {
-                if (threadIdx.x == 0) atomicOr(pl.status, kErrCapacity);
-                continue;
-            }
-            const int hq = FUSED ? 25 * B : 0;
-            const int nrec = 5 * B + hq + 36;
-            float *rec = pl.partials + static_cast<long long>(w) * pl.rec_len;
-            for (int i = threadIdx.x; i < nrec; i += blockDim.x) {
-                float v;
-                if (i < 5 * B) v = S.hist[(i / B) * Bm + (i % B)];
-                else if (i < 5 * B + hq) {
-                    const int k = i - 5 * B;
-                    v = S.histq[((k / 5) / B * Bm + (k / 5) % B) * 5 + k % 5];
-                } else v = S.tot[i - 5 * B - hq];
-                rec[i] = v;
-            }
+        if (C > 1) {
+            // a record of this chunk's beacons; the last chunk of the node gathers
+            float *recp = pl.frec + static_cast<long long>(w) * stride;
+            const bool room = static_cast<long long>(w + 1) * stride <= pl.n_frec;
+            if (room)
+                for (int i = threadIdx.x; i < (k1 - k0) * 30; i += blockDim.x) {
+                    const int k = k0 + i / 30, t = i % 30;
+                    recp[i] = t < 5 ? S.hist[t * Bm + k] : S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5];
+                }
             __syncthreads();
             if (threadIdx.x == 0) {
+                if (!room) atomicOr(pl.status, kErrCapacity);
                 const unsigned prev = arrive_acq_rel(pl.node_cnt + iid);
-                const int last = prev == static_cast<unsigned>(items - 1);
+                const int last = prev == static_cast<unsigned>(C - 1);
                 if (last) pl.node_cnt[iid] = 0u;
                 S.flags[0] = last;
             }
             __syncthreads();
-            QV_TRACE_MARK(tr, 6);
-            if (!S.flags[0]) {
-#ifdef QV_TRACE
-                trace_commit(tr, kTraceWords);
-#endif
-                continue;
+            if (!S.flags[0]) continue;
+            for (int i = threadIdx.x; i < B * 30; i += blockDim.x) {
+                const int k = i / 30, t = i - k * 30, c = k / bpc;
+                if (c == chunk) continue;
+                const long long wi = static_cast<long long>(w - chunk + c);
+                if ((wi + 1) * stride > pl.n_frec) continue;
+                const float v = __ldcg(pl.frec + wi * stride + (k - c * bpc) * 30 + t);
+                if (t < 5) S.hist[t * Bm + k] = v;
+                else if (FUSED) S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5] = v;
             }
-            // the last item sums every record of the node in item order
-            const float *base = pl.partials + static_cast<long long>(w0e + local * items) * pl.rec_len;
-            for (int i = threadIdx.x; i < nrec; i += blockDim.x) {
-                float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-                int it = 0;
-                for (; it + 4 <= items; it += 4) {
-                    t0 += __ldcg(base + static_cast<long long>(it) * pl.rec_len + i);
-                    t1 += __ldcg(base + static_cast<long long>(it + 1) * pl.rec_len + i);
-                    t2 += __ldcg(base + static_cast<long long>(it + 2) * pl.rec_len + i);
-                    t3 += __ldcg(base + static_cast<long long>(it + 3) * pl.rec_len + i);
+        }
+        // the node's totals: final, or the records of its group's items in order
+        {
+            int jg = e, r = 0;
+            if (l > 0) {
+                jg = __ldcg(pl.npre + (l - 1) * (E + 1) + e) + lp;
+                const int cnt = __ldcg(pl.count + l * E + e);
+                const int c0 = min(__ldcg(pl.choff + static_cast<long long>(ep.inode_base[l - 1] + lp) * 5), cnt);
+                r = local - c0;
+            }
+            const int *goff = pl.grp_off + pl.gbase[l] + l;
+            const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
+            constexpr int kGroups = kThreads / kTot;  // 7 partial sums per value
+            if (rec < 0) {
+                if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
+            } else {
+                const int nit = __ldcg(goff + jg + 1) - __ldcg(goff + jg);
+                const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
+                if (g < kGroups) {
+                    float sum = 0.0f;
+                    for (int it = g; it < nit; it += kGroups) {
+                        const long long x = static_cast<long long>(rec + it) * pl.cmax + r;
+                        if (x < pl.n_xrec) sum += __ldcg(pl.xrec + x * kTot + t);
+                    }
+                    S.red[g * kTot + t] = sum;
                 }
-                for (; it < items; ++it) t0 += __ldcg(base + static_cast<long long>(it) * pl.rec_len + i);
-                const float t = (t0 + t1) + (t2 + t3);
-                if (i < 5 * B) S.hist[(i / B) * Bm + (i % B)] = t;
-                else if (i < 5 * B + hq) {
-                    const int k = i - 5 * B;
-                    S.histq[((k / 5) / B * Bm + (k / 5) % B) * 5 + k % 5] = t;
-                } else S.tot[i - 5 * B - hq] = t;
+                __syncthreads();
+                if (threadIdx.x < kTot) {
+                    float sum = 0.0f;
+                    for (int g2 = 0; g2 < kGroups; ++g2) sum += S.red[g2 * kTot + threadIdx.x];
+                    S.tot[threadIdx.x] = sum;
+                }
+            }
+            if (threadIdx.x == 0) {
+                // the node's belief at the goal, whose arrivals R(b, a) must not pay
+                const int y = ep.goal;
+                float bg;
+                if (l == 0) {
+                    bg = __ldg(par + y);
+                } else {
+                    const unsigned cw = __ldg(ep.cell + y);
+                    const unsigned in = QV_CELL_INFLOW(cw);
+                    float nb[4];
+                    nb[kDirN] = (in & 1u) ? __ldcg(par + y - ep.P) : 0.0f;
+                    nb[kDirE] = (in & 2u) ? __ldcg(par + y + 1) : 0.0f;
+                    nb[kDirS] = (in & 4u) ? __ldcg(par + y + ep.P) : 0.0f;
+                    nb[kDirW] = (in & 8u) ? __ldcg(par + y - 1) : 0.0f;
+                    bg = predict_one(nb, __ldcg(par + y), cw, true, ep.slip, S.lut, pa) *
+                         (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+                }
+                S.flags[4] = __float_as_int(bg);
             }
             __syncthreads();
         }
-        QV_TRACE_MARK(tr, 7);
-        finalize_node(pl, ep, l, local, FUSED, S.tot[35], code, S);
-        QV_TRACE_MARK(tr, 8);
-        // the fused level's children are leaves: they are numbered in the
-        // backup phase, beside the backup, and need no work lists
-        if constexpr (!FUSED) node_done(pl, l, e, ep, S);
-        QV_TRACE_MARK(tr, 9);
-#ifdef QV_TRACE
-        tr[0] |= 1ull << 56;  // this item finalised its node
-        trace_commit(tr, kTraceWords);
-#endif
+        const unsigned long long code = __ldcg(pl.code + gid);
+        finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
+        if constexpr (NUMBER) node_done(pl, l, e, ep, S);
     }
     return true;
 }
@@ -1205,19 +1385,28 @@ __device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep,
 // its finalisation); every CTA writes leaf records, one CTA per episode backs
 // up the levels above.  Materialised leaves: one CTA per episode backs up
 // every level.  Each level handles its (node, action) pairs in parallel.
-__device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
-    const int K = pl.K, D = pl.depth;
+// D: the depth of the tree built (the plan's depth, or less when its
+// deadline ran out; then the leaves' records are written here and the
+// counts of the levels not built are cleared).
+__device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e, int D) {
+    const int K = pl.K;
     const bool fused = pl.leaf_mode != QV_LEAF_MATERIALISE;
+    const bool cut = D < pl.depth;
     if (fused) {
         // number the leaves of every episode (the children of the fused
         // level), on CTAs other than those that back the episode up when
         // there are enough; their records are written on demand
-        // (k_leaf_records)
+        // (k_leaf_records), or here when the search stopped early
         const int first = gridDim.x >= 2 * pl.E ? pl.E : 0;
         for (int e = static_cast<int>(blockIdx.x) - first; e >= 0 && e < pl.E;
              e += static_cast<int>(gridDim.x) - first) {
             load_ep(pl, e, S, cur_e);
             compact_episode(pl, D - 1, *S.ep, e, S);
+            if (cut) {
+                const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
+                for (int t = threadIdx.x; t < 5 * K * n; t += blockDim.x) leaf_records(pl, *S.ep, D - 1, t, true);
+                for (int l = D + 1 + threadIdx.x; l <= pl.depth; l += blockDim.x) pl.count[l * pl.E + e] = 0;
+            }
         }
     }
     for (int e = blockIdx.x; e < pl.E; e += gridDim.x) {
@@ -1269,7 +1458,7 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
             r.action = best;
             for (int a = 0; a < 5; ++a) r.q[a] = q[a];
             r.value = __ldcg(pl.value + ep.node_base[0]);
-            r.pad = 0;
+            r.pad = D;  // the depth reached
             pl.result[e] = r;
         }
         __syncthreads();
@@ -1280,9 +1469,15 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e) {
 __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
-    const SmemLayout L = SmemLayout::make(pl.sb_floats, pl.sp_floats, pl.q_floats, pl.Bmax, pl.K);
+    const SmemLayout L = SmemLayout::make(pl.sb_floats, pl.sp_floats, pl.q_floats, pl.Bmax, pl.K, pl.cmax);
     Smem S;
     S.sb = reinterpret_cast<float *>(smem_raw + L.sb);
+    S.tile = reinterpret_cast<float *>(smem_raw + L.tile);
+    S.acc = reinterpret_cast<float *>(smem_raw + L.acc);
+    S.c_pa = reinterpret_cast<int *>(smem_raw + L.c_pa);
+    S.c_z = reinterpret_cast<int *>(smem_raw + L.c_z);
+    S.c_sa = reinterpret_cast<float *>(smem_raw + L.c_sa);
+    S.c_se = reinterpret_cast<float *>(smem_raw + L.c_se);
     S.sp = reinterpret_cast<float *>(smem_raw + L.sp);
     S.cw = reinterpret_cast<uint16_t *>(smem_raw + L.cw);
     S.q = reinterpret_cast<float *>(smem_raw + L.q);
@@ -1316,23 +1511,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     stamp(pl, slot++);
     const int D = pl.depth;
     const bool mat = pl.leaf_mode == QV_LEAF_MATERIALISE;
+    // with a deadline every level also forms its children's leaf values, so
+    // that the search can stop after any level (anytime, Sec. IV-C)
+    const bool dl = pl.deadline_ns != 0ull;
+    int Deff = D;
     for (int l = 0; l < D; ++l) {
-        const bool fused = (l == D - 1) && !mat;
+        const bool last = l == D - 1;
+        const bool fused = (last && !mat) || dl;
+        const bool number = !(last && !mat);  // a level below is numbered by this one's finalisation
         // a level's beliefs are stored when a later phase reads them
         const bool store = l > 0 && (l < D - 1 || mat);
         const bool ok = fused ? phase_expand<true>(pl, l, store, S, &mbar, mphase, cur_e)
                               : phase_expand<false>(pl, l, store, S, &mbar, mphase, cur_e);
         if (!ok && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
-#ifdef QV_TRACE
-        {
-            const unsigned long long t[3] = {static_cast<unsigned long long>(l) | (0xFFull << 8) |
-                                                 (static_cast<unsigned long long>(blockIdx.x) << 24),
-                                             0ull, globaltimer()};
-            trace_commit(t, 3);
-        }
-#endif
         if (!grid_sync(pl)) return;
         stamp(pl, slot++);
+        if (!fused) phase_finalize<false, true>(pl, l, S, cur_e);
+        else if (number) phase_finalize<true, true>(pl, l, S, cur_e);
+        else phase_finalize<true, false>(pl, l, S, cur_e);
+        if (!grid_sync(pl, dl && !last)) return;
+        stamp(pl, slot++);
+        if (dl && !last) {
+            if (threadIdx.x == 0) S.flags[5] = static_cast<int>(*((volatile unsigned *)(pl.status + 1)));
+            __syncthreads();
+            if (S.flags[5]) {
+                Deff = l + 1;
+                break;
+            }
+        }
     }
     if (D > 0 && mat) {
         if (!phase_update(pl, D - 1, S, &mbar, mphase, cur_e) && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
@@ -1345,7 +1551,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         stamp(pl, slot++);
     }
     if (D > 0) {
-        phase_backup(pl, S, cur_e);
+        phase_backup(pl, S, cur_e, Deff);
         stamp(pl, slot++);
     }
 }
@@ -1357,6 +1563,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
 __global__ void __launch_bounds__(256) k_leaf_records(PlanDev pl) {
     const int D = pl.depth, K = pl.K;
     for (int e = 0; e < pl.E; ++e) {
+        if (pl.result[e].pad < D) continue;  // stopped early: its leaves' records are written
         const EpDev &ep = pl.eps[e];
         const int n = __ldcg(pl.count + (D - 1) * pl.E + e);
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 5 * K * n; t += gridDim.x * blockDim.x)

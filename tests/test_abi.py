@@ -75,6 +75,16 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
     assert L.qv_plan_autotune_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) >= \
         L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p))
+    # the anytime stop: a budget in ms, >= 0 (0 = none), fused leaves only
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 0, 0, 5.0)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 0, 0, -1.0)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 0, 0, float("nan"))
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, N.QV_LEAF_MATERIALISE, None, 0, 0, 0, 5.0)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    assert b"deadline" in L.qv_last_error()
     p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
     m.num_beacons = N.QV_MAX_BEACONS + 1
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
