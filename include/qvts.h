@@ -30,6 +30,14 @@
  *   - Device scratch comes from a caller-provided workspace (d_ws, ws_bytes);
  *     the matching *_workspace_bytes call gives its size.  The library itself
  *     allocates no device memory in any call declared here.
+ *   - Fault injection for tests of the caller's error handling, read from
+ *     the environment variable QVTS_FAULT on every call, before any device
+ *     work: "timeout" makes every wait on other CTAs give up at once (the
+ *     call reports QV_ERR_TIMEOUT and the context stays usable), "oom" makes
+ *     mdp_value_iterate, fib_value_iterate, belief_correct and
+ *     qv_plan_create report QV_ERR_WORKSPACE (this library's out-of-memory),
+ *     "invalid" makes those and belief_predict and qv_plan_run report
+ *     QV_ERR_INVALID.  Unset (or any other value): no injection.
  */
 #ifndef QVTS_H
 #define QVTS_H
@@ -341,6 +349,14 @@ qv_status qv_plan_create(int32_t E, const qv_model_t *models, const float *const
                          void *d_ws, size_t ws_bytes, qv_plan_t **plan_out,
                          qv_stream_t stream);
 qv_status qv_plan_run(qv_plan_t *plan, qv_stream_t stream);
+/* qv_plan_set_episode_word: take the Philox episode word of the plan's
+ * draws (counter word 1, Alg. 3) from a caller-owned device uint32 read at
+ * every run: episode e of the batch draws with *d_word + e instead of
+ * params.episode + e.  A closed loop (Alg. 1's outer loop) then re-runs one
+ * plan step after step, writing the step's word on its stream, instead of
+ * creating a plan per step.  NULL returns to params.episode.  Drops a
+ * captured graph (capture again after this call). */
+qv_status qv_plan_set_episode_word(qv_plan_t *plan, const uint32_t *d_word);
 /* Capture the launches of qv_plan_run in a CUDA graph owned by the plan;
  * later qv_plan_run calls launch the graph. */
 qv_status qv_plan_capture_graph(qv_plan_t *plan, qv_stream_t stream);

@@ -102,7 +102,7 @@ def lib():
         L.or_env_step.restype = C.c_int
         L.or_closed_loop.argtypes = [P, vp, C.c_int, vp, vp, C.c_int, C.c_int, C.c_uint64, C.c_int] + [vp] * 8
         L.or_closed_loop.restype = C.c_int
-        L.or_forward_sample.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_uint64, vp]
+        L.or_forward_sample.argtypes = [P, vp, C.c_int, C.c_int, C.c_uint64, C.c_uint32, C.c_int, C.c_uint64, vp, vp]
         L.or_forward_sample.restype = None
         P9 = C.POINTER(_Problem9)
         L.or9_tprime_row.argtypes = [P9, C.c_int, C.c_int, vp, vp, vp]
@@ -554,14 +554,18 @@ def closed_loop(w, Q, b0s, x0s, depth=None, K=None, seed=None, max_steps=50, **k
     return o
 
 
-def forward_sample(w, b, a, K, seed=0, episode=0, level=0, path=0):
+def forward_sample(w, b, a, K, seed=0, episode=0, level=0, path=0, want_boundary=False):
     """K measurements for (b, a) by Alg. 4's ancestral sampler: x ~ b,
-    x' ~ T(x, a, .), z ~ O(x', .)."""
+    x' ~ T(x, a, .), z ~ O(x', .).  With want_boundary also the flags of
+    draws whose x lies within 1e-5 of the total from a step of b's FP32
+    cumulative sum."""
     p = _prob(w)
     b = np.ascontiguousarray(np.asarray(b, np.float64).reshape(-1))
     z = np.zeros(K, np.int32)
-    lib().or_forward_sample(p.ref, _p(b), int(a), int(K), int(seed), int(episode), int(level), int(path), _p(z))
-    return z
+    bd = np.zeros(K, np.int32) if want_boundary else None
+    lib().or_forward_sample(p.ref, _p(b), int(a), int(K), int(seed), int(episode), int(level), int(path), _p(z),
+                            None if bd is None else _p(bd))
+    return (z, bd) if want_boundary else z
 
 
 def transition_row_dslip(w, x, a):

@@ -1238,7 +1238,7 @@ int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0
  * uniforms of sample k are words 3k, 3k + 1, 3k + 2 of the Philox stream of
  * (level, path); the CDF of b runs in FP32, as the sampler kernels' do.    */
 void or_forward_sample(const or_problem *p, const double *b, int a, int K, uint64_t seed, uint32_t episode,
-                       int level, uint64_t path, int *z) {
+                       int level, uint64_t path, int *z, int *boundary) {
     const int n = p->H * p->W, nz = p->B + 1;
     int *label = (int *)malloc(sizeof(int) * n);
     float *C = (float *)malloc(sizeof(float) * n);
@@ -1258,6 +1258,13 @@ void or_forward_sample(const or_problem *p, const double *b, int a, int K, uint6
         int x = n - 1;
         for (int i = 0; i < n; ++i)
             if (t < C[i]) { x = i; break; }
+        /* a draw within 1e-5 of the total from a step of the cumulative sum:
+         * another summation order of the same FP32 sums may pick the
+         * neighbouring cell there */
+        if (boundary) {
+            const double tol = 1e-5 * (double)C[n - 1];
+            boundary[k] = fabs((double)t - (double)C[x]) < tol || (x > 0 && fabs((double)t - (double)C[x - 1]) < tol);
+        }
         /* x' ~ T(x, a, .) */
         int y = x;
         if (!p->occ[x] && x != p->goal && a != 4) {

@@ -139,7 +139,7 @@ int or_closed_loop(const or_problem *p, const double *Q, int E, const double *b0
 
 /* ---- Ancestral forward sampling (Alg. 4) ---- */
 void or_forward_sample(const or_problem *p, const double *b, int a, int K, uint64_t seed, uint32_t episode,
-                       int level, uint64_t path, int *z);
+                       int level, uint64_t path, int *z, int *boundary);
 
 int or_num_threads(void);
 void or_set_threads(int n);

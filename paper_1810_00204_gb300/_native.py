@@ -133,6 +133,7 @@ SIGNATURES = {
     "qv_plan_workspace_bytes": (_sz, [_i32, _M, _PP]),
     "qv_plan_create": (C.c_int, [_i32, _M, _vp, _vp, _PP, _vp, _sz, C.POINTER(_vp), _vp]),
     "qv_plan_run": (C.c_int, [_vp, _vp]),
+    "qv_plan_set_episode_word": (C.c_int, [_vp, _vp]),
     "qv_plan_capture_graph": (C.c_int, [_vp, _vp]),
     "qv_plan_read": (C.c_int, [_vp, C.POINTER(qv_plan_result_t), _vp]),
     "qv_plan_readback_bytes": (_sz, [_vp]),

@@ -356,12 +356,20 @@ def run_episodes(model: Model, Q: torch.Tensor, b0s: Sequence[torch.Tensor], sta
     hist_z = torch.full((max_steps, E), -1, dtype=torch.int32, device=dev) if history else None
     if history:
         hist_s[0].copy_(state)
+    # one batched plan for every step: it reads the beliefs B in place, and
+    # the step's Philox episode word t * E comes from a device word written
+    # on the stream before each run
+    plan = Plan([model] * E, [Q] * E, [B[e] for e in range(E)], depth=depth, K=K, seed=seed, episode=0,
+                stream=stream)
+    word = torch.zeros(1, dtype=torch.int32, device=dev)
+    plan.set_episode_word(word)
+    act = lib().qv_plan_actions_device(plan.handle, C.byref(stride))
+    cs = torch.cuda.current_stream(dev) if stream is None else stream
     t = 0
     for t in range(max_steps):
-        plan = Plan([model] * E, [Q] * E, [B[e] for e in range(E)], depth=depth, K=K, seed=seed, episode=t * E,
-                    stream=stream)
+        with torch.cuda.stream(cs):
+            word.fill_(t * E)
         plan.run(stream)
-        act = lib().qv_plan_actions_device(plan.handle, C.byref(stride))
         check(lib().qv_env_step(C.byref(model.struct), E, act, stride.value, _ptr(state), int(seed), t, _ptr(obs),
                                 _ptr(steps), _ptr(ret), _ptr(done), _stream(stream)), "qv_env_step")
         check(lib().qv_belief_update_batched(C.byref(model.struct), E, _ptr(B), act, stride.value, _ptr(obs), wsp,
@@ -557,6 +565,13 @@ class Plan:
 
     def run(self, stream=None):
         check(lib().qv_plan_run(self.handle, _stream(stream)), "qv_plan_run")
+
+    def set_episode_word(self, word: Optional[torch.Tensor]):
+        """Draw with the device uint32 word[0] + e (read at every run) as the
+        Philox episode word of episode e (qv_plan_set_episode_word); None
+        returns to the episode given at creation.  Drops a captured graph."""
+        self._episode_word = word
+        check(lib().qv_plan_set_episode_word(self.handle, _ptr(word)), "qv_plan_set_episode_word")
 
     def capture_graph(self, stream=None):
         s = torch.cuda.Stream() if stream is None else stream

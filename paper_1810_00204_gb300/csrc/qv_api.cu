@@ -28,6 +28,17 @@ unsigned qv_cross_spin_limit() {
     return (f && std::strcmp(f, "timeout") == 0) ? 0u : qv::kSpinLimit;
 }
 
+qv_status qv_injected_fault(const char *where, bool takes_workspace) {
+    const char *f = std::getenv("QVTS_FAULT");
+    if (!f) return QV_OK;
+    if (takes_workspace && std::strcmp(f, "oom") == 0)
+        return qv_set_error(QV_ERR_WORKSPACE, "%s: injected fault (QVTS_FAULT=oom): the workspace cannot hold the call",
+                            where);
+    if (std::strcmp(f, "invalid") == 0)
+        return qv_set_error(QV_ERR_INVALID, "%s: injected fault (QVTS_FAULT=invalid)", where);
+    return QV_OK;
+}
+
 int qv_num_sms() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;

@@ -211,7 +211,9 @@ qv_status check_model(const qv_model_t *m, const char *who) {
 
 extern "C" qv_status belief_predict(const qv_model_t *m, const float *d_b, int32_t action, float *d_bbar,
                                     qv_stream_t stream) {
-    qv_status st = qv::check_model(m, "belief_predict");
+    qv_status st = qv_injected_fault("belief_predict", false);
+    if (st != QV_OK) return st;
+    st = qv::check_model(m, "belief_predict");
     if (st != QV_OK) return st;
     if (!d_b || !d_bbar) return qv_set_error(QV_ERR_INVALID, "belief_predict: null pointer");
     if (action < 0 || action >= QV_NUM_ACTIONS) return qv_set_error(QV_ERR_INVALID, "belief_predict: action %d", action);
@@ -230,6 +232,7 @@ extern "C" size_t belief_correct_workspace_bytes(const qv_model_t *) {
 
 extern "C" qv_status belief_correct(const qv_model_t *m, const float *d_bbar, int32_t z, float *d_bout, float *d_pz,
                                     void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    if (const qv_status inj = qv_injected_fault("belief_correct", true)) return inj;
     qv_status st = qv::check_model(m, "belief_correct");
     if (st != QV_OK) return st;
     if (!d_bbar || !d_bout || !d_pz || !d_ws) return qv_set_error(QV_ERR_INVALID, "belief_correct: null pointer");

@@ -218,3 +218,9 @@ int qv_num_sms();
 // that is not already satisfied gives up at once and reports QV_ERR_TIMEOUT,
 // so the timeout path runs without a real hang).
 unsigned qv_cross_spin_limit();
+// Host-side fault injection by the environment variable QVTS_FAULT, checked
+// on entry before any device work: "oom" makes calls that take a workspace
+// return QV_ERR_WORKSPACE (the library's out-of-memory: it allocates no
+// device memory itself), "invalid" makes the instrumented calls return
+// QV_ERR_INVALID; each leaves a message naming the injection.
+qv_status qv_injected_fault(const char *where, bool takes_workspace);

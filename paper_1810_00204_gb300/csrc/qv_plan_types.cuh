@@ -78,6 +78,7 @@ struct PlanDev {
     int E, depth, K, weight_mode, leaf_mode, Bmax, rec_len, target, n_part;
     int sb_floats, sp_floats, q_floats;  // shared-memory band buffers
     int cmax;          // children of one V-node at most: 5 min(K, Bmax + 1)
+    int kslots;        // per-warp child slots of the expand phase (expand_slots)
     int n_xrec;        // per-(item, child) total records of multi-item groups
     int n_frec;        // floats of the finalize chunk records
     uint64_t seed;
@@ -126,6 +127,8 @@ struct PlanDev {
     unsigned long long *stamps;  // [kStamps] globaltimer at phase boundaries
     ResultDev *result; // [E]
     const int *replay;
+    const uint32_t *episode_word;  // nullable: episode e draws with *episode_word + e (read at each run)
+    uint32_t episode0;             // params.episode: episode e's own word is episode0 + e
     unsigned long long deadline_ns;  // anytime stop, 0 = none (status[1] set when it has run out)
     unsigned spin_limit;  // polls before a wait on other CTAs gives up
     EpDev ep0;            // the descriptor of a one-episode plan, in parameter space

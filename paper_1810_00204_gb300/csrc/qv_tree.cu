@@ -197,7 +197,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
         if (p->leaf_mode == QV_LEAF_FUSED && D > 0) L.q_floats = std::max(L.q_floats, 5 * ep.band_rows * ep.P);
     }
     L.cmax = 5 * std::min(K, L.Bmax + 1);
-    L.smem = qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax).total;
+    L.smem = qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax, qv::expand_slots(L.cmax))
+                 .total;
     if (L.smem > 200 * 1024) return qv_set_error(QV_ERR_INVALID, "plan: %zu bytes of shared memory", L.smem);
     L.grid = need_grid ? plan_grid(L.smem) : 0;
     if (need_grid && L.grid < 1) return qv_set_error(QV_ERR_CUDA, "plan: k_plan does not fit an SM");
@@ -360,6 +361,7 @@ extern "C" size_t qv_plan_workspace_bytes(int32_t E, const qv_model_t *models, c
 extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const float *const *d_Q,
                                     const float *const *d_b0, const qv_plan_params_t *params, void *d_ws,
                                     size_t ws_bytes, qv_plan_t **plan_out, qv_stream_t stream) {
+    if (const qv_status inj = qv_injected_fault("qv_plan_create", true)) return inj;
     if (!plan_out || !d_Q || !d_b0 || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_plan_create: null pointer");
     *plan_out = nullptr;
     Layout L;
@@ -412,6 +414,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.uitems = at<int>(ws, L.off_uitems);
     d.wb_upd = at<int>(ws, L.off_wbu);
     d.cmax = L.cmax;
+    d.kslots = qv::expand_slots(L.cmax);
     d.n_xrec = static_cast<int>(std::min<long long>(L.n_xrec, (1LL << 31) - 1));
     d.n_frec = static_cast<int>(std::min<long long>(L.n_frec, (1LL << 31) - 1));
     d.ngrp = at<int>(ws, L.off_ngrp);
@@ -457,6 +460,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
+    d.episode_word = nullptr;
+    d.episode0 = params->episode;
     d.deadline_ns = params->deadline_ms > 0.0
                         ? std::max<unsigned long long>(1ull, static_cast<unsigned long long>(params->deadline_ms * 1e6))
                         : 0ull;
@@ -524,7 +529,20 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     return QV_OK;
 }
 
+extern "C" qv_status qv_plan_set_episode_word(qv_plan_t *pl, const uint32_t *d_word) {
+    if (!pl) return qv_set_error(QV_ERR_INVALID, "qv_plan_set_episode_word: null plan");
+    if (reinterpret_cast<uintptr_t>(d_word) & 3)
+        return qv_set_error(QV_ERR_INVALID, "qv_plan_set_episode_word: word not 4-byte aligned");
+    pl->dev.episode_word = d_word;
+    if (pl->graph) {  // the captured launch holds the old parameters
+        cudaGraphExecDestroy(pl->graph);
+        pl->graph = nullptr;
+    }
+    return QV_OK;
+}
+
 extern "C" qv_status qv_plan_run(qv_plan_t *pl, qv_stream_t stream) {
+    if (const qv_status inj = qv_injected_fault("qv_plan_run", false)) return inj;
     if (!pl) return qv_set_error(QV_ERR_INVALID, "qv_plan_run: null plan");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     pl->records_fresh = false;

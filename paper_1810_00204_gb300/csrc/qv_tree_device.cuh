@@ -54,8 +54,9 @@ constexpr int kTot = 36;
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
     size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, u_n, u_off, u_z, u_sa, u_se,
-        scan, flags, acc, c_pa, c_z, c_sa, c_se, total;
-    __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K, int cmax) {
+        scan, flags, acc, c_pa, c_z, c_sa, c_se, wpart, wchild, total;
+    __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K, int cmax,
+                                               int kslots) {
         SmemLayout s;
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -96,6 +97,8 @@ struct SmemLayout {
         s.c_z = take(sizeof(int) * cmax);
         s.c_sa = take(sizeof(float) * cmax);
         s.c_se = take(sizeof(float) * cmax);
+        s.wpart = take(sizeof(float) * kTot * kWarps * kslots);  // per-warp sums of a band
+        s.wchild = take(sizeof(int) * kWarps * kslots);          // the child of each slot, -1 unused
         s.total = (o + 127) & ~size_t(127);
         return s;
     }
@@ -114,7 +117,13 @@ struct Smem {
     float *acc;
     int *c_pa, *c_z;
     float *c_sa, *c_se;
+    float *wpart;
+    int *wchild;
 };
+
+// Slots per warp for the per-child sums of one band: a warp's contiguous
+// range of (child, strip, row) tasks spans at most cmax / kWarps + 3 children.
+__host__ __device__ __forceinline__ int expand_slots(int cmax) { return cmax / kWarps + 3; }
 
 // ---------------------------------------------------------------- helpers
 __device__ __forceinline__ int find_episode(const int *wb, int E, int w) {
@@ -396,10 +405,11 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
         pl.R[iid * 5 + a] = S.tot[5 + a] - 100.0f * bgoal;
     }
     __syncthreads();
+    const uint32_t epw = pl.episode_word ? __ldcg(pl.episode_word) + (ep.episode - pl.episode0) : ep.episode;
     for (int t = threadIdx.x; t < 5 * K; t += blockDim.x) {
         const int a = t / K, k = t - a * K;
         const float *C = S.C + a * nz;
-        const float u = sample_uniform(pl.seed, ep.episode, l, code * 5ull + a, k);
+        const float u = sample_uniform(pl.seed, epw, l, code * 5ull + a, k);
         int z;
         if (pl.replay) {
             z = __ldg(pl.replay + (static_cast<long long>(iid) * 5 + a) * K + k);
@@ -672,49 +682,61 @@ __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem
     __syncthreads();
 }
 
-// Node band from the parent band: rows [r0-1, r1+1) of Phi(parent, a, z)
-// into `sb` (zero outside the grid), rows [r0, r1) also to `dst` if given.
-// `sp` holds parent rows [r0-2, r1+2), `cw` the cell words of [r0-1, r1+1).
-__device__ __forceinline__ void build_band(const EpReg &ep, const float *sp, const uint16_t *cw, float *sb, int r0,
-                                           int r1, int a, int z, float sa, float se, const float *lut, float *dst) {
-    const int P = ep.P, P4 = P >> 2;
-    const int rows = r1 - r0 + 2;
-    for (int gi = threadIdx.x; gi < rows * P4; gi += blockDim.x) {
-        const int ri = gi / P4, col = (gi - ri * P4) << 2;
-        const int r = r0 - 1 + ri;
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (r >= 0 && r < ep.H) {
-            const int y = r * P + col;
-            Nbr4 n;
-            load_nbr(ep, sp + (ri + 1) * P, cw + ri * P, col, n);
-            float v[4];
+// ---------------------------------------------------------------- expand phase
+// A node's belief at four cells (band-relative row y in [-1, R], columns
+// col..col+3) from its parent's staged band: Phi(parent, a, z) of Eq. 3,
+// zero outside the grid.  `sp` holds the parent's rows [r0-2, r1+2), `cw`
+// the cell words of [r0-1, r1+1).
+__device__ __forceinline__ float4 child4(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int col,
+                                         int a, int z, float sa, float se, const float *lut) {
+    const int P = ep.P, r = r0 + y;
+    if (r < 0 || r >= ep.H || col >= P) return make_float4(0.f, 0.f, 0.f, 0.f);
+    Nbr4 n;
+    load_nbr(ep, sp + (y + 2) * P, cw + (y + 1) * P, col, n);
+    float v[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float nb[4];
-                inflow_nb(n, j, nb);
-                const float pa = predict_one(nb, n.m[j + 1], n.cw[j], (y + j) == ep.goal, ep.slip, lut, a);
-                v[j] = pa * (static_cast<int>(QV_CELL_LABEL(n.cw[j])) == z ? sa : se);
-            }
-            o = make_float4(v[0], v[1], v[2], v[3]);
-            if (dst && ri >= 1 && ri <= r1 - r0) *reinterpret_cast<float4 *>(dst + y) = o;
-        }
-        *reinterpret_cast<float4 *>(sb + ri * P + col) = o;
+    for (int j = 0; j < 4; ++j) {
+        float nb[4];
+        inflow_nb(n, j, nb);
+        const float p = predict_one(nb, n.m[j + 1], n.cw[j], r * P + col + j == ep.goal, ep.slip, lut, a);
+        v[j] = p * (static_cast<int>(QV_CELL_LABEL(n.cw[j])) == z ? sa : se);
     }
-    __syncthreads();
+    return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// ---------------------------------------------------------------- expand phase
+// The same at one cell (band-relative row y, column c), for the edge of a
+// column strip.
+__device__ __forceinline__ float child1(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int c,
+                                        int a, int z, float sa, float se, const float *lut) {
+    const int P = ep.P, r = r0 + y;
+    if (r < 0 || r >= ep.H || c < 0 || c >= P) return 0.0f;
+    const float *m = sp + (y + 2) * P + c;
+    const unsigned w = cw[(y + 1) * P + c];
+    const unsigned in = QV_CELL_INFLOW(w);
+    float nb[4];
+    nb[kDirN] = (in & 1u) ? m[-P] : 0.0f;
+    nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
+    nb[kDirS] = (in & 4u) ? m[P] : 0.0f;
+    nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
+    const float p = predict_one(nb, m[0], w, r * P + c == ep.goal, ep.slip, lut, a);
+    return p * (static_cast<int>(QV_CELL_LABEL(w)) == z ? sa : se);
+}
+
 // Work items are (group, band range).  A group is one V-node of level l - 1
 // with all its children at level l (at l = 0, the root of one episode), so
 // the parent's band, the cell words and (fused level) Q are staged once per
-// band for every child.  Per band and child: the child's band Phi(parent, a,
-// z) (Eq. 3; written out when a later phase reads it), then on that band the
-// motion stencil for all five actions (Eq. 3 numerator, Eq. 10) and the sums
-// of the null-label cells and of the rewards (Sec. III), and at the fused
-// level the Q-weighted null sums.  The per-cell sums stay in registers; a
-// warp reduce-scatter per (child, band) and a fixed-order sum over the warps
-// add them into the child's totals in shared memory.  Cells with a beacon's
-// label enter through phase_finalize's tiles.
+// band for every child.  Within a band the (child, column strip of 128
+// cells, row) tasks are split into eight contiguous ranges, one per warp, so
+// that each warp streams rows on its own: per row, each lane forms the
+// child's belief at its four cells (Phi(parent, a, z), Eq. 3; written out
+// when a later phase reads it) rolling three rows in registers, takes the
+// row's east/west neighbours from the adjacent lanes, and applies the motion
+// stencil for all five actions (Eq. 3 numerator, Eq. 10), summing the
+// null-label masses, the rewards (Sec. III) and, at the fused level, the
+// Q-weighted null masses in registers.  A warp's sums go to a per-warp slot
+// when its task range moves to another child; at the end of the band the
+// slots are added into each child's totals in warp order.  Cells with a
+// beacon's label enter through phase_finalize's tiles.
 template <bool FUSED>
 __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
                              int &cur_e) {
@@ -724,9 +746,14 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
     const int *grec = pl.grp_rec + pl.gbase[l];
     const int total = __ldcg(goff + G);
     const int *np = l > 0 ? pl.npre + (l - 1) * (E + 1) : nullptr;
+    const int KS = pl.kslots;
     constexpr int NV = FUSED ? 35 : 10;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
+#ifdef QV_TRACE
+        unsigned long long tr[kTraceWords] = {};
+#endif
+        QV_TRACE_MARK(tr, 2);
         const int j = find_episode(goff, G, w);
         int e = j, lp = 0;
         if (l > 0) {
@@ -775,101 +802,171 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         }
         for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) S.acc[i] = 0.0f;
         __syncthreads();
+        QV_TRACE_MARK(tr, 3);
         const int band0 = static_cast<int>((static_cast<long long>(item) * ep.bands) / items);
         const int band1 = static_cast<int>((static_cast<long long>(item + 1) * ep.bands) / items);
         const int band_rows = ep.band_rows;
         const EpReg er = ep_reg(ep);
         const int P = er.P, P4 = P >> 2, goal = er.goal;
+        const int NS = (P4 + 31) >> 5;  // column strips of 32 float4 groups
         const float slip = er.slip;
         const float *cost = er.cost;
         float *dst0 = (l > 0 && store) ? pl.beliefs + ep.belief_off[l] : nullptr;
         for (int band = band0; band < band1; ++band) {
-            const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows);
-            const int qstride = (r1 - r0) * P;
-            if (!stage_band(er, src, r0, r1, l == 0 ? 1 : 2, l == 0 ? S.sb : S.sp, S.cw, FUSED ? S.q : nullptr, mbar,
-                            mphase, pl.status))
+            const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows), R = r1 - r0;
+            const int qstride = R * P;
+            if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
                 return false;
-            for (int r = 0; r < nc; ++r) {
-                if (l > 0)
-                    build_band(er, S.sp, S.cw, S.sb, r0, r1, S.c_pa[r], S.c_z[r], S.c_sa[r], S.c_se[r], S.lut,
-                               dst0 ? dst0 + static_cast<long long>(c0 + r) * er.N : nullptr);
-                float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
+            if (band == band0) QV_TRACE_MARK(tr, 4);
+            // this warp's contiguous range of (child, strip, row) tasks
+            const int T = nc * NS * R;
+            int t = static_cast<int>(static_cast<long long>(T) * wid / kWarps);
+            const int tend = static_cast<int>(static_cast<long long>(T) * (wid + 1) / kWarps);
+            int slot = 0, cur = -1;
+            float acc_null[5], acc_r[5], acc_q[FUSED ? 25 : 1];
+            auto zero_acc = [&]() {
 #pragma unroll
                 for (int a = 0; a < 5; ++a) acc_null[a] = acc_r[a] = 0.0f;
 #pragma unroll
                 for (int i = 0; i < (FUSED ? 25 : 1); ++i) acc_q[i] = 0.0f;
-                const int ng = (r1 - r0) * P4;
-                for (int gi = threadIdx.x; gi < ng; gi += blockDim.x) {
-                    const int rr = gi / P4, col = (gi - rr * P4) << 2;
-                    const int y = (r0 + rr) * P + col;
-                    Nbr4 n;
-                    load_nbr(er, S.sb + (rr + 1) * P, S.cw + (rr + 1) * P, col, n);
-                    float4 q4[5];
-                    if constexpr (FUSED) {
+            };
+            // the warp's sums of child `cur` into its next slot: values 0..31
+            // by a reduce-scatter (lane i gets value i), 32..34 by warp sums
+            auto flush = [&]() {
+                float v[32];
 #pragma unroll
-                        for (int ap = 0; ap < 5; ++ap)
-                            q4[ap] = *reinterpret_cast<const float4 *>(S.q + ap * qstride + rr * P + col);
+                for (int a = 0; a < 5; ++a) {
+                    v[a] = acc_null[a];
+                    v[5 + a] = acc_r[a];
+                }
+#pragma unroll
+                for (int i = 0; i < 22; ++i) {
+                    if constexpr (FUSED) v[10 + i] = acc_q[i];
+                    else v[10 + i] = 0.0f;
+                }
+                warp_reduce_scatter32(v);
+                if (slot >= KS) {  // cannot happen (expand_slots); reported, never written past
+                    if (lane == 0) atomicOr(pl.status, kErrCapacity);
+                    return;
+                }
+                float *dstp = S.wpart + (wid * KS + slot) * kTot;
+                dstp[lane] = v[0];
+                if constexpr (FUSED) {
+#pragma unroll
+                    for (int i = 22; i < 25; ++i) {
+                        const float tt = warp_sum(acc_q[i]);
+                        if (lane == 0) dstp[10 + i] = tt;
                     }
-                    float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (cost) c4 = __ldg(reinterpret_cast<const float4 *>(cost + y));
-                    const float cst[4] = {c4.x, c4.y, c4.z, c4.w};
+                }
+                if (lane == 0) S.wchild[wid * KS + slot] = cur;
+                ++slot;
+            };
+            zero_acc();
+            while (t < tend) {
+                const int r = t / (NS * R);
+                const int rem = t - r * NS * R;
+                const int s = rem / R, ya = rem - s * R;
+                const int yb = min(R, ya + (tend - t));
+                if (r != cur) {
+                    if (cur >= 0) flush();
+                    zero_acc();
+                    cur = r;
+                }
+                int pa = 0, pz = 0;
+                float sa = 1.0f, se = 1.0f;
+                if (l > 0) {
+                    pa = S.c_pa[r];
+                    pz = S.c_z[r];
+                    sa = S.c_sa[r];
+                    se = S.c_se[r];
+                }
+                const int gcol = s * 32 + lane;
+                const bool act = gcol < P4;
+                const int col = gcol << 2;
+                float *dst = dst0 ? dst0 + static_cast<long long>(c0 + r) * er.N : nullptr;
+                auto row4 = [&](int y) -> float4 {
+                    if (!act) return make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (l == 0) {
+                        const int rr = r0 + y;
+                        return (rr >= 0 && rr < er.H) ? *reinterpret_cast<const float4 *>(S.sp + (y + 2) * P + col)
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    return child4(er, S.sp, S.cw, r0, y, col, pa, pz, sa, se, S.lut);
+                };
+                auto row1 = [&](int y, int c) -> float {
+                    if (l == 0) {
+                        const int rr = r0 + y;
+                        return (rr >= 0 && rr < er.H && c >= 0 && c < P) ? S.sp[(y + 2) * P + c] : 0.0f;
+                    }
+                    return child1(er, S.sp, S.cw, r0, y, c, pa, pz, sa, se, S.lut);
+                };
+                float4 up = row4(ya - 1), md = row4(ya);
+                for (int y = ya; y < yb; ++y) {
+                    const float4 dn = row4(y + 1);
+                    // the row's west and east neighbours from the adjacent lanes;
+                    // the strip's edges are formed directly
+                    float hw = __shfl_up_sync(0xffffffffu, md.w, 1);
+                    float he = __shfl_down_sync(0xffffffffu, md.x, 1);
+                    if (lane == 0) hw = (act && col > 0) ? row1(y, col - 1) : 0.0f;
+                    if (lane == 31) he = (act && col + 4 < P) ? row1(y, col + 4) : 0.0f;
+                    if (act) {
+                        const int yg = (r0 + y) * P + col;
+                        if (dst) *reinterpret_cast<float4 *>(dst + yg) = md;
+                        const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(S.cw + (y + 1) * P + col);
+                        const unsigned cws[4] = {cw4.x, cw4.y, cw4.z, cw4.w};
+                        const float ups[4] = {up.x, up.y, up.z, up.w};
+                        const float mds[6] = {hw, md.x, md.y, md.z, md.w, he};
+                        const float dns[4] = {dn.x, dn.y, dn.z, dn.w};
+                        const float *qrow = S.q + y * P + col;
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        const unsigned cw = n.cw[jj];
-                        float nb[4], out[5];
-                        inflow_nb(n, jj, nb);
-                        predict_cell(nb, n.m[jj + 1], cw, (y + jj) == goal, slip, S.lut, out);
-                        const float rw = stage_reward(QV_CELL_FREE(cw), (y + jj) == goal, cst[jj]);
-                        const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
-#pragma unroll
-                        for (int a = 0; a < 5; ++a) {
-                            const float v = out[a];
-                            acc_r[a] = fmaf(v, rw, acc_r[a]);
-                            const float vn = v * isnull;
-                            acc_null[a] += vn;
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const unsigned cw = cws[jj];
+                            const unsigned in = QV_CELL_INFLOW(cw);
+                            float nb[4], out[5];
+                            nb[kDirN] = (in & 1u) ? ups[jj] : 0.0f;
+                            nb[kDirE] = (in & 2u) ? mds[jj + 2] : 0.0f;
+                            nb[kDirS] = (in & 4u) ? dns[jj] : 0.0f;
+                            nb[kDirW] = (in & 8u) ? mds[jj] : 0.0f;
+                            predict_cell(nb, mds[jj + 1], cw, (yg + jj) == goal, slip, S.lut, out);
+                            const float cst = cost ? __ldg(cost + yg + jj) : 0.0f;
+                            const float rw = stage_reward(QV_CELL_FREE(cw), (yg + jj) == goal, cst);
+                            const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
+                            float qj[5];
                             if constexpr (FUSED) {
-                                const float qj[5] = {(&q4[0].x)[jj], (&q4[1].x)[jj], (&q4[2].x)[jj], (&q4[3].x)[jj],
-                                                     (&q4[4].x)[jj]};
 #pragma unroll
-                                for (int ap = 0; ap < 5; ++ap)
-                                    acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                                for (int ap = 0; ap < 5; ++ap) qj[ap] = qrow[ap * qstride + jj];
+                            }
+#pragma unroll
+                            for (int a = 0; a < 5; ++a) {
+                                const float v = out[a];
+                                acc_r[a] = fmaf(v, rw, acc_r[a]);
+                                const float vn = v * isnull;
+                                acc_null[a] += vn;
+                                if constexpr (FUSED) {
+#pragma unroll
+                                    for (int ap = 0; ap < 5; ++ap)
+                                        acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                                }
                             }
                         }
                     }
+                    up = md;
+                    md = dn;
                 }
-                // this (child, band)'s per-thread sums into the warp's slot:
-                // values 0..31 by a reduce-scatter (lane i gets value i),
-                // 32..34 by plain warp sums
-                {
-                    float v[32];
-#pragma unroll
-                    for (int a = 0; a < 5; ++a) {
-                        v[a] = acc_null[a];
-                        v[5 + a] = acc_r[a];
-                    }
-#pragma unroll
-                    for (int i = 0; i < 22; ++i) {
-                        if constexpr (FUSED) v[10 + i] = acc_q[i];
-                        else v[10 + i] = 0.0f;
-                    }
-                    warp_reduce_scatter32(v);
-                    S.red[wid * kTot + lane] = v[0];
-                    if constexpr (FUSED) {
-#pragma unroll
-                        for (int i = 22; i < 25; ++i) {
-                            const float t = warp_sum(acc_q[i]);
-                            if (lane == 0) S.red[wid * kTot + 10 + i] = t;
-                        }
-                    }
-                }
-                __syncthreads();
-                // the warps' slots in warp order into the child's totals (the
-                // next child's build touches neither S.red nor S.acc)
-                if (threadIdx.x < NV) {
-                    float t = 0.0f;
-                    for (int k = 0; k < kWarps; ++k) t += S.red[k * kTot + threadIdx.x];
-                    S.acc[r * kTot + threadIdx.x] += t;
-                }
+                t += yb - ya;
+            }
+            if (cur >= 0) flush();
+            for (int sl = slot + lane; sl < KS; sl += 32) S.wchild[wid * KS + sl] = -1;
+            __syncthreads();
+            if (band == band0) QV_TRACE_MARK(tr, 5);
+            // the warps' slots into each child's totals, in (warp, slot) order
+            for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
+                const int r = i / kTot, v = i - r * kTot;
+                if (v >= NV) continue;
+                float sum = 0.0f;
+                for (int sl = 0; sl < kWarps * KS; ++sl)
+                    if (S.wchild[sl] == r) sum += S.wpart[sl * kTot + v];
+                S.acc[i] += sum;
             }
         }
         __syncthreads();
@@ -885,6 +982,13 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                 if (x < pl.n_xrec) pl.xrec[x * kTot + k] = v;
             }
         }
+        QV_TRACE_MARK(tr, 6);
+#ifdef QV_TRACE
+        tr[0] = 2ull | (static_cast<unsigned long long>(l) << 8) | (static_cast<unsigned long long>(blockIdx.x) << 16) |
+                (static_cast<unsigned long long>(nc) << 32) | (static_cast<unsigned long long>(band1 - band0) << 48);
+        tr[1] = static_cast<unsigned long long>(w);
+        trace_commit(tr, 7);
+#endif
     }
     return true;
 }
@@ -907,33 +1011,69 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
     const int rlo = max(0, br - R), rhi = min(H - 1, br + R);
     const int clo = max(0, bc - R), chi = min(W - 1, bc + R);
     constexpr int PW = kTileW + 4, CW = kTileW + 2;
+    constexpr int NP = (kTileP + 31) / 32, NC = (kTileC + 31) / 32, ND = (kTileH * kTileW + 31) / 32;
     for (int y0 = rlo; y0 <= rhi; y0 += kTileH) {
         for (int x0 = clo; x0 <= chi; x0 += kTileW) {
             __syncwarp();
-            if (!root) {
-                for (int i = lane; i < kTileP; i += 32) {
-                    const int rr = i / PW, cc = i - rr * PW;
-                    const int r = y0 - 2 + rr, c = x0 - 2 + cc;
-                    tp[i] = (r >= 0 && r < H && c >= 0 && c < P) ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
+            // the tile's global loads issued a batch at a time, before any is used
+            if (root) {
+                // b0 on the tile and its rim, with the cell words
+                uint16_t cv[NC];
+                float bv[NC];
+#pragma unroll
+                for (int u = 0; u < NC; ++u) {
+                    const int i = lane + 32 * u, rr = i / CW, cc = i - rr * CW;
+                    const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                    const bool in = i < kTileC && r >= 0 && r < H && c >= 0 && c < P;
+                    cv[u] = in ? __ldg(ep.cell + static_cast<size_t>(r) * P + c) : static_cast<uint16_t>(0);
+                    bv[u] = in ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
                 }
-            }
-            for (int i = lane; i < kTileC; i += 32) {
-                const int rr = i / CW, cc = i - rr * CW;
-                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                tcw[i] = (r >= 0 && r < H && c >= 0 && c < P) ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
-                                                              : static_cast<uint16_t>(0);
-            }
-            __syncwarp();
-            // the node's belief on the tile and its rim
-            for (int i = lane; i < kTileC; i += 32) {
-                const int rr = i / CW, cc = i - rr * CW;
-                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                float v = 0.0f;
-                if (r >= 0 && r < H && c >= 0 && c < P) {
-                    const unsigned cw = tcw[i];
-                    if (root) {
-                        v = QV_CELL_FREE(cw) ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
-                    } else {
+#pragma unroll
+                for (int u = 0; u < NC; ++u) {
+                    const int i = lane + 32 * u;
+                    if (i < kTileC) {
+                        tcw[i] = cv[u];
+                        tc[i] = QV_CELL_FREE(static_cast<unsigned>(cv[u])) ? bv[u] : 0.0f;
+                    }
+                }
+                __syncwarp();
+            } else {
+                {
+                    float pv[NP];
+#pragma unroll
+                    for (int u = 0; u < NP; ++u) {
+                        const int i = lane + 32 * u, rr = i / PW, cc = i - rr * PW;
+                        const int r = y0 - 2 + rr, c = x0 - 2 + cc;
+                        pv[u] = (i < kTileP && r >= 0 && r < H && c >= 0 && c < P)
+                                    ? __ldcg(par + static_cast<size_t>(r) * P + c)
+                                    : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < NP; ++u)
+                        if (lane + 32 * u < kTileP) tp[lane + 32 * u] = pv[u];
+                }
+                {
+                    uint16_t cv[NC];
+#pragma unroll
+                    for (int u = 0; u < NC; ++u) {
+                        const int i = lane + 32 * u, rr = i / CW, cc = i - rr * CW;
+                        const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                        cv[u] = (i < kTileC && r >= 0 && r < H && c >= 0 && c < P)
+                                    ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
+                                    : static_cast<uint16_t>(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < NC; ++u)
+                        if (lane + 32 * u < kTileC) tcw[lane + 32 * u] = cv[u];
+                }
+                __syncwarp();
+                // the node's belief on the tile and its rim
+                for (int i = lane; i < kTileC; i += 32) {
+                    const int rr = i / CW, cc = i - rr * CW;
+                    const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                    float v = 0.0f;
+                    if (r >= 0 && r < H && c >= 0 && c < P) {
+                        const unsigned cw = tcw[i];
                         const float *m = tp + (rr + 1) * PW + (cc + 1);
                         const unsigned in = QV_CELL_INFLOW(cw);
                         float nb[4];
@@ -944,17 +1084,37 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
                         const float p = predict_one(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, pa);
                         v = p * (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
                     }
+                    tc[i] = v;
                 }
-                tc[i] = v;
+                __syncwarp();
+            }
+            // the diamond's cells of label k inside the tile, listed in the
+            // warp's free parent buffer; then per listed cell its Q values
+            // (fused) and the predicted masses
+            int *list = reinterpret_cast<int *>(tp);
+            int nh = 0;
+#pragma unroll
+            for (int u = 0; u < ND; ++u) {
+                const int i = lane + 32 * u, rr = i / kTileW, cc = i - rr * kTileW;
+                const int r = y0 + rr, c = x0 + cc;
+                const bool hit = i < kTileH * kTileW && r <= rhi && c <= chi && abs(r - br) + abs(c - bc) <= R &&
+                                 static_cast<int>(QV_CELL_LABEL(tcw[(rr + 1) * CW + cc + 1])) == k;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) list[nh + __popc(bal & ((1u << lane) - 1u))] = i;
+                nh += __popc(bal);
             }
             __syncwarp();
-            // the diamond's cells of label k inside the tile
-            for (int i = lane; i < kTileH * kTileW; i += 32) {
-                const int rr = i / kTileW, cc = i - rr * kTileW;
+            for (int h = lane; h < nh; h += 32) {
+                const int cell = list[h];
+                const int rr = cell / kTileW, cc = cell - rr * kTileW;
                 const int r = y0 + rr, c = x0 + cc;
-                if (r > rhi || c > chi || abs(r - br) + abs(c - bc) > R) continue;
+                float qv[FUSED ? 5 : 1];
+                if constexpr (FUSED) {
+#pragma unroll
+                    for (int ap = 0; ap < 5; ++ap)
+                        qv[ap] = __ldg(ep.Q + static_cast<size_t>(ap) * ep.N + static_cast<size_t>(r) * P + c);
+                }
                 const unsigned cw = tcw[(rr + 1) * CW + cc + 1];
-                if (static_cast<int>(QV_CELL_LABEL(cw)) != k) continue;
                 const float *m = tc + (rr + 1) * CW + (cc + 1);
                 const unsigned in = QV_CELL_INFLOW(cw);
                 float nb[4], out[5];
@@ -966,9 +1126,6 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
 #pragma unroll
                 for (int a = 0; a < 5; ++a) la[a] += out[a];
                 if constexpr (FUSED) {
-                    float qv[5];
-#pragma unroll
-                    for (int ap = 0; ap < 5; ++ap) qv[ap] = __ldg(ep.Q + static_cast<size_t>(ap) * ep.N + r * P + c);
 #pragma unroll
                     for (int a = 0; a < 5; ++a)
 #pragma unroll
@@ -1002,6 +1159,10 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
     float *tc = tp + kTileP;
     uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
+#ifdef QV_TRACE
+        unsigned long long tr[kTraceWords] = {};
+#endif
+        QV_TRACE_MARK(tr, 2);
         const int e = find_episode(wb, E, w);
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
@@ -1050,6 +1211,7 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             else if (FUSED && lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] = v[0];
         }
         __syncthreads();
+        QV_TRACE_MARK(tr, 3);
         if (C > 1) {
             // a record of this chunk's beacons; the last chunk of the node gathers
             float *recp = pl.frec + static_cast<long long>(w) * stride;
@@ -1068,17 +1230,39 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 S.flags[0] = last;
             }
             __syncthreads();
-            if (!S.flags[0]) continue;
-            for (int i = threadIdx.x; i < B * 30; i += blockDim.x) {
-                const int k = i / 30, t = i - k * 30, c = k / bpc;
-                if (c == chunk) continue;
-                const long long wi = static_cast<long long>(w - chunk + c);
-                if ((wi + 1) * stride > pl.n_frec) continue;
-                const float v = __ldcg(pl.frec + wi * stride + (k - c * bpc) * 30 + t);
-                if (t < 5) S.hist[t * Bm + k] = v;
-                else if (FUSED) S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5] = v;
+            QV_TRACE_MARK(tr, 4);
+            if (!S.flags[0]) {
+#ifdef QV_TRACE
+                tr[0] = 1ull | (static_cast<unsigned long long>(l) << 8) |
+                        (static_cast<unsigned long long>(blockIdx.x) << 16);
+                tr[1] = static_cast<unsigned long long>(w);
+                trace_commit(tr, 5);
+#endif
+                continue;
+            }
+            for (int i0 = threadIdx.x; i0 < B * 30; i0 += 4 * blockDim.x) {
+                // four loads in flight per thread
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    const int k = i / 30, t = i - k * 30, c = k / bpc;
+                    const long long wi = static_cast<long long>(w - chunk + c);
+                    v[u] = (i < B * 30 && c != chunk && (wi + 1) * stride <= pl.n_frec)
+                               ? __ldcg(pl.frec + wi * stride + (k - c * bpc) * 30 + t)
+                               : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    const int k = i / 30, t = i - k * 30, c = k / bpc;
+                    if (i >= B * 30 || c == chunk) continue;
+                    if (t < 5) S.hist[t * Bm + k] = v[u];
+                    else if (FUSED) S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5] = v[u];
+                }
             }
         }
+        QV_TRACE_MARK(tr, 5);
         // the node's totals: final, or the records of its group's items in order
         {
             int jg = e, r = 0;
@@ -1097,10 +1281,18 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 const int nit = __ldcg(goff + jg + 1) - __ldcg(goff + jg);
                 const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
                 if (g < kGroups) {
+                    // items g, g + 7, ... in order, eight loads in flight at a time
                     float sum = 0.0f;
-                    for (int it = g; it < nit; it += kGroups) {
-                        const long long x = static_cast<long long>(rec + it) * pl.cmax + r;
-                        if (x < pl.n_xrec) sum += __ldcg(pl.xrec + x * kTot + t);
+                    for (int it0 = g; it0 < nit; it0 += 8 * kGroups) {
+                        float v[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int it = it0 + u * kGroups;
+                            const long long x = static_cast<long long>(rec + it) * pl.cmax + r;
+                            v[u] = (it < nit && x < pl.n_xrec) ? __ldcg(pl.xrec + x * kTot + t) : 0.0f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) sum += v[u];
                     }
                     S.red[g * kTot + t] = sum;
                 }
@@ -1132,9 +1324,18 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             }
             __syncthreads();
         }
+        QV_TRACE_MARK(tr, 6);
         const unsigned long long code = __ldcg(pl.code + gid);
         finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
+        QV_TRACE_MARK(tr, 7);
         if constexpr (NUMBER) node_done(pl, l, e, ep, S);
+        QV_TRACE_MARK(tr, 8);
+#ifdef QV_TRACE
+        tr[0] = 1ull | (static_cast<unsigned long long>(l) << 8) | (static_cast<unsigned long long>(blockIdx.x) << 16) |
+                (1ull << 56);
+        tr[1] = static_cast<unsigned long long>(w);
+        trace_commit(tr, 9);
+#endif
     }
     return true;
 }
@@ -1469,7 +1670,8 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e, int D) {
 __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
-    const SmemLayout L = SmemLayout::make(pl.sb_floats, pl.sp_floats, pl.q_floats, pl.Bmax, pl.K, pl.cmax);
+    const SmemLayout L =
+        SmemLayout::make(pl.sb_floats, pl.sp_floats, pl.q_floats, pl.Bmax, pl.K, pl.cmax, pl.kslots);
     Smem S;
     S.sb = reinterpret_cast<float *>(smem_raw + L.sb);
     S.tile = reinterpret_cast<float *>(smem_raw + L.tile);
@@ -1478,6 +1680,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     S.c_z = reinterpret_cast<int *>(smem_raw + L.c_z);
     S.c_sa = reinterpret_cast<float *>(smem_raw + L.c_sa);
     S.c_se = reinterpret_cast<float *>(smem_raw + L.c_se);
+    S.wpart = reinterpret_cast<float *>(smem_raw + L.wpart);
+    S.wchild = reinterpret_cast<int *>(smem_raw + L.wchild);
     S.sp = reinterpret_cast<float *>(smem_raw + L.sp);
     S.cw = reinterpret_cast<uint16_t *>(smem_raw + L.cw);
     S.q = reinterpret_cast<float *>(smem_raw + L.q);

@@ -158,3 +158,25 @@ def test_noalloc_binding_checks_tensors_before_the_library():
         api._check_tensor(torch.zeros(1, dtype=torch.float64), None, "cpu", "f", "pz")
     with pytest.raises(ValueError):
         api._check_tensor(torch.zeros(8, 4).t(), (4, 8), "cpu", "f", "bbar")  # not contiguous
+
+
+def test_injected_faults_are_reported_before_any_device_work(libpath, monkeypatch):
+    """QVTS_FAULT=oom|invalid: the instrumented calls return the injected
+    status and a message naming it before they read any argument or touch a
+    device (here there is none), so the fake pointers below are never used."""
+    from paper_1810_00204_gb300 import _native as N
+    L = N.lib()
+    fake = ctypes.c_void_p(0x1000)
+    m = N.qv_model_t(4, 5, 8, 16, 1, 0, 0.1, 0.9, 0.95, None, 32, 3)
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
+    h = ctypes.c_void_p()
+    qp = (ctypes.c_void_p * 1)(0x1000)
+    monkeypatch.setenv("QVTS_FAULT", "oom")
+    st = L.qv_plan_create(1, ctypes.byref(m), qp, qp, ctypes.byref(p), fake, 1 << 20, ctypes.byref(h), None)
+    assert st == N.QV_ERR_WORKSPACE and b"QVTS_FAULT=oom" in L.qv_last_error()
+    monkeypatch.setenv("QVTS_FAULT", "invalid")
+    st = L.qv_plan_create(1, ctypes.byref(m), qp, qp, ctypes.byref(p), fake, 1 << 20, ctypes.byref(h), None)
+    assert st == N.QV_ERR_INVALID and b"QVTS_FAULT=invalid" in L.qv_last_error()
+    assert L.belief_predict(ctypes.byref(m), fake, 0, fake, None) == N.QV_ERR_INVALID
+    assert b"QVTS_FAULT=invalid" in L.qv_last_error()
+    assert not h.value

@@ -81,3 +81,33 @@ def test_value_iteration_adjoint_timeout_is_reported(api, monkeypatch):
                                   cost=w.cost.astype(np.float64).ravel()), 40,
                         m.from_grid(Qbar).reshape(5, -1))
     assert float(dslip[0]) == pytest.approx(ref["dslip"], rel=1e-9)
+
+
+@pytest.mark.parametrize("mode,status", [("oom", "QV_ERR_WORKSPACE"), ("invalid", "QV_ERR_INVALID")])
+def test_injected_host_faults_and_recovery(api, monkeypatch, mode, status):
+    """QVTS_FAULT=oom|invalid: the value iteration, the plan's creation and
+    the Bayes correction report the injected status with a message naming
+    it, and the same calls succeed once the variable is unset."""
+    from paper_1810_00204_gb300 import _native as N
+    code = getattr(N, status)
+    w = WL.tiny(2)
+    m = api.Model(w)
+    Q = api.mdp_value_iterate(m, dtype="f64", tol=w.vi_tol)["Q"]
+    b = m.b0()
+    monkeypatch.setenv("QVTS_FAULT", mode)
+    for call in (lambda: api.mdp_value_iterate(m, dtype="f32"),
+                 lambda: api.Plan([m], [Q], [b], depth=w.depth, K=w.K, seed=w.seed),
+                 lambda: api.belief_correct(m, b, 0)):
+        with pytest.raises(N.QVError) as ei:
+            call()
+        assert ei.value.status == code
+        assert f"QVTS_FAULT={mode}".encode() in N.lib().qv_last_error()
+    monkeypatch.delenv("QVTS_FAULT")
+    assert api.mdp_value_iterate(m, dtype="f32")["status"] == N.QV_OK
+    p = api.Plan([m], [Q], [b], depth=w.depth, K=w.K, seed=w.seed)
+    p.run()
+    r = p.read()[0]
+    o = O.tree_plan(w, m.from_grid(Q).reshape(5, -1).astype(np.float64))
+    assert abs(r["value"] - o["root_value"]) <= 1e-5 * max(1.0, abs(o["root_value"]))
+    out, pz = api.belief_correct(m, b, 0)
+    assert torch.isfinite(out).all()
