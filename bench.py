@@ -4,9 +4,11 @@
 Default workload: the 512x512 plain configuration (rooms of 32 cells with
 1-cell walls and 3-wide doors plus random walls to 25 %, 64 beacons with
 range 8 and accuracy 0.8, slip 0.1, discount 0.97, Gaussian b0 with sigma 4,
-depth 3, K = 4, FP32 beliefs and Q), one plan per launch.  A step is R
-planning requests (different start cells on the same map), each a complete
-plan from b0 to the chosen action.  The offline value iteration is run once
+depth 3, K = 4, FP32 beliefs and Q).  A step is R planning requests
+(different start cells on the same map), each a complete plan from b0 to the
+chosen action, run either as one plan per launch on concurrent streams or as
+one batched launch of all R plans (the faster of the two in a short trial,
+unless --execution says which).  The offline value iteration is run once
 per map and reported separately.  The 128x128 configuration, the batched
 forms and the other parts of the method are timed as sub-measurements.
 
@@ -55,6 +57,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["mid", "large", "tiny"], default="large")
     ap.add_argument("--plans-per-step", type=int, default=32)
+    ap.add_argument("--execution", choices=["auto", "plain", "batched"], default="auto",
+                    help="how a step's requests run: one plan per launch on streams (plain), all in one launch "
+                         "(batched), or the faster of the two in a short trial (auto)")
     ap.add_argument("--leaf-mode", choices=["fused", "materialise"], default="fused")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=10)
@@ -111,16 +116,47 @@ def time_offline(solve):
     return r, first, statistics.median(runs)
 
 
+_L2_GBPS = None
+
+
+def l2_bandwidth():
+    """Copy bandwidth of a buffer that stays in L2 (2 x 24 MiB, read + write
+    bytes, best of 20 back-to-back copies timed with CUDA events), measured
+    once per process: the roof of the offline solves, whose state fits L2."""
+    global _L2_GBPS
+    if _L2_GBPS is None:
+        import torch
+        a = torch.ones(24 << 20, dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        for _ in range(5):
+            b.copy_(a)
+        best = None
+        for _ in range(20):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.copy_(a)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        _L2_GBPS = 2 * a.numel() / (best * 1e-3) / 1e9
+    return _L2_GBPS
+
+
 def offline_line(r, first_ms, ms, model, bytes_per_cell, peak):
     """Sweeps, time and per-sweep bandwidth of an offline solve; the
     algorithmic bytes of one sweep are `bytes_per_cell` for every cell of the
-    padded grid (values in and out, the cell word)."""
+    padded grid (values in and out, the cell word).  The state of a solve
+    fits L2, so the fraction of the L2 copy bandwidth measured in this
+    process is reported beside the HBM one."""
     cells = model.H * model.P
     sweep_s = ms / 1e3 / max(r["sweeps"], 1)
     gbps = cells * bytes_per_cell / sweep_s / 1e9
+    l2 = l2_bandwidth()
     return {"sweeps": r["sweeps"], "ms": ms, "first_call_ms": first_ms, "cells": model.H * model.W,
             "us_per_sweep": 1e6 * sweep_s, "cell_sweeps_per_s": model.H * model.W * r["sweeps"] / (ms / 1e3),
-            "bytes_per_cell_sweep": bytes_per_cell, "GBps": gbps, "frac_of_measured_hbm": gbps / peak}
+            "bytes_per_cell_sweep": bytes_per_cell, "GBps": gbps, "frac_of_measured_hbm": gbps / peak,
+            "l2_copy_GBps_measured": l2, "frac_of_measured_l2": gbps / l2}
 
 
 def pbvi_measurement(args, dev, K, flush, stream, with_cpu=True):
@@ -316,12 +352,13 @@ def episodes_measurement(args, dev, stream, E=64, max_steps=200):
     return out
 
 
-def extra_measurements(args, dev, flush, stream, plain_plans_per_s, arm, model, Qd, eps, w):
+def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, eps, w, plain_arm=None,
+                       batched_arm=None, exec_trial=None):
     """Sub-measurements beside the headline: the step's requests as one
-    batched launch against the plain arm's one launch per plan (same
-    requests); the 256-episode batch of uneven maps as one launch against one
-    launch per episode (same episodes); the 128x128 configuration; the
-    512x512 plan with materialised leaves; the other parts of the method."""
+    batched launch against one launch per plan (same requests); the
+    256-episode batch of uneven maps as one launch against one launch per
+    episode (same episodes); the 128x128 configuration; the 512x512 plan
+    with materialised leaves; the other parts of the method."""
     import torch
     from paper_1810_00204_gb300 import _native as N
     from paper_1810_00204_gb300 import api, workloads as WL
@@ -330,25 +367,20 @@ def extra_measurements(args, dev, flush, stream, plain_plans_per_s, arm, model, 
     peak, peak_kind = measured_peak()
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
     # (1) the same R requests in one launch (E = R episodes on one map)
-    b0s = [model.to_grid(e.b0) for e in eps]
-    api.autotune([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
-                 episode=eps[0].episode, leaf_mode=leaf_mode, reps=3)
-    pb = api.Plan([model] * len(eps), [Qd] * len(eps), b0s, depth=w.depth, K=w.K, seed=w.seed,
-                  episode=eps[0].episode, leaf_mode=leaf_mode)
-    pb.capture_graph()
-    for _ in range(3):
-        pb.run()
-    ms = time_device(pb.run, K, flush, stream)
-    same = [r["nodes_per_level"] for r in pb.read()]
-    plain_nodes = [p.read()[0]["nodes_per_level"] for p in arm.plans]
-    out["same_requests_one_launch"] = {
-        "plans_per_s": len(eps) * K / (ms / 1e3), "E": len(eps), "plain_plans_per_s": plain_plans_per_s,
-        "vs_plain": (len(eps) * K / (ms / 1e3)) / plain_plans_per_s, "tuning": pb.tuning,
-        "same_trees_as_plain": same == plain_nodes, "workspace_GB": pb.workspace_bytes / 1e9,
-        "note": "the headline's requests (same map, b0s, seeds and episode words) in one batched launch; the "
-                "plain figure is the headline's one launch per plan"}
-    del pb
-    torch.cuda.empty_cache()
+    # against one launch per request, both timed over K steps
+    if plain_arm is not None and batched_arm is not None:
+        ms_p = plain_arm.time(K)
+        ms_b = batched_arm.time(K)
+        same = [r["nodes_per_level"] for r in batched_arm.plan.read()]
+        plain_nodes = [p.read()[0]["nodes_per_level"] for p in plain_arm.plans]
+        R = len(eps)
+        out["same_requests_one_launch"] = {
+            "plans_per_s": R * K / (ms_b / 1e3), "E": R, "plain_plans_per_s": R * K / (ms_p / 1e3),
+            "vs_plain": ms_p / ms_b, "tuning": batched_arm.plan.tuning, "plain_streams": plain_arm.S,
+            "same_trees_as_plain": same == plain_nodes,
+            "workspace_GB": batched_arm.plan.workspace_bytes / 1e9,
+            "note": "the headline's requests (same map, b0s, seeds and episode words): one batched launch against "
+                    "one launch per plan on streams"}
     # (2) 256 independent episodes on maps of uneven size: one launch per
     # step against one launch per episode, the same episodes
     ws = WL.batched(args.seed, E=256)
@@ -637,11 +669,11 @@ def make_workload(name, seed):
     if name == "mid":
         w = WL.mid(seed)
         desc = ("mid 128x128, 20% rect obstacles, B=16 range 5 acc 0.85, slip 0.1, gamma 0.97, "
-                "gaussian b0 sigma 4, depth 3, K=8, one plan per launch")
+                "gaussian b0 sigma 4, depth 3, K=8")
     elif name == "large":
         w = WL.large(seed)
         desc = ("large 512x512 rooms+walls 25%, B=64 range 8 acc 0.8, slip 0.1, gamma 0.97, "
-                "gaussian b0 sigma 4, depth 3, K=4, one plan per launch")
+                "gaussian b0 sigma 4, depth 3, K=4")
     else:
         w = WL.tiny(seed)
         desc = "tiny 20x20, 15% iid obstacles, B=4 range 3 acc 0.9, depth 2, K=4"
@@ -930,6 +962,27 @@ class PlainArm:
         return time_device(self.step, steps, self.flush, self.stream)
 
 
+class BatchedArm:
+    """The R requests of a step as one batched launch (pattern 2): one plan
+    of E = R episodes (consecutive episode words, so the same trees as one
+    plan per request) with its autotuned launch shape, from a CUDA graph."""
+
+    def __init__(self, api, models, Qs, b0s, episodes, depth, K, seed, leaf_mode, use_graph, flush, stream):
+        self.flush, self.stream = flush, stream
+        api.autotune(models, Qs, b0s, depth=depth, K=K, seed=seed, episode=episodes[0], leaf_mode=leaf_mode, reps=3)
+        self.plan = api.Plan(models, Qs, b0s, depth=depth, K=K, seed=seed, episode=episodes[0], leaf_mode=leaf_mode)
+        if use_graph:
+            self.plan.capture_graph()
+        self.plans, self.streams, self.S, self.trial = [self.plan], [stream], 1, {}
+        self.full_grid = self.grid_ctas = self.plan.grid
+
+    def step(self):
+        self.plan.run()
+
+    def time(self, steps):
+        return time_device(self.step, steps, self.flush, self.stream)
+
+
 def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_plan, flush, reps, peak, peak_kind,
                   job_plans_per_s=None, nodes_avg=None):
     """The dominant kernel (k_plan, the whole plan in one launch) against the
@@ -1064,8 +1117,23 @@ def main():
     if tune is not None:
         knobs = dict(band_cells=tune["band_cells"], items_per_cta=tune["items_per_cta"])
     choices = [args.streams] if args.streams > 0 else [1, 2, 4, 8]
-    arm = PlainArm(api, [model] * R, [Qd] * R, b0s, [e.episode for e in eps], w.depth, w.K, w.seed, leaf_mode,
-                   knobs, use_graph, flush, stream, choices)
+    plain = batched = None
+    if args.execution in ("auto", "plain"):
+        plain = PlainArm(api, [model] * R, [Qd] * R, b0s, [e.episode for e in eps], w.depth, w.K, w.seed,
+                         leaf_mode, knobs, use_graph, flush, stream, choices)
+    if args.execution in ("auto", "batched"):
+        batched = BatchedArm(api, [model] * R, [Qd] * R, b0s, [e.episode for e in eps], w.depth, w.K, w.seed,
+                             leaf_mode, use_graph, flush, stream)
+    exec_trial = {}
+    if plain is not None and batched is not None:
+        for name, a_ in (("plain", plain), ("batched", batched)):
+            for _ in range(3):
+                a_.step()
+            exec_trial[name] = R * 6 / (a_.time(6) * 1e-3)
+        arm = batched if exec_trial["batched"] > exec_trial["plain"] else plain
+    else:
+        arm = plain if plain is not None else batched
+    execution = "batched" if arm is batched else "plain"
 
     # warm-up
     for k in range(max(args.warmup, 0)):
@@ -1107,8 +1175,26 @@ def main():
     peak, peak_kind = measured_peak()
     nodes_avg = [sum(n[l] for n in nodes_per_plan) / len(nodes_per_plan) for l in range(w.depth + 1)]
     roofline, _ = plan_roofline(api, model, Qd, b0s[0], eps[0], args.leaf_mode, leaf_mode, knobs,
-                                arm.plans[0] if arm.S > 1 else None, flush, args.profile_steps, peak, peak_kind,
-                                job_plans_per_s=plans_per_s / world_size, nodes_avg=nodes_avg)
+                                arm.plans[0] if (arm is plain and arm.S > 1) else None, flush, args.profile_steps,
+                                peak, peak_kind, job_plans_per_s=plans_per_s / world_size, nodes_avg=nodes_avg)
+    if arm is batched:
+        # the dominant kernel as the timed region runs it: the batched
+        # launch of the step's R plans, L2 flushed before each launch
+        ms_b = []
+        for k in range(max(1, args.profile_steps)):
+            flush.fill_(k & 255)
+            ms_b.append(batched.plan.profile()[0]["ms"])
+        solo = {k: roofline[k] for k in ("achieved", "frac", "avg_launch_ms", "launch", "algorithmic_bytes_per_launch",
+                                          "fused_design_bytes_per_launch", "fused_design_frac")}
+        b_ms = statistics.mean(ms_b)
+        b_bytes = roofline["algorithmic_bytes_per_launch"] * R
+        roofline.update({"achieved": b_bytes / (b_ms * 1e-3) / 1e9, "frac": b_bytes / (b_ms * 1e-3) / 1e9 / peak,
+                         "avg_launch_ms": b_ms, "algorithmic_bytes_per_launch": b_bytes,
+                         "kernel": f"k_plan ({R} plans, one batched launch)",
+                         "launch": f"the step's batched launch ({batched.plan.grid} CTAs), L2 flushed",
+                         "fused_design_bytes_per_launch": roofline["fused_design_bytes_per_launch"] * R,
+                         "fused_design_frac": roofline["fused_design_bytes_per_launch"] * R / (b_ms * 1e-3) / 1e9 / peak,
+                         "solo": solo})
     roofline["traffic"] = recorded_traffic("k_plan", 0, args.workload)
 
     # end to end through the public API with host buffers: pinned b0 -> device,
@@ -1130,27 +1216,32 @@ def main():
             t0 = time.perf_counter()
             for s_ in arm.streams:
                 s_.wait_stream(stream)
+            # every request's b0 in from pinned memory on its plan's stream
+            for i in range(R):
+                with torch.cuda.stream(arm.streams[(i if arm is plain else 0) % len(arm.streams)]):
+                    b0s[i].copy_(pinned[i], non_blocking=True)
             for i, p in enumerate(arm.plans):
                 s_ = arm.streams[i % len(arm.streams)]
-                with torch.cuda.stream(s_):
-                    b0s[i].copy_(pinned[i], non_blocking=True)
                 p.run(s_)
                 p.read_async(rbufs[i], s_)
             for s_ in arm.streams:
                 s_.synchronize()
-            got = [p.decode(rbufs[i])[0] for i, p in enumerate(arm.plans)]
+            got = [g for i, p in enumerate(arm.plans) for g in p.decode(rbufs[i])]
             t_e2e += time.perf_counter() - t0
-        assert all(g["nodes_per_level"][0] == 1 for g in got)
+        assert len(got) == R and all(g["nodes_per_level"][0] == 1 for g in got)
         e2e_val = R * n_e2e / t_e2e
         e2e_val = replicas.reduce_sum(e2e_val, dev) if world_size > 1 else e2e_val
         e2e = {"value": e2e_val, "unit": "plans/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": n_e2e}
 
-    launch = {"autotune": tune, "streams": arm.S, "grid_ctas": arm.grid_ctas, "full_grid": arm.full_grid,
-              "concurrency_trial_plans_per_s": arm.trial}
+    launch = {"execution": execution, "execution_trial_plans_per_s": exec_trial, "autotune": tune,
+              "streams": arm.S, "grid_ctas": arm.grid_ctas, "full_grid": arm.full_grid,
+              "concurrency_trial_plans_per_s": arm.trial,
+              "batched_tuning": batched.plan.tuning if batched is not None else None}
     extra = None
     if not args.no_extra and rank == 0:
-        extra = extra_measurements(args, dev, flush, stream, plans_per_s / world_size, arm, model, Qd, eps, w)
+        extra = extra_measurements(args, dev, flush, stream, plans_per_s / world_size, arm, model, Qd, eps, w,
+                                   plain_arm=plain, batched_arm=batched, exec_trial=exec_trial)
 
     # oracle CPU baseline (rank 0, N = 1 only), bounded sample
     cpu = None
@@ -1187,7 +1278,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": R * K,
+            "gpu_launches": (R if arm is plain else 1) * K,
             "clocks": clocks,
             "vi": dict(offline_line(vi, vi_first_ms, vi_ms, model, VI_BYTES_PER_CELL, peak),
                        note="offline, once per map; not part of plans/s; ms = median of 3 calls after the first"),

@@ -53,7 +53,7 @@ constexpr int kTot = 36;
 
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
-    size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, u_n, u_off, u_z, u_sa, u_se,
+    size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, lut4, u_n, u_off, u_z, u_sa, u_se,
         scan, flags, acc, c_pa, c_z, c_sa, c_se, wpart, wchild, total;
     __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K, int cmax,
                                                int kslots) {
@@ -67,7 +67,7 @@ struct SmemLayout {
         };
         s.sb = take(sizeof(float) * sb_floats);      // node band, one halo row
         s.sp = take(sizeof(float) * sp_floats);      // parent band, two halo rows
-        s.cw = take(sizeof(uint16_t) * sb_floats);   // cell words, one halo row
+        s.cw = take(sizeof(uint16_t) * (sp_floats > sb_floats ? sp_floats : sb_floats));  // cell words, two halo rows
         s.q = take(sizeof(float) * q_floats);        // the band's rows of Q
         // the label tiles of the finalize phase share the band buffers (the
         // two phases are separated by grid barriers) when those are large enough
@@ -85,6 +85,7 @@ struct SmemLayout {
         s.T = take(sizeof(float) * 28);
         s.uq = take(sizeof(float) * 8);
         s.lut = take(sizeof(float) * 64);
+        s.lut4 = take(sizeof(float) * 64);           // the same weights as float4 [blocked nibble][action]
         s.u_n = take(sizeof(int) * 8);
         s.u_off = take(sizeof(int) * 8);
         s.u_z = take(sizeof(int) * 5 * K);
@@ -110,6 +111,7 @@ struct Smem {
     EpDev *ep;
     int *bco;
     float *hist, *histq, *tot, *red, *P, *C, *T, *uq, *lut;
+    float4 *lut4;
     int *cnt;
     int *u_n, *u_off, *u_z;
     float *u_sa, *u_se;
@@ -144,6 +146,12 @@ __device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpD
 __device__ __forceinline__ void fill_self_lut(float *lut, float slip) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, slip);
 }
+// lut4[blocked nibble] = the four move actions' self weights, one 16-byte load.
+__device__ __forceinline__ void fill_self_lut4(float4 *lut4, float slip) {
+    for (int i = threadIdx.x; i < 16; i += blockDim.x)
+        lut4[i] = make_float4(self_weight(0, i, slip), self_weight(1, i, slip), self_weight(2, i, slip),
+                              self_weight(3, i, slip));
+}
 
 // Copy the descriptor of episode e (and its beacon coordinates) into shared
 // memory, once per change of episode.
@@ -166,6 +174,7 @@ __device__ __forceinline__ void load_ep(const PlanDev &pl, int e, Smem &S, int &
         S.bco[2 * k + 1] = b - (b / ep.P) * ep.P;
     }
     fill_self_lut(S.lut, ep.slip);
+    fill_self_lut4(S.lut4, ep.slip);
     __syncthreads();
     cur_e = e;
 }
@@ -261,12 +270,12 @@ __device__ __forceinline__ void trace_commit(const unsigned long long *t, int n)
 #endif
 
 // Stage one band on one mbarrier: belief rows [r0-h, r1+h) of `b` (zero
-// outside the grid) into bbuf; the cell words of rows [r0-1, r1+1) into cw
-// (cw row i = grid row r0-1+i); and, when q is given, rows [r0, r1) of the
+// outside the grid) into bbuf; the cell words of rows [r0-ch, r1+ch) into cw
+// (cw row i = grid row r0-ch+i); and, when q is given, rows [r0, r1) of the
 // five Q planes into q (plane stride (r1-r0)*P).  Bounded wait, one decision
 // for the whole CTA.
 __device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int h, float *bbuf, uint16_t *cw,
-                           float *q, uint64_t *bar, unsigned &phase, unsigned *status) {
+                           float *q, uint64_t *bar, unsigned &phase, unsigned *status, int ch = 1) {
     const int P = ep.P;
     __syncthreads();  // previous readers of the buffers are done
     for (int r = r0 - h; r < r0; ++r)
@@ -280,13 +289,13 @@ __device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int 
     if (threadIdx.x == 0) {
         fence_proxy_async_global();
         const int lo = max(0, r0 - h), hi = min(ep.H, r1 + h);
-        const int clo = max(0, r0 - 1), chi = min(ep.H, r1 + 1);
+        const int clo = max(0, r0 - ch), chi = min(ep.H, r1 + ch);
         const unsigned bb = static_cast<unsigned>((hi - lo) * P * sizeof(float));
         const unsigned cb = static_cast<unsigned>((chi - clo) * P * sizeof(uint16_t));
         const unsigned qb = static_cast<unsigned>((r1 - r0) * P * sizeof(float));
         mbar_arrive_expect_tx(bar, bb + cb + (q ? 5u * qb : 0u));
         bulk_copy_g2s(bbuf + (lo - (r0 - h)) * P, b + static_cast<size_t>(lo) * P, bb, bar);
-        bulk_copy_g2s(cw + (clo - (r0 - 1)) * P, ep.cell + static_cast<size_t>(clo) * P, cb, bar);
+        bulk_copy_g2s(cw + (clo - (r0 - ch)) * P, ep.cell + static_cast<size_t>(clo) * P, cb, bar);
         if (q)
             for (int a = 0; a < 5; ++a)
                 bulk_copy_g2s(q + a * (r1 - r0) * P, ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0) * P,
@@ -686,13 +695,13 @@ __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem
 // A node's belief at four cells (band-relative row y in [-1, R], columns
 // col..col+3) from its parent's staged band: Phi(parent, a, z) of Eq. 3,
 // zero outside the grid.  `sp` holds the parent's rows [r0-2, r1+2), `cw`
-// the cell words of [r0-1, r1+1).
+// the cell words of the same rows.
 __device__ __forceinline__ float4 child4(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int col,
                                          int a, int z, float sa, float se, const float *lut) {
     const int P = ep.P, r = r0 + y;
     if (r < 0 || r >= ep.H || col >= P) return make_float4(0.f, 0.f, 0.f, 0.f);
     Nbr4 n;
-    load_nbr(ep, sp + (y + 2) * P, cw + (y + 1) * P, col, n);
+    load_nbr(ep, sp + (y + 2) * P, cw + (y + 2) * P, col, n);
     float v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -704,6 +713,44 @@ __device__ __forceinline__ float4 child4(const EpReg &ep, const float *sp, const
     return make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// child4 where no cell within two rows is the goal and the staged parent is
+// zero on occupied cells (phase_expand masks it once per band): every
+// neighbour then moves its mass in without the inflow test, and the
+// blocked moves' mass stays by the self weight of the action.
+__device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *sp, const uint16_t *cw, int y, int col,
+                                              int a, int z, float sa, float se, const float *lut) {
+    const int P = ep.P;
+    const float *mid = sp + (y + 2) * P + col;
+    const float4 up = *reinterpret_cast<const float4 *>(mid - P);
+    const float4 md = *reinterpret_cast<const float4 *>(mid);
+    const float4 dn = *reinterpret_cast<const float4 *>(mid + P);
+    const float west = col > 0 ? mid[-1] : 0.0f;
+    const float east = col + 4 < P ? mid[4] : 0.0f;
+    const ushort4 c4 = *reinterpret_cast<const ushort4 *>(cw + (y + 2) * P + col);
+    const float fwd = 1.0f - 2.0f * ep.slip, slip = ep.slip;
+    const float u[4] = {up.x, up.y, up.z, up.w}, d[4] = {dn.x, dn.y, dn.z, dn.w};
+    const float m[6] = {west, md.x, md.y, md.z, md.w, east};
+    const unsigned cws[4] = {c4.x, c4.y, c4.z, c4.w};
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned w = cws[j];
+        float p;
+        if (a == 4) {
+            p = m[j + 1];
+        } else {
+            // intended move from the neighbour opposite a's step, slips from
+            // the two perpendicular ones (a uniform over the warp)
+            const float n_in = a == 0 ? d[j] : a == 1 ? m[j] : a == 2 ? u[j] : m[j + 2];
+            const float n_pp = (a & 1) ? u[j] + d[j] : m[j] + m[j + 2];
+            p = fmaf(lut[a * 16 + QV_CELL_BLOCKED(w)], m[j + 1], fmaf(fwd, n_in, slip * n_pp));
+        }
+        const float o = static_cast<int>(QV_CELL_LABEL(w)) == z ? sa : se;
+        v[j] = QV_CELL_FREE(w) ? p * o : 0.0f;
+    }
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
 // The same at one cell (band-relative row y, column c), for the edge of a
 // column strip.
 __device__ __forceinline__ float child1(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int c,
@@ -711,7 +758,7 @@ __device__ __forceinline__ float child1(const EpReg &ep, const float *sp, const 
     const int P = ep.P, r = r0 + y;
     if (r < 0 || r >= ep.H || c < 0 || c >= P) return 0.0f;
     const float *m = sp + (y + 2) * P + c;
-    const unsigned w = cw[(y + 1) * P + c];
+    const unsigned w = cw[(y + 2) * P + c];
     const unsigned in = QV_CELL_INFLOW(w);
     float nb[4];
     nb[kDirN] = (in & 1u) ? m[-P] : 0.0f;
@@ -815,8 +862,17 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         for (int band = band0; band < band1; ++band) {
             const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows), R = r1 - r0;
             const int qstride = R * P;
-            if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status))
+            if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status, 2))
                 return false;
+            // occupied cells of the staged parent (or root) carry no belief:
+            // zero them once, so that rows away from the goal can move every
+            // neighbour's mass without the per-cell inflow test
+            {
+                const int lo = max(0, r0 - 2) - (r0 - 2), hi = min(er.H, r1 + 2) - (r0 - 2);
+                for (int i = lo * P + threadIdx.x; i < hi * P; i += blockDim.x)
+                    if (!QV_CELL_FREE(static_cast<unsigned>(S.cw[i]))) S.sp[i] = 0.0f;
+                __syncthreads();
+            }
             if (band == band0) QV_TRACE_MARK(tr, 4);
             // this warp's contiguous range of (child, strip, row) tasks
             const int T = nc * NS * R;
@@ -861,6 +917,8 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                 if (lane == 0) S.wchild[wid * KS + slot] = cur;
                 ++slot;
             };
+            const int grow = goal / P;
+            const float fwd = 1.0f - 2.0f * slip;
             zero_acc();
             while (t < tend) {
                 const int r = t / (NS * R);
@@ -884,13 +942,13 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                 const bool act = gcol < P4;
                 const int col = gcol << 2;
                 float *dst = dst0 ? dst0 + static_cast<long long>(c0 + r) * er.N : nullptr;
+                // the node's belief at this lane's four cells of band row y;
+                // rows more than one row from the goal's take the open form
                 auto row4 = [&](int y) -> float4 {
-                    if (!act) return make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (l == 0) {
-                        const int rr = r0 + y;
-                        return (rr >= 0 && rr < er.H) ? *reinterpret_cast<const float4 *>(S.sp + (y + 2) * P + col)
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+                    const int rr = r0 + y;
+                    if (!act || rr < 0 || rr >= er.H) return make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (l == 0) return *reinterpret_cast<const float4 *>(S.sp + (y + 2) * P + col);
+                    if (abs(rr - grow) >= 2) return child4_open(er, S.sp, S.cw, y, col, pa, pz, sa, se, S.lut);
                     return child4(er, S.sp, S.cw, r0, y, col, pa, pz, sa, se, S.lut);
                 };
                 auto row1 = [&](int y, int c) -> float {
@@ -904,48 +962,98 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                 for (int y = ya; y < yb; ++y) {
                     const float4 dn = row4(y + 1);
                     // the row's west and east neighbours from the adjacent lanes;
-                    // the strip's edges are formed directly
+                    // the strip's two edges are formed directly, in one pass
                     float hw = __shfl_up_sync(0xffffffffu, md.w, 1);
                     float he = __shfl_down_sync(0xffffffffu, md.x, 1);
-                    if (lane == 0) hw = (act && col > 0) ? row1(y, col - 1) : 0.0f;
-                    if (lane == 31) he = (act && col + 4 < P) ? row1(y, col + 4) : 0.0f;
+                    if (lane == 0 || lane == 31) {
+                        const int c = lane == 0 ? col - 1 : col + 4;
+                        const float v = (act && c >= 0 && c < P) ? row1(y, c) : 0.0f;
+                        if (lane == 0) hw = v;
+                        else he = v;
+                    }
                     if (act) {
                         const int yg = (r0 + y) * P + col;
                         if (dst) *reinterpret_cast<float4 *>(dst + yg) = md;
-                        const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(S.cw + (y + 1) * P + col);
+                        const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(S.cw + (y + 2) * P + col);
                         const unsigned cws[4] = {cw4.x, cw4.y, cw4.z, cw4.w};
                         const float ups[4] = {up.x, up.y, up.z, up.w};
                         const float mds[6] = {hw, md.x, md.y, md.z, md.w, he};
                         const float dns[4] = {dn.x, dn.y, dn.z, dn.w};
-                        const float *qrow = S.q + y * P + col;
+                        if (abs(r0 + y - grow) >= 2) {
+                            // open form: the node's belief is zero on occupied
+                            // cells and no cell within a row is the goal, so
+                            // every neighbour moves its mass in; occupied cells'
+                            // outputs are masked by their reward and null weights
+                            float vn[4][5];
 #pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const unsigned cw = cws[jj];
-                            const unsigned in = QV_CELL_INFLOW(cw);
-                            float nb[4], out[5];
-                            nb[kDirN] = (in & 1u) ? ups[jj] : 0.0f;
-                            nb[kDirE] = (in & 2u) ? mds[jj + 2] : 0.0f;
-                            nb[kDirS] = (in & 4u) ? dns[jj] : 0.0f;
-                            nb[kDirW] = (in & 8u) ? mds[jj] : 0.0f;
-                            predict_cell(nb, mds[jj + 1], cw, (yg + jj) == goal, slip, S.lut, out);
-                            const float cst = cost ? __ldg(cost + yg + jj) : 0.0f;
-                            const float rw = stage_reward(QV_CELL_FREE(cw), (yg + jj) == goal, cst);
-                            const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
-                            float qj[5];
-                            if constexpr (FUSED) {
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const unsigned cw = cws[jj];
+                                const float nN = ups[jj], nS = dns[jj], nW = mds[jj], nE = mds[jj + 2];
+                                const float sf = mds[jj + 1];
+                                const float4 sw = S.lut4[QV_CELL_BLOCKED(cw)];
+                                const float ew = slip * (nE + nW), ns = slip * (nN + nS);
+                                float out[5];
+                                out[0] = fmaf(sw.x, sf, fmaf(fwd, nS, ew));
+                                out[1] = fmaf(sw.y, sf, fmaf(fwd, nW, ns));
+                                out[2] = fmaf(sw.z, sf, fmaf(fwd, nN, ew));
+                                out[3] = fmaf(sw.w, sf, fmaf(fwd, nE, ns));
+                                out[4] = sf;
+                                const bool fr = QV_CELL_FREE(cw) != 0u;
+                                const float cst = cost ? __ldg(cost + yg + jj) : 0.0f;
+                                const float rw = fr ? -1.0f - cst : 0.0f;
+                                const float nf = (fr && static_cast<int>(QV_CELL_LABEL(cw)) >= B) ? 1.0f : 0.0f;
 #pragma unroll
-                                for (int ap = 0; ap < 5; ++ap) qj[ap] = qrow[ap * qstride + jj];
+                                for (int a = 0; a < 5; ++a) {
+                                    acc_r[a] = fmaf(out[a], rw, acc_r[a]);
+                                    vn[jj][a] = out[a] * nf;
+                                    acc_null[a] += vn[jj][a];
+                                }
                             }
+                            if constexpr (FUSED) {
+                                // the Q-weighted null masses, one 16-byte Q load per action
 #pragma unroll
-                            for (int a = 0; a < 5; ++a) {
-                                const float v = out[a];
-                                acc_r[a] = fmaf(v, rw, acc_r[a]);
-                                const float vn = v * isnull;
-                                acc_null[a] += vn;
+                                for (int ap = 0; ap < 5; ++ap) {
+                                    const float4 q4 = *reinterpret_cast<const float4 *>(S.q + ap * qstride + y * P + col);
+#pragma unroll
+                                    for (int a = 0; a < 5; ++a)
+                                        acc_q[a * 5 + ap] =
+                                            fmaf(vn[3][a], q4.w,
+                                                 fmaf(vn[2][a], q4.z, fmaf(vn[1][a], q4.y, fmaf(vn[0][a], q4.x, acc_q[a * 5 + ap]))));
+                                }
+                            }
+                        } else {
+                            // the exact form near the goal: inflow masks and the
+                            // goal's own mass staying put
+                            const float *qrow = S.q + y * P + col;
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) {
+                                const unsigned cw = cws[jj];
+                                const unsigned in = QV_CELL_INFLOW(cw);
+                                float nb[4], out[5];
+                                nb[kDirN] = (in & 1u) ? ups[jj] : 0.0f;
+                                nb[kDirE] = (in & 2u) ? mds[jj + 2] : 0.0f;
+                                nb[kDirS] = (in & 4u) ? dns[jj] : 0.0f;
+                                nb[kDirW] = (in & 8u) ? mds[jj] : 0.0f;
+                                predict_cell(nb, mds[jj + 1], cw, (yg + jj) == goal, slip, S.lut, out);
+                                const float cst = cost ? __ldg(cost + yg + jj) : 0.0f;
+                                const float rw = stage_reward(QV_CELL_FREE(cw), (yg + jj) == goal, cst);
+                                const float isnull = static_cast<int>(QV_CELL_LABEL(cw)) >= B ? 1.0f : 0.0f;
+                                float qj[5];
                                 if constexpr (FUSED) {
 #pragma unroll
-                                    for (int ap = 0; ap < 5; ++ap)
-                                        acc_q[a * 5 + ap] = fmaf(vn, qj[ap], acc_q[a * 5 + ap]);
+                                    for (int ap = 0; ap < 5; ++ap) qj[ap] = qrow[ap * qstride + jj];
+                                }
+#pragma unroll
+                                for (int a = 0; a < 5; ++a) {
+                                    const float v = out[a];
+                                    acc_r[a] = fmaf(v, rw, acc_r[a]);
+                                    const float vnn = v * isnull;
+                                    acc_null[a] += vnn;
+                                    if constexpr (FUSED) {
+#pragma unroll
+                                        for (int ap = 0; ap < 5; ++ap)
+                                            acc_q[a * 5 + ap] = fmaf(vnn, qj[ap], acc_q[a * 5 + ap]);
+                                    }
                                 }
                             }
                         }
@@ -960,12 +1068,17 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
             __syncthreads();
             if (band == band0) QV_TRACE_MARK(tr, 5);
             // the warps' slots into each child's totals, in (warp, slot) order
+            // (a warp's slots hold increasing children, -1 after the last)
             for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
                 const int r = i / kTot, v = i - r * kTot;
                 if (v >= NV) continue;
                 float sum = 0.0f;
-                for (int sl = 0; sl < kWarps * KS; ++sl)
-                    if (S.wchild[sl] == r) sum += S.wpart[sl * kTot + v];
+                for (int ww = 0; ww < kWarps; ++ww)
+                    for (int sl = ww * KS; sl < (ww + 1) * KS; ++sl) {
+                        const int c = S.wchild[sl];
+                        if (c < 0 || c > r) break;
+                        if (c == r) sum += S.wpart[sl * kTot + v];
+                    }
                 S.acc[i] += sum;
             }
         }
@@ -1697,6 +1810,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     S.T = reinterpret_cast<float *>(smem_raw + L.T);
     S.uq = reinterpret_cast<float *>(smem_raw + L.uq);
     S.lut = reinterpret_cast<float *>(smem_raw + L.lut);
+    S.lut4 = reinterpret_cast<float4 *>(smem_raw + L.lut4);
     S.u_n = reinterpret_cast<int *>(smem_raw + L.u_n);
     S.u_off = reinterpret_cast<int *>(smem_raw + L.u_off);
     S.u_z = reinterpret_cast<int *>(smem_raw + L.u_z);
