@@ -366,6 +366,7 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
     K = max(3, args.extra_steps)
     peak, peak_kind = measured_peak()
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
+    b0s = [model.to_grid(e.b0) for e in eps]
     # (1) the same R requests in one launch (E = R episodes on one map)
     # against one launch per request, both timed over K steps
     if plain_arm is not None and batched_arm is not None:
