@@ -16,6 +16,9 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kLeafGroup = 4;
 constexpr float kBoundaryEps = 1e-6f;
 constexpr int kStamps = 4 * kMaxD + 8;
+// Offset of the encoded support-window words (PlanDev::win): a bound that
+// exceeds every grid coordinate, so that 0 encodes "no cell yet".
+constexpr int kWinBig = 1 << 24;
 
 struct __align__(16) EpDev {
     int H, W, P, N;          // N = H * P
@@ -101,6 +104,10 @@ struct PlanDev {
     float *xrec;       // [n_xrec][kTot] per (item, child rank) totals
     float *frec;       // [n_frec] label-histogram records of beacon chunks
     int *wb_leaf;      // [E+1]
+    // [E][4] support window of b0: the largest kWinBig - row, row + 1,
+    // kWinBig - col, col + 1 over its nonzero free cells (0 = none), found by
+    // the root's expand pass and cleared at the end of every run
+    unsigned *win;
     int *leaf_split;   // chunks per group of leaves in the leaf phase
     unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
     // per node (gid over every level)

@@ -21,7 +21,7 @@ struct Layout {
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
-        off_status, off_boundary, off_bar, off_stamps, off_result, off_beliefs;
+        off_status, off_boundary, off_bar, off_win, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0, cmax = 0;
     long long n_xrec = 0, n_frec = 0;
@@ -316,6 +316,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_lvl_cnt = take(sizeof(unsigned) * D1);
     L.off_leaf_cnt = take(sizeof(unsigned) * static_cast<size_t>(L.n_part));
     L.off_bar = take(sizeof(qv::GridBar));
+    L.off_win = take(sizeof(unsigned) * 4 * E);
     L.off_beliefs = take(sizeof(float) * std::max<long long>(L.n_belief, 4));
     L.total = align_up(o, 256);
     return QV_OK;
@@ -457,6 +458,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.status = at<unsigned>(ws, L.off_status);
     d.boundary = at<unsigned long long>(ws, L.off_boundary);
     d.bar = at<qv::GridBar>(ws, L.off_bar);
+    d.win = at<unsigned>(ws, L.off_win);
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;

@@ -143,6 +143,76 @@ __device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpD
     return pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N;
 }
 
+// ---------------------------------------------------------------- support windows
+// The motion stencil (Eq. 3 numerator, Eq. 10) moves mass by at most one
+// cell and the observation weights (Eq. 3) only rescale it, so a node d
+// levels below the root is zero outside the bounding box of b0's nonzero
+// free cells dilated by d cells.  The expand and finalize phases restrict
+// their sums to that window; every cell outside it contributes exactly zero.
+struct Win {
+    int r0, r1, c0, c1;  // rows [r0, r1), columns [c0, c1); empty when r1 <= r0
+};
+__device__ __forceinline__ Win support_window(const PlanDev &pl, int e, int H, int W, int d) {
+    const unsigned *w = pl.win + 4 * e;
+    const int rmin = kWinBig - static_cast<int>(__ldcg(w)), rmax = static_cast<int>(__ldcg(w + 1)) - 1;
+    const int cmin = kWinBig - static_cast<int>(__ldcg(w + 2)), cmax = static_cast<int>(__ldcg(w + 3)) - 1;
+    Win v;
+    if (rmax < rmin || cmax < cmin) {
+        v.r0 = v.r1 = v.c0 = v.c1 = 0;
+        return v;
+    }
+    v.r0 = max(0, rmin - d);
+    v.r1 = min(H, rmax + d + 1);
+    v.c0 = max(0, cmin - d);
+    v.c1 = min(W, cmax + d + 1);
+    return v;
+}
+
+// Band geometry of the expand phase at level l: task rows [r0, r1) and
+// float4 column groups [g0, g1) (where the level's predicted masses can be
+// nonzero: the support window of level l + 1), the staged columns
+// [sc0, sc0 + sw) (the task columns with the two-cell reach of a child's
+// stencil, rounded out to multiples of 8 so that every staged row starts and
+// ends on a 16-byte boundary), `rows` task rows per band and `nb` bands.
+// The root's pass (l = 0) covers the whole grid, since it finds the window.
+// rows * sw never exceeds band_rows * P, so a windowed band fits the buffers
+// sized for a full-width one.
+struct BandGeo {
+    int r0, r1, g0, g1, sc0, sw, rows, nb;
+};
+__device__ __forceinline__ BandGeo band_geo(const PlanDev &pl, int e, int H, int W, int P, int band_rows, int l) {
+    BandGeo g;
+    if (l == 0) {
+        g.r0 = 0;
+        g.r1 = H;
+        g.g0 = 0;
+        g.g1 = P >> 2;
+        g.sc0 = 0;
+        g.sw = P;
+        g.rows = band_rows;
+        g.nb = (H + band_rows - 1) / band_rows;
+        return g;
+    }
+    const Win t = support_window(pl, e, H, W, l + 1);
+    g.r0 = t.r0;
+    g.r1 = t.r1;
+    g.g0 = t.c0 >> 2;
+    g.g1 = (t.c1 + 3) >> 2;
+    if (t.r1 <= t.r0 || t.c1 <= t.c0) {
+        g.g1 = g.g0;
+        g.sc0 = 0;
+        g.sw = 8;
+        g.rows = 1;
+        g.nb = 0;
+        return g;
+    }
+    g.sc0 = max(0, 4 * g.g0 - 2) & ~7;
+    g.sw = min(P, (4 * g.g1 + 2 + 7) & ~7) - g.sc0;
+    g.rows = max(1, min(t.r1 - t.r0, (band_rows * P) / g.sw));
+    g.nb = (t.r1 - t.r0 + g.rows - 1) / g.rows;
+    return g;
+}
+
 __device__ __forceinline__ void fill_self_lut(float *lut, float slip) {
     for (int i = threadIdx.x; i < 64; i += blockDim.x) lut[i] = self_weight(i >> 4, i & 15, slip);
 }
@@ -300,6 +370,57 @@ __device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int 
             for (int a = 0; a < 5; ++a)
                 bulk_copy_g2s(q + a * (r1 - r0) * P, ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0) * P,
                               qb, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, phase);
+    const int failed = __syncthreads_or(ok ? 0 : 1);
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(status, kErrTimeout);
+        if (!ok) mbar_wait_bounded(bar, phase);  // let the copies in flight land before leaving
+    }
+    phase ^= 1u;
+    return failed == 0;
+}
+
+// The expand phase's staging of one band of a column window: belief rows
+// [r0-2, r1+2) (zero outside the grid) and cell words of the same rows,
+// columns [sc0, sc0 + sw), into rows of sw values; with q, rows [r0, r1) of
+// the five Q planes (plane stride (r1-r0)*sw).  A full-width window is
+// contiguous and takes stage_band's copies; a narrower one takes one bulk
+// copy per row and array, issued by the lanes of warp 0.
+__device__ bool stage_window(const EpReg &ep, const float *b, int r0, int r1, int sc0, int sw, float *bbuf,
+                             uint16_t *cw, float *q, uint64_t *bar, unsigned &phase, unsigned *status) {
+    const int P = ep.P;
+    if (sw == P) return stage_band(ep, b, r0, r1, 2, bbuf, cw, q, bar, phase, status, 2);
+    __syncthreads();  // previous readers of the buffers are done
+    for (int r = r0 - 2; r < r0; ++r)
+        if (r < 0)
+            for (int i = threadIdx.x; i < sw; i += blockDim.x) bbuf[(r - (r0 - 2)) * sw + i] = 0.0f;
+    for (int r = r1; r < r1 + 2; ++r)
+        if (r >= ep.H)
+            for (int i = threadIdx.x; i < sw; i += blockDim.x) bbuf[(r - (r0 - 2)) * sw + i] = 0.0f;
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int lo = max(0, r0 - 2), hi = min(ep.H, r1 + 2), R = r1 - r0;
+        const int nbr = hi - lo, nq = q ? 5 * R : 0;
+        const unsigned rb = static_cast<unsigned>(sw * sizeof(float)), cb = static_cast<unsigned>(sw * sizeof(uint16_t));
+        if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<unsigned>(nbr) * (rb + cb) + static_cast<unsigned>(nq) * rb);
+        __syncwarp();
+        fence_proxy_async_global();
+        for (int i = lane; i < 2 * nbr + nq; i += 32) {
+            if (i < nbr) {
+                const int r = lo + i;
+                bulk_copy_g2s(bbuf + (r - (r0 - 2)) * sw, b + static_cast<size_t>(r) * P + sc0, rb, bar);
+            } else if (i < 2 * nbr) {
+                const int r = lo + i - nbr;
+                bulk_copy_g2s(cw + (r - (r0 - 2)) * sw, ep.cell + static_cast<size_t>(r) * P + sc0, cb, bar);
+            } else {
+                const int a = (i - 2 * nbr) / R, y = (i - 2 * nbr) - a * R;
+                bulk_copy_g2s(q + (a * R + y) * sw,
+                              ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0 + y) * P + sc0, rb, bar);
+            }
+        }
     }
     const bool ok = mbar_wait_bounded(bar, phase);
     const int failed = __syncthreads_or(ok ? 0 : 1);
@@ -636,7 +757,9 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         const int cnt = __ldcg(pl.count + l1 * E + e);
         const int c0 = min(__ldcg(pl.choff + ia), cnt);
         const int c1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
-        return make_int2(max(0, c1 - c0), __ldg(&pl.eps[e].bands));
+        const EpDev *ep = pl.eps + e;
+        const BandGeo geo = band_geo(pl, e, __ldg(&ep->H), __ldg(&ep->W), __ldg(&ep->P), __ldg(&ep->band_rows), l1);
+        return make_int2(max(0, c1 - c0), max(geo.nb, 1));  // an empty window still writes its zero totals
     };
     int wi = 0, wr = 0;
     for (int base = 0; base < G; base += blockDim.x) {
@@ -692,23 +815,32 @@ __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem
 }
 
 // ---------------------------------------------------------------- expand phase
-// A node's belief at four cells (band-relative row y in [-1, R], columns
-// col..col+3) from its parent's staged band: Phi(parent, a, z) of Eq. 3,
-// zero outside the grid.  `sp` holds the parent's rows [r0-2, r1+2), `cw`
-// the cell words of the same rows.
-__device__ __forceinline__ float4 child4(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int col,
+// A node's belief at four cells (grid row r, columns col..col+3) from its
+// parent's staged band: Phi(parent, a, z) of Eq. 3, zero outside the grid.
+// `m` points at the staged parent value of (r, col), `c` at its cell word;
+// staged rows are SW values apart.
+__device__ __forceinline__ float4 child4(const EpReg &ep, const float *m, const uint16_t *c, int SW, int r, int col,
                                          int a, int z, float sa, float se, const float *lut) {
-    const int P = ep.P, r = r0 + y;
+    const int P = ep.P;
     if (r < 0 || r >= ep.H || col >= P) return make_float4(0.f, 0.f, 0.f, 0.f);
-    Nbr4 n;
-    load_nbr(ep, sp + (y + 2) * P, cw + (y + 2) * P, col, n);
+    const float4 up = *reinterpret_cast<const float4 *>(m - SW);
+    const float4 md = *reinterpret_cast<const float4 *>(m);
+    const float4 dn = *reinterpret_cast<const float4 *>(m + SW);
+    const float u[4] = {up.x, up.y, up.z, up.w}, d[4] = {dn.x, dn.y, dn.z, dn.w};
+    const float mm[6] = {col > 0 ? m[-1] : 0.0f, md.x, md.y, md.z, md.w, col + 4 < P ? m[4] : 0.0f};
+    const ushort4 c4 = *reinterpret_cast<const ushort4 *>(c);
+    const unsigned cws[4] = {c4.x, c4.y, c4.z, c4.w};
     float v[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+        const unsigned in = QV_CELL_INFLOW(cws[j]);
         float nb[4];
-        inflow_nb(n, j, nb);
-        const float p = predict_one(nb, n.m[j + 1], n.cw[j], r * P + col + j == ep.goal, ep.slip, lut, a);
-        v[j] = p * (static_cast<int>(QV_CELL_LABEL(n.cw[j])) == z ? sa : se);
+        nb[kDirN] = (in & 1u) ? u[j] : 0.0f;
+        nb[kDirE] = (in & 2u) ? mm[j + 2] : 0.0f;
+        nb[kDirS] = (in & 4u) ? d[j] : 0.0f;
+        nb[kDirW] = (in & 8u) ? mm[j] : 0.0f;
+        const float p = predict_one(nb, mm[j + 1], cws[j], r * P + col + j == ep.goal, ep.slip, lut, a);
+        v[j] = p * (static_cast<int>(QV_CELL_LABEL(cws[j])) == z ? sa : se);
     }
     return make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -717,19 +849,18 @@ __device__ __forceinline__ float4 child4(const EpReg &ep, const float *sp, const
 // zero on occupied cells (phase_expand masks it once per band): every
 // neighbour then moves its mass in without the inflow test, and the
 // blocked moves' mass stays by the self weight of the action.
-__device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *sp, const uint16_t *cw, int y, int col,
+__device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *m, const uint16_t *c, int SW, int col,
                                               int a, int z, float sa, float se, const float *lut) {
     const int P = ep.P;
-    const float *mid = sp + (y + 2) * P + col;
-    const float4 up = *reinterpret_cast<const float4 *>(mid - P);
-    const float4 md = *reinterpret_cast<const float4 *>(mid);
-    const float4 dn = *reinterpret_cast<const float4 *>(mid + P);
-    const float west = col > 0 ? mid[-1] : 0.0f;
-    const float east = col + 4 < P ? mid[4] : 0.0f;
-    const ushort4 c4 = *reinterpret_cast<const ushort4 *>(cw + (y + 2) * P + col);
+    const float4 up = *reinterpret_cast<const float4 *>(m - SW);
+    const float4 md = *reinterpret_cast<const float4 *>(m);
+    const float4 dn = *reinterpret_cast<const float4 *>(m + SW);
+    const float west = col > 0 ? m[-1] : 0.0f;
+    const float east = col + 4 < P ? m[4] : 0.0f;
+    const ushort4 c4 = *reinterpret_cast<const ushort4 *>(c);
     const float fwd = 1.0f - 2.0f * ep.slip, slip = ep.slip;
     const float u[4] = {up.x, up.y, up.z, up.w}, d[4] = {dn.x, dn.y, dn.z, dn.w};
-    const float m[6] = {west, md.x, md.y, md.z, md.w, east};
+    const float mm[6] = {west, md.x, md.y, md.z, md.w, east};
     const unsigned cws[4] = {c4.x, c4.y, c4.z, c4.w};
     float v[4];
 #pragma unroll
@@ -737,13 +868,13 @@ __device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *sp, 
         const unsigned w = cws[j];
         float p;
         if (a == 4) {
-            p = m[j + 1];
+            p = mm[j + 1];
         } else {
             // intended move from the neighbour opposite a's step, slips from
             // the two perpendicular ones (a uniform over the warp)
-            const float n_in = a == 0 ? d[j] : a == 1 ? m[j] : a == 2 ? u[j] : m[j + 2];
-            const float n_pp = (a & 1) ? u[j] + d[j] : m[j] + m[j + 2];
-            p = fmaf(lut[a * 16 + QV_CELL_BLOCKED(w)], m[j + 1], fmaf(fwd, n_in, slip * n_pp));
+            const float n_in = a == 0 ? d[j] : a == 1 ? mm[j] : a == 2 ? u[j] : mm[j + 2];
+            const float n_pp = (a & 1) ? u[j] + d[j] : mm[j] + mm[j + 2];
+            p = fmaf(lut[a * 16 + QV_CELL_BLOCKED(w)], mm[j + 1], fmaf(fwd, n_in, slip * n_pp));
         }
         const float o = static_cast<int>(QV_CELL_LABEL(w)) == z ? sa : se;
         v[j] = QV_CELL_FREE(w) ? p * o : 0.0f;
@@ -751,19 +882,18 @@ __device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *sp, 
     return make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// The same at one cell (band-relative row y, column c), for the edge of a
-// column strip.
-__device__ __forceinline__ float child1(const EpReg &ep, const float *sp, const uint16_t *cw, int r0, int y, int c,
+// The same at one cell (grid row r, column c; `m`, `cw` its staged value and
+// word), for the edge of a column strip.
+__device__ __forceinline__ float child1(const EpReg &ep, const float *m, const uint16_t *cwp, int SW, int r, int c,
                                         int a, int z, float sa, float se, const float *lut) {
-    const int P = ep.P, r = r0 + y;
+    const int P = ep.P;
     if (r < 0 || r >= ep.H || c < 0 || c >= P) return 0.0f;
-    const float *m = sp + (y + 2) * P + c;
-    const unsigned w = cw[(y + 2) * P + c];
+    const unsigned w = *cwp;
     const unsigned in = QV_CELL_INFLOW(w);
     float nb[4];
-    nb[kDirN] = (in & 1u) ? m[-P] : 0.0f;
+    nb[kDirN] = (in & 1u) ? m[-SW] : 0.0f;
     nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
-    nb[kDirS] = (in & 4u) ? m[P] : 0.0f;
+    nb[kDirS] = (in & 4u) ? m[SW] : 0.0f;
     nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
     const float p = predict_one(nb, m[0], w, r * P + c == ep.goal, ep.slip, lut, a);
     return p * (static_cast<int>(QV_CELL_LABEL(w)) == z ? sa : se);
@@ -850,27 +980,52 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) S.acc[i] = 0.0f;
         __syncthreads();
         QV_TRACE_MARK(tr, 3);
-        const int band0 = static_cast<int>((static_cast<long long>(item) * ep.bands) / items);
-        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * ep.bands) / items);
-        const int band_rows = ep.band_rows;
+        const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
+        const int band0 = static_cast<int>((static_cast<long long>(item) * geo.nb) / items);
+        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * geo.nb) / items);
         const EpReg er = ep_reg(ep);
-        const int P = er.P, P4 = P >> 2, goal = er.goal;
-        const int NS = (P4 + 31) >> 5;  // column strips of 32 float4 groups
+        const int P = er.P, P4 = P >> 2, goal = er.goal, SW = geo.sw;
+        const int NS = (geo.g1 - geo.g0 + 31) >> 5;  // column strips of 32 float4 groups
         const float slip = er.slip;
         const float *cost = er.cost;
         float *dst0 = (l > 0 && store) ? pl.beliefs + ep.belief_off[l] : nullptr;
         for (int band = band0; band < band1; ++band) {
-            const int r0 = band * band_rows, r1 = min(er.H, r0 + band_rows), R = r1 - r0;
-            const int qstride = R * P;
-            if (!stage_band(er, src, r0, r1, 2, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase, pl.status, 2))
+            const int r0 = geo.r0 + band * geo.rows, r1 = min(geo.r1, r0 + geo.rows), R = r1 - r0;
+            const int qstride = R * SW;
+            if (!stage_window(er, src, r0, r1, geo.sc0, SW, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase,
+                              pl.status))
                 return false;
             // occupied cells of the staged parent (or root) carry no belief:
             // zero them once, so that rows away from the goal can move every
-            // neighbour's mass without the per-cell inflow test
+            // neighbour's mass without the per-cell inflow test.  The root's
+            // pass also finds the support window of b0 from its own rows.
             {
                 const int lo = max(0, r0 - 2) - (r0 - 2), hi = min(er.H, r1 + 2) - (r0 - 2);
-                for (int i = lo * P + threadIdx.x; i < hi * P; i += blockDim.x)
-                    if (!QV_CELL_FREE(static_cast<unsigned>(S.cw[i]))) S.sp[i] = 0.0f;
+                unsigned wr0 = 0u, wr1 = 0u, wc0 = 0u, wc1 = 0u;
+                for (int i = lo * SW + threadIdx.x; i < hi * SW; i += blockDim.x) {
+                    if (!QV_CELL_FREE(static_cast<unsigned>(S.cw[i]))) {
+                        S.sp[i] = 0.0f;
+                    } else if (l == 0 && S.sp[i] != 0.0f && i >= 2 * SW && i < (R + 2) * SW) {
+                        const int rr = r0 - 2 + i / SW, cc = geo.sc0 + i % SW;
+                        wr0 = max(wr0, static_cast<unsigned>(kWinBig - rr));
+                        wr1 = max(wr1, static_cast<unsigned>(rr + 1));
+                        wc0 = max(wc0, static_cast<unsigned>(kWinBig - cc));
+                        wc1 = max(wc1, static_cast<unsigned>(cc + 1));
+                    }
+                }
+                if (l == 0) {
+                    wr0 = __reduce_max_sync(0xffffffffu, wr0);
+                    wr1 = __reduce_max_sync(0xffffffffu, wr1);
+                    wc0 = __reduce_max_sync(0xffffffffu, wc0);
+                    wc1 = __reduce_max_sync(0xffffffffu, wc1);
+                    if (lane == 0 && wr1 != 0u) {
+                        unsigned *wv = pl.win + 4 * e;
+                        atomicMax(wv, wr0);
+                        atomicMax(wv + 1, wr1);
+                        atomicMax(wv + 2, wc0);
+                        atomicMax(wv + 3, wc1);
+                    }
+                }
                 __syncthreads();
             }
             if (band == band0) QV_TRACE_MARK(tr, 4);
@@ -938,25 +1093,26 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                     sa = S.c_sa[r];
                     se = S.c_se[r];
                 }
-                const int gcol = s * 32 + lane;
-                const bool act = gcol < P4;
-                const int col = gcol << 2;
+                const int gcol = geo.g0 + s * 32 + lane;
+                const bool act = gcol < geo.g1;
+                const int col = gcol << 2, sc = col - geo.sc0;
                 float *dst = dst0 ? dst0 + static_cast<long long>(c0 + r) * er.N : nullptr;
                 // the node's belief at this lane's four cells of band row y;
                 // rows more than one row from the goal's take the open form
                 auto row4 = [&](int y) -> float4 {
                     const int rr = r0 + y;
                     if (!act || rr < 0 || rr >= er.H) return make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (l == 0) return *reinterpret_cast<const float4 *>(S.sp + (y + 2) * P + col);
-                    if (abs(rr - grow) >= 2) return child4_open(er, S.sp, S.cw, y, col, pa, pz, sa, se, S.lut);
-                    return child4(er, S.sp, S.cw, r0, y, col, pa, pz, sa, se, S.lut);
+                    const int o = (y + 2) * SW + sc;
+                    if (l == 0) return *reinterpret_cast<const float4 *>(S.sp + o);
+                    if (abs(rr - grow) >= 2) return child4_open(er, S.sp + o, S.cw + o, SW, col, pa, pz, sa, se, S.lut);
+                    return child4(er, S.sp + o, S.cw + o, SW, rr, col, pa, pz, sa, se, S.lut);
                 };
+                // (c is within the staged columns: the window keeps two
+                // columns of reach on each side of its task columns)
                 auto row1 = [&](int y, int c) -> float {
-                    if (l == 0) {
-                        const int rr = r0 + y;
-                        return (rr >= 0 && rr < er.H && c >= 0 && c < P) ? S.sp[(y + 2) * P + c] : 0.0f;
-                    }
-                    return child1(er, S.sp, S.cw, r0, y, c, pa, pz, sa, se, S.lut);
+                    const int rr = r0 + y, o = (y + 2) * SW + (c - geo.sc0);
+                    if (l == 0) return (rr >= 0 && rr < er.H && c >= 0 && c < P) ? S.sp[o] : 0.0f;
+                    return child1(er, S.sp + o, S.cw + o, SW, rr, c, pa, pz, sa, se, S.lut);
                 };
                 float4 up = row4(ya - 1), md = row4(ya);
                 for (int y = ya; y < yb; ++y) {
@@ -974,7 +1130,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                     if (act) {
                         const int yg = (r0 + y) * P + col;
                         if (dst) *reinterpret_cast<float4 *>(dst + yg) = md;
-                        const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(S.cw + (y + 2) * P + col);
+                        const ushort4 cw4 = *reinterpret_cast<const ushort4 *>(S.cw + (y + 2) * SW + sc);
                         const unsigned cws[4] = {cw4.x, cw4.y, cw4.z, cw4.w};
                         const float ups[4] = {up.x, up.y, up.z, up.w};
                         const float mds[6] = {hw, md.x, md.y, md.z, md.w, he};
@@ -1013,7 +1169,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                                 // the Q-weighted null masses, one 16-byte Q load per action
 #pragma unroll
                                 for (int ap = 0; ap < 5; ++ap) {
-                                    const float4 q4 = *reinterpret_cast<const float4 *>(S.q + ap * qstride + y * P + col);
+                                    const float4 q4 = *reinterpret_cast<const float4 *>(S.q + ap * qstride + y * SW + sc);
 #pragma unroll
                                     for (int a = 0; a < 5; ++a)
                                         acc_q[a * 5 + ap] =
@@ -1024,7 +1180,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                         } else {
                             // the exact form near the goal: inflow masks and the
                             // goal's own mass staying put
-                            const float *qrow = S.q + y * P + col;
+                            const float *qrow = S.q + y * SW + sc;
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj) {
                                 const unsigned cw = cws[jj];
@@ -1082,6 +1238,21 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                 S.acc[i] += sum;
             }
         }
+        if (dst0) {
+            // the stored children are zero outside the task window: this
+            // item's share of the grid's rows, one warp per (child, row)
+            const int zr0 = static_cast<int>((static_cast<long long>(item) * er.H) / items);
+            const int zr1 = static_cast<int>((static_cast<long long>(item + 1) * er.H) / items);
+            const int nr = zr1 - zr0;
+            for (int t2 = wid; t2 < nc * nr; t2 += kWarps) {
+                const int r = t2 / nr, row = zr0 + (t2 - r * nr);
+                float4 *d4 = reinterpret_cast<float4 *>(dst0 + static_cast<long long>(c0 + r) * er.N +
+                                                        static_cast<long long>(row) * P);
+                const bool in = row >= geo.r0 && row < geo.r1;
+                for (int g = lane; g < P4; g += 32)
+                    if (!in || g < geo.g0 || g >= geo.g1) d4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
         __syncthreads();
         // the item's totals of every child: final when the group has one item,
         // else one record per (item, child) that phase_finalize adds in order
@@ -1114,15 +1285,17 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
 // is covered by tiles of kTileH x kTileW cells; per tile the parent's values
 // with a two-cell rim and the cell words with a one-cell rim are read into
 // the warp's shared buffers, the node's belief is formed on the tile with a
-// one-cell rim, and the diamond's cells of label k predict from it.
+// one-cell rim, and the diamond's cells of label k predict from it.  Only
+// the part of the diamond inside `win` (where the node's predicted masses
+// can be nonzero) is visited.
 template <bool FUSED>
 __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa, int zc, float sa, float se, int k,
-                            int br, int bc, float *tp, float *tc, uint16_t *tcw, const float *lut, float la[5],
-                            float lq[FUSED ? 25 : 1]) {
+                            int br, int bc, const Win &win, float *tp, float *tc, uint16_t *tcw, const float *lut,
+                            float la[5], float lq[FUSED ? 25 : 1]) {
     const int lane = threadIdx.x & 31;
     const int R = ep.range, P = ep.P, H = ep.H, W = ep.W;
-    const int rlo = max(0, br - R), rhi = min(H - 1, br + R);
-    const int clo = max(0, bc - R), chi = min(W - 1, bc + R);
+    const int rlo = max(max(0, br - R), win.r0), rhi = min(min(H - 1, br + R), win.r1 - 1);
+    const int clo = max(max(0, bc - R), win.c0), chi = min(min(W - 1, bc + R), win.c1 - 1);
     constexpr int PW = kTileW + 4, CW = kTileW + 2;
     constexpr int NP = (kTileP + 31) / 32, NC = (kTileC + 31) / 32, ND = (kTileH * kTileW + 31) / 32;
     for (int y0 = rlo; y0 <= rhi; y0 += kTileH) {
@@ -1298,6 +1471,7 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             par = node_belief(pl, ep, l - 1, lp);
         }
         const EpReg er = ep_reg(ep);
+        const Win win = support_window(pl, e, ep.H, ep.W, l + 1);
         const int bpc = (B + C - 1) / C;
         const int k0 = min(B, chunk * bpc), k1 = min(B, k0 + bpc);
         __syncthreads();  // the previous item's readers of the histograms are done
@@ -1306,8 +1480,8 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             float lq[FUSED ? 25 : 1];
 #pragma unroll
             for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
-            label_tiles<FUSED>(er, par, l == 0, pa, zc, sa, se, k, S.bco[2 * k], S.bco[2 * k + 1], tp, tc, tcw, S.lut,
-                               la, lq);
+            label_tiles<FUSED>(er, par, l == 0, pa, zc, sa, se, k, S.bco[2 * k], S.bco[2 * k + 1], win, tp, tc, tcw,
+                               S.lut, la, lq);
             // lane i ends with the warp total of value i: 0..4 the label
             // masses, 5..29 the Q-weighted ones
             float v[32];
@@ -1868,6 +2042,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         if (!grid_sync(pl)) return;
         stamp(pl, slot++);
     }
+    // every reader of the support windows is past the last grid barrier: the
+    // next run's root pass finds them afresh
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 4 * pl.E; i += blockDim.x) pl.win[i] = 0u;
     if (D > 0) {
         phase_backup(pl, S, cur_e, Deff);
         stamp(pl, slot++);
