@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched (256 uneven maps) and 512x512 sub-measurements")
     ap.add_argument("--extra-steps", type=int, default=20)
+    ap.add_argument("--sm-max-mhz", type=float, default=NOMINAL_SM_MHZ,
+                    help="SM clock of the FP32 peak (replaced by the sampled maximum when clocks are sampled)")
     return ap.parse_args()
 
 
@@ -365,6 +367,7 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
     out = {}
     K = max(3, args.extra_steps)
     peak, peak_kind = measured_peak()
+    alu_peak = alu_peak_tflops(torch.cuda.get_device_properties(dev).multi_processor_count, args.sm_max_mhz)
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
     b0s = [model.to_grid(e.b0) for e in eps]
     # (1) the same R requests in one launch (E = R episodes on one map)
@@ -431,8 +434,8 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
     ndm = [p.read()[0]["nodes_per_level"] for p in armm.plans]
     nda = [sum(n[l] for n in ndm) / len(ndm) for l in range(wm.depth + 1)]
     rl, _ = plan_roofline(api, mm, Qm, bm[0], epm[0], "fused", N.QV_LEAF_FUSED, {},
-                          armm.plans[0] if armm.S > 1 else None, flush, 5, peak, peak_kind, job_plans_per_s=pps,
-                          nodes_avg=nda)
+                          armm.plans[0] if armm.S > 1 else None, flush, 5, peak, peak_kind, alu_peak,
+                          support_cells(epm[0].b0, wm.occ, wm.depth), job_plans_per_s=pps, nodes_avg=nda)
     mid.update({"plans_per_s": pps, "streams": armm.S, "trial_plans_per_s": armm.trial,
                 "updates_per_s": sum(sum(n[1:]) for n in ndm) * K / (msm / 1e3), "roofline": rl})
     out["mid_128"] = mid
@@ -458,10 +461,13 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
             nm, lv = it["name"].split(":", 1)[1], it["level"]
             t = statistics.mean(pr[i]["ms"] for pr in prof_runs for i in range(len(pr))
                                 if pr[i]["name"] == it["name"] and pr[i]["level"] == lv)
-            b = phase_bytes(nm, lv, nodes, Ncell, w.depth, "materialise")
-            gbps = b / (t * 1e-3) / 1e9 if t > 0 else None
-            phases[f"{nm}[{lv}]"] = {"ms": t, "bytes": b, "GBps": gbps,
-                                     "frac_of_measured_hbm": (gbps / peak) if gbps else None}
+            if nm in ("update", "leaf"):  # the dense leaf passes: every leaf written and read in full
+                b = phase_bytes(nm, lv, nodes, Ncell, w.depth, "materialise")
+                gbps = b / (t * 1e-3) / 1e9 if t > 0 else None
+                phases[f"{nm}[{lv}]"] = {"ms": t, "bytes": b, "GBps": gbps,
+                                         "frac_of_measured_hbm": (gbps / peak) if gbps else None}
+            else:
+                phases[f"{nm}[{lv}]"] = {"ms": t}
         sb = survey_bytes(nodes, Ncell, w.depth, "materialise")
         out["large_512_materialise"] = {"plans_per_s": K / (ms4 / 1e3), "ms_per_plan": ms4 / K,
                                         "nodes_per_level": nodes,
@@ -889,6 +895,74 @@ def survey_bytes(nodes, N, depth, leaf_mode):
     return tot
 
 
+def support_cells(b0, occ, depth):
+    """Cells of the support window of every level d = 0 .. depth + 1: the
+    bounding box of b0's nonzero cells dilated by d cells and clipped to the
+    grid -- the window k_plan restricts level d's sums to (the motion stencil
+    moves mass by one cell per level)."""
+    import numpy as np
+    occ = np.asarray(occ)
+    b = np.asarray(b0).reshape(occ.shape)
+    r, c = np.nonzero(b != 0)
+    if r.size == 0:
+        return [0] * (depth + 2)
+    H, W = occ.shape
+    out = []
+    for d in range(depth + 2):
+        rows = min(H, int(r.max()) + d + 1) - max(0, int(r.min()) - d)
+        cols = min(W, int(c.max()) + d + 1) - max(0, int(c.min()) - d)
+        out.append(rows * cols)
+    return out
+
+
+def window_bytes(nodes, cells, depth, leaf_mode):
+    """survey_bytes with each belief's N the cells of its level's support
+    window (cells[l] for a level-l belief): the same reads and writes, over
+    the cells where the belief can be nonzero."""
+    if depth == 0:
+        return 4 * cells[0]
+    tot = 0
+    for lv in range(depth):
+        if lv < depth - 1 or leaf_mode == "materialise":
+            tot += 2 * nodes[lv] * 4 * cells[lv] + nodes[lv + 1] * 4 * cells[lv + 1]
+        else:
+            tot += nodes[lv] * 4 * cells[lv]
+    if leaf_mode == "materialise":
+        tot += nodes[depth] * 4 * cells[depth]
+    return tot
+
+
+# FP32 operations (an FMA counts two) of the expand pass per cell of a
+# level-l node's task window (the window of level l + 1): forming the node's
+# belief from its parent (one action's stencil and the observation weight,
+# l > 0), the five actions' predicted masses (two shared slip sums and four
+# multiply-adds per move action), the reward and null-label sums (the reward
+# of the cell, five multiply-adds, five masks and five adds) and, at the
+# fused level, the 25 Q-weighted null sums.
+FLOPS_CHILD, FLOPS_STENCIL, FLOPS_SUMS, FLOPS_QSUMS = 7, 20, 21, 50
+FP32_LANES_PER_SM = 128
+NOMINAL_SM_MHZ = 2070.0
+
+
+def expand_flops(nodes, cells, depth, leaf_mode):
+    """FP32 operations of one plan's expand phases: level l's nodes over the
+    window of level l + 1 (cells[l + 1]).  The finalize phase's label
+    histograms (the beacons' sensing diamonds inside the window) are not
+    counted."""
+    tot = 0
+    for lv in range(depth):
+        f = FLOPS_STENCIL + FLOPS_SUMS + (FLOPS_CHILD if lv > 0 else 0)
+        if lv == depth - 1 and leaf_mode == "fused":
+            f += FLOPS_QSUMS
+        tot += nodes[lv] * cells[lv + 1] * f
+    return tot
+
+
+def alu_peak_tflops(sms, sm_mhz=NOMINAL_SM_MHZ):
+    """FP32 peak from the unit counts: SMs x 128 FP32 lanes x 2 (FMA) x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
 class PlainArm:
     """R single-plan launches per step (the plain one-tree-per-launch form):
     each request is its own plan and its own k_plan launch from a CUDA
@@ -968,9 +1042,12 @@ class BatchedArm:
     of E = R episodes (consecutive episode words, so the same trees as one
     plan per request) with its autotuned launch shape, from a CUDA graph."""
 
-    def __init__(self, api, models, Qs, b0s, episodes, depth, K, seed, leaf_mode, use_graph, flush, stream):
+    def __init__(self, api, models, Qs, b0s, episodes, depth, K, seed, leaf_mode, use_graph, flush, stream,
+                 tune=True):
         self.flush, self.stream = flush, stream
-        api.autotune(models, Qs, b0s, depth=depth, K=K, seed=seed, episode=episodes[0], leaf_mode=leaf_mode, reps=3)
+        if tune:
+            api.autotune(models, Qs, b0s, depth=depth, K=K, seed=seed, episode=episodes[0], leaf_mode=leaf_mode,
+                         reps=3)
         self.plan = api.Plan(models, Qs, b0s, depth=depth, K=K, seed=seed, episode=episodes[0], leaf_mode=leaf_mode)
         if use_graph:
             self.plan.capture_graph()
@@ -985,13 +1062,16 @@ class BatchedArm:
 
 
 def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_plan, flush, reps, peak, peak_kind,
-                  job_plans_per_s=None, nodes_avg=None):
-    """The dominant kernel (k_plan, the whole plan in one launch) against the
-    HBM roofline: algorithmic bytes of one plan (the unfused accounting of
-    survey_bytes) over the CUDA-event time of one launch alone on the whole
-    grid, L2 flushed before each launch; the same launch on the benchmark's
-    slice of the grid; the fused design's own minimum bytes beside it; the
-    per-phase device times of the full-grid launch."""
+                  alu_peak, cells, job_plans_per_s=None, nodes_avg=None):
+    """The dominant kernel (k_plan, the whole plan in one launch) against its
+    roofline, one plan alone on the whole grid, L2 flushed before each
+    launch: FP32 operations of the expand passes over the levels' support
+    windows (expand_flops) against the FP32 peak -- the windowed passes do
+    about 100 operations per 4 bytes of belief, so the kernel is bound by
+    arithmetic issue, not HBM; beside it the window bytes (window_bytes)
+    against measured HBM, and the paper's dense byte count over the same
+    time (a dense-equivalent rate, not a bandwidth).  Also the same launch on
+    the benchmark's slice of the grid and the per-phase device times."""
     full = api.Plan([model], [Q], [b0], depth=w.depth, K=w.K, seed=w.seed, episode=w.episode,
                     leaf_mode=leaf_mode, **knobs)
     for _ in range(3):
@@ -1008,34 +1088,43 @@ def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_
         if slice_plan is not None:
             flush.fill_(k & 255)
             ms_slice.append(slice_plan.profile()[0]["ms"])
-    nd = nodes if nodes_avg is None else nodes_avg
-    sbytes = survey_bytes(nd, Ncell, w.depth, leaf_mode_name)
-    fbytes = sum(phase_bytes(nm, lv, nd, Ncell, w.depth, leaf_mode_name) for nm, lv in plan_phases(w.depth, leaf_mode_name))
     avg = statistics.mean(ms_full)
-    achieved = sbytes / (avg * 1e-3) / 1e9
+    sec = avg * 1e-3
+    flops = expand_flops(nodes, cells, w.depth, leaf_mode_name)
+    wbytes = window_bytes(nodes, cells, w.depth, leaf_mode_name)
+    nd = nodes if nodes_avg is None else nodes_avg
+    dbytes = survey_bytes(nodes, Ncell, w.depth, leaf_mode_name)
+    achieved = flops / sec / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+           "traffic": None, "kernel": "k_plan (whole plan, one launch)", "kernel_share": 1.0,
+           "flops_per_launch": flops,
+           "flops_rule": "FP32 operations of the expand passes, level l's nodes over the window of level l+1: "
+                         f"{FLOPS_STENCIL + FLOPS_SUMS} per cell, +{FLOPS_CHILD} below the root, "
+                         f"+{FLOPS_QSUMS} at the fused level (label histograms not counted)",
+           "peak_source": "SMs x 128 FP32 lanes x 2 x the sampled maximum SM clock",
+           "nodes_per_level": nodes, "window_cells_per_level": cells,
+           "avg_launch_ms": avg, "launch": f"one plan alone on the whole grid ({full.grid} CTAs), L2 flushed",
+           "hbm_window": {"bytes_per_launch": wbytes, "achieved": wbytes / sec / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": wbytes / sec / 1e9 / peak,
+                          "rule": "8N + 4N C per V-node with materialised children, 4N per leaf-parent V-node, "
+                                  "N = the cells of the belief's support window",
+                          "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured"
+                          else "fallback 6800 GB/s"},
+           "dense_equivalent": {"bytes_per_launch": dbytes, "GBps": dbytes / sec / 1e9,
+                                "of_measured_hbm": dbytes / sec / 1e9 / peak,
+                                "note": "the dense per-plan count (N = every cell of the grid) over the launch "
+                                        "time; the kernel skips the cells outside the support windows, which "
+                                        "are exactly zero, so this is a rate, not a bandwidth"}}
     per_phase = {}
     for (nm, lv), v in ph_ms.items():
-        pb = phase_bytes(nm, lv, nodes, Ncell, w.depth, leaf_mode_name)
-        ms = statistics.mean(v)
-        per_phase[f"{nm}[{lv}]"] = {"ms": ms, "fused_design_bytes": pb,
-                                    "GBps": pb / (ms * 1e-3) / 1e9 if ms > 0 else None}
-    out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-           "traffic": None, "kernel": "k_plan (whole plan, one launch)", "kernel_share": 1.0,
-           "algorithmic_bytes_per_launch": sbytes,
-           "bytes_rule": "per plan: 8N + 4N C per V-node with materialised children, 4N per leaf-parent "
-                         "V-node (N cells x 4 B beliefs)",
-           "nodes_per_level": nd,
-           "avg_launch_ms": avg, "launch": f"one plan alone on the whole grid ({full.grid} CTAs), L2 flushed",
-           "fused_design_bytes_per_launch": fbytes, "fused_design_frac": fbytes / (avg * 1e-3) / 1e9 / peak,
-           "peak_source": "measured hbm_gbs, MEASURED_PEAKS.json" if peak_kind == "measured" else "fallback 6800 GB/s",
-           "phases": per_phase}
+        per_phase[f"{nm}[{lv}]"] = {"ms": statistics.mean(v)}
+    out["phases"] = per_phase
     if ms_slice:
         s_avg = statistics.mean(ms_slice)
-        out["slice"] = {"avg_launch_ms": s_avg, "grid_ctas": slice_plan.grid, "achieved": sbytes / (s_avg * 1e-3) / 1e9,
-                        "frac": sbytes / (s_avg * 1e-3) / 1e9 / peak}
+        out["slice"] = {"avg_launch_ms": s_avg, "grid_ctas": slice_plan.grid,
+                        "achieved": flops / (s_avg * 1e-3) / 1e12, "frac": flops / (s_avg * 1e-3) / 1e12 / alu_peak}
     if job_plans_per_s is not None:
-        out["job_achieved_GBps"] = sbytes * job_plans_per_s / 1e9
-        out["job_frac"] = sbytes * job_plans_per_s / 1e9 / peak
+        out["job_dense_equivalent_GBps"] = survey_bytes(nd, Ncell, w.depth, leaf_mode_name) * job_plans_per_s / 1e9
     return out, full
 
 
@@ -1124,7 +1213,7 @@ def main():
                          leaf_mode, knobs, use_graph, flush, stream, choices)
     if args.execution in ("auto", "batched"):
         batched = BatchedArm(api, [model] * R, [Qd] * R, b0s, [e.episode for e in eps], w.depth, w.K, w.seed,
-                             leaf_mode, use_graph, flush, stream)
+                             leaf_mode, use_graph, flush, stream, tune=not args.no_tune)
     exec_trial = {}
     if plain is not None and batched is not None:
         for name, a_ in (("plain", plain), ("batched", batched)):
@@ -1141,7 +1230,7 @@ def main():
         flush.fill_(k & 255)
         arm.step()
     torch.cuda.synchronize()
-    results = [p.read()[0] for p in arm.plans]
+    results = [g for p in arm.plans for g in p.read()]  # every episode of every plan
     nodes_per_plan = [r["nodes_per_level"] for r in results]
     updates_per_step = sum(sum(n[1:]) for n in nodes_per_plan)
 
@@ -1174,28 +1263,45 @@ def main():
     # the dominant kernel against its roofline: one plan alone on the whole
     # grid and on the step's slice, with the mean level sizes of the step
     peak, peak_kind = measured_peak()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if clocks and clocks.get("sm_max_mhz"):
+        args.sm_max_mhz = float(clocks["sm_max_mhz"])
+    alu_peak = alu_peak_tflops(sms, args.sm_max_mhz)
     nodes_avg = [sum(n[l] for n in nodes_per_plan) / len(nodes_per_plan) for l in range(w.depth + 1)]
+    cells_per_plan = [support_cells(e.b0, w.occ, w.depth) for e in eps]
     roofline, _ = plan_roofline(api, model, Qd, b0s[0], eps[0], args.leaf_mode, leaf_mode, knobs,
                                 arm.plans[0] if (arm is plain and arm.S > 1) else None, flush, args.profile_steps,
-                                peak, peak_kind, job_plans_per_s=plans_per_s / world_size, nodes_avg=nodes_avg)
+                                peak, peak_kind, alu_peak, cells_per_plan[0],
+                                job_plans_per_s=plans_per_s / world_size, nodes_avg=nodes_avg)
+    # the step's work, summed over its R plans (each with its own tree and windows)
+    step_flops = sum(expand_flops(n, c, w.depth, args.leaf_mode) for n, c in zip(nodes_per_plan, cells_per_plan))
+    step_wbytes = sum(window_bytes(n, c, w.depth, args.leaf_mode) for n, c in zip(nodes_per_plan, cells_per_plan))
+    step_dbytes = sum(survey_bytes(n, model.H * model.P, w.depth, args.leaf_mode) for n in nodes_per_plan)
     if arm is batched:
         # the dominant kernel as the timed region runs it: the batched
         # launch of the step's R plans, L2 flushed before each launch
-        ms_b = []
+        ms_b, ph_b = [], {}
         for k in range(max(1, args.profile_steps)):
             flush.fill_(k & 255)
-            ms_b.append(batched.plan.profile()[0]["ms"])
-        solo = {k: roofline[k] for k in ("achieved", "frac", "avg_launch_ms", "launch", "algorithmic_bytes_per_launch",
-                                          "fused_design_bytes_per_launch", "fused_design_frac")}
+            lst = batched.plan.profile()
+            ms_b.append(lst[0]["ms"])
+            for it in lst[1:]:
+                ph_b.setdefault(f'{it["name"].split(":", 1)[1]}[{it["level"]}]', []).append(it["ms"])
+        solo = {k: roofline[k] for k in ("achieved", "frac", "avg_launch_ms", "launch", "flops_per_launch",
+                                          "hbm_window", "dense_equivalent", "phases")}
         b_ms = statistics.mean(ms_b)
-        b_bytes = roofline["algorithmic_bytes_per_launch"] * R
-        roofline.update({"achieved": b_bytes / (b_ms * 1e-3) / 1e9, "frac": b_bytes / (b_ms * 1e-3) / 1e9 / peak,
-                         "avg_launch_ms": b_ms, "algorithmic_bytes_per_launch": b_bytes,
-                         "kernel": f"k_plan ({R} plans, one batched launch)",
-                         "launch": f"the step's batched launch ({batched.plan.grid} CTAs), L2 flushed",
-                         "fused_design_bytes_per_launch": roofline["fused_design_bytes_per_launch"] * R,
-                         "fused_design_frac": roofline["fused_design_bytes_per_launch"] * R / (b_ms * 1e-3) / 1e9 / peak,
-                         "solo": solo})
+        sec = b_ms * 1e-3
+        roofline.update({
+            "achieved": step_flops / sec / 1e12, "frac": step_flops / sec / 1e12 / alu_peak,
+            "avg_launch_ms": b_ms, "flops_per_launch": step_flops,
+            "kernel": f"k_plan ({R} plans, one batched launch)",
+            "launch": f"the step's batched launch ({batched.plan.grid} CTAs), L2 flushed",
+            "hbm_window": dict(roofline["hbm_window"], bytes_per_launch=step_wbytes, achieved=step_wbytes / sec / 1e9,
+                               frac=step_wbytes / sec / 1e9 / peak),
+            "dense_equivalent": dict(roofline["dense_equivalent"], bytes_per_launch=step_dbytes,
+                                     GBps=step_dbytes / sec / 1e9, of_measured_hbm=step_dbytes / sec / 1e9 / peak),
+            "phases": {k: {"ms": statistics.mean(v)} for k, v in ph_b.items()},
+            "solo": solo})
     roofline["traffic"] = recorded_traffic("k_plan", 0, args.workload)
 
     # end to end through the public API with host buffers: pinned b0 -> device,

@@ -108,6 +108,12 @@ struct PlanDev {
     // kWinBig - col, col + 1 over its nonzero free cells (0 = none), found by
     // the root's expand pass and cleared at the end of every run
     unsigned *win;
+    // [(d+1)][E][4] per stored level: a box holding every value an earlier
+    // run left in the level's belief slots, rows [w0 - 1, w1) x float4
+    // groups [w2, w3); w0 = 0: the slots are zero (the stored beliefs are
+    // zeroed with the counters at creation and after a failed run)
+    int *dirty;
+    unsigned *work;    // [2 (d+1)] items taken so far of expand(l) and finalize(l) (cleared at the end of a run)
     int *leaf_split;   // chunks per group of leaves in the leaf phase
     unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
     // per node (gid over every level)

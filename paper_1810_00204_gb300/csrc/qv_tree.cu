@@ -21,7 +21,7 @@ struct Layout {
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
-        off_status, off_boundary, off_bar, off_win, off_stamps, off_result, off_beliefs;
+        off_status, off_boundary, off_bar, off_win, off_dirty, off_work, off_stamps, off_result, off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0, cmax = 0;
     long long n_xrec = 0, n_frec = 0;
@@ -317,6 +317,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_leaf_cnt = take(sizeof(unsigned) * static_cast<size_t>(L.n_part));
     L.off_bar = take(sizeof(qv::GridBar));
     L.off_win = take(sizeof(unsigned) * 4 * E);
+    L.off_dirty = take(sizeof(int) * 4 * E * D1);
+    L.off_work = take(sizeof(unsigned) * 2 * D1);
     L.off_beliefs = take(sizeof(float) * std::max<long long>(L.n_belief, 4));
     L.total = align_up(o, 256);
     return QV_OK;
@@ -459,6 +461,8 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.boundary = at<unsigned long long>(ws, L.off_boundary);
     d.bar = at<qv::GridBar>(ws, L.off_bar);
     d.win = at<unsigned>(ws, L.off_win);
+    d.dirty = at<int>(ws, L.off_dirty);
+    d.work = at<unsigned>(ws, L.off_work);
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
@@ -469,7 +473,11 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
                         : 0ull;
     d.ep0 = L.eps[0];
     pl->reset_off = L.off_status;
-    pl->reset_bytes = L.off_beliefs - L.off_status;
+    // the stored beliefs too: the kernel writes zeros only where an earlier
+    // run may have left values (PlanDev::dirty), so the region starts zeroed
+    // and is zeroed again after a failed run
+    pl->reset_bytes = L.off_beliefs + sizeof(float) * static_cast<size_t>(std::max<long long>(L.n_belief, 4)) -
+                      L.off_status;
     pl->read_off = L.off_count;
     pl->read_bytes = L.off_boundary + sizeof(unsigned long long) - L.off_count;
     // static state: descriptors, the root of every episode, level-0 work lists

@@ -92,7 +92,7 @@ struct SmemLayout {
         s.u_sa = take(sizeof(float) * 5 * K);
         s.u_se = take(sizeof(float) * 5 * K);
         s.scan = take(sizeof(int) * (kWarps + 4));
-        s.flags = take(sizeof(int) * 8);
+        s.flags = take(sizeof(int) * 12);
         s.acc = take(sizeof(float) * kTot * cmax);   // per-child totals of a work item
         s.c_pa = take(sizeof(int) * cmax);           // per child: action, observation, alpha / P, eta / P
         s.c_z = take(sizeof(int) * cmax);
@@ -138,6 +138,48 @@ __device__ __forceinline__ int find_episode(const int *wb, int E, int w) {
     return lo;
 }
 
+// The same search by one warp, 32 probes per step (log32 of n dependent
+// loads instead of log2 of n): last j in [0, n) with wb[j] <= w, for a
+// nondecreasing wb with wb[0] <= w.
+__device__ __forceinline__ int warp_find(const int *wb, int n, int w) {
+    const int lane = threadIdx.x & 31;
+    int lo = 0, hi = n - 1;
+    while (hi > lo) {
+        const long long span = hi - lo;
+        const int base = lo;
+        auto probe = [&](int i) { return base + static_cast<int>((span * (i + 1) + 31) / 32); };
+        const unsigned bal = __ballot_sync(0xffffffffu, __ldcg(wb + probe(lane)) <= w);
+        const int m = __popc(bal);
+        if (m == 0) {
+            hi = probe(0) - 1;
+        } else {
+            if (m < 32) hi = probe(m) - 1;
+            lo = probe(m - 1);
+        }
+    }
+    return lo;
+}
+// warp_find by warp 0 for the whole CTA (one CTA barrier); `slot` is a
+// shared word not read again before the CTA's next barrier.
+__device__ __forceinline__ int block_find(const int *wb, int n, int w, int *slot) {
+    if (threadIdx.x < 32) {
+        const int r = warp_find(wb, n, w);
+        if (threadIdx.x == 0) *slot = r;
+    }
+    __syncthreads();
+    return *slot;
+}
+
+// Dynamic work distribution: the CTA's next item of a phase, taken from
+// the phase's counter (one atomic per item; every item writes its own
+// records, so the results do not depend on which CTA takes which item).
+__device__ __forceinline__ int next_item(unsigned *ctr, int *slot) {
+    __syncthreads();  // every thread has read the previous item's index
+    if (threadIdx.x == 0) *slot = static_cast<int>(atomicAdd(ctr, 1u));
+    __syncthreads();
+    return *slot;
+}
+
 __device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpDev &ep, int l, int local) {
     if (l == 0) return ep.b0;
     return pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N;
@@ -147,8 +189,8 @@ __device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpD
 // The motion stencil (Eq. 3 numerator, Eq. 10) moves mass by at most one
 // cell and the observation weights (Eq. 3) only rescale it, so a node d
 // levels below the root is zero outside the bounding box of b0's nonzero
-// free cells dilated by d cells.  The expand and finalize phases restrict
-// their sums to that window; every cell outside it contributes exactly zero.
+// cells dilated by d cells.  The expand and finalize phases restrict their
+// sums to that window; every cell outside it contributes exactly zero.
 struct Win {
     int r0, r1, c0, c1;  // rows [r0, r1), columns [c0, c1); empty when r1 <= r0
 };
@@ -174,7 +216,6 @@ __device__ __forceinline__ Win support_window(const PlanDev &pl, int e, int H, i
 // [sc0, sc0 + sw) (the task columns with the two-cell reach of a child's
 // stencil, rounded out to multiples of 8 so that every staged row starts and
 // ends on a 16-byte boundary), `rows` task rows per band and `nb` bands.
-// The root's pass (l = 0) covers the whole grid, since it finds the window.
 // rows * sw never exceeds band_rows * P, so a windowed band fits the buffers
 // sized for a full-width one.
 struct BandGeo {
@@ -182,17 +223,6 @@ struct BandGeo {
 };
 __device__ __forceinline__ BandGeo band_geo(const PlanDev &pl, int e, int H, int W, int P, int band_rows, int l) {
     BandGeo g;
-    if (l == 0) {
-        g.r0 = 0;
-        g.r1 = H;
-        g.g0 = 0;
-        g.g1 = P >> 2;
-        g.sc0 = 0;
-        g.sw = P;
-        g.rows = band_rows;
-        g.nb = (H + band_rows - 1) / band_rows;
-        return g;
-    }
     const Win t = support_window(pl, e, H, W, l + 1);
     g.r0 = t.r0;
     g.r1 = t.r1;
@@ -385,13 +415,14 @@ __device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int 
 // [r0-2, r1+2) (zero outside the grid) and cell words of the same rows,
 // columns [sc0, sc0 + sw), into rows of sw values; with q, rows [r0, r1) of
 // the five Q planes (plane stride (r1-r0)*sw).  A full-width window is
-// contiguous and takes stage_band's copies; a narrower one takes one bulk
-// copy per row and array, issued by the lanes of warp 0.
-__device__ bool stage_window(const EpReg &ep, const float *b, int r0, int r1, int sc0, int sw, float *bbuf,
-                             uint16_t *cw, float *q, uint64_t *bar, unsigned &phase, unsigned *status) {
+// contiguous: one bulk copy per array (five for Q); a narrower one takes one
+// bulk copy per row and array.  The lanes of warp 0 issue the copies;
+// stage_wait then waits for them (bounded), so that other work can run in
+// between.  The caller has passed a CTA barrier since the buffers' last
+// readers.
+__device__ void stage_issue(const EpReg &ep, const float *b, int r0, int r1, int sc0, int sw, float *bbuf,
+                            uint16_t *cw, float *q, uint64_t *bar) {
     const int P = ep.P;
-    if (sw == P) return stage_band(ep, b, r0, r1, 2, bbuf, cw, q, bar, phase, status, 2);
-    __syncthreads();  // previous readers of the buffers are done
     for (int r = r0 - 2; r < r0; ++r)
         if (r < 0)
             for (int i = threadIdx.x; i < sw; i += blockDim.x) bbuf[(r - (r0 - 2)) * sw + i] = 0.0f;
@@ -403,25 +434,41 @@ __device__ bool stage_window(const EpReg &ep, const float *b, int r0, int r1, in
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
         const int lo = max(0, r0 - 2), hi = min(ep.H, r1 + 2), R = r1 - r0;
-        const int nbr = hi - lo, nq = q ? 5 * R : 0;
+        const int nbr = hi - lo;
         const unsigned rb = static_cast<unsigned>(sw * sizeof(float)), cb = static_cast<unsigned>(sw * sizeof(uint16_t));
-        if (lane == 0) mbar_arrive_expect_tx(bar, static_cast<unsigned>(nbr) * (rb + cb) + static_cast<unsigned>(nq) * rb);
+        if (lane == 0)
+            mbar_arrive_expect_tx(bar, static_cast<unsigned>(nbr) * (rb + cb) + (q ? 5u * R * rb : 0u));
         __syncwarp();
         fence_proxy_async_global();
-        for (int i = lane; i < 2 * nbr + nq; i += 32) {
-            if (i < nbr) {
-                const int r = lo + i;
-                bulk_copy_g2s(bbuf + (r - (r0 - 2)) * sw, b + static_cast<size_t>(r) * P + sc0, rb, bar);
-            } else if (i < 2 * nbr) {
-                const int r = lo + i - nbr;
-                bulk_copy_g2s(cw + (r - (r0 - 2)) * sw, ep.cell + static_cast<size_t>(r) * P + sc0, cb, bar);
-            } else {
-                const int a = (i - 2 * nbr) / R, y = (i - 2 * nbr) - a * R;
-                bulk_copy_g2s(q + (a * R + y) * sw,
-                              ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0 + y) * P + sc0, rb, bar);
+        if (sw == P) {
+            if (lane == 0) bulk_copy_g2s(bbuf + (lo - (r0 - 2)) * P, b + static_cast<size_t>(lo) * P, nbr * rb, bar);
+            if (lane == 1)
+                bulk_copy_g2s(cw + (lo - (r0 - 2)) * P, ep.cell + static_cast<size_t>(lo) * P, nbr * cb, bar);
+            if (q && lane >= 2 && lane < 7) {
+                const int a = lane - 2;
+                bulk_copy_g2s(q + a * R * P, ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0) * P,
+                              R * rb, bar);
+            }
+        } else {
+            const int nq = q ? 5 * R : 0;
+            for (int i = lane; i < 2 * nbr + nq; i += 32) {
+                if (i < nbr) {
+                    const int r = lo + i;
+                    bulk_copy_g2s(bbuf + (r - (r0 - 2)) * sw, b + static_cast<size_t>(r) * P + sc0, rb, bar);
+                } else if (i < 2 * nbr) {
+                    const int r = lo + i - nbr;
+                    bulk_copy_g2s(cw + (r - (r0 - 2)) * sw, ep.cell + static_cast<size_t>(r) * P + sc0, cb, bar);
+                } else {
+                    const int a = (i - 2 * nbr) / R, y = (i - 2 * nbr) - a * R;
+                    bulk_copy_g2s(q + (a * R + y) * sw,
+                                  ep.Q + static_cast<size_t>(a) * ep.N + static_cast<size_t>(r0 + y) * P + sc0, rb,
+                                  bar);
+                }
             }
         }
     }
+}
+__device__ bool stage_wait(uint64_t *bar, unsigned &phase, unsigned *status) {
     const bool ok = mbar_wait_bounded(bar, phase);
     const int failed = __syncthreads_or(ok ? 0 : 1);
     if (failed) {
@@ -512,27 +559,45 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
     const float eta = ep.eta, acc = ep.acc;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 5 * nz; i += blockDim.x) S.cnt[i] = 0;
-    if (fused)
-        for (int t = threadIdx.x; t < 25; t += blockDim.x) {
+    if (fused) {
+        // T[a][a'] = the Q-weighted masses over every label: eight threads
+        // per entry, each over every eighth beacon
+        const int t = threadIdx.x >> 3, sub = threadIdx.x & 7;
+        float s = 0.0f;
+        if (t < 25) {
             const int a = t / 5, ap = t % 5;
-            float s = S.tot[10 + t];
-            for (int z = 0; z < B; ++z) s += S.histq[(a * Bm + z) * 5 + ap];
-            S.T[t] = s;
+            for (int z = sub; z < B; z += 8) s += S.histq[(a * Bm + z) * 5 + ap];
         }
-    for (int a = wid; a < 5 && lane == 0; a += kWarps) {
-        // the cumulative sum runs in ascending z, in FP32, as the sampler's
-        // inverse CDF is defined
-        float Ssum = S.tot[a];
-        for (int z = 0; z < B; ++z) Ssum += S.hist[a * Bm + z];
-        float run = 0.0f;
-        for (int z = 0; z < nz; ++z) {
-            const float M = z < B ? S.hist[a * Bm + z] : S.tot[a];
-            const float p = fmaf(acc - eta, M, eta * Ssum);
-            S.P[a * nz + z] = p;
-            run = run + p;
-            S.C[a * nz + z] = run;
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        if (t < 25 && sub == 0) S.T[t] = s + S.tot[10 + t];
+    }
+    for (int a = wid; a < 5; a += kWarps) {
+        // one warp per action: P(z | b, a) for every z, and its cumulative
+        // sum in ascending z (FP32, a warp scan per 32 values)
+        float m = 0.0f;
+        for (int z = lane; z < B; z += 32) m += S.hist[a * Bm + z];
+        const float Ssum = warp_sum(m) + S.tot[a];
+        float carry = 0.0f;
+        for (int zc = 0; zc < nz; zc += 32) {
+            const int z = zc + lane;
+            const float M = z < B ? S.hist[a * Bm + z] : (z == B ? S.tot[a] : 0.0f);
+            const float p = z < nz ? fmaf(acc - eta, M, eta * Ssum) : 0.0f;
+            float x = p;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            x += carry;
+            if (z < nz) {
+                S.P[a * nz + z] = p;
+                S.C[a * nz + z] = x;
+            }
+            carry = __shfl_sync(0xffffffffu, x, 31);
         }
-        pl.R[iid * 5 + a] = S.tot[5 + a] - 100.0f * bgoal;
+        if (lane == 0) pl.R[iid * 5 + a] = S.tot[5 + a] - 100.0f * bgoal;
     }
     __syncthreads();
     const uint32_t epw = pl.episode_word ? __ldcg(pl.episode_word) + (ep.episode - pl.episode0) : ep.episode;
@@ -589,6 +654,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
                     }
                     pl.slot_val[sb + pos] = best;
                     pl.slot_arg[sb + pos] = barg;
+                    S.C[a * nz + z] = best;  // the CDF is no longer read: it holds the leaf values now
                 }
             }
             psum += warp_sum(c > 0 ? p : 0.0f);
@@ -605,7 +671,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
                 const float wgt = pl.weight_mode == QV_WEIGHT_MARGINAL ? S.P[a * nz + z] / psum
                                                                         : static_cast<float>(c) / K;
                 pl.slot_w[sb + pos] = wgt;
-                if (fused) sv += wgt * pl.slot_val[sb + pos];
+                if (fused) sv += wgt * S.C[a * nz + z];
             }
             base += __popc(bal);
         }
@@ -814,6 +880,58 @@ __device__ void node_done(const PlanDev &pl, int l, int e, const EpDev &ep, Smem
     __syncthreads();
 }
 
+// ---------------------------------------------------------------- window phase
+// The support window of every episode's b0: the bounding box of its nonzero
+// cells, one streaming read of b0 before the root's pass.  Each episode's
+// float4 groups are split over gridDim / E CTAs (one CTA per episode when
+// E >= gridDim); a CTA reduces its share and merges it with four atomicMax.
+// (A float4 never straddles two rows: the pitch is a multiple of 8.)
+__device__ void phase_window(const PlanDev &pl, Smem &S) {
+    const int E = pl.E, G = gridDim.x;
+    const int per = max(1, G / E);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *red = reinterpret_cast<unsigned *>(S.red);
+    for (int v = blockIdx.x; v < E * per; v += G) {
+        const int e = v / per, part = v - e * per;
+        const EpDev *ep = pl.eps + e;
+        const int H = __ldg(&ep->H), P = __ldg(&ep->P);
+        const float4 *b4 = reinterpret_cast<const float4 *>(ep->b0);
+        const long long n4 = static_cast<long long>(H) * P / 4;
+        const long long i0 = n4 * part / per, i1 = n4 * (part + 1) / per;
+        unsigned wr0 = 0u, wr1 = 0u, wc0 = 0u, wc1 = 0u;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const float4 x = __ldcs(b4 + i);
+            const float xs[4] = {x.x, x.y, x.z, x.w};
+            const int row = static_cast<int>((4 * i) / P), col = static_cast<int>(4 * i - static_cast<long long>(row) * P);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                if (xs[jj] != 0.0f) {
+                    wr0 = max(wr0, static_cast<unsigned>(kWinBig - row));
+                    wr1 = max(wr1, static_cast<unsigned>(row + 1));
+                    wc0 = max(wc0, static_cast<unsigned>(kWinBig - (col + jj)));
+                    wc1 = max(wc1, static_cast<unsigned>(col + jj + 1));
+                }
+        }
+        wr0 = __reduce_max_sync(0xffffffffu, wr0);
+        wr1 = __reduce_max_sync(0xffffffffu, wr1);
+        wc0 = __reduce_max_sync(0xffffffffu, wc0);
+        wc1 = __reduce_max_sync(0xffffffffu, wc1);
+        __syncthreads();  // the previous episode's reader of red is done
+        if (lane == 0) {
+            red[wid * 4] = wr0;
+            red[wid * 4 + 1] = wr1;
+            red[wid * 4 + 2] = wc0;
+            red[wid * 4 + 3] = wc1;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            unsigned m = 0u;
+            for (int k = 0; k < kWarps; ++k) m = max(m, red[k * 4 + threadIdx.x]);
+            if (m != 0u) atomicMax(pl.win + 4 * e + threadIdx.x, m);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- expand phase
 // A node's belief at four cells (grid row r, columns col..col+3) from its
 // parent's staged band: Phi(parent, a, z) of Eq. 3, zero outside the grid.
@@ -926,21 +1044,30 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
     const int KS = pl.kslots;
     constexpr int NV = FUSED ? 35 : 10;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    unsigned *ctr = pl.work + 2 * l;
+    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
 #ifdef QV_TRACE
         unsigned long long tr[kTraceWords] = {};
 #endif
         QV_TRACE_MARK(tr, 2);
-        const int j = find_episode(goff, G, w);
+        const int j = block_find(goff, G, w, S.flags + 6);
         int e = j, lp = 0;
         if (l > 0) {
-            e = find_episode(np, E, j);
+            e = block_find(np, E, j, S.flags + 7);
             lp = j - __ldcg(np + e);
         }
+        const int g0 = __ldcg(goff + j);
+        const int item = w - g0;
+        // a group has no more items than its window has bands (at least one,
+        // which writes the zero totals of an empty window); surplus items
+        // of the list do nothing
+        const EpDev *epg = pl.eps + e;
+        const BandGeo geo =
+            band_geo(pl, e, __ldg(&epg->H), __ldg(&epg->W), __ldg(&epg->P), __ldg(&epg->band_rows), l);
+        const int items = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
+        if (item >= items) continue;
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
-        const int g0 = __ldcg(goff + j);
-        const int items = __ldcg(goff + j + 1) - g0, item = w - g0;
         const int rec = __ldcg(grec + j);
         const int B = ep.B;
         int c0 = 0, nc = 1;
@@ -953,7 +1080,15 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
             nc = min(max(0, c1 - c0), pl.cmax);
             src = node_belief(pl, ep, l - 1, lp);
         }
-        __syncthreads();  // the previous item's readers of the child table and totals are done
+        __syncthreads();  // the previous item's readers of the child table, totals and band buffers are done
+        const int band0 = static_cast<int>((static_cast<long long>(item) * geo.nb) / items);
+        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * geo.nb) / items);
+        const EpReg er = ep_reg(ep);
+        // the first band's copies fly while the child table is read
+        if (band0 < band1) {
+            const int r0 = geo.r0 + band0 * geo.rows, r1 = min(geo.r1, r0 + geo.rows);
+            stage_issue(er, src, r0, r1, geo.sc0, geo.sw, S.sp, S.cw, FUSED ? S.q : nullptr, mbar);
+        }
         if (l > 0) {
             for (int r = threadIdx.x; r < nc; r += blockDim.x) {
                 const int gid = ep.node_base[l] + c0 + r;
@@ -980,11 +1115,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) S.acc[i] = 0.0f;
         __syncthreads();
         QV_TRACE_MARK(tr, 3);
-        const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
-        const int band0 = static_cast<int>((static_cast<long long>(item) * geo.nb) / items);
-        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * geo.nb) / items);
-        const EpReg er = ep_reg(ep);
-        const int P = er.P, P4 = P >> 2, goal = er.goal, SW = geo.sw;
+        const int P = er.P, goal = er.goal, SW = geo.sw;
         const int NS = (geo.g1 - geo.g0 + 31) >> 5;  // column strips of 32 float4 groups
         const float slip = er.slip;
         const float *cost = er.cost;
@@ -992,40 +1123,18 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         for (int band = band0; band < band1; ++band) {
             const int r0 = geo.r0 + band * geo.rows, r1 = min(geo.r1, r0 + geo.rows), R = r1 - r0;
             const int qstride = R * SW;
-            if (!stage_window(er, src, r0, r1, geo.sc0, SW, S.sp, S.cw, FUSED ? S.q : nullptr, mbar, mphase,
-                              pl.status))
-                return false;
+            if (band > band0) {
+                __syncthreads();  // the previous band's readers are done
+                stage_issue(er, src, r0, r1, geo.sc0, SW, S.sp, S.cw, FUSED ? S.q : nullptr, mbar);
+            }
+            if (!stage_wait(mbar, mphase, pl.status)) return false;
             // occupied cells of the staged parent (or root) carry no belief:
             // zero them once, so that rows away from the goal can move every
-            // neighbour's mass without the per-cell inflow test.  The root's
-            // pass also finds the support window of b0 from its own rows.
+            // neighbour's mass without the per-cell inflow test
             {
                 const int lo = max(0, r0 - 2) - (r0 - 2), hi = min(er.H, r1 + 2) - (r0 - 2);
-                unsigned wr0 = 0u, wr1 = 0u, wc0 = 0u, wc1 = 0u;
-                for (int i = lo * SW + threadIdx.x; i < hi * SW; i += blockDim.x) {
-                    if (!QV_CELL_FREE(static_cast<unsigned>(S.cw[i]))) {
-                        S.sp[i] = 0.0f;
-                    } else if (l == 0 && S.sp[i] != 0.0f && i >= 2 * SW && i < (R + 2) * SW) {
-                        const int rr = r0 - 2 + i / SW, cc = geo.sc0 + i % SW;
-                        wr0 = max(wr0, static_cast<unsigned>(kWinBig - rr));
-                        wr1 = max(wr1, static_cast<unsigned>(rr + 1));
-                        wc0 = max(wc0, static_cast<unsigned>(kWinBig - cc));
-                        wc1 = max(wc1, static_cast<unsigned>(cc + 1));
-                    }
-                }
-                if (l == 0) {
-                    wr0 = __reduce_max_sync(0xffffffffu, wr0);
-                    wr1 = __reduce_max_sync(0xffffffffu, wr1);
-                    wc0 = __reduce_max_sync(0xffffffffu, wc0);
-                    wc1 = __reduce_max_sync(0xffffffffu, wc1);
-                    if (lane == 0 && wr1 != 0u) {
-                        unsigned *wv = pl.win + 4 * e;
-                        atomicMax(wv, wr0);
-                        atomicMax(wv + 1, wr1);
-                        atomicMax(wv + 2, wc0);
-                        atomicMax(wv + 3, wc1);
-                    }
-                }
+                for (int i = lo * SW + threadIdx.x; i < hi * SW; i += blockDim.x)
+                    if (!QV_CELL_FREE(static_cast<unsigned>(S.cw[i]))) S.sp[i] = 0.0f;
                 __syncthreads();
             }
             if (band == band0) QV_TRACE_MARK(tr, 4);
@@ -1115,18 +1224,27 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                     return child1(er, S.sp + o, S.cw + o, SW, rr, c, pa, pz, sa, se, S.lut);
                 };
                 float4 up = row4(ya - 1), md = row4(ya);
+                // the strip's two edge cells (west of lane 0, east of lane 31),
+                // formed for 16 rows at a time by the whole warp: lane k holds
+                // row y0 + k / 2, the west edge for even k, the east for odd
+                const int scol = (geo.g0 + s * 32) << 2;
+                const bool east_in = geo.g0 + s * 32 + 31 < geo.g1;
+                float edge = 0.0f;
                 for (int y = ya; y < yb; ++y) {
+                    const int k = (y - ya) & 15;
+                    if (k == 0) {
+                        const int ye = y + (lane >> 1);
+                        const int c = (lane & 1) ? scol + 128 : scol - 1;
+                        edge = (ye < yb && c >= 0 && c < P && ((lane & 1) == 0 || east_in)) ? row1(ye, c) : 0.0f;
+                    }
                     const float4 dn = row4(y + 1);
-                    // the row's west and east neighbours from the adjacent lanes;
-                    // the strip's two edges are formed directly, in one pass
+                    // the row's west and east neighbours from the adjacent lanes
                     float hw = __shfl_up_sync(0xffffffffu, md.w, 1);
                     float he = __shfl_down_sync(0xffffffffu, md.x, 1);
-                    if (lane == 0 || lane == 31) {
-                        const int c = lane == 0 ? col - 1 : col + 4;
-                        const float v = (act && c >= 0 && c < P) ? row1(y, c) : 0.0f;
-                        if (lane == 0) hw = v;
-                        else he = v;
-                    }
+                    const float e_w = __shfl_sync(0xffffffffu, edge, 2 * k);
+                    const float e_e = __shfl_sync(0xffffffffu, edge, 2 * k + 1);
+                    if (lane == 0) hw = e_w;
+                    if (lane == 31) he = e_e;
                     if (act) {
                         const int yg = (r0 + y) * P + col;
                         if (dst) *reinterpret_cast<float4 *>(dst + yg) = md;
@@ -1140,7 +1258,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                             // cells and no cell within a row is the goal, so
                             // every neighbour moves its mass in; occupied cells'
                             // outputs are masked by their reward and null weights
-                            float vn[4][5];
+                            const float *qrow = S.q + y * SW + sc;
 #pragma unroll
                             for (int jj = 0; jj < 4; ++jj) {
                                 const unsigned cw = cws[jj];
@@ -1158,23 +1276,22 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
                                 const float cst = cost ? __ldg(cost + yg + jj) : 0.0f;
                                 const float rw = fr ? -1.0f - cst : 0.0f;
                                 const float nf = (fr && static_cast<int>(QV_CELL_LABEL(cw)) >= B) ? 1.0f : 0.0f;
+                                float vn[5];
 #pragma unroll
                                 for (int a = 0; a < 5; ++a) {
                                     acc_r[a] = fmaf(out[a], rw, acc_r[a]);
-                                    vn[jj][a] = out[a] * nf;
-                                    acc_null[a] += vn[jj][a];
+                                    vn[a] = out[a] * nf;
+                                    acc_null[a] += vn[a];
                                 }
-                            }
-                            if constexpr (FUSED) {
-                                // the Q-weighted null masses, one 16-byte Q load per action
+                                if constexpr (FUSED) {
+                                    // the cell's Q-weighted null masses (one cell at a
+                                    // time, so that few values stay live)
 #pragma unroll
-                                for (int ap = 0; ap < 5; ++ap) {
-                                    const float4 q4 = *reinterpret_cast<const float4 *>(S.q + ap * qstride + y * SW + sc);
+                                    for (int ap = 0; ap < 5; ++ap) {
+                                        const float q = qrow[ap * qstride + jj];
 #pragma unroll
-                                    for (int a = 0; a < 5; ++a)
-                                        acc_q[a * 5 + ap] =
-                                            fmaf(vn[3][a], q4.w,
-                                                 fmaf(vn[2][a], q4.z, fmaf(vn[1][a], q4.y, fmaf(vn[0][a], q4.x, acc_q[a * 5 + ap]))));
+                                        for (int a = 0; a < 5; ++a) acc_q[a * 5 + ap] = fmaf(vn[a], q, acc_q[a * 5 + ap]);
+                                    }
                                 }
                             }
                         } else {
@@ -1239,18 +1356,28 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
             }
         }
         if (dst0) {
-            // the stored children are zero outside the task window: this
-            // item's share of the grid's rows, one warp per (child, row)
-            const int zr0 = static_cast<int>((static_cast<long long>(item) * er.H) / items);
-            const int zr1 = static_cast<int>((static_cast<long long>(item + 1) * er.H) / items);
-            const int nr = zr1 - zr0;
-            for (int t2 = wid; t2 < nc * nr; t2 += kWarps) {
-                const int r = t2 / nr, row = zr0 + (t2 - r * nr);
-                float4 *d4 = reinterpret_cast<float4 *>(dst0 + static_cast<long long>(c0 + r) * er.N +
-                                                        static_cast<long long>(row) * P);
-                const bool in = row >= geo.r0 && row < geo.r1;
-                for (int g = lane; g < P4; g += 32)
-                    if (!in || g < geo.g0 || g >= geo.g1) d4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+            // the stored children are zero outside the task window: zeros go
+            // where an earlier run may have left values (the level's dirty
+            // box, nothing when it lies inside the window); this item's share
+            // of the box's rows, one warp per (child, row)
+            const int *dw = pl.dirty + 4 * (l * E + e);
+            const int w0 = __ldcg(dw);
+            if (w0 != 0) {
+                const int dr0 = w0 - 1, dr1 = __ldcg(dw + 1), dg0 = __ldcg(dw + 2), dg1 = __ldcg(dw + 3);
+                const bool inside = geo.nb > 0 && dr0 >= geo.r0 && dr1 <= geo.r1 && dg0 >= geo.g0 && dg1 <= geo.g1;
+                if (!inside) {
+                    const int zr0 = dr0 + static_cast<int>((static_cast<long long>(item) * (dr1 - dr0)) / items);
+                    const int zr1 = dr0 + static_cast<int>((static_cast<long long>(item + 1) * (dr1 - dr0)) / items);
+                    const int nr = zr1 - zr0;
+                    for (int t2 = wid; t2 < nc * nr; t2 += kWarps) {
+                        const int r = t2 / nr, row = zr0 + (t2 - r * nr);
+                        float4 *d4 = reinterpret_cast<float4 *>(dst0 + static_cast<long long>(c0 + r) * er.N +
+                                                                static_cast<long long>(row) * P);
+                        const bool in = row >= geo.r0 && row < geo.r1;
+                        for (int g = dg0 + lane; g < dg1; g += 32)
+                            if (!in || g < geo.g0 || g >= geo.g1) d4[g] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -1444,12 +1571,13 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
     float *tp = S.tile + wid * kTileFloats;
     float *tc = tp + kTileP;
     uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    unsigned *ctr = pl.work + 2 * l + 1;
+    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
 #ifdef QV_TRACE
         unsigned long long tr[kTraceWords] = {};
 #endif
         QV_TRACE_MARK(tr, 2);
-        const int e = find_episode(wb, E, w);
+        const int e = block_find(wb, E, w, S.flags + 6);
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
         const int rel = w - __ldcg(wb + e);
@@ -1476,6 +1604,13 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
         const int k0 = min(B, chunk * bpc), k1 = min(B, k0 + bpc);
         __syncthreads();  // the previous item's readers of the histograms are done
         for (int k = k0 + wid; k < k1; k += kWarps) {
+            const int br = S.bco[2 * k], bc = S.bco[2 * k + 1], R = ep.range;
+            if (br + R < win.r0 || br - R >= win.r1 || bc + R < win.c0 || bc - R >= win.c1) {
+                // the beacon's diamond lies outside the window: its masses are zero
+                if (lane < 5) S.hist[lane * Bm + k] = 0.0f;
+                else if (FUSED && lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] = 0.0f;
+                continue;
+            }
             float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             float lq[FUSED ? 25 : 1];
 #pragma unroll
@@ -1565,7 +1700,8 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             if (rec < 0) {
                 if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
             } else {
-                const int nit = __ldcg(goff + jg + 1) - __ldcg(goff + jg);
+                const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
+                const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
                 const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
                 if (g < kGroups) {
                     // items g, g + 7, ... in order, eight loads in flight at a time
@@ -2007,6 +2143,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     // that the search can stop after any level (anytime, Sec. IV-C)
     const bool dl = pl.deadline_ns != 0ull;
     int Deff = D;
+    if (D > 0) {
+        phase_window(pl, S);
+        if (!grid_sync(pl)) return;
+    }
     for (int l = 0; l < D; ++l) {
         const bool last = l == D - 1;
         const bool fused = (last && !mat) || dl;
@@ -2042,10 +2182,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         if (!grid_sync(pl)) return;
         stamp(pl, slot++);
     }
-    // every reader of the support windows is past the last grid barrier: the
-    // next run's root pass finds them afresh
-    if (blockIdx.x == 0)
+    // every reader of the support windows is past the last grid barrier:
+    // each stored level's dirty box takes in the window this run wrote, then
+    // the windows are cleared for the next run's root pass to find afresh
+    if (blockIdx.x == 0) {
+        for (int i = threadIdx.x; i < pl.E * D; i += blockDim.x) {
+            const int e = i / D, l = i - e * D;
+            if (l == 0 || l >= Deff || !(l < D - 1 || mat)) continue;
+            const EpDev *ep = pl.eps + e;
+            const BandGeo geo = band_geo(pl, e, __ldg(&ep->H), __ldg(&ep->W), __ldg(&ep->P), __ldg(&ep->band_rows), l);
+            if (geo.nb == 0) continue;
+            int *dw = pl.dirty + 4 * (l * pl.E + e);
+            int r0 = geo.r0, r1 = geo.r1, g0 = geo.g0, g1 = geo.g1;
+            if (dw[0] != 0) {
+                r0 = min(r0, dw[0] - 1);
+                r1 = max(r1, dw[1]);
+                g0 = min(g0, dw[2]);
+                g1 = max(g1, dw[3]);
+            }
+            dw[0] = r0 + 1;
+            dw[1] = r1;
+            dw[2] = g0;
+            dw[3] = g1;
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < 4 * pl.E; i += blockDim.x) pl.win[i] = 0u;
+        for (int i = threadIdx.x; i < 2 * (D + 1); i += blockDim.x) pl.work[i] = 0u;
+    }
     if (D > 0) {
         phase_backup(pl, S, cur_e, Deff);
         stamp(pl, slot++);
