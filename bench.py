@@ -1302,7 +1302,10 @@ def main():
                                      GBps=step_dbytes / sec / 1e9, of_measured_hbm=step_dbytes / sec / 1e9 / peak),
             "phases": {k: {"ms": statistics.mean(v)} for k, v in ph_b.items()},
             "solo": solo})
-    roofline["traffic"] = recorded_traffic("k_plan", 0, args.workload)
+    # DRAM bytes of the timed launch from a committed ncu summary taken on the
+    # current sources: the batched launch of R plans, or one plan alone
+    roofline["traffic"] = recorded_traffic("k_plan", 0, f"{args.workload}_b{R}" if arm is batched
+                                           else f"{args.workload}_p1")
 
     # end to end through the public API with host buffers: pinned b0 -> device,
     # run, results -> host, every step
