@@ -114,6 +114,7 @@ struct PlanDev {
     // zeroed with the counters at creation and after a failed run)
     int *dirty;
     unsigned *work;    // [2 (d+1)] items taken so far of expand(l) and finalize(l) (cleared at the end of a run)
+    unsigned *grp_done;  // per group (gbase[l] + j): expand items done, deepest fused level (cleared at the end)
     int *leaf_split;   // chunks per group of leaves in the leaf phase
     unsigned *leaf_cnt;  // [n_part] chunk arrivals per group of leaves
     // per node (gid over every level)

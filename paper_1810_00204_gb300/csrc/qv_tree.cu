@@ -21,7 +21,8 @@ struct Layout {
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
-        off_status, off_boundary, off_bar, off_win, off_dirty, off_work, off_stamps, off_result, off_beliefs;
+        off_status, off_boundary, off_bar, off_win, off_dirty, off_work, off_grp_done, off_stamps, off_result,
+        off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0, cmax = 0;
     long long n_xrec = 0, n_frec = 0;
@@ -319,6 +320,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_win = take(sizeof(unsigned) * 4 * E);
     L.off_dirty = take(sizeof(int) * 4 * E * D1);
     L.off_work = take(sizeof(unsigned) * 2 * D1);
+    L.off_grp_done = take(sizeof(unsigned) * std::max<long long>(L.ngrp_cap, 1));
     L.off_beliefs = take(sizeof(float) * std::max<long long>(L.n_belief, 4));
     L.total = align_up(o, 256);
     return QV_OK;
@@ -463,6 +465,7 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.win = at<unsigned>(ws, L.off_win);
     d.dirty = at<int>(ws, L.off_dirty);
     d.work = at<unsigned>(ws, L.off_work);
+    d.grp_done = at<unsigned>(ws, L.off_grp_done);
     d.stamps = at<unsigned long long>(ws, L.off_stamps);
     d.result = at<qv::ResultDev>(ws, L.off_result);
     d.replay = params->d_replay;
@@ -600,8 +603,12 @@ extern "C" qv_status qv_plan_profile(qv_plan_t *pl, qv_launch_time_t *out, int32
         };
         std::vector<Ph> ph;
         for (int l = 0; l < D; ++l) {
-            ph.push_back({(l == D - 1 && !mat) ? "expand_fused" : "expand", l});
-            ph.push_back({(l == D - 1 && !mat) ? "finalize_fused" : "finalize", l});
+            if (l == D - 1 && !mat) {  // one phase: expand and finalize of the deepest level
+                ph.push_back({"fused", l});
+                continue;
+            }
+            ph.push_back({"expand", l});
+            ph.push_back({"finalize", l});
         }
         if (D > 0 && mat) ph.push_back({"update", D - 1});
         if (D == 0 || mat) ph.push_back({"leaf", D});

@@ -1032,20 +1032,21 @@ __device__ __forceinline__ float child1(const EpReg &ep, const float *m, const u
 // when its task range moves to another child; at the end of the band the
 // slots are added into each child's totals in warp order.  Cells with a
 // beacon's label enter through phase_finalize's tiles.
+// One expand work item w of level l (false when a wait gave up).  With
+// `signal` the item also counts itself done on its group's counter
+// (grp_done), which the fused level's finalize items wait on.
 template <bool FUSED>
-__device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
-                             int &cur_e) {
+__device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
+                            int &cur_e, int w, bool signal) {
     const int E = pl.E, K = pl.K;
     const int G = __ldcg(pl.ngrp + l);
     const int *goff = pl.grp_off + pl.gbase[l] + l;
     const int *grec = pl.grp_rec + pl.gbase[l];
-    const int total = __ldcg(goff + G);
     const int *np = l > 0 ? pl.npre + (l - 1) * (E + 1) : nullptr;
     const int KS = pl.kslots;
     constexpr int NV = FUSED ? 35 : 10;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned *ctr = pl.work + 2 * l;
-    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
+    {
 #ifdef QV_TRACE
         unsigned long long tr[kTraceWords] = {};
 #endif
@@ -1065,7 +1066,7 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         const BandGeo geo =
             band_geo(pl, e, __ldg(&epg->H), __ldg(&epg->W), __ldg(&epg->P), __ldg(&epg->band_rows), l);
         const int items = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
-        if (item >= items) continue;
+        if (item >= items) return true;
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
         const int rec = __ldcg(grec + j);
@@ -1400,7 +1401,21 @@ __device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint
         tr[1] = static_cast<unsigned long long>(w);
         trace_commit(tr, 7);
 #endif
+        if (signal) {
+            __syncthreads();  // every thread's totals are written
+            if (threadIdx.x == 0) arrive_acq_rel(pl.grp_done + pl.gbase[l] + j);
+        }
     }
+    return true;
+}
+
+template <bool FUSED>
+__device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
+                             int &cur_e) {
+    const int total = __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
+    unsigned *ctr = pl.work + 2 * l;
+    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8))
+        if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, false)) return false;
     return true;
 }
 
@@ -1560,19 +1575,21 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
 // node's U_Q and U_V (Alg. 5-7).  At other levels the last node of an
 // episode numbers its children and the last episode publishes the next
 // level's work lists (NUMBER: every level but the fused deepest one).
+// One finalize work item w of level l.  With `wait_group` the node first
+// waits (bounded) until every expand item of its group has counted itself
+// done on grp_done: the fused level runs its expand and finalize items as
+// one phase, without a grid barrier between them.
 template <bool FUSED, bool NUMBER>
-__device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
+__device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w, bool wait_group) {
     const int E = pl.E, K = pl.K, Bm = pl.Bmax;
     const int *wb = pl.wb_fin + l * (E + 1);
-    const int total = __ldcg(wb + E);
     const int C = max(1, __ldcg(pl.fchunks + l));
     const int stride = 30 * ((Bm + C - 1) / C);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *tp = S.tile + wid * kTileFloats;
     float *tc = tp + kTileP;
     uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
-    unsigned *ctr = pl.work + 2 * l + 1;
-    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
+    {
 #ifdef QV_TRACE
         unsigned long long tr[kTraceWords] = {};
 #endif
@@ -1660,7 +1677,7 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 tr[1] = static_cast<unsigned long long>(w);
                 trace_commit(tr, 5);
 #endif
-                continue;
+                return;
             }
             for (int i0 = threadIdx.x; i0 < B * 30; i0 += 4 * blockDim.x) {
                 // four loads in flight per thread
@@ -1697,11 +1714,28 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
             const int *goff = pl.grp_off + pl.gbase[l] + l;
             const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
             constexpr int kGroups = kThreads / kTot;  // 7 partial sums per value
+            const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
+            const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
+            if (wait_group) {
+                if (threadIdx.x == 0) {
+                    const unsigned *gd = pl.grp_done + pl.gbase[l] + jg;
+                    unsigned i = 0;
+                    for (;;) {
+                        unsigned v;
+                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
+                        if (v >= static_cast<unsigned>(nit)) break;
+                        if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+                            atomicOr(pl.status, kErrTimeout);
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                __syncthreads();
+            }
             if (rec < 0) {
                 if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
             } else {
-                const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
-                const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
                 const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
                 if (g < kGroups) {
                     // items g, g + 7, ... in order, eight loads in flight at a time
@@ -1759,6 +1793,35 @@ __device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
         tr[1] = static_cast<unsigned long long>(w);
         trace_commit(tr, 9);
 #endif
+    }
+}
+
+template <bool FUSED, bool NUMBER>
+__device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
+    const int total = __ldcg(pl.wb_fin + l * (pl.E + 1) + pl.E);
+    unsigned *ctr = pl.work + 2 * l + 1;
+    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8))
+        finalize_item<FUSED, NUMBER>(pl, l, S, cur_e, w, false);
+    return true;
+}
+
+// The deepest level of the fused mode as one phase: its expand items, then
+// its finalize items, from one counter.  A finalize item forms its label
+// histograms at once and waits only for its own group's expand records, so
+// CTAs that finish their last expand item start finalising instead of
+// waiting at a grid barrier.  Every expand item is taken before any
+// finalize item, and expand items wait on nothing but their own copies, so
+// every wait ends.
+__device__ bool phase_fused_last(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, unsigned &mphase, int &cur_e) {
+    const int n_exp = __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
+    const int total = n_exp + __ldcg(pl.wb_fin + l * (pl.E + 1) + pl.E);
+    unsigned *ctr = pl.work + 2 * l;
+    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
+        if (w < n_exp) {
+            if (!expand_item<true>(pl, l, false, S, mbar, mphase, cur_e, w, true)) return false;
+        } else {
+            finalize_item<true, false>(pl, l, S, cur_e, w - n_exp, true);
+        }
     }
     return true;
 }
@@ -2150,17 +2213,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     for (int l = 0; l < D; ++l) {
         const bool last = l == D - 1;
         const bool fused = (last && !mat) || dl;
-        const bool number = !(last && !mat);  // a level below is numbered by this one's finalisation
         // a level's beliefs are stored when a later phase reads them
         const bool store = l > 0 && (l < D - 1 || mat);
+        if (last && !mat) {
+            // expand and finalize of the deepest level in one phase
+            if (!phase_fused_last(pl, l, S, &mbar, mphase, cur_e) && threadIdx.x == 0)
+                atomicOr(pl.status, kErrTimeout);
+            if (!grid_sync(pl)) return;
+            stamp(pl, slot++);
+            continue;
+        }
         const bool ok = fused ? phase_expand<true>(pl, l, store, S, &mbar, mphase, cur_e)
                               : phase_expand<false>(pl, l, store, S, &mbar, mphase, cur_e);
         if (!ok && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
         if (!grid_sync(pl)) return;
         stamp(pl, slot++);
         if (!fused) phase_finalize<false, true>(pl, l, S, cur_e);
-        else if (number) phase_finalize<true, true>(pl, l, S, cur_e);
-        else phase_finalize<true, false>(pl, l, S, cur_e);
+        else phase_finalize<true, true>(pl, l, S, cur_e);
         if (!grid_sync(pl, dl && !last)) return;
         stamp(pl, slot++);
         if (dl && !last) {
@@ -2208,6 +2277,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         __syncthreads();
         for (int i = threadIdx.x; i < 4 * pl.E; i += blockDim.x) pl.win[i] = 0u;
         for (int i = threadIdx.x; i < 2 * (D + 1); i += blockDim.x) pl.work[i] = 0u;
+        if (D > 0 && !mat && Deff == D) {
+            const int ng = __ldcg(pl.ngrp + D - 1);
+            for (int i = threadIdx.x; i < ng; i += blockDim.x) pl.grp_done[pl.gbase[D - 1] + i] = 0u;
+        }
     }
     if (D > 0) {
         phase_backup(pl, S, cur_e, Deff);
