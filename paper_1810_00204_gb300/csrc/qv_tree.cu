@@ -193,7 +193,8 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
             NB[l] += c;
             c *= br;
         }
-        L.sb_floats = std::max(L.sb_floats, (ep.band_rows + 2) * ep.P);
+        if (p->leaf_mode == QV_LEAF_MATERIALISE && D > 0)  // the update phase's node band
+            L.sb_floats = std::max(L.sb_floats, (ep.band_rows + 2) * ep.P);
         L.sp_floats = std::max(L.sp_floats, (ep.band_rows + 4) * ep.P);
         if (p->leaf_mode == QV_LEAF_FUSED && D > 0) L.q_floats = std::max(L.q_floats, 5 * ep.band_rows * ep.P);
     }

@@ -65,23 +65,34 @@ struct SmemLayout {
             o += bytes;
             return r;
         };
-        s.sb = take(sizeof(float) * sb_floats);      // node band, one halo row
+        s.sb = take(sizeof(float) * sb_floats);      // node band, one halo row (materialised leaves only)
         s.sp = take(sizeof(float) * sp_floats);      // parent band, two halo rows
         s.cw = take(sizeof(uint16_t) * (sp_floats > sb_floats ? sp_floats : sb_floats));  // cell words, two halo rows
         s.q = take(sizeof(float) * q_floats);        // the band's rows of Q
-        // the label tiles of the finalize phase share the band buffers (the
-        // two phases are separated by grid barriers) when those are large enough
-        const size_t tile_bytes = sizeof(float) * kTileFloats * kWarps;
-        s.tile = (o - s.sb >= tile_bytes) ? s.sb : take(tile_bytes);
+        // what only a finalize item uses -- the label tiles, the histograms,
+        // P(z), the CDF and the draw counts -- shares the band buffers, which
+        // only expand and update items use (a CTA runs one item at a time,
+        // with a CTA barrier between items), as far as they are large enough
+        const size_t band_end = o;
+        size_t in = s.sb;
+        auto place = [&](size_t bytes) {
+            const size_t r = (in + 15) & ~size_t(15);
+            if (r + bytes <= band_end) {
+                in = r + bytes;
+                return r;
+            }
+            return take(bytes);
+        };
+        s.tile = place(sizeof(float) * kTileFloats * kWarps);
+        s.hist = place(sizeof(float) * 5 * Bm);
+        s.histq = place(sizeof(float) * 25 * Bm);
+        s.P = place(sizeof(float) * 5 * (Bm + 1));
+        s.C = place(sizeof(float) * 5 * (Bm + 1));
+        s.cnt = place(sizeof(int) * 5 * (Bm + 1));
         s.ep = take(sizeof(EpDev));
         s.bco = take(sizeof(int) * 2 * Bm);          // beacon (row, col)
-        s.hist = take(sizeof(float) * 5 * Bm);
-        s.histq = take(sizeof(float) * 25 * Bm);
         s.tot = take(sizeof(float) * kTot);
         s.red = take(sizeof(float) * kWarps * kTot);
-        s.P = take(sizeof(float) * 5 * (Bm + 1));
-        s.C = take(sizeof(float) * 5 * (Bm + 1));
-        s.cnt = take(sizeof(int) * 5 * (Bm + 1));
         s.T = take(sizeof(float) * 28);
         s.uq = take(sizeof(float) * 8);
         s.lut = take(sizeof(float) * 64);
