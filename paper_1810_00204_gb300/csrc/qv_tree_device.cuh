@@ -573,16 +573,18 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
     if (fused) {
         // T[a][a'] = the Q-weighted masses over every label: eight threads
         // per entry, each over every eighth beacon
-        const int t = threadIdx.x >> 3, sub = threadIdx.x & 7;
-        float s = 0.0f;
-        if (t < 25) {
-            const int a = t / 5, ap = t % 5;
-            for (int z = sub; z < B; z += 8) s += S.histq[(a * Bm + z) * 5 + ap];
+        for (int t0 = 0; t0 < 25; t0 += kThreads / 8) {
+            const int t = t0 + (threadIdx.x >> 3), sub = threadIdx.x & 7;
+            float s = 0.0f;
+            if (t < 25) {
+                const int a = t / 5, ap = t % 5;
+                for (int z = sub; z < B; z += 8) s += S.histq[(a * Bm + z) * 5 + ap];
+            }
+            s += __shfl_xor_sync(0xffffffffu, s, 1);
+            s += __shfl_xor_sync(0xffffffffu, s, 2);
+            s += __shfl_xor_sync(0xffffffffu, s, 4);
+            if (t < 25 && sub == 0) S.T[t] = s + S.tot[10 + t];
         }
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if (t < 25 && sub == 0) S.T[t] = s + S.tot[10 + t];
     }
     for (int a = wid; a < 5; a += kWarps) {
         // one warp per action: P(z | b, a) for every z, and its cumulative
@@ -1631,14 +1633,36 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
         const int bpc = (B + C - 1) / C;
         const int k0 = min(B, chunk * bpc), k1 = min(B, k0 + bpc);
         __syncthreads();  // the previous item's readers of the histograms are done
-        for (int k = k0 + wid; k < k1; k += kWarps) {
-            const int br = S.bco[2 * k], bc = S.bco[2 * k + 1], R = ep.range;
-            if (br + R < win.r0 || br - R >= win.r1 || bc + R < win.c0 || bc - R >= win.c1) {
-                // the beacon's diamond lies outside the window: its masses are zero
-                if (lane < 5) S.hist[lane * Bm + k] = 0.0f;
-                else if (FUSED && lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] = 0.0f;
-                continue;
+        // the chunk's beacons whose diamond meets the window, listed by warp 0
+        // (in the draw counts' buffer, unused until the node is finalised) and
+        // dealt to the warps in turn; the others' masses are zero
+        const int R = ep.range;
+        auto meets = [&](int k) {
+            const int br = S.bco[2 * k], bc = S.bco[2 * k + 1];
+            return !(br + R < win.r0 || br - R >= win.r1 || bc + R < win.c0 || bc - R >= win.c1);
+        };
+        int *klist = S.cnt;
+        if (wid == 0) {
+            int n = 0;
+            for (int kb = k0; kb < k1; kb += 32) {
+                const int k = kb + lane;
+                const bool hit = k < k1 && meets(k);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) klist[n + __popc(bal & ((1u << lane) - 1u))] = k;
+                n += __popc(bal);
             }
+            if (lane == 0) S.flags[9] = n;
+        }
+        for (int i = threadIdx.x; i < (k1 - k0) * 30; i += blockDim.x) {
+            const int k = k0 + i / 30, t = i - (i / 30) * 30;
+            if (meets(k)) continue;
+            if (t < 5) S.hist[t * Bm + k] = 0.0f;
+            else if (FUSED) S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5] = 0.0f;
+        }
+        __syncthreads();
+        const int nlist = S.flags[9];
+        for (int li = wid; li < nlist; li += kWarps) {
+            const int k = klist[li];
             float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             float lq[FUSED ? 25 : 1];
 #pragma unroll
@@ -1724,7 +1748,7 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
             }
             const int *goff = pl.grp_off + pl.gbase[l] + l;
             const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
-            constexpr int kGroups = kThreads / kTot;  // 7 partial sums per value
+            constexpr int kGroups = kThreads / kTot;  // partial sums per value
             const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
             const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
             if (wait_group) {
@@ -1771,24 +1795,35 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
                     S.tot[threadIdx.x] = sum;
                 }
             }
-            if (threadIdx.x == 0) {
-                // the node's belief at the goal, whose arrivals R(b, a) must not pay
-                const int y = ep.goal;
-                float bg;
-                if (l == 0) {
-                    bg = __ldg(par + y);
-                } else {
-                    const unsigned cw = __ldg(ep.cell + y);
-                    const unsigned in = QV_CELL_INFLOW(cw);
-                    float nb[4];
-                    nb[kDirN] = (in & 1u) ? __ldcg(par + y - ep.P) : 0.0f;
-                    nb[kDirE] = (in & 2u) ? __ldcg(par + y + 1) : 0.0f;
-                    nb[kDirS] = (in & 4u) ? __ldcg(par + y + ep.P) : 0.0f;
-                    nb[kDirW] = (in & 8u) ? __ldcg(par + y - 1) : 0.0f;
-                    bg = predict_one(nb, __ldcg(par + y), cw, true, ep.slip, S.lut, pa) *
-                         (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+            if (wid == 0) {
+                // the node's belief at the goal, whose arrivals R(b, a) must not
+                // pay: lanes 0-4 load the parent there and at its four
+                // neighbours (inside the grid) at once
+                const int y = ep.goal, P = ep.P, gr = y / P, gc = y - gr * P;
+                const int dy[5] = {0, -P, 1, P, -1};
+                const bool inside = lane < 5 && (lane != 1 || gr > 0) && (lane != 2 || gc + 1 < P) &&
+                                    (lane != 3 || gr + 1 < ep.H) && (lane != 4 || gc > 0);
+                const float pv = inside ? __ldcg(par + y + dy[lane < 5 ? lane : 0]) : 0.0f;
+                const unsigned cw = __ldg(ep.cell + y);
+                const float m0 = __shfl_sync(0xffffffffu, pv, 0), mN = __shfl_sync(0xffffffffu, pv, 1);
+                const float mE = __shfl_sync(0xffffffffu, pv, 2), mS = __shfl_sync(0xffffffffu, pv, 3);
+                const float mW = __shfl_sync(0xffffffffu, pv, 4);
+                if (lane == 0) {
+                    float bg;
+                    if (l == 0) {
+                        bg = m0;
+                    } else {
+                        const unsigned in = QV_CELL_INFLOW(cw);
+                        float nb[4];
+                        nb[kDirN] = (in & 1u) ? mN : 0.0f;
+                        nb[kDirE] = (in & 2u) ? mE : 0.0f;
+                        nb[kDirS] = (in & 4u) ? mS : 0.0f;
+                        nb[kDirW] = (in & 8u) ? mW : 0.0f;
+                        bg = predict_one(nb, m0, cw, true, ep.slip, S.lut, pa) *
+                             (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+                    }
+                    S.flags[4] = __float_as_int(bg);
                 }
-                S.flags[4] = __float_as_int(bg);
             }
             __syncthreads();
         }
