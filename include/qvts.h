@@ -38,6 +38,13 @@
  *     qv_plan_create report QV_ERR_WORKSPACE (this library's out-of-memory),
  *     "invalid" makes those and belief_predict and qv_plan_run report
  *     QV_ERR_INVALID.  Unset (or any other value): no injection.
+ *   - Profiling: every call that launches device work opens an NVTX range
+ *     "qvts:<call>" for its host-side duration (closed on every return);
+ *     calls that issue a tree's levels one launch at a time (the adjoint,
+ *     the nine-action plan, the bounds) also open "qvts:<call> level <l>"
+ *     per level.  The plan kernel runs every level inside one launch: its
+ *     per-level times come from qv_plan_profile's device clock stamps.
+ *     Without an NVTX tool attached the ranges cost a pointer test.
  */
 #ifndef QVTS_H
 #define QVTS_H

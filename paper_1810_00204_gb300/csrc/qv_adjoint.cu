@@ -637,6 +637,7 @@ extern "C" size_t qv_tree_backward_workspace_bytes(const qv_plan_t *pl, int32_t 
 extern "C" qv_status qv_tree_backward(const qv_plan_t *pl, int32_t e, double dL_dV, double *d_Qbar, double *d_dslip,
                                       double *d_dacc, double *d_dcost, double *d_db0, void *d_ws, size_t ws_bytes,
                                       qv_stream_t stream) {
+    QV_RANGE("qv_tree_backward");
     using namespace qv;
     if (!pl || !d_Qbar || !d_dslip || !d_dacc || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "qv_tree_backward: null pointer");
@@ -700,6 +701,7 @@ extern "C" qv_status qv_tree_backward(const qv_plan_t *pl, int32_t e, double dL_
                       "qv_tree_backward smem") != QV_OK)
         return QV_ERR_CUDA;
     for (int l = D - 1; l >= 0; --l) {
+        QV_RANGE("qv_tree_backward", l);
         const dim3 grid(L.bands, std::min(L.caps[l], 65535));
         k_adj_level<<<grid, kAdjThreads, smem, st>>>(a, l);
         if (qv_check_cuda(cudaGetLastError(), "qv_tree_backward level") != QV_OK) return QV_ERR_CUDA;
@@ -740,6 +742,7 @@ extern "C" size_t mdp_value_backward_workspace_bytes(const qv_model_t *m, int32_
 extern "C" qv_status mdp_value_backward(const qv_model_t *m, int32_t sweeps, int32_t every, const double *d_Vckpt,
                                         const double *d_Qbar, double *d_dslip, double *d_dcost, void *d_ws,
                                         size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("mdp_value_backward");
     using namespace qv;
     if (!m || !m->d_cell || !d_Vckpt || !d_Qbar || !d_dslip || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_backward: null pointer");

@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qv_common.cuh"
 
 namespace {
@@ -38,6 +40,20 @@ qv_status qv_injected_fault(const char *where, bool takes_workspace) {
         return qv_set_error(QV_ERR_INVALID, "%s: injected fault (QVTS_FAULT=invalid)", where);
     return QV_OK;
 }
+
+QvRange::QvRange(const char *name) {
+    char b[96];
+    std::snprintf(b, sizeof(b), "qvts:%s", name);
+    nvtxRangePushA(b);
+}
+
+QvRange::QvRange(const char *name, int level) {
+    char b[96];
+    std::snprintf(b, sizeof(b), "qvts:%s level %d", name, level);
+    nvtxRangePushA(b);
+}
+
+QvRange::~QvRange() { nvtxRangePop(); }
 
 int qv_num_sms() {
     int dev = 0, n = 0;

@@ -211,6 +211,7 @@ qv_status check_model(const qv_model_t *m, const char *who) {
 
 extern "C" qv_status belief_predict(const qv_model_t *m, const float *d_b, int32_t action, float *d_bbar,
                                     qv_stream_t stream) {
+    QV_RANGE("belief_predict");
     qv_status st = qv_injected_fault("belief_predict", false);
     if (st != QV_OK) return st;
     st = qv::check_model(m, "belief_predict");
@@ -232,6 +233,7 @@ extern "C" size_t belief_correct_workspace_bytes(const qv_model_t *) {
 
 extern "C" qv_status belief_correct(const qv_model_t *m, const float *d_bbar, int32_t z, float *d_bout, float *d_pz,
                                     void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("belief_correct");
     if (const qv_status inj = qv_injected_fault("belief_correct", true)) return inj;
     qv_status st = qv::check_model(m, "belief_correct");
     if (st != QV_OK) return st;
@@ -343,6 +345,7 @@ extern "C" qv_status belief_correct_noalloc(const qv_model_t *m, const float *d_
 
 extern "C" qv_status leaf_value(const qv_model_t *m, const float *d_Q, const float *d_b, int32_t n, float *d_value,
                                 qv_stream_t stream) {
+    QV_RANGE("leaf_value");
     qv_status st = qv::check_model(m, "leaf_value");
     if (st != QV_OK) return st;
     if (!d_Q || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "leaf_value: null pointer");

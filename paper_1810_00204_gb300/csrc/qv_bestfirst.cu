@@ -484,6 +484,7 @@ extern "C" void qv_bf_destroy(qv_bf_t *h) {
 }
 
 extern "C" qv_status qv_bf_reset(qv_bf_t *h, const float *d_b0, void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("qv_bf_reset");
     if (!h || !d_b0 || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_bf_reset: null pointer");
     if (ws_bytes < h->bytes)
         return qv_set_error(QV_ERR_WORKSPACE, "qv_bf_reset: workspace %zu < %zu bytes", ws_bytes, h->bytes);
@@ -541,6 +542,7 @@ extern "C" qv_status qv_bf_reset(qv_bf_t *h, const float *d_b0, void *d_ws, size
 }
 
 extern "C" qv_status qv_bf_run(qv_bf_t *h, int32_t iters, qv_stream_t stream) {
+    QV_RANGE("qv_bf_run");
     if (!h) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: null pointer");
     if (!h->ready) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: no tree (qv_bf_reset)");
     if (iters < 0) return qv_set_error(QV_ERR_INVALID, "qv_bf_run: iters %d", iters);
@@ -602,6 +604,7 @@ extern "C" qv_status qv_bf_set_replay(qv_bf_t *h, const int32_t *d_expand, int32
 }
 
 extern "C" qv_status qv_bf_read(qv_bf_t *h, qv_bf_result_t *r, qv_stream_t stream) {
+    QV_RANGE("qv_bf_read");
     if (!h || !r) return qv_set_error(QV_ERR_INVALID, "qv_bf_read: null pointer");
     if (!h->ready) return qv_set_error(QV_ERR_INVALID, "qv_bf_read: no tree (qv_bf_reset)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);

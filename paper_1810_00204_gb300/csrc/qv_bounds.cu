@@ -189,6 +189,7 @@ extern "C" qv_status qv_plan_bounds_view(const qv_plan_t *pl, int32_t e, int32_t
 
 extern "C" qv_status qv_plan_bounds(const qv_plan_t *pl, int32_t e, const float *d_leaf_L, void *d_ws,
                                     size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("qv_plan_bounds");
     if (!pl || !d_leaf_L || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_plan_bounds: null pointer");
     if (e < 0 || e >= pl->E) return qv_set_error(QV_ERR_INVALID, "qv_plan_bounds: episode %d out of range", e);
     const qv::BoundsLayout L = qv::bounds_layout(pl, e);
@@ -210,6 +211,7 @@ extern "C" qv_status qv_plan_bounds(const qv_plan_t *pl, int32_t e, const float 
     qv::k_bounds_leaf<<<std::max(1, std::min((capd + 255) / 256, 4 * qv_num_sms())), 256, 0, st>>>(
         lv[D].d_count, lv[D].d_value, d_leaf_L, bv[D].d_LV, bv[D].d_HV, bv[D].d_EV);
     for (int l = D - 1; l >= 0; --l) {
+        QV_RANGE("qv_plan_bounds", l);
         qv::BoundsLevel v;
         v.count = lv[l].d_count;
         v.value = lv[l].d_value;

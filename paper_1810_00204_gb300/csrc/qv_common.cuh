@@ -224,3 +224,19 @@ unsigned qv_cross_spin_limit();
 // device memory itself), "invalid" makes the instrumented calls return
 // QV_ERR_INVALID; each leaves a message naming the injection.
 qv_status qv_injected_fault(const char *where, bool takes_workspace);
+
+// NVTX range over a host-side call (NVTX v3, header only): a profiler that
+// reads NVTX (nsys, ncu --nvtx) shows every launching entry point as
+// "qvts:<name>" and, where the host issues a tree's levels one by one, each
+// level as "qvts:<name> level <l>".  Without a tool attached a push or pop is
+// a call through a null-checked function pointer.  The plan kernel runs all of
+// a tree's levels inside one launch, so its per-level times come from the
+// device clock stamps (qv_plan_profile), not from ranges.
+struct QvRange {
+    explicit QvRange(const char *name);
+    QvRange(const char *name, int level);
+    ~QvRange();
+    QvRange(const QvRange &) = delete;
+    QvRange &operator=(const QvRange &) = delete;
+};
+#define QV_RANGE(...) QvRange qv_nvtx_range_(__VA_ARGS__)

@@ -268,6 +268,7 @@ extern "C" size_t qv_forward_sample_workspace_bytes(const qv_model_t *m, int32_t
 extern "C" qv_status qv_forward_sample(const qv_model_t *m, int32_t n, const float *d_B, const int32_t *d_action,
                                        const uint64_t *d_path, int32_t level, uint64_t seed, uint32_t episode,
                                        int32_t K, int32_t *d_z, void *d_ws, size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("qv_forward_sample");
     if (!m || !m->d_cell || !d_B || !d_action || !d_path || !d_z || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "qv_forward_sample: null pointer");
     if (n < 0 || K < 0 || level < 0 || level > 255 || m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
@@ -293,6 +294,7 @@ extern "C" const int32_t *qv_plan_actions_device(const qv_plan_t *pl, int32_t *s
 extern "C" qv_status qv_env_step(const qv_model_t *m, int32_t E, const int32_t *d_action, int32_t action_stride,
                                  int32_t *d_state, uint64_t seed, int32_t step, int32_t *d_obs, int32_t *d_steps,
                                  float *d_return, int32_t *d_done, qv_stream_t stream) {
+    QV_RANGE("qv_env_step");
     if (!m || !m->d_cell || !d_action || !d_state || !d_obs || !d_steps || !d_return || !d_done)
         return qv_set_error(QV_ERR_INVALID, "qv_env_step: null pointer");
     if (E < 0 || action_stride < 1 || step < 0 || m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
@@ -313,6 +315,7 @@ extern "C" size_t qv_belief_update_batched_workspace_bytes(const qv_model_t *m, 
 extern "C" qv_status qv_belief_update_batched(const qv_model_t *m, int32_t E, float *d_B, const int32_t *d_action,
                                               int32_t action_stride, const int32_t *d_obs, void *d_ws,
                                               size_t ws_bytes, qv_stream_t stream) {
+    QV_RANGE("qv_belief_update_batched");
     if (!m || !m->d_cell || !d_B || !d_action || !d_obs || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "qv_belief_update_batched: null pointer");
     if (E < 0 || action_stride < 1) return qv_set_error(QV_ERR_INVALID, "qv_belief_update_batched: bad arguments");

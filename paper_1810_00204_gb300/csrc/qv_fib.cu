@@ -383,6 +383,7 @@ extern "C" size_t fib_value_iterate_workspace_bytes(const qv_model_t *m, int32_t
 extern "C" qv_status fib_value_iterate(const qv_model_t *m, int32_t dtype, double tol, int32_t max_sweeps,
                                        int32_t truncated, void *d_alpha, float *d_Q, void *d_ws, size_t ws_bytes,
                                        int32_t *sweeps_out, double *residual_out, qv_stream_t stream) {
+    QV_RANGE("fib_value_iterate");
     if (const qv_status inj = qv_injected_fault("fib_value_iterate", true)) return inj;
     if (!m || !m->d_cell || !d_Q || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "fib_value_iterate: null pointer");

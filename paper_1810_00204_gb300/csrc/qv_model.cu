@@ -49,6 +49,7 @@ k_model_build(int H, int W, int P, const uint8_t *__restrict__ occ, const int32_
 extern "C" qv_status qv_model_build(int32_t H, int32_t W, int32_t pitch, const uint8_t *d_occ,
                                     const int32_t *d_beacons, int32_t B, int32_t sense_range,
                                     int32_t goal, uint16_t *d_cell, qv_stream_t stream) {
+    QV_RANGE("qv_model_build");
     if (H < 1 || W < 1 || W > QV_MAX_WIDTH || pitch != QV_PITCH(W))
         return qv_set_error(QV_ERR_INVALID, "qv_model_build: bad grid %dx%d pitch %d", H, W, pitch);
     if (B < 1 || B > QV_MAX_BEACONS)

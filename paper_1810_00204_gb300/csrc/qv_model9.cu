@@ -599,6 +599,7 @@ float *belief9(const qv9 *h, int l) {
 }  // namespace
 
 extern "C" qv_status qv9_create(const qv9_model_t *m, int32_t depth, int32_t K, qv9_t **out) {
+    QV_RANGE("qv9_create");
     if (!m || !m->d_occ || !out) return qv_set_error(QV_ERR_INVALID, "qv9_create: null pointer");
     *out = nullptr;
     if (m->H < 1 || m->W < 1 || m->W > QV_MAX_WIDTH || m->goal < 0 || m->goal >= m->H * m->W)
@@ -783,6 +784,7 @@ qv_status vi9(qv9 *h, double tol, int max_sweeps, int truncated, T *d_V, float *
 extern "C" qv_status qv9_value_iterate(qv9_t *h, int32_t dtype, double tol, int32_t max_sweeps, int32_t truncated,
                                        void *d_V, float *d_Q, int32_t *sweeps_out, double *residual_out,
                                        qv_stream_t stream) {
+    QV_RANGE("qv9_value_iterate");
     if (!h || !d_V || !d_Q) return qv_set_error(QV_ERR_INVALID, "qv9_value_iterate: null pointer");
     if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv9_value_iterate: no workspace (qv9_set_workspace)");
     if (dtype != QV_F32 && dtype != QV_F64) return qv_set_error(QV_ERR_INVALID, "qv9_value_iterate: dtype");
@@ -799,6 +801,7 @@ extern "C" qv_status qv9_value_iterate(qv9_t *h, int32_t dtype, double tol, int3
 
 extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uint64_t seed, uint32_t episode,
                               qv9_plan_result_t *res, qv_stream_t stream) {
+    QV_RANGE("qv9_plan");
     if (!h || !d_Q || !d_b0 || !res) return qv_set_error(QV_ERR_INVALID, "qv9_plan: null pointer");
     if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv9_plan: no workspace (qv9_set_workspace)");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -825,6 +828,7 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
     qv::k9_root<<<rgrid, qv::kT9, 0, st>>>(m, d_b0, belief9(h, 0), level9(h, 0), bcount);
     h->n_level[0] = 1;
     for (int l = 0; l < D; ++l) {
+        QV_RANGE("qv9_plan", l);
         const int nl = h->n_level[l];
         const bool leaf = l + 1 == D;
         const size_t q0 = static_cast<size_t>(h->node_off[l]) * qv::kA9;  // Q-node base of the level
@@ -865,6 +869,7 @@ extern "C" qv_status qv9_plan(qv9_t *h, const float *d_Q, const float *d_b0, uin
                                                                                               belief9(h, l + 1));
     }
     for (int l = D - 1; l >= 0; --l) {
+        QV_RANGE("qv9_plan backup", l);
         const size_t q0 = static_cast<size_t>(h->node_off[l]) * qv::kA9;
         const qv::Lvl9 L = level9(h, l), N = level9(h, l + 1);
         qv::k9_backup<<<(h->n_level[l] + qv::kT9 - 1) / qv::kT9, qv::kT9, 0, st>>>(

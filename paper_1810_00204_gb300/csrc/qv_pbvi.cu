@@ -1192,6 +1192,7 @@ extern "C" int32_t qv_pbvi_layout(const qv_pbvi *h, int32_t *seg_out) {
 }
 
 extern "C" qv_status qv_pbvi_init(const qv_model_t *m, float *d_alpha0, qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_init");
     if (!m || !m->d_cell || !d_alpha0) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_init: null pointer");
     if (!(m->discount > 0.0f && m->discount < 1.0f) || m->num_beacons < 1)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_init: bad model");
@@ -1202,6 +1203,7 @@ extern "C" qv_status qv_pbvi_init(const qv_model_t *m, float *d_alpha0, qv_strea
 extern "C" qv_status qv_pbvi_expand(const qv_model_t *m, const float *d_B, int32_t nB, int32_t round, uint64_t seed,
                                     float *d_out, int32_t *d_action, int32_t *d_obs, int32_t *d_boundary,
                                     qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_expand");
     if (!m || !m->d_cell || !d_B || !d_out || !d_action || !d_obs || !d_boundary)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_expand: null pointer");
     if (nB < 0 || round < 0 || m->num_beacons < 1 || m->num_beacons > QV_MAX_BEACONS)
@@ -1220,6 +1222,7 @@ extern "C" qv_status qv_pbvi_expand(const qv_model_t *m, const float *d_B, int32
 
 extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB, void *d_ws, size_t ws_bytes,
                                         qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_set_points");
     if (!h || !d_B || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_set_points: null pointer");
     if (nB < 1 || nB > h->max_points)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_set_points: %d points outside 1..%d", nB, h->max_points);
@@ -1261,12 +1264,14 @@ extern "C" qv_status qv_pbvi_set_points(qv_pbvi *h, const float *d_B, int32_t nB
 
 extern "C" qv_status qv_pbvi_backup(qv_pbvi *h, const float *d_G, int32_t nG, float *d_Gout, float *d_value,
                                     int32_t *d_astar, int32_t *d_best, float *d_q, qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_backup");
     return qv_pbvi_backup_fixed(h, d_G, nG, d_Gout, d_value, d_astar, d_best, d_q, nullptr, nullptr, stream);
 }
 
 extern "C" qv_status qv_pbvi_backup_fixed(qv_pbvi *h, const float *d_G, int32_t nG, float *d_Gout, float *d_value,
                                           int32_t *d_astar, int32_t *d_best, float *d_q, const int32_t *d_fix_astar,
                                           const int32_t *d_fix_best, qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_backup_fixed");
     if (!h || !d_G || !d_Gout) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup: null pointer");
     if (d_fix_best && !d_fix_astar)
         return qv_set_error(QV_ERR_INVALID, "qv_pbvi_backup_fixed: fixed winners need the fixed actions");
@@ -1328,6 +1333,7 @@ extern "C" qv_status qv_pbvi_backup_fixed(qv_pbvi *h, const float *d_G, int32_t 
 
 extern "C" qv_status qv_pbvi_value(qv_pbvi *h, const float *d_G, int32_t nG, const float *d_b, int32_t nb,
                                    float *d_value, int32_t *d_arg, qv_stream_t stream) {
+    QV_RANGE("qv_pbvi_value");
     if (!h || !d_b || !d_value) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: null pointer");
     if (!h->ws) return qv_set_error(QV_ERR_INVALID, "qv_pbvi_value: no workspace yet (qv_pbvi_set_points)");
     if (nG < 1 || nG > h->max_vectors || nb < 0)

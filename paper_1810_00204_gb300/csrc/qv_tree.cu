@@ -367,6 +367,7 @@ extern "C" size_t qv_plan_workspace_bytes(int32_t E, const qv_model_t *models, c
 extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const float *const *d_Q,
                                     const float *const *d_b0, const qv_plan_params_t *params, void *d_ws,
                                     size_t ws_bytes, qv_plan_t **plan_out, qv_stream_t stream) {
+    QV_RANGE("qv_plan_create");
     if (const qv_status inj = qv_injected_fault("qv_plan_create", true)) return inj;
     if (!plan_out || !d_Q || !d_b0 || !d_ws) return qv_set_error(QV_ERR_INVALID, "qv_plan_create: null pointer");
     *plan_out = nullptr;
@@ -556,6 +557,7 @@ extern "C" qv_status qv_plan_set_episode_word(qv_plan_t *pl, const uint32_t *d_w
 }
 
 extern "C" qv_status qv_plan_run(qv_plan_t *pl, qv_stream_t stream) {
+    QV_RANGE("qv_plan_run");
     if (const qv_status inj = qv_injected_fault("qv_plan_run", false)) return inj;
     if (!pl) return qv_set_error(QV_ERR_INVALID, "qv_plan_run: null plan");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -566,6 +568,7 @@ extern "C" qv_status qv_plan_run(qv_plan_t *pl, qv_stream_t stream) {
 
 extern "C" qv_status qv_plan_profile(qv_plan_t *pl, qv_launch_time_t *out, int32_t max_launches, int32_t *n_out,
                                      qv_stream_t stream) {
+    QV_RANGE("qv_plan_profile");
     if (!pl || !out || !n_out || max_launches < 0)
         return qv_set_error(QV_ERR_INVALID, "qv_plan_profile: bad argument");
     *n_out = 0;
@@ -629,6 +632,7 @@ extern "C" qv_status qv_plan_profile(qv_plan_t *pl, qv_launch_time_t *out, int32
 }
 
 extern "C" qv_status qv_plan_capture_graph(qv_plan_t *pl, qv_stream_t stream) {
+    QV_RANGE("qv_plan_capture_graph");
     if (!pl) return qv_set_error(QV_ERR_INVALID, "qv_plan_capture_graph: null plan");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (st == nullptr) return qv_set_error(QV_ERR_INVALID, "qv_plan_capture_graph: needs a non-default stream");
@@ -693,6 +697,7 @@ extern "C" qv_status qv_plan_decode(qv_plan_t *pl, const void *h_buf, qv_plan_re
 }
 
 extern "C" qv_status qv_plan_read(qv_plan_t *pl, qv_plan_result_t *h, qv_stream_t stream) {
+    QV_RANGE("qv_plan_read");
     if (!pl || !h) return qv_set_error(QV_ERR_INVALID, "qv_plan_read: null pointer");
     std::vector<char> buf(pl->read_bytes);
     if (qv_plan_read_async(pl, buf.data(), stream) != QV_OK ||
@@ -758,6 +763,7 @@ extern "C" qv_status qv_plan_level(const qv_plan_t *cpl, int32_t e, int32_t l, q
 extern "C" qv_status qv_tree_plan_batched(int32_t E, const qv_model_t *models, const float *const *d_Q,
                                           const float *const *d_b0, const qv_plan_params_t *params, void *d_ws,
                                           size_t ws_bytes, qv_plan_result_t *h_results, qv_stream_t stream) {
+    QV_RANGE("qv_tree_plan_batched");
     qv_plan_t *pl = nullptr;
     qv_status st = qv_plan_create(E, models, d_Q, d_b0, params, d_ws, ws_bytes, &pl, stream);
     if (st != QV_OK) return st;
@@ -770,6 +776,7 @@ extern "C" qv_status qv_tree_plan_batched(int32_t E, const qv_model_t *models, c
 extern "C" qv_status qv_tree_plan(const qv_model_t *model, const float *d_Q, const float *d_b0,
                                   const qv_plan_params_t *params, void *d_ws, size_t ws_bytes,
                                   qv_plan_result_t *h_result, qv_stream_t stream) {
+    QV_RANGE("qv_tree_plan");
     return qv_tree_plan_batched(1, model, &d_Q, &d_b0, params, d_ws, ws_bytes, h_result, stream);
 }
 
@@ -812,6 +819,7 @@ extern "C" qv_status qv_plan_autotune(int32_t E, const qv_model_t *models, const
                                       const float *const *d_b0, const qv_plan_params_t *params, void *d_ws,
                                       size_t ws_bytes, int32_t reps, qv_tune_t *best, qv_tune_t *all, int32_t max_all,
                                       int32_t *n_all, qv_stream_t stream) {
+    QV_RANGE("qv_plan_autotune");
     if (!params || !best) return qv_set_error(QV_ERR_INVALID, "qv_plan_autotune: null pointer");
     if (reps < 1) return qv_set_error(QV_ERR_INVALID, "qv_plan_autotune: reps %d", reps);
     qv_status st = validate(E, models, params);

@@ -284,6 +284,7 @@ extern "C" size_t mdp_value_iterate_workspace_bytes(const qv_model_t *m, int32_t
 extern "C" qv_status mdp_value_iterate(const qv_model_t *m, int32_t dtype, double tol, int32_t max_sweeps,
                                        int32_t truncated, void *d_V, float *d_Q, void *d_ws, size_t ws_bytes,
                                        int32_t *sweeps_out, double *residual_out, qv_stream_t stream) {
+    QV_RANGE("mdp_value_iterate");
     if (const qv_status inj = qv_injected_fault("mdp_value_iterate", true)) return inj;
     if (!m || !m->d_cell || !d_V || !d_Q || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate: null pointer");
@@ -308,6 +309,7 @@ extern "C" qv_status mdp_value_iterate(const qv_model_t *m, int32_t dtype, doubl
 extern "C" qv_status mdp_value_iterate_checkpointed(const qv_model_t *m, int32_t sweeps, int32_t every, double *d_V,
                                                     float *d_Q, double *d_Vckpt, void *d_ws, size_t ws_bytes,
                                                     qv_stream_t stream) {
+    QV_RANGE("mdp_value_iterate_checkpointed");
     if (!m || !m->d_cell || !d_V || !d_Q || !d_Vckpt || !d_ws)
         return qv_set_error(QV_ERR_INVALID, "mdp_value_iterate_checkpointed: null pointer");
     if (m->H < 1 || m->W < 1 || m->pitch != QV_PITCH(m->W) || m->W > QV_MAX_WIDTH)
