@@ -37,7 +37,15 @@
  *     mdp_value_iterate, fib_value_iterate, belief_correct and
  *     qv_plan_create report QV_ERR_WORKSPACE (this library's out-of-memory),
  *     "invalid" makes those and belief_predict and qv_plan_run report
- *     QV_ERR_INVALID.  Unset (or any other value): no injection.
+ *     QV_ERR_INVALID, and "bounds" (bounds-checked build only, below) makes
+ *     the plan's node-record check report a failure on every run although its
+ *     indices are in range.  Unset (or any other value): no injection.
+ *   - Bounds-checked debug build: libqvts_debug.so, the same ABI compiled with
+ *     -DQV_BOUNDS_CHECK.  The plan kernel then checks its workspace indices,
+ *     the rows and columns of its bulk copies and its stored-belief offsets
+ *     before each access; an index out of range skips the access (no fault)
+ *     and the plan's read reports QV_ERR_BOUNDS with the site's name, the
+ *     index and the limit.  Release builds compile the checks out.
  *   - Profiling: every call that launches device work opens an NVTX range
  *     "qvts:<call>" for its host-side duration (closed on every return);
  *     calls that issue a tree's levels one launch at a time (the adjoint,
@@ -65,7 +73,8 @@ typedef enum {
     QV_ERR_WORKSPACE = 3,      /* ws_bytes smaller than the *_workspace_bytes figure  */
     QV_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up                  */
     QV_ERR_NOT_CONVERGED = 5,  /* value iteration hit max_sweeps before tol           */
-    QV_ERR_CAPACITY = 6        /* a tree level outgrew its preallocated capacity      */
+    QV_ERR_CAPACITY = 6,       /* a tree level outgrew its preallocated capacity      */
+    QV_ERR_BOUNDS = 7          /* a device bounds check failed (debug build only)     */
 } qv_status;
 
 #define QV_NUM_ACTIONS 5

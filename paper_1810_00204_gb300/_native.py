@@ -10,11 +10,14 @@ import ctypes as C
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libqvts.so")
+# QVTS_LIB=debug loads the bounds-checked debug build (libqvts_debug.so, the
+# same ABI; device bounds checks report QV_ERR_BOUNDS instead of faulting)
+LIB_PATH = os.path.join(PKG, "libqvts_debug.so" if os.environ.get("QVTS_LIB") == "debug" else "libqvts.so")
 
-QV_OK, QV_ERR_INVALID, QV_ERR_CUDA, QV_ERR_WORKSPACE, QV_ERR_TIMEOUT, QV_ERR_NOT_CONVERGED, QV_ERR_CAPACITY = range(7)
+(QV_OK, QV_ERR_INVALID, QV_ERR_CUDA, QV_ERR_WORKSPACE, QV_ERR_TIMEOUT, QV_ERR_NOT_CONVERGED, QV_ERR_CAPACITY,
+ QV_ERR_BOUNDS) = range(8)
 STATUS_NAMES = {0: "QV_OK", 1: "QV_ERR_INVALID", 2: "QV_ERR_CUDA", 3: "QV_ERR_WORKSPACE",
-                4: "QV_ERR_TIMEOUT", 5: "QV_ERR_NOT_CONVERGED", 6: "QV_ERR_CAPACITY"}
+                4: "QV_ERR_TIMEOUT", 5: "QV_ERR_NOT_CONVERGED", 6: "QV_ERR_CAPACITY", 7: "QV_ERR_BOUNDS"}
 QV_NUM_ACTIONS = 5
 QV_MAX_DEPTH = 6
 QV_MAX_BEACONS = 126

@@ -41,6 +41,11 @@ qv_status qv_injected_fault(const char *where, bool takes_workspace) {
     return QV_OK;
 }
 
+unsigned qv_bounds_injected_site() {
+    const char *f = std::getenv("QVTS_FAULT");
+    return (f && std::strcmp(f, "bounds") == 0) ? 1u : 0u;
+}
+
 QvRange::QvRange(const char *name) {
     char b[96];
     std::snprintf(b, sizeof(b), "qvts:%s", name);

@@ -31,6 +31,7 @@ constexpr int kDirN = 0, kDirE = 1, kDirS = 2, kDirW = 3;
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned kErrCapacity = 2u;
 constexpr unsigned kErrInput = 4u;
+constexpr unsigned kErrBounds = 8u;  // a device bounds check failed (bounds-checked debug build)
 
 // Bounded spin: after this many polls a wait gives up and reports a timeout.
 // Waits on the CTA's own bulk copies always use it; waits on other CTAs (grid
@@ -224,6 +225,10 @@ unsigned qv_cross_spin_limit();
 // device memory itself), "invalid" makes the instrumented calls return
 // QV_ERR_INVALID; each leaves a message naming the injection.
 qv_status qv_injected_fault(const char *where, bool takes_workspace);
+// QVTS_FAULT=bounds: the device bounds check whose site number this returns
+// (1, the node records) reports a failure on every run although its index is
+// in range (bounds-checked debug build only; 0 = no injection).
+unsigned qv_bounds_injected_site();
 
 // NVTX range over a host-side call (NVTX v3, header only): a profiler that
 // reads NVTX (nsys, ncu --nvtx) shows every launching entry point as

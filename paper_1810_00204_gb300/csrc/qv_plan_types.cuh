@@ -145,6 +145,9 @@ struct PlanDev {
     uint32_t episode0;             // params.episode: episode e's own word is episode0 + e
     unsigned long long deadline_ns;  // anytime stop, 0 = none (status[1] set when it has run out)
     unsigned spin_limit;  // polls before a wait on other CTAs gives up
+    // capacities of the workspace arrays, for the bounds-checked debug build
+    long long n_nodes, n_inodes, n_belief;  // node ids, internal node ids, floats of stored beliefs
+    int ngrp_cap;                           // expand group entries over every level
     EpDev ep0;            // the descriptor of a one-episode plan, in parameter space
 };
 

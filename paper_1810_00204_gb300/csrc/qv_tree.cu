@@ -311,7 +311,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_count = take(sizeof(int) * D1 * E);
     L.off_result = take(sizeof(qv::ResultDev) * E);
     // counters and status words: one contiguous region, zeroed at create
-    L.off_status = take(sizeof(unsigned) * 4);
+    L.off_status = take(sizeof(unsigned) * 8);
     L.off_boundary = take(sizeof(unsigned long long));
     L.off_node_cnt = take(sizeof(unsigned) * L.NI);
     L.off_ep_cnt = take(sizeof(unsigned) * D1 * E);
@@ -353,7 +353,18 @@ qv_status launch_plan(qv_plan_t *pl, cudaStream_t st) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+#ifdef QV_BOUNDS_CHECK
+    const unsigned inject = qv_bounds_injected_site();
+    if (qv_check_cuda(cudaMemcpyToSymbolAsync(qv::g_bounds_inject, &inject, sizeof(inject), 0,
+                                              cudaMemcpyHostToDevice, st),
+                      "bounds injection") != QV_OK)
+        return QV_ERR_CUDA;
+    if (qv_check_cuda(cudaLaunchKernelEx(&cfg, qv::k_plan, pl->dev), "k_plan launch") != QV_OK) return QV_ERR_CUDA;
+    qv::k_bounds_collect<<<1, 1, 0, st>>>(pl->dev.status);
+    return qv_check_cuda(cudaGetLastError(), "k_bounds_collect launch");
+#else
     return qv_check_cuda(cudaLaunchKernelEx(&cfg, qv::k_plan, pl->dev), "k_plan launch");
+#endif
 }
 
 }  // namespace
@@ -476,6 +487,10 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.deadline_ns = params->deadline_ms > 0.0
                         ? std::max<unsigned long long>(1ull, static_cast<unsigned long long>(params->deadline_ms * 1e6))
                         : 0ull;
+    d.n_nodes = L.NT;
+    d.n_inodes = L.NI;
+    d.n_belief = L.n_belief;
+    d.ngrp_cap = static_cast<int>(L.ngrp_cap);
     d.ep0 = L.eps[0];
     pl->reset_off = L.off_status;
     // the stored beliefs too: the kernel writes zeros only where an earlier
@@ -691,6 +706,15 @@ extern "C" qv_status qv_plan_decode(qv_plan_t *pl, const void *h_buf, qv_plan_re
         o.depth_reached = r[e].pad;
     }
     if (status) pl->dirty = true;  // counters may be mid-way: the next run re-zeroes them
+    if (status & qv::kErrBounds) {
+        unsigned site = 0;
+        unsigned long long idx[2] = {0ull, 0ull};
+        std::memcpy(&site, at_host(pl->dev.status + 2), sizeof(site));
+        std::memcpy(idx, at_host(pl->dev.status + 4), sizeof(idx));
+        return qv_set_error(QV_ERR_BOUNDS, "qv_plan: device bounds check failed at site %u (%s): index %lld, limit %lld",
+                            site, qv::bounds_site_name(site), static_cast<long long>(idx[0]),
+                            static_cast<long long>(idx[1]));
+    }
     if (status & qv::kErrTimeout) return qv_set_error(QV_ERR_TIMEOUT, "qv_plan: a bounded device wait timed out");
     if (status & qv::kErrCapacity) return qv_set_error(QV_ERR_CAPACITY, "qv_plan: a level outgrew its capacity");
     return QV_OK;

@@ -51,6 +51,73 @@ constexpr int kTileFloats = kTileP + kTileC + (kTileC + 1) / 2;
 // R(b, a) sums, [10, 35) Q-weighted null masses (fused level), [35] unused.
 constexpr int kTot = 36;
 
+// Bounds-checked debug build (compiled in with -DQV_BOUNDS_CHECK, the
+// library libqvts_debug.so): QV_IN_BOUNDS(site, i, n) is false when i lies
+// outside [0, n), and the access it guards is then skipped instead of
+// faulting.  A failure is counted in g_bounds[0] and the first one is kept
+// (site, index, limit); after the kernel, k_bounds_collect moves them into
+// the plan's status words, so the call returns QV_ERR_BOUNDS with the site's
+// name.  A site equal to g_bounds_inject (host-side fault injection,
+// QVTS_FAULT=bounds) reports a failure while its index is in range, and its
+// access still runs.  In release builds the checks compile to `true`.
+enum BoundsSite : unsigned {
+    kSiteNode = 1,     // per-node records at a node id (parent, action, obs, weight, pz, code, value)
+    kSiteInode,        // per-internal-node arrays (R, UQ, samples, sample slots, child counts)
+    kSiteSlot,         // a unique draw's slot within its (node, action) run of K
+    kSiteChild,        // child numbering: child offsets and source slots
+    kSiteBelief,       // a stored belief (read or written) within the level's slots
+    kSiteCopy,         // the rows and columns of a band's bulk copies within the grid
+    kSiteRecord,       // beacon-chunk and item records
+    kSiteEpisode,      // per-episode results and level counts
+    kSiteGroup,        // expand group lists
+    kSiteCount
+};
+inline const char *bounds_site_name(unsigned site) {
+    switch (site) {
+        case kSiteNode: return "node record";
+        case kSiteInode: return "internal node arrays";
+        case kSiteSlot: return "sample slot";
+        case kSiteChild: return "child numbering";
+        case kSiteBelief: return "stored belief";
+        case kSiteCopy: return "band copy";
+        case kSiteRecord: return "chunk or item record";
+        case kSiteEpisode: return "episode result or level count";
+        case kSiteGroup: return "expand group list";
+        default: return "unknown";
+    }
+}
+#ifdef QV_BOUNDS_CHECK
+__device__ unsigned long long g_bounds[4];  // failures, first site, its index, its limit
+__device__ unsigned g_bounds_inject;
+__device__ __noinline__ void bounds_record(unsigned site, long long i, long long n) {
+    if (atomicAdd(&g_bounds[0], 1ull) == 0ull) {
+        g_bounds[1] = site;
+        g_bounds[2] = static_cast<unsigned long long>(i);
+        g_bounds[3] = static_cast<unsigned long long>(n);
+    }
+}
+__device__ __forceinline__ bool bounds_ok(unsigned site, long long i, long long n) {
+    const bool in = i >= 0 && i < n;
+    if (!in || site == *((volatile unsigned *)&g_bounds_inject)) bounds_record(site, i, n);
+    return in;
+}
+#define QV_IN_BOUNDS(site, i, n) qv::bounds_ok((site), static_cast<long long>(i), static_cast<long long>(n))
+// After k_plan on the same stream: the failure words into the plan's status
+// (status[0] |= kErrBounds, status[2] = site, status[4..5] = index,
+// status[6..7] = limit, as 64-bit words), then cleared for the next run.
+__global__ void k_bounds_collect(unsigned *status) {
+    if (g_bounds[0]) {
+        status[0] |= kErrBounds;
+        status[2] = static_cast<unsigned>(g_bounds[1]);
+        reinterpret_cast<unsigned long long *>(status + 4)[0] = g_bounds[2];
+        reinterpret_cast<unsigned long long *>(status + 4)[1] = g_bounds[3];
+    }
+    g_bounds[0] = g_bounds[1] = g_bounds[2] = g_bounds[3] = 0ull;
+}
+#else
+#define QV_IN_BOUNDS(site, i, n) true
+#endif
+
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
     size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, lut4, u_n, u_off, u_z, u_sa, u_se,
@@ -193,7 +260,9 @@ __device__ __forceinline__ int next_item(unsigned *ctr, int *slot) {
 
 __device__ __forceinline__ const float *node_belief(const PlanDev &pl, const EpDev &ep, int l, int local) {
     if (l == 0) return ep.b0;
-    return pl.beliefs + ep.belief_off[l] + static_cast<long long>(local) * ep.N;
+    const long long off = ep.belief_off[l] + static_cast<long long>(local) * ep.N;
+    if (!QV_IN_BOUNDS(kSiteBelief, off + ep.N - 1, pl.n_belief)) return ep.b0;  // debug build: a readable stand-in
+    return pl.beliefs + off;
 }
 
 // ---------------------------------------------------------------- support windows
@@ -380,6 +449,7 @@ __device__ __forceinline__ void trace_commit(const unsigned long long *t, int n)
     } while (0)
 #endif
 
+
 // Stage one band on one mbarrier: belief rows [r0-h, r1+h) of `b` (zero
 // outside the grid) into bbuf; the cell words of rows [r0-ch, r1+ch) into cw
 // (cw row i = grid row r0-ch+i); and, when q is given, rows [r0, r1) of the
@@ -397,7 +467,9 @@ __device__ bool stage_band(const EpReg &ep, const float *b, int r0, int r1, int 
             for (int i = threadIdx.x; i < P; i += blockDim.x) bbuf[(r - (r0 - h)) * P + i] = 0.0f;
     fence_proxy_async();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !(QV_IN_BOUNDS(kSiteCopy, r0, ep.H) && QV_IN_BOUNDS(kSiteCopy, r1 - 1, ep.H))) {
+        mbar_arrive_expect_tx(bar, 0u);  // debug build: no copy leaves the grid
+    } else if (threadIdx.x == 0) {
         fence_proxy_async_global();
         const int lo = max(0, r0 - h), hi = min(ep.H, r1 + h);
         const int clo = max(0, r0 - ch), chi = min(ep.H, r1 + ch);
@@ -447,6 +519,12 @@ __device__ void stage_issue(const EpReg &ep, const float *b, int r0, int r1, int
         const int lo = max(0, r0 - 2), hi = min(ep.H, r1 + 2), R = r1 - r0;
         const int nbr = hi - lo;
         const unsigned rb = static_cast<unsigned>(sw * sizeof(float)), cb = static_cast<unsigned>(sw * sizeof(uint16_t));
+        if (!(QV_IN_BOUNDS(kSiteCopy, sc0, P - sw + 1) && QV_IN_BOUNDS(kSiteCopy, r0, ep.H) &&
+              QV_IN_BOUNDS(kSiteCopy, r1 - 1, ep.H))) {
+            // debug build: no copy leaves the grid; the barrier completes empty
+            if (lane == 0) mbar_arrive_expect_tx(bar, 0u);
+            return;
+        }
         if (lane == 0)
             mbar_arrive_expect_tx(bar, static_cast<unsigned>(nbr) * (rb + cb) + (q ? 5u * R * rb : 0u));
         __syncwarp();
@@ -567,6 +645,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
                               unsigned long long code, Smem &S) {
     const int B = ep.B, nz = B + 1, K = pl.K, Bm = pl.Bmax;
     const int iid = ep.inode_base[l] + local;
+    if (!QV_IN_BOUNDS(kSiteInode, iid, pl.n_inodes)) return;  // uniform over the CTA
     const float eta = ep.eta, acc = ep.acc;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 5 * nz; i += blockDim.x) S.cnt[i] = 0;
@@ -650,7 +729,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
             const float p = z < nz ? S.P[a * nz + z] : 0.0f;
             const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
             const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (c > 0) {
+            if (c > 0 && QV_IN_BOUNDS(kSiteSlot, pos, K)) {
                 pl.slot_z[sb + pos] = z;
                 pl.slot_cnt[sb + pos] = c;
                 pl.slot_P[sb + pos] = p;
@@ -680,7 +759,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
             const int c = z < nz ? S.cnt[a * nz + z] : 0;
             const unsigned bal = __ballot_sync(0xffffffffu, c > 0);
             const int pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (c > 0) {
+            if (c > 0 && QV_IN_BOUNDS(kSiteSlot, pos, K)) {
                 const float wgt = pl.weight_mode == QV_WEIGHT_MARGINAL ? S.P[a * nz + z] / psum
                                                                         : static_cast<float>(c) / K;
                 pl.slot_w[sb + pos] = wgt;
@@ -700,7 +779,7 @@ __device__ void finalize_node(const PlanDev &pl, const EpDev &ep, int l, int loc
         }
     }
     __syncthreads();
-    if (fused && threadIdx.x == 0) {
+    if (fused && threadIdx.x == 0 && QV_IN_BOUNDS(kSiteNode, ep.node_base[l] + local, pl.n_nodes)) {
         float best = S.uq[0];
         for (int a = 1; a < 5; ++a) best = fmaxf(best, S.uq[a]);
         pl.value[ep.node_base[l] + local] = best;
@@ -724,11 +803,12 @@ __device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e
         const int v = i < M ? __ldcg(pl.nchild + ia + i) : 0;
         int total;
         const int ex = block_exclusive_scan(v, S.scan, total);
-        if (i < M) {
+        if (i < M && QV_IN_BOUNDS(kSiteChild, ia + i, 5 * pl.n_inodes)) {
             const int off = running + ex;
             pl.choff[ia + i] = off;
             for (int j = 0; j < v; ++j)
-                if (off + j < cap) pl.src_slot[ep.node_base[l + 1] + off + j] = (ia + i) * K + j;
+                if (off + j < cap && QV_IN_BOUNDS(kSiteChild, ep.node_base[l + 1] + off + j, pl.n_nodes))
+                    pl.src_slot[ep.node_base[l + 1] + off + j] = (ia + i) * K + j;
         }
         running += total;
     }
@@ -737,7 +817,8 @@ __device__ void compact_episode(const PlanDev &pl, int l, const EpDev &ep, int e
         if (threadIdx.x == 0) atomicOr(pl.status, kErrCapacity);
         nn = cap;
     }
-    if (threadIdx.x == 0) pl.count[(l + 1) * pl.E + e] = nn;
+    if (threadIdx.x == 0 && QV_IN_BOUNDS(kSiteEpisode, (l + 1) * pl.E + e, (pl.depth + 1) * pl.E))
+        pl.count[(l + 1) * pl.E + e] = nn;
     __syncthreads();
 }
 
@@ -1065,6 +1146,7 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
 #endif
         QV_TRACE_MARK(tr, 2);
         const int j = block_find(goff, G, w, S.flags + 6);
+        if (!QV_IN_BOUNDS(kSiteGroup, pl.gbase[l] + j, pl.ngrp_cap)) return true;  // uniform over the CTA
         int e = j, lp = 0;
         if (l > 0) {
             e = block_find(np, E, j, S.flags + 7);
@@ -1088,6 +1170,7 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
         const float *src = ep.b0;
         if (l > 0) {
             const long long ia = static_cast<long long>(ep.inode_base[l - 1] + lp) * 5;
+            if (!QV_IN_BOUNDS(kSiteInode, ep.inode_base[l - 1] + lp, pl.n_inodes)) return true;
             const int cnt = __ldcg(pl.count + l * E + e);
             c0 = min(__ldcg(pl.choff + ia), cnt);
             const int c1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
@@ -1106,8 +1189,20 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
         if (l > 0) {
             for (int r = threadIdx.x; r < nc; r += blockDim.x) {
                 const int gid = ep.node_base[l] + c0 + r;
+                if (!QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) {
+                    S.c_pa[r] = 0;
+                    S.c_z[r] = 0;
+                    S.c_sa[r] = S.c_se[r] = 0.0f;
+                    continue;
+                }
                 // the child's sample record in its parent's arrays: (iid_p * 5 + a) * K + j
                 const long long s = __ldcg(pl.src_slot + gid);
+                if (!QV_IN_BOUNDS(kSiteSlot, s, 5 * K * pl.n_inodes)) {
+                    S.c_pa[r] = 0;
+                    S.c_z[r] = 0;
+                    S.c_sa[r] = S.c_se[r] = 0.0f;
+                    continue;
+                }
                 const int a = static_cast<int>((s / K) % 5);
                 const int z = __ldcg(pl.slot_z + s);
                 const float p = __ldcg(pl.slot_P + s);
@@ -1134,6 +1229,9 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
         const float slip = er.slip;
         const float *cost = er.cost;
         float *dst0 = (l > 0 && store) ? pl.beliefs + ep.belief_off[l] : nullptr;
+        if (dst0 && !QV_IN_BOUNDS(kSiteBelief, ep.belief_off[l] + static_cast<long long>(c0 + nc) * ep.N - 1,
+                                  pl.n_belief))
+            dst0 = nullptr;  // debug build: the children are not stored
         for (int band = band0; band < band1; ++band) {
             const int r0 = geo.r0 + band * geo.rows, r1 = min(geo.r1, r0 + geo.rows), R = r1 - r0;
             const int qstride = R * SW;
@@ -1938,6 +2036,9 @@ __device__ bool phase_update(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, 
                         o.y = outs[1][a] * (lab[1] == z ? sa : se);
                         o.z = outs[2][a] * (lab[2] == z ? sa : se);
                         o.w = outs[3][a] * (lab[3] == z ? sa : se);
+                        if (!QV_IN_BOUNDS(kSiteBelief, ep.belief_off[l + 1] + static_cast<long long>(c) * N + y + 3,
+                                          pl.n_belief))
+                            continue;
                         __stcs(reinterpret_cast<float4 *>(child0 + static_cast<long long>(c) * N + y), o);
                     }
                 }
@@ -2062,6 +2163,7 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                     ba = a;
                 }
             }
+            if (!QV_IN_BOUNDS(kSiteNode, ep.node_base[l] + first + i, pl.n_nodes)) return;
             pl.value[ep.node_base[l] + first + i] = best;
             pl.leaf_arg[ep.node_base[l] + first + i] = ba;
             if (l == 0) {  // depth-0 plan: the root is the leaf
@@ -2070,7 +2172,7 @@ __device__ void phase_leaf(const PlanDev &pl, int l, Smem &S, int &cur_e) {
                 r.value = best;
                 for (int a = 0; a < 5; ++a) r.q[a] = sums[a];
                 r.pad = 0;
-                pl.result[e] = r;
+                if (QV_IN_BOUNDS(kSiteEpisode, e, pl.E)) pl.result[e] = r;
             }
         }
         __syncthreads();
@@ -2087,6 +2189,7 @@ __device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep,
     const int K = pl.K, nz = ep.B + 1;
     const int node = t / (5 * K), a = (t / K) % 5, j = t % K;
     const long long ia = static_cast<long long>(ep.inode_base[l] + node) * 5 + a;
+    if (!QV_IN_BOUNDS(kSiteInode, ep.inode_base[l] + node, pl.n_inodes)) return;
     const int m = __ldcg(pl.nchild + ia);
     if (j >= m) return;
     const int off = __ldcg(pl.choff + ia);
@@ -2102,6 +2205,7 @@ __device__ __forceinline__ void leaf_records(const PlanDev &pl, const EpDev &ep,
         arg = __ldcg(pl.slot_arg + sb);
     }
     const int g = ep.node_base[l + 1] + off + j;
+    if (!QV_IN_BOUNDS(kSiteNode, g, pl.n_nodes)) return;
     pl.parent[g] = node;
     pl.action[g] = a;
     pl.obs[g] = z;
@@ -2192,7 +2296,7 @@ __device__ void phase_backup(const PlanDev &pl, Smem &S, int &cur_e, int D) {
             for (int a = 0; a < 5; ++a) r.q[a] = q[a];
             r.value = __ldcg(pl.value + ep.node_base[0]);
             r.pad = D;  // the depth reached
-            pl.result[e] = r;
+            if (QV_IN_BOUNDS(kSiteEpisode, e, pl.E)) pl.result[e] = r;
         }
         __syncthreads();
     }

@@ -180,3 +180,11 @@ def test_injected_faults_are_reported_before_any_device_work(libpath, monkeypatc
     assert L.belief_predict(ctypes.byref(m), fake, 0, fake, None) == N.QV_ERR_INVALID
     assert b"QVTS_FAULT=invalid" in L.qv_last_error()
     assert not h.value
+
+
+def test_debug_build_exports_the_same_symbols():
+    """The bounds-checked build (-DQV_BOUNDS_CHECK) compiles and has the same ABI."""
+    from paper_1810_00204_gb300 import build
+    L = ctypes.CDLL(build.build(debug=True))
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, missing

@@ -75,12 +75,14 @@ def _gpu_samples_flat(plan, depth, K, B):
 
 
 def _tree_case(api, w, depth, K, sweeps, leaf_mode, every=16):
-    """GPU VI (checkpointed) and plan; the oracle tree on the GPU's Q with its
-    own samples, replayed into the GPU plan so both trees are the same."""
+    """GPU VI (checkpointed) and plan on the GPU's Q; the oracle tree on the
+    oracle's own Q of the same truncated VI, with its own samples, replayed
+    into the GPU plan so both trees are the same."""
     m = api.Model(w)
     vi = api.mdp_value_iterate_checkpointed(m, sweeps, every)
-    Qf = m.from_grid(vi["Q"]).reshape(5, -1).astype(np.float64)
     p = _prob(w)
+    Qf = O.value_iteration(p, truncated=sweeps)["Q"]
+    _close(m.from_grid(vi["Q"]).reshape(5, -1), Qf, 1e-6, floor=1.0, what="Q of the truncated VI")
     o = O.tree_plan(p, Qf, depth=depth, K=K, store_levels=max(depth - 1, 0))
     rep = torch.from_numpy(o["samples_flat"].copy()).cuda()
     r, plan = api.qv_tree_plan(m, vi["Q"], m.b0(), depth=depth, K=K, seed=w.seed, episode=w.episode,

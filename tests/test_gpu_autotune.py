@@ -39,9 +39,10 @@ def _vi(api, m):
 def test_every_launch_shape_gives_the_oracle_tree(api, band_cells, items):
     w = WL.mid(0)
     m = api.Model(w)
-    Q = _vi(api, m)
-    Qf = m.from_grid(Q).reshape(5, -1).astype(np.float64)
-    o = O.tree_plan(w, Qf)
+    Q = _vi(api, m)  # the GPU's VI runs; the plans take the oracle's Q (in FP32)
+    Qo = O.value_iteration(w)["Q"].astype(np.float32)
+    Q = m.to_grid(Qo.reshape(5, w.H, w.W))
+    o = O.tree_plan(w, Qo.astype(np.float64))
     rep = torch.from_numpy(o["samples_flat"].copy()).cuda()
     for leaf_mode in (0, 1):
         p = api.Plan([m], [Q], [m.b0()], depth=w.depth, K=w.K, seed=w.seed, leaf_mode=leaf_mode, replay=rep,

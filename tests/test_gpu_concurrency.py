@@ -23,7 +23,7 @@ def api():
 def _setup(api, n=12):
     w = WL.mid(0)
     m = api.Model(w)
-    Q = api.mdp_value_iterate(m, dtype="f32")["Q"]
+    Q = m.to_grid(O.value_iteration(w)["Q"].astype(np.float32).reshape(5, w.H, w.W))  # the oracle's Q
     eps = WL.episodes(w, n, seed=3)
     return w, m, Q, eps, [m.to_grid(e.b0) for e in eps]
 
@@ -64,7 +64,7 @@ def test_concurrent_streams_match_one_stream(api):
         for s in streams:
             main.wait_stream(s)
     torch.cuda.synchronize()
-    Qh = m.from_grid(Q).reshape(5, -1).astype(np.float64)
+    Qh = O.value_iteration(w)["Q"].astype(np.float32).astype(np.float64)  # the plans' Q
     for i, (p, q) in enumerate(zip(seq, con)):
         a, b = p.read()[0], q.read()[0]
         assert a["nodes_per_level"] == b["nodes_per_level"] and a["action"] == b["action"]

@@ -131,11 +131,12 @@ def test_closed_loop_mid_map(api):
     w = WL.mid(0)
     m = api.Model(w)
     eps = WL.episodes(w, 16, seed=5)
-    vi = api.mdp_value_iterate(m, dtype="f32")
+    Qo = O.value_iteration(w)["Q"].astype(np.float32)  # the oracle's Q feeds both sides
+    vi = {"Q": m.to_grid(Qo.reshape(5, w.H, w.W))}
     g = api.run_episodes(m, vi["Q"], [m.to_grid(e.b0) for e in eps], [e.start for e in eps], depth=3, K=8,
                          seed=w.seed, max_steps=60)
     assert g["steps"].max() <= 60 and set(np.unique(g["success"])) <= {0, 1}
-    Qh = m.from_grid(vi["Q"]).reshape(5, -1).astype(np.float64)
+    Qh = Qo.astype(np.float64)
     o = O.closed_loop(w, Qh, [eps[0].b0, eps[1].b0], [eps[0].start, eps[1].start], depth=3, K=8, max_steps=60)
     # episodes 0 and 1 of a 2-episode oracle run use episode words t * 2 + e;
     # the GPU run's are t * 16 + e, so compare against a GPU run of the same two

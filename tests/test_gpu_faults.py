@@ -26,7 +26,8 @@ def test_plan_timeout_is_reported_and_the_plan_recovers(api, monkeypatch):
     from paper_1810_00204_gb300 import _native as N
     w = WL.tiny(0)
     m = api.Model(w)
-    Q = api.mdp_value_iterate(m, dtype="f64", tol=w.vi_tol)["Q"]
+    Qo = O.value_iteration(w)["Q"].astype(np.float32)  # the oracle's Q feeds both sides
+    Q = m.to_grid(Qo.reshape(5, w.H, w.W))
     p = api.Plan([m], [Q], [m.b0()], depth=w.depth, K=w.K, seed=w.seed)
     p.run()
     ref = p.read()[0]
@@ -41,8 +42,7 @@ def test_plan_timeout_is_reported_and_the_plan_recovers(api, monkeypatch):
     got = p.read()[0]
     assert got["nodes_per_level"] == ref["nodes_per_level"]
     assert got["value"] == ref["value"] and got["action"] == ref["action"]
-    Qf = m.from_grid(Q).reshape(5, -1).astype(np.float64)
-    o = O.tree_plan(w, Qf)
+    o = O.tree_plan(w, Qo.astype(np.float64))
     assert abs(got["value"] - o["root_value"]) <= 1e-5 * max(1.0, abs(o["root_value"]))
 
 
@@ -92,7 +92,8 @@ def test_injected_host_faults_and_recovery(api, monkeypatch, mode, status):
     code = getattr(N, status)
     w = WL.tiny(2)
     m = api.Model(w)
-    Q = api.mdp_value_iterate(m, dtype="f64", tol=w.vi_tol)["Q"]
+    Qo = O.value_iteration(w)["Q"].astype(np.float32)  # the oracle's Q feeds both sides
+    Q = m.to_grid(Qo.reshape(5, w.H, w.W))
     b = m.b0()
     monkeypatch.setenv("QVTS_FAULT", mode)
     for call in (lambda: api.mdp_value_iterate(m, dtype="f32"),
@@ -107,7 +108,7 @@ def test_injected_host_faults_and_recovery(api, monkeypatch, mode, status):
     p = api.Plan([m], [Q], [b], depth=w.depth, K=w.K, seed=w.seed)
     p.run()
     r = p.read()[0]
-    o = O.tree_plan(w, m.from_grid(Q).reshape(5, -1).astype(np.float64))
+    o = O.tree_plan(w, Qo.astype(np.float64))
     assert abs(r["value"] - o["root_value"]) <= 1e-5 * max(1.0, abs(o["root_value"]))
     out, pz = api.belief_correct(m, b, 0)
     assert torch.isfinite(out).all()

@@ -83,9 +83,9 @@ def large_case(api):
     assert vi["status"] == 0
     ovi = O.value_iteration(w, truncated=vi["sweeps"])
     _close(m.from_grid(vi["V"]), ovi["V"], what="large V")
-    Qf = m.from_grid(vi["Q"]).reshape(5, -1)  # the GPU's own Q feeds both sides
+    Qf = ovi["Q"].astype(np.float32)  # the oracle's Q (in FP32) feeds both sides
     o = O.tree_plan(w, Qf.astype(np.float64))
-    return w, m, vi["Q"], o
+    return w, m, m.to_grid(Qf.reshape(5, w.H, w.W)), o
 
 
 @pytest.mark.parametrize("leaf_mode", [0, 1])
@@ -103,27 +103,31 @@ def test_large_tree(api, large_case, leaf_mode):
 def test_batched_256_episodes(api):
     ws = WL.batched(0, E=256)
     ms = [api.Model(w) for w in ws]
-    Qs = []
-    for m in ms:
-        vi = api.mdp_value_iterate(m, dtype="f32")
-        assert vi["status"] == 0
-        Qs.append(vi["Q"])
-    b0s = [m.b0() for m in ms]
-    plan = api.Plan(ms, Qs, b0s, depth=3, K=8, seed=0, episode=0)
-    plan.run()
-    res = plan.read()
-    assert len(res) == 256
     cells = np.array([w.H * w.W for w in ws])
     order = np.argsort(cells, kind="stable")
     rng = np.random.default_rng(1)
     rest = rng.choice(order[2:-2], size=28, replace=False)
     picked = sorted(set(order[:2].tolist() + order[-2:].tolist() + rest.tolist()))
     assert len(picked) == 32
+    # the checked episodes plan on the oracle's Q (in FP32), the others on the GPU's
+    Qs, Qo = [], {}
+    for e, m in enumerate(ms):
+        vi = api.mdp_value_iterate(m, dtype="f32")
+        assert vi["status"] == 0
+        if e in picked:
+            Qo[e] = O.value_iteration(ws[e])["Q"].astype(np.float32)
+            Qs.append(m.to_grid(Qo[e].reshape(5, ws[e].H, ws[e].W)))
+        else:
+            Qs.append(vi["Q"])
+    b0s = [m.b0() for m in ms]
+    plan = api.Plan(ms, Qs, b0s, depth=3, K=8, seed=0, episode=0)
+    plan.run()
+    res = plan.read()
+    assert len(res) == 256
     replayed = 0
     for e in picked:
         w, m = ws[e], ms[e]
-        Qf = m.from_grid(Qs[e]).reshape(5, -1).astype(np.float64)
-        o = O.tree_plan(w, Qf, depth=3, K=8, seed=0, episode=int(e))
+        o = O.tree_plan(w, Qo[e].astype(np.float64), depth=3, K=8, seed=0, episode=int(e))
         if _samples_agree(plan, e, o, 3):
             _check_levels(plan, e, o, 3, f"episode {e}")
             _check_root(res[e], o, f"episode {e}")

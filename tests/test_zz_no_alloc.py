@@ -46,7 +46,8 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls(mods, make):
     for call, z in enumerate((2, w.B)):
         b = rng.random(w.H * w.W) * (1 - w.occ.ravel())
         b = (b / b.sum()).astype(np.float32)
-        bbar = api.belief_predict(m, m.to_grid(b.reshape(w.H, w.W)), call)
+        bbar_o = O.predict(w, b.astype(np.float64), call).astype(np.float32)  # the oracle's prediction
+        bbar = m.to_grid(bbar_o.reshape(w.H, w.W))
         ref, ref_pz = api.belief_correct(m, bbar, z)
         out.fill_(-1.0)
         pz.fill_(-1.0)
@@ -58,7 +59,7 @@ def test_noalloc_matches_workspace_version_on_consecutive_calls(mods, make):
         assert abs(pz.item() - ref_pz.item()) <= REL * abs(ref_pz.item()), f"call {call}"
         assert o[:, w.W:].max(initial=0.0) == 0.0  # padding columns stay empty
         # and directly against the oracle's Bayes update of the same bbar
-        ob, opz = O.correct(w, m.from_grid(bbar).astype(np.float64), z)
+        ob, opz = O.correct(w, bbar_o.astype(np.float64), z)
         assert np.abs(o[:, :w.W].ravel() - ob).max() <= REL * np.abs(ob).max(), f"call {call} vs oracle"
         assert abs(pz.item() - opz) <= REL * abs(opz), f"call {call} P(z) vs oracle"
 
