@@ -1061,6 +1061,63 @@ class BatchedArm:
         return time_device(self.step, steps, self.flush, self.stream)
 
 
+def e2e_pipelined(api, arm, b0_all, models, Qs, episodes, w, leaf_mode, use_graph, flush, stream, n):
+    """End to end through the public API with host buffers, as a serving loop
+    runs it: every step copies its R start beliefs in from pinned host memory
+    (one transfer of the [R][H][P] batch, on a copy stream), flushes L2, runs
+    the batched plan and copies its results back into pinned memory; the host
+    decodes them.  Two plans on two device batches alternate, so step k's
+    copy in overlaps step k - 1's plan and the host decodes step k - 1 while
+    step k runs.  Every copy, flush, launch and decode is inside the timed
+    region; value = R n / wall time."""
+    import torch
+    pinned = b0_all.cpu().pin_memory()
+    b0_b = torch.empty_like(b0_all)
+    other = api.Plan(models, Qs, list(b0_b.unbind(0)), depth=w.depth, K=w.K, seed=w.seed, episode=episodes[0],
+                     leaf_mode=leaf_mode)
+    if use_graph:
+        other.capture_graph()
+    plans, bufs = [arm.plan, other], [b0_all, b0_b]
+    rbufs = [p.readback_buffer() for p in plans]
+    cs = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    R = b0_all.shape[0]
+
+    def loop(steps):
+        got, pending = [], None
+        for k in range(steps):
+            j = k & 1
+            if k >= 2:
+                cs.wait_event(done[j])  # plan j's previous run has read its batch
+            with torch.cuda.stream(cs):
+                bufs[j].copy_(pinned, non_blocking=True)
+                copied[j].record(cs)
+            stream.wait_event(copied[j])
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            plans[j].run(stream)
+            plans[j].read_async(rbufs[j], stream)
+            done[j].record(stream)
+            if pending is not None:
+                done[pending].synchronize()
+                got = plans[pending].decode(rbufs[pending])
+            pending = j
+        done[pending].synchronize()
+        return plans[pending].decode(rbufs[pending])
+
+    loop(4)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    got = loop(n)
+    t = time.perf_counter() - t0
+    assert len(got) == R and all(g["nodes_per_level"][0] == 1 for g in got)
+    return {"value": R * n / t, "unit": "plans/s", "h2d_bytes_per_step": int(b0_all.numel() * 4),
+            "d2h_bytes_per_step": int(rbufs[0].numel()), "steps": n,
+            "note": "pinned [R][H][P] batch in (one copy), L2 flush, batched plan, results out and decoded, "
+                    "every step; two plans alternate so a step's copy in overlaps the previous step's plan"}
+
+
 def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_plan, flush, reps, peak, peak_kind,
                   alu_peak, cells, job_plans_per_s=None, nodes_avg=None):
     """The dominant kernel (k_plan, the whole plan in one launch) against its
@@ -1191,7 +1248,10 @@ def main():
     fib, fib_first_ms, fib_ms = time_offline(lambda: api.fib_value_iterate(model, dtype="f32", want_alpha=False))
     Qd = vi["Q"]
     leaf_mode = N.QV_LEAF_FUSED if args.leaf_mode == "fused" else N.QV_LEAF_MATERIALISE
-    b0s = [model.to_grid(e.b0) for e in eps]
+    # the step's start beliefs as one device batch [R][H][P] (views per request),
+    # so that the end-to-end leg copies a step's inputs in with one transfer
+    b0_all = torch.stack([model.to_grid(e.b0) for e in eps])
+    b0s = list(b0_all.unbind(0))
     # launch-shape autotuner (offline, like the value iteration): the choice is
     # cached in the library and taken by the plans created below
     tune = None
@@ -1310,7 +1370,11 @@ def main():
     # end to end through the public API with host buffers: pinned b0 -> device,
     # run, results -> host, every step
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and arm is batched:
+        e2e = e2e_pipelined(api, arm, b0_all, [model] * R, [Qd] * R, [e.episode for e in eps], w, leaf_mode,
+                            use_graph, flush, stream, max(3, min(K, 200)))
+        e2e["value"] = replicas.reduce_sum(e2e["value"], dev) if world_size > 1 else e2e["value"]
+    elif not args.no_e2e:
         pinned = [torch.from_numpy(np.ascontiguousarray(
             np.pad(e.b0.astype(np.float32), ((0, 0), (0, model.P - model.W))))).pin_memory() for e in eps]
         h2d = sum(p.numel() * 4 for p in pinned)

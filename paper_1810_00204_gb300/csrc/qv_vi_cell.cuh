@@ -148,6 +148,21 @@ __device__ __forceinline__ T arrive_value(const Args &a, int y, const T *Vs_row,
     return r + a.gamma * Vs_row[col];
 }
 
+// Q_a(x) for the 5 actions from the arrival values r(y) + gamma V(y) of x
+// (wx) and of its four neighbours (wn, taken only where the move is not
+// blocked; a blocked move stays at x).
+template <typename T>
+__device__ __forceinline__ void q_from_arrivals(unsigned blk, T wx, T wn[4], float slip, T q[5]) {
+    if (blk & 1u) wn[kDirN] = wx;
+    if (blk & 2u) wn[kDirE] = wx;
+    if (blk & 4u) wn[kDirS] = wx;
+    if (blk & 8u) wn[kDirW] = wx;
+    const T fwd = T(1) - T(2) * T(slip), eps = T(slip);
+#pragma unroll
+    for (int d = 0; d < 4; ++d) q[d] = fwd * wn[d] + eps * (wn[(d + 1) & 3] + wn[(d + 3) & 3]);
+    q[4] = wx;
+}
+
 // Q_a(x) for the 5 actions of a free, non-goal cell, V staged in smem rows
 // (row stride P) where `rowp` points at x's row.
 template <typename T, typename Args>
@@ -160,10 +175,7 @@ __device__ __forceinline__ void cell_q(const Args &a, int y, int col, unsigned c
     wn[kDirE] = (blk & 2u) ? wx : arrive_value(a, y + 1, rowp, col + 1);
     wn[kDirS] = (blk & 4u) ? wx : arrive_value(a, y + a.P, rowp + a.P, col);
     wn[kDirW] = (blk & 8u) ? wx : arrive_value(a, y - 1, rowp, col - 1);
-    const T fwd = T(1) - T(2) * T(a.slip), eps = T(a.slip);
-#pragma unroll
-    for (int d = 0; d < 4; ++d) q[d] = fwd * wn[d] + eps * (wn[(d + 1) & 3] + wn[(d + 3) & 3]);
-    q[4] = wx;
+    q_from_arrivals(blk, wx, wn, a.slip, q);
 }
 
 }  // namespace qv
