@@ -43,7 +43,7 @@ namespace qv {
 // Per-warp buffers of the label histograms (phase_finalize): a tile of
 // kTileH x kTileW cells of the node's belief is formed from the parent's
 // belief with a two-cell rim, its cell words with a one-cell rim.
-constexpr int kTileH = 8, kTileW = 28;
+constexpr int kTileH = 17, kTileW = 18;  // one tile holds a range-8 diamond's 17 x 17 box
 constexpr int kTileP = (kTileH + 4) * (kTileW + 4);   // parent values
 constexpr int kTileC = (kTileH + 2) * (kTileW + 2);   // node values, cell words
 constexpr int kTileFloats = kTileP + kTileC + (kTileC + 1) / 2;
@@ -1551,59 +1551,69 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
     const int clo = max(max(0, bc - R), win.c0), chi = min(min(W - 1, bc + R), win.c1 - 1);
     constexpr int PW = kTileW + 4, CW = kTileW + 2;
     constexpr int NP = (kTileP + 31) / 32, NC = (kTileC + 31) / 32, ND = (kTileH * kTileW + 31) / 32;
+    constexpr int kLoadBatch = 8;  // loads in flight per lane (the values wait in registers)
     for (int y0 = rlo; y0 <= rhi; y0 += kTileH) {
         for (int x0 = clo; x0 <= chi; x0 += kTileW) {
             __syncwarp();
-            // the tile's global loads issued a batch at a time, before any is used
+            // the tile's global loads issued kLoadBatch at a time, before any
+            // of the batch is used (only the diamond's box and its rims)
             if (root) {
                 // b0 on the tile and its rim, with the cell words
-                uint16_t cv[NC];
-                float bv[NC];
+#pragma unroll 1
+                for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
+                    uint16_t cv[kLoadBatch];
+                    float bv[kLoadBatch];
 #pragma unroll
-                for (int u = 0; u < NC; ++u) {
-                    const int i = lane + 32 * u, rr = i / CW, cc = i - rr * CW;
-                    const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                    const bool in = i < kTileC && r >= 0 && r < H && c >= 0 && c < P;
-                    cv[u] = in ? __ldg(ep.cell + static_cast<size_t>(r) * P + c) : static_cast<uint16_t>(0);
-                    bv[u] = in ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
-                }
+                    for (int v = 0; v < kLoadBatch; ++v) {
+                        const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
+                        const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                        const bool in = u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P &&
+                                        r <= rhi + 1 && c <= chi + 1;
+                        cv[v] = in ? __ldg(ep.cell + static_cast<size_t>(r) * P + c) : static_cast<uint16_t>(0);
+                        bv[v] = in ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
+                    }
 #pragma unroll
-                for (int u = 0; u < NC; ++u) {
-                    const int i = lane + 32 * u;
-                    if (i < kTileC) {
-                        tcw[i] = cv[u];
-                        tc[i] = QV_CELL_FREE(static_cast<unsigned>(cv[u])) ? bv[u] : 0.0f;
+                    for (int v = 0; v < kLoadBatch; ++v) {
+                        const int i = lane + 32 * (u0 + v);
+                        if (u0 + v < NC && i < kTileC) {
+                            tcw[i] = cv[v];
+                            tc[i] = QV_CELL_FREE(static_cast<unsigned>(cv[v])) ? bv[v] : 0.0f;
+                        }
                     }
                 }
                 __syncwarp();
             } else {
-                {
-                    float pv[NP];
+#pragma unroll 1
+                for (int u0 = 0; u0 < NP; u0 += kLoadBatch) {
+                    float pv[kLoadBatch];
 #pragma unroll
-                    for (int u = 0; u < NP; ++u) {
-                        const int i = lane + 32 * u, rr = i / PW, cc = i - rr * PW;
+                    for (int v = 0; v < kLoadBatch; ++v) {
+                        const int i = lane + 32 * (u0 + v), rr = i / PW, cc = i - rr * PW;
                         const int r = y0 - 2 + rr, c = x0 - 2 + cc;
-                        pv[u] = (i < kTileP && r >= 0 && r < H && c >= 0 && c < P)
+                        pv[v] = (u0 + v < NP && i < kTileP && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 2 &&
+                                 c <= chi + 2)
                                     ? __ldcg(par + static_cast<size_t>(r) * P + c)
                                     : 0.0f;
                     }
 #pragma unroll
-                    for (int u = 0; u < NP; ++u)
-                        if (lane + 32 * u < kTileP) tp[lane + 32 * u] = pv[u];
+                    for (int v = 0; v < kLoadBatch; ++v)
+                        if (u0 + v < NP && lane + 32 * (u0 + v) < kTileP) tp[lane + 32 * (u0 + v)] = pv[v];
                 }
-                {
-                    uint16_t cv[NC];
+#pragma unroll 1
+                for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
+                    uint16_t cv[kLoadBatch];
 #pragma unroll
-                    for (int u = 0; u < NC; ++u) {
-                        const int i = lane + 32 * u, rr = i / CW, cc = i - rr * CW;
+                    for (int v = 0; v < kLoadBatch; ++v) {
+                        const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
                         const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                        cv[u] = (i < kTileC && r >= 0 && r < H && c >= 0 && c < P)
+                        cv[v] = (u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 &&
+                                 c <= chi + 1)
                                     ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
                                     : static_cast<uint16_t>(0);
                     }
 #pragma unroll
-                    for (int u = 0; u < NC; ++u)
-                        if (lane + 32 * u < kTileC) tcw[lane + 32 * u] = cv[u];
+                    for (int v = 0; v < kLoadBatch; ++v)
+                        if (u0 + v < NC && lane + 32 * (u0 + v) < kTileC) tcw[lane + 32 * (u0 + v)] = cv[v];
                 }
                 __syncwarp();
                 // the node's belief on the tile and its rim
@@ -1611,7 +1621,7 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
                     const int rr = i / CW, cc = i - rr * CW;
                     const int r = y0 - 1 + rr, c = x0 - 1 + cc;
                     float v = 0.0f;
-                    if (r >= 0 && r < H && c >= 0 && c < P) {
+                    if (r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 && c <= chi + 1) {
                         const unsigned cw = tcw[i];
                         const float *m = tp + (rr + 1) * PW + (cc + 1);
                         const unsigned in = QV_CELL_INFLOW(cw);
@@ -1632,7 +1642,7 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
             // (fused) and the predicted masses
             int *list = reinterpret_cast<int *>(tp);
             int nh = 0;
-#pragma unroll
+#pragma unroll 1
             for (int u = 0; u < ND; ++u) {
                 const int i = lane + 32 * u, rr = i / kTileW, cc = i - rr * kTileW;
                 const int r = y0 + rr, c = x0 + cc;
