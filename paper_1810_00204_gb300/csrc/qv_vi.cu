@@ -294,10 +294,12 @@ __global__ void __launch_bounds__(kVIBThreads) k_vi_blocked(VIArgs<T> a) {
     const int glo = max(0, base), ghi = min(H, base + nrows);  // grid rows held
     const size_t nb = static_cast<size_t>(nrows) * P;
     // V_k and the arrival values A_k(y) = r(y) + gamma V_k(y), two of each
-    // (ping-pong), and the cell words of the rows held
+    // (ping-pong), the arrival rewards r(y) and the cell words of the rows
+    // held (the goal's free bit cleared there: the goal is never updated)
     T *const V0s = reinterpret_cast<T *>(smem_raw), *const V1s = V0s + nb;
     T *const A0s = V0s + 2 * nb, *const A1s = V0s + 3 * nb;
-    uint16_t *cws = reinterpret_cast<uint16_t *>(V0s + 4 * nb);
+    T *const rws = V0s + 4 * nb;
+    uint16_t *cws = reinterpret_cast<uint16_t *>(V0s + 5 * nb);
     const size_t plane = static_cast<size_t>(H) * P;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // division-free cell walk: thread (rsub, c0) visits rows rsub, rsub +
@@ -312,9 +314,13 @@ __global__ void __launch_bounds__(kVIBThreads) k_vi_blocked(VIArgs<T> a) {
         mbar_init(&bar, 1);
         fence_barrier_init();
     }
-    // the cell words of every row held, once (they do not change)
-    for (int i = threadIdx.x; i < (ghi - glo) * P; i += blockDim.x)
-        cws[(glo - base) * P + i] = __ldg(a.cell + static_cast<size_t>(glo) * P + i);
+    // the cell words and arrival rewards of every row held, once (they do not change)
+    for (int i = threadIdx.x; i < (ghi - glo) * P; i += blockDim.x) {
+        const int y = glo * P + i;
+        const uint16_t cw = __ldg(a.cell + y);
+        cws[(glo - base) * P + i] = y == a.goal ? static_cast<uint16_t>(cw & 0x7FFFu) : cw;
+        rws[(glo - base) * P + i] = arrive_reward(a, y);
+    }
     if (a.ckpt)  // V_0
         for (int i = r_begin * P + threadIdx.x; i < r_end * P; i += blockDim.x) a.ckpt[i] = a.V0[i];
     __syncthreads();
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(kVIBThreads) k_vi_blocked(VIArgs<T> a) {
             for (int row = glo + rsub; row < ghi; row += rstep)
                 for (int col = c0; col < P; col += cstep) {
                     const int t = (row - base) * P + col;
-                    A0s[t] = arrive_reward(a, row * P + col) + a.gamma * V0s[t];
+                    A0s[t] = rws[t] + a.gamma * V0s[t];
                 }
         __syncthreads();
         int cur = 0;
@@ -382,16 +388,14 @@ __global__ void __launch_bounds__(kVIBThreads) k_vi_blocked(VIArgs<T> a) {
                         const int y = row * P + col;
                         const unsigned cw = cws[t];
                         T v = T(0);
-                        if (QV_CELL_FREE(cw) && y != a.goal) {
+                        if (QV_CELL_FREE(cw)) {  // free and not the goal
                             T wn[4] = {Ac[t - P], Ac[t + 1], Ac[t + P], Ac[t - 1]};
                             T q[5];
                             q_from_arrivals(QV_CELL_BLOCKED(cw), Ac[t], wn, a.slip, q);
-                            v = q[0];
-#pragma unroll
-                            for (int d = 1; d < 5; ++d) v = q[d] > v ? q[d] : v;
+                            v = fmax(fmax(fmax(q[0], q[1]), fmax(q[2], q[3])), q[4]);
                         }
                         Vn[t] = v;
-                        An[t] = arrive_reward(a, y) + a.gamma * v;
+                        An[t] = rws[t] + a.gamma * v;
                         if (own) {
                             const T diff = fabs(v - Vc[t]);
                             lm = diff > lm ? diff : lm;
@@ -515,7 +519,7 @@ bool vi_block_shape(int H, int P, int nsm, int &G, int &R, int &s, int &nh, size
     for (int c : {8, 4, 2, 1}) {
         if (forced > 0 && c != forced) continue;
         const int h = (c + R - 1) / R;
-        const size_t sm = static_cast<size_t>(R + 2 * c) * P * (4 * sizeof(T) + sizeof(uint16_t));
+        const size_t sm = static_cast<size_t>(R + 2 * c) * P * (5 * sizeof(T) + sizeof(uint16_t));
         if (2 * h > 32 || sm > 200 * 1024) continue;
         const double t = xb / c + cb * static_cast<double>(R + c - 1) * P + ob;
         if (t < best) {
