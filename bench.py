@@ -385,6 +385,28 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
             "workspace_GB": batched_arm.plan.workspace_bytes / 1e9,
             "note": "the headline's requests (same map, b0s, seeds and episode words): one batched launch against "
                     "one launch per plan on streams"}
+    # (1b) the headline's workload with more requests per batched launch: the
+    # deepest level's work grows with the batch, the upper levels' latency
+    # chain is shared by more plans
+    scaling = {}
+    for R2 in (64, 128):
+        eps2 = WL.episodes(w, R2, seed=args.seed)
+        b02 = [model.to_grid(e.b0) for e in eps2]
+        api.autotune([model] * R2, [Qd] * R2, b02, depth=w.depth, K=w.K, seed=w.seed, episode=eps2[0].episode,
+                     leaf_mode=leaf_mode, reps=3)
+        p2 = api.Plan([model] * R2, [Qd] * R2, b02, depth=w.depth, K=w.K, seed=w.seed, episode=eps2[0].episode,
+                      leaf_mode=leaf_mode)
+        p2.capture_graph()
+        for _ in range(3):
+            p2.run()
+        ms2 = time_device(p2.run, K, flush, stream)
+        scaling[str(R2)] = {"plans_per_s": R2 * K / (ms2 / 1e3), "ms_per_launch": ms2 / K, "tuning": p2.tuning,
+                            "workspace_GB": p2.workspace_bytes / 1e9}
+        del p2, b02
+        torch.cuda.empty_cache()
+    out["batch_size_scaling"] = dict(scaling, note="plans per batched launch on the headline's map (episodes of "
+                                                   "the same generator, L2 flushed before every launch); the "
+                                                   "headline keeps the step's requests per launch")
     # (2) 256 independent episodes on maps of uneven size: one launch per
     # step against one launch per episode, the same episodes
     ws = WL.batched(args.seed, E=256)

@@ -621,14 +621,8 @@ extern "C" qv_status qv_plan_profile(qv_plan_t *pl, qv_launch_time_t *out, int32
             int level;
         };
         std::vector<Ph> ph;
-        for (int l = 0; l < D; ++l) {
-            if (l == D - 1 && !mat) {  // one phase: expand and finalize of the deepest level
-                ph.push_back({"fused", l});
-                continue;
-            }
-            ph.push_back({"expand", l});
-            ph.push_back({"finalize", l});
-        }
+        // one phase per level: its expand and finalize items
+        for (int l = 0; l < D; ++l) ph.push_back({(l == D - 1 && !mat) ? "fused" : "level", l});
         if (D > 0 && mat) ph.push_back({"update", D - 1});
         if (D == 0 || mat) ph.push_back({"leaf", D});
         if (D > 0) ph.push_back({"backup", 0});

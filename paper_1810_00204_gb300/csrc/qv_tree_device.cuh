@@ -1,7 +1,9 @@
 // qv_tree_device.cuh -- device side of the QV-tree search: one persistent
 // cooperative kernel (k_plan) per plan or per batch of episodes.
 //
-// Phases of k_plan, separated by a bounded grid barrier:
+// Phases of k_plan, separated by a bounded grid barrier: the support windows
+// of every b0, then one phase per level l whose expand items run first and
+// whose finalize items wait only for their own group's expand items, then:
 //   expand(l)  for every V-node of level l (Alg. 2: every action) and a range
 //              of row bands: the node's belief band.  At the root that is b0;
 //              below it the band is recomputed from the parent's band (staged
@@ -11,8 +13,9 @@
 //              the label histograms that give P(z | b, a) (Eq. 3
 //              denominator) and R(b, a) (Sec. III).  Cells of the null label
 //              are summed in registers; each beacon's sensing diamond is
-//              summed by one warp, so no histogram needs atomics.  The last
-//              work item of a node finalises it: K Philox draws per action
+//              summed by one warp (the finalize items), so no histogram
+//              needs atomics.  The last work item of a node finalises it:
+//              K Philox draws per action
 //              inverted through the CDF (Alg. 3-4), the unique draws with
 //              their frequencies.  The last node of an episode numbers its
 //              children (prefix sum in (parent, action, z) order); the last
@@ -40,7 +43,7 @@
 
 namespace qv {
 
-// Per-warp buffers of the label histograms (phase_finalize): a tile of
+// Per-warp buffers of the label histograms (finalize items): a tile of
 // kTileH x kTileW cells of the node's belief is formed from the parent's
 // belief with a two-cell rim, its cell words with a one-cell rim.
 constexpr int kTileH = 17, kTileW = 18;  // one tile holds a range-8 diamond's 17 x 17 box
@@ -1058,7 +1061,7 @@ __device__ __forceinline__ float4 child4(const EpReg &ep, const float *m, const 
 }
 
 // child4 where no cell within two rows is the goal and the staged parent is
-// zero on occupied cells (phase_expand masks it once per band): every
+// zero on occupied cells (the expand items mask it once per band): every
 // neighbour then moves its mass in without the inflow test, and the
 // blocked moves' mass stays by the self weight of the action.
 __device__ __forceinline__ float4 child4_open(const EpReg &ep, const float *m, const uint16_t *c, int SW, int col,
@@ -1125,7 +1128,7 @@ __device__ __forceinline__ float child1(const EpReg &ep, const float *m, const u
 // Q-weighted null masses in registers.  A warp's sums go to a per-warp slot
 // when its task range moves to another child; at the end of the band the
 // slots are added into each child's totals in warp order.  Cells with a
-// beacon's label enter through phase_finalize's tiles.
+// beacon's label enter through the finalize items' tiles.
 // One expand work item w of level l (false when a wait gave up).  With
 // `signal` the item also counts itself done on its group's counter
 // (grp_done), which the fused level's finalize items wait on.
@@ -1494,7 +1497,7 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
         }
         __syncthreads();
         // the item's totals of every child: final when the group has one item,
-        // else one record per (item, child) that phase_finalize adds in order
+        // else one record per (item, child) that the finalize item adds in order
         for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
             const int r = i / kTot, k = i - r * kTot;
             const float v = S.acc[i];
@@ -1517,16 +1520,6 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
             if (threadIdx.x == 0) arrive_acq_rel(pl.grp_done + pl.gbase[l] + j);
         }
     }
-    return true;
-}
-
-template <bool FUSED>
-__device__ bool phase_expand(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
-                             int &cur_e) {
-    const int total = __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
-    unsigned *ctr = pl.work + 2 * l;
-    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8))
-        if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, false)) return false;
     return true;
 }
 
@@ -1950,31 +1943,26 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
     }
 }
 
+// One level as one phase: its expand items, then its finalize items, from
+// one counter.  A finalize item forms its label histograms at once and waits
+// only for its own group's expand records (grp_done), so CTAs that finish
+// their last expand item start finalising instead of waiting at a grid
+// barrier.  Every expand item is taken before any finalize item, and expand
+// items wait on nothing but their own copies, so every wait ends.  NUMBER:
+// the level's last nodes number their children and publish the next level's
+// work lists (every level but the fused mode's deepest); the next level's
+// expand reads this level's stored beliefs only after the grid barrier.
 template <bool FUSED, bool NUMBER>
-__device__ bool phase_finalize(const PlanDev &pl, int l, Smem &S, int &cur_e) {
-    const int total = __ldcg(pl.wb_fin + l * (pl.E + 1) + pl.E);
-    unsigned *ctr = pl.work + 2 * l + 1;
-    for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8))
-        finalize_item<FUSED, NUMBER>(pl, l, S, cur_e, w, false);
-    return true;
-}
-
-// The deepest level of the fused mode as one phase: its expand items, then
-// its finalize items, from one counter.  A finalize item forms its label
-// histograms at once and waits only for its own group's expand records, so
-// CTAs that finish their last expand item start finalising instead of
-// waiting at a grid barrier.  Every expand item is taken before any
-// finalize item, and expand items wait on nothing but their own copies, so
-// every wait ends.
-__device__ bool phase_fused_last(const PlanDev &pl, int l, Smem &S, uint64_t *mbar, unsigned &mphase, int &cur_e) {
+__device__ bool phase_level(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
+                            int &cur_e) {
     const int n_exp = __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
     const int total = n_exp + __ldcg(pl.wb_fin + l * (pl.E + 1) + pl.E);
     unsigned *ctr = pl.work + 2 * l;
     for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
         if (w < n_exp) {
-            if (!expand_item<true>(pl, l, false, S, mbar, mphase, cur_e, w, true)) return false;
+            if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, true)) return false;
         } else {
-            finalize_item<true, false>(pl, l, S, cur_e, w - n_exp, true);
+            finalize_item<FUSED, NUMBER>(pl, l, S, cur_e, w - n_exp, true);
         }
     }
     return true;
@@ -2375,21 +2363,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         const bool fused = (last && !mat) || dl;
         // a level's beliefs are stored when a later phase reads them
         const bool store = l > 0 && (l < D - 1 || mat);
-        if (last && !mat) {
-            // expand and finalize of the deepest level in one phase
-            if (!phase_fused_last(pl, l, S, &mbar, mphase, cur_e) && threadIdx.x == 0)
-                atomicOr(pl.status, kErrTimeout);
-            if (!grid_sync(pl)) return;
-            stamp(pl, slot++);
-            continue;
-        }
-        const bool ok = fused ? phase_expand<true>(pl, l, store, S, &mbar, mphase, cur_e)
-                              : phase_expand<false>(pl, l, store, S, &mbar, mphase, cur_e);
+        // expand and finalize of the level in one phase
+        bool ok;
+        if (last && !mat) ok = phase_level<true, false>(pl, l, false, S, &mbar, mphase, cur_e);
+        else if (fused) ok = phase_level<true, true>(pl, l, store, S, &mbar, mphase, cur_e);
+        else ok = phase_level<false, true>(pl, l, store, S, &mbar, mphase, cur_e);
         if (!ok && threadIdx.x == 0) atomicOr(pl.status, kErrTimeout);
-        if (!grid_sync(pl)) return;
-        stamp(pl, slot++);
-        if (!fused) phase_finalize<false, true>(pl, l, S, cur_e);
-        else phase_finalize<true, true>(pl, l, S, cur_e);
         if (!grid_sync(pl, dl && !last)) return;
         stamp(pl, slot++);
         if (dl && !last) {
@@ -2437,9 +2416,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
         __syncthreads();
         for (int i = threadIdx.x; i < 4 * pl.E; i += blockDim.x) pl.win[i] = 0u;
         for (int i = threadIdx.x; i < 2 * (D + 1); i += blockDim.x) pl.work[i] = 0u;
-        if (D > 0 && !mat && Deff == D) {
-            const int ng = __ldcg(pl.ngrp + D - 1);
-            for (int i = threadIdx.x; i < ng; i += blockDim.x) pl.grp_done[pl.gbase[D - 1] + i] = 0u;
+        for (int l = 0; l < Deff; ++l) {  // the group counters of every level run
+            const int ng = __ldcg(pl.ngrp + l);
+            for (int i = threadIdx.x; i < ng; i += blockDim.x) pl.grp_done[pl.gbase[l] + i] = 0u;
         }
     }
     if (D > 0) {
