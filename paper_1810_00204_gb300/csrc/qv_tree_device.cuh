@@ -49,7 +49,7 @@ namespace qv {
 constexpr int kTileH = 17, kTileW = 18;  // one tile holds a range-8 diamond's 17 x 17 box
 constexpr int kTileP = (kTileH + 4) * (kTileW + 4);   // parent values
 constexpr int kTileC = (kTileH + 2) * (kTileW + 2);   // node values, cell words
-constexpr int kTileFloats = kTileP + kTileC + (kTileC + 1) / 2;
+constexpr int kTileFloats = kTileP + kTileC + (kTileC + 1) / 2 + kTileH * kTileW;  // + the cell list
 // Totals of one V-node per work item: [0, 5) null-label masses, [5, 10)
 // R(b, a) sums, [10, 35) Q-weighted null masses (fused level), [35] unused.
 constexpr int kTot = 36;
@@ -872,7 +872,11 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         if (threadIdx.x == 0) *pl.leaf_split = C;
     }
     const int fch = l1 < pl.depth ? finalize_chunks(Tt, pl.target, pl.Bmax) : 1;
-    if (threadIdx.x == 0 && l1 < pl.depth) pl.fchunks[l1] = fch;
+    // the fused mode's deepest level with one beacon chunk per node takes
+    // finalize items per group (a V-node of level l1 - 1 and a piece of its
+    // children, finalize_group_item), flagged by zero chunks
+    const bool grp_mode = l1 >= 1 && l1 == pl.depth - 1 && pl.leaf_mode == QV_LEAF_FUSED && fch == 1;
+    if (threadIdx.x == 0 && l1 < pl.depth) pl.fchunks[l1] = grp_mode ? 0 : fch;
     int wn = 0, wu = 0, wl = 0;
     for (int base = 0; base < E; base += blockDim.x) {
         const int e = base + threadIdx.x;
@@ -891,7 +895,8 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         const int xl = block_exclusive_scan(vl, S.scan, tl);
         if (e < E) {
             pl.npre[l1 * (E + 1) + e] = wn + xn;
-            if (l1 < pl.depth) pl.wb_fin[l1 * (E + 1) + e] = (wn + xn) * fch;
+            if (l1 < pl.depth)
+                pl.wb_fin[l1 * (E + 1) + e] = grp_mode ? __ldcg(pl.npre + (l1 - 1) * (E + 1) + e) : (wn + xn) * fch;
             pl.uitems[l1 * E + e] = it;
             pl.wb_upd[l1 * (E + 1) + e] = wu + xu;
             if (l1 == pl.depth) pl.wb_leaf[e] = wl + xl;
@@ -902,7 +907,8 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
     }
     if (threadIdx.x == 0) {
         pl.npre[l1 * (E + 1) + E] = wn;
-        if (l1 < pl.depth) pl.wb_fin[l1 * (E + 1) + E] = wn * fch;
+        if (l1 < pl.depth)
+            pl.wb_fin[l1 * (E + 1) + E] = grp_mode ? __ldcg(pl.npre + (l1 - 1) * (E + 1) + E) : wn * fch;
         pl.wb_upd[l1 * (E + 1) + E] = wu;
         if (l1 == pl.depth) pl.wb_leaf[E] = wl;
     }
@@ -946,6 +952,9 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
     if (threadIdx.x == 0) {
         goff[G] = wi;
         pl.ngrp[l1] = G;
+        // group mode: one finalize item per expand item, a group's children
+        // cut into as many pieces as it has expand items
+        if (grp_mode) pl.wb_fin[l1 * (E + 1) + E] = wi;
         if (static_cast<long long>(wr) * pl.cmax > pl.n_xrec) atomicOr(pl.status, kErrCapacity);
     }
 }
@@ -1530,152 +1539,296 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
 // into la / lq of the calling lane.  One warp: the beacon's sensing diamond
 // is covered by tiles of kTileH x kTileW cells; per tile the parent's values
 // with a two-cell rim and the cell words with a one-cell rim are read into
-// the warp's shared buffers, the node's belief is formed on the tile with a
-// one-cell rim, and the diamond's cells of label k predict from it.  Only
-// the part of the diamond inside `win` (where the node's predicted masses
-// can be nonzero) is visited.
-template <bool FUSED>
-__device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa, int zc, float sa, float se, int k,
-                            int br, int bc, const Win &win, float *tp, float *tc, uint16_t *tcw, const float *lut,
-                            float la[5], float lq[FUSED ? 25 : 1]) {
+// the warp's shared buffers (tile_load), the diamond's cells of label k in
+// the tile are listed (tile_list), the node's belief is formed on the tile
+// with a one-cell rim (tile_form) and the listed cells predict from it
+// (tile_predict).  Only the part of the diamond inside `win` (where the
+// node's predicted masses can be nonzero) is visited.  The load and the
+// list depend on the parent and the beacon only, so every child of one
+// parent can reuse them.
+struct TileBox {
+    int rlo, rhi, clo, chi;  // the diamond's bounding box inside the grid and the window
+};
+__device__ __forceinline__ TileBox tile_box(const EpReg &ep, int br, int bc, const Win &win) {
+    const int R = ep.range;
+    TileBox b;
+    b.rlo = max(max(0, br - R), win.r0);
+    b.rhi = min(min(ep.H - 1, br + R), win.r1 - 1);
+    b.clo = max(max(0, bc - R), win.c0);
+    b.chi = min(min(ep.W - 1, bc + R), win.c1 - 1);
+    return b;
+}
+
+// The tile at (y0, x0): at the root b0 itself (into tc) with the cell
+// words; below it the parent's values with a two-cell rim (into tp) and the
+// cell words with a one-cell rim; loads issued kLoadBatch at a time, before
+// any of the batch is used, and only over the box and its rims.
+__device__ void tile_load(const EpReg &ep, const float *par, bool root, int y0, int x0, const TileBox &bx, float *tp,
+                          float *tc, uint16_t *tcw) {
     const int lane = threadIdx.x & 31;
-    const int R = ep.range, P = ep.P, H = ep.H, W = ep.W;
-    const int rlo = max(max(0, br - R), win.r0), rhi = min(min(H - 1, br + R), win.r1 - 1);
-    const int clo = max(max(0, bc - R), win.c0), chi = min(min(W - 1, bc + R), win.c1 - 1);
+    const int P = ep.P, H = ep.H, rhi = bx.rhi, chi = bx.chi;
     constexpr int PW = kTileW + 4, CW = kTileW + 2;
-    constexpr int NP = (kTileP + 31) / 32, NC = (kTileC + 31) / 32, ND = (kTileH * kTileW + 31) / 32;
+    constexpr int NP = (kTileP + 31) / 32, NC = (kTileC + 31) / 32;
     constexpr int kLoadBatch = 8;  // loads in flight per lane (the values wait in registers)
-    for (int y0 = rlo; y0 <= rhi; y0 += kTileH) {
-        for (int x0 = clo; x0 <= chi; x0 += kTileW) {
-            __syncwarp();
-            // the tile's global loads issued kLoadBatch at a time, before any
-            // of the batch is used (only the diamond's box and its rims)
-            if (root) {
-                // b0 on the tile and its rim, with the cell words
+    __syncwarp();
+    if (root) {
 #pragma unroll 1
-                for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
-                    uint16_t cv[kLoadBatch];
-                    float bv[kLoadBatch];
+        for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
+            uint16_t cv[kLoadBatch];
+            float bv[kLoadBatch];
 #pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v) {
-                        const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
-                        const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                        const bool in = u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P &&
-                                        r <= rhi + 1 && c <= chi + 1;
-                        cv[v] = in ? __ldg(ep.cell + static_cast<size_t>(r) * P + c) : static_cast<uint16_t>(0);
-                        bv[v] = in ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
-                    }
-#pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v) {
-                        const int i = lane + 32 * (u0 + v);
-                        if (u0 + v < NC && i < kTileC) {
-                            tcw[i] = cv[v];
-                            tc[i] = QV_CELL_FREE(static_cast<unsigned>(cv[v])) ? bv[v] : 0.0f;
-                        }
-                    }
-                }
-                __syncwarp();
-            } else {
-#pragma unroll 1
-                for (int u0 = 0; u0 < NP; u0 += kLoadBatch) {
-                    float pv[kLoadBatch];
-#pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v) {
-                        const int i = lane + 32 * (u0 + v), rr = i / PW, cc = i - rr * PW;
-                        const int r = y0 - 2 + rr, c = x0 - 2 + cc;
-                        pv[v] = (u0 + v < NP && i < kTileP && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 2 &&
-                                 c <= chi + 2)
-                                    ? __ldcg(par + static_cast<size_t>(r) * P + c)
-                                    : 0.0f;
-                    }
-#pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v)
-                        if (u0 + v < NP && lane + 32 * (u0 + v) < kTileP) tp[lane + 32 * (u0 + v)] = pv[v];
-                }
-#pragma unroll 1
-                for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
-                    uint16_t cv[kLoadBatch];
-#pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v) {
-                        const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
-                        const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                        cv[v] = (u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 &&
-                                 c <= chi + 1)
-                                    ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
-                                    : static_cast<uint16_t>(0);
-                    }
-#pragma unroll
-                    for (int v = 0; v < kLoadBatch; ++v)
-                        if (u0 + v < NC && lane + 32 * (u0 + v) < kTileC) tcw[lane + 32 * (u0 + v)] = cv[v];
-                }
-                __syncwarp();
-                // the node's belief on the tile and its rim
-                for (int i = lane; i < kTileC; i += 32) {
-                    const int rr = i / CW, cc = i - rr * CW;
-                    const int r = y0 - 1 + rr, c = x0 - 1 + cc;
-                    float v = 0.0f;
-                    if (r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 && c <= chi + 1) {
-                        const unsigned cw = tcw[i];
-                        const float *m = tp + (rr + 1) * PW + (cc + 1);
-                        const unsigned in = QV_CELL_INFLOW(cw);
-                        float nb[4];
-                        nb[kDirN] = (in & 1u) ? m[-PW] : 0.0f;
-                        nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
-                        nb[kDirS] = (in & 4u) ? m[PW] : 0.0f;
-                        nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
-                        const float p = predict_one(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, pa);
-                        v = p * (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
-                    }
-                    tc[i] = v;
-                }
-                __syncwarp();
+            for (int v = 0; v < kLoadBatch; ++v) {
+                const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
+                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                const bool in = u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 &&
+                                c <= chi + 1;
+                cv[v] = in ? __ldg(ep.cell + static_cast<size_t>(r) * P + c) : static_cast<uint16_t>(0);
+                bv[v] = in ? __ldcg(par + static_cast<size_t>(r) * P + c) : 0.0f;
             }
-            // the diamond's cells of label k inside the tile, listed in the
-            // warp's free parent buffer; then per listed cell its Q values
-            // (fused) and the predicted masses
-            int *list = reinterpret_cast<int *>(tp);
-            int nh = 0;
-#pragma unroll 1
-            for (int u = 0; u < ND; ++u) {
-                const int i = lane + 32 * u, rr = i / kTileW, cc = i - rr * kTileW;
-                const int r = y0 + rr, c = x0 + cc;
-                const bool hit = i < kTileH * kTileW && r <= rhi && c <= chi && abs(r - br) + abs(c - bc) <= R &&
-                                 static_cast<int>(QV_CELL_LABEL(tcw[(rr + 1) * CW + cc + 1])) == k;
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (hit) list[nh + __popc(bal & ((1u << lane) - 1u))] = i;
-                nh += __popc(bal);
-            }
-            __syncwarp();
-            for (int h = lane; h < nh; h += 32) {
-                const int cell = list[h];
-                const int rr = cell / kTileW, cc = cell - rr * kTileW;
-                const int r = y0 + rr, c = x0 + cc;
-                float qv[FUSED ? 5 : 1];
-                if constexpr (FUSED) {
 #pragma unroll
-                    for (int ap = 0; ap < 5; ++ap)
-                        qv[ap] = __ldg(ep.Q + static_cast<size_t>(ap) * ep.N + static_cast<size_t>(r) * P + c);
-                }
-                const unsigned cw = tcw[(rr + 1) * CW + cc + 1];
-                const float *m = tc + (rr + 1) * CW + (cc + 1);
-                const unsigned in = QV_CELL_INFLOW(cw);
-                float nb[4], out[5];
-                nb[kDirN] = (in & 1u) ? m[-CW] : 0.0f;
-                nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
-                nb[kDirS] = (in & 4u) ? m[CW] : 0.0f;
-                nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
-                predict_cell(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, out);
-#pragma unroll
-                for (int a = 0; a < 5; ++a) la[a] += out[a];
-                if constexpr (FUSED) {
-#pragma unroll
-                    for (int a = 0; a < 5; ++a)
-#pragma unroll
-                        for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
+            for (int v = 0; v < kLoadBatch; ++v) {
+                const int i = lane + 32 * (u0 + v);
+                if (u0 + v < NC && i < kTileC) {
+                    tcw[i] = cv[v];
+                    tc[i] = QV_CELL_FREE(static_cast<unsigned>(cv[v])) ? bv[v] : 0.0f;
                 }
             }
         }
+    } else {
+#pragma unroll 1
+        for (int u0 = 0; u0 < NP; u0 += kLoadBatch) {
+            float pv[kLoadBatch];
+#pragma unroll
+            for (int v = 0; v < kLoadBatch; ++v) {
+                const int i = lane + 32 * (u0 + v), rr = i / PW, cc = i - rr * PW;
+                const int r = y0 - 2 + rr, c = x0 - 2 + cc;
+                pv[v] = (u0 + v < NP && i < kTileP && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 2 &&
+                         c <= chi + 2)
+                            ? __ldcg(par + static_cast<size_t>(r) * P + c)
+                            : 0.0f;
+            }
+#pragma unroll
+            for (int v = 0; v < kLoadBatch; ++v)
+                if (u0 + v < NP && lane + 32 * (u0 + v) < kTileP) tp[lane + 32 * (u0 + v)] = pv[v];
+        }
+#pragma unroll 1
+        for (int u0 = 0; u0 < NC; u0 += kLoadBatch) {
+            uint16_t cv[kLoadBatch];
+#pragma unroll
+            for (int v = 0; v < kLoadBatch; ++v) {
+                const int i = lane + 32 * (u0 + v), rr = i / CW, cc = i - rr * CW;
+                const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+                cv[v] = (u0 + v < NC && i < kTileC && r >= 0 && r < H && c >= 0 && c < P && r <= rhi + 1 &&
+                         c <= chi + 1)
+                            ? __ldg(ep.cell + static_cast<size_t>(r) * P + c)
+                            : static_cast<uint16_t>(0);
+            }
+#pragma unroll
+            for (int v = 0; v < kLoadBatch; ++v)
+                if (u0 + v < NC && lane + 32 * (u0 + v) < kTileC) tcw[lane + 32 * (u0 + v)] = cv[v];
+        }
     }
+    __syncwarp();
+}
+
+// The diamond's cells of label k inside the tile at (y0, x0), as tile
+// indices in `list` (ascending); returns their number.
+__device__ int tile_list(const EpReg &ep, int k, int br, int bc, int y0, int x0, const TileBox &bx,
+                         const uint16_t *tcw, int *list) {
+    const int lane = threadIdx.x & 31;
+    constexpr int CW = kTileW + 2, ND = (kTileH * kTileW + 31) / 32;
+    int nh = 0;
+#pragma unroll 1
+    for (int u = 0; u < ND; ++u) {
+        const int i = lane + 32 * u, rr = i / kTileW, cc = i - rr * kTileW;
+        const int r = y0 + rr, c = x0 + cc;
+        const bool hit = i < kTileH * kTileW && r <= bx.rhi && c <= bx.chi &&
+                         abs(r - br) + abs(c - bc) <= ep.range &&
+                         static_cast<int>(QV_CELL_LABEL(tcw[(rr + 1) * CW + cc + 1])) == k;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) list[nh + __popc(bal & ((1u << lane) - 1u))] = i;
+        nh += __popc(bal);
+    }
+    __syncwarp();
+    return nh;
+}
+
+// The node's belief Phi(parent, pa, zc) (Eq. 3) on the tile and its rim,
+// from the parent's values in tp (not used at the root, where tc holds b0).
+__device__ void tile_form(const EpReg &ep, int pa, int zc, float sa, float se, int y0, int x0, const TileBox &bx,
+                          const float *tp, float *tc, const uint16_t *tcw, const float *lut) {
+    const int lane = threadIdx.x & 31;
+    const int P = ep.P, H = ep.H;
+    constexpr int PW = kTileW + 4, CW = kTileW + 2;
+    for (int i = lane; i < kTileC; i += 32) {
+        const int rr = i / CW, cc = i - rr * CW;
+        const int r = y0 - 1 + rr, c = x0 - 1 + cc;
+        float v = 0.0f;
+        if (r >= 0 && r < H && c >= 0 && c < P && r <= bx.rhi + 1 && c <= bx.chi + 1) {
+            const unsigned cw = tcw[i];
+            const float *m = tp + (rr + 1) * PW + (cc + 1);
+            const unsigned in = QV_CELL_INFLOW(cw);
+            float nb[4];
+            nb[kDirN] = (in & 1u) ? m[-PW] : 0.0f;
+            nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
+            nb[kDirS] = (in & 4u) ? m[PW] : 0.0f;
+            nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
+            const float p = predict_one(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, pa);
+            v = p * (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+        }
+        tc[i] = v;
+    }
+    __syncwarp();
+}
+
+// The listed cells' predicted masses for the five actions (from the node's
+// belief in tc), added to la and, fused, their Q-weighted ones to lq.
+template <bool FUSED>
+__device__ void tile_predict(const EpReg &ep, int y0, int x0, const float *tc, const uint16_t *tcw, const int *list,
+                             int nh, const float *lut, float la[5], float lq[FUSED ? 25 : 1]) {
+    const int lane = threadIdx.x & 31;
+    const int P = ep.P;
+    constexpr int CW = kTileW + 2;
+    for (int h = lane; h < nh; h += 32) {
+        const int cell = list[h];
+        const int rr = cell / kTileW, cc = cell - rr * kTileW;
+        const int r = y0 + rr, c = x0 + cc;
+        float qv[FUSED ? 5 : 1];
+        if constexpr (FUSED) {
+#pragma unroll
+            for (int ap = 0; ap < 5; ++ap)
+                qv[ap] = __ldg(ep.Q + static_cast<size_t>(ap) * ep.N + static_cast<size_t>(r) * P + c);
+        }
+        const unsigned cw = tcw[(rr + 1) * CW + cc + 1];
+        const float *m = tc + (rr + 1) * CW + (cc + 1);
+        const unsigned in = QV_CELL_INFLOW(cw);
+        float nb[4], out[5];
+        nb[kDirN] = (in & 1u) ? m[-CW] : 0.0f;
+        nb[kDirE] = (in & 2u) ? m[1] : 0.0f;
+        nb[kDirS] = (in & 4u) ? m[CW] : 0.0f;
+        nb[kDirW] = (in & 8u) ? m[-1] : 0.0f;
+        predict_cell(nb, m[0], cw, r * P + c == ep.goal, ep.slip, lut, out);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) la[a] += out[a];
+        if constexpr (FUSED) {
+#pragma unroll
+            for (int a = 0; a < 5; ++a)
+#pragma unroll
+                for (int ap = 0; ap < 5; ++ap) lq[a * 5 + ap] = fmaf(out[a], qv[ap], lq[a * 5 + ap]);
+        }
+    }
+}
+
+template <bool FUSED>
+__device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa, int zc, float sa, float se, int k,
+                            int br, int bc, const Win &win, float *tp, float *tc, uint16_t *tcw, int *list,
+                            const float *lut, float la[5], float lq[FUSED ? 25 : 1]) {
+    const TileBox bx = tile_box(ep, br, bc, win);
+    for (int y0 = bx.rlo; y0 <= bx.rhi; y0 += kTileH) {
+        for (int x0 = bx.clo; x0 <= bx.chi; x0 += kTileW) {
+            tile_load(ep, par, root, y0, x0, bx, tp, tc, tcw);
+            const int nh = tile_list(ep, k, br, bc, y0, x0, bx, tcw, list);
+            if (!root) tile_form(ep, pa, zc, sa, se, y0, x0, bx, tp, tc, tcw, lut);
+            tile_predict<FUSED>(ep, y0, x0, tc, tcw, list, nh, lut, la, lq);
+        }
+    }
+}
+
+// A node's totals -- final, or the records of its group's expand items in
+// item order -- into S.tot, and its belief at the goal (whose arrivals
+// R(b, a) must not pay) into S.flags[4].  With wait_group, first waits
+// (bounded) until every expand item of its group has counted itself done.
+__device__ void node_totals(const PlanDev &pl, int l, const EpDev &ep, int e, int lp, int local, int iid,
+                            const float *par, int pa, int zc, float sa, float se, bool wait_group, Smem &S) {
+    const int E = pl.E;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int jg = e, r = 0;
+    if (l > 0) {
+        jg = __ldcg(pl.npre + (l - 1) * (E + 1) + e) + lp;
+        const int cnt = __ldcg(pl.count + l * E + e);
+        const int c0 = min(__ldcg(pl.choff + static_cast<long long>(ep.inode_base[l - 1] + lp) * 5), cnt);
+        r = local - c0;
+    }
+    const int *goff = pl.grp_off + pl.gbase[l] + l;
+    const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
+    constexpr int kGroups = kThreads / kTot;  // partial sums per value
+    const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
+    const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
+    if (wait_group) {
+        if (threadIdx.x == 0) {
+            const unsigned *gd = pl.grp_done + pl.gbase[l] + jg;
+            unsigned i = 0;
+            for (;;) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
+                if (v >= static_cast<unsigned>(nit)) break;
+                if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+                    atomicOr(pl.status, kErrTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+    }
+    if (rec < 0) {
+        if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
+    } else {
+        const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
+        if (g < kGroups) {
+            // items g, g + 7, ... in order, eight loads in flight at a time
+            float sum = 0.0f;
+            for (int it0 = g; it0 < nit; it0 += 8 * kGroups) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int it = it0 + u * kGroups;
+                    const long long x = static_cast<long long>(rec + it) * pl.cmax + r;
+                    v[u] = (it < nit && x < pl.n_xrec) ? __ldcg(pl.xrec + x * kTot + t) : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sum += v[u];
+            }
+            S.red[g * kTot + t] = sum;
+        }
+        __syncthreads();
+        if (threadIdx.x < kTot) {
+            float sum = 0.0f;
+            for (int g2 = 0; g2 < kGroups; ++g2) sum += S.red[g2 * kTot + threadIdx.x];
+            S.tot[threadIdx.x] = sum;
+        }
+    }
+    if (wid == 0) {
+        // the node's belief at the goal, whose arrivals R(b, a) must not
+        // pay: lanes 0-4 load the parent there and at its four
+        // neighbours (inside the grid) at once
+        const int y = ep.goal, P = ep.P, gr = y / P, gc = y - gr * P;
+        const int dy[5] = {0, -P, 1, P, -1};
+        const bool inside = lane < 5 && (lane != 1 || gr > 0) && (lane != 2 || gc + 1 < P) &&
+                            (lane != 3 || gr + 1 < ep.H) && (lane != 4 || gc > 0);
+        const float pv = inside ? __ldcg(par + y + dy[lane < 5 ? lane : 0]) : 0.0f;
+        const unsigned cw = __ldg(ep.cell + y);
+        const float m0 = __shfl_sync(0xffffffffu, pv, 0), mN = __shfl_sync(0xffffffffu, pv, 1);
+        const float mE = __shfl_sync(0xffffffffu, pv, 2), mS = __shfl_sync(0xffffffffu, pv, 3);
+        const float mW = __shfl_sync(0xffffffffu, pv, 4);
+        if (lane == 0) {
+            float bg;
+            if (l == 0) {
+                bg = m0;
+            } else {
+                const unsigned in = QV_CELL_INFLOW(cw);
+                float nb[4];
+                nb[kDirN] = (in & 1u) ? mN : 0.0f;
+                nb[kDirE] = (in & 2u) ? mE : 0.0f;
+                nb[kDirS] = (in & 4u) ? mS : 0.0f;
+                nb[kDirW] = (in & 8u) ? mW : 0.0f;
+                bg = predict_one(nb, m0, cw, true, ep.slip, S.lut, pa) *
+                     (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
+            }
+            S.flags[4] = __float_as_int(bg);
+        }
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- finalize phase
@@ -1703,6 +1856,7 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
     float *tp = S.tile + wid * kTileFloats;
     float *tc = tp + kTileP;
     uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
+    int *tlist = reinterpret_cast<int *>(tc + kTileC + (kTileC + 1) / 2);
     {
 #ifdef QV_TRACE
         unsigned long long tr[kTraceWords] = {};
@@ -1769,7 +1923,7 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
 #pragma unroll
             for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
             label_tiles<FUSED>(er, par, l == 0, pa, zc, sa, se, k, S.bco[2 * k], S.bco[2 * k + 1], win, tp, tc, tcw,
-                               S.lut, la, lq);
+                               tlist, S.lut, la, lq);
             // lane i ends with the warp total of value i: 0..4 the label
             // masses, 5..29 the Q-weighted ones
             float v[32];
@@ -1839,95 +1993,7 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
         }
         QV_TRACE_MARK(tr, 5);
         // the node's totals: final, or the records of its group's items in order
-        {
-            int jg = e, r = 0;
-            if (l > 0) {
-                jg = __ldcg(pl.npre + (l - 1) * (E + 1) + e) + lp;
-                const int cnt = __ldcg(pl.count + l * E + e);
-                const int c0 = min(__ldcg(pl.choff + static_cast<long long>(ep.inode_base[l - 1] + lp) * 5), cnt);
-                r = local - c0;
-            }
-            const int *goff = pl.grp_off + pl.gbase[l] + l;
-            const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
-            constexpr int kGroups = kThreads / kTot;  // partial sums per value
-            const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
-            const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
-            if (wait_group) {
-                if (threadIdx.x == 0) {
-                    const unsigned *gd = pl.grp_done + pl.gbase[l] + jg;
-                    unsigned i = 0;
-                    for (;;) {
-                        unsigned v;
-                        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
-                        if (v >= static_cast<unsigned>(nit)) break;
-                        if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
-                            atomicOr(pl.status, kErrTimeout);
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                }
-                __syncthreads();
-            }
-            if (rec < 0) {
-                if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
-            } else {
-                const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
-                if (g < kGroups) {
-                    // items g, g + 7, ... in order, eight loads in flight at a time
-                    float sum = 0.0f;
-                    for (int it0 = g; it0 < nit; it0 += 8 * kGroups) {
-                        float v[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const int it = it0 + u * kGroups;
-                            const long long x = static_cast<long long>(rec + it) * pl.cmax + r;
-                            v[u] = (it < nit && x < pl.n_xrec) ? __ldcg(pl.xrec + x * kTot + t) : 0.0f;
-                        }
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) sum += v[u];
-                    }
-                    S.red[g * kTot + t] = sum;
-                }
-                __syncthreads();
-                if (threadIdx.x < kTot) {
-                    float sum = 0.0f;
-                    for (int g2 = 0; g2 < kGroups; ++g2) sum += S.red[g2 * kTot + threadIdx.x];
-                    S.tot[threadIdx.x] = sum;
-                }
-            }
-            if (wid == 0) {
-                // the node's belief at the goal, whose arrivals R(b, a) must not
-                // pay: lanes 0-4 load the parent there and at its four
-                // neighbours (inside the grid) at once
-                const int y = ep.goal, P = ep.P, gr = y / P, gc = y - gr * P;
-                const int dy[5] = {0, -P, 1, P, -1};
-                const bool inside = lane < 5 && (lane != 1 || gr > 0) && (lane != 2 || gc + 1 < P) &&
-                                    (lane != 3 || gr + 1 < ep.H) && (lane != 4 || gc > 0);
-                const float pv = inside ? __ldcg(par + y + dy[lane < 5 ? lane : 0]) : 0.0f;
-                const unsigned cw = __ldg(ep.cell + y);
-                const float m0 = __shfl_sync(0xffffffffu, pv, 0), mN = __shfl_sync(0xffffffffu, pv, 1);
-                const float mE = __shfl_sync(0xffffffffu, pv, 2), mS = __shfl_sync(0xffffffffu, pv, 3);
-                const float mW = __shfl_sync(0xffffffffu, pv, 4);
-                if (lane == 0) {
-                    float bg;
-                    if (l == 0) {
-                        bg = m0;
-                    } else {
-                        const unsigned in = QV_CELL_INFLOW(cw);
-                        float nb[4];
-                        nb[kDirN] = (in & 1u) ? mN : 0.0f;
-                        nb[kDirE] = (in & 2u) ? mE : 0.0f;
-                        nb[kDirS] = (in & 4u) ? mS : 0.0f;
-                        nb[kDirW] = (in & 8u) ? mW : 0.0f;
-                        bg = predict_one(nb, m0, cw, true, ep.slip, S.lut, pa) *
-                             (static_cast<int>(QV_CELL_LABEL(cw)) == zc ? sa : se);
-                    }
-                    S.flags[4] = __float_as_int(bg);
-                }
-            }
-            __syncthreads();
-        }
+        node_totals(pl, l, ep, e, lp, local, iid, par, pa, zc, sa, se, wait_group, S);
         QV_TRACE_MARK(tr, 6);
         const unsigned long long code = __ldcg(pl.code + gid);
         finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
@@ -1940,6 +2006,148 @@ __device__ void finalize_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int
         tr[1] = static_cast<unsigned long long>(w);
         trace_commit(tr, 9);
 #endif
+    }
+}
+
+// A group's finalize item (the fused mode's deepest level when a node's
+// beacons form one chunk): one V-node p of level l - 1 and a contiguous
+// piece of its children (a group has as many pieces as expand items, which
+// are in proportion to its children).  While the beacons whose diamond meets the window are at most one per
+// warp and each diamond's box fits one tile, a warp loads its beacon's tile
+// of p's values and cell words and lists its label cells once, and every
+// child reuses them: per child the warps form the child's belief on their
+// tiles (Eq. 3) and its label histograms, then the node is finalised as by
+// a node item.  Otherwise each child walks its beacons' tiles afresh.
+template <bool FUSED>
+__device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w) {
+    const int E = pl.E, K = pl.K, Bm = pl.Bmax;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *tp = S.tile + wid * kTileFloats;
+    float *tc = tp + kTileP;
+    uint16_t *tcw = reinterpret_cast<uint16_t *>(tc + kTileC);
+    int *tlist = reinterpret_cast<int *>(tc + kTileC + (kTileC + 1) / 2);
+    const int G = __ldcg(pl.ngrp + l);
+    const int *goff = pl.grp_off + pl.gbase[l] + l;
+    const int *np = pl.npre + (l - 1) * (E + 1);
+    const int j = block_find(goff, G, w, S.flags + 6);
+    if (!QV_IN_BOUNDS(kSiteGroup, pl.gbase[l] + j, pl.ngrp_cap)) return;  // uniform over the CTA
+    const int e = block_find(np, E, j, S.flags + 7);
+    load_ep(pl, e, S, cur_e);
+    const EpDev &ep = *S.ep;
+    const int lp = j - __ldcg(np + e);  // the group's V-node p: node lp of level l - 1
+    const int g0 = __ldcg(goff + j), pieces = max(1, __ldcg(goff + j + 1) - g0), piece = w - g0;
+    const int B = ep.B;
+    const long long ia = static_cast<long long>(ep.inode_base[l - 1] + lp) * 5;
+    if (!QV_IN_BOUNDS(kSiteInode, ep.inode_base[l - 1] + lp, pl.n_inodes)) return;
+    const int cnt = __ldcg(pl.count + l * E + e);
+    const int cg0 = min(__ldcg(pl.choff + ia), cnt);
+    const int cg1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
+    const int ncg = max(0, cg1 - cg0);
+    // this item's piece of the children
+    const int c0 = cg0 + static_cast<int>((static_cast<long long>(ncg) * piece) / pieces);
+    const int nc = cg0 + static_cast<int>((static_cast<long long>(ncg) * (piece + 1)) / pieces) - c0;
+    if (nc <= 0) return;
+    const float *par = node_belief(pl, ep, l - 1, lp);
+    const EpReg er = ep_reg(ep);
+    const Win win = support_window(pl, e, ep.H, ep.W, l + 1);
+    const int R = ep.range;
+    auto meets = [&](int k) {
+        const int br = S.bco[2 * k], bc = S.bco[2 * k + 1];
+        return !(br + R < win.r0 || br - R >= win.r1 || bc + R < win.c0 || bc - R >= win.c1);
+    };
+    int *klist = S.cnt;  // free until a node is finalised
+    auto list_beacons = [&]() {
+        __syncthreads();  // the previous readers of the list and the histograms are done
+        if (wid == 0) {
+            int n = 0;
+            for (int kb = 0; kb < B; kb += 32) {
+                const int k = kb + lane;
+                const bool hit = k < B && meets(k);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (hit) klist[n + __popc(bal & ((1u << lane) - 1u))] = k;
+                n += __popc(bal);
+            }
+            if (lane == 0) S.flags[9] = n;
+        }
+        __syncthreads();
+    };
+    // beacons whose diamond misses the window keep zero masses for every child
+    __syncthreads();  // the previous item's readers of the histograms are done
+    for (int i = threadIdx.x; i < B * 30; i += blockDim.x) {
+        const int k = i / 30, t = i - (i / 30) * 30;
+        if (meets(k)) continue;
+        if (t < 5) S.hist[t * Bm + k] = 0.0f;
+        else if (FUSED) S.histq[(((t - 5) / 5) * Bm + k) * 5 + (t - 5) % 5] = 0.0f;
+    }
+    list_beacons();
+    const int nlist = S.flags[9];
+    const bool resident = nlist <= kWarps && 2 * R + 1 <= kTileH && 2 * R + 1 <= kTileW;
+    int myk = -1, nh = 0;
+    TileBox bx{0, -1, 0, -1};
+    if (resident && wid < nlist) {
+        myk = klist[wid];
+        bx = tile_box(er, S.bco[2 * myk], S.bco[2 * myk + 1], win);
+        if (bx.rlo <= bx.rhi && bx.clo <= bx.chi) {
+            tile_load(er, par, false, bx.rlo, bx.clo, bx, tp, tc, tcw);
+            nh = tile_list(er, myk, S.bco[2 * myk], S.bco[2 * myk + 1], bx.rlo, bx.clo, bx, tcw, tlist);
+        }
+    }
+    for (int r = 0; r < nc; ++r) {
+        const int local = c0 + r;
+        const int gid = ep.node_base[l] + local, iid = ep.inode_base[l] + local;
+        if (!QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) return;  // uniform over the CTA
+        // the child's action, observation and Eq. 3 weights
+        const long long sl = __ldcg(pl.src_slot + gid);
+        if (!QV_IN_BOUNDS(kSiteSlot, sl, 5 * K * pl.n_inodes)) return;
+        const int pa = static_cast<int>((sl / K) % 5);
+        const int zc = __ldcg(pl.slot_z + sl);
+        const float p = __ldcg(pl.slot_P + sl);
+        const float sa = ep.acc / p, se = ep.eta / p;
+        if (!resident) list_beacons();
+        float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float lq[FUSED ? 25 : 1];
+#pragma unroll
+        for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
+        auto store_hist = [&](int k) {
+            // lane i ends with the warp total of value i: 0..4 the label
+            // masses, 5..29 the Q-weighted ones
+            float v[32];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) v[a] = la[a];
+#pragma unroll
+            for (int i = 0; i < 25; ++i) {
+                if constexpr (FUSED) v[5 + i] = lq[i];
+                else v[5 + i] = 0.0f;
+            }
+            v[30] = v[31] = 0.0f;
+            warp_reduce_scatter32(v);
+            if (lane < 5) S.hist[lane * Bm + k] = v[0];
+            else if (FUSED && lane < 30) S.histq[(((lane - 5) / 5) * Bm + k) * 5 + (lane - 5) % 5] = v[0];
+        };
+        if (resident) {
+            if (myk >= 0) {
+                if (nh > 0) {
+                    tile_form(er, pa, zc, sa, se, bx.rlo, bx.clo, bx, tp, tc, tcw, S.lut);
+                    tile_predict<FUSED>(er, bx.rlo, bx.clo, tc, tcw, tlist, nh, S.lut, la, lq);
+                }
+                store_hist(myk);
+            }
+        } else {
+            for (int li = wid; li < nlist; li += kWarps) {
+                const int k = klist[li];
+#pragma unroll
+                for (int a = 0; a < 5; ++a) la[a] = 0.0f;
+#pragma unroll
+                for (int i = 0; i < (FUSED ? 25 : 1); ++i) lq[i] = 0.0f;
+                label_tiles<FUSED>(er, par, false, pa, zc, sa, se, k, S.bco[2 * k], S.bco[2 * k + 1], win, tp, tc,
+                                   tcw, tlist, S.lut, la, lq);
+                store_hist(k);
+            }
+        }
+        __syncthreads();
+        node_totals(pl, l, ep, e, lp, local, iid, par, pa, zc, sa, se, true, S);
+        const unsigned long long code = __ldcg(pl.code + gid);
+        finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
     }
 }
 
@@ -1961,6 +2169,8 @@ __device__ bool phase_level(const PlanDev &pl, int l, bool store, Smem &S, uint6
     for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
         if (w < n_exp) {
             if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, true)) return false;
+        } else if (!NUMBER && __ldcg(pl.fchunks + l) == 0) {
+            finalize_group_item<FUSED>(pl, l, S, cur_e, w - n_exp);
         } else {
             finalize_item<FUSED, NUMBER>(pl, l, S, cur_e, w - n_exp, true);
         }
