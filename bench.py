@@ -330,19 +330,35 @@ def episodes_measurement(args, dev, stream, E=64, max_steps=200):
     api.run_episodes(m, Q, b0s[:4], starts[:4], depth=w.depth, K=w.K, seed=w.seed, max_steps=3)  # warm-up
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     torch.cuda.synchronize()
+    t0 = time.perf_counter()
     ev[0].record(stream)
     g = api.run_episodes(m, Q, b0s, starts, depth=w.depth, K=w.K, seed=w.seed, max_steps=max_steps)
     ev[1].record(stream)
     torch.cuda.synchronize()
+    wall_ms = 1e3 * (time.perf_counter() - t0)
     ms = ev[0].elapsed_time(ev[1])
+    # where the loop's time goes: the device time of one batched plan of the
+    # robots' start beliefs and of their beliefs after the loop (the plan is
+    # most of a step's GPU work; its support windows follow the beliefs)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    plan_ms = {}
+    for tag, bel in (("start_beliefs", b0s), ("end_beliefs", list(g["beliefs"].unbind(0)))):
+        p_ = api.Plan([m] * E, [Q] * E, [b.contiguous() for b in bel], depth=w.depth, K=w.K, seed=w.seed)
+        for _ in range(2):
+            p_.run()
+        plan_ms[tag] = time_device(p_.run, 10, flush, stream) / 10
+        del p_
+    del flush
     robot_steps = int(g["steps"].sum())
     ok = g["success"].astype(bool)
     out = {"episodes": E, "max_steps": max_steps, "steps_run": g["steps_run"], "ms": ms,
            "robot_steps": robot_steps, "robot_steps_per_s": robot_steps / (ms * 1e-3),
            "plans_per_s": E * g["steps_run"] / (ms * 1e-3),
            "success_rate": float(ok.mean()), "mean_steps_success": float(g["steps"][ok].mean()) if ok.any() else None,
-           "mean_return": float(g["ret"].mean()),
-           "note": "plans for finished episodes still run inside the batch (counted in plans_per_s)"}
+           "mean_return": float(g["ret"].mean()), "wall_ms": wall_ms,
+           "plan_device_ms": plan_ms,
+           "note": "plans for finished episodes still run inside the batch (counted in plans_per_s); "
+                   "plan_device_ms: one batched plan of the 64 beliefs alone, L2 flushed"}
     if not args.no_cpu:
         Qh = m.from_grid(Q).reshape(5, -1).astype("float64")
         t0 = time.perf_counter()

@@ -21,6 +21,7 @@
 // a row are contiguous ([H][5][pitch]) so that one bulk copy stages all of
 // them.
 #include <algorithm>
+#include <cstdlib>
 
 #include "qv_vi_cell.cuh"
 
@@ -52,13 +53,25 @@ struct FibArgs {
     unsigned *done;      // [gridDim.x] sweeps completed per CTA
     unsigned *arrive;    // [kResRing] cumulative residual postings per ring slot
     unsigned spin_limit;
+    // temporally blocked sweeps (k_fib_blocked)
+    int s;               // sweeps per exchange (1..kMaxBlock)
+    int R;               // rows owned per CTA
+    int nh;              // neighbouring CTAs on each side whose rows a block's halo reaches
+    T *hist;             // [2 s][H][5][P] alpha_k of the last two blocks, plane k mod 2 s
+    T *bres;             // [kResRing][kMaxBlock][gridDim.x] per-sweep residuals of a block
 };
+
+constexpr int kFIBThreads = 512;  // threads of a k_fib_blocked CTA
 
 template <typename T>
 __device__ __forceinline__ T fib_stage_reward(const FibArgs<T> &a, int y) {
     const float c = a.cost ? __ldg(a.cost + y) : 0.0f;
     return (y == a.goal) ? T(100) : T(-1) - T(c);
 }
+
+template <typename T>
+__device__ __forceinline__ T fib_core(const FibArgs<T> &a, const T (&al)[5][5], const unsigned (&lab)[5],
+                                      const T (&r)[5], T out[5]);
 
 // Eq. 7 for the five actions of a free, non-goal cell y; `rowp` points at
 // y's staged row (five planes of P values each, rows 5P apart).  Returns
@@ -95,6 +108,16 @@ __device__ __forceinline__ T fib_cell(const FibArgs<T> &a, int y, int col, unsig
             r[d] = fib_stage_reward(a, y + dy[d]);
         }
     }
+    return fib_core(a, al, lab, r, out);
+}
+
+// Eq. 7's backup of one free, non-goal cell from the alpha values al[d][b]
+// at the cell move d reaches (d = 4: the cell itself; a blocked move
+// reaches the cell itself, Eq. 10), their labels and their arrival rewards;
+// returns max_a |alpha'^a - alpha^a| at the cell.
+template <typename T>
+__device__ __forceinline__ T fib_core(const FibArgs<T> &a, const T (&al)[5][5], const unsigned (&lab)[5],
+                                      const T (&r)[5], T out[5]) {
     const T fwd = T(1) - T(2) * T(a.slip), eps = T(a.slip);
     const T dlt = a.acc - a.eta;
     T diff = T(0);
@@ -257,6 +280,205 @@ __global__ void __launch_bounds__(256) k_fib_iteration(FibArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------- temporally blocked sweeps
+// The same iteration with s sweeps per exchange, as k_vi_blocked does it for
+// the value iteration: CTA i owns rows [i R, i R + R) and stages alpha_{b s}
+// (five planes a row) on rows [i R - s, i R + R + s) once per block; sweep j
+// of the block covers the owned rows widened by s - 1 - j rows, reading the
+// cell words and arrival rewards from shared memory; every sweep's owned
+// rows go to plane k mod 2 s of a ring in global memory and its residual to
+// a per-block slot; the test of block b runs before block b + 2, so the
+// result is exactly the first alpha_{k+1} with max |alpha_{k+1} - alpha_k| <
+// tol (or alpha_truncated).
+template <typename T>
+__global__ void __launch_bounds__(kFIBThreads) k_fib_blocked(FibArgs<T> a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ T s_red[kFIBThreads / 32][kMaxBlock];
+    const int s = a.s, R = a.R, P = a.P, H = a.H, RS = 5 * P;
+    const int r_begin = static_cast<int>(blockIdx.x) * R, r_end = min(H, r_begin + R);
+    const int base = r_begin - s;  // grid row of shared row 0
+    const int nrows = R + 2 * s;
+    const int glo = max(0, base), ghi = min(H, base + nrows);  // grid rows held
+    const size_t nb = static_cast<size_t>(nrows) * RS;
+    T *const A0s = reinterpret_cast<T *>(smem_raw), *const A1s = A0s + nb;
+    T *const rws = A0s + 2 * nb;  // arrival rewards, [row][P]
+    uint16_t *cws = reinterpret_cast<uint16_t *>(rws + static_cast<size_t>(nrows) * P);
+    const size_t plane = static_cast<size_t>(H) * RS;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = static_cast<int>(blockDim.x);
+    const int rstep = P <= nt ? nt / P : 1;
+    const int rsub = P <= nt ? static_cast<int>(threadIdx.x) / P : 0;
+    const int c0 = P <= nt ? static_cast<int>(threadIdx.x) - rsub * P : static_cast<int>(threadIdx.x);
+    const int cstep = P <= nt ? P : nt;
+    const bool active = rsub < rstep;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    // cell words (the goal's free bit cleared: it is never updated) and
+    // arrival rewards of every row held, once
+    for (int i = threadIdx.x; i < (ghi - glo) * P; i += blockDim.x) {
+        const int y = glo * P + i;
+        const uint16_t cw = __ldg(a.cell + y);
+        cws[(glo - base) * P + i] = y == a.goal ? static_cast<uint16_t>(cw & 0x7FFFu) : cw;
+        rws[(glo - base) * P + i] = fib_stage_reward(a, y);
+    }
+    __syncthreads();
+    unsigned phase = 0;
+    const bool trunc = a.truncated > 0;
+    const int limit = trunc ? a.truncated : a.max_sweeps;
+    const int nblk = (limit + s - 1) / s;
+    int F = -1;
+    T res = T(0);
+    for (int b = 0; b < nblk; ++b) {
+        if (!trunc && b >= 2) {
+            int f;
+            T r;
+            if (!block_test(a, b - 2, s, false, f, r)) return;
+            if (f >= 0) {
+                F = f + 1;
+                res = r;
+                break;
+            }
+        }
+        const int k0 = b * s, ns = min(s, limit - k0);
+        if (b > 0 && !wait_range(a.done, b, a.nh, &a.work->status, a.spin_limit)) return;
+        const T *src = b == 0 ? a.A0 : a.hist + static_cast<size_t>(k0 % (2 * s)) * plane;
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            fence_proxy_async();
+            const unsigned bytes = static_cast<unsigned>((ghi - glo) * RS * sizeof(T));
+            mbar_arrive_expect_tx(&bar, bytes);
+            bulk_copy_g2s(A0s + (glo - base) * RS, src + static_cast<size_t>(glo) * RS, bytes, &bar);
+        }
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        const int failed = __syncthreads_or(ok ? 0 : 1);
+        if (failed) {
+            if (threadIdx.x == 0) atomicOr(&a.work->status, kErrTimeout);
+            if (!ok) mbar_wait_bounded(&bar, phase);  // let the copy in flight land before leaving
+            return;
+        }
+        phase ^= 1u;
+        int cur = 0;
+        for (int j = 0; j < ns; ++j) {
+            const int k = k0 + j;  // this sweep makes alpha_{k+1}
+            const int ext = ns - 1 - j;
+            const int lo = max(0, r_begin - ext), hi = min(H, r_end + ext);
+            T *dst = a.hist + static_cast<size_t>((k + 1) % (2 * s)) * plane;
+            const T *Ac = cur ? A1s : A0s;
+            T *An = cur ? A0s : A1s;
+            T lm = T(0);
+            if (active)
+                for (int row = lo + rsub; row < hi; row += rstep) {
+                    const bool own = row >= r_begin && row < r_end;
+                    const int sr = row - base;
+                    for (int col = c0; col < P; col += cstep) {
+                        const int t = sr * P + col;
+                        const unsigned cw = cws[t];
+                        const T *rowp = Ac + static_cast<size_t>(sr) * RS;
+                        T o[5] = {T(0), T(0), T(0), T(0), T(0)};
+                        T diff = T(0);
+                        if (QV_CELL_FREE(cw)) {  // free and not the goal
+                            const unsigned blk = QV_CELL_BLOCKED(cw);
+                            T al[5][5];
+                            unsigned lab[5];
+                            T r[5];
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) al[4][q] = rowp[q * P + col];
+                            lab[4] = QV_CELL_LABEL(cw);
+                            r[4] = rws[t];
+                            const int drow[4] = {-RS, 0, RS, 0};
+                            const int dcol[4] = {0, 1, 0, -1};
+                            const int dt[4] = {-P, 1, P, -1};
+#pragma unroll
+                            for (int d = 0; d < 4; ++d) {
+                                if (blk & (1u << d)) {
+#pragma unroll
+                                    for (int q = 0; q < 5; ++q) al[d][q] = al[4][q];
+                                    lab[d] = lab[4];
+                                    r[d] = r[4];
+                                } else {
+                                    const T *qp = rowp + drow[d] + col + dcol[d];
+#pragma unroll
+                                    for (int q = 0; q < 5; ++q) al[d][q] = qp[q * P];
+                                    lab[d] = QV_CELL_LABEL(static_cast<unsigned>(cws[t + dt[d]]));
+                                    r[d] = rws[t + dt[d]];
+                                }
+                            }
+                            diff = fib_core(a, al, lab, r, o);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) {
+                                const T dd = fabs(rowp[q * P + col]);
+                                diff = dd > diff ? dd : diff;
+                            }
+                        }
+                        T *np_ = An + static_cast<size_t>(sr) * RS + col;
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) np_[q * P] = o[q];
+                        if (own) {
+                            lm = diff > lm ? diff : lm;
+                            T *gp = dst + static_cast<size_t>(row) * RS + col;
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) gp[q * P] = o[q];
+                        }
+                    }
+                }
+            lm = warp_max(lm);
+            if (lane == 0) s_red[wid][j] = lm;
+            __syncthreads();
+            cur ^= 1;
+        }
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (threadIdx.x < ns) {
+            T m = T(0);
+            for (int w = 0; w < kFIBThreads / 32; ++w) m = s_red[w][threadIdx.x] > m ? s_red[w][threadIdx.x] : m;
+            a.bres[(static_cast<size_t>(b % kResRing) * kMaxBlock + threadIdx.x) * gridDim.x + blockIdx.x] = m;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.arrive + b % kResRing, 1u);
+        }
+        publish_step(a.done, static_cast<unsigned>(b + 1));
+    }
+    if (F < 0) {
+        for (int bt = max(0, nblk - 2); bt < nblk && F < 0; ++bt) {
+            const int ns = min(s, limit - bt * s);
+            if (trunc && bt < nblk - 1) continue;
+            int f;
+            T r;
+            if (!block_test(a, bt, ns, trunc, f, r)) return;
+            if (f >= 0) {
+                F = f + 1;
+                res = r;
+            } else if (bt == nblk - 1) {
+                F = limit;
+                res = r;
+            }
+        }
+    }
+    // alpha_F on this CTA's own rows (plane F mod 2 s, written by its own
+    // threads): Q and the caller's alpha
+    __syncthreads();
+    const T *Af = a.hist + static_cast<size_t>(F % (2 * s)) * plane;
+    const size_t qplane = static_cast<size_t>(H) * P;
+    const int n = (r_end - r_begin) * RS;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int rr = i / RS, rem = i - rr * RS;
+        const int q = rem / P, col = rem - q * P;
+        const size_t y = static_cast<size_t>(r_begin + rr) * P + col;
+        const T v = Af[static_cast<size_t>(r_begin) * RS + i];
+        a.Q[q * qplane + y] = static_cast<float>(v);
+        if (a.alpha_out) a.alpha_out[q * qplane + y] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.sweeps_out = F;
+        *a.residual_out = res;
+    }
+}
+
 template <typename T>
 size_t fib_ws_bytes(int H, int P, int nslots) {
     size_t b = sizeof(VIWork);
@@ -266,13 +488,70 @@ size_t fib_ws_bytes(int H, int P, int nslots) {
     b += kResRing * nslots * sizeof(T) + sizeof(int) + sizeof(T) + 64;
     b = (b + 255) & ~size_t(255);
     b += nslots * sizeof(unsigned) + 64;  // progress flags, residual arrival counters
+    b = (b + 255) & ~size_t(255);
+    b += 2 * kMaxBlock * static_cast<size_t>(H) * 5 * P * sizeof(T);  // the blocked sweeps' ring of planes
+    b = (b + 255) & ~size_t(255);
+    b += static_cast<size_t>(kResRing) * kMaxBlock * nslots * sizeof(T);  // their per-block residuals
     return (b + 255) & ~size_t(255);
+}
+
+// Shape of the blocked FIB sweeps (one 512-thread CTA per SM, R rows each,
+// s sweeps per exchange) from the same kind of cost model as the value
+// iteration's: an exchange of about 4 us shared by s sweeps against the
+// R + s - 1 rows a sweep computes on average, each cell's Eq. 7 backup about
+// six times a Bellman backup; the one-sweep-per-exchange kernel
+// (exchange plus cells per SM) is kept unless the blocked one is predicted
+// 10 % faster.  FP32 only (the FP64 backup needs more registers than a
+// 512-thread CTA leaves).  QVTS_VI_BLOCK (1, 2, 4, 8; "0") forces s or the
+// one-sweep kernel, as for the value iteration.
+template <typename T>
+bool fib_block_shape(int H, int P, int nsm, int &G, int &R, int &s, int &nh, size_t &smem) {
+    if (sizeof(T) != 4) return false;
+    R = (H + nsm - 1) / nsm;
+    G = (H + R - 1) / R;
+    const char *env = std::getenv("QVTS_VI_BLOCK");
+    const int forced = env ? std::atoi(env) : 0;
+    if (env && *env && forced == 0) return false;
+    const double xb = 4000.0, cb = 2.5, ob = 1000.0;  // ns: exchange, per cell computed, fixed
+    const double xo = 4300.0, co = 4.6;
+    const double t_old = xo + co * static_cast<double>(H) * P / nsm;
+    double best = 1e30;
+    for (int c : {8, 4, 2, 1}) {
+        if (forced > 0 && c != forced) continue;
+        const int h = (c + R - 1) / R;
+        const size_t sm = static_cast<size_t>(R + 2 * c) * P * (10 * sizeof(T) + sizeof(T) + sizeof(uint16_t));
+        if (2 * h > 32 || sm > 200 * 1024) continue;
+        const double t = xb / c + cb * static_cast<double>(R + c - 1) * P + ob;
+        if (t < best) {
+            best = t;
+            s = c;
+            nh = h;
+            smem = sm;
+        }
+    }
+    if (best > 1e29) return false;
+    return forced > 0 || best < 0.9 * t_old;
 }
 
 template <typename T>
 qv_status run_fib(const qv_model_t *m, double tol, int max_sweeps, int truncated, T *d_alpha, float *d_Q,
                   void *d_ws, size_t ws_bytes, int *sweeps_out, double *residual_out, cudaStream_t st) {
     const int H = m->H, P = m->pitch;
+    int bG = 0, bR = 0, bs = 0, bnh = 0;
+    size_t bsmem = 0;
+    bool blocked = fib_block_shape<T>(H, P, qv_num_sms(), bG, bR, bs, bnh, bsmem) && bG <= 1024;
+    if (blocked) {
+        void *bk = reinterpret_cast<void *>(k_fib_blocked<T>);
+        if (qv_check_cuda(cudaFuncSetAttribute(bk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(bsmem)),
+                          "smem attr") != QV_OK)
+            return QV_ERR_CUDA;
+        int per_sm = 0;
+        if (qv_check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bk, kFIBThreads, bsmem),
+                          "occupancy") != QV_OK)
+            return QV_ERR_CUDA;
+        blocked = per_sm >= 1 && bG <= per_sm * qv_num_sms();
+    }
     const size_t row_bytes = static_cast<size_t>(5) * P * sizeof(T);
     int dev = 0, optin = 0;
     if (qv_check_cuda(cudaGetDevice(&dev), "device") != QV_OK ||
@@ -350,10 +629,24 @@ qv_status run_fib(const qv_model_t *m, double tol, int max_sweeps, int truncated
     a.done = flags;
     a.arrive = arrive;
     a.spin_limit = qv_cross_spin_limit();
+    const size_t off_hist = (off_flags + 1024 * sizeof(unsigned) + 64 + 255) & ~size_t(255);
+    a.hist = reinterpret_cast<T *>(ws + off_hist);
+    const size_t off_bres =
+        (off_hist + 2 * kMaxBlock * static_cast<size_t>(H) * 5 * P * sizeof(T) + 255) & ~size_t(255);
+    a.bres = reinterpret_cast<T *>(ws + off_bres);
+    a.s = bs;
+    a.R = bR;
+    a.nh = bnh;
     void *args[] = {&a};
-    if (qv_check_cuda(cudaLaunchCooperativeKernel(kern, grid, 256, args, smem, st), "FIB iteration launch") !=
-        QV_OK)
+    if (blocked) {
+        if (qv_check_cuda(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_fib_blocked<T>), bG, kFIBThreads,
+                                                      args, bsmem, st),
+                          "FIB iteration launch") != QV_OK)
+            return QV_ERR_CUDA;
+    } else if (qv_check_cuda(cudaLaunchCooperativeKernel(kern, grid, 256, args, smem, st), "FIB iteration launch") !=
+               QV_OK) {
         return QV_ERR_CUDA;
+    }
     VIWork hw;
     int hs = 0;
     T hr = T(0);

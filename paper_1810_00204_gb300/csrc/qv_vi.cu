@@ -54,7 +54,6 @@ struct VIArgs {
     T *bres;             // [kResRing][kMaxBlock][gridDim.x] per-sweep residuals of a block
 };
 
-constexpr int kMaxBlock = 8;       // sweeps per exchange at most
 constexpr int kVIBThreads = 1024;  // threads of a k_vi_blocked CTA
 
 // Jacobi sweeps by bands of rows, one band per CTA.  Sweep k reads one halo
@@ -197,82 +196,6 @@ __global__ void __launch_bounds__(256) k_value_iteration(VIArgs<T> a) {
 // residual over every CTA is below tol) is taken before block b + 2, the
 // first block that reuses b's planes: the result is exactly the first
 // V_{k+1} with max |V_{k+1} - V_k| < tol, as in k_value_iteration.
-
-// Bounded wait for the CTAs within nh of this one to have completed `step`
-// blocks (lane c of warp 0 watches CTA blockIdx.x - nh + c).
-__device__ bool wait_range(const unsigned *done, unsigned step, int nh, unsigned *status, unsigned limit) {
-    __shared__ int s_ok;
-    if (threadIdx.x < 32) {
-        int ok = 1;
-        const int nb = static_cast<int>(blockIdx.x) - nh + static_cast<int>(threadIdx.x) +
-                       (static_cast<int>(threadIdx.x) >= nh ? 1 : 0);  // skip this CTA
-        if (static_cast<int>(threadIdx.x) < 2 * nh && nb >= 0 && nb < static_cast<int>(gridDim.x)) {
-            unsigned i = 0;
-            while (ld_acquire(done + nb) < step) {
-                if (++i > limit || (*((volatile unsigned *)status) & kErrTimeout)) {
-                    atomicOr(status, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        ok = __all_sync(0xffffffffu, ok);
-        if (threadIdx.x == 0) s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// The stopping test of block bt: waits (bounded) until every CTA has posted
-// it, then f = the first sweep k of the block whose largest residual is below
-// tol (-1 if none) and r = that residual; with last_only, r = the residual of
-// the block's last sweep (a truncated run).  Same result in every CTA.
-template <typename T>
-__device__ bool block_test(const VIArgs<T> &a, int bt, int ns, bool last_only, int &f, T &r) {
-    __shared__ int s_ok;
-    __shared__ T s_m[kMaxBlock];
-    const unsigned G = gridDim.x;
-    if (threadIdx.x == 0) {
-        const unsigned want = G * static_cast<unsigned>(bt / kResRing + 1);
-        unsigned i = 0;
-        int ok = 1;
-        while (ld_acquire(a.arrive + bt % kResRing) < want) {
-            if (++i > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
-                atomicOr(&a.work->status, kErrTimeout);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    if (!s_ok) return false;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T *slot = a.bres + static_cast<size_t>(bt % kResRing) * kMaxBlock * G;
-    for (int j = wid; j < ns; j += kVIBThreads / 32) {
-        T m = T(0);
-        for (unsigned c = lane; c < G; c += 32) {
-            const T v = __ldcg(slot + static_cast<size_t>(j) * G + c);
-            m = v > m ? v : m;
-        }
-        m = warp_max(m);
-        if (lane == 0) s_m[j] = m;
-    }
-    __syncthreads();
-    f = -1;
-    r = s_m[ns - 1];
-    if (!last_only)
-        for (int j = 0; j < ns; ++j)
-            if (s_m[j] < a.tol) {
-                f = bt * a.s + j;
-                r = s_m[j];
-                break;
-            }
-    __syncthreads();
-    return true;
-}
 
 // r(x) for a free cell x (the arrival reward of Sec. V's cost): +100 at the
 // goal, -1 - c(x) elsewhere

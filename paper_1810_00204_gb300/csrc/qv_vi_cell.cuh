@@ -140,6 +140,88 @@ __device__ bool sweep_residual(const Args &a, int j, T &res) {
     return true;
 }
 
+// Temporally blocked sweeps (k_vi_blocked, k_fib_blocked) run at most this
+// many sweeps between two exchanges with the neighbouring CTAs; `Args`
+// provides s, bres ([kResRing][kMaxBlock][gridDim.x] per-sweep residuals of
+// a block), arrive, tol, work and spin_limit.
+constexpr int kMaxBlock = 8;
+
+// Bounded wait for the CTAs within nh of this one to have completed `step`
+// blocks (lane c of warp 0 watches CTA blockIdx.x - nh + c).
+static __device__ bool wait_range(const unsigned *done, unsigned step, int nh, unsigned *status, unsigned limit) {
+    __shared__ int s_ok;
+    if (threadIdx.x < 32) {
+        int ok = 1;
+        const int nb = static_cast<int>(blockIdx.x) - nh + static_cast<int>(threadIdx.x) +
+                       (static_cast<int>(threadIdx.x) >= nh ? 1 : 0);  // skip this CTA
+        if (static_cast<int>(threadIdx.x) < 2 * nh && nb >= 0 && nb < static_cast<int>(gridDim.x)) {
+            unsigned i = 0;
+            while (ld_acquire(done + nb) < step) {
+                if (++i > limit || (*((volatile unsigned *)status) & kErrTimeout)) {
+                    atomicOr(status, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The stopping test of block bt: waits (bounded) until every CTA has posted
+// it, then f = the first sweep k of the block whose largest residual is below
+// tol (-1 if none) and r = that residual; with last_only, r = the residual of
+// the block's last sweep (a truncated run).  Same result in every CTA.
+template <typename T, typename Args>
+__device__ bool block_test(const Args &a, int bt, int ns, bool last_only, int &f, T &r) {
+    __shared__ int s_ok;
+    __shared__ T s_m[kMaxBlock];
+    const unsigned G = gridDim.x;
+    if (threadIdx.x == 0) {
+        const unsigned want = G * static_cast<unsigned>(bt / kResRing + 1);
+        unsigned i = 0;
+        int ok = 1;
+        while (ld_acquire(a.arrive + bt % kResRing) < want) {
+            if (++i > a.spin_limit || (*((volatile unsigned *)&a.work->status) & kErrTimeout)) {
+                atomicOr(&a.work->status, kErrTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *slot = a.bres + static_cast<size_t>(bt % kResRing) * kMaxBlock * G;
+    for (int j = wid; j < ns; j += static_cast<int>(blockDim.x >> 5)) {
+        T m = T(0);
+        for (unsigned c = lane; c < G; c += 32) {
+            const T v = __ldcg(slot + static_cast<size_t>(j) * G + c);
+            m = v > m ? v : m;
+        }
+        m = warp_max(m);
+        if (lane == 0) s_m[j] = m;
+    }
+    __syncthreads();
+    f = -1;
+    r = s_m[ns - 1];
+    if (!last_only)
+        for (int j = 0; j < ns; ++j)
+            if (s_m[j] < a.tol) {
+                f = bt * a.s + j;
+                r = s_m[j];
+                break;
+            }
+    __syncthreads();
+    return true;
+}
+
 template <typename T, typename Args>
 __device__ __forceinline__ T arrive_value(const Args &a, int y, const T *Vs_row, int col) {
     // r(y) + gamma V(y) for a free cell y
