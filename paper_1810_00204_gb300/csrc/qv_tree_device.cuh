@@ -2092,6 +2092,56 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
             nh = tile_list(er, myk, S.bco[2 * myk], S.bco[2 * myk + 1], bx.rlo, bx.clo, bx, tcw, tlist);
         }
     }
+    // the group's expand items all done (bounded wait), then the totals of
+    // every child of the piece at once -- final, or the records of the
+    // group's items in item order -- into S.acc (free in a finalize item),
+    // and p's values at the goal and its four neighbours (every child's
+    // belief there is formed from them)
+    {
+        const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + j);
+        const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
+        const int nit = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
+        if (threadIdx.x == 0) {
+            const unsigned *gd = pl.grp_done + pl.gbase[l] + j;
+            unsigned i = 0;
+            for (;;) {
+                unsigned v;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
+                if (v >= static_cast<unsigned>(nit)) break;
+                if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+                    atomicOr(pl.status, kErrTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
+            const int rr = i / kTot, v = i - rr * kTot;
+            float sum = 0.0f;
+            if (rec < 0) {
+                sum = __ldcg(pl.ntot + static_cast<long long>(ep.inode_base[l] + c0 + rr) * kTot + v);
+            } else {
+                const int rk = c0 - cg0 + rr;  // the child's rank in the group
+                for (int it = 0; it < nit; ++it) {
+                    const long long x = static_cast<long long>(rec + it) * pl.cmax + rk;
+                    sum += x < pl.n_xrec ? __ldcg(pl.xrec + x * kTot + v) : 0.0f;
+                }
+            }
+            S.acc[i] = sum;
+        }
+        if (wid == 0) {
+            const int y = ep.goal, P = ep.P, gr = y / P, gc = y - gr * P;
+            const int dy[5] = {0, -P, 1, P, -1};
+            const bool inside = lane < 5 && (lane != 1 || gr > 0) && (lane != 2 || gc + 1 < P) &&
+                                (lane != 3 || gr + 1 < ep.H) && (lane != 4 || gc > 0);
+            const float pv = inside ? __ldcg(par + y + dy[lane < 5 ? lane : 0]) : 0.0f;
+            if (lane < 5) S.uq[lane] = pv;  // S.uq is written by finalize_node only at its end
+        }
+        __syncthreads();
+    }
+    const unsigned cwg = __ldg(ep.cell + ep.goal);
+    const float pg0 = S.uq[0], pgN = S.uq[1], pgE = S.uq[2], pgS = S.uq[3], pgW = S.uq[4];
     for (int r = 0; r < nc; ++r) {
         const int local = c0 + r;
         const int gid = ep.node_base[l] + local, iid = ep.inode_base[l] + local;
@@ -2144,8 +2194,21 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
                 store_hist(k);
             }
         }
+        // the child's totals and its belief at the goal (whose arrivals
+        // R(b, a) must not pay)
+        if (threadIdx.x < kTot) S.tot[threadIdx.x] = S.acc[r * kTot + threadIdx.x];
+        if (threadIdx.x == 0) {
+            const unsigned in = QV_CELL_INFLOW(cwg);
+            float nb[4];
+            nb[kDirN] = (in & 1u) ? pgN : 0.0f;
+            nb[kDirE] = (in & 2u) ? pgE : 0.0f;
+            nb[kDirS] = (in & 4u) ? pgS : 0.0f;
+            nb[kDirW] = (in & 8u) ? pgW : 0.0f;
+            const float bg = predict_one(nb, pg0, cwg, true, ep.slip, S.lut, pa) *
+                             (static_cast<int>(QV_CELL_LABEL(cwg)) == zc ? sa : se);
+            S.flags[4] = __float_as_int(bg);
+        }
         __syncthreads();
-        node_totals(pl, l, ep, e, lp, local, iid, par, pa, zc, sa, se, true, S);
         const unsigned long long code = __ldcg(pl.code + gid);
         finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
     }
