@@ -2130,6 +2130,31 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
             }
             S.acc[i] = sum;
         }
+        // every child's action, observation, Eq. 3 weights and path code
+        // (S.c_* and S.red are free in a finalize item)
+        unsigned long long *codes = reinterpret_cast<unsigned long long *>(S.red);
+        for (int rr = threadIdx.x; rr < nc; rr += blockDim.x) {
+            const int gid = ep.node_base[l] + c0 + rr;
+            int a = 0, z = 0;
+            float ca = 0.0f, ce = 0.0f;
+            unsigned long long cd = 0ull;
+            if (QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) {
+                const long long sl = __ldcg(pl.src_slot + gid);
+                cd = __ldcg(pl.code + gid);
+                if (QV_IN_BOUNDS(kSiteSlot, sl, 5 * K * pl.n_inodes)) {
+                    a = static_cast<int>((sl / K) % 5);
+                    z = __ldcg(pl.slot_z + sl);
+                    const float p = __ldcg(pl.slot_P + sl);
+                    ca = ep.acc / p;
+                    ce = ep.eta / p;
+                }
+            }
+            S.c_pa[rr] = a;
+            S.c_z[rr] = z;
+            S.c_sa[rr] = ca;
+            S.c_se[rr] = ce;
+            codes[rr] = cd;
+        }
         if (wid == 0) {
             const int y = ep.goal, P = ep.P, gr = y / P, gc = y - gr * P;
             const int dy[5] = {0, -P, 1, P, -1};
@@ -2147,12 +2172,8 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
         const int gid = ep.node_base[l] + local, iid = ep.inode_base[l] + local;
         if (!QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) return;  // uniform over the CTA
         // the child's action, observation and Eq. 3 weights
-        const long long sl = __ldcg(pl.src_slot + gid);
-        if (!QV_IN_BOUNDS(kSiteSlot, sl, 5 * K * pl.n_inodes)) return;
-        const int pa = static_cast<int>((sl / K) % 5);
-        const int zc = __ldcg(pl.slot_z + sl);
-        const float p = __ldcg(pl.slot_P + sl);
-        const float sa = ep.acc / p, se = ep.eta / p;
+        const int pa = S.c_pa[r], zc = S.c_z[r];
+        const float sa = S.c_sa[r], se = S.c_se[r];
         if (!resident) list_beacons();
         float la[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         float lq[FUSED ? 25 : 1];
@@ -2209,7 +2230,7 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
             S.flags[4] = __float_as_int(bg);
         }
         __syncthreads();
-        const unsigned long long code = __ldcg(pl.code + gid);
+        const unsigned long long code = reinterpret_cast<const unsigned long long *>(S.red)[r];
         finalize_node(pl, ep, l, local, FUSED, __int_as_float(S.flags[4]), code, S);
     }
 }
