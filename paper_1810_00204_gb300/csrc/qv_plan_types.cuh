@@ -84,6 +84,14 @@ struct PlanDev {
     int kslots;        // per-warp child slots of the expand phase (expand_slots)
     int n_xrec;        // per-(item, child) total records of multi-item groups
     int n_frec;        // floats of the finalize chunk records
+    // the deepest fused level's contraction form (ctr_item): allowed by the
+    // host (ctr), chosen per run by the work lists (c_mode[0]); work items
+    // per episode as a prefix (c_items [E+1]) and each episode's first
+    // total record in xrec (c_rbase [E])
+    int ctr;
+    int *c_items;
+    int *c_rbase;
+    int *c_mode;
     uint64_t seed;
     const EpDev *eps;
     float *beliefs;

@@ -21,7 +21,7 @@ struct Layout {
         off_weight, off_pz, off_value, off_code, off_src_slot, off_node_cnt, off_R, off_UQ, off_nchild, off_choff, off_samples,
         off_slot_z, off_slot_cnt, off_slot_P, off_slot_w, off_slot_val, off_slot_arg, off_leaf_arg, off_ep_cnt, off_lvl_cnt, off_partials,
         off_leaf_split, off_leaf_cnt,
-        off_status, off_boundary, off_bar, off_win, off_dirty, off_work, off_grp_done, off_stamps, off_result,
+        off_status, off_boundary, off_bar, off_win, off_dirty, off_work, off_grp_done, off_stamps, off_result, off_c_items, off_c_rbase, off_c_mode,
         off_beliefs;
     long long NT = 0, NI = 0, n_belief = 0;
     int Bmax = 1, rec_len = 0, grid = 0, target = 0, n_part = 0, cmax = 0;
@@ -30,6 +30,7 @@ struct Layout {
     long long ngrp_cap = 0;  // group slots over every level
     int band_cells = 0, items_per_cta = 0;  // the launch-shape knobs in effect
     int sb_floats = 0, sp_floats = 0, q_floats = 0;
+    int ctr = 0;  // the deepest fused level may take the contraction form
     size_t smem = 0;
     std::vector<qv::EpDev> eps;
 };
@@ -199,6 +200,15 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
         if (p->leaf_mode == QV_LEAF_FUSED && D > 0) L.q_floats = std::max(L.q_floats, 5 * ep.band_rows * ep.P);
     }
     L.cmax = 5 * std::min(K, L.Bmax + 1);
+    // the contraction form of the deepest fused level works in the band
+    // buffers: grow the Q buffer until they hold its arrays
+    L.ctr = (p->leaf_mode == QV_LEAF_FUSED && D >= 2) ? 1 : 0;
+    if (L.ctr) {
+        const qv::SmemLayout s0 =
+            qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax, qv::expand_slots(L.cmax));
+        const size_t need = sizeof(float) * static_cast<size_t>(qv::ctr_layout().total) + 64;
+        if (s0.band_end - s0.sb < need) L.q_floats += static_cast<int>((need - (s0.band_end - s0.sb)) / sizeof(float)) + 16;
+    }
     L.smem = qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax, qv::expand_slots(L.cmax))
                  .total;
     if (L.smem > 200 * 1024) return qv_set_error(QV_ERR_INVALID, "plan: %zu bytes of shared memory", L.smem);
@@ -218,7 +228,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     // sized for the largest grid so that sizing needs no device
     const long long per_sm = std::max<long long>(1, std::min<long long>(8, (228 * 1024) / std::max<size_t>(L.smem, 1)));
     const long long tmax = static_cast<long long>(L.items_per_cta) * kSizingSMs * per_sm;
-    L.n_xrec = 2 * tmax * L.cmax;
+    L.n_xrec = (L.ctr ? 6 : 2) * tmax * L.cmax;
     L.n_frec = tmax * 30 * ((L.Bmax + 1) / 2) + 30LL * L.Bmax;
     long long gbase = 0, ibase = 0;
     long long run_g[QV_MAX_DEPTH + 1], run_i[QV_MAX_DEPTH + 1];
@@ -279,6 +289,9 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.off_npre = take(sizeof(int) * D1 * E1);
     L.off_fchunks = take(sizeof(int) * D1);
     L.off_wb_fin = take(sizeof(int) * D1 * E1);
+    L.off_c_items = take(sizeof(int) * E1);
+    L.off_c_rbase = take(sizeof(int) * E1);
+    L.off_c_mode = take(sizeof(int));
     L.off_ntot = take(sizeof(float) * L.NI * qv::kTot);
     L.off_xrec = take(sizeof(float) * L.n_xrec * qv::kTot);
     L.off_frec = take(sizeof(float) * L.n_frec);
@@ -442,6 +455,10 @@ extern "C" qv_status qv_plan_create(int32_t E, const qv_model_t *models, const f
     d.npre = at<int>(ws, L.off_npre);
     d.fchunks = at<int>(ws, L.off_fchunks);
     d.wb_fin = at<int>(ws, L.off_wb_fin);
+    d.ctr = L.ctr;
+    d.c_items = at<int>(ws, L.off_c_items);
+    d.c_rbase = at<int>(ws, L.off_c_rbase);
+    d.c_mode = at<int>(ws, L.off_c_mode);
     d.ntot = at<float>(ws, L.off_ntot);
     d.xrec = at<float>(ws, L.off_xrec);
     d.frec = at<float>(ws, L.off_frec);

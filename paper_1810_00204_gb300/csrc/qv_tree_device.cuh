@@ -121,10 +121,49 @@ __global__ void k_bounds_collect(unsigned *status) {
 #define QV_IN_BOUNDS(site, i, n) true
 #endif
 
+// The contraction form of the deepest fused level (ctr_item): a row
+// segment of kCSC cells at a time, children in blocks of at most kCMB (of
+// at most kCPar parents: every V-node has at least five children), 36
+// planes per cell (the kTot totals).  Its arrays live in the band buffers.
+constexpr int kCSC = 64;
+constexpr int kCMB = 64;
+constexpr int kCPar = kCMB / 5 + 3;
+// staged columns: the segment with a one-cell rim, rounded out to 8-column
+// chunks so that every copy is 16 bytes on a 16-byte boundary
+constexpr int kCSW = kCSC + 16;
+constexpr int kCBP = kCSC + 1;  // row stride of the predicted beliefs (rows of different children fall in different banks)
+struct CtrLayout {
+    int par, q, cost, cw, bp, W, cpi, ca, cz, csa, cse, total;  // float offsets from the band buffers
+};
+__host__ __device__ inline CtrLayout ctr_layout() {
+    CtrLayout c;
+    int o = 0;
+    auto take = [&](int n) {
+        o = (o + 3) & ~3;  // 16-byte aligned
+        const int r = o;
+        o += n;
+        return r;
+    };
+    // two stages of the staged rows y - 1 .. y + 1 (double-buffered copies)
+    c.par = take(2 * kCPar * 3 * kCSW);  // [stage][parent][row][column] the parents' values
+    c.q = take(2 * 5 * 3 * kCSW);        // [stage][a'][row][column] Q
+    c.cost = take(2 * 3 * kCSW);         // [stage][row][column] the cost map
+    c.cw = take(2 * 3 * kCSW / 2);       // [stage][row][column] cell words (uint16)
+    c.bp = take(kCPar * 5 * kCBP);       // [parent][a][cell] the parents' predicted beliefs T_a b_p
+    c.W = take(kCSC * kTot);             // [cell][plane] T_a^T of the null, reward and null-Q weights
+    c.cpi = take(kCMB);                  // per child of the block: parent slot, action, observation, alpha / P, eta / P
+    c.ca = take(kCMB);
+    c.cz = take(kCMB);
+    c.csa = take(kCMB);
+    c.cse = take(kCMB);
+    c.total = o;
+    return c;
+}
+
 // Shared-memory carve-up of k_plan (same arithmetic on host and device).
 struct SmemLayout {
     size_t sb, sp, cw, q, tile, ep, bco, hist, histq, tot, red, P, C, cnt, T, uq, lut, lut4, u_n, u_off, u_z, u_sa, u_se,
-        scan, flags, acc, c_pa, c_z, c_sa, c_se, wpart, wchild, total;
+        scan, flags, acc, c_pa, c_z, c_sa, c_se, wpart, wchild, band_end, total;
     __host__ __device__ static SmemLayout make(int sb_floats, int sp_floats, int q_floats, int Bm, int K, int cmax,
                                                int kslots) {
         SmemLayout s;
@@ -144,6 +183,7 @@ struct SmemLayout {
         // only expand and update items use (a CTA runs one item at a time,
         // with a CTA barrier between items), as far as they are large enough
         const size_t band_end = o;
+        s.band_end = band_end;
         size_t in = s.sb;
         auto place = [&](size_t bytes) {
             const size_t r = (in + 15) & ~size_t(15);
@@ -955,8 +995,94 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         // group mode: one finalize item per expand item, a group's children
         // cut into as many pieces as it has expand items
         if (grp_mode) pl.wb_fin[l1 * (E + 1) + E] = wi;
-        if (static_cast<long long>(wr) * pl.cmax > pl.n_xrec) atomicOr(pl.status, kErrCapacity);
     }
+    // the contraction form of the deepest fused level (ctr_item) in place of
+    // the group expand items: per episode, work items in proportion to its
+    // children times its window's cells (at least one, at most one per
+    // window row), all of them within the total records xrec holds; when
+    // they cannot fit, the level keeps the group expand items
+    bool groups = true;  // the level's expand runs as group items
+    if (pl.ctr && l1 == pl.depth - 1 && pl.leaf_mode == QV_LEAF_FUSED) {
+        unsigned long long *wsum = reinterpret_cast<unsigned long long *>(S.red);
+        __syncthreads();
+        if (threadIdx.x < 2) wsum[threadIdx.x] = 0ull;
+        __syncthreads();
+        auto geom = [&](int e, long long &n, long long &rows, long long &cells) {
+            const EpDev *ep = pl.eps + e;
+            const Win v = support_window(pl, e, __ldg(&ep->H), __ldg(&ep->W), l1);
+            n = __ldcg(pl.count + l1 * E + e);
+            rows = max(0, v.r1 - v.r0);
+            cells = rows * max(0, v.c1 - v.c0);
+        };
+        unsigned long long wl = 0;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            long long n, rows, cells;
+            geom(e, n, rows, cells);
+            wl += static_cast<unsigned long long>(n * max(cells, 1LL));
+        }
+        atomicAdd(wsum, wl);  // integer sums: the same items whatever the order
+        __syncthreads();
+        const unsigned long long wt = max(wsum[0], 1ull);
+        // items of episode e, scaled by num / den when den > 0
+        auto items_of = [&](int e, unsigned long long num, unsigned long long den) -> long long {
+            long long n, rows, cells;
+            geom(e, n, rows, cells);
+            if (n <= 0) return 0;
+            const unsigned long long w = static_cast<unsigned long long>(n * max(cells, 1LL));
+            long long it = static_cast<long long>((static_cast<unsigned long long>(pl.target) * w + wt - 1) / wt);
+            it = min(max(it, 1LL), max(rows, 1LL));
+            if (den > 0) it = max(1LL, static_cast<long long>(static_cast<unsigned long long>(it) * num / den));
+            return it;
+        };
+        unsigned long long rl = 0;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            long long n, rows, cells;
+            geom(e, n, rows, cells);
+            rl += static_cast<unsigned long long>(items_of(e, 0, 0) * n);
+        }
+        atomicAdd(wsum + 1, rl);
+        __syncthreads();
+        const unsigned long long r0 = wsum[1], cap = static_cast<unsigned long long>(max(pl.n_xrec, 0));
+        const unsigned long long num = r0 > cap ? cap : 0ull, den = r0 > cap ? r0 : 0ull;
+        __syncthreads();
+        if (threadIdx.x == 0) wsum[1] = 0ull;
+        __syncthreads();
+        rl = 0;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            long long n, rows, cells;
+            geom(e, n, rows, cells);
+            rl += static_cast<unsigned long long>(items_of(e, num, den) * n);
+        }
+        atomicAdd(wsum + 1, rl);
+        __syncthreads();
+        const bool fits = wsum[1] <= cap;
+        groups = !fits;
+        int ci = 0, cr = 0;
+        for (int base = 0; base < E; base += blockDim.x) {
+            const int e = base + threadIdx.x;
+            int vi = 0, vr = 0;
+            if (e < E && fits) {
+                long long n, rows, cells;
+                geom(e, n, rows, cells);
+                vi = static_cast<int>(items_of(e, num, den));
+                vr = static_cast<int>(vi * n);
+            }
+            int ti, tr;
+            const int xi = block_exclusive_scan(vi, S.scan, ti);
+            const int xr = block_exclusive_scan(vr, S.scan, tr);
+            if (e < E) {
+                pl.c_items[e] = ci + xi;
+                pl.c_rbase[e] = cr + xr;
+            }
+            ci += ti;
+            cr += tr;
+        }
+        if (threadIdx.x == 0) {
+            pl.c_items[E] = ci;
+            pl.c_mode[0] = fits ? 1 : 0;
+        }
+    }
+    if (threadIdx.x == 0 && groups && static_cast<long long>(wr) * pl.cmax > pl.n_xrec) atomicOr(pl.status, kErrCapacity);
 }
 
 // A node of episode e at level l is final: the last one numbers the
@@ -1738,6 +1864,42 @@ __device__ void label_tiles(const EpReg &ep, const float *par, bool root, int pa
 // item order -- into S.tot, and its belief at the goal (whose arrivals
 // R(b, a) must not pay) into S.flags[4].  With wait_group, first waits
 // (bounded) until every expand item of its group has counted itself done.
+// Totals of the deepest fused level's contraction form (ctr_item).
+// A child's total v: its records of items 0 .. items - 1 added in item order.
+__device__ __forceinline__ float ctr_total(const PlanDev &pl, int rb, int items, int n, int c, int v) {
+    float sum = 0.0f;
+    for (int i0 = 0; i0 < items; i0 += 8) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const long long x = static_cast<long long>(rb) + static_cast<long long>(i0 + u) * n + c;
+            t[u] = (i0 + u < items && x < pl.n_xrec) ? __ldcg(pl.xrec + x * kTot + v) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += t[u];
+    }
+    return sum;
+}
+
+__device__ __forceinline__ bool ctr_level(const PlanDev &pl, int l) {
+    return pl.ctr && l >= 1 && l == pl.depth - 1 && pl.leaf_mode == QV_LEAF_FUSED && __ldcg(pl.c_mode) != 0;
+}
+
+// Bounded wait until *gd >= need (thread 0; the caller's barrier follows).
+__device__ __forceinline__ void wait_count(const PlanDev &pl, const unsigned *gd, unsigned need) {
+    unsigned i = 0;
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
+        if (v >= need) break;
+        if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
+            atomicOr(pl.status, kErrTimeout);
+            break;
+        }
+        __nanosleep(64);
+    }
+}
+
 __device__ void node_totals(const PlanDev &pl, int l, const EpDev &ep, int e, int lp, int local, int iid,
                             const float *par, int pa, int zc, float sa, float se, bool wait_group, Smem &S) {
     const int E = pl.E;
@@ -1754,24 +1916,19 @@ __device__ void node_totals(const PlanDev &pl, int l, const EpDev &ep, int e, in
     constexpr int kGroups = kThreads / kTot;  // partial sums per value
     const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
     const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
+    const bool cform = ctr_level(pl, l);
+    const int cit0 = cform ? __ldcg(pl.c_items + e) : 0;
+    const int citems = cform ? __ldcg(pl.c_items + e + 1) - cit0 : 0;
     if (wait_group) {
-        if (threadIdx.x == 0) {
-            const unsigned *gd = pl.grp_done + pl.gbase[l] + jg;
-            unsigned i = 0;
-            for (;;) {
-                unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
-                if (v >= static_cast<unsigned>(nit)) break;
-                if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
-                    atomicOr(pl.status, kErrTimeout);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
+        if (threadIdx.x == 0)
+            wait_count(pl, pl.grp_done + pl.gbase[l] + (cform ? e : jg), static_cast<unsigned>(cform ? citems : nit));
         __syncthreads();
     }
-    if (rec < 0) {
+    if (cform) {
+        if (threadIdx.x < kTot)
+            S.tot[threadIdx.x] = ctr_total(pl, __ldcg(pl.c_rbase + e), citems, __ldcg(pl.count + l * E + e), local,
+                                           threadIdx.x);
+    } else if (rec < 0) {
         if (threadIdx.x < kTot) S.tot[threadIdx.x] = __ldcg(pl.ntot + static_cast<long long>(iid) * kTot + threadIdx.x);
     } else {
         const int t = threadIdx.x % kTot, g = threadIdx.x / kTot;
@@ -2101,25 +2258,20 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
         const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + j);
         const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
         const int nit = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
-        if (threadIdx.x == 0) {
-            const unsigned *gd = pl.grp_done + pl.gbase[l] + j;
-            unsigned i = 0;
-            for (;;) {
-                unsigned v;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(gd) : "memory");
-                if (v >= static_cast<unsigned>(nit)) break;
-                if (++i > pl.spin_limit || (*((volatile unsigned *)pl.status) & kErrTimeout)) {
-                    atomicOr(pl.status, kErrTimeout);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
+        // in the contraction form the episode's items instead (ctr_item)
+        const bool cform = ctr_level(pl, l);
+        const int cit0 = cform ? __ldcg(pl.c_items + e) : 0;
+        const int citems = cform ? __ldcg(pl.c_items + e + 1) - cit0 : 0;
+        const int crb = cform ? __ldcg(pl.c_rbase + e) : 0;
+        if (threadIdx.x == 0)
+            wait_count(pl, pl.grp_done + pl.gbase[l] + (cform ? e : j), static_cast<unsigned>(cform ? citems : nit));
         __syncthreads();
         for (int i = threadIdx.x; i < nc * kTot; i += blockDim.x) {
             const int rr = i / kTot, v = i - rr * kTot;
             float sum = 0.0f;
-            if (rec < 0) {
+            if (cform) {
+                sum = ctr_total(pl, crb, citems, cnt, c0 + rr, v);
+            } else if (rec < 0) {
                 sum = __ldcg(pl.ntot + static_cast<long long>(ep.inode_base[l] + c0 + rr) * kTot + v);
             } else {
                 const int rk = c0 - cg0 + rr;  // the child's rank in the group
@@ -2235,6 +2387,340 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
     }
 }
 
+// ---------------------------------------------------------------- contraction form (deepest fused level)
+// At the fused mode's deepest level l every total of a child c is linear in
+// its belief b_c = Phi(p, a_c, z_c) (Eq. 3): for each action a the
+// null-label mass sum_y nf(y) bbar_a(y), the reward sum sum_y r(y) bbar_a(y)
+// and the Q-weighted null masses sum_y nf(y) Q(a', y) bbar_a(y), with
+// bbar_a = T_a b_c (Eq. 3 numerator, Eq. 10).  Moving T_a onto the weights
+// gives sum_x b_c(x) W_j(x), W_j(x) = sum_y T(x, a, y) u_j(y), 35 planes
+// that depend on the map and Q only.  A work item (episode, band of window
+// rows) therefore multiplies the children's beliefs [children x cells] with
+// the planes [cells x 36] for every child of the episode at once: per row
+// segment of kCSC cells the parents' rows, Q, the cell words and the cost
+// are staged, the planes and the children's beliefs formed in shared
+// memory, and each thread accumulates a tile of 4 children x 12 planes over
+// its share of the segment's cells (FP32 FMAs).  The tiles' partial sums
+// are added in a fixed order and written as one record per (item, child);
+// a child's finalize adds its records in item order.  The episode's first
+// item also writes the children's records (parent, action, observation,
+// weight, P(z), path code).  Items count themselves done on the episode's
+// counter (grp_done at gbase[l] + e), which the finalize items wait on.
+
+// 16-byte asynchronous copy global -> shared through L2 (zero-filled when
+// !valid; src must still be a valid address).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ void ctr_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w) {
+    const int E = pl.E, K = pl.K, tid = threadIdx.x;
+    const int wid = tid >> 5, lane = tid & 31;
+    const int e = block_find(pl.c_items, E, w, S.flags + 6);
+    if (!QV_IN_BOUNDS(kSiteEpisode, e, E)) return;  // uniform over the CTA
+    const int i0 = __ldcg(pl.c_items + e);
+    const int it = w - i0, items = __ldcg(pl.c_items + e + 1) - i0;
+    load_ep(pl, e, S, cur_e);
+    const EpDev &ep = *S.ep;
+    const EpReg er = ep_reg(ep);
+    const int n = __ldcg(pl.count + l * E + e);
+    const int rb = __ldcg(pl.c_rbase + e);
+    const int B = er.B, P = er.P, H = er.H, goal = er.goal;
+    const long long N = er.N;
+    const float slip = er.slip, fwd = 1.0f - 2.0f * slip;
+    const Win win = support_window(pl, e, er.H, er.W, l);  // where the level's beliefs can be nonzero
+    const int nr = max(0, win.r1 - win.r0), wc = max(0, win.c1 - win.c0);
+    const int y0 = win.r0 + static_cast<int>((static_cast<long long>(it) * nr) / items);
+    const int y1 = win.r0 + static_cast<int>((static_cast<long long>(it + 1) * nr) / items);
+    const int nseg = (wc + kCSC - 1) / kCSC;
+    const int segw = nseg > 0 ? (wc + nseg - 1) / nseg : 0;
+    const CtrLayout CL = ctr_layout();
+    float *spar = S.sb + CL.par, *sq = S.sb + CL.q, *scost = S.sb + CL.cost, *sbp = S.sb + CL.bp, *sW = S.sb + CL.W;
+    uint16_t *scw = reinterpret_cast<uint16_t *>(S.sb + CL.cw);
+    int *cpi = reinterpret_cast<int *>(S.sb + CL.cpi), *ca = reinterpret_cast<int *>(S.sb + CL.ca);
+    int *cz = reinterpret_cast<int *>(S.sb + CL.cz);
+    float *csa = S.sb + CL.csa, *cse = S.sb + CL.cse;
+    const float *cost = er.cost;
+    // the parents: level l - 1's stored beliefs, or the root's b0 (l = 1)
+    const bool proot = l == 1;
+    const float *pbase = proot ? ep.b0 : pl.beliefs + ep.belief_off[l - 1];
+    if (it == 0)
+        for (int r = tid; r < n; r += blockDim.x) {
+            const int gid = ep.node_base[l] + r;
+            if (!QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) continue;
+            const long long sl = __ldcg(pl.src_slot + gid);
+            if (!QV_IN_BOUNDS(kSiteSlot, sl, 5LL * K * pl.n_inodes)) continue;
+            const int lp = static_cast<int>(sl / (5LL * K)) - ep.inode_base[l - 1];
+            const int a = static_cast<int>((sl / K) % 5);
+            const int z = __ldcg(pl.slot_z + sl);
+            const unsigned long long pcode = __ldcg(pl.code + ep.node_base[l - 1] + lp);
+            pl.parent[gid] = lp;
+            pl.action[gid] = a;
+            pl.obs[gid] = z;
+            pl.weight[gid] = __ldcg(pl.slot_w + sl);
+            pl.pz[gid] = __ldcg(pl.slot_P + sl);
+            pl.code[gid] = (pcode * 5ull + a) * static_cast<unsigned long long>(B + 1) + z;
+        }
+    const int nblk = (n + kCMB - 1) / kCMB;
+    for (int bk = 0; bk < nblk; ++bk) {
+        const int cb0 = static_cast<int>((static_cast<long long>(bk) * n) / nblk);
+        const int nb = static_cast<int>((static_cast<long long>(bk + 1) * n) / nblk) - cb0;
+        __syncthreads();  // the previous block's readers of the child table and the sum buffer are done
+        for (int r = tid; r < kCMB; r += blockDim.x) {
+            int lp = -1, a = 0, z = -1;
+            float sa = 0.0f, se = 0.0f;
+            if (r < nb) {
+                const int gid = ep.node_base[l] + cb0 + r;
+                if (QV_IN_BOUNDS(kSiteNode, gid, pl.n_nodes)) {
+                    const long long sl = __ldcg(pl.src_slot + gid);
+                    if (QV_IN_BOUNDS(kSiteSlot, sl, 5LL * K * pl.n_inodes)) {
+                        lp = static_cast<int>(sl / (5LL * K)) - ep.inode_base[l - 1];
+                        a = static_cast<int>((sl / K) % 5);
+                        z = __ldcg(pl.slot_z + sl);
+                        const float pz = __ldcg(pl.slot_P + sl);
+                        sa = ep.acc / pz;
+                        se = ep.eta / pz;
+                    }
+                }
+            }
+            cpi[r] = lp;
+            ca[r] = a;
+            cz[r] = z;
+            csa[r] = sa;
+            cse[r] = se;
+        }
+        __syncthreads();
+        // the block's parents [lp0, lp0 + npar) (children are numbered parent by parent)
+        if (tid < 32) {
+            int mn = 0x7fffffff, mx = -1;
+            for (int r = tid; r < nb; r += 32) {
+                const int v = cpi[r];
+                if (v >= 0) {
+                    mn = min(mn, v);
+                    mx = max(mx, v);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (tid == 0) {
+                S.scan[0] = mn;
+                S.scan[1] = mx >= mn ? mx - mn + 1 : 0;
+            }
+        }
+        __syncthreads();
+        const int lp0 = S.scan[0], npar = S.scan[1];
+        const bool fit = npar <= kCPar;  // always: a V-node has at least five children
+        if (!fit && tid == 0) atomicOr(pl.status, kErrCapacity);
+        // the GEMM tile of this thread: children c4 .. c4 + 3, planes j0 .. j0 + 11,
+        // cells kg, kg + KG, ... of each segment
+        const int cq = (nb + 3) >> 2, T = cq * 3;
+        const int KG = T > 0 ? static_cast<int>(blockDim.x) / T : 1;
+        const int tile = T > 0 ? tid % T : 0, kg = T > 0 ? tid / T : 0;
+        const bool gt = T > 0 && kg < KG;
+        const int c4 = (tile / 3) * 4, j0 = (tile - (tile / 3) * 3) * 12;
+        int po[4], zz[4];
+        float sa4[4], se4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = c4 + i;
+            const bool ok = gt && c < nb && cpi[c] >= 0 && fit;
+            po[i] = ok ? ((cpi[c] - lp0) * 5 + ca[c]) * kCBP : 0;
+            zz[i] = ok ? cz[c] : -1;
+            sa4[i] = ok ? csa[c] : 0.0f;
+            se4[i] = ok ? cse[c] : 0.0f;
+        }
+        float acc[4][12];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 12; ++j) acc[i][j] = 0.0f;
+        // one step: window row y, columns [x0, x0 + xw); its rows y - 1 .. y + 1
+        // are staged from column xa = x0 - 1 rounded down to 8, into stage bf
+        auto issue = [&](int y, int x0, int xw, int bf) {
+            const int xa = (x0 - 1) & ~7;
+            const int width = ((x0 + xw + 1 - xa) + 7) & ~7;
+            const int n4 = width >> 2, n8 = width >> 3;
+            float *pb = spar + bf * (kCPar * 3 * kCSW);
+            float *qb = sq + bf * (15 * kCSW);
+            float *cb = scost + bf * (3 * kCSW);
+            uint16_t *wb = scw + bf * (3 * kCSW);
+            const int np4 = npar * 3 * n4, nq4 = 15 * n4, nc4 = cost ? 3 * n4 : 0;
+            const int tot = np4 + nq4 + nc4 + 3 * n8;
+            for (int t = tid; t < tot; t += blockDim.x) {
+                int u = t;
+                if (u < np4) {
+                    const int rr = u / n4, ch = u - rr * n4, pi = rr / 3, r = rr - pi * 3;
+                    const int row = y - 1 + r, col = xa + 4 * ch;
+                    const long long o = static_cast<long long>(lp0 + pi) * N + static_cast<long long>(row) * P + col;
+                    bool valid = row >= 0 && row < H && col >= 0 && col < P;
+                    if (valid && !proot && !QV_IN_BOUNDS(kSiteBelief, ep.belief_off[l - 1] + o + 3, pl.n_belief))
+                        valid = false;
+                    cp_async16(pb + rr * kCSW + 4 * ch, valid ? pbase + o : pbase, valid);
+                    continue;
+                }
+                u -= np4;
+                if (u < nq4) {
+                    const int rr = u / n4, ch = u - rr * n4, ap = rr / 3, r = rr - ap * 3;
+                    const int row = y - 1 + r, col = xa + 4 * ch;
+                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
+                    cp_async16(qb + rr * kCSW + 4 * ch,
+                               valid ? er.Q + ap * N + static_cast<long long>(row) * P + col : er.Q, valid);
+                    continue;
+                }
+                u -= nq4;
+                if (u < nc4) {
+                    const int r = u / n4, ch = u - r * n4;
+                    const int row = y - 1 + r, col = xa + 4 * ch;
+                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
+                    cp_async16(cb + r * kCSW + 4 * ch, valid ? cost + static_cast<long long>(row) * P + col : cost,
+                               valid);
+                    continue;
+                }
+                u -= nc4;
+                {
+                    const int r = u / n8, ch = u - r * n8;
+                    const int row = y - 1 + r, col = xa + 8 * ch;
+                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
+                    cp_async16(wb + r * kCSW + 8 * ch,
+                               valid ? er.cell + static_cast<long long>(row) * P + col : er.cell, valid);
+                }
+            }
+            cp_async_commit();
+        };
+        const int nsteps = fit ? (y1 - y0) * nseg : 0;
+        if (nsteps > 0) issue(y0, win.c0, min(segw, win.c1 - win.c0), 0);
+        int y = y0, sg = 0;
+        for (int st = 0; st < nsteps; ++st) {
+            const int bf = st & 1;
+            const int x0 = win.c0 + sg * segw, xw = min(segw, win.c1 - x0), off = x0 - ((x0 - 1) & ~7);
+            cp_async_wait_all();
+            __syncthreads();  // stage bf landed for every thread; the previous step's readers are done
+            int ny = y, nsg = sg + 1;
+            if (nsg == nseg) {
+                nsg = 0;
+                ++ny;
+            }
+            if (st + 1 < nsteps) {
+                const int nx0 = win.c0 + nsg * segw;
+                issue(ny, nx0, min(segw, win.c1 - nx0), bf ^ 1);
+            }
+            const float *pb = spar + bf * (kCPar * 3 * kCSW);
+            const float *qb = sq + bf * (15 * kCSW);
+            const float *cb = scost + bf * (3 * kCSW);
+            const uint16_t *wb = scw + bf * (3 * kCSW);
+            // the parents' predicted beliefs for the five actions (Eq. 3
+            // numerator, Eq. 10), one warp per parent
+            for (int pi = wid; pi < npar; pi += kWarps)
+                for (int xi = lane; xi < xw; xi += 32) {
+                    const int c = off + xi;
+                    const unsigned cwx = wb[kCSW + c];
+                    const float *pp = pb + (pi * 3 + 1) * kCSW + c;
+                    const unsigned in = QV_CELL_INFLOW(cwx);
+                    float nbv[4], out[5];
+                    nbv[kDirN] = (in & 1u) ? pp[-kCSW] : 0.0f;
+                    nbv[kDirE] = (in & 2u) ? pp[1] : 0.0f;
+                    nbv[kDirS] = (in & 4u) ? pp[kCSW] : 0.0f;
+                    nbv[kDirW] = (in & 8u) ? pp[-1] : 0.0f;
+                    predict_cell(nbv, pp[0], cwx, y * P + x0 + xi == goal, slip, S.lut, out);
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) sbp[(pi * 5 + a) * kCBP + xi] = out[a];
+                }
+            // the planes of the segment's cells: W(x, a) = sum_y T(x, a, y) u(y)
+            for (int t = tid; t < 5 * kCSC; t += blockDim.x) {
+                const int a = t >> 6, xi = t & (kCSC - 1);
+                if (xi >= xw) continue;
+                const int c = off + xi;
+                const unsigned cwx = wb[kCSW + c];
+                float wn = 0.0f, wr = 0.0f, wq[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+                // weight g of the move from x to the staged cell (r, cc)
+                auto add = [&](int r, int cc, float g) {
+                    const unsigned cu = wb[r * kCSW + cc];
+                    const bool fr = QV_CELL_FREE(cu) != 0u;
+                    const bool gl = (y - 1 + r) * P + (x0 - off + cc) == goal;
+                    wr = fmaf(g, stage_reward(fr, gl, cost ? cb[r * kCSW + cc] : 0.0f), wr);
+                    const float gn = (fr && static_cast<int>(QV_CELL_LABEL(cu)) >= B) ? g : 0.0f;
+                    wn += gn;
+#pragma unroll
+                    for (int ap = 0; ap < 5; ++ap) wq[ap] = fmaf(gn, qb[(ap * 3 + r) * kCSW + cc], wq[ap]);
+                };
+                if (QV_CELL_FREE(cwx)) {
+                    if (y * P + x0 + xi == goal || a == 4) {
+                        add(1, c, 1.0f);  // the goal keeps its mass; stay
+                    } else {
+                        // the intended move (1 - 2 slip) and the two
+                        // perpendicular slips; a blocked one stays on x
+                        const unsigned blk = QV_CELL_BLOCKED(cwx);
+                        add(1, c, S.lut[a * 16 + blk]);
+                        const int dirs[3] = {a, (a + 1) & 3, (a + 3) & 3};
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            const int d = dirs[m];
+                            if ((blk >> d) & 1u) continue;
+                            const int dr = d == kDirN ? -1 : (d == kDirS ? 1 : 0);
+                            const int dc = d == kDirE ? 1 : (d == kDirW ? -1 : 0);
+                            add(1 + dr, c + dc, m == 0 ? fwd : slip);
+                        }
+                    }
+                }
+                float *wp = sW + xi * kTot;
+                wp[a] = wn;
+                wp[5 + a] = wr;
+#pragma unroll
+                for (int ap = 0; ap < 5; ++ap) wp[10 + a * 5 + ap] = wq[ap];
+                if (a == 0) wp[35] = 0.0f;
+            }
+            __syncthreads();
+            // the children's beliefs Phi(p, a_c, z_c) = T_a b_p O(., z_c) / P(z_c)
+            // (Eq. 3) against the planes
+            if (gt)
+                for (int xi = kg; xi < xw; xi += KG) {
+                    const int lab = static_cast<int>(QV_CELL_LABEL(static_cast<unsigned>(wb[kCSW + off + xi])));
+                    float av[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) av[i] = sbp[po[i] + xi] * (lab == zz[i] ? sa4[i] : se4[i]);
+                    const float4 *wp = reinterpret_cast<const float4 *>(sW + xi * kTot + j0);
+                    const float4 w0 = wp[0], w1 = wp[1], w2 = wp[2];
+                    const float wv[12] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w, w2.x, w2.y, w2.z, w2.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 12; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
+                }
+            y = ny;
+            sg = nsg;
+        }
+        // the tiles' sums in K-group order into the child records (the sum
+        // buffer is the predicted beliefs' area)
+        cp_async_wait_all();
+        __syncthreads();  // every tile's last reads are done
+        for (int g = 0; g < KG; ++g) {
+            if (gt && kg == g)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 12; ++j) {
+                        const int x = (c4 + i) * kTot + j0 + j;
+                        sbp[x] = (g == 0 ? 0.0f : sbp[x]) + acc[i][j];
+                    }
+            __syncthreads();
+        }
+        for (int i = tid; i < nb * kTot; i += blockDim.x) {
+            const int r = i / kTot, v = i - r * kTot;
+            const long long x = static_cast<long long>(rb) + static_cast<long long>(it) * n + cb0 + r;
+            if (QV_IN_BOUNDS(kSiteRecord, x, pl.n_xrec)) pl.xrec[x * kTot + v] = sbp[i];
+        }
+    }
+    __syncthreads();  // every record of the item is written
+    if (tid == 0) arrive_acq_rel(pl.grp_done + pl.gbase[l] + e);
+}
+
 // One level as one phase: its expand items, then its finalize items, from
 // one counter.  A finalize item forms its label histograms at once and waits
 // only for its own group's expand records (grp_done), so CTAs that finish
@@ -2247,12 +2733,16 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
 template <bool FUSED, bool NUMBER>
 __device__ bool phase_level(const PlanDev &pl, int l, bool store, Smem &S, uint64_t *mbar, unsigned &mphase,
                             int &cur_e) {
-    const int n_exp = __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
+    // the deepest fused level in its contraction form: ctr_item in place of
+    // the group expand items
+    const bool cform = !NUMBER && FUSED && ctr_level(pl, l);
+    const int n_exp = cform ? __ldcg(pl.c_items + pl.E) : __ldcg(pl.grp_off + pl.gbase[l] + l + __ldcg(pl.ngrp + l));
     const int total = n_exp + __ldcg(pl.wb_fin + l * (pl.E + 1) + pl.E);
     unsigned *ctr = pl.work + 2 * l;
     for (int w = next_item(ctr, S.flags + 8); w < total; w = next_item(ctr, S.flags + 8)) {
         if (w < n_exp) {
-            if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, true)) return false;
+            if (cform) ctr_item(pl, l, S, cur_e, w);
+            else if (!expand_item<FUSED>(pl, l, store, S, mbar, mphase, cur_e, w, true)) return false;
         } else if (!NUMBER && __ldcg(pl.fchunks + l) == 0) {
             finalize_group_item<FUSED>(pl, l, S, cur_e, w - n_exp);
         } else {
