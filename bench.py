@@ -978,17 +978,28 @@ def window_bytes(nodes, cells, depth, leaf_mode):
 # of the cell, five multiply-adds, five masks and five adds) and, at the
 # fused level, the 25 Q-weighted null sums.
 FLOPS_CHILD, FLOPS_STENCIL, FLOPS_SUMS, FLOPS_QSUMS = 7, 20, 21, 50
+# The deepest fused level of a plan of depth >= 2 runs in the contraction
+# form: per (child, cell of its level's own window) the child's belief (one
+# multiply) and 35 multiply-adds against the planes; per (parent, cell) the
+# five actions' predicted masses (FLOPS_STENCIL); per cell the planes once
+# (five actions, up to four moves each: the reward multiply-add, the null
+# mask, its add and five Q multiply-adds).
+FLOPS_CTR_CHILD, FLOPS_CTR_PLANES = 71, 280
 FP32_LANES_PER_SM = 128
 NOMINAL_SM_MHZ = 2070.0
 
 
 def expand_flops(nodes, cells, depth, leaf_mode):
     """FP32 operations of one plan's expand phases: level l's nodes over the
-    window of level l + 1 (cells[l + 1]).  The finalize phase's label
-    histograms (the beacons' sensing diamonds inside the window) are not
-    counted."""
+    window of level l + 1 (cells[l + 1]); the deepest fused level (depth >=
+    2) in its contraction form over its own window (cells[l]).  The finalize
+    phase's label histograms (the beacons' sensing diamonds inside the
+    window) are not counted."""
     tot = 0
     for lv in range(depth):
+        if lv == depth - 1 and leaf_mode == "fused" and depth >= 2:
+            tot += cells[lv] * (nodes[lv] * FLOPS_CTR_CHILD + nodes[lv - 1] * FLOPS_STENCIL + FLOPS_CTR_PLANES)
+            continue
         f = FLOPS_STENCIL + FLOPS_SUMS + (FLOPS_CHILD if lv > 0 else 0)
         if lv == depth - 1 and leaf_mode == "fused":
             f += FLOPS_QSUMS
@@ -1194,8 +1205,10 @@ def plan_roofline(api, model, Q, b0, w, leaf_mode_name, leaf_mode, knobs, slice_
            "traffic": None, "kernel": "k_plan (whole plan, one launch)", "kernel_share": 1.0,
            "flops_per_launch": flops,
            "flops_rule": "FP32 operations of the expand passes, level l's nodes over the window of level l+1: "
-                         f"{FLOPS_STENCIL + FLOPS_SUMS} per cell, +{FLOPS_CHILD} below the root, "
-                         f"+{FLOPS_QSUMS} at the fused level (label histograms not counted)",
+                         f"{FLOPS_STENCIL + FLOPS_SUMS} per cell, +{FLOPS_CHILD} below the root; the deepest fused "
+                         f"level (contraction form) over its own window: {FLOPS_CTR_CHILD} per (child, cell), "
+                         f"{FLOPS_STENCIL} per (parent, cell), {FLOPS_CTR_PLANES} per cell for the planes "
+                         "(label histograms not counted)",
            "peak_source": "SMs x 128 FP32 lanes x 2 x the sampled maximum SM clock",
            "nodes_per_level": nodes, "window_cells_per_level": cells,
            "avg_launch_ms": avg, "launch": f"one plan alone on the whole grid ({full.grid} CTAs), L2 flushed",

@@ -126,11 +126,12 @@ __global__ void k_bounds_collect(unsigned *status) {
 // at most kCPar parents: every V-node has at least five children), 36
 // planes per cell (the kTot totals).  Its arrays live in the band buffers.
 constexpr int kCSC = 64;
-constexpr int kCMB = 64;
+constexpr int kCMB = 96;
 constexpr int kCPar = kCMB / 5 + 3;
 // staged columns: the segment with a one-cell rim, rounded out to 8-column
 // chunks so that every copy is 16 bytes on a 16-byte boundary
 constexpr int kCSW = kCSC + 16;
+static_assert(kCSC == 64, "the contraction's task loops index cells with 6-bit shifts");
 constexpr int kCBP = kCSC + 1;  // row stride of the predicted beliefs (rows of different children fall in different banks)
 struct CtrLayout {
     int par, q, cost, cw, bp, W, cpi, ca, cz, csa, cse, total;  // float offsets from the band buffers
@@ -2543,53 +2544,54 @@ __device__ void ctr_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w) {
             for (int j = 0; j < 12; ++j) acc[i][j] = 0.0f;
         // one step: window row y, columns [x0, x0 + xw); its rows y - 1 .. y + 1
         // are staged from column xa = x0 - 1 rounded down to 8, into stage bf
+        // one warp per staged row (the parents', Q's, the cost's, the cell
+        // words'), one 16-byte copy per lane and chunk
+        const int nprow = npar * 3, ncrow = cost ? 3 : 0;
+        const int nrows = nprow + 15 + ncrow + 3;
         auto issue = [&](int y, int x0, int xw, int bf) {
             const int xa = (x0 - 1) & ~7;
             const int width = ((x0 + xw + 1 - xa) + 7) & ~7;
             const int n4 = width >> 2, n8 = width >> 3;
-            float *pb = spar + bf * (kCPar * 3 * kCSW);
-            float *qb = sq + bf * (15 * kCSW);
-            float *cb = scost + bf * (3 * kCSW);
-            uint16_t *wb = scw + bf * (3 * kCSW);
-            const int np4 = npar * 3 * n4, nq4 = 15 * n4, nc4 = cost ? 3 * n4 : 0;
-            const int tot = np4 + nq4 + nc4 + 3 * n8;
-            for (int t = tid; t < tot; t += blockDim.x) {
-                int u = t;
-                if (u < np4) {
-                    const int rr = u / n4, ch = u - rr * n4, pi = rr / 3, r = rr - pi * 3;
-                    const int row = y - 1 + r, col = xa + 4 * ch;
-                    const long long o = static_cast<long long>(lp0 + pi) * N + static_cast<long long>(row) * P + col;
-                    bool valid = row >= 0 && row < H && col >= 0 && col < P;
-                    if (valid && !proot && !QV_IN_BOUNDS(kSiteBelief, ep.belief_off[l - 1] + o + 3, pl.n_belief))
-                        valid = false;
-                    cp_async16(pb + rr * kCSW + 4 * ch, valid ? pbase + o : pbase, valid);
-                    continue;
+            for (int rr = wid; rr < nrows; rr += kWarps) {
+                int k = rr, r;
+                const float *src;
+                void *dst;
+                bool fl = true;  // a float row (4-value chunks), else cell words (8 per chunk)
+                if (k < nprow) {
+                    const int pi = k / 3;
+                    r = k - pi * 3;
+                    src = pbase + static_cast<long long>(lp0 + pi) * N;
+                    dst = spar + bf * (kCPar * 3 * kCSW) + k * kCSW;
+                } else if ((k -= nprow) < 15) {
+                    const int ap = k / 3;
+                    r = k - ap * 3;
+                    src = er.Q + ap * N;
+                    dst = sq + bf * (15 * kCSW) + k * kCSW;
+                } else if ((k -= 15) < ncrow) {
+                    r = k;
+                    src = cost;
+                    dst = scost + bf * (3 * kCSW) + k * kCSW;
+                } else {
+                    r = k - ncrow;
+                    src = nullptr;
+                    dst = scw + bf * (3 * kCSW) + r * kCSW;
+                    fl = false;
                 }
-                u -= np4;
-                if (u < nq4) {
-                    const int rr = u / n4, ch = u - rr * n4, ap = rr / 3, r = rr - ap * 3;
-                    const int row = y - 1 + r, col = xa + 4 * ch;
-                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
-                    cp_async16(qb + rr * kCSW + 4 * ch,
-                               valid ? er.Q + ap * N + static_cast<long long>(row) * P + col : er.Q, valid);
-                    continue;
-                }
-                u -= nq4;
-                if (u < nc4) {
-                    const int r = u / n4, ch = u - r * n4;
-                    const int row = y - 1 + r, col = xa + 4 * ch;
-                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
-                    cp_async16(cb + r * kCSW + 4 * ch, valid ? cost + static_cast<long long>(row) * P + col : cost,
-                               valid);
-                    continue;
-                }
-                u -= nc4;
-                {
-                    const int r = u / n8, ch = u - r * n8;
-                    const int row = y - 1 + r, col = xa + 8 * ch;
-                    const bool valid = row >= 0 && row < H && col >= 0 && col < P;
-                    cp_async16(wb + r * kCSW + 8 * ch,
-                               valid ? er.cell + static_cast<long long>(row) * P + col : er.cell, valid);
+                const int row = y - 1 + r;
+                const bool rin = row >= 0 && row < H;
+                const int nch = fl ? n4 : n8;
+                for (int ch = lane; ch < nch; ch += 32) {
+                    const int col = xa + (fl ? 4 : 8) * ch;
+                    bool valid = rin && col >= 0 && col < P;
+                    const long long o = static_cast<long long>(row) * P + col;
+                    if (fl) {
+                        if (valid && rr < nprow && !proot &&
+                            !QV_IN_BOUNDS(kSiteBelief, ep.belief_off[l - 1] + (src - pbase) + o + 3, pl.n_belief))
+                            valid = false;
+                        cp_async16(static_cast<float *>(dst) + 4 * ch, valid ? src + o : src, valid);
+                    } else {
+                        cp_async16(static_cast<uint16_t *>(dst) + 8 * ch, valid ? er.cell + o : er.cell, valid);
+                    }
                 }
             }
             cp_async_commit();
@@ -2615,10 +2617,15 @@ __device__ void ctr_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w) {
             const float *qb = sq + bf * (15 * kCSW);
             const float *cb = scost + bf * (3 * kCSW);
             const uint16_t *wb = scw + bf * (3 * kCSW);
-            // the parents' predicted beliefs for the five actions (Eq. 3
-            // numerator, Eq. 10), one warp per parent
-            for (int pi = wid; pi < npar; pi += kWarps)
-                for (int xi = lane; xi < xw; xi += 32) {
+            // one loop over the parents' predicted beliefs for the five actions
+            // (Eq. 3 numerator, Eq. 10; task (parent, cell)) and the planes of
+            // the segment's cells (W(x, a) = sum_y T(x, a, y) u(y); task
+            // (action, cell)), dealt evenly to the threads
+            const int nbp_t = npar * kCSC;
+            for (int t = tid; t < nbp_t + 5 * kCSC; t += blockDim.x) {
+                if (t < nbp_t) {
+                    const int pi = t >> 6, xi = t & (kCSC - 1);
+                    if (xi >= xw) continue;
                     const int c = off + xi;
                     const unsigned cwx = wb[kCSW + c];
                     const float *pp = pb + (pi * 3 + 1) * kCSW + c;
@@ -2631,10 +2638,10 @@ __device__ void ctr_item(const PlanDev &pl, int l, Smem &S, int &cur_e, int w) {
                     predict_cell(nbv, pp[0], cwx, y * P + x0 + xi == goal, slip, S.lut, out);
 #pragma unroll
                     for (int a = 0; a < 5; ++a) sbp[(pi * 5 + a) * kCBP + xi] = out[a];
+                    continue;
                 }
-            // the planes of the segment's cells: W(x, a) = sum_y T(x, a, y) u(y)
-            for (int t = tid; t < 5 * kCSC; t += blockDim.x) {
-                const int a = t >> 6, xi = t & (kCSC - 1);
+                // (action fastest: a warp's plane stores fall in different banks)
+                const int xi = (t - nbp_t) / 5, a = (t - nbp_t) - xi * 5;
                 if (xi >= xw) continue;
                 const int c = off + xi;
                 const unsigned cwx = wb[kCSW + c];

@@ -48,10 +48,14 @@ def test_window_bytes_reduce_to_the_dense_count_on_full_windows():
 
 def test_expand_flops_per_level():
     # depth 2, fused: the root (no child formation) over the level-1 window,
-    # then level 1 (child formation and the Q-weighted sums) over level 2's
+    # then level 1 in the contraction form over its own window: per child
+    # and cell, per parent (the root) and cell, and the planes per cell
     base = bench.FLOPS_STENCIL + bench.FLOPS_SUMS
     got = bench.expand_flops([1, 6, 40], [100, 110, 121, 130], 2, "fused")
-    assert got == 1 * 110 * base + 6 * 121 * (base + bench.FLOPS_CHILD + bench.FLOPS_QSUMS)
+    assert got == 1 * 110 * base + 110 * (6 * bench.FLOPS_CTR_CHILD + 1 * bench.FLOPS_STENCIL + bench.FLOPS_CTR_PLANES)
+    # depth 1, fused: the root's own pass with the Q-weighted sums (no contraction form)
+    got = bench.expand_flops([1, 6], [100, 110, 121], 1, "fused")
+    assert got == 1 * 110 * (base + bench.FLOPS_QSUMS)
     got = bench.expand_flops([1, 6, 40], [100, 110, 121, 130], 2, "materialise")
     assert got == 1 * 110 * base + 6 * 121 * (base + bench.FLOPS_CHILD)
     # 152 SMs at 2070 MHz: 152 * 128 * 2 * 2.07e9 = 80.55 TFLOP/s
