@@ -243,6 +243,7 @@ struct Smem {
     float *c_sa, *c_se;
     float *wpart;
     int *wchild;
+    int nband;  // 4-byte words of the band buffers (from sb), free for scratch outside expand and update items
 };
 
 // Slots per warp for the per-child sums of one band: a warp's contiguous
@@ -878,11 +879,24 @@ __host__ __device__ __forceinline__ int finalize_chunks(long long n, int target,
 }
 
 // Work items of one expand group: in proportion to its children, at least
-// one, at most one per band.
+// one; an item takes a range of the window's bands and a part of the
+// group's children (at least two), so at most bands x children / 2.
 __host__ __device__ __forceinline__ int group_items(int children, long long all_children, int target, int bands) {
     if (children <= 0) return 0;
     const long long want = (static_cast<long long>(target) * children + all_children - 1) / all_children;
-    return static_cast<int>(want < 1 ? 1 : (want > bands ? bands : want));
+    const long long cap = static_cast<long long>(bands) * (children / 2 > 1 ? children / 2 : 1);
+    return static_cast<int>(want < 1 ? 1 : (want > cap ? cap : want));
+}
+// The requested items of a group over nb bands: bi band ranges times
+// `parts` parts of the children (an empty window: one item).
+__host__ __device__ __forceinline__ void group_split(int requested, int nb, int &bi, int &parts) {
+    if (nb <= 0 || requested <= 1) {
+        bi = 1;
+        parts = 1;
+        return;
+    }
+    bi = requested < nb ? requested : nb;
+    parts = requested / bi;
 }
 
 // The work lists of level l1 once every node of level l1 - 1 is final and
@@ -960,24 +974,69 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
     const int G = __ldcg(np + E);
     int *goff = pl.grp_off + pl.gbase[l1] + l1;
     int *grec = pl.grp_rec + pl.gbase[l1];
+    // the per-episode inputs of the lists, read once into the band buffers
+    // (free in a finalize item once its node is final) when they fit: the
+    // level sizes' prefix, internal-node bases, child counts, band counts
+    // and the support window's rows and cells, so that no group search or
+    // window needs a chain of global loads
+    int *s_np = reinterpret_cast<int *>(S.sb), *s_ib = s_np + (E + 1), *s_cnt = s_ib + E, *s_nb = s_cnt + E;
+    int *s_rows = s_nb + E, *s_cells = s_rows + E;
+    const bool cache = 6 * (E + 1) <= S.nband;
+    if (cache) {
+        for (int e = threadIdx.x; e <= E; e += blockDim.x) {
+            s_np[e] = __ldcg(np + e);
+            if (e < E) {
+                const EpDev *ep = pl.eps + e;
+                const int H = __ldg(&ep->H), W = __ldg(&ep->W);
+                s_ib[e] = __ldg(&ep->inode_base[l1 - 1]);
+                s_cnt[e] = __ldcg(pl.count + l1 * E + e);
+                s_nb[e] = band_geo(pl, e, H, W, __ldg(&ep->P), __ldg(&ep->band_rows), l1).nb;
+                const Win v = support_window(pl, e, H, W, l1);
+                s_rows[e] = max(0, v.r1 - v.r0);
+                s_cells[e] = max(0, v.r1 - v.r0) * max(0, v.c1 - v.c0);
+            }
+        }
+        __syncthreads();
+    }
     auto children = [&](int j) {
-        const int e = find_episode(np, E, j);
-        const int lp = j - __ldcg(np + e);
-        const long long ia = static_cast<long long>(__ldg(&pl.eps[e].inode_base[l1 - 1]) + lp) * 5;
-        const int cnt = __ldcg(pl.count + l1 * E + e);
+        int e, lp, ib, cnt, nb;
+        if (cache) {
+            int lo = 0, hi = E - 1;  // last e with s_np[e] <= j
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_np[mid] <= j) lo = mid;
+                else hi = mid - 1;
+            }
+            e = lo;
+            lp = j - s_np[e];
+            ib = s_ib[e];
+            cnt = s_cnt[e];
+            nb = s_nb[e];
+        } else {
+            e = find_episode(np, E, j);
+            lp = j - __ldcg(np + e);
+            const EpDev *ep = pl.eps + e;
+            ib = __ldg(&ep->inode_base[l1 - 1]);
+            cnt = __ldcg(pl.count + l1 * E + e);
+            nb = band_geo(pl, e, __ldg(&ep->H), __ldg(&ep->W), __ldg(&ep->P), __ldg(&ep->band_rows), l1).nb;
+        }
+        const long long ia = static_cast<long long>(ib + lp) * 5;
         const int c0 = min(__ldcg(pl.choff + ia), cnt);
         const int c1 = min(__ldcg(pl.choff + ia + 4) + __ldcg(pl.nchild + ia + 4), cnt);
-        const EpDev *ep = pl.eps + e;
-        const BandGeo geo = band_geo(pl, e, __ldg(&ep->H), __ldg(&ep->W), __ldg(&ep->P), __ldg(&ep->band_rows), l1);
-        return make_int2(max(0, c1 - c0), max(geo.nb, 1));  // an empty window still writes its zero totals
+        return make_int2(max(0, c1 - c0), max(nb, 1));  // an empty window still writes its zero totals
     };
+    // (the deepest fused level in its contraction form cuts its finalize
+    // pieces by these items: two per CTA, whatever the items per CTA)
+    const int gtarget = (pl.ctr && l1 == pl.depth - 1 && pl.leaf_mode == QV_LEAF_FUSED)
+                            ? max(pl.target, 2 * static_cast<int>(gridDim.x))
+                            : pl.target;
     int wi = 0, wr = 0;
     for (int base = 0; base < G; base += blockDim.x) {
         const int j = base + threadIdx.x;
         int vi = 0, vr = 0;
         if (j < G) {
             const int2 cb = children(j);
-            vi = group_items(cb.x, Tt, pl.target, cb.y);
+            vi = group_items(cb.x, Tt, gtarget, cb.y);
             vr = vi >= 2 ? vi : 0;
         }
         int ti, tr;
@@ -1009,6 +1068,12 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         if (threadIdx.x < 2) wsum[threadIdx.x] = 0ull;
         __syncthreads();
         auto geom = [&](int e, long long &n, long long &rows, long long &cells) {
+            if (cache) {
+                n = s_cnt[e];
+                rows = s_rows[e];
+                cells = s_cells[e];
+                return;
+            }
             const EpDev *ep = pl.eps + e;
             const Win v = support_window(pl, e, __ldg(&ep->H), __ldg(&ep->W), l1);
             n = __ldcg(pl.count + l1 * E + e);
@@ -1024,13 +1089,16 @@ __device__ void level_prefix(const PlanDev &pl, int l1, Smem &S) {
         atomicAdd(wsum, wl);  // integer sums: the same items whatever the order
         __syncthreads();
         const unsigned long long wt = max(wsum[0], 1ull);
-        // items of episode e, scaled by num / den when den > 0
+        // items of episode e, scaled by num / den when den > 0: two per CTA
+        // over the level (the items are alike, so two waves balance them),
+        // whatever the launch shape's items per CTA
+        const unsigned long long ctarget = 2ull * gridDim.x;
         auto items_of = [&](int e, unsigned long long num, unsigned long long den) -> long long {
             long long n, rows, cells;
             geom(e, n, rows, cells);
             if (n <= 0) return 0;
             const unsigned long long w = static_cast<unsigned long long>(n * max(cells, 1LL));
-            long long it = static_cast<long long>((static_cast<unsigned long long>(pl.target) * w + wt - 1) / wt);
+            long long it = static_cast<long long>((ctarget * w + wt - 1) / wt);
             it = min(max(it, 1LL), max(rows, 1LL));
             if (den > 0) it = max(1LL, static_cast<long long>(static_cast<unsigned long long>(it) * num / den));
             return it;
@@ -1293,14 +1361,17 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
         }
         const int g0 = __ldcg(goff + j);
         const int item = w - g0;
-        // a group has no more items than its window has bands (at least one,
-        // which writes the zero totals of an empty window); surplus items
-        // of the list do nothing
+        // a group's items are bi band ranges times `parts` parts of its
+        // children (at least one item, which writes the zero totals of an
+        // empty window); surplus items of the list do nothing
         const EpDev *epg = pl.eps + e;
         const BandGeo geo =
             band_geo(pl, e, __ldg(&epg->H), __ldg(&epg->W), __ldg(&epg->P), __ldg(&epg->band_rows), l);
-        const int items = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
+        int bi, parts;
+        group_split(__ldcg(goff + j + 1) - g0, geo.nb, bi, parts);
+        const int items = bi * parts;
         if (item >= items) return true;
+        const int bslot = item % bi, part = item / bi;
         load_ep(pl, e, S, cur_e);
         const EpDev &ep = *S.ep;
         const int rec = __ldcg(grec + j);
@@ -1317,8 +1388,11 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
             src = node_belief(pl, ep, l - 1, lp);
         }
         __syncthreads();  // the previous item's readers of the child table, totals and band buffers are done
-        const int band0 = static_cast<int>((static_cast<long long>(item) * geo.nb) / items);
-        const int band1 = static_cast<int>((static_cast<long long>(item + 1) * geo.nb) / items);
+        const int band0 = static_cast<int>((static_cast<long long>(bslot) * geo.nb) / bi);
+        const int band1 = static_cast<int>((static_cast<long long>(bslot + 1) * geo.nb) / bi);
+        // this item's part of the group's children
+        const int cp0 = static_cast<int>((static_cast<long long>(part) * nc) / parts);
+        const int ncp = static_cast<int>((static_cast<long long>(part + 1) * nc) / parts) - cp0;
         const EpReg er = ep_reg(ep);
         // the first band's copies fly while the child table is read
         if (band0 < band1) {
@@ -1389,8 +1463,8 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
                 __syncthreads();
             }
             if (band == band0) QV_TRACE_MARK(tr, 4);
-            // this warp's contiguous range of (child, strip, row) tasks
-            const int T = nc * NS * R;
+            // this warp's contiguous range of (child, strip, row) tasks over the item's children
+            const int T = ncp * NS * R;
             int t = static_cast<int>(static_cast<long long>(T) * wid / kWarps);
             const int tend = static_cast<int>(static_cast<long long>(T) * (wid + 1) / kWarps);
             int slot = 0, cur = -1;
@@ -1436,8 +1510,8 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
             const float fwd = 1.0f - 2.0f * slip;
             zero_acc();
             while (t < tend) {
-                const int r = t / (NS * R);
-                const int rem = t - r * NS * R;
+                const int r = cp0 + t / (NS * R);
+                const int rem = t - (r - cp0) * NS * R;
                 const int s = rem / R, ya = rem - s * R;
                 const int yb = min(R, ya + (tend - t));
                 if (r != cur) {
@@ -1617,11 +1691,11 @@ __device__ bool expand_item(const PlanDev &pl, int l, bool store, Smem &S, uint6
                 const int dr0 = w0 - 1, dr1 = __ldcg(dw + 1), dg0 = __ldcg(dw + 2), dg1 = __ldcg(dw + 3);
                 const bool inside = geo.nb > 0 && dr0 >= geo.r0 && dr1 <= geo.r1 && dg0 >= geo.g0 && dg1 <= geo.g1;
                 if (!inside) {
-                    const int zr0 = dr0 + static_cast<int>((static_cast<long long>(item) * (dr1 - dr0)) / items);
-                    const int zr1 = dr0 + static_cast<int>((static_cast<long long>(item + 1) * (dr1 - dr0)) / items);
+                    const int zr0 = dr0 + static_cast<int>((static_cast<long long>(bslot) * (dr1 - dr0)) / bi);
+                    const int zr1 = dr0 + static_cast<int>((static_cast<long long>(bslot + 1) * (dr1 - dr0)) / bi);
                     const int nr = zr1 - zr0;
-                    for (int t2 = wid; t2 < nc * nr; t2 += kWarps) {
-                        const int r = t2 / nr, row = zr0 + (t2 - r * nr);
+                    for (int t2 = wid; t2 < ncp * nr; t2 += kWarps) {
+                        const int r = cp0 + t2 / nr, row = zr0 + (t2 - (t2 / nr) * nr);
                         float4 *d4 = reinterpret_cast<float4 *>(dst0 + static_cast<long long>(c0 + r) * er.N +
                                                                 static_cast<long long>(row) * P);
                         const bool in = row >= geo.r0 && row < geo.r1;
@@ -1916,7 +1990,9 @@ __device__ void node_totals(const PlanDev &pl, int l, const EpDev &ep, int e, in
     const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + jg);
     constexpr int kGroups = kThreads / kTot;  // partial sums per value
     const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
-    const int nit = max(1, min(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb));
+    int gbi, gparts;
+    group_split(__ldcg(goff + jg + 1) - __ldcg(goff + jg), geo.nb, gbi, gparts);
+    const int nit = gbi * gparts;
     const bool cform = ctr_level(pl, l);
     const int cit0 = cform ? __ldcg(pl.c_items + e) : 0;
     const int citems = cform ? __ldcg(pl.c_items + e + 1) - cit0 : 0;
@@ -2258,7 +2334,9 @@ __device__ void finalize_group_item(const PlanDev &pl, int l, Smem &S, int &cur_
     {
         const int rec = __ldcg(pl.grp_rec + pl.gbase[l] + j);
         const BandGeo geo = band_geo(pl, e, ep.H, ep.W, ep.P, ep.band_rows, l);
-        const int nit = max(1, min(__ldcg(goff + j + 1) - g0, geo.nb));
+        int gbi, gparts;
+        group_split(__ldcg(goff + j + 1) - g0, geo.nb, gbi, gparts);
+        const int nit = gbi * gparts;
         // in the contraction form the episode's items instead (ctr_item)
         const bool cform = ctr_level(pl, l);
         const int cit0 = cform ? __ldcg(pl.c_items + e) : 0;
@@ -3130,6 +3208,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_plan(PlanDev pl) {
     S.u_se = reinterpret_cast<float *>(smem_raw + L.u_se);
     S.scan = reinterpret_cast<int *>(smem_raw + L.scan);
     S.flags = reinterpret_cast<int *>(smem_raw + L.flags);
+    S.nband = static_cast<int>((L.band_end - L.sb) / 4);
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);
         fence_barrier_init();
