@@ -401,6 +401,27 @@ def extra_measurements(args, dev, flush, stream, plans_per_s, arm, model, Qd, ep
             "workspace_GB": batched_arm.plan.workspace_bytes / 1e9,
             "note": "the headline's requests (same map, b0s, seeds and episode words): one batched launch against "
                     "one launch per plan on streams"}
+    # (1a) the same batched launch with the deepest level in its per-child
+    # stencil form instead of the contraction form (same requests and trees)
+    if batched_arm is not None and leaf_mode == N.QV_LEAF_FUSED and w.depth >= 2:
+        R = len(eps)
+        pf = api.Plan([model] * R, [Qd] * R, b0s, depth=w.depth, K=w.K, seed=w.seed, episode=eps[0].episode,
+                      leaf_mode=leaf_mode, band_cells=batched_arm.plan.tuning["band_cells"],
+                      items_per_cta=batched_arm.plan.tuning["items_per_cta"], deepest_form=N.QV_DEEPEST_STENCIL)
+        pf.capture_graph()
+        for _ in range(3):
+            pf.run()
+        ms_f = time_device(pf.run, K, flush, stream)
+        ms_c = batched_arm.time(K)
+        out["deepest_level_forms"] = {
+            "contraction_plans_per_s": R * K / (ms_c / 1e3), "stencil_plans_per_s": R * K / (ms_f / 1e3),
+            "contraction_vs_stencil": ms_f / ms_c,
+            "same_trees": [r["nodes_per_level"] for r in pf.read()] == [r["nodes_per_level"]
+                                                                         for r in batched_arm.plan.read()],
+            "note": "the headline's batched launch with the deepest level's sums as the contraction of every "
+                    "child's belief with the planes (default) or as each child's five-action stencil"}
+        del pf
+        torch.cuda.empty_cache()
     # (1b) the headline's workload with more requests per batched launch: the
     # deepest level's work grows with the batch, the upper levels' latency
     # chain is shared by more plans

@@ -135,7 +135,17 @@ typedef struct {
                                   far (depth_reached of the result; level 0 is always
                                   built).  Needs QV_LEAF_FUSED; every level then also
                                   sums its children's leaf values                     */
+    int32_t deepest_form;      /* how the deepest level of a fused plan (depth >= 2)
+                                  forms its children's sums: QV_DEEPEST_AUTO (0) the
+                                  contraction of every child's belief with planes of
+                                  the motion model applied to the weights, where its
+                                  records fit the workspace; QV_DEEPEST_STENCIL (1)
+                                  each child's five-action stencil.  Both compute the
+                                  same sums of Eq. 3 and Alg. 5 (in another FP32
+                                  order); other values return QV_ERR_INVALID          */
 } qv_plan_params_t;
+#define QV_DEEPEST_AUTO 0
+#define QV_DEEPEST_STENCIL 1
 
 typedef struct {
     int32_t action;            /* argmax_a U_Q(b0, a); ties to the lower index          */

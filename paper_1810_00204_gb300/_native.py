@@ -27,6 +27,7 @@ QV_NOALLOC_MAX_CELLS = 4096 * 1024
 QV_F32, QV_F64 = 0, 1
 QV_WEIGHT_FREQ, QV_WEIGHT_MARGINAL = 0, 1
 QV_LEAF_FUSED, QV_LEAF_MATERIALISE = 0, 1
+QV_DEEPEST_AUTO, QV_DEEPEST_STENCIL = 0, 1
 
 
 class qv_model_t(C.Structure):
@@ -40,7 +41,7 @@ class qv_plan_params_t(C.Structure):
     _fields_ = [("depth", C.c_int32), ("K", C.c_int32), ("seed", C.c_uint64), ("episode", C.c_uint32),
                 ("weight_mode", C.c_int32), ("leaf_mode", C.c_int32), ("d_replay", C.c_void_p),
                 ("band_cells", C.c_int32), ("items_per_cta", C.c_int32), ("grid_ctas", C.c_int32),
-                ("deadline_ms", C.c_double)]
+                ("deadline_ms", C.c_double), ("deepest_form", C.c_int32)]
 
 
 class qv_tune_t(C.Structure):

@@ -496,10 +496,10 @@ def leaf_value(model: Model, Q: torch.Tensor, b: torch.Tensor, stream=None):
 
 
 def _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells=0, items_per_cta=0, grid_ctas=0,
-            deadline_ms=0.0):
+            deadline_ms=0.0, deepest_form=0):
     return N.qv_plan_params_t(int(depth), int(K), int(seed), int(episode), int(weight_mode), int(leaf_mode),
                               None if replay is None else replay.data_ptr(), int(band_cells), int(items_per_cta),
-                              int(grid_ctas), float(deadline_ms))
+                              int(grid_ctas), float(deadline_ms), int(deepest_form))
 
 
 def _result_dict(r: N.qv_plan_result_t, depth: int):
@@ -519,7 +519,7 @@ class Plan:
     def __init__(self, models: Sequence[Model], Qs: Sequence[torch.Tensor], b0s: Sequence[torch.Tensor],
                  depth=2, K=4, seed=0, episode=0, weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED,
                  replay: Optional[torch.Tensor] = None, stream=None, band_cells=0, items_per_cta=0, grid_ctas=0,
-                 deadline_ms=0.0):
+                 deadline_ms=0.0, deepest_form=0):
         self.models = list(models)
         self.E = len(self.models)
         self.depth, self.K = int(depth), int(K)
@@ -527,7 +527,7 @@ class Plan:
         self.b0s = [b.contiguous() for b in b0s]
         self.replay = replay
         self.params = _params(depth, K, seed, episode, weight_mode, leaf_mode, replay, band_cells, items_per_cta,
-                              grid_ctas, deadline_ms)
+                              grid_ctas, deadline_ms, deepest_form)
         self.mstructs = (N.qv_model_t * self.E)(*[m.struct for m in self.models])
         self.qptrs = (C.c_void_p * self.E)(*[q.data_ptr() for q in self.Qs])
         self.bptrs = (C.c_void_p * self.E)(*[b.data_ptr() for b in self.b0s])
@@ -738,11 +738,12 @@ def qv_tree_backward(plan: Plan, e: int = 0, dL: float = 1.0, Qbar=None, dslip=N
 
 def qv_tree_plan(model: Model, Q: torch.Tensor, b0: torch.Tensor, depth=2, K=4, seed=0, episode=0,
                  weight_mode=N.QV_WEIGHT_FREQ, leaf_mode=N.QV_LEAF_FUSED, replay=None, keep=False, stream=None,
-                 deadline_ms=0.0):
+                 deadline_ms=0.0, deepest_form=0):
     """One plan from b0 to the chosen action (Alg. 1 inner loop, one step);
-    deadline_ms > 0 stops at the first level that is final after the budget."""
+    deadline_ms > 0 stops at the first level that is final after the budget;
+    deepest_form picks the deepest fused level's form (N.QV_DEEPEST_*)."""
     p = Plan([model], [Q], [b0], depth, K, seed, episode, weight_mode, leaf_mode, replay, stream,
-             deadline_ms=deadline_ms)
+             deadline_ms=deadline_ms, deepest_form=deepest_form)
     p.run(stream)
     r = p.read(stream)[0]
     return (r, p) if keep else r

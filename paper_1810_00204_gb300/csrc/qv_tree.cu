@@ -96,6 +96,8 @@ qv_status validate(int E, const qv_model_t *models, const qv_plan_params_t *p) {
         return qv_set_error(QV_ERR_INVALID, "plan: deadline_ms %g", p->deadline_ms);
     if (p->deadline_ms > 0.0 && p->leaf_mode != QV_LEAF_FUSED)
         return qv_set_error(QV_ERR_INVALID, "plan: a deadline needs QV_LEAF_FUSED");
+    if (p->deepest_form != QV_DEEPEST_AUTO && p->deepest_form != QV_DEEPEST_STENCIL)
+        return qv_set_error(QV_ERR_INVALID, "plan: deepest_form %d", p->deepest_form);
     if (p->band_cells < 0 || p->band_cells > (1 << 16))
         return qv_set_error(QV_ERR_INVALID, "plan: band_cells %d", p->band_cells);
     if (p->items_per_cta < 0 || p->items_per_cta > kMaxItemsPerCta)
@@ -202,7 +204,7 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     L.cmax = 5 * std::min(K, L.Bmax + 1);
     // the contraction form of the deepest fused level works in the band
     // buffers: grow the Q buffer until they hold its arrays
-    L.ctr = (p->leaf_mode == QV_LEAF_FUSED && D >= 2) ? 1 : 0;
+    L.ctr = (p->leaf_mode == QV_LEAF_FUSED && D >= 2 && p->deepest_form == QV_DEEPEST_AUTO) ? 1 : 0;
     if (L.ctr) {
         const qv::SmemLayout s0 =
             qv::SmemLayout::make(L.sb_floats, L.sp_floats, L.q_floats, L.Bmax, K, L.cmax, qv::expand_slots(L.cmax));

@@ -85,6 +85,13 @@ def test_invalid_arguments_are_rejected_without_gpu(libpath):
     p = N.qv_plan_params_t(2, 4, 0, 0, 0, N.QV_LEAF_MATERIALISE, None, 0, 0, 0, 5.0)
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
     assert b"deadline" in L.qv_last_error()
+    # the deepest fused level's form: auto (contraction) or the per-child stencil
+    for form in (N.QV_DEEPEST_AUTO, N.QV_DEEPEST_STENCIL):
+        p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 0, 0, 0.0, form)
+        assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) > 0
+    p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None, 0, 0, 0, 0.0, 2)
+    assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0
+    assert b"deepest_form" in L.qv_last_error()
     p = N.qv_plan_params_t(2, 4, 0, 0, 0, 0, None)
     m.num_beacons = N.QV_MAX_BEACONS + 1
     assert L.qv_plan_workspace_bytes(1, ctypes.byref(m), ctypes.byref(p)) == 0

@@ -151,9 +151,11 @@ def _oracle_Q(w):
     return vi["Q"].astype(np.float32)
 
 
-def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_beliefs=True, Qf=None):
+def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_beliefs=True, Qf=None,
+                 deepest_form=0):
     """Run both sides on the same inputs (leaf alpha-vectors Qf, float32
-    [5][n], the oracle's QMDP ones by default); return (gpu result, oracle tree)."""
+    [5][n], the oracle's QMDP ones by default); return (gpu result, oracle tree).
+    deepest_form: the GPU's form of the deepest fused level (QV_DEEPEST_*)."""
     seed = w.seed if seed is None else seed
     m = api.Model(w)
     Qf = _oracle_Q(w) if Qf is None else Qf
@@ -163,7 +165,7 @@ def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_be
                     store_levels=depth if check_beliefs else -1)
     replay = None
     r, plan = api.qv_tree_plan(m, Qd, b0, depth=depth, K=K, seed=seed, episode=w.episode,
-                               weight_mode=weight_mode, leaf_mode=leaf_mode, keep=True)
+                               weight_mode=weight_mode, leaf_mode=leaf_mode, keep=True, deepest_form=deepest_form)
     # sampled observations: identical except at flagged CDF boundaries
     for l in range(depth):
         lv = plan.level(0, l)
@@ -180,7 +182,8 @@ def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_be
         assert o["boundary_count"] > 0, "tree shapes differ without a boundary sample"
         r, plan = api.qv_tree_plan(m, Qd, b0, depth=depth, K=K, seed=seed, episode=w.episode,
                                    weight_mode=weight_mode, leaf_mode=leaf_mode,
-                                   replay=torch.from_numpy(o["samples_flat"].copy()).cuda(), keep=True)
+                                   replay=torch.from_numpy(o["samples_flat"].copy()).cuda(), keep=True,
+                                   deepest_form=deepest_form)
     assert r["nodes_per_level"] == [int(x) for x in o["n_level"]]
     for l in range(depth + 1):
         lv = plan.level(0, l)
@@ -211,6 +214,21 @@ def compare_tree(api, w, depth, K, leaf_mode, weight_mode=0, seed=None, check_be
 def test_tree_tiny(api, seed, leaf_mode):
     w = WL.tiny(seed)
     compare_tree(api, w, depth=2, K=4, leaf_mode=leaf_mode)
+
+
+@pytest.mark.parametrize("make,depth,K", [(lambda: WL.tiny(1), 2, 4), (lambda: WL.tiny(2, H=17, W=23), 3, 5),
+                                          (lambda: WL.mid(0), 3, 8)])
+def test_deepest_level_in_both_forms(api, make, depth, K):
+    """The deepest fused level in its per-child stencil form (QV_DEEPEST_STENCIL,
+    also the form a plan falls back to when the contraction's records do not
+    fit) and in its contraction form (the default), each against the oracle
+    tree, and the two roots against each other within the value tolerance."""
+    from paper_1810_00204_gb300 import _native as N
+    w = make()
+    rs, o = compare_tree(api, w, depth, K, 0, deepest_form=N.QV_DEEPEST_STENCIL, check_beliefs=False)
+    rc, _ = compare_tree(api, w, depth, K, 0, deepest_form=N.QV_DEEPEST_AUTO, check_beliefs=False)
+    _close(np.array([rc["value"]]), np.array([rs["value"]], np.float64), floor=1.0, what="root value, two forms")
+    _close(rc["q"], rs["q"].astype(np.float64), floor=1.0, what="root q, two forms")
 
 
 @pytest.mark.parametrize("weight_mode", [0, 1])
