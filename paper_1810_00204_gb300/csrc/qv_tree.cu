@@ -230,7 +230,10 @@ qv_status make_layout(int E, const qv_model_t *models, const qv_plan_params_t *p
     // sized for the largest grid so that sizing needs no device
     const long long per_sm = std::max<long long>(1, std::min<long long>(8, (228 * 1024) / std::max<size_t>(L.smem, 1)));
     const long long tmax = static_cast<long long>(L.items_per_cta) * kSizingSMs * per_sm;
-    L.n_xrec = (L.ctr ? 6 : 2) * tmax * L.cmax;
+    L.n_xrec = 2 * tmax * L.cmax;
+    // the contraction form's records: its items are cut at two per CTA
+    // whatever items_per_cta is, each with a record per child of its episode
+    if (L.ctr) L.n_xrec = std::max<long long>(L.n_xrec, 12LL * kSizingSMs * per_sm * L.cmax);
     L.n_frec = tmax * 30 * ((L.Bmax + 1) / 2) + 30LL * L.Bmax;
     long long gbase = 0, ibase = 0;
     long long run_g[QV_MAX_DEPTH + 1], run_i[QV_MAX_DEPTH + 1];
