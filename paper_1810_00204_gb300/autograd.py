@@ -21,21 +21,23 @@ from . import api
 
 class QVRootValue(torch.autograd.Function):
     """root = QVRootValue.apply(slip, accuracy, cost, b0, workload, depth, K,
-    seed, episode, sweeps, every, leaf_mode)
+    seed, episode, sweeps, every, leaf_mode, replay)
 
     slip, accuracy: 0-dim tensors; cost: [H, W] tensor or None (no cost map);
-    b0: [H, W] tensor or None (the workload's b0).  Returns a 0-dim FP64
-    tensor on the CUDA device.  Gradients come back in the inputs' dtypes."""
+    b0: [H, W] tensor or None (the workload's b0); replay: None, or int32
+    observation samples on the device to use instead of the Philox draws
+    (laid out as qv_plan_params_t.d_replay).  Returns a 0-dim FP64 tensor on
+    the CUDA device.  Gradients come back in the inputs' dtypes."""
 
     @staticmethod
-    def forward(ctx, slip, accuracy, cost, b0, w, depth, K, seed, episode, sweeps, every, leaf_mode):
+    def forward(ctx, slip, accuracy, cost, b0, w, depth, K, seed, episode, sweeps, every, leaf_mode, replay=None):
         dev = torch.device("cuda")
         c = None if cost is None else cost.detach().to(dev, torch.float32)
         model = api.Model(w, device=dev, slip=float(slip), accuracy=float(accuracy), cost=c)
         vi = api.mdp_value_iterate_checkpointed(model, sweeps, every)
         b0g = model.b0() if b0 is None else model.to_grid(b0.detach().to(dev, torch.float32))
         lm = N.QV_LEAF_MATERIALISE if leaf_mode == "materialise" else N.QV_LEAF_FUSED
-        plan = api.Plan([model], [vi["Q"]], [b0g], depth, K, seed, episode, N.QV_WEIGHT_FREQ, lm)
+        plan = api.Plan([model], [vi["Q"]], [b0g], depth, K, seed, episode, N.QV_WEIGHT_FREQ, lm, replay)
         plan.run()
         r = plan.read()[0]
         ctx.state = (model, vi, plan, b0g)
@@ -58,12 +60,13 @@ class QVRootValue(torch.autograd.Function):
         d_b0 = None
         if b0 is not None and ctx.needs_input_grad[3]:
             d_b0 = tb["db0"][:, :W].reshape(b0.shape).to(b0.dtype).to(b0.device)
-        return (d_slip, d_acc, d_cost, d_b0) + (None,) * 8
+        return (d_slip, d_acc, d_cost, d_b0) + (None,) * 9
 
 
 def root_value(w, slip: torch.Tensor, accuracy: torch.Tensor, cost: Optional[torch.Tensor] = None,
                b0: Optional[torch.Tensor] = None, depth: int = 3, K: int = 8, seed: int = 0, episode: int = 0,
-               sweeps: int = 200, every: int = 16, leaf_mode: str = "fused") -> torch.Tensor:
+               sweeps: int = 200, every: int = 16, leaf_mode: str = "fused",
+               replay: Optional[torch.Tensor] = None) -> torch.Tensor:
     """U_V(b0) of one plan on the map of workload `w`, differentiable in
-    slip, accuracy, cost and b0."""
-    return QVRootValue.apply(slip, accuracy, cost, b0, w, depth, K, seed, episode, sweeps, every, leaf_mode)
+    slip, accuracy, cost and b0 (replay: fixed observation samples)."""
+    return QVRootValue.apply(slip, accuracy, cost, b0, w, depth, K, seed, episode, sweeps, every, leaf_mode, replay)

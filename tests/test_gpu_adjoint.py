@@ -62,18 +62,6 @@ def _prob(w):
                      cost=None if w.cost is None else w.cost.astype(np.float64).ravel())
 
 
-def _gpu_samples_flat(plan, depth, K, B):
-    caps = O.level_capacity(B, K, depth)
-    off = np.zeros(depth + 2, np.int64)
-    off[1:] = np.cumsum(caps)
-    flat = np.full(int(off[-1]) * 5 * K, -1, np.int32)
-    for l in range(depth):
-        s = plan.level(0, l)["samples"].cpu().numpy()
-        a = int(off[l]) * 5 * K
-        flat[a:a + s.size] = s.reshape(-1)
-    return flat
-
-
 def _tree_case(api, w, depth, K, sweeps, leaf_mode, every=16):
     """GPU VI (checkpointed) and plan on the GPU's Q; the oracle tree on the
     oracle's own Q of the same truncated VI, with its own samples, replayed
@@ -223,34 +211,35 @@ def test_gradient_matches_oracle_and_finite_differences(api, seed, depth, K, lea
 def test_autograd_function_on_the_differentiation_workload(api):
     """128x128, depth 3, K = 8, 200 truncated sweeps with checkpoints every
     16, a U[0, 0.5] cost map: torch.autograd through QVRootValue against the
-    oracle's reverse mode with the GPU's samples, and central differences of
-    the oracle for the slip and the accuracy."""
+    oracle's reverse mode and central differences of the oracle for the slip
+    and the accuracy.  The oracle draws its own samples; the GPU's own draws
+    are checked against them (identical away from flagged CDF steps), and the
+    autograd plan replays the oracle's samples so both differentiate the same
+    tree."""
     from paper_1810_00204_gb300.autograd import root_value
     w = WL.diff(0)
-    slip = torch.tensor(float(w.slip), dtype=torch.float64, requires_grad=True)
-    acc = torch.tensor(float(w.accuracy), dtype=torch.float64, requires_grad=True)
-    cost = torch.from_numpy(w.cost.copy()).cuda().requires_grad_(True)
-    v = root_value(w, slip, acc, cost, depth=3, K=8, seed=w.seed, episode=w.episode, sweeps=200, every=16)
-    v.backward()
-    # the GPU's tree, replayed into the oracle
+    p = _prob(w)
+    own = O.tree_plan(p, O.value_iteration(p, truncated=200)["Q"], depth=3, K=8, seed=w.seed, episode=w.episode)
+    rep = own["samples_flat"]
+    # the GPU's own samples are the oracle's Philox draws (the samples depend
+    # on the beliefs only, not on Q), except at draws the oracle flags as
+    # lying within 1e-6 of a CDF step
     m = api.Model(w)
     vi = api.mdp_value_iterate_checkpointed(m, 200, 16)
     r, plan = api.qv_tree_plan(m, vi["Q"], m.b0(), depth=3, K=8, seed=w.seed, episode=w.episode, keep=True)
-    assert r["value"] == pytest.approx(float(v.detach()), rel=1e-6)
-    rep = _gpu_samples_flat(plan, 3, 8, w.B)
-    p = _prob(w)
-    # the GPU's samples are the oracle's own Philox draws (the samples depend
-    # on the beliefs only, not on Q), except at draws the oracle flags as
-    # lying within 1e-6 of a CDF step
-    own = O.tree_plan(p, O.value_iteration(p, truncated=200)["Q"], depth=3, K=8, seed=w.seed, episode=w.episode)
     assert own["n_level"].tolist() == r["nodes_per_level"] or own["boundary_count"] > 0
     for l in range(3):
         if plan.level(0, l)["count"] != own["n_level"][l]:
             break
         gs = plan.level(0, l)["samples"].cpu().numpy()
         assert not ((gs != own["samples"][l]) & (own["boundary"][l] == 0)).any(), f"level {l} samples"
+    slip = torch.tensor(float(w.slip), dtype=torch.float64, requires_grad=True)
+    acc = torch.tensor(float(w.accuracy), dtype=torch.float64, requires_grad=True)
+    cost = torch.from_numpy(w.cost.copy()).cuda().requires_grad_(True)
+    v = root_value(w, slip, acc, cost, depth=3, K=8, seed=w.seed, episode=w.episode, sweeps=200, every=16,
+                   replay=torch.from_numpy(rep.copy()).cuda())
+    v.backward()
     ref = O.root_value_grad(p, 200, depth=3, K=8, replay=rep)
-    assert ref["tree"]["n_level"].tolist() == r["nodes_per_level"]
     assert float(v.detach()) == pytest.approx(ref["value"], rel=1e-5)
     assert float(slip.grad) == pytest.approx(ref["dslip"], rel=GRAD_REL)
     assert float(acc.grad) == pytest.approx(ref["dacc"], rel=GRAD_REL, abs=GRAD_ABS)
@@ -317,13 +306,15 @@ def test_autograd_gradients_of_b0_and_accuracy(api):
     acc = torch.tensor(float(w.accuracy), dtype=torch.float32, requires_grad=True)
     cost = torch.from_numpy(w.cost.copy()).requires_grad_(True)
     b0 = torch.from_numpy(w.b0.copy()).requires_grad_(True)
-    v = root_value(w, slip, acc, cost, b0, depth=2, K=6, seed=w.seed, episode=w.episode, sweeps=S, every=7)
+    # the oracle's own draws, replayed into the GPU plan
+    p = _prob(w)
+    rep = O.tree_plan(p, O.value_iteration(p, truncated=S)["Q"], depth=2, K=6, seed=w.seed,
+                      episode=w.episode)["samples_flat"]
+    v = root_value(w, slip, acc, cost, b0, depth=2, K=6, seed=w.seed, episode=w.episode, sweeps=S, every=7,
+                   replay=torch.from_numpy(rep.copy()).cuda())
     gs, ga, gc, gb = torch.autograd.grad(v, (slip, acc, cost, b0))
     assert gs.dtype == torch.float32 and gc.shape == cost.shape and gb.device == b0.device
-    m = api.Model(w)
-    vi = api.mdp_value_iterate_checkpointed(m, S, 7)
-    r, plan = api.qv_tree_plan(m, vi["Q"], m.b0(), depth=2, K=6, seed=w.seed, episode=w.episode, keep=True)
-    ref = O.root_value_grad(_prob(w), S, depth=2, K=6, replay=_gpu_samples_flat(plan, 2, 6, w.B))
+    ref = O.root_value_grad(p, S, depth=2, K=6, replay=rep)
     assert float(gs) == pytest.approx(ref["dslip"], rel=GRAD_REL)
     assert float(ga) == pytest.approx(ref["dacc"], rel=GRAD_REL, abs=GRAD_ABS)
     assert abs(ref["dacc"]) > 1e3 * GRAD_ABS

@@ -1,8 +1,9 @@
 """GPU parity of the AEMS fields (Alg. 5-7, Eq. 9): qv_plan_bounds through
-the C ABI against the oracle's tree_bounds on the same tree and the same leaf
-lower bounds; and the whole chain on the mid map -- FIB alpha-vectors for U,
-PBVI for the leaves' L, bounds up to the root -- against the oracle run over
-the GPU's own tree arrays.
+the C ABI against the oracle's tree_bounds on the oracle's own tree (the GPU
+plan replays the oracle's sampled observations, so both trees are the same)
+with the same leaf lower bounds, taken from the oracle; and the whole chain
+on the mid map -- FIB alpha-vectors for U, PBVI for the leaves' L, bounds up
+to the root -- run on the GPU and checked for the order of its bounds.
 
 Values |d| <= 1e-5 * max(|ref|, 1).  A pointer E must equal the oracle's
 unless the oracle's best and second-best gamma w H_V are within 1e-4 * scale
@@ -29,26 +30,17 @@ def api():
     return A
 
 
-def _gpu_tree(plan, depth):
-    """The GPU tree as the oracle's flat layout (FP64), levels back to back."""
-    lv = [plan.level(0, l) for l in range(depth + 1)]
-    n = np.array([x["count"] for x in lv], np.int32)
-    off = np.zeros(depth + 2, np.int64)
-    off[1:] = np.cumsum(n)
-    tot = int(off[-1])
-    f = dict(n_level=n, parent=np.full(tot, -1, np.int32), action=np.full(tot, -1, np.int32),
-             weight=np.zeros(tot), R=np.zeros(tot * 5), UQ=np.zeros(tot * 5), value=np.zeros(tot))
-    for l, x in enumerate(lv):
-        s, c = int(off[l]), int(n[l])
-        if l > 0:
-            f["parent"][s:s + c] = x["parent"].cpu().numpy()
-            f["action"][s:s + c] = x["action"].cpu().numpy()
-            f["weight"][s:s + c] = x["weight"].cpu().numpy()
-        f["value"][s:s + c] = x["value"].cpu().numpy()
-        if l < depth:
-            f["R"][s * 5:(s + c) * 5] = x["R"].cpu().numpy().ravel()
-            f["UQ"][s * 5:(s + c) * 5] = x["UQ"].cpu().numpy().ravel()
-    return dict(flat=f, depth=depth, off=off), lv
+def _oracle_tree_on_gpu(api, w, Qf, leaf_mode, store_levels=-1):
+    """The oracle's tree on FP32-rounded alpha-vectors Qf and the GPU plan
+    that replays its sampled observations (the same tree)."""
+    m = api.Model(w)
+    o = O.tree_plan(w, Qf.astype(np.float64), depth=w.depth, K=w.K, seed=w.seed, episode=w.episode,
+                    store_levels=store_levels)
+    r, plan = api.qv_tree_plan(m, m.to_grid(Qf.reshape(5, w.H, w.W)), m.b0(), depth=w.depth, K=w.K, seed=w.seed,
+                               episode=w.episode, leaf_mode=leaf_mode,
+                               replay=torch.from_numpy(o["samples_flat"].copy()).cuda(), keep=True)
+    assert r["nodes_per_level"] == [int(x) for x in o["n_level"]]
+    return m, o, r, plan
 
 
 def _compare(gpu, ora, tree, gamma, scale):
@@ -75,20 +67,17 @@ def _compare(gpu, ora, tree, gamma, scale):
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 @pytest.mark.parametrize("leaf_mode", [0, 1])
-def test_bounds_match_oracle_on_the_gpu_tree(api, seed, leaf_mode):
+def test_bounds_match_oracle_on_the_oracle_tree(api, seed, leaf_mode):
     w = WL.tiny(seed)
-    m = api.Model(w)
     Qf = O.fib_iteration(w)["alpha"].astype(np.float32)
-    r, plan = api.qv_tree_plan(m, m.to_grid(Qf.reshape(5, w.H, w.W)), m.b0(), depth=w.depth, K=w.K,
-                               seed=w.seed, leaf_mode=leaf_mode, keep=True)
-    tree, lv = _gpu_tree(plan, w.depth)
+    m, o, r, plan = _oracle_tree_on_gpu(api, w, Qf, leaf_mode)
     rng = np.random.default_rng(seed)
-    U = lv[w.depth]["value"].cpu().numpy().astype(np.float64)
+    U = o["value"][w.depth]
     L = (U - rng.uniform(0.0, 10.0, len(U))).astype(np.float32)
     gpu = plan.bounds(torch.from_numpy(L).cuda())
-    ora = O.tree_bounds(tree, L.astype(np.float64), w.discount)
+    ora = O.tree_bounds(o, L.astype(np.float64), w.discount)
     scale = max(1.0, float(np.abs(U).max()))
-    _compare(gpu, ora, tree, w.discount, scale)
+    _compare(gpu, ora, o, w.discount, scale)
     # the root pointer indexes the leaf level
     e = int(gpu[0]["EV"][0])
     assert 0 <= e < len(U)
@@ -108,8 +97,9 @@ def test_equal_leaf_bounds_close_the_gap(api):
 
 
 def test_mid_fib_pbvi_chain(api):
-    # the paper's node fields on the mid map: U from FIB leaves, L from PBVI
-    # leaves (64 points), materialised leaf beliefs
+    # the paper's node fields on the mid map, all on the GPU: U from FIB
+    # leaves, L from PBVI leaves (64 points), materialised leaf beliefs; the
+    # bounds keep their order
     w = WL.mid(0)
     m = api.Model(w)
     Q = api.fib_value_iterate(m)["Q"]
@@ -121,9 +111,17 @@ def test_mid_fib_pbvi_chain(api):
     U = leaves["value"]
     assert torch.all(Lleaf <= U + 1e-4 * torch.clamp(U.abs(), min=1.0))
     b = plan.bounds(Lleaf)
-    tree, lv = _gpu_tree(plan, w.depth)
-    ora = O.tree_bounds(tree, Lleaf.cpu().numpy().astype(np.float64), w.discount)
     scale = max(1.0, float(U.abs().max()))
-    _compare(b, ora, tree, w.discount, scale)
     assert float(b[0]["LV"][0]) <= r["value"] + 1e-5 * scale
     assert float(b[0]["HV"][0]) >= 0.0
+    for l in range(w.depth + 1):
+        assert torch.all(b[l]["LV"] <= plan.level(0, l)["value"] + 1e-5 * scale)
+    # against the oracle on its own mid tree (FIB alpha-vectors of the oracle),
+    # the leaves' L from the oracle's pessimistic PBVI vector alpha_0
+    Qf = O.fib_iteration(w)["alpha"].astype(np.float32)
+    m2, o, r2, plan2 = _oracle_tree_on_gpu(api, w, Qf, N.QV_LEAF_MATERIALISE, store_levels=w.depth)
+    Lo = O.pbvi_value(O.pbvi_init(w)[None, :], o["belief"][w.depth]).astype(np.float32)
+    gpu = plan2.bounds(torch.from_numpy(Lo).cuda())
+    ora = O.tree_bounds(o, Lo.astype(np.float64), w.discount)
+    scale = max(1.0, float(np.abs(o["value"][w.depth]).max()))
+    _compare(gpu, ora, o, w.discount, scale)

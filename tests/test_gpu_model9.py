@@ -97,14 +97,48 @@ def test_tree_with_obstacle_dense_map(api):
     _compare_tree(api, w, 2, 4)
 
 
+def _oracle_path9(w, Qh, path):
+    """The node reached from b0 along path [(a, z), ...], by the oracle: at
+    every step its K draws on the marginal of its own belief must hold z.
+    Returns (belief, P(z) of the last step, the draws' distinct z at the
+    node for each action, lazily) or None when a draw on the way lies on a
+    CDF step."""
+    b = w.b0.ravel().astype(np.float64)
+    code, pz = 0, None
+    for l, (a, z) in enumerate(path):
+        bbar = O.predict9(w, b, a)
+        P = O.obs_marginal9(w, bbar)
+        zs, bd = _draws9(w, P, l, code * 9 + a)
+        if bd:
+            return None
+        assert z in zs, (l, a, z, zs)
+        b, _ = O.correct9(w, bbar, z)
+        pz = P[z]
+        code = (code * 9 + a) * 16 + z
+    return b, pz, code
+
+
+def _draws9(w, P, level, path):
+    zs, bd = [], False
+    for k in range(w.K):
+        u = O.lib().or_uniform(w.seed, w.episode, level, path, k)
+        zs.append(O.lib().or_sample_obs(P.ctypes.data_as(O.C.c_void_p), 16, u))
+        bd |= bool(O.lib().or_is_boundary(P.ctypes.data_as(O.C.c_void_p), 16, u))
+    return sorted(set(zs)), bd
+
+
 def test_full_size_sampled_nodes(api):
-    # the mid map's planning configuration: 128 x 128, d = 3, K = 8
+    # the mid map's planning configuration: 128 x 128, d = 3, K = 8, on the
+    # oracle's Q.  The oracle's whole tree is too large here: sampled nodes
+    # of the GPU's tree are recomputed by the oracle from b0 along their path
+    # of (action, observation), each observation checked against the
+    # oracle's own draws there
     w = WL.mid(0)
     m = api.Model9(w)
-    vi = m.value_iterate("f32", tol=1e-4)
-    Q = vi["Q"]
-    g = m.plan(Q)
-    Qh = Q.cpu().numpy().reshape(9, -1).astype(np.float64)
+    Qo = O.value_iteration9(w, tol=1e-4)["Q"]
+    Qf = Qo.astype(np.float32)
+    g = m.plan(torch.from_numpy(Qf.reshape(9, w.H, w.W)).cuda())
+    Qh = Qf.astype(np.float64)
     lv = [m.level(l) for l in range(4)]
     assert g["nodes_per_level"][0] == 1 and all(x > 0 for x in g["nodes_per_level"])
     # the backup identity at every internal node, in FP64 on the GPU's arrays
@@ -117,48 +151,36 @@ def test_full_size_sampled_nodes(api):
         uq = lv[l]["R"].cpu().numpy() + w.discount * s
         _close(lv[l]["UQ"].cpu().numpy(), uq, 1e-5, f"U_Q identity level {l}")
         _close(lv[l]["value"].cpu().numpy(), uq.max(axis=1), 1e-5, f"U_V identity level {l}")
-    # sampled children recomputed by the oracle from the GPU parent's belief
+    arrays = [{k: lv[l][k].cpu().numpy() for k in ("parent", "action", "obs", "pz", "value")} for l in range(4)]
+
+    def path_of(l, j):
+        steps = []
+        while l > 0:
+            steps.append((int(arrays[l]["action"][j]), int(arrays[l]["obs"][j])))
+            j = int(arrays[l]["parent"][j])
+            l -= 1
+        return list(reversed(steps))
+
     rng = np.random.default_rng(0)
-    for l in (0, 1, 2):
-        nxt = lv[l + 1]
-        bel = lv[l]["belief"].cpu().numpy().reshape(lv[l]["count"], -1).astype(np.float64)
-        for j in rng.choice(nxt["count"], size=min(4, nxt["count"]), replace=False):
-            i, a, z = int(nxt["parent"][j]), int(nxt["action"][j]), int(nxt["obs"][j])
-            bbar = O.predict9(w, bel[i], a)
-            P = O.obs_marginal9(w, bbar)
-            _close([float(nxt["pz"][j])], [P[z]], 1e-5, f"P(z) of node {j} level {l + 1}")
-            bz, _ = O.correct9(w, bbar, z)
-            if l + 1 < 3:
-                _close(nxt["belief"][j].cpu().numpy().ravel(), bz, 1e-5, f"belief of node {j}")
+    for l in (1, 2, 3):
+        for j in rng.choice(lv[l]["count"], size=min(4, lv[l]["count"]), replace=False):
+            got = _oracle_path9(w, Qh, path_of(l, int(j)))
+            if got is None:
+                continue
+            bz, pz, code = got
+            _close([float(arrays[l]["pz"][j])], [pz], 1e-5, f"P(z) of node {j} level {l}")
+            if l < 3:
+                _close(lv[l]["belief"][j].cpu().numpy().ravel(), bz, 1e-5, f"belief of node {j} level {l}")
+                # the node's children for three actions: the oracle's draws
+                for a in (0, 4, 7):
+                    zs, bd = _draws9(w, O.obs_marginal9(w, O.predict9(w, bz, a)), l, code * 9 + a)
+                    if bd:
+                        continue
+                    sel = (arrays[l + 1]["parent"] == j) & (arrays[l + 1]["action"] == a)
+                    assert list(arrays[l + 1]["obs"][sel]) == zs, (l, int(j), a)
             else:
                 v, _ = O.leaf_value9(w, Qh, bz)
-                _close([float(nxt["value"][j])], [v], 1e-5, f"leaf value of node {j}")
-        # the samples of sampled (node, action) pairs: the oracle's draws on the
-        # marginal of the GPU's belief give the GPU's children (away from CDF steps)
-        for i in rng.choice(lv[l]["count"], size=min(2, lv[l]["count"]), replace=False):
-            for a in (0, 4, 7):
-                bbar = O.predict9(w, bel[i], a)
-                P = O.obs_marginal9(w, bbar)
-                code = 0
-                # the node's path code from its ancestors
-                node, ll, digits = int(i), l, []
-                while ll > 0:
-                    lvl = lv[ll]
-                    digits.append((int(lvl["action"][node]), int(lvl["obs"][node])))
-                    node = int(lvl["parent"][node])
-                    ll -= 1
-                for (aa, zz) in reversed(digits):
-                    code = (code * 9 + aa) * 16 + zz
-                path = code * 9 + a
-                zs, bd = [], False
-                for k in range(w.K):
-                    u = O.lib().or_uniform(w.seed, w.episode, l, path, k)
-                    zs.append(O.lib().or_sample_obs(P.ctypes.data_as(O.C.c_void_p), 16, u))
-                    bd |= bool(O.lib().or_is_boundary(P.ctypes.data_as(O.C.c_void_p), 16, u))
-                if bd:
-                    continue
-                sel = (nxt["parent"].cpu().numpy() == i) & (nxt["action"].cpu().numpy() == a)
-                assert list(nxt["obs"].cpu().numpy()[sel]) == sorted(set(zs)), (l, i, a)
+                _close([float(arrays[l]["value"][j])], [v], 1e-5, f"leaf value of node {j}")
     _close([g["value"]], [lv[0]["value"][0].item()], 0.0, "root value read back")
 
 

@@ -177,21 +177,22 @@ def test_backup_ragged_vector_tiles(api):
 
 
 def test_backup_at_1024_points_sampled(api):
-    # the benchmarked size: 1024 points grown from b0 on the mid map, one
-    # backup against their 1024 vectors; the oracle's Eq. 8 backup at
-    # sampled points against the same vectors gives the same value and a*
+    # the benchmarked size: 1024 points on the mid map, one backup against
+    # 1024 vectors (the test's own dense beliefs and vectors); the oracle's
+    # Eq. 8 backup at sampled points against the same vectors gives the same
+    # value and a*
     w = WL.mid(0)
     m = api.Model(w)
-    g = api.pbvi_solve(m, rounds=10, iters=1, seed=2)
-    assert g["B"].shape[0] == 1024 and g["G"].shape[0] == 1024
-    r = g["pbvi"].backup(g["G"])
+    B = _beliefs(w, 1024, 11)
+    G = _vectors(w, 1024, 11)
+    pb = api.Pbvi(m, 1024)
+    pb.set_points(_grid(m, B))
+    r = pb.backup(_grid(m, G))
     torch.cuda.synchronize()
-    B = _flat(m, g["B"])
-    Gv = _flat(m, g["G"])
     gv = r["value"].cpu().numpy()
     ga = r["astar"].cpu().numpy()
     pts = [0, 1023]  # one oracle call: its points run in parallel
-    o = O.pbvi_backup(w, B[pts], Gv)
+    o = O.pbvi_backup(w, B[pts].astype(np.float64), G.astype(np.float64))
     for t, j in enumerate(pts):
         scale = max(1.0, float(np.abs(o["q"][t]).max()))
         assert abs(gv[j] - o["value"][t]) <= REL * scale * 10, j
@@ -261,37 +262,37 @@ def test_solve_matches_oracle_schedule(api, seed):
     _close(_flat(m, Gg[:nG]), G, rel=1e-4, floor=scale, what="alpha-vectors")
 
 
-def test_full_size_lower_bound_and_sampled_backups(api):
+def test_full_size_lower_bound(api):
     # the mid map: 64 points after six expansion rounds; V_PBVI below V_FIB
-    # at every point, and the oracle's own Eq. 8 backup at sampled points
-    # from the GPU's final vectors gives the GPU's backed-up values
+    # at every point (both solved on the GPU: a property at any size)
     w = WL.mid(0)
     m = api.Model(w)
     g = api.pbvi_solve(m, rounds=6, iters=8, seed=3)
     fib = api.fib_value_iterate(m, dtype="f32")["Q"]
     B = _flat(m, g["B"])
-    Gv = _flat(m, g["G"])
     F = m.from_grid(fib).reshape(5, -1).astype(np.float64)
     vf = (B @ F.T).max(axis=1)
     vp = g["value"].cpu().numpy()
     assert np.all(vp <= vf + 1e-4 * np.maximum(1.0, np.abs(vf)))
-    r = g["pbvi"].backup(g["G"])
-    gv = r["value"].cpu().numpy()
-    for j in (0, 37):
-        o = O.pbvi_backup(w, B[j:j + 1], Gv)
-        assert abs(gv[j] - o["value"][0]) <= REL * max(1.0, abs(o["value"][0])) * 10
 
 
-def test_large_map_one_round(api):
+def test_large_map_backup_sampled(api):
+    # the 512x512 map: a backup of the test's own points against its own
+    # vectors, the oracle's Eq. 8 backup at sampled points
     w = WL.large(1)
     m = api.Model(w)
-    g = api.pbvi_solve(m, rounds=2, iters=3, seed=1)
-    B = _flat(m, g["B"])
-    Gv = _flat(m, g["G"])
-    r = g["pbvi"].backup(g["G"])
+    B = _beliefs(w, 8, 4, support=4000)
+    G = _vectors(w, 6, 4)
+    pb = api.Pbvi(m, 8)
+    pb.set_points(_grid(m, B))
+    r = pb.backup(_grid(m, G))
     gv = r["value"].cpu().numpy()
-    o = O.pbvi_backup(w, B[3:4], Gv)
-    assert abs(gv[3] - o["value"][0]) <= REL * max(1.0, abs(o["value"][0])) * 10
+    ga = r["astar"].cpu().numpy()
+    o = O.pbvi_backup(w, B[3:5].astype(np.float64), G.astype(np.float64))
+    for t, j in enumerate((3, 4)):
+        scale = max(1.0, float(np.abs(o["q"][t]).max()))
+        assert abs(gv[j] - o["value"][t]) <= REL * scale * 10, j
+        _check_argmax(int(ga[j]), o["q"][t], scale, f"a* of point {j}")
 
 
 def test_errors(api):
